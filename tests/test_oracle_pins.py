@@ -1,0 +1,384 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks one oracle function against something other than itself:
+closed forms, invariants, special cases that reduce to a textbook result,
+brute force on small inputs, or the paper's printed statements.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2310_20374_gb300 import diskgen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- direct sum
+def test_direct_two_body_closed_form(oracle_lib):
+    # |a| = G m / r^2 along -r_hat (Sect. 3.2 direct summation)
+    pos = np.array([[1.0, 2.0, -0.5], [1.3, 1.6, 0.7]])
+    m = np.array([0.3, 2.5])
+    a = oracle_lib.direct_accel(pos, m, G=1.7)
+    r = pos[0] - pos[1]
+    d = np.linalg.norm(r)
+    np.testing.assert_allclose(a[0], -1.7 * m[1] * r / d ** 3, rtol=1e-14)
+    np.testing.assert_allclose(a[1], 1.7 * m[0] * r / d ** 3, rtol=1e-14)
+
+
+def test_direct_newton_third_law_and_cube_symmetry(oracle_lib):
+    d = diskgen.make_disk(500, 7)
+    a = oracle_lib.direct_accel(d["pos"], d["mass"])
+    tot = (d["mass"][:, None] * a).sum(0)
+    assert np.linalg.norm(tot) <= 1e-15 * np.abs(d["mass"][:, None] * a).sum()
+    corners = np.array(list(itertools.product([-1.0, 1.0], repeat=3))) * 0.7 + 3.0
+    pos = np.vstack([corners, [[3.0, 3.0, 3.0]]])
+    a = oracle_lib.direct_accel(pos, np.ones(9), targets=np.array([8]))
+    assert np.abs(a).max() < 1e-15
+
+
+# ------------------------------------------------- Green-function derivatives
+@pytest.mark.parametrize("R", [[0.3, -1.2, 0.7], [2.0, 0.1, -0.4]])
+def test_dtensor_low_orders_closed_form(oracle_lib, R):
+    R = np.array(R)
+    r = np.linalg.norm(R)
+    np.testing.assert_allclose(oracle_lib.dtensor(1, R), -R / r ** 3, rtol=1e-14)
+    D2 = (3 * np.outer(R, R) - r * r * np.eye(3)) / r ** 5
+    np.testing.assert_allclose(oracle_lib.dtensor(2, R), D2, rtol=1e-13, atol=1e-15)
+    D3 = np.zeros((3, 3, 3))
+    I = np.eye(3)
+    for i, j, k in itertools.product(range(3), repeat=3):
+        D3[i, j, k] = (-15 * R[i] * R[j] * R[k] + 3 * r * r * (R[i] * I[j, k] + R[j] * I[i, k] + R[k] * I[i, j])) / r ** 7
+    np.testing.assert_allclose(oracle_lib.dtensor(3, R), D3, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_dtensor_symmetric_traceless_and_finite_difference(oracle_lib, n):
+    R = np.array([0.8, -0.35, 0.52])
+    D = oracle_lib.dtensor(n, R)
+    scale = np.abs(D).max()
+    for perm in itertools.permutations(range(n)):
+        assert np.abs(np.transpose(D, perm) - D).max() <= 1e-13 * scale
+    # harmonic: every pair trace vanishes (Laplacian of 1/R is zero)
+    tr = np.trace(D, axis1=0, axis2=1)
+    assert np.abs(tr).max() <= 1e-12 * scale
+    # D^(n) is the gradient of D^(n-1) (Eq. gradient): central differences
+    h = 1e-5
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        fd = (oracle_lib.dtensor(n - 1, R + e) - oracle_lib.dtensor(n - 1, R - e)) / (2 * h)
+        assert np.abs(fd - D[..., j]).max() <= 1e-6 * scale
+
+
+# ---------------------------------------------------------------- P2M / M2M
+def _cluster(rng, k, centre, spread):
+    return rng.normal(size=(k, 3)) * spread + centre, rng.random(k) + 0.1
+
+
+def test_p2m_dipole_vanishes_about_barycentre(oracle_lib):
+    rng = np.random.default_rng(1)
+    x, mu = _cluster(rng, 40, [1.0, -2.0, 0.5], 0.3)
+    s = (mu[:, None] * x).sum(0) / mu.sum()
+    M = oracle_lib.p2m(4, x, mu, s)
+    assert abs(M[0] - mu.sum()) <= 1e-14 * mu.sum()
+    assert np.abs(M[1:4]).max() <= 1e-14 * mu.sum()
+    # order 2 is the plain second moment
+    d = x - s
+    np.testing.assert_allclose(M[4:13].reshape(3, 3), (mu[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0),
+                               rtol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_m2m_appendix_c_equals_direct_p2m(oracle_lib, p):
+    # App. C shift of each child's moments == P2M of all members about the parent centre
+    rng = np.random.default_rng(10 + p)
+    xs, mus = [], []
+    M_parent = np.zeros((3 ** p - 1) // 2)
+    kids = []
+    for c in range(5):
+        x, mu = _cluster(rng, 12, rng.normal(size=3) * 0.5, 0.15)
+        s = (mu[:, None] * x).sum(0) / mu.sum()
+        kids.append((oracle_lib.p2m(p, x, mu, s), s))
+        xs.append(x)
+        mus.append(mu)
+    X, MU = np.vstack(xs), np.concatenate(mus)
+    sB = (MU[:, None] * X).sum(0) / MU.sum()
+    for Mc, sc in kids:
+        M_parent += oracle_lib.m2m(p, Mc, sc, sB)
+    ref = oracle_lib.p2m(p, X, MU, sB)
+    for n in range(p):
+        if n == 1:
+            continue
+        a, b = M_parent[oracle_lib.off(n):oracle_lib.off(n + 1)], ref[oracle_lib.off(n):oracle_lib.off(n + 1)]
+        assert np.abs(a - b).max() <= 1e-13 * max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------- L2L / L2P
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_l2l_exact_on_polynomials(oracle_lib, p):
+    rng = np.random.default_rng(3)
+    C0 = rng.normal(size=(3 ** (p + 1) - 1) // 2)
+    C0[0] = 0.0
+    s0, s1, s2 = np.zeros(3), np.array([0.3, -0.1, 0.2]), np.array([0.1, 0.25, -0.3])
+    # symmetrise so that C is a proper symmetric tensor set
+    for m in range(1, p + 1):
+        T = C0[oracle_lib.off(m):oracle_lib.off(m + 1)].reshape((3,) * m)
+        S = sum(np.transpose(T, pp) for pp in itertools.permutations(range(m))) / math.factorial(m)
+        C0[oracle_lib.off(m):oracle_lib.off(m + 1)] = S.reshape(-1)
+    two_hops = oracle_lib.l2l(p, oracle_lib.l2l(p, C0, s0, s1), s1, s2)
+    one_hop = oracle_lib.l2l(p, C0, s0, s2)
+    assert np.abs(two_hops - one_hop).max() <= 1e-13 * np.abs(one_hop).max()
+    # L2P at the expansion centre gives C^(1) itself; L2P == L2L then read C^(1)
+    np.testing.assert_allclose(oracle_lib.l2p(p, C0, s0, s0), C0[1:4], rtol=1e-15)
+    np.testing.assert_allclose(oracle_lib.l2p(p, C0, s0, s2), one_hop[1:4], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------- M2L one pair
+def _pair_setup(rng, p, dist):
+    xa, ma = _cluster(rng, 25, [0, 0, 0], 0.1)
+    xb, mb = _cluster(rng, 25, dist, 0.1)
+    sA = (ma[:, None] * xa).sum(0) / ma.sum()
+    sB = (mb[:, None] * xb).sum(0) / mb.sum()
+    return xa, ma, sA, xb, mb, sB
+
+
+def test_m2l_error_decays_with_p_and_newton(oracle_lib):
+    errs = []
+    for p in range(1, 7):
+        rng = np.random.default_rng(5)
+        xa, ma, sA, xb, mb, sB = _pair_setup(rng, p, np.array([1.5, 0.6, -0.2]))
+        CA, CB = oracle_lib.m2l(p, sA, oracle_lib.p2m(p, xa, ma, sA), sB, oracle_lib.p2m(p, xb, mb, sB))
+        aA = np.array([oracle_lib.l2p(p, CA, sA, x) for x in xa])
+        aB = np.array([oracle_lib.l2p(p, CB, sB, x) for x in xb])
+        ref = np.array([-(mb[:, None] * (x - xb) / np.linalg.norm(x - xb, axis=1)[:, None] ** 3).sum(0) for x in xa])
+        errs.append(np.abs(aA - ref).max() / np.abs(ref).max())
+        FA, FB = (ma[:, None] * aA).sum(0), (mb[:, None] * aB).sum(0)
+        assert np.linalg.norm(FA + FB) <= 1e-14 * np.linalg.norm(FA)   # symmetric M2L: Newton's third law
+    # truncation error ~ ((rA+rB)/R)^(p+1): strictly decreasing, ~ 1e-5 at p = 6 here
+    assert all(errs[k + 1] < errs[k] for k in range(5)), errs
+    assert errs[-1] < 1e-4 and errs[0] > 1e-2
+
+
+def test_m2l_top_order_relation(oracle_lib):
+    # Sect. 3.4.3: M_A C^(p)_{B->A} = (-1)^p M_B C^(p)_{A->B}, same for p-1
+    for p in (2, 3, 5, 6):
+        rng = np.random.default_rng(p)
+        xa, ma, sA, xb, mb, sB = _pair_setup(rng, p, np.array([1.1, -0.7, 0.4]))
+        MA, MB = oracle_lib.p2m(p, xa, ma, sA), oracle_lib.p2m(p, xb, mb, sB)
+        CA, CB = oracle_lib.m2l(p, sA, MA, sB, MB)
+        for q in (p, p - 1):
+            lhs = MA[0] * CA[oracle_lib.off(q):oracle_lib.off(q + 1)]
+            rhs = (-1) ** q * MB[0] * CB[oracle_lib.off(q):oracle_lib.off(q + 1)]
+            assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(lhs).max()
+
+
+# ------------------------------------------------------------- theta(M)
+def test_theta_law(oracle_lib):
+    for tmin in (0.2, 0.5, 0.6, 0.8):
+        assert abs(oracle_lib.theta(3.0, 3.0, tmin) - tmin) <= 4e-16   # theta(M_tot) = theta_min
+        prev = tmin
+        for frac in (0.5, 1e-2, 1e-4, 1e-7):
+            t = oracle_lib.theta(frac * 3.0, 3.0, tmin)
+            lhs = t ** 5 / (1 - t) ** 2
+            rhs = tmin ** 5 / (1 - tmin) ** 2 * frac ** (-1.0 / 3.0)
+            assert abs(lhs - rhs) <= 1e-12 * rhs
+            assert prev < t < 1.0     # lighter cells get larger opening angles
+            prev = t
+
+
+# ------------------------------------------------------------- Hilbert keys
+@pytest.mark.parametrize("bits", [1, 2, 3, 4])
+def test_hilbert_bijection_adjacency_prefix(oracle_lib, bits):
+    side = 1 << bits
+    pts = np.array(list(itertools.product(range(side), repeat=3)), dtype=np.int64)
+    keys = np.array([oracle_lib.hilbert_key(*p, bits=bits) for p in pts], dtype=np.int64)
+    assert sorted(keys.tolist()) == list(range(side ** 3))          # bijection
+    walk = pts[np.argsort(keys)]
+    assert (np.abs(np.diff(walk, axis=0)).sum(1) == 1).all()         # face-adjacent steps
+    for lev in range(1, bits + 1):                                  # 3*lev-bit prefix = level-lev cell
+        cell = walk >> (bits - lev)
+        pref = np.sort(keys) >> (3 * (bits - lev))
+        change_cell = (np.diff(cell, axis=0) != 0).any(1)
+        change_pref = np.diff(pref) != 0
+        assert np.array_equal(change_cell, change_pref)
+
+
+def test_keys_root_cube_and_quantisation(oracle_lib):
+    d = diskgen.make_disk(2000, 3)
+    r, q, k = oracle_lib.keys(d["pos"])
+    L = r[3]
+    ext = (d["pos"].max(0) - d["pos"].min(0)).max()
+    assert L >= ext * (1 + 2 ** -20) and L / 2 < ext * (1 + 2 ** -20)
+    assert math.log2(L) == int(math.log2(L))                        # power of two
+    h = L / 2 ** 21
+    lo = r[:3] + q * h
+    assert ((d["pos"] >= lo - 1e-12) & (d["pos"] <= lo + h + 1e-12)).all()
+    assert len(np.unique(k)) == len(np.unique(q, axis=0))
+
+
+# ------------------------------------------------------------------ tree
+def test_tree_partition_and_split_rule(oracle_lib):
+    d = diskgen.make_disk(3000, 4)
+    s = 20
+    P = oracle_lib.params(p=3, leaf_size=s)
+    t = oracle_lib.tree_export(P, d["pos"], d["mass"])
+    r, q, k = oracle_lib.keys(d["pos"])
+    order, cells = t["order"], t["cells"]
+    assert np.array_equal(order, np.lexsort((np.arange(len(k)), k)))   # canonical (key, index)
+    lev = cells[:, 0]
+    assert (np.diff(lev) >= 0).all()
+    qs = q[order].astype(np.int64)
+    for lv, cx, cy, cz, first, cnt, nch in cells:
+        members = qs[first:first + cnt] >> (21 - lv)
+        assert (members == [cx, cy, cz]).all()
+        # brute-force count of that cube
+        assert ((q.astype(np.int64) >> (21 - lv)) == [cx, cy, cz]).all(1).sum() == cnt
+        assert (nch == 0) == (cnt <= s)
+    leaves = cells[cells[:, 6] == 0]
+    assert leaves[:, 5].sum() == len(k)
+
+
+def test_gravity_and_collision_geometry(oracle_lib):
+    d = diskgen.make_disk(2000, 5)
+    pos, vel, m, R = d["pos"], d["vel"], d["mass"], d["radius"]
+    P = oracle_lib.params(p=3, theta=0.5, leaf_size=16)
+    dt = 1e-3
+    t = oracle_lib.tree_export(P, pos, m, vel, R, dt)
+    Mtot = m.sum()
+    for (lv, cx, cy, cz, first, cnt, nch), g, c in zip(t["cells"], t["ggeo"], t["cgeo"]):
+        idx = t["order"][first:first + cnt]
+        M = m[idx].sum()
+        assert abs(g[0] - M) <= 1e-14 * M
+        s = (m[idx, None] * pos[idx]).sum(0) / M
+        assert np.abs(g[1:4] - s).max() <= 1e-14 * np.abs(s).max()
+        assert g[4] >= np.linalg.norm(pos[idx] - g[1:4], axis=1).max() * (1 - 1e-14)
+        assert abs(g[5] - g[4] / oracle_lib.theta(g[0], Mtot, 0.5)) <= 1e-15 * g[5]
+        sb = pos[idx].mean(0)
+        assert np.abs(c[:3] - sb).max() <= 1e-14 * np.abs(sb).max()
+        reach = np.linalg.norm(pos[idx] - c[:3], axis=1) + R[idx] + dt * np.linalg.norm(vel[idx], axis=1)
+        assert c[4] >= reach.max() * (1 - 1e-14)
+
+
+# ------------------------------------------------------------- whole falcON
+def test_falcon_reduces_to_direct_without_m2l(oracle_lib):
+    d = diskgen.make_disk(1500, 6)
+    ad = oracle_lib.direct_accel(d["pos"], d["mass"])
+    big = 10 ** 12
+    P = oracle_lib.params(p=4, theta=0.5, leaf_size=16, gravity_thresholds=(big, big, big))
+    a, st = oracle_lib.falcon_accel(P, d["pos"], d["mass"])
+    assert st["m2l"] == 0
+    assert np.abs(a - ad).max() <= 1e-13 * np.abs(ad).max()
+    P = oracle_lib.params(p=4, theta=1e-6, leaf_size=16)
+    a, st = oracle_lib.falcon_accel(P, d["pos"], d["mass"])
+    assert st["m2l"] == 0 and np.abs(a - ad).max() <= 1e-13 * np.abs(ad).max()
+
+
+def test_falcon_momentum_and_convergence_in_p(oracle_lib):
+    d = diskgen.make_disk(3000, 1)
+    pos, m = d["pos"], d["mass"]
+    ad = oracle_lib.direct_accel(pos, m)
+    ext = oracle_lib.external_accel(oracle_lib.params(), pos)
+    med, med_c = [], []
+    for p in range(1, 7):
+        P = oracle_lib.params(p=p, theta=0.5, leaf_size=24, gravity_thresholds=(64, 8, 64))
+        a, st = oracle_lib.falcon_accel(P, pos, m)
+        ma = m[:, None] * a
+        assert np.linalg.norm(ma.sum(0)) <= 1e-13 * np.abs(ma).sum()
+        med.append(np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)))
+        med_c.append(np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad + ext, axis=1)))
+    assert all(med[k + 1] < med[k] for k in range(5)), med
+    # Sect. 4.2: ~1e-5 at p = 3 and ~1e-7 at p = 6 (Earth gravity included): order of magnitude
+    with open(os.path.join(GOLDEN, "paper_accuracy.json")) as f:
+        g = json.load(f)
+    assert g["p3"] / 30 < med_c[2] < g["p3"] * 30
+    assert g["p6"] / 30 < med_c[5] < g["p6"] * 30
+
+
+# ------------------------------------------------------------- collisions
+def _coll(oracle_lib, x1, v1, R1, x2, v2, R2, dt):
+    return oracle_lib.collide_pair(np.array(x1, float), np.array(v1, float), R1,
+                                   np.array(x2, float), np.array(v2, float), R2, dt)
+
+
+def test_collision_predicate_closed_forms(oracle_lib):
+    # head-on: gap d - R1 - R2 = 0.5 closed at speed 1 -> dt_c = 0.5
+    assert _coll(oracle_lib, [0, 0, 0], [1, 0, 0], 0.25, [1, 0, 0], [0, 0, 0], 0.25, 0.5)       # dt_c == dt
+    assert not _coll(oracle_lib, [0, 0, 0], [1, 0, 0], 0.25, [1, 0, 0], [0, 0, 0], 0.25, 0.4375)
+    assert _coll(oracle_lib, [0, 0, 0], [1, 0, 0], 0.25, [1, 0, 0], [0, 0, 0], 0.25, 0.75)
+    # receding pair, zero relative velocity, already overlapping (dt_c < 0)
+    assert not _coll(oracle_lib, [0, 0, 0], [-1, 0, 0], 0.25, [1, 0, 0], [0, 0, 0], 0.25, 10.0)
+    assert not _coll(oracle_lib, [0, 0, 0], [1, 2, 3], 0.25, [1, 0, 0], [1, 2, 3], 0.25, 10.0)
+    assert not _coll(oracle_lib, [0, 0, 0], [1, 0, 0], 0.75, [1, 0, 0], [0, 0, 0], 0.75, 10.0)
+    # grazing: impact parameter exactly R1+R2 gives Delta = 0 -> contact at the closest point
+    assert _coll(oracle_lib, [0, 0.5, 0], [1, 0, 0], 0.25, [2, 0, 0], [0, 0, 0], 0.25, 2.0)
+    assert not _coll(oracle_lib, [0, 0.5, 0], [1, 0, 0], 0.25, [2, 0, 0], [0, 0, 0], 0.25, 1.5)
+    assert not _coll(oracle_lib, [0, 0.5000001, 0], [1, 0, 0], 0.25, [2, 0, 0], [0, 0, 0], 0.25, 5.0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_collision_tree_equals_brute_small(oracle_lib, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 65))
+    pos = rng.random((n, 3))
+    vel = rng.normal(size=(n, 3))
+    R = rng.random(n) * 0.05 + 0.01
+    dt = 0.05
+    brute = oracle_lib.collide_brute(pos, vel, R, dt)
+    P = oracle_lib.params(p=3, leaf_size=int(rng.integers(1, 9)))
+    tree, st = oracle_lib.collide_tree(P, pos, vel, R, dt)
+    assert np.array_equal(brute, tree)
+    assert st["col_found"] == len(brute)
+
+
+def test_collision_tree_equals_brute_disk(oracle_lib):
+    # a narrow, thick ring of large moonlets so that a step sees dozens of impacts
+    d = diskgen.make_disk(3000, 9, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
+    P = oracle_lib.params(p=3, leaf_size=17)
+    brute = oracle_lib.collide_brute(d["pos"], d["vel"], d["radius"], 0.05)
+    tree, st = oracle_lib.collide_tree(P, d["pos"], d["vel"], d["radius"], 0.05)
+    assert len(brute) > 5
+    assert np.array_equal(brute, tree)
+    assert st["col_tests"] < 3000 * 2999 // 20   # the walk prunes most pairs
+
+
+# ------------------------------------------------------------------ KDK
+def test_kdk_kepler_energy_bounded_and_reversible(oracle_lib):
+    P = oracle_lib.params(p=3, leaf_size=8)
+    pos = np.array([[2.0, 0.0, 0.0], [0.0, 3.0, 0.1]])
+    vel = np.array([[0.0, 0.8, 0.05], [-0.55, 0.0, 0.0]])
+    m = np.array([1e-12, 1e-12])
+    R = np.array([1e-6, 1e-6])
+
+    def energy(x, v):
+        return 0.5 * (v * v).sum(1) - 1.0 / np.linalg.norm(x, axis=1)
+
+    e0 = energy(pos, vel)
+    x, v, a = pos, vel, None
+    errs = []
+    for chunk in range(24):      # ~8 periods of the outer orbit, step 0.05
+        x, v, a, _ = oracle_lib.kdk(P, x, v, m, R, 0.05, 100, acc0=a)
+        errs.append(np.abs(energy(x, v) - e0).max())
+    errs = np.array(errs)
+    assert errs.max() < 1e-3 and errs[12:].max() < 2 * errs[:12].max()   # bounded, not secular
+    # time reversibility
+    d = diskgen.make_disk(300, 11)
+    P = oracle_lib.params(p=3, leaf_size=16)
+    x1, v1, a1, _ = oracle_lib.kdk(P, d["pos"], d["vel"], d["mass"], d["radius"], 1e-3, 10)
+    x2, v2, _, _ = oracle_lib.kdk(P, x1, v1, d["mass"], d["radius"], -1e-3, 10, acc0=a1)
+    assert np.abs(x2 - d["pos"]).max() <= 1e-13 * np.abs(d["pos"]).max()
+    assert np.abs(v2 - d["vel"]).max() <= 1e-12 * np.abs(d["vel"]).max()
+
+
+def test_external_forces(oracle_lib):
+    P = oracle_lib.params(G=2.0, central_mass=3.0)
+    x = np.array([[1.0, 2.0, 2.0]])
+    np.testing.assert_allclose(oracle_lib.external_accel(P, x), -6.0 * x / 27.0, rtol=1e-15)
+    # star tide (App. B.3): at t = 0 the star sits on +x; a moonlet on the x axis is pulled outward by 2 G Ms x / a^3
+    P = oracle_lib.params(G=1.0, central_mass=0.0, star=(5.0, 40.0, 0.4))
+    a = oracle_lib.external_accel(P, np.array([[0.5, 0.0, 0.0], [0.0, 0.5, 0.0]]), 0.0)
+    np.testing.assert_allclose(a[0], [2 * 5.0 * 0.5 / 40.0 ** 3, 0, 0], rtol=1e-14, atol=1e-20)
+    np.testing.assert_allclose(a[1], [0, -5.0 * 0.5 / 40.0 ** 3, 0], rtol=1e-14, atol=1e-20)
