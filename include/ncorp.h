@@ -1,0 +1,169 @@
+/*
+ * ncorp.h -- C ABI of the GB300 falcON step library (libncorp.so).
+ *
+ * The library computes one O(N) falcON step for a disk of N moonlets orbiting
+ * a central mass, as described by Couturier, Quillen & Nakajima (arXiv
+ * 2310.20374): Hilbert-key sort and octree build (Sect. 3.4.1, 3.4.6), tree
+ * climbing with P2M/M2M multipoles (Sect. 3.4.2, Eq. multipole_moment,
+ * App. C), the symmetric dual-tree walk of Algorithm TreeWalk (Sect. 3.4.5)
+ * with M2L (Eq. phi_expanded), near-field direct gravity and a tree-based
+ * collision search (Sect. 3.1), and the tree descent L2L/L2P (Eq. shifting),
+ * inside an SBAB1 kick-drift-kick leapfrog with merged kicks (Sect. 4.1) and
+ * the central-body / distant-star forces of App. B.1 and B.3.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: NCORP_OK (0) or a negative
+ *     NCORP_E* code.  ncorp_last_error() gives a message for the last failure
+ *     on that context.  No C++ exception crosses this interface.
+ *   - Array arguments may point to host memory or to device memory on the
+ *     context's device; the library tells them apart with
+ *     cudaPointerGetAttributes.  Host arrays are copied in and out inside the
+ *     call.  The library never frees or retains caller memory.
+ *   - Vectors are laid out [n][3] (x, y, z interleaved), doubles, row-major.
+ *   - All device work is enqueued on the context's CUDA stream; every call
+ *     synchronises that stream before it returns (to read the status word),
+ *     so outputs are ready when the call returns.
+ *   - Units are the caller's; the configuration fixes G and the central mass.
+ *   - Invalid arguments (n < 1, p outside 1..6, theta outside (0,1), dt <= 0
+ *     where a time step is needed, null pointers, non-finite inputs) return
+ *     NCORP_EINVAL before any device work.
+ */
+#ifndef NCORP_H
+#define NCORP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NCORP_OK         0
+#define NCORP_EINVAL    -1   /* bad argument */
+#define NCORP_ENOMEM    -2   /* device or host allocation failed */
+#define NCORP_ECUDA     -3   /* a CUDA call failed; see ncorp_last_error */
+#define NCORP_EOVERFLOW -4   /* an output did not fit the caller's capacity */
+#define NCORP_ETIMEOUT  -5   /* a bounded device-side wait gave up */
+#define NCORP_ESTATE    -6   /* call out of sequence (e.g. no state yet) */
+
+#define NCORP_FP64  0        /* every stage in FP64 */
+#define NCORP_MIXED 1        /* multipoles, M2L, P2P, L2L/L2P in FP32 with per-cell scaling;
+                                positions, velocities, kicks/drifts, external forces, keys,
+                                tree geometry and the collision test in FP64 */
+
+typedef struct ncorp_ctx ncorp_ctx;
+
+typedef struct {
+    double G;                 /* gravitational constant */
+    double central_mass;      /* M_c (App. B.1) */
+    double central_radius;    /* R_c (informational; collisions with the central body are not searched) */
+    int leaf_size;            /* s: cells with more than s moonlets are split (Sect. 3.4.1); 0 = default for p */
+    int n_cs, n_cc_pre, n_cc_post;  /* gravity TreeWalk thresholds (Sect. 3.4.5); all 0 = defaults for p */
+    int c_cs, c_cc_pre, c_cc_post;  /* collision TreeWalk thresholds; all 0 = 12, 0, 16 (Sect. 4.2) */
+    int precision;            /* NCORP_FP64 or NCORP_MIXED */
+    int collisions;           /* 1: search colliding pairs in every step's drift (Sect. 4.1) */
+    double star_mass;         /* distant star (App. B.3); 0 disables the tidal term */
+    double star_a;            /* star orbital radius */
+    double star_obliquity;    /* obliquity epsilon of the central body (radians) */
+    double t0;                /* initial time (sets the star's longitude n t) */
+} ncorp_config;
+
+/* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
+ * NCORP_MIXED, collisions on, no star. */
+void ncorp_config_default(ncorp_config *cfg);
+
+/* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream); the
+ * context allocates its own device workspace (it grows on demand).
+ * Errors: NCORP_EINVAL (null out/cfg, n_max < 1, bad config), NCORP_ECUDA,
+ * NCORP_ENOMEM. */
+int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream);
+
+/* Changes the stream later calls enqueue their work on. */
+int ncorp_set_stream(ncorp_ctx *ctx, void *cuda_stream);
+
+/* One SBAB1 step (Sect. 4.1): v += dt/2 a(x); collision search on (x, v)
+ * during the drift (Sect. 3.1, Algorithm TreeWalk); x += dt v; rebuild the
+ * tree and compute a(x) = falcON mutual gravity + central (+ star); v += dt/2 a.
+ * positions/velocities [n][3] are read and overwritten with the new state in
+ * the caller's order; masses/radii [n] are read.
+ * Kicks are merged across calls: the acceleration and tree of the previous
+ * call's final positions are kept on the device and reused when the next call
+ * passes the same position/velocity/mass/radius pointers, the same n, p and
+ * theta and the context was not used by ncorp_accel/ncorp_collide in between;
+ * call ncorp_reset() after changing the arrays' contents yourself.
+ * The pairs found are kept for ncorp_collisions().
+ * Errors: NCORP_EINVAL, NCORP_ECUDA, NCORP_ENOMEM, NCORP_ETIMEOUT. */
+int ncorp_step(ncorp_ctx *ctx, double *positions, double *velocities, const double *masses,
+               const double *radii, int64_t n, int p, double theta, double dt);
+
+/* Forgets the resident state, so the next ncorp_step re-reads its inputs. */
+int ncorp_reset(ncorp_ctx *ctx);
+
+/* Colliding pairs found by the last ncorp_step or ncorp_collide: rows (i, j)
+ * of caller indices with i < j, sorted lexicographically, no duplicates.
+ * pairs: [cap][2] int64 (host or device); *n_pairs receives the total found.
+ * If the total exceeds cap, the first cap rows are written and
+ * NCORP_EOVERFLOW is returned (nothing is lost: call again with more room). */
+int ncorp_collisions(ncorp_ctx *ctx, int64_t *pairs, int64_t cap, int64_t *n_pairs);
+
+/* Accelerations at the given positions (one tree build, climb, walk, M2L,
+ * near field and descent): acc [n][3] = mutual + central (+ star at the
+ * context's time); acc_mutual [n][3] (nullable) = falcON mutual part only.
+ * Invalidates the resident step state.  Errors as ncorp_step. */
+int ncorp_accel(ncorp_ctx *ctx, const double *positions, const double *masses, int64_t n, int p,
+                double theta, double *acc, double *acc_mutual);
+
+/* Collision search alone (Sect. 3.1, tree climb for collisions of Sect.
+ * 3.4.2, Algorithm TreeWalk) on the given positions and velocities over a
+ * step dt, with the tree of those positions.  Results via ncorp_collisions.
+ * Invalidates the resident step state.  Errors as ncorp_step. */
+int ncorp_collide(ncorp_ctx *ctx, const double *positions, const double *velocities,
+                  const double *radii, int64_t n, double dt);
+
+/* Copies the resident state (caller order) into positions/velocities [n][3].
+ * NCORP_ESTATE if no step has run since init/reset. */
+int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
+
+/* Counters of the last call (int64 slots, see NCORP_STAT_*); writes
+ * min(n_stats, NCORP_NSTATS) values to host memory. */
+#define NCORP_STAT_CELLS        0
+#define NCORP_STAT_LEAVES       1
+#define NCORP_STAT_DEPTH        2
+#define NCORP_STAT_M2L          3   /* well-separated cell pairs (gravity walk) */
+#define NCORP_STAT_P2P_PAIRS    4   /* cell pairs treated directly (gravity walk decisions) */
+#define NCORP_STAT_P2P_SELF     5   /* cells treated directly with themselves (gravity) */
+#define NCORP_STAT_P2P_INTER    6   /* particle pairs summed directly (gravity, unordered) */
+#define NCORP_STAT_COL_PAIRS    7   /* cell pairs searched directly (collision walk decisions) */
+#define NCORP_STAT_COL_SELF     8
+#define NCORP_STAT_COL_TESTS    9   /* moonlet pairs examined by the collision test */
+#define NCORP_STAT_COL_FOUND   10
+#define NCORP_STAT_WALK_ITERS  11   /* frontier iterations of the last walk */
+#define NCORP_STAT_M2L_DIRECTED 12  /* directed M2L entries evaluated */
+#define NCORP_STAT_P2P_DIRECTED 13  /* directed leaf-source entries evaluated */
+#define NCORP_NSTATS           16
+int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
+
+/* Diagnostic export of the tree of the last ncorp_accel/ncorp_collide/ncorp_step
+ * (level-major cells, Hilbert order within a level), for parity checks.
+ * Any output may be NULL; all are host or device arrays:
+ *   order [n] int64: caller index of the i-th moonlet in tree order
+ *   keys  [n] uint64: 63-bit Hilbert key of the i-th moonlet in tree order
+ *   root  [4] double: x_lo, y_lo, z_lo, L of the root cube
+ *   cells [cap][7] int64: level, cx, cy, cz, first, count, n_children
+ *   ggeo  [cap][6] double: M, s_x, s_y, s_z, r_max, r_crit (gravity climb)
+ *   cgeo  [cap][5] double: sbar_x, sbar_y, sbar_z, r_max, r_crit (collision climb)
+ * *n_cells receives the number of cells; NCORP_EOVERFLOW if it exceeds cap. */
+int ncorp_tree_export(ncorp_ctx *ctx, int64_t *order, uint64_t *keys, double *root, int64_t *cells,
+                      double *ggeo, double *cgeo, int64_t cap, int64_t *n_cells);
+
+/* Releases the context and its device workspace (NULL is ignored). */
+void ncorp_free(ncorp_ctx *ctx);
+
+/* Message of the last failure on ctx (static storage owned by ctx; never NULL). */
+const char *ncorp_last_error(const ncorp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCORP_H */

@@ -1,0 +1,121 @@
+// collide.cu -- the pairwise collision test of Sect. 3.1 over the direct lists
+// of the collision walk, and the sorting of the colliding pairs.
+//
+// Straight-line trajectories over the step: with dr = r1 - r2, dv = v1 - v2,
+//   Delta = (dr.dv)^2 + dv^2 ((R1 + R2)^2 - dr^2),
+//   dt_c  = -(dr.dv + sqrt(Delta)) / dv^2,
+// the pair collides within the step iff Delta >= 0 and 0 <= dt_c <= dt
+// (dv = 0: no collision).  Evaluated in FP64 with exactly rounded operations
+// in a fixed order, (1, 2) being the pair in increasing caller index, so that
+// the set of pairs is reproducible bit for bit.
+#include "ctx.h"
+
+namespace ncorp {
+
+__device__ __forceinline__ bool collide_test(double x1, double y1, double z1, double u1, double v1, double w1,
+                                             double R1, double x2, double y2, double z2, double u2, double v2,
+                                             double w2, double R2, double dt) {
+    const double dx = dsub(x1, x2), dy = dsub(y1, y2), dz = dsub(z1, z2);
+    const double ux = dsub(u1, u2), uy = dsub(v1, v2), uz = dsub(w1, w2);
+    const double b = dadd(dadd(dmul(dx, ux), dmul(dy, uy)), dmul(dz, uz));
+    const double dr2 = dsq3(dx, dy, dz);
+    const double dv2 = dsq3(ux, uy, uz);
+    if (dv2 == 0.0) return false;
+    const double Rs = dadd(R1, R2);
+    const double Delta = dadd(dmul(b, b), dmul(dv2, dsub(dmul(Rs, Rs), dr2)));
+    if (Delta < 0.0) return false;
+    const double tc = ddiv(-dadd(b, dsqrt(Delta)), dv2);
+    return tc >= 0.0 && tc <= dt;
+}
+
+struct CollideArgs {
+    const int2 *p2p;
+    const int *self;
+    const int *first, *count;
+    const double *x, *y, *z, *vx, *vy, *vz, *R;
+    const int *perm;
+    double dt;
+    uint64_t *pairs;
+    int cap, self_cap, p2p_cap;
+    Ctrl *ctl;
+};
+
+__device__ __forceinline__ void test_and_emit(const CollideArgs &A, int u, int v) {
+    int a = u, b = v;
+    if (A.perm[a] > A.perm[b]) {
+        a = v;
+        b = u;
+    }
+    if (collide_test(A.x[a], A.y[a], A.z[a], A.vx[a], A.vy[a], A.vz[a], A.R[a], A.x[b], A.y[b], A.z[b], A.vx[b],
+                     A.vy[b], A.vz[b], A.R[b], A.dt)) {
+        const int slot = atomicAdd(&A.ctl->n_found, 1);
+        if (slot < A.cap)
+            A.pairs[slot] = (static_cast<unsigned long long>(A.perm[a]) << 32) | static_cast<unsigned>(A.perm[b]);
+        else
+            atomicOr(&A.ctl->err, ERR_PAIRS);
+    }
+}
+
+__global__ void k_collide(CollideArgs A) {
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
+    const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    long long tests = 0;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ns + np; w += nwarps) {
+        if (w < ns) {
+            const int c = A.self[w];
+            const int f = A.first[c], cnt = A.count[c];
+            for (int u = lane; u < cnt; u += 32)
+                for (int v = u + 1; v < cnt; v++) test_and_emit(A, f + u, f + v);
+            if (lane == 0) tests += static_cast<long long>(cnt) * (cnt - 1) / 2;
+        } else {
+            const int2 e = A.p2p[w - ns];
+            const int fa = A.first[e.x], ca = A.count[e.x], fb = A.first[e.y], cb = A.count[e.y];
+            for (int u = lane; u < ca; u += 32)
+                for (int v = 0; v < cb; v++) test_and_emit(A, fa + u, fb + v);
+            if (lane == 0) tests += static_cast<long long>(ca) * cb;
+        }
+    }
+    if (lane == 0 && tests)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_tests), static_cast<unsigned long long>(tests));
+}
+
+void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
+                    double dt) {
+    CollideArgs A;
+    A.p2p = c->wl.p2p; A.self = c->wl.self;
+    A.first = c->cells.first; A.count = c->cells.count;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.vx = vx; A.vy = vy; A.vz = vz; A.R = P.R;
+    A.perm = P.perm;
+    A.dt = dt;
+    A.pairs = c->pairs;
+    A.cap = c->pair_cap;
+    A.self_cap = c->wl.self_cap;
+    A.p2p_cap = c->wl.p2p_cap;
+    A.ctl = c->ctl;
+    k_collide<<<8 * c->num_sms, 256, 0, c->stream>>>(A);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+__global__ void k_unpack_pairs(const uint64_t *__restrict__ packed, int64_t *__restrict__ out, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const uint64_t v = packed[i];
+        out[2 * i] = static_cast<int64_t>(v >> 32);
+        out[2 * i + 1] = static_cast<int64_t>(v & 0xffffffffull);
+    }
+}
+
+void launch_sort_pairs(ncorp_ctx *c, int count) {
+    if (count <= 0) return;
+    launch_iota(c, c->pair_idx, count);
+    radix_sort_u64(c, c->pairs, c->pair_idx, c->pairs_alt, c->pair_idx_alt, count, 64);
+}
+
+void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count) {
+    if (count <= 0) return;
+    k_unpack_pairs<<<grid_for(count, 256, 4 * c->num_sms), 256, 0, c->stream>>>(packed, out, count);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace ncorp

@@ -1,0 +1,194 @@
+// common.cuh -- device-side definitions shared by the falcON step kernels.
+//
+// Symmetric Cartesian tensors (Sect. 3.4.3: an order-n symmetric tensor has
+// (n+1)(n+2)/2 independent components) are stored by multi-index
+// alpha = (a, b, c), a + b + c = n: within order n the components run over
+// k = n - a = 0..n and, for each k, c = 0..k (b = k - c).  Orders are packed
+// one after the other; order n starts at n(n+1)(n+2)/6.
+//   multipoles M-hat: orders 0, 2..p-1 (the dipole vanishes about the centre
+//                     of mass, Sect. 3.4.3), p = 6 -> 53 values
+//   locals C-hat:     orders 1..p (C^(0) is never needed), p = 6 -> 83 values
+//   derivatives D:    orders 0..p
+//
+// Scaled storage (per cell, rho = a power of two >= r_max of the cell):
+//   M-hat_beta = M_beta / (beta! rho^|beta|),   C-hat_alpha = C_alpha rho^|alpha|
+// which keeps every stored coefficient within a few orders of magnitude of the
+// cell mass (or of the field) whatever the cell size, so that FP32 storage and
+// arithmetic lose nothing to the exponent range.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ncorp {
+
+constexpr int MAXP = 6;
+constexpr int KEY_BITS = 21;                 // bits per axis of the quantised coordinates
+constexpr int MAX_LEVEL = KEY_BITS;          // deepest tree level
+
+__host__ __device__ constexpr int tri(int k) { return k * (k + 1) / 2; }
+__host__ __device__ constexpr int nsym(int n) { return (n + 1) * (n + 2) / 2; }
+__host__ __device__ constexpr int off(int n) { return n * (n + 1) * (n + 2) / 6; }
+// packed index of multi-index (a, b, c) among all orders
+__host__ __device__ constexpr int sidx(int a, int b, int c) { return off(a + b + c) + tri(b + c) + c; }
+// multipole index (orders 0, 2, 3, ...)
+__host__ __device__ constexpr int midx(int a, int b, int c) { return (a + b + c) >= 2 ? sidx(a, b, c) - 3 : 0; }
+// local-coefficient index (orders 1..p)
+__host__ __device__ constexpr int cidx(int a, int b, int c) { return sidx(a, b, c) - 1; }
+__host__ __device__ constexpr int num_m(int p) { return p >= 2 ? off(p) - 3 : 1; }
+__host__ __device__ constexpr int num_c(int p) { return off(p + 1) - 1; }
+__host__ __device__ constexpr int num_d(int p) { return off(p + 1); }
+__host__ __device__ constexpr double ifact(int n) {
+    return n <= 1 ? 1.0 : n == 2 ? 0.5 : n == 3 ? 1.0 / 6.0 : n == 4 ? 1.0 / 24.0 : n == 5 ? 1.0 / 120.0
+         : n == 6 ? 1.0 / 720.0 : 1.0 / 5040.0;
+}
+__host__ __device__ constexpr double inv_mfact(int a, int b, int c) { return ifact(a) * ifact(b) * ifact(c); }
+// 1/n! for run-time n (0..7)
+static __constant__ double c_ifact[8] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0};
+
+// ---- exactly rounded FP64 (never contracted into FMA) --------------------
+// Tree geometry, walk decisions, keys, kicks/drifts and the collision test use
+// these so that their results are bit-identical to a plain IEEE evaluation in
+// the written order.
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double dnorm3(double x, double y, double z) {
+    return dsqrt(dadd(dadd(dmul(x, x), dmul(y, y)), dmul(z, z)));
+}
+__device__ __forceinline__ double dsq3(double x, double y, double z) {
+    return dadd(dadd(dmul(x, x), dmul(y, y)), dmul(z, z));
+}
+
+// smallest power of two >= v (v > 0), exact; 1 for v <= 0
+__device__ __forceinline__ double pow2_ceil(double v) {
+    if (!(v > 0.0)) return 1.0;
+    int e;
+    double f = frexp(v, &e);           // v = f 2^e, f in [0.5, 1)
+    return f == 0.5 ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+// ---- error word -----------------------------------------------------------
+enum : int {
+    ERR_CELLS = 1,        // cell capacity exceeded
+    ERR_FRONTIER = 2,     // walk frontier capacity exceeded
+    ERR_M2L = 4,          // M2L list capacity exceeded
+    ERR_P2P = 8,          // direct list capacity exceeded
+    ERR_PAIRS = 16,       // collision pair buffer exceeded
+    ERR_TIMEOUT = 32,     // a bounded grid barrier gave up
+    ERR_DIRECTED = 64,    // directed list capacity exceeded
+    ERR_LEVEL = 128,      // internal: tree deeper than MAX_LEVEL
+    ERR_NONFINITE = 256,  // a position was NaN or infinite
+};
+
+constexpr int ERR_ABORT_MASK = ERR_CELLS | ERR_FRONTIER | ERR_M2L | ERR_P2P | ERR_TIMEOUT | ERR_DIRECTED | ERR_LEVEL;
+
+// Device control block: counters written by kernels, read back by the host.
+struct Ctrl {
+    int err;
+    int n_cells;
+    int n_leaves;
+    int max_level;
+    int level_start[MAX_LEVEL + 3];
+    int frontier_count[2];
+    int n_m2l;             // unordered well-separated pairs
+    int n_p2p;             // leaf-leaf direct pairs
+    int n_self;            // leaves interacting with themselves
+    int n_found;           // colliding pairs found
+    int walk_iters;
+    int n_m2l_dir;
+    int n_p2p_dir;
+    unsigned bar_count;
+    unsigned bar_gen;
+    int bar_snap;          // error word as seen by the last block to reach the latest barrier
+    long long dec_pairs;   // walk decisions: direct cell pairs
+    long long dec_self;    // walk decisions: direct self cells
+    long long n_inter;     // direct particle pairs (unordered)
+    long long n_tests;     // collision tests
+    unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
+    double root[4];        // x_lo, y_lo, z_lo, L
+};
+
+// order-preserving map double -> uint64 (for atomicMin/atomicMax)
+__device__ __forceinline__ unsigned long long ord_encode(double v) {
+    unsigned long long u = __double_as_longlong(v);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_decode(unsigned long long u) {
+    unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+// true when an earlier stage overflowed a buffer or timed out: later kernels
+// then do nothing (their inputs may reference entries that were never
+// written), and the host reruns the call with larger buffers.
+__device__ __forceinline__ bool aborted(const Ctrl *ctl) {
+    return (*reinterpret_cast<const volatile int *>(&ctl->err) & ERR_ABORT_MASK) != 0;
+}
+
+// ---- bounded grid barrier (cooperative launches only) ----------------------
+// Every block must be resident (cudaLaunchCooperativeKernel guarantees it or
+// fails).  A wait that exceeds ~2 s sets ERR_TIMEOUT and returns false; the
+// kernels then leave their loops, so no launch can hang.
+__device__ __forceinline__ bool grid_sync(Ctrl *ctl) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctl->bar_gen;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            ctl->bar_snap = *((volatile int *)&ctl->err);
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > (1ll << 25)) { atomicOr(&ctl->err, ERR_TIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = (*((volatile int *)&ctl->err) & ERR_TIMEOUT) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Error word captured when the latest barrier completed: identical for every
+// block until the next barrier, so loop exits decided from it are uniform.
+__device__ __forceinline__ bool barrier_aborted(const Ctrl *ctl) {
+    return (*reinterpret_cast<const volatile int *>(&ctl->bar_snap) & ERR_ABORT_MASK) != 0;
+}
+
+// ---- warp helpers -----------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Warp-aggregated append: every active lane wants `k` slots in a list whose
+// length is *counter; returns the lane's first slot (slots >= cap must be
+// treated as overflow by the caller).  All lanes of the warp must call it.
+__device__ __forceinline__ int warp_append(int *counter, int k) {
+    unsigned lane = lane_id();
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - k;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace ncorp

@@ -1,0 +1,174 @@
+// ctx.h -- host-side context of the falcON step library and the launchers
+// each translation unit provides.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "../../include/ncorp.h"
+#include "common.cuh"
+
+namespace ncorp {
+
+// One set of per-moonlet arrays in tree (Hilbert) order, SoA.
+struct ParticleSet {
+    double *x = nullptr, *y = nullptr, *z = nullptr;
+    double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+    double *m = nullptr, *R = nullptr;
+    double *ax = nullptr, *ay = nullptr, *az = nullptr;   // total acceleration (mutual + external)
+    int *perm = nullptr;                                   // caller index of each moonlet
+    uint32_t *qx = nullptr, *qy = nullptr, *qz = nullptr; // quantised coordinates
+    uint64_t *key = nullptr;                               // Hilbert key
+};
+
+struct Cells {
+    int cap = 0;
+    int *level = nullptr, *first = nullptr, *count = nullptr, *child0 = nullptr, *nchild = nullptr,
+        *parent = nullptr, *arrive = nullptr;
+    uint32_t *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    double *M = nullptr, *sx = nullptr, *sy = nullptr, *sz = nullptr, *rmax = nullptr, *rcrit = nullptr,
+           *rho = nullptr;                                 // gravity climb
+    double *bx = nullptr, *by = nullptr, *bz = nullptr, *bmax = nullptr, *bcrit = nullptr;  // collision climb
+    void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
+    void *Ch = nullptr;       // [cap][num_c(p)] local coefficients (float or double)
+    int *leaves = nullptr;    // leaf cell ids
+    int *bounds = nullptr;    // [cap][9] scratch of the build
+    int *blocksum = nullptr;  // per-block scratch of cooperative kernels
+};
+
+struct WalkLists {
+    int front_cap = 0, m2l_cap = 0, p2p_cap = 0, self_cap = 0, m2l_dir_cap = 0, p2p_dir_cap = 0;
+    int2 *front[2] = {nullptr, nullptr};
+    int *front_count = nullptr;   // [MAX_ITERS + 1]
+    int2 *m2l = nullptr;          // well-separated cell pairs
+    int2 *p2p = nullptr;          // leaf-leaf direct pairs
+    int *self = nullptr;          // leaves interacting with themselves
+    int *cnt = nullptr, *offs = nullptr, *cursor = nullptr;     // per-cell counting sort scratch [cap+1]
+    int2 *m2l_dir = nullptr;      // (target, source) grouped by target
+    int *p2p_off = nullptr;       // [cap+1] offsets of each target leaf's sources
+    int *p2p_src = nullptr;       // source leaf of each directed entry
+};
+
+constexpr int WALK_MAX_ITERS = 96;
+
+}  // namespace ncorp
+
+struct ncorp_ctx {
+    ncorp_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    char err[512] = {0};
+
+    int64_t n_cap = 0;
+    int n = 0;
+    int p = 0;
+    double theta = 0.5;
+    int s = 0;
+    long long g_cs = 0, g_pre = 0, g_post = 0;
+    long long c_cs = 12, c_pre = 0, c_post = 16;
+
+    ncorp::ParticleSet A, B, Cset;   // A: resident state; B: scratch (half-kicked v, drifted x); Cset: next order
+    double *amx = nullptr, *amy = nullptr, *amz = nullptr;   // mutual acceleration (tree order)
+    uint64_t *key_alt = nullptr;
+    uint32_t *idx = nullptr, *idx_alt = nullptr;
+    int *tile_hist = nullptr;
+    int tile_hist_cap = 0;
+    int *scan_tmp = nullptr;
+    int scan_tmp_cap = 0;
+    double *stage = nullptr;         // [n][3] AoS staging
+    double *stage2 = nullptr;
+
+    ncorp::Cells cells;
+    ncorp::WalkLists wl;
+    int pair_cap = 0;
+    uint64_t *pairs = nullptr, *pairs_alt = nullptr;
+    uint32_t *pair_idx = nullptr, *pair_idx_alt = nullptr;
+    int64_t *pairs_out = nullptr;
+
+    ncorp::Ctrl *ctl = nullptr;      // device
+    ncorp::Ctrl *ctl_h = nullptr;    // pinned host mirror
+
+    // resident-state bookkeeping
+    bool have_state = false;         // A holds a state
+    bool tree_valid = false;         // cells describe A's positions, A.a valid
+    bool pairs_sorted = false;
+    int n_found = 0;
+    const void *last_pos = nullptr, *last_vel = nullptr, *last_m = nullptr, *last_R = nullptr;
+    int last_p = -1;
+    double last_theta = -1.0;
+    double time = 0.0;
+    int64_t stats[NCORP_NSTATS] = {0};
+    int tree_kind = 0;               // 1: gravity geometry valid, 2: collision geometry valid (bit mask)
+};
+
+namespace ncorp {
+
+// ---- launchers (sort.cu) ----
+void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz);
+void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
+                    int bits);
+void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
+                   const uint32_t *idx);
+void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total);
+void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
+
+// ---- tree.cu ----
+void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s);
+void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta);
+void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
+                            const double *vz, double dt);
+
+// ---- walk.cu ----
+void launch_walk(ncorp_ctx *c, bool gravity);
+void launch_directed_lists(ncorp_ctx *c);
+
+// ---- m2l.cu / eval.cu ----
+void launch_m2l(ncorp_ctx *c, int p, bool mixed);
+struct ExtForce {
+    double GMc;            // G * central mass
+    double star_k;         // G M_star / r_star^3 (0: off)
+    double sx, sy, sz;     // star position
+    double inv_rs2;        // 1 / r_star^2
+};
+void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual);
+
+// ---- collide.cu ----
+void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
+                    double dt);
+void launch_sort_pairs(ncorp_ctx *c, int count);
+
+// ---- kdk.cu ----
+void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n);
+void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm,
+                        double *aos, int n);
+void launch_scatter_scalar(ncorp_ctx *c, const double *v, const int *perm, double *out, int n);
+void launch_kick(ncorp_ctx *c, const double *vx, const double *vy, const double *vz, const double *ax,
+                 const double *ay, const double *az, double h, double *ox, double *oy, double *oz, int n);
+void launch_drift(ncorp_ctx *c, const double *x, const double *y, const double *z, const double *vx,
+                  const double *vy, const double *vz, double dt, double *ox, double *oy, double *oz, int n);
+void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count);
+
+// host-side error helper used by every launcher
+#define NCORP_CUDA_CHECK(expr)                                                       \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) throw ::ncorp::CudaError(_e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+struct CudaError {
+    cudaError_t code;
+    const char *expr, *file;
+    int line;
+    CudaError(cudaError_t c, const char *e, const char *f, int l) : code(c), expr(e), file(f), line(l) {}
+};
+
+inline int grid_for(int n, int block, int max_blocks = 1 << 20) {
+    long long g = (static_cast<long long>(n) + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return static_cast<int>(g);
+}
+
+}  // namespace ncorp

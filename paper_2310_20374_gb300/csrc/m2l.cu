@@ -1,0 +1,175 @@
+// m2l.cu -- cell-cell interactions of well-separated pairs (Eq. phi_expanded).
+//
+// For a target cell A and a source cell B, R = s_A - s_B:
+//   C_alpha(s_A) = sum_beta (-1)^|beta| D_{alpha+beta}(R) M_beta(s_B) / beta!,
+//   1 <= |alpha| <= p, |alpha| + |beta| <= p, beta in {0} U {|beta| >= 2},
+// which is Eq. phi_expanded with the full-index contraction written over
+// symmetric multi-indices (the multinomial count of equal index tuples turns
+// 1/n! into 1/beta!).  D_gamma = d^gamma (1/|R|) follows from the identity
+// r^2 d_i(1/r) + x_i (1/r) = 0 differentiated gamma times, which gives
+//   n r^2 D_gamma = -(2n-1) sum_j gamma_j x_j D_{gamma-e_j}
+//                   - (n-1) sum_j gamma_j (gamma_j - 1) D_{gamma-2e_j},  n = |gamma|.
+//
+// Scaling: with rho_A, rho_B the cells' power-of-two scales and u = R/rho_A,
+//   C-hat_alpha(A) = C_alpha rho_A^|alpha|
+//                  = (1/rho_A) sum_beta D_{alpha+beta}(u) (-rho_B/rho_A)^|beta| M-hat_beta(B),
+// so that the per-entry sum needs no alpha-dependent factor and the 1/rho_A is
+// applied once per target.
+//
+// Work layout: the directed entries (target, source) are grouped by target;
+// each thread takes a contiguous run of entries, keeps the target's
+// coefficients in registers while the target does not change, and adds them
+// to the target's C-hat with one atomic per coefficient when it does.  Both
+// directions of a pair are evaluated (A <- B and B <- A), which is the
+// symmetric treatment of Sect. 3.4.3 split into its two halves.
+#include "ctx.h"
+
+namespace ncorp {
+
+template <int P, typename real>
+__device__ __forceinline__ void green_derivatives(real ux, real uy, real uz, real *D) {
+    const real r2 = ux * ux + uy * uy + uz * uz;
+    const real ir2 = real(1) / r2;
+    D[0] = sqrt(ir2);
+#pragma unroll
+    for (int n = 1; n <= P; n++) {
+#pragma unroll
+        for (int k = 0; k <= n; k++) {
+#pragma unroll
+            for (int c = 0; c <= k; c++) {
+                const int a = n - k, b = k - c;
+                real s1 = real(0), s2 = real(0);
+                if (a >= 1) s1 += real(a) * ux * D[sidx(a - 1, b, c)];
+                if (b >= 1) s1 += real(b) * uy * D[sidx(a, b - 1, c)];
+                if (c >= 1) s1 += real(c) * uz * D[sidx(a, b, c - 1)];
+                if (a >= 2) s2 += real(a * (a - 1)) * D[sidx(a - 2, b, c)];
+                if (b >= 2) s2 += real(b * (b - 1)) * D[sidx(a, b - 2, c)];
+                if (c >= 2) s2 += real(c * (c - 1)) * D[sidx(a, b, c - 2)];
+                D[sidx(a, b, c)] = -(real(2 * n - 1) * s1 + real(n - 1) * s2) * (ir2 * real(1.0 / n));
+            }
+        }
+    }
+}
+
+struct M2LArgs {
+    const int2 *dir;
+    int dir_cap;
+    const double *sx, *sy, *sz, *rho;
+    const void *Mh;
+    void *Ch;
+    const Ctrl *ctl;
+};
+
+__device__ __forceinline__ void atomic_add_real(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_real(double *p, double v) { atomicAdd(p, v); }
+
+template <int P, typename real>
+__global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
+    constexpr int NM = num_m(P), NC = num_c(P), ND = num_d(P);
+    const real *__restrict__ Mh = static_cast<const real *>(A.Mh);
+    real *Ch = static_cast<real *>(A.Ch);
+    if (aborted(A.ctl)) return;
+    const int E = min(A.ctl->n_m2l_dir, A.dir_cap);
+    const int T = gridDim.x * blockDim.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = (E + T - 1) / T;
+    const int e0 = min(E, t * per), e1 = min(E, e0 + per);
+    real acc[NC];
+#pragma unroll
+    for (int i = 0; i < NC; i++) acc[i] = real(0);
+    int cur = -1;
+    double irho = 1.0;
+    double tx = 0, ty = 0, tz = 0;
+    auto flush = [&]() {
+        const real f = static_cast<real>(irho);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            atomic_add_real(&Ch[(size_t)cur * NC + i], acc[i] * f);
+            acc[i] = real(0);
+        }
+    };
+    for (int e = e0; e < e1; e++) {
+        const int2 d = A.dir[e];
+        if (d.x != cur) {
+            if (cur >= 0) flush();
+            cur = d.x;
+            irho = 1.0 / A.rho[cur];
+            tx = A.sx[cur];
+            ty = A.sy[cur];
+            tz = A.sz[cur];
+        }
+        const int src = d.y;
+        const real ux = static_cast<real>((tx - A.sx[src]) * irho);
+        const real uy = static_cast<real>((ty - A.sy[src]) * irho);
+        const real uz = static_cast<real>((tz - A.sz[src]) * irho);
+        const real q = static_cast<real>(-A.rho[src] * irho);   // -rho_B / rho_A
+        real D[ND];
+        green_derivatives<P, real>(ux, uy, uz, D);
+        const real *Ms = Mh + (size_t)src * NM;
+        real qn = real(1);
+#pragma unroll
+        for (int nb = 0; nb < P; nb++) {
+            if (nb == 1) {
+                qn *= q;
+                continue;
+            }
+#pragma unroll
+            for (int kb = 0; kb <= nb; kb++) {
+#pragma unroll
+                for (int cb = 0; cb <= kb; cb++) {
+                    const int ab = nb - kb, bb = kb - cb;
+                    const real w = qn * __ldg(&Ms[midx(ab, bb, cb)]);
+#pragma unroll
+                    for (int na = 1; na <= P - nb; na++) {
+#pragma unroll
+                        for (int ka = 0; ka <= na; ka++) {
+#pragma unroll
+                            for (int ca = 0; ca <= ka; ca++) {
+                                const int aa = na - ka, ba = ka - ca;
+                                acc[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
+                            }
+                        }
+                    }
+                }
+            }
+            qn *= q;
+        }
+    }
+    if (cur >= 0) flush();
+}
+
+template <int P, typename real>
+static void m2l_t(ncorp_ctx *c, const M2LArgs &A) {
+    k_m2l<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A);
+}
+
+void launch_m2l(ncorp_ctx *c, int p, bool mixed) {
+    Cells &C = c->cells;
+    M2LArgs A;
+    A.dir = c->wl.m2l_dir;
+    A.dir_cap = c->wl.m2l_dir_cap;
+    A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
+    A.Mh = C.Mh;
+    A.Ch = C.Ch;
+    A.ctl = c->ctl;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    NCORP_CUDA_CHECK(cudaMemsetAsync(C.Ch, 0, esz * num_c(p) * C.cap, c->stream));
+#define NCORP_M2L_CASE(PP)                       \
+    case PP:                                     \
+        if (mixed) m2l_t<PP, float>(c, A);       \
+        else m2l_t<PP, double>(c, A);            \
+        break;
+    switch (p) {
+        NCORP_M2L_CASE(1)
+        NCORP_M2L_CASE(2)
+        NCORP_M2L_CASE(3)
+        NCORP_M2L_CASE(4)
+        NCORP_M2L_CASE(5)
+        NCORP_M2L_CASE(6)
+        default: break;
+    }
+#undef NCORP_M2L_CASE
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace ncorp

@@ -1,0 +1,682 @@
+// ncorp.cu -- C ABI entry points (include/ncorp.h) and the order in which one
+// falcON step runs its kernels.
+//
+// Step (SBAB1 with merged kicks, Sect. 4.1), on the state A kept in tree order:
+//   B.v = A.v + dt/2 A.a                         half kick
+//   collision climb + walk + pair test on (A.x, B.v) with A's tree (Sect. 3.1)
+//   B.x = A.x + dt B.v                           drift
+//   keys -> radix sort -> gather into C -> build  (Sect. 3.4.1, 3.4.6)
+//   climb (geometry, P2M/M2M) -> walk -> lists -> M2L -> L2L/L2P + P2P + external
+//   C.v += dt/2 C.a                              half kick
+//   A <-> C
+// A is never written during a step, so a step whose lists overflowed is rerun
+// from it with larger buffers.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace ncorp;
+
+namespace {
+
+int fail(ncorp_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+template <typename T>
+void dalloc(T *&p, size_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * count);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void alloc_set(ParticleSet &S, size_t n) {
+    dalloc(S.x, n); dalloc(S.y, n); dalloc(S.z, n);
+    dalloc(S.vx, n); dalloc(S.vy, n); dalloc(S.vz, n);
+    dalloc(S.m, n); dalloc(S.R, n);
+    dalloc(S.ax, n); dalloc(S.ay, n); dalloc(S.az, n);
+    dalloc(S.perm, n);
+    dalloc(S.qx, n); dalloc(S.qy, n); dalloc(S.qz, n);
+    dalloc(S.key, n);
+}
+
+void free_set(ParticleSet &S) {
+    dfree(S.x); dfree(S.y); dfree(S.z); dfree(S.vx); dfree(S.vy); dfree(S.vz); dfree(S.m); dfree(S.R);
+    dfree(S.ax); dfree(S.ay); dfree(S.az); dfree(S.perm); dfree(S.qx); dfree(S.qy); dfree(S.qz); dfree(S.key);
+}
+
+void ensure_particles(ncorp_ctx *c, int64_t n) {
+    if (n <= c->n_cap) return;
+    int64_t cap = std::max<int64_t>(n, c->n_cap * 3 / 2);
+    alloc_set(c->A, cap);
+    alloc_set(c->B, cap);
+    alloc_set(c->Cset, cap);
+    dalloc(c->amx, cap); dalloc(c->amy, cap); dalloc(c->amz, cap);
+    dalloc(c->key_alt, cap);
+    dalloc(c->idx, cap); dalloc(c->idx_alt, cap);
+    dalloc(c->stage, 3 * cap);
+    dalloc(c->stage2, 3 * cap);
+    c->n_cap = cap;
+    c->have_state = false;
+    c->tree_valid = false;
+}
+
+void alloc_cells(ncorp_ctx *c, int cap) {
+    Cells &C = c->cells;
+    dalloc(C.level, cap); dalloc(C.first, cap); dalloc(C.count, cap); dalloc(C.child0, cap);
+    dalloc(C.nchild, cap); dalloc(C.parent, cap); dalloc(C.arrive, cap);
+    dalloc(C.cx, cap); dalloc(C.cy, cap); dalloc(C.cz, cap);
+    dalloc(C.M, cap); dalloc(C.sx, cap); dalloc(C.sy, cap); dalloc(C.sz, cap);
+    dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
+    dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
+    double *mh = nullptr, *ch = nullptr;
+    dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
+    dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
+    if (C.Mh) cudaFree(C.Mh);
+    if (C.Ch) cudaFree(C.Ch);
+    C.Mh = mh;
+    C.Ch = ch;
+    dalloc(C.leaves, cap);
+    dalloc(C.bounds, static_cast<size_t>(cap) * 9);
+    dalloc(C.blocksum, 8192);
+    WalkLists &W = c->wl;
+    dalloc(W.cnt, cap + 1); dalloc(W.offs, cap + 1); dalloc(W.cursor, cap + 1); dalloc(W.p2p_off, cap + 1);
+    C.cap = cap;
+    c->tree_valid = false;
+}
+
+void alloc_lists(ncorp_ctx *c, int front, int m2l, int p2p, int self) {
+    WalkLists &W = c->wl;
+    if (front != W.front_cap) {
+        dalloc(W.front[0], front);
+        dalloc(W.front[1], front);
+        W.front_cap = front;
+    }
+    if (!W.front_count) dalloc(W.front_count, WALK_MAX_ITERS + 2);
+    if (m2l != W.m2l_cap) {
+        dalloc(W.m2l, m2l);
+        dalloc(W.m2l_dir, 2 * static_cast<size_t>(m2l));
+        W.m2l_cap = m2l;
+        W.m2l_dir_cap = 2 * m2l;
+    }
+    if (p2p != W.p2p_cap || self != W.self_cap) {
+        dalloc(W.p2p, p2p);
+        dalloc(W.self, self);
+        dalloc(W.p2p_src, 2 * static_cast<size_t>(p2p) + self);
+        W.p2p_cap = p2p;
+        W.self_cap = self;
+        W.p2p_dir_cap = 2 * p2p + self;
+    }
+}
+
+void alloc_pairs(ncorp_ctx *c, int cap) {
+    dalloc(c->pairs, cap);
+    dalloc(c->pairs_alt, cap);
+    dalloc(c->pair_idx, cap);
+    dalloc(c->pair_idx_alt, cap);
+    dalloc(c->pairs_out, 2 * static_cast<size_t>(cap));
+    c->pair_cap = cap;
+}
+
+// leaf size and thresholds for expansion order p (config values win when set)
+void choose_parameters(ncorp_ctx *c, int p) {
+    const ncorp_config &g = c->cfg;
+    c->s = g.leaf_size > 0 ? g.leaf_size : (p <= 3 ? 32 : (p <= 5 ? 48 : 64));
+    if (g.n_cs || g.n_cc_pre || g.n_cc_post) {
+        c->g_cs = g.n_cs; c->g_pre = g.n_cc_pre; c->g_post = g.n_cc_post;
+    } else if (p >= 6) {
+        c->g_cs = 256; c->g_pre = 256; c->g_post = 512;   // Sect. 4.2, p = 6
+    } else {
+        c->g_cs = 64; c->g_pre = 8; c->g_post = 64;        // Sect. 4.2, p = 3
+    }
+    if (g.c_cs || g.c_cc_pre || g.c_cc_post) {
+        c->c_cs = g.c_cs; c->c_pre = g.c_cc_pre; c->c_post = g.c_cc_post;
+    } else {
+        c->c_cs = 12; c->c_pre = 0; c->c_post = 16;        // Sect. 4.2, collisions
+    }
+}
+
+void ensure_tree_capacity(ncorp_ctx *c, int n) {
+    int want = std::max(4096, 4 * (n / std::max(1, c->s)) + 1024);
+    if (c->cells.cap < want) alloc_cells(c, want);
+    const int cc = c->cells.cap;
+    int front = std::max(1 << 16, 48 * cc), m2l = std::max(1 << 16, 64 * cc), p2p = std::max(1 << 16, 48 * cc);
+    if (c->wl.front_cap < front || c->wl.m2l_cap < m2l || c->wl.p2p_cap < p2p || c->wl.self_cap < cc)
+        alloc_lists(c, std::max(front, c->wl.front_cap), std::max(m2l, c->wl.m2l_cap), std::max(p2p, c->wl.p2p_cap),
+                    std::max(cc, c->wl.self_cap));
+    int pc = std::max(1 << 16, 4 * n);
+    if (c->pair_cap < pc) alloc_pairs(c, pc);
+}
+
+// grows whatever overflowed; returns false if nothing can be grown
+bool grow_after(ncorp_ctx *c, int err) {
+    bool grew = false;
+    if (err & ERR_CELLS) {
+        alloc_cells(c, std::max(2 * c->cells.cap, c->ctl_h->n_cells + 1024));
+        grew = true;
+    }
+    WalkLists &W = c->wl;
+    int front = W.front_cap, m2l = W.m2l_cap, p2p = W.p2p_cap, self = W.self_cap;
+    if (err & ERR_FRONTIER) { front *= 2; grew = true; }
+    if (err & (ERR_M2L | ERR_DIRECTED)) { m2l = std::max(2 * m2l, c->ctl_h->n_m2l + 1024); grew = true; }
+    if (err & (ERR_P2P | ERR_DIRECTED)) {
+        p2p = std::max(2 * p2p, c->ctl_h->n_p2p + 1024);
+        self = std::max(2 * self, c->ctl_h->n_self + 1024);
+        grew = true;
+    }
+    if (grew) alloc_lists(c, front, m2l, p2p, self);
+    if (err & ERR_PAIRS) {
+        alloc_pairs(c, std::max(2 * c->pair_cap, c->ctl_h->n_found + 1024));
+        grew = true;
+    }
+    return grew;
+}
+
+bool is_device_ptr(ncorp_ctx *c, const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice) {
+        if (a.device != c->device) throw CudaError(cudaErrorInvalidDevicePointer, "pointer on another device",
+                                                   __FILE__, __LINE__);
+        return true;
+    }
+    return a.type == cudaMemoryTypeManaged;
+}
+
+void upload_vec(ncorp_ctx *c, const double *user, double *x, double *y, double *z, int n) {
+    if (is_device_ptr(c, user)) {
+        launch_aos_to_soa(c, user, x, y, z, n);
+    } else {
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(c->stage, user, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+        launch_aos_to_soa(c, c->stage, x, y, z, n);
+    }
+}
+
+void upload_scalar(ncorp_ctx *c, const double *user, double *dst, int n) {
+    NCORP_CUDA_CHECK(cudaMemcpyAsync(dst, user, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+}
+
+void download_vec(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm, double *user,
+                  int n, double *stage) {
+    if (is_device_ptr(c, user)) {
+        launch_scatter_aos(c, x, y, z, perm, user, n);
+    } else {
+        launch_scatter_aos(c, x, y, z, perm, stage, n);
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(user, stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    }
+}
+
+ExtForce external(ncorp_ctx *c, double t) {
+    ExtForce e{};
+    const ncorp_config &g = c->cfg;
+    e.GMc = g.G * g.central_mass;
+    if (g.star_mass != 0.0) {
+        const double a = g.star_a;
+        const double nsun = std::sqrt(g.G * g.star_mass / (a * a * a));
+        const double lam = nsun * t;
+        e.sx = a * std::cos(lam);
+        e.sy = a * std::sin(lam) * std::cos(g.star_obliquity);
+        e.sz = a * std::sin(lam) * std::sin(g.star_obliquity);
+        const double rs2 = e.sx * e.sx + e.sy * e.sy + e.sz * e.sz;
+        e.star_k = (g.G * g.star_mass) / (rs2 * std::sqrt(rs2));
+        e.inv_rs2 = 1.0 / rs2;
+    }
+    return e;
+}
+
+void reset_ctl(ncorp_ctx *c) { NCORP_CUDA_CHECK(cudaMemsetAsync(c->ctl, 0, sizeof(Ctrl), c->stream)); }
+
+int finish(ncorp_ctx *c) {
+    NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return c->ctl_h->err;
+}
+
+// keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
+void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
+                int n) {
+    launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
+    radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
+    ParticleSet view = sr;
+    view.x = sx.x; view.y = sx.y; view.z = sx.z;
+    view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
+    view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
+    launch_gather(c, view, view, dst, n, c->idx);
+    launch_build(c, dst, n, c->s);
+}
+
+void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual) {
+    const bool mixed = c->cfg.precision == NCORP_MIXED;
+    launch_climb_gravity(c, S, p, mixed, c->cfg.G, theta);
+    launch_walk(c, true);
+    launch_directed_lists(c);
+    launch_m2l(c, p, mixed);
+    launch_eval(c, S, p, mixed, c->cfg.G, external(c, t), want_mutual);
+}
+
+void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
+    launch_climb_collision(c, S, vx, vy, vz, dt);
+    launch_walk(c, false);
+    launch_collide(c, S, vx, vy, vz, dt);
+}
+
+void record_stats(ncorp_ctx *c, bool grav) {
+    const Ctrl &h = *c->ctl_h;
+    c->stats[NCORP_STAT_CELLS] = h.n_cells;
+    c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
+    c->stats[NCORP_STAT_DEPTH] = h.max_level;
+    c->stats[NCORP_STAT_WALK_ITERS] = h.walk_iters;
+    if (grav) {
+        c->stats[NCORP_STAT_M2L] = h.n_m2l;
+        c->stats[NCORP_STAT_P2P_PAIRS] = h.dec_pairs;
+        c->stats[NCORP_STAT_P2P_SELF] = h.dec_self;
+        c->stats[NCORP_STAT_P2P_INTER] = h.n_inter;
+        c->stats[NCORP_STAT_M2L_DIRECTED] = h.n_m2l_dir;
+        c->stats[NCORP_STAT_P2P_DIRECTED] = h.n_p2p_dir;
+    } else {
+        c->stats[NCORP_STAT_COL_PAIRS] = h.dec_pairs;
+        c->stats[NCORP_STAT_COL_SELF] = h.dec_self;
+        c->stats[NCORP_STAT_COL_TESTS] = h.n_tests;
+        c->stats[NCORP_STAT_COL_FOUND] = h.n_found;
+    }
+}
+
+bool finite_ok(ncorp_ctx *c) { return (c->ctl_h->err & ERR_NONFINITE) == 0; }
+
+int check_common(ncorp_ctx *c, int64_t n, int p, double theta) {
+    if (!c) return NCORP_EINVAL;
+    if (n < 1 || n > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "n = %lld out of range", (long long)n);
+    if (p < 1 || p > MAXP) return fail(c, NCORP_EINVAL, "p = %d outside 1..6", p);
+    if (!(theta > 0.0 && theta < 1.0)) return fail(c, NCORP_EINVAL, "theta = %g outside (0, 1)", theta);
+    return NCORP_OK;
+}
+
+constexpr int MAX_RETRIES = 6;
+
+#define NCORP_API_BODY(ctxp, ...)                                                               \
+    try {                                                                                       \
+        NCORP_CUDA_CHECK(cudaSetDevice((ctxp)->device));                                        \
+        __VA_ARGS__                                                                             \
+    } catch (const CudaError &e) {                                                              \
+        (ctxp)->have_state = false;                                                             \
+        (ctxp)->tree_valid = false;                                                             \
+        return fail((ctxp), NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line); \
+    } catch (const std::bad_alloc &) {                                                          \
+        return fail((ctxp), NCORP_ENOMEM, "host allocation failed");                             \
+    }
+
+}  // namespace
+
+extern "C" {
+
+void ncorp_config_default(ncorp_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->G = 1.0;
+    cfg->central_mass = 1.0;
+    cfg->central_radius = 1.0;
+    cfg->precision = NCORP_MIXED;
+    cfg->collisions = 1;
+}
+
+int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream) {
+    if (!out || !cfg || n_max < 1) return NCORP_EINVAL;
+    if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
+    if (!(cfg->G > 0.0) || !(cfg->central_mass >= 0.0) || cfg->leaf_size < 0) return NCORP_EINVAL;
+    *out = nullptr;
+    ncorp_ctx *c = new (std::nothrow) ncorp_ctx();
+    if (!c) return NCORP_ENOMEM;
+    c->cfg = *cfg;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->time = cfg->t0;
+    try {
+        NCORP_CUDA_CHECK(cudaSetDevice(device));
+        NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+        int coop = 0;
+        NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+        if (!coop) throw CudaError(cudaErrorNotSupported, "cooperative launch unsupported", __FILE__, __LINE__);
+        dalloc(c->ctl, 1);
+        NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
+        std::memset(c->ctl_h, 0, sizeof(Ctrl));
+        NCORP_CUDA_CHECK(cudaMemset(c->ctl, 0, sizeof(Ctrl)));
+        ensure_particles(c, n_max);
+        choose_parameters(c, 6);
+        ensure_tree_capacity(c, static_cast<int>(n_max));
+    } catch (const CudaError &e) {
+        int code = (e.code == cudaErrorMemoryAllocation) ? NCORP_ENOMEM : NCORP_ECUDA;
+        ncorp_free(c);
+        return code;
+    }
+    *out = c;
+    return NCORP_OK;
+}
+
+int ncorp_set_stream(ncorp_ctx *c, void *cuda_stream) {
+    if (!c) return NCORP_EINVAL;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return NCORP_OK;
+}
+
+int ncorp_reset(ncorp_ctx *c) {
+    if (!c) return NCORP_EINVAL;
+    c->have_state = false;
+    c->tree_valid = false;
+    return NCORP_OK;
+}
+
+int ncorp_accel(ncorp_ctx *c, const double *positions, const double *masses, int64_t n64, int p, double theta,
+                double *acc, double *acc_mutual) {
+    int st = check_common(c, n64, p, theta);
+    if (st) return st;
+    if (!positions || !masses || !acc) return fail(c, NCORP_EINVAL, "null pointer");
+    NCORP_API_BODY(c, {
+        const int n = static_cast<int>(n64);
+        ensure_particles(c, n);
+        choose_parameters(c, p);
+        c->have_state = false;
+        c->tree_valid = false;
+        for (int attempt = 0;; attempt++) {
+            ensure_tree_capacity(c, n);
+            reset_ctl(c);
+            ParticleSet &A = c->A;
+            upload_vec(c, positions, A.x, A.y, A.z, n);
+            upload_scalar(c, masses, A.m, n);
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vx, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vy, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vz, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.R, 0, sizeof(double) * n, c->stream));
+            launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+            build_tree(c, A, A, A, c->Cset, n);
+            std::swap(c->A, c->Cset);
+            gravity(c, c->A, p, theta, c->time, true);
+            download_vec(c, c->A.ax, c->A.ay, c->A.az, c->A.perm, acc, n, c->stage);
+            if (acc_mutual) download_vec(c, c->amx, c->amy, c->amz, c->A.perm, acc_mutual, n, c->stage2);
+            int err = finish(c);
+            if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
+            if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+            if (err == 0) break;
+            if (attempt >= MAX_RETRIES || !grow_after(c, err))
+                return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+        }
+        c->n = n;
+        c->tree_kind = 1;
+        record_stats(c, true);
+        return NCORP_OK;
+    })
+}
+
+int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocities, const double *radii, int64_t n64,
+                  double dt) {
+    if (!c) return NCORP_EINVAL;
+    if (n64 < 1 || n64 > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "n out of range");
+    if (!positions || !velocities || !radii) return fail(c, NCORP_EINVAL, "null pointer");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NCORP_EINVAL, "dt must be > 0");
+    NCORP_API_BODY(c, {
+        const int n = static_cast<int>(n64);
+        ensure_particles(c, n);
+        if (c->s == 0) choose_parameters(c, 6);
+        c->have_state = false;
+        c->tree_valid = false;
+        for (int attempt = 0;; attempt++) {
+            ensure_tree_capacity(c, n);
+            reset_ctl(c);
+            ParticleSet &A = c->A;
+            upload_vec(c, positions, A.x, A.y, A.z, n);
+            upload_vec(c, velocities, A.vx, A.vy, A.vz, n);
+            upload_scalar(c, radii, A.R, n);
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.m, 0, sizeof(double) * n, c->stream));
+            launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+            build_tree(c, A, A, A, c->Cset, n);
+            std::swap(c->A, c->Cset);
+            collisions(c, c->A, c->A.vx, c->A.vy, c->A.vz, dt);
+            int err = finish(c);
+            if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
+            if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+            if (err == 0) break;
+            if (attempt >= MAX_RETRIES || !grow_after(c, err))
+                return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+        }
+        c->n = n;
+        c->n_found = c->ctl_h->n_found;
+        c->pairs_sorted = false;
+        c->tree_kind = 2;
+        record_stats(c, false);
+        return NCORP_OK;
+    })
+}
+
+int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double *masses, const double *radii,
+               int64_t n64, int p, double theta, double dt) {
+    int st = check_common(c, n64, p, theta);
+    if (st) return st;
+    if (!positions || !velocities || !masses || !radii) return fail(c, NCORP_EINVAL, "null pointer");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NCORP_EINVAL, "dt must be > 0");
+    NCORP_API_BODY(c, {
+        const int n = static_cast<int>(n64);
+        const bool resident = c->have_state && c->tree_valid && c->n == n && c->last_pos == positions &&
+                              c->last_vel == velocities && c->last_m == masses && c->last_R == radii &&
+                              c->last_p == p && c->last_theta == theta;
+        ensure_particles(c, n);
+        choose_parameters(c, p);
+        const double h = 0.5 * dt;
+        bool have = resident && c->have_state;
+        bool tree = resident;
+        for (int attempt = 0;; attempt++) {
+            ensure_tree_capacity(c, n);
+            reset_ctl(c);
+            if (!have) {   // read the caller's state (caller order)
+                ParticleSet &A = c->A;
+                upload_vec(c, positions, A.x, A.y, A.z, n);
+                upload_vec(c, velocities, A.vx, A.vy, A.vz, n);
+                upload_scalar(c, masses, A.m, n);
+                upload_scalar(c, radii, A.R, n);
+                launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+                tree = false;
+            }
+            if (!tree) {   // tree and acceleration of the current positions
+                build_tree(c, c->A, c->A, c->A, c->Cset, n);
+                std::swap(c->A, c->Cset);
+                gravity(c, c->A, p, theta, c->time, false);
+            }
+            ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
+            launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n);
+            if (c->cfg.collisions) collisions(c, A, B.vx, B.vy, B.vz, dt);
+            launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n);
+            build_tree(c, B, B, A, Cn, n);
+            gravity(c, Cn, p, theta, c->time + dt, false);
+            launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n);
+            download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
+            download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
+            int err = finish(c);
+            if (!finite_ok(c)) {
+                c->have_state = false;
+                c->tree_valid = false;
+                return fail(c, NCORP_EINVAL, "non-finite position");
+            }
+            if (err & ERR_TIMEOUT) {
+                c->have_state = false;
+                c->tree_valid = false;
+                return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+            }
+            if (err == 0) break;
+            // A was not written: rerun from it with larger buffers (its tree is rebuilt)
+            have = true;
+            tree = false;
+            if (attempt >= MAX_RETRIES || !grow_after(c, err)) {
+                c->tree_valid = false;
+                return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+            }
+        }
+        if (c->cfg.collisions) {
+            c->n_found = c->ctl_h->n_found;
+            c->pairs_sorted = false;
+        } else {
+            c->n_found = 0;
+        }
+        std::swap(c->A, c->Cset);
+        c->time += dt;
+        c->n = n;
+        c->have_state = true;
+        c->tree_valid = true;
+        c->tree_kind = 1;
+        c->last_pos = positions;
+        c->last_vel = velocities;
+        c->last_m = masses;
+        c->last_R = radii;
+        c->last_p = p;
+        c->last_theta = theta;
+        record_stats(c, true);
+        c->stats[NCORP_STAT_COL_FOUND] = c->n_found;
+        return NCORP_OK;
+    })
+}
+
+int ncorp_collisions(ncorp_ctx *c, int64_t *pairs, int64_t cap, int64_t *n_pairs) {
+    if (!c || cap < 0 || (cap > 0 && !pairs)) return NCORP_EINVAL;
+    NCORP_API_BODY(c, {
+        const int found = c->n_found;
+        const int stored = std::min(found, c->pair_cap);
+        if (!c->pairs_sorted) {
+            launch_sort_pairs(c, stored);
+            launch_unpack_pairs(c, c->pairs, c->pairs_out, stored);
+            c->pairs_sorted = true;
+        }
+        const int64_t k = std::min<int64_t>(cap, stored);
+        if (k > 0)
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(pairs, c->pairs_out, sizeof(int64_t) * 2 * k, cudaMemcpyDefault, c->stream));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        if (n_pairs) *n_pairs = found;
+        if (found > c->pair_cap) return fail(c, NCORP_EOVERFLOW, "pair buffer overflowed (%d found)", found);
+        if (found > cap) return fail(c, NCORP_EOVERFLOW, "%d pairs found, room for %lld", found, (long long)cap);
+        return NCORP_OK;
+    })
+}
+
+int ncorp_get_state(ncorp_ctx *c, double *positions, double *velocities) {
+    if (!c || !positions || !velocities) return NCORP_EINVAL;
+    if (!c->have_state) return fail(c, NCORP_ESTATE, "no resident state");
+    NCORP_API_BODY(c, {
+        download_vec(c, c->A.x, c->A.y, c->A.z, c->A.perm, positions, c->n, c->stage);
+        download_vec(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, velocities, c->n, c->stage2);
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        return NCORP_OK;
+    })
+}
+
+int ncorp_stats(ncorp_ctx *c, int64_t *stats, int n_stats) {
+    if (!c || !stats || n_stats < 0) return NCORP_EINVAL;
+    for (int i = 0; i < n_stats && i < NCORP_NSTATS; i++) stats[i] = c->stats[i];
+    return NCORP_OK;
+}
+
+int ncorp_tree_export(ncorp_ctx *c, int64_t *order, uint64_t *keys, double *root, int64_t *cells, double *ggeo,
+                      double *cgeo, int64_t cap, int64_t *n_cells) {
+    if (!c || cap < 0) return NCORP_EINVAL;
+    if (c->n <= 0 || c->tree_kind == 0) return fail(c, NCORP_ESTATE, "no tree yet");
+    NCORP_API_BODY(c, {
+        const int n = c->n;
+        const int nc = std::min(c->ctl_h->n_cells, c->cells.cap);
+        const Cells &C = c->cells;
+        if (n_cells) *n_cells = nc;
+        if (order) {
+            std::vector<int> perm(n);
+            std::vector<int64_t> o(n);
+            NCORP_CUDA_CHECK(cudaMemcpy(perm.data(), c->A.perm, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; i++) o[i] = perm[i];
+            NCORP_CUDA_CHECK(cudaMemcpy(order, o.data(), sizeof(int64_t) * n, cudaMemcpyDefault));
+        }
+        if (keys) NCORP_CUDA_CHECK(cudaMemcpy(keys, c->A.key, sizeof(uint64_t) * n, cudaMemcpyDefault));
+        if (root) NCORP_CUDA_CHECK(cudaMemcpy(root, c->ctl_h->root, sizeof(double) * 4, cudaMemcpyDefault));
+        const int k = static_cast<int>(std::min<int64_t>(cap, nc));
+        if (k > 0 && cells) {
+            std::vector<int> lv(k), f(k), cnt(k), nch(k);
+            std::vector<uint32_t> x(k), y(k), z(k);
+            NCORP_CUDA_CHECK(cudaMemcpy(lv.data(), C.level, sizeof(int) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(f.data(), C.first, sizeof(int) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(cnt.data(), C.count, sizeof(int) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(nch.data(), C.nchild, sizeof(int) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(x.data(), C.cx, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(y.data(), C.cy, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+            NCORP_CUDA_CHECK(cudaMemcpy(z.data(), C.cz, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+            std::vector<int64_t> rows(7 * static_cast<size_t>(k));
+            for (int i = 0; i < k; i++) {
+                int64_t *r = &rows[7 * static_cast<size_t>(i)];
+                r[0] = lv[i]; r[1] = x[i]; r[2] = y[i]; r[3] = z[i]; r[4] = f[i]; r[5] = cnt[i]; r[6] = nch[i];
+            }
+            NCORP_CUDA_CHECK(cudaMemcpy(cells, rows.data(), sizeof(int64_t) * rows.size(), cudaMemcpyDefault));
+        }
+        auto pack = [&](double *dst, std::initializer_list<const double *> cols) {
+            const int w = static_cast<int>(cols.size());
+            std::vector<double> tmp(k), out(static_cast<size_t>(k) * w);
+            int j = 0;
+            for (const double *col : cols) {
+                NCORP_CUDA_CHECK(cudaMemcpy(tmp.data(), col, sizeof(double) * k, cudaMemcpyDeviceToHost));
+                for (int i = 0; i < k; i++) out[static_cast<size_t>(i) * w + j] = tmp[i];
+                j++;
+            }
+            NCORP_CUDA_CHECK(cudaMemcpy(dst, out.data(), sizeof(double) * out.size(), cudaMemcpyDefault));
+        };
+        if (k > 0 && ggeo && (c->tree_kind & 1)) pack(ggeo, {C.M, C.sx, C.sy, C.sz, C.rmax, C.rcrit});
+        if (k > 0 && cgeo && (c->tree_kind & 2)) pack(cgeo, {C.bx, C.by, C.bz, C.bmax, C.bcrit});
+        if (nc > cap) return fail(c, NCORP_EOVERFLOW, "%d cells, room for %lld", nc, (long long)cap);
+        return NCORP_OK;
+    })
+}
+
+void ncorp_free(ncorp_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_set(c->A);
+    free_set(c->B);
+    free_set(c->Cset);
+    dfree(c->amx); dfree(c->amy); dfree(c->amz);
+    dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
+    dfree(c->tile_hist); dfree(c->scan_tmp); dfree(c->stage); dfree(c->stage2);
+    Cells &C = c->cells;
+    dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
+    dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
+    dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
+    dfree(C.bcrit); dfree(C.Mh); dfree(C.Ch); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+    WalkLists &W = c->wl;
+    dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
+    dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
+    dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
+    dfree(c->ctl);
+    if (c->ctl_h) cudaFreeHost(c->ctl_h);
+    delete c;
+}
+
+const char *ncorp_last_error(const ncorp_ctx *c) {
+    if (!c) return "null context";
+    return c->err[0] ? c->err : "no error";
+}
+
+}  // extern "C"

@@ -1,0 +1,426 @@
+// sort.cu -- root cube, quantisation, 3-D Hilbert keys, LSD radix sort of the
+// keys, gather of the moonlet state into key order, and exclusive scans.
+//
+// Sect. 3.4.6: cells of a level are ordered along a 3-D Hilbert curve and
+// moonlets are inserted in the Hilbert order of their leaves.  Here every
+// moonlet gets the 63-bit Hilbert index of its quantised position (21 bits
+// per axis inside the root cube) and the state is sorted by (key, previous
+// position) with a stable radix sort, so that every cell of every level owns
+// a contiguous range of moonlets and consecutive cells of a level are
+// consecutive along the curve.
+#include <cfloat>
+
+#include "ctx.h"
+
+namespace ncorp {
+
+// ---------------------------------------------------------------------------
+// bounding box
+// ---------------------------------------------------------------------------
+__global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                       int n, Ctrl *ctl) {
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            bad |= !isfinite(v[k]);
+            lo[k] = fmin(lo[k], v[k]);
+            hi[k] = fmax(hi[k], v[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(&ctl->err, ERR_NONFINITE);
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            atomicMin(&ctl->bbox[k], ord_encode(lo[k]));
+            atomicMax(&ctl->bbox[3 + k], ord_encode(hi[k]));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Hilbert index: J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc.
+// 707 (2004).  The axes are first brought to the curve's "transpose" form by
+// walking the bit planes from the top (a set bit reflects the lower bits of
+// axis 0, a clear bit swaps the lower bits of axis 0 and the current axis),
+// then Gray-encoded; the key interleaves the three transposed words, axis 0
+// first, most significant plane first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32_t a2) {
+    uint32_t w0 = a0, w1 = a1, w2 = a2;
+    for (uint32_t Q = 1u << (KEY_BITS - 1); Q > 1u; Q >>= 1) {
+        const uint32_t P = Q - 1u;
+        if (w0 & Q) w0 ^= P;
+        if (w1 & Q) {
+            w0 ^= P;
+        } else {
+            uint32_t t = (w0 ^ w1) & P;
+            w0 ^= t;
+            w1 ^= t;
+        }
+        if (w2 & Q) {
+            w0 ^= P;
+        } else {
+            uint32_t t = (w0 ^ w2) & P;
+            w0 ^= t;
+            w2 ^= t;
+        }
+    }
+    w1 ^= w0;
+    w2 ^= w1;
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << (KEY_BITS - 1); Q > 1u; Q >>= 1)
+        if (w2 & Q) t ^= Q - 1u;
+    w0 ^= t;
+    w1 ^= t;
+    w2 ^= t;
+    return (spread3(w0) << 2) | (spread3(w1) << 1) | spread3(w2);
+}
+
+// Root cube: centre = midpoint of the bounding box, side L = smallest power of
+// two >= (max extent)(1 + 2^-20); q = floor((x - x_lo) 2^21 / L), clamped.
+__device__ void root_cube(const Ctrl *ctl, double out[4]) {
+    double lo[3], hi[3], ext = 0.0;
+    for (int k = 0; k < 3; k++) {
+        lo[k] = ord_decode(ctl->bbox[k]);
+        hi[k] = ord_decode(ctl->bbox[3 + k]);
+        double e = dsub(hi[k], lo[k]);
+        if (e > ext) ext = e;
+    }
+    double t = dmul(ext, 1.0 + 0x1p-20);
+    double L = 1.0;
+    if (t > 0.0) {
+        while (L < t) L = dmul(L, 2.0);
+        while (dmul(L, 0.5) >= t) L = dmul(L, 0.5);
+    }
+    for (int k = 0; k < 3; k++) out[k] = dsub(dmul(dadd(lo[k], hi[k]), 0.5), dmul(L, 0.5));
+    out[3] = L;
+}
+
+__device__ __forceinline__ uint32_t quantise(double v, double lo, double scale) {
+    double f = floor(dmul(dsub(v, lo), scale));
+    f = fmax(f, 0.0);
+    f = fmin(f, (double)((1u << KEY_BITS) - 1u));
+    return static_cast<uint32_t>(f);
+}
+
+__global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                       int n, Ctrl *ctl, uint64_t *__restrict__ key, uint32_t *__restrict__ idx,
+                       uint32_t *__restrict__ qx, uint32_t *__restrict__ qy, uint32_t *__restrict__ qz) {
+    __shared__ double s_root[4];
+    if (threadIdx.x == 0) {
+        root_cube(ctl, s_root);
+        if (blockIdx.x == 0)
+            for (int k = 0; k < 4; k++) ctl->root[k] = s_root[k];
+    }
+    __syncthreads();
+    const double scale = ddiv(static_cast<double>(1u << KEY_BITS), s_root[3]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t a = quantise(x[i], s_root[0], scale);
+        uint32_t b = quantise(y[i], s_root[1], scale);
+        uint32_t c = quantise(z[i], s_root[2], scale);
+        qx[i] = a;
+        qy[i] = b;
+        qz[i] = c;
+        key[i] = hilbert_key(a, b, c);
+        idx[i] = static_cast<uint32_t>(i);
+    }
+}
+
+void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz) {
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[0], 0xff, 3 * sizeof(unsigned long long), c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[3], 0x00, 3 * sizeof(unsigned long long), c->stream));
+    int g = grid_for(n, 256, 4 * c->num_sms);
+    k_bbox<<<g, 256, 0, c->stream>>>(x, y, z, n, c->ctl);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int arrays: block sums, scan of the sums, block scans.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 512, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? s_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < nw) s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    int res = s_warp[wid] + incl - v;
+    if (total) *total = s_warp[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_reduce(const int *__restrict__ in, int n, int *__restrict__ bsum) {
+    __shared__ int s_warp[33];
+    long long base = static_cast<long long>(blockIdx.x) * SCAN_TILE;
+    int sum = 0;
+    for (int k = 0; k < SCAN_I; k++) {
+        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
+        if (i < n) sum += in[i];
+    }
+    int tot;
+    block_excl_scan(sum, s_warp, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int *bsum, int nb) {
+    __shared__ int s_warp[33];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        int i = b0 + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        int tot;
+        int ex = block_excl_scan(v, s_warp, &tot);
+        if (i < nb) bsum[i] = ex + s_carry;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[nb] = s_carry;
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, int n, const int *__restrict__ bsum,
+                             int nb, int *total) {
+    __shared__ int s_warp[33];
+    __shared__ int s_tile[SCAN_TILE];
+    long long base = static_cast<long long>(blockIdx.x) * SCAN_TILE;
+    for (int k = 0; k < SCAN_I; k++) {
+        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
+        s_tile[k * SCAN_T + threadIdx.x] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    int v[SCAN_I], sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        v[k] = s_tile[threadIdx.x * SCAN_I + k];
+        sum += v[k];
+    }
+    int ex = block_excl_scan(sum, s_warp, nullptr) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        s_tile[threadIdx.x * SCAN_I + k] = ex;
+        ex += v[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < SCAN_I; k++) {
+        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
+        if (i < n) out[i] = s_tile[k * SCAN_T + threadIdx.x];
+    }
+    if (total && blockIdx.x == 0 && threadIdx.x == 0) *total = bsum[nb];
+}
+
+void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
+    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb < 1) nb = 1;
+    if (c->scan_tmp_cap < nb + 1) {
+        if (c->scan_tmp) cudaFree(c->scan_tmp);
+        c->scan_tmp_cap = nb + 1024;
+        NCORP_CUDA_CHECK(cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_cap));
+    }
+    k_scan_reduce<<<nb, SCAN_T, 0, c->stream>>>(in, n, c->scan_tmp);
+    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_tmp, nb);
+    k_scan_apply<<<nb, SCAN_T, 0, c->stream>>>(in, out, n, c->scan_tmp, nb, total);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, uint32 value), 8-bit digits.  Each pass: tile
+// histograms, a scan of the digit-major histogram table, and a stable scatter.
+// Stability inside a tile comes from warp-synchronous ranking: each warp owns
+// a contiguous slice of the tile and walks it 32 keys at a time, ranking equal
+// digits with __match_any_sync; warps are then ordered by a per-digit prefix.
+// ---------------------------------------------------------------------------
+constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_SLICE = RS_TILE / RS_W;
+
+__global__ void k_rs_hist(const uint64_t *__restrict__ keys, int n, int shift, int *__restrict__ hist, int ntiles) {
+    __shared__ int s_cnt[256];
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    long long base = static_cast<long long>(blockIdx.x) * RS_TILE;
+    for (int k = 0; k < RS_I; k++) {
+        long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 0xffu], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
+                             const int *__restrict__ offs, int ntiles) {
+    __shared__ int s_cnt[RS_W][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
+    __syncwarp();
+    const long long base = static_cast<long long>(blockIdx.x) * RS_TILE + static_cast<long long>(w) * RS_SLICE;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t kk[RS_I];
+    uint32_t vv[RS_I];
+    int rank[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        long long i = base + r * 32 + lane;
+        bool ok = i < n;
+        kk[r] = ok ? kin[i] : 0ull;
+        vv[r] = ok ? vin[i] : 0u;
+        int d = ok ? static_cast<int>((kk[r] >> shift) & 0xffu) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = ok ? s_cnt[w][d] : 0;
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && (__ffs(peers) - 1) == lane) s_cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps, per digit
+        int d = threadIdx.x;
+        int acc = 0;
+        for (int ww = 0; ww < RS_W; ww++) {
+            int t = s_cnt[ww][d];
+            s_cnt[ww][d] = acc;
+            acc += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        long long i = base + r * 32 + lane;
+        if (i < n) {
+            int d = static_cast<int>((kk[r] >> shift) & 0xffu);
+            int pos = offs[d * ntiles + blockIdx.x] + s_cnt[w][d] + rank[r];
+            kout[pos] = kk[r];
+            vout[pos] = vv[r];
+        }
+    }
+}
+
+// Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
+// the key are significant (a multiple of 8 passes is rounded up; an even
+// number of passes leaves the result in the input buffers).
+void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
+                    int bits) {
+    if (n <= 1) return;
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    int need = 256 * ntiles;
+    if (c->tile_hist_cap < need) {
+        if (c->tile_hist) cudaFree(c->tile_hist);
+        c->tile_hist_cap = need + 4096;
+        NCORP_CUDA_CHECK(cudaMalloc(&c->tile_hist, sizeof(int) * c->tile_hist_cap));
+    }
+    int passes = (bits + 7) / 8;
+    if (passes & 1) passes++;
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    for (int ps = 0; ps < passes; ps++) {
+        int shift = 8 * ps;
+        k_rs_hist<<<ntiles, RS_T, 0, c->stream>>>(ki, n, shift, c->tile_hist, ntiles);
+        scan_exclusive(c, c->tile_hist, c->tile_hist, need, nullptr);
+        k_rs_scatter<<<ntiles, RS_T, 0, c->stream>>>(ki, vi, ko, vo, n, shift, c->tile_hist, ntiles);
+        NCORP_CUDA_CHECK(cudaGetLastError());
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+}
+
+__global__ void k_iota(uint32_t *idx, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
+}
+
+void launch_iota(ncorp_ctx *c, uint32_t *idx, int n) {
+    k_iota<<<grid_for(n, 256, 8 * c->num_sms), 256, 0, c->stream>>>(idx, n);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// gather: dst[i] = src[idx[i]] for the state (positions and velocities from
+// src_xv, the rest from src_rest), the caller index and the quantised coords.
+// ---------------------------------------------------------------------------
+struct GatherArgs {
+    const double *x, *y, *z, *vx, *vy, *vz, *m, *R;
+    const int *perm;
+    const uint32_t *qx, *qy, *qz;
+    double *ox, *oy, *oz, *ovx, *ovy, *ovz, *om, *oR;
+    int *operm;
+    uint32_t *oqx, *oqy, *oqz;
+    const uint32_t *idx;
+    int n;
+};
+
+__global__ void k_gather(GatherArgs g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        int j = static_cast<int>(g.idx[i]);
+        g.ox[i] = g.x[j];
+        g.oy[i] = g.y[j];
+        g.oz[i] = g.z[j];
+        g.ovx[i] = g.vx[j];
+        g.ovy[i] = g.vy[j];
+        g.ovz[i] = g.vz[j];
+        g.om[i] = g.m[j];
+        g.oR[i] = g.R[j];
+        g.operm[i] = g.perm[j];
+        g.oqx[i] = g.qx[j];
+        g.oqy[i] = g.qy[j];
+        g.oqz[i] = g.qz[j];
+    }
+}
+
+void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
+                   const uint32_t *idx) {
+    GatherArgs g;
+    g.x = src_xv.x; g.y = src_xv.y; g.z = src_xv.z;
+    g.vx = src_xv.vx; g.vy = src_xv.vy; g.vz = src_xv.vz;
+    g.m = src_rest.m; g.R = src_rest.R; g.perm = src_rest.perm;
+    g.qx = src_xv.qx; g.qy = src_xv.qy; g.qz = src_xv.qz;
+    g.ox = dst.x; g.oy = dst.y; g.oz = dst.z;
+    g.ovx = dst.vx; g.ovy = dst.vy; g.ovz = dst.vz;
+    g.om = dst.m; g.oR = dst.R; g.operm = dst.perm;
+    g.oqx = dst.qx; g.oqy = dst.qy; g.oqz = dst.qz;
+    g.idx = idx;
+    g.n = n;
+    k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace ncorp

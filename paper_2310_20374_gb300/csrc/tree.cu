@@ -1,0 +1,601 @@
+// tree.cu -- octree build from sorted Hilbert keys (Sect. 3.4.1, 3.4.6) and
+// the two tree climbs of Sect. 3.4.2 (collision search: Eqs. center, rmax,
+// rcrit; gravity: Eqs. expansion_center, rmax_2, rcrit_2 with the corner cap,
+// the opening angle theta(M) of Dehnen 2002 Eq. 13) with P2M
+// (Eq. multipole_moment) at the leaves and M2M (App. C) at the parents.
+//
+// Cells are stored level-major, in Hilbert order within a level, children of a
+// cell contiguous; every cell owns a contiguous range of the key-sorted
+// moonlets.  All geometry that decides the walk (centres, r_max, r_crit) is
+// computed with exactly rounded FP64 operations in the same order as a plain
+// sequential evaluation (moonlets in key order, children in cell order), so
+// it is reproducible bit for bit.
+#include "ctx.h"
+
+namespace ncorp {
+
+// exponents (a, b, c) of every packed symmetric index up to order 7
+struct ExpTable {
+    unsigned char e[off(MAXP + 2)][3];
+};
+constexpr ExpTable make_exp_table() {
+    ExpTable t{};
+    for (int n = 0; n <= MAXP + 1; n++)
+        for (int k = 0; k <= n; k++)
+            for (int c = 0; c <= k; c++) {
+                int idx = off(n) + tri(k) + c;
+                t.e[idx][0] = static_cast<unsigned char>(n - k);
+                t.e[idx][1] = static_cast<unsigned char>(k - c);
+                t.e[idx][2] = static_cast<unsigned char>(c);
+            }
+    return t;
+}
+__constant__ ExpTable c_exp = make_exp_table();
+
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *__restrict__ a, int lo, int hi, uint64_t t) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Build: one cooperative launch, one pass per level.  Phase 1 (warp per cell
+// of the level): a cell with more than s moonlets finds the boundaries of its
+// octants by binary search on the next 3 key bits (the Hilbert digit of the
+// child), so the non-empty children come out in Hilbert order.  Phase 2: a
+// grid-wide exclusive scan of the children counts places the children of the
+// level contiguously after it, in the order of their parents.
+// ---------------------------------------------------------------------------
+struct BuildArgs {
+    const uint64_t *key;
+    const uint32_t *qx, *qy, *qz;
+    int n, s, cap;
+    int *level, *first, *count, *child0, *nchild, *parent;
+    uint32_t *cx, *cy, *cz;
+    int *bounds, *blocksum;
+    Ctrl *ctl;
+};
+
+__global__ void k_build_init(BuildArgs A) {
+    A.level[0] = 0;
+    A.first[0] = 0;
+    A.count[0] = A.n;
+    A.child0[0] = -1;
+    A.nchild[0] = 0;
+    A.parent[0] = -1;
+    A.cx[0] = A.cy[0] = A.cz[0] = 0;
+    A.ctl->level_start[0] = 0;
+    A.ctl->level_start[1] = 1;
+    A.ctl->n_cells = 1;
+    A.ctl->max_level = 0;
+    A.ctl->n_leaves = 0;
+    A.ctl->bar_count = 0;
+}
+
+__global__ void __launch_bounds__(256) k_build(BuildArgs A) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ int s_red[32];
+    __shared__ int s_base;
+    volatile Ctrl *vc = A.ctl;
+    for (int lev = 0; lev < MAX_LEVEL; lev++) {
+        const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
+        if (ls >= le) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->max_level = lev;
+        const int ncl = le - ls;
+        const int chunk = (ncl + gridDim.x - 1) / gridDim.x;
+        const int cb = min(le, ls + blockIdx.x * chunk), ce = min(le, cb + chunk);
+        // ---- phase 1: octant boundaries
+        int wsum = 0;
+        for (int c = cb + wid; c < ce; c += nw) {
+            const int cnt = c < A.cap ? __ldcg(&A.count[c]) : 0, f = c < A.cap ? __ldcg(&A.first[c]) : 0;
+            int nch = 0;
+            if (cnt > A.s && c < A.cap) {
+                const uint64_t pref = A.key[f] >> (63 - 3 * lev);
+                const int shift = 60 - 3 * lev;
+                int b = f + cnt;
+                if (lane < 8) b = lower_bound_u64(A.key, f, f + cnt, ((pref << 3) | (uint64_t)lane) << shift);
+                const int bn = __shfl_down_sync(0xffffffffu, b, 1);
+                const unsigned mask = __ballot_sync(0xffffffffu, lane < 8 && bn > b);
+                nch = __popc(mask);
+                if (lane < 9) A.bounds[(size_t)c * 9 + lane] = b;
+            }
+            if (lane == 0 && c < A.cap) A.nchild[c] = nch;
+            wsum += nch;
+        }
+        if (lane == 0) s_red[wid] = wsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; w++) t += s_red[w];
+            A.blocksum[blockIdx.x] = t;
+        }
+        if (!grid_sync(A.ctl)) return;
+        // ---- phase 2: place the children of this level
+        if (wid == 0) {
+            int t = 0;
+            for (int b = lane; b < (int)blockIdx.x; b += 32) t += ((volatile int *)A.blocksum)[b];
+            t = warp_sum(t);
+            int run = le + t;
+            for (int c0 = cb; c0 < ce; c0 += 32) {
+                const int c = c0 + lane;
+                const int v = (c < ce && c < A.cap) ? ((volatile int *)A.nchild)[c] : 0;
+                int incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (c < ce && c < A.cap) A.child0[c] = v > 0 ? run + incl - v : -1;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) s_base = run;
+        }
+        __syncthreads();
+        for (int c = cb + wid; c < ce; c += nw) {
+            if (c >= A.cap) break;
+            const int nch = ((volatile int *)A.nchild)[c];
+            if (nch == 0) continue;
+            const int c0 = ((volatile int *)A.child0)[c];
+            int b = 0, bn = 0;
+            if (lane < 9) b = ((volatile int *)A.bounds)[(size_t)c * 9 + lane];
+            bn = __shfl_down_sync(0xffffffffu, b, 1);
+            const bool ne = lane < 8 && bn > b;
+            const unsigned mask = __ballot_sync(0xffffffffu, ne);
+            if (ne) {
+                const int ci = c0 + __popc(mask & ((1u << lane) - 1u));
+                if (ci < A.cap) {
+                    const int sh = KEY_BITS - (lev + 1);
+                    A.level[ci] = lev + 1;
+                    A.first[ci] = b;
+                    A.count[ci] = bn - b;
+                    A.child0[ci] = -1;
+                    A.nchild[ci] = 0;
+                    A.parent[ci] = c;
+                    A.cx[ci] = A.qx[b] >> sh;
+                    A.cy[ci] = A.qy[b] >> sh;
+                    A.cz[ci] = A.qz[b] >> sh;
+                } else {
+                    atomicOr(&A.ctl->err, ERR_CELLS);
+                }
+            }
+        }
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+            A.ctl->level_start[lev + 2] = s_base;
+            A.ctl->n_cells = s_base;
+        }
+        if (!grid_sync(A.ctl)) return;
+    }
+}
+
+__global__ void k_collect_leaves(const int *__restrict__ nchild, const Ctrl *ctl, int cap, int *leaves, int *n_leaves) {
+    if (aborted(ctl)) return;
+    const int nc = min(ctl->n_cells, cap);
+    for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int is_leaf = (i < nc && nchild[i] == 0) ? 1 : 0;
+        const int slot = warp_append(n_leaves, is_leaf);
+        if (is_leaf) leaves[slot] = i;
+    }
+}
+
+static int coop_grid(ncorp_ctx *c, const void *kernel, int block, size_t smem) {
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    return per_sm * c->num_sms;
+}
+
+void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
+    Cells &C = c->cells;
+    BuildArgs A;
+    A.key = P.key;
+    A.qx = P.qx; A.qy = P.qy; A.qz = P.qz;
+    A.n = n; A.s = s; A.cap = C.cap;
+    A.level = C.level; A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
+    A.parent = C.parent; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
+    A.bounds = C.bounds; A.blocksum = C.blocksum; A.ctl = c->ctl;
+    k_build_init<<<1, 1, 0, c->stream>>>(A);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    const int block = 256;
+    int grid = coop_grid(c, reinterpret_cast<const void *>(k_build), block, 0);
+    void *args[] = {&A};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_build), dim3(grid), dim3(block),
+                                                 args, 0, c->stream));
+    k_collect_leaves<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(C.nchild, c->ctl, C.cap, C.leaves,
+                                                                                 &c->ctl->n_leaves);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Corner cap (Sect. 3.4.2): distance from s to the farthest corner of the
+// cell's cube, the cube widened by L 2^-48 on each side.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double corner_distance(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz,
+                                                  double sx, double sy, double sz) {
+    const double L = ctl->root[3];
+    double h = L;
+    for (int k = 0; k < lev; k++) h = dmul(h, 0.5);
+    const double eps = dmul(L, 0x1p-48);
+    const uint32_t cc[3] = {cx, cy, cz};
+    const double s[3] = {sx, sy, sz};
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double lo = dadd(ctl->root[k], dmul(static_cast<double>(cc[k]), h));
+        const double a = dsub(s[k], dsub(lo, eps));
+        const double b = dsub(dadd(dadd(lo, h), eps), s[k]);
+        d[k] = a > b ? a : b;
+    }
+    return dnorm3(d[0], d[1], d[2]);
+}
+
+__device__ __forceinline__ double cell_side(const Ctrl *ctl, int lev) {
+    double h = ctl->root[3];
+    for (int k = 0; k < lev; k++) h = dmul(h, 0.5);
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// Gravity climb: warp per leaf, bottom-up through per-cell arrival counters
+// (the last child to finish climbs to its parent; no waiting).  Lane 0 does
+// the geometry sequentially; all lanes share the multipole coefficients.
+// ---------------------------------------------------------------------------
+struct ClimbArgs {
+    const double *x, *y, *z, *m;
+    const double *vx, *vy, *vz, *R;
+    int *first, *count, *child0, *nchild, *parent, *level, *arrive;
+    uint32_t *cx, *cy, *cz;
+    double *M, *sx, *sy, *sz, *rmax, *rcrit, *rho;
+    void *Mh;
+    const int *leaves;
+    const Ctrl *ctl;
+    double G, dt, theta;
+};
+
+template <int P, typename real>
+__device__ void p2m_leaf(const ClimbArgs &A, int c, double sx, double sy, double sz, double rho, real *Mh) {
+    constexpr int NM = num_m(P);
+    const int lane = threadIdx.x & 31;
+    const int f = A.first[c], cnt = A.count[c];
+    const double irho = 1.0 / rho;   // exact: rho is a power of two
+    real acc[(NM + 31) / 32];
+    int ex[(NM + 31) / 32][3];
+#pragma unroll
+    for (int r = 0; r < (NM + 31) / 32; r++) {
+        acc[r] = real(0);
+        const int j = lane + 32 * r;
+        const int si = j == 0 ? 0 : j + 3;
+        ex[r][0] = j < NM ? c_exp.e[si][0] : 0;
+        ex[r][1] = j < NM ? c_exp.e[si][1] : 0;
+        ex[r][2] = j < NM ? c_exp.e[si][2] : 0;
+    }
+    for (int k0 = 0; k0 < cnt; k0 += 32) {
+        real dx = 0, dy = 0, dz = 0, mu = 0;
+        if (k0 + lane < cnt) {
+            const int k = f + k0 + lane;
+            dx = static_cast<real>(dmul(dsub(A.x[k], sx), irho));
+            dy = static_cast<real>(dmul(dsub(A.y[k], sy), irho));
+            dz = static_cast<real>(dmul(dsub(A.z[k], sz), irho));
+            mu = static_cast<real>(A.G * A.m[k]);
+        }
+        const int lim = min(32, cnt - k0);
+        for (int t = 0; t < lim; t++) {
+            const real px = __shfl_sync(0xffffffffu, dx, t), py = __shfl_sync(0xffffffffu, dy, t);
+            const real pz = __shfl_sync(0xffffffffu, dz, t), pm = __shfl_sync(0xffffffffu, mu, t);
+#pragma unroll
+            for (int r = 0; r < (NM + 31) / 32; r++) {
+                real v = pm;
+                for (int i = 0; i < ex[r][0]; i++) v *= px;
+                for (int i = 0; i < ex[r][1]; i++) v *= py;
+                for (int i = 0; i < ex[r][2]; i++) v *= pz;
+                acc[r] += v;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < (NM + 31) / 32; r++) {
+        const int j = lane + 32 * r;
+        if (j < NM) {
+            const real inv = static_cast<real>(c_ifact[ex[r][0]] * c_ifact[ex[r][1]] * c_ifact[ex[r][2]]);
+            Mh[(size_t)c * NM + j] = acc[r] * inv;
+        }
+    }
+}
+
+// M-hat_alpha(P) = sum_children sum_{gamma <= alpha, |gamma| != 1}
+//   (-Lambda/rho_P)^(alpha-gamma)/(alpha-gamma)! (rho_c/rho_P)^|gamma| M-hat_gamma(child),
+// Lambda = s_P - s_child  (App. C with the binomial expansion in multi-index form)
+template <int P, typename real>
+__device__ void m2m_parent(const ClimbArgs &A, int pc, double sx, double sy, double sz, double rho, real *Mh) {
+    constexpr int NM = num_m(P);
+    const int lane = threadIdx.x & 31;
+    const int c0 = A.child0[pc], nch = A.nchild[pc];
+    const double irho = 1.0 / rho;
+    for (int j = lane; j < NM; j += 32) {
+        const int si = j == 0 ? 0 : j + 3;
+        const int a = c_exp.e[si][0], b = c_exp.e[si][1], cc = c_exp.e[si][2];
+        real acc = 0;
+        for (int ch = c0; ch < c0 + nch; ch++) {
+            const real lx = static_cast<real>(-dmul(dsub(sx, __ldcg(&A.sx[ch])), irho));
+            const real ly = static_cast<real>(-dmul(dsub(sy, __ldcg(&A.sy[ch])), irho));
+            const real lz = static_cast<real>(-dmul(dsub(sz, __ldcg(&A.sz[ch])), irho));
+            const real ratio = static_cast<real>(__ldcg(&A.rho[ch]) * irho);
+            const real *Mc = Mh + (size_t)ch * NM;
+            for (int ga = 0; ga <= a; ga++)
+                for (int gb = 0; gb <= b; gb++)
+                    for (int gc = 0; gc <= cc; gc++) {
+                        const int gn = ga + gb + gc;
+                        if (gn == 1) continue;
+                        const real mg = __ldcg(&Mc[midx(ga, gb, gc)]);
+                        real t = static_cast<real>(c_ifact[a - ga] * c_ifact[b - gb] * c_ifact[cc - gc]) * mg;
+                        for (int i = 0; i < a - ga; i++) t *= lx;
+                        for (int i = 0; i < b - gb; i++) t *= ly;
+                        for (int i = 0; i < cc - gc; i++) t *= lz;
+                        for (int i = 0; i < gn; i++) t *= ratio;
+                        acc += t;
+                    }
+        }
+        Mh[(size_t)pc * NM + j] = acc;
+    }
+}
+
+template <int P, typename real>
+__global__ void __launch_bounds__(256) k_climb_gravity(ClimbArgs A) {
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
+    const int n_leaves = A.ctl->n_leaves;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    real *Mh = static_cast<real *>(A.Mh);
+    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
+    int c = A.leaves[gw];
+    // ---- leaf geometry (lane 0, sequential in key order)
+    double gsx = 0, gsy = 0, gsz = 0, grho = 1;
+    if (lane == 0) {
+        const int f = A.first[c], cnt = A.count[c];
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int k = f; k < f + cnt; k++) {
+            const double m = A.m[k];
+            M = dadd(M, m);
+            sx = dadd(sx, dmul(m, A.x[k]));
+            sy = dadd(sy, dmul(m, A.y[k]));
+            sz = dadd(sz, dmul(m, A.z[k]));
+        }
+        sx = ddiv(sx, M);
+        sy = ddiv(sy, M);
+        sz = ddiv(sz, M);
+        double rmax = 0;
+        for (int k = f; k < f + cnt; k++) {
+            const double r = dnorm3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz));
+            if (r > rmax) rmax = r;
+        }
+        const int lev = A.level[c];
+        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        const double rho = rmax > 0.0 ? pow2_ceil(rmax) : cell_side(A.ctl, lev);
+        A.M[c] = M;
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rho[c] = rho;
+        gsx = sx; gsy = sy; gsz = sz; grho = rho;
+    }
+    gsx = __shfl_sync(0xffffffffu, gsx, 0);
+    gsy = __shfl_sync(0xffffffffu, gsy, 0);
+    gsz = __shfl_sync(0xffffffffu, gsz, 0);
+    grho = __shfl_sync(0xffffffffu, grho, 0);
+    p2m_leaf<P, real>(A, c, gsx, gsy, gsz, grho, Mh);
+    // ---- climb
+    while (true) {
+        __threadfence();
+        __syncwarp();
+        int pc = A.parent[c];
+        if (pc < 0) break;
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) break;
+        __threadfence();
+        c = pc;
+        if (lane == 0) {
+            const int c0 = A.child0[c], nch = A.nchild[c];
+            double M = 0, sx = 0, sy = 0, sz = 0;
+            for (int ch = c0; ch < c0 + nch; ch++) {
+                const double mc = __ldcg(&A.M[ch]);
+                M = dadd(M, mc);
+                sx = dadd(sx, dmul(mc, __ldcg(&A.sx[ch])));
+                sy = dadd(sy, dmul(mc, __ldcg(&A.sy[ch])));
+                sz = dadd(sz, dmul(mc, __ldcg(&A.sz[ch])));
+            }
+            sx = ddiv(sx, M);
+            sy = ddiv(sy, M);
+            sz = ddiv(sz, M);
+            double rmax = 0;
+            for (int ch = c0; ch < c0 + nch; ch++) {
+                const double r = dadd(__ldcg(&A.rmax[ch]), dnorm3(dsub(__ldcg(&A.sx[ch]), sx),
+                                                                   dsub(__ldcg(&A.sy[ch]), sy),
+                                                                   dsub(__ldcg(&A.sz[ch]), sz)));
+                if (r > rmax) rmax = r;
+            }
+            const int lev = A.level[c];
+            const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+            if (cap < rmax) rmax = cap;
+            const double rho = rmax > 0.0 ? pow2_ceil(rmax) : cell_side(A.ctl, lev);
+            A.M[c] = M;
+            A.sx[c] = sx;
+            A.sy[c] = sy;
+            A.sz[c] = sz;
+            A.rmax[c] = rmax;
+            A.rho[c] = rho;
+            gsx = sx; gsy = sy; gsz = sz; grho = rho;
+        }
+        gsx = __shfl_sync(0xffffffffu, gsx, 0);
+        gsy = __shfl_sync(0xffffffffu, gsy, 0);
+        gsz = __shfl_sync(0xffffffffu, gsz, 0);
+        grho = __shfl_sync(0xffffffffu, grho, 0);
+        m2m_parent<P, real>(A, c, gsx, gsy, gsz, grho, Mh);
+    }
+    }
+}
+
+// theta(M) of Dehnen (2002) Eq. 13: theta^5/(1-theta)^2 = K (M/M_tot)^(-1/3),
+// K = theta_min^5/(1-theta_min)^2, solved as f(theta) = theta^15 M -
+// K^3 M_tot (1-theta)^6 = 0 by 64 bisection steps on [theta_min, 1).
+__device__ double theta_of(double M, double Mtot, double tmin) {
+    const double t2 = dmul(tmin, tmin), t4 = dmul(t2, t2), t5 = dmul(t4, tmin);
+    const double u = dsub(1.0, tmin), u2 = dmul(u, u);
+    const double K = ddiv(t5, u2);
+    const double K3 = dmul(dmul(K, K), K);
+    const double rhs = dmul(K3, Mtot);
+    double lo = tmin, hi = 1.0;
+    for (int it = 0; it < 64; it++) {
+        const double mid = dmul(dadd(lo, hi), 0.5);
+        const double m2 = dmul(mid, mid), m3 = dmul(m2, mid), m6 = dmul(m3, m3), m12 = dmul(m6, m6),
+                     m15 = dmul(m12, m3);
+        const double w = dsub(1.0, mid), w2 = dmul(w, w), w3 = dmul(w2, w), w6 = dmul(w3, w3);
+        const double f = dsub(dmul(m15, M), dmul(rhs, w6));
+        if (f > 0.0) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+__global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__ rmax, double *__restrict__ rcrit,
+                        const Ctrl *ctl, int cap, double tmin) {
+    if (aborted(ctl)) return;
+    const int nc = min(ctl->n_cells, cap);
+    const double Mtot = M[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        rcrit[i] = ddiv(rmax[i], theta_of(M[i], Mtot, tmin));
+}
+
+template <int P, typename real>
+static void climb_gravity_t(ncorp_ctx *c, const ClimbArgs &A) {
+    const int block = 256;
+    k_climb_gravity<P, real><<<8 * c->num_sms, block, 0, c->stream>>>(A);
+}
+
+void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
+    Cells &C = c->cells;
+    ClimbArgs A{};
+    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;
+    A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
+    A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
+    A.M = C.M; A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rmax = C.rmax; A.rcrit = C.rcrit; A.rho = C.rho;
+    A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
+#define NCORP_CLIMB_CASE(PP)                                             \
+    case PP:                                                             \
+        if (mixed) climb_gravity_t<PP, float>(c, A);                     \
+        else climb_gravity_t<PP, double>(c, A);                          \
+        break;
+    switch (p) {
+        NCORP_CLIMB_CASE(1)
+        NCORP_CLIMB_CASE(2)
+        NCORP_CLIMB_CASE(3)
+        NCORP_CLIMB_CASE(4)
+        NCORP_CLIMB_CASE(5)
+        NCORP_CLIMB_CASE(6)
+        default: break;
+    }
+#undef NCORP_CLIMB_CASE
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    k_rcrit<<<grid_for(C.cap, 256, 8 * c->num_sms), 256, 0, c->stream>>>(C.M, C.rmax, C.rcrit, c->ctl, C.cap, theta);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Collision climb: thread per leaf, bottom-up.  s-bar is the mean moonlet
+// position (children weighted by their moonlet counts), r_max as above, and
+// r_crit = r_max + max over children of (r_crit - r_max), a moonlet's being
+// R + dt |v|.
+// ---------------------------------------------------------------------------
+__global__ void k_climb_collision(ClimbArgs A) {
+    if (aborted(A.ctl)) return;
+    const int n_leaves = A.ctl->n_leaves;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
+    int c = A.leaves[t];
+    {
+        const int f = A.first[c], cnt = A.count[c];
+        double sx = 0, sy = 0, sz = 0;
+        for (int k = f; k < f + cnt; k++) {
+            sx = dadd(sx, A.x[k]);
+            sy = dadd(sy, A.y[k]);
+            sz = dadd(sz, A.z[k]);
+        }
+        const double w = static_cast<double>(cnt);
+        sx = ddiv(sx, w);
+        sy = ddiv(sy, w);
+        sz = ddiv(sz, w);
+        double rmax = 0, ex = 0;
+        for (int k = f; k < f + cnt; k++) {
+            const double r = dnorm3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz));
+            if (r > rmax) rmax = r;
+            const double e = dadd(A.R[k], dmul(A.dt, dnorm3(A.vx[k], A.vy[k], A.vz[k])));
+            if (e > ex) ex = e;
+        }
+        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rcrit[c] = dadd(rmax, ex);
+    }
+    while (true) {
+        __threadfence();
+        const int pc = A.parent[c];
+        if (pc < 0) break;
+        if (atomicAdd(&A.arrive[pc], 1) != A.nchild[pc] - 1) break;
+        __threadfence();
+        c = pc;
+        const int c0 = A.child0[c], nch = A.nchild[c];
+        double sx = 0, sy = 0, sz = 0;
+        for (int ch = c0; ch < c0 + nch; ch++) {
+            const double w = static_cast<double>(A.count[ch]);
+            sx = dadd(sx, dmul(w, __ldcg(&A.sx[ch])));
+            sy = dadd(sy, dmul(w, __ldcg(&A.sy[ch])));
+            sz = dadd(sz, dmul(w, __ldcg(&A.sz[ch])));
+        }
+        const double w = static_cast<double>(A.count[c]);
+        sx = ddiv(sx, w);
+        sy = ddiv(sy, w);
+        sz = ddiv(sz, w);
+        double rmax = 0, ex = 0;
+        for (int ch = c0; ch < c0 + nch; ch++) {
+            const double rm = __ldcg(&A.rmax[ch]);
+            const double r = dadd(rm, dnorm3(dsub(__ldcg(&A.sx[ch]), sx), dsub(__ldcg(&A.sy[ch]), sy),
+                                             dsub(__ldcg(&A.sz[ch]), sz)));
+            if (r > rmax) rmax = r;
+            const double e = dsub(__ldcg(&A.rcrit[ch]), rm);
+            if (e > ex) ex = e;
+        }
+        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rcrit[c] = dadd(rmax, ex);
+    }
+    }
+}
+
+void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
+                            const double *vz, double dt) {
+    Cells &C = c->cells;
+    ClimbArgs A{};
+    A.x = P.x; A.y = P.y; A.z = P.z; A.R = P.R; A.vx = vx; A.vy = vy; A.vz = vz;
+    A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
+    A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
+    A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
+    A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
+    k_climb_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace ncorp

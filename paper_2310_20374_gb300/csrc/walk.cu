@@ -1,0 +1,343 @@
+// walk.cu -- the symmetric dual-tree walk of Algorithm TreeWalk (Sect. 3.4.5)
+// for mutual gravity and for collision search, run breadth first.
+//
+// The recursive walk is replaced by a frontier of pending (A, B) cell pairs
+// that is expanded one generation per pass of a single cooperative launch;
+// every pair takes the branch the algorithm gives it, in the algorithm's
+// order:
+//   A == B : N_A <= N_cs or A a leaf -> direct self interaction,
+//            else all pairs (a, b), a <= b, of children (up to 36);
+//   A != B : N_A N_B < N_cc,pre      -> direct;
+//            well separated          -> M2L (gravity) / nothing (collisions);
+//            N_A N_B < N_cc,post or both leaves -> direct;
+//            split A if A is not a leaf and (r_crit,A > r_crit,B or B is a
+//            leaf), else split B.
+// Well separated: (r_crit,A + r_crit,B)^2 <= |s_A - s_B|^2 for gravity; for
+// collisions the pair is pruned only if ((r_crit,A + r_crit,B)(1 + 2^-40))^2
+// < |s_A - s_B|^2, a margin that keeps rounding from dropping a pair that the
+// pairwise test would accept.
+//
+// A direct interaction between cells that are not both leaves is refined into
+// leaf-leaf and leaf-self pieces covering exactly the same moonlet pairs (a
+// "forced" frontier entry that is only ever split), so that the direct lists
+// only hold leaves; the decision itself is counted once, where it is taken.
+#include "ctx.h"
+
+namespace ncorp {
+
+struct WalkArgs {
+    int gravity;
+    long long n_cs, pre, post;
+    const int *count, *child0, *nchild;
+    const double *sx, *sy, *sz, *rcrit;
+    int2 *front0, *front1;
+    int *fcount;
+    int front_cap;
+    int2 *m2l;
+    int m2l_cap;
+    int2 *p2p;
+    int p2p_cap;
+    int *self;
+    int self_cap;
+    Ctrl *ctl;
+};
+
+constexpr int FORCED = static_cast<int>(0x80000000u);
+
+__global__ void k_walk_init(WalkArgs A) {
+    A.front0[0] = make_int2(0, 0);
+    A.fcount[0] = 1;
+    A.ctl->n_m2l = 0;
+    A.ctl->n_p2p = 0;
+    A.ctl->n_self = 0;
+    A.ctl->dec_pairs = 0;
+    A.ctl->dec_self = 0;
+    A.ctl->n_inter = 0;
+    A.ctl->walk_iters = 0;
+    A.ctl->bar_count = 0;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
+    const int lane = threadIdx.x & 31;
+    if (aborted(A.ctl)) return;
+    volatile int *vcount = A.fcount;
+    int it = 0;
+    for (; it < WALK_MAX_ITERS; it++) {
+        const int nf = min(vcount[it], A.front_cap);
+        if (nf == 0) break;
+        const int2 *cur = (it & 1) ? A.front1 : A.front0;
+        int2 *nxt = (it & 1) ? A.front0 : A.front1;
+        int *ncount = A.fcount + it + 1;
+        const int stride = gridDim.x * blockDim.x;
+        for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nf; base += stride) {
+            const int i = base + lane;
+            const bool valid = i < nf;
+            int cA = 0, cB = 0;
+            bool forced = false;
+            if (valid) {
+                const int2 e = __ldcg(&cur[i]);
+                cA = e.x;
+                cB = e.y & 0x7fffffff;
+                forced = (e.y & FORCED) != 0;
+            }
+            // outcome of this lane
+            int emit_m2l = 0, emit_p2p = 0, emit_self = 0;
+            int split_kind = 0;       // 0 none, 1 self-split of cA, 2 split cA against cB, 3 split cB against cA
+            bool split_forced = false;
+            long long dpair = 0, dself = 0, inter = 0;
+            if (valid) {
+                const int nA = A.count[cA], nB = A.count[cB];
+                const bool leafA = A.nchild[cA] == 0, leafB = A.nchild[cB] == 0;
+                if (cA == cB) {
+                    if (forced || nA <= A.n_cs || leafA) {
+                        if (!forced) {
+                            dself = 1;
+                            inter = static_cast<long long>(nA) * (nA - 1) / 2;
+                        }
+                        if (leafA) emit_self = 1;
+                        else { split_kind = 1; split_forced = true; }
+                    } else {
+                        split_kind = 1;
+                    }
+                } else if (forced) {
+                    if (leafA && leafB) emit_p2p = 1;
+                    else { split_kind = leafA ? 3 : 2; split_forced = true; }
+                } else {
+                    const long long prod = static_cast<long long>(nA) * nB;
+                    bool direct = false;
+                    if (prod < A.pre) {
+                        direct = true;
+                    } else {
+                        const double dx = dsub(A.sx[cA], A.sx[cB]);
+                        const double dy = dsub(A.sy[cA], A.sy[cB]);
+                        const double dz = dsub(A.sz[cA], A.sz[cB]);
+                        const double d2 = dsq3(dx, dy, dz);
+                        const double rA = A.rcrit[cA], rB = A.rcrit[cB];
+                        bool sep;
+                        if (A.gravity) {
+                            const double t = dadd(rA, rB);
+                            sep = dmul(t, t) <= d2;
+                        } else {
+                            const double t = dmul(dadd(rA, rB), 1.0 + 0x1p-40);
+                            sep = dmul(t, t) < d2;
+                        }
+                        if (sep) {
+                            if (A.gravity) emit_m2l = 1;
+                        } else if (prod < A.post || (leafA && leafB)) {
+                            direct = true;
+                        } else if (!leafA && (rA > rB || leafB)) {
+                            split_kind = 2;
+                        } else {
+                            split_kind = 3;
+                        }
+                    }
+                    if (direct) {
+                        dpair = 1;
+                        inter = prod;
+                        if (leafA && leafB) emit_p2p = 1;
+                        else { split_kind = leafA ? 3 : 2; split_forced = true; }
+                    }
+                }
+            }
+            // statistics
+            dpair = warp_sum_ll(dpair);
+            dself = warp_sum_ll(dself);
+            inter = warp_sum_ll(inter);
+            if (lane == 0) {
+                if (dpair) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_pairs),
+                                     static_cast<unsigned long long>(dpair));
+                if (dself) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_self),
+                                     static_cast<unsigned long long>(dself));
+                if (inter) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_inter),
+                                     static_cast<unsigned long long>(inter));
+            }
+            // outputs
+            {
+                const int slot = warp_append(&A.ctl->n_m2l, emit_m2l);
+                if (emit_m2l) {
+                    if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
+                    else atomicOr(&A.ctl->err, ERR_M2L);
+                }
+            }
+            {
+                const int slot = warp_append(&A.ctl->n_p2p, emit_p2p);
+                if (emit_p2p) {
+                    if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
+                    else atomicOr(&A.ctl->err, ERR_P2P);
+                }
+            }
+            {
+                const int slot = warp_append(&A.ctl->n_self, emit_self);
+                if (emit_self) {
+                    if (slot < A.self_cap) A.self[slot] = cA;
+                    else atomicOr(&A.ctl->err, ERR_P2P);
+                }
+            }
+            {
+                int k = 0, c0 = 0, nch = 0;
+                if (split_kind == 1) {
+                    c0 = A.child0[cA];
+                    nch = A.nchild[cA];
+                    k = nch * (nch + 1) / 2;
+                } else if (split_kind == 2) {
+                    c0 = A.child0[cA];
+                    nch = A.nchild[cA];
+                    k = nch;
+                } else if (split_kind == 3) {
+                    c0 = A.child0[cB];
+                    nch = A.nchild[cB];
+                    k = nch;
+                }
+                int slot = warp_append(ncount, k);
+                if (k > 0) {
+                    if (slot + k > A.front_cap) {
+                        atomicOr(&A.ctl->err, ERR_FRONTIER);
+                    } else {
+                        const int fl = split_forced ? FORCED : 0;
+                        if (split_kind == 1) {
+                            for (int a = 0; a < nch; a++)
+                                for (int b = a; b < nch; b++) nxt[slot++] = make_int2(c0 + a, (c0 + b) | fl);
+                        } else if (split_kind == 2) {
+                            for (int a = 0; a < nch; a++) nxt[slot++] = make_int2(c0 + a, cB | fl);
+                        } else {
+                            for (int b = 0; b < nch; b++) nxt[slot++] = make_int2(cA, (c0 + b) | fl);
+                        }
+                    }
+                }
+            }
+        }
+        if (!grid_sync(A.ctl)) return;
+        if (barrier_aborted(A.ctl)) { it++; break; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.ctl->walk_iters = it;
+        if (it >= WALK_MAX_ITERS) atomicOr(&A.ctl->err, ERR_FRONTIER);
+    }
+}
+
+void launch_walk(ncorp_ctx *c, bool gravity) {
+    Cells &C = c->cells;
+    WalkLists &W = c->wl;
+    WalkArgs A;
+    A.gravity = gravity ? 1 : 0;
+    A.n_cs = gravity ? c->g_cs : c->c_cs;
+    A.pre = gravity ? c->g_pre : c->c_pre;
+    A.post = gravity ? c->g_post : c->c_post;
+    A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
+    A.sx = gravity ? C.sx : C.bx;
+    A.sy = gravity ? C.sy : C.by;
+    A.sz = gravity ? C.sz : C.bz;
+    A.rcrit = gravity ? C.rcrit : C.bcrit;
+    A.front0 = W.front[0]; A.front1 = W.front[1]; A.fcount = W.front_count; A.front_cap = W.front_cap;
+    A.m2l = W.m2l; A.m2l_cap = W.m2l_cap;
+    A.p2p = W.p2p; A.p2p_cap = W.p2p_cap;
+    A.self = W.self; A.self_cap = W.self_cap;
+    A.ctl = c->ctl;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(W.front_count, 0, sizeof(int) * (WALK_MAX_ITERS + 1), c->stream));
+    k_walk_init<<<1, 1, 0, c->stream>>>(A);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_walk),
+                                                                   256, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int grid = per_sm * c->num_sms;
+    void *args[] = {&A};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
+                                                 0, c->stream));
+}
+
+// ---------------------------------------------------------------------------
+// Per-target lists (counting sort by target).
+//   M2L: every well-separated pair (A, B) gives the directed entries A <- B
+//        and B <- A, grouped by target cell.
+//   P2P: every leaf pair gives A <- B and B <- A, every self leaf A <- A,
+//        grouped by target leaf (offsets indexed by cell id).
+// ---------------------------------------------------------------------------
+__global__ void k_count_lists(const int2 *__restrict__ m2l, const int2 *__restrict__ p2p, const int *__restrict__ self,
+                              const Ctrl *ctl, int *cnt_m2l, int *cnt_p2p, int m2l_cap, int p2p_cap, int self_cap) {
+    if (aborted(ctl)) return;
+    const int nm = min(ctl->n_m2l, m2l_cap), np = min(ctl->n_p2p, p2p_cap), ns = min(ctl->n_self, self_cap);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + np + ns; i += stride) {
+        if (i < nm) {
+            const int2 e = m2l[i];
+            atomicAdd(&cnt_m2l[e.x], 1);
+            atomicAdd(&cnt_m2l[e.y], 1);
+        } else if (i < nm + np) {
+            const int2 e = p2p[i - nm];
+            atomicAdd(&cnt_p2p[e.x], 1);
+            atomicAdd(&cnt_p2p[e.y], 1);
+        } else {
+            atomicAdd(&cnt_p2p[self[i - nm - np]], 1);
+        }
+    }
+}
+
+__global__ void k_scatter_lists(const int2 *__restrict__ m2l, const int2 *__restrict__ p2p,
+                                const int *__restrict__ self, Ctrl *ctl, int *cur_m2l, int *cur_p2p, int2 *m2l_dir,
+                                int m2l_dir_cap, int *p2p_src, int p2p_dir_cap, int m2l_cap, int p2p_cap,
+                                int self_cap) {
+    if (aborted(ctl)) return;
+    const int nm = min(ctl->n_m2l, m2l_cap), np = min(ctl->n_p2p, p2p_cap), ns = min(ctl->n_self, self_cap);
+    const int stride = gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->n_m2l_dir = 2 * nm;
+        ctl->n_p2p_dir = 2 * np + ns;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + np + ns; i += stride) {
+        if (i < nm) {
+            const int2 e = m2l[i];
+            const int a = atomicAdd(&cur_m2l[e.x], 1), b = atomicAdd(&cur_m2l[e.y], 1);
+            if (a < m2l_dir_cap && b < m2l_dir_cap) {
+                m2l_dir[a] = make_int2(e.x, e.y);
+                m2l_dir[b] = make_int2(e.y, e.x);
+            } else {
+                atomicOr(&ctl->err, ERR_DIRECTED);
+            }
+        } else if (i < nm + np) {
+            const int2 e = p2p[i - nm];
+            const int a = atomicAdd(&cur_p2p[e.x], 1), b = atomicAdd(&cur_p2p[e.y], 1);
+            if (a < p2p_dir_cap && b < p2p_dir_cap) {
+                p2p_src[a] = e.y;
+                p2p_src[b] = e.x;
+            } else {
+                atomicOr(&ctl->err, ERR_DIRECTED);
+            }
+        } else {
+            const int s = self[i - nm - np];
+            const int a = atomicAdd(&cur_p2p[s], 1);
+            if (a < p2p_dir_cap) p2p_src[a] = s;
+            else atomicOr(&ctl->err, ERR_DIRECTED);
+        }
+    }
+}
+
+void launch_directed_lists(ncorp_ctx *c) {
+    Cells &C = c->cells;
+    WalkLists &W = c->wl;
+    const int n = C.cap + 1;
+    // cnt (m2l) uses W.cnt, (p2p) uses W.cursor as scratch counts
+    NCORP_CUDA_CHECK(cudaMemsetAsync(W.cnt, 0, sizeof(int) * n, c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(W.p2p_off, 0, sizeof(int) * n, c->stream));
+    const int grid = 4 * c->num_sms;
+    k_count_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cnt, W.p2p_off, W.m2l_cap, W.p2p_cap,
+                                               W.self_cap);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    scan_exclusive(c, W.cnt, W.offs, n, nullptr);
+    scan_exclusive(c, W.p2p_off, W.p2p_off, n, nullptr);
+    NCORP_CUDA_CHECK(cudaMemcpyAsync(W.cursor, W.offs, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream));
+    NCORP_CUDA_CHECK(cudaMemcpyAsync(W.cnt, W.p2p_off, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream));
+    k_scatter_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cursor, W.cnt, W.m2l_dir,
+                                                 W.m2l_dir_cap, W.p2p_src, W.p2p_dir_cap, W.m2l_cap, W.p2p_cap,
+                                                 W.self_cap);
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace ncorp

@@ -1,0 +1,179 @@
+"""Thin Python binding of libncorp.so (the C ABI declared in include/ncorp.h).
+
+Functions carry the C names and only marshal arguments: array arguments may
+be torch tensors (CPU or CUDA), numpy arrays or raw integer addresses; all
+computation happens in the CUDA library.  A non-zero status raises NcorpError
+with the library's message.  There is no fallback: if the library has not been
+built (``paper_2310_20374_gb300.build``) or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+from . import build as _build
+
+NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEOUT, NCORP_ESTATE = 0, -1, -2, -3, -4, -5, -6
+NCORP_FP64, NCORP_MIXED = 0, 1
+STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
+              "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "_14", "_15"]
+HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
+
+
+class NcorpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ncorp error {code}: {msg}")
+        self.code = code
+
+
+class ncorp_config(C.Structure):
+    _fields_ = [("G", C.c_double), ("central_mass", C.c_double), ("central_radius", C.c_double),
+                ("leaf_size", C.c_int), ("n_cs", C.c_int), ("n_cc_pre", C.c_int), ("n_cc_post", C.c_int),
+                ("c_cs", C.c_int), ("c_cc_pre", C.c_int), ("c_cc_post", C.c_int),
+                ("precision", C.c_int), ("collisions", C.c_int),
+                ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
+                ("t0", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads libncorp.so (raises if it is missing: no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build the CUDA library first (paper_2310_20374_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, i64, dbl, ip = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    L.ncorp_config_default.argtypes = [C.POINTER(ncorp_config)]
+    L.ncorp_config_default.restype = None
+    L.ncorp_init.argtypes = [C.POINTER(vp), C.POINTER(ncorp_config), i64, ip, vp]
+    L.ncorp_set_stream.argtypes = [vp, vp]
+    L.ncorp_step.argtypes = [vp, vp, vp, vp, vp, i64, ip, dbl, dbl]
+    L.ncorp_reset.argtypes = [vp]
+    L.ncorp_collisions.argtypes = [vp, vp, i64, C.POINTER(i64)]
+    L.ncorp_accel.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
+    L.ncorp_collide.argtypes = [vp, vp, vp, vp, i64, dbl]
+    L.ncorp_get_state.argtypes = [vp, vp, vp]
+    L.ncorp_stats.argtypes = [vp, C.POINTER(i64), ip]
+    L.ncorp_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
+    L.ncorp_free.argtypes = [vp]
+    L.ncorp_free.restype = None
+    L.ncorp_last_error.argtypes = [vp]
+    L.ncorp_last_error.restype = C.c_char_p
+    for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
+                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/ncorp.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ncorp_[a-z_0-9]+)\s*\(", text)))
+
+
+def _ptr(a):
+    """Address of a tensor / ndarray / int (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _check(ctx, st):
+    if st != NCORP_OK:
+        msg = load().ncorp_last_error(ctx)
+        raise NcorpError(st, msg.decode() if msg else "")
+    return st
+
+
+def ncorp_config_default() -> ncorp_config:
+    cfg = ncorp_config()
+    load().ncorp_config_default(C.byref(cfg))
+    return cfg
+
+
+def ncorp_init(cfg: ncorp_config, n_max: int, device: int = 0, stream=None):
+    h = C.c_void_p()
+    st = load().ncorp_init(C.byref(h), C.byref(cfg), int(n_max), int(device), _ptr(stream))
+    if st != NCORP_OK:
+        raise NcorpError(st, "ncorp_init failed")
+    return h
+
+
+def ncorp_set_stream(ctx, stream):
+    return _check(ctx, load().ncorp_set_stream(ctx, _ptr(stream)))
+
+
+def ncorp_step(ctx, positions, velocities, masses, radii, n, p, theta, dt):
+    return _check(ctx, load().ncorp_step(ctx, _ptr(positions), _ptr(velocities), _ptr(masses), _ptr(radii),
+                                         int(n), int(p), float(theta), float(dt)))
+
+
+def ncorp_reset(ctx):
+    return _check(ctx, load().ncorp_reset(ctx))
+
+
+def ncorp_collisions(ctx, pairs, cap):
+    """Fills pairs [cap][2] int64; returns the total number found."""
+    found = C.c_int64(0)
+    st = load().ncorp_collisions(ctx, _ptr(pairs), int(cap), C.byref(found))
+    if st not in (NCORP_OK, NCORP_EOVERFLOW):
+        _check(ctx, st)
+    return int(found.value)
+
+
+def ncorp_accel(ctx, positions, masses, n, p, theta, acc, acc_mutual=None):
+    return _check(ctx, load().ncorp_accel(ctx, _ptr(positions), _ptr(masses), int(n), int(p), float(theta),
+                                          _ptr(acc), _ptr(acc_mutual)))
+
+
+def ncorp_collide(ctx, positions, velocities, radii, n, dt):
+    return _check(ctx, load().ncorp_collide(ctx, _ptr(positions), _ptr(velocities), _ptr(radii), int(n), float(dt)))
+
+
+def ncorp_get_state(ctx, positions, velocities):
+    return _check(ctx, load().ncorp_get_state(ctx, _ptr(positions), _ptr(velocities)))
+
+
+def ncorp_stats(ctx) -> dict:
+    arr = (C.c_int64 * 16)()
+    _check(ctx, load().ncorp_stats(ctx, arr, 16))
+    return {k: int(v) for k, v in zip(STAT_NAMES, arr) if not k.startswith("_")}
+
+
+def ncorp_tree_export(ctx, order=None, keys=None, root=None, cells=None, ggeo=None, cgeo=None, cap=0):
+    nc = C.c_int64(0)
+    st = load().ncorp_tree_export(ctx, _ptr(order), _ptr(keys), _ptr(root), _ptr(cells), _ptr(ggeo), _ptr(cgeo),
+                                  int(cap), C.byref(nc))
+    if st not in (NCORP_OK, NCORP_EOVERFLOW):
+        _check(ctx, st)
+    return int(nc.value)
+
+
+def ncorp_free(ctx):
+    if ctx:
+        load().ncorp_free(ctx)
+
+
+def ncorp_last_error(ctx) -> str:
+    m = load().ncorp_last_error(ctx)
+    return m.decode() if m else ""
