@@ -157,6 +157,23 @@ int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
 int ncorp_tree_export(ncorp_ctx *ctx, int64_t *order, uint64_t *keys, double *root, int64_t *cells,
                       double *ggeo, double *cgeo, int64_t cap, int64_t *n_cells);
 
+/* Diagnostic export of the expansions of the last gravity evaluation
+ * (ncorp_accel or ncorp_step), cells in the order of ncorp_tree_export, all
+ * unscaled and in FP64 (host or device arrays, any may be NULL):
+ *   mult  [cap][nm]: multipole moments M_beta = sum_i mu_i (x_i - s)^beta of
+ *         Eq. multipole_moment in symmetric multi-index form, orders 0 and
+ *         2..p-1 (nm = 1 for p = 1, else p(p+1)(p+2)/6 - 3)
+ *   local [cap][nc]: the M2L sums C_alpha of Eq. phi_expanded accumulated on
+ *         each cell by the walk, before the descent, orders 1..p
+ *         (nc = (p+1)(p+2)(p+3)/6 - 1)
+ *   rho   [cap]: the cell's power-of-two scale
+ * Within order n the components run over k = 0..n, c = 0..k with
+ * (a, b, c) = (n-k, k-c, c) the powers of (x, y, z).  *p receives p.
+ * NCORP_ESTATE if no gravity evaluation has run; NCORP_EOVERFLOW if the
+ * cell count exceeds cap (the first cap cells are written). */
+int ncorp_expansions(ncorp_ctx *ctx, double *mult, double *local, double *rho, int64_t cap, int64_t *n_cells,
+                     int *p);
+
 /* Releases the context and its device workspace (NULL is ignored). */
 void ncorp_free(ncorp_ctx *ctx);
 

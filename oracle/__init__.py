@@ -96,6 +96,8 @@ def lib():
             L.or_tree_export.argtypes = [PP, i64, _dp, _opt(_dp), _opt(_dp), _opt(_dp), dbl,
                                          _opt(_ip), _opt(_up), _opt(_dp), _opt(_ip), _opt(_dp), _opt(_dp), i64]
             L.or_tree_export.restype = i64
+            L.or_expansions.argtypes = [PP, i64, _dp, _dp, _opt(_dp), _opt(_dp), i64]
+            L.or_expansions.restype = i64
             L.or_kdk.argtypes = [PP, i64, _dp, _dp, _dp, _dp, dbl, C.c_int, _opt(_dp), _opt(_dp), _ip, i64]
             L.or_kdk.restype = i64
             _lib = L
@@ -271,6 +273,32 @@ def tree_export(P: Params, pos, mass=None, vel=None, rad=None, dt=0.0):
                               None if cg is None else cg.reshape(-1), cap)
     return {"order": ord_, "keys": k, "root": r, "cells": cells[:nc],
             "ggeo": None if gg is None else gg[:nc], "cgeo": None if cg is None else cg[:nc]}
+
+
+def expansions(P: Params, pos, mass):
+    """Per-cell multipoles M[k][(3^p-1)/2] and M2L sums C[k][(3^(p+1)-1)/2] (full tensors, packed by order),
+    level-major cell order, before the descent."""
+    pos = _f64(pos)
+    n = len(pos)
+    cap = 4 * n + 64
+    M = np.zeros((cap, off(P.p)))
+    Cc = np.zeros((cap, off(P.p + 1)))
+    nc = lib().or_expansions(C.byref(P), n, pos.reshape(-1), _f64(mass), M.reshape(-1), Cc.reshape(-1), cap)
+    return M[:nc], Cc[:nc]
+
+
+def full_to_multi(T, order):
+    """Symmetric multi-index components (a, b, c) of a full order-n tensor given flat, in the library's
+    packed order (k = b + c = 0..n, c = 0..k)."""
+    out = []
+    for k in range(order + 1):
+        for c in range(k + 1):
+            a, b = order - k, k - c
+            idx = 0
+            for d in [0] * a + [1] * b + [2] * c:
+                idx = idx * 3 + d
+            out.append(T[idx])
+    return np.array(out)
 
 
 def kdk(P: Params, pos, vel, mass, rad, dt, nsteps, acc0=None, cap=1 << 16):

@@ -899,6 +899,37 @@ int or_falcon_accel(const or_params *P, int64_t n, const double *pos, const doub
     return 0;
 }
 
+/* Per-cell expansions for parity of the multipole stages: after the climb and
+ * the walk (before the descent), cells in level-major order; M: packed full
+ * tensors of orders 0..p-1 (OFF(p) values per cell), C: the M2L sums of orders
+ * 0..p (OFF(p+1) values per cell, order 0 unused).  Returns the cell count. */
+int64_t or_expansions(const or_params *P, int64_t n, const double *pos, const double *mass,
+                      double *Mout, double *Cout, int64_t cap)
+{
+    if (n <= 0) return 0;
+    Tree T;
+    memset(&T, 0, sizeof(T));
+    T.P = P; T.n = n; T.pos = pos; T.mass = mass;
+    T.acc = (double *)calloc((size_t)3 * n, sizeof(double));
+    tree_build(&T);
+    climb_gravity(&T, T.rootn);
+    finish_gravity(&T);
+    tree_walk(&T, T.rootn, T.rootn, 1);
+    Node **sorted = (Node **)malloc(sizeof(Node *) * T.nnodes);
+    memcpy(sorted, T.nodes, sizeof(Node *) * T.nnodes);
+    qsort(sorted, (size_t)T.nnodes, sizeof(Node *), cmp_node);
+    int nm = OFF(P->p), nc = OFF(P->p + 1);
+    for (int64_t k = 0; k < T.nnodes && k < cap; k++) {
+        if (Mout) memcpy(Mout + (size_t)k * nm, sorted[k]->Mt, sizeof(double) * nm);
+        if (Cout) memcpy(Cout + (size_t)k * nc, sorted[k]->Ct, sizeof(double) * nc);
+    }
+    int64_t cnt = T.nnodes;
+    free(sorted);
+    free(T.acc);
+    tree_free(&T);
+    return cnt;
+}
+
 /* tree-based collision search (pairs user indices, sorted, i < j) */
 static int cmp_pair(const void *a, const void *b)
 {

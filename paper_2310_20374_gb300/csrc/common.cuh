@@ -10,7 +10,7 @@
 //   locals C-hat:     orders 1..p (C^(0) is never needed), p = 6 -> 83 values
 //   derivatives D:    orders 0..p
 //
-// Scaled storage (per cell, rho = a power of two >= r_max of the cell):
+// Scaled storage (per cell, rho = a power of two >= max(r_max, side/256)):
 //   M-hat_beta = M_beta / (beta! rho^|beta|),   C-hat_alpha = C_alpha rho^|alpha|
 // which keeps every stored coefficient within a few orders of magnitude of the
 // cell mass (or of the field) whatever the cell size, so that FP32 storage and

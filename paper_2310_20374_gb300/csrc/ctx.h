@@ -100,6 +100,8 @@ struct ncorp_ctx {
     double time = 0.0;
     int64_t stats[NCORP_NSTATS] = {0};
     int tree_kind = 0;               // 1: gravity geometry valid, 2: collision geometry valid (bit mask)
+    int grav_p = 0;                  // p of the last gravity evaluation (0: none)
+    bool grav_mixed = false;
 };
 
 namespace ncorp {

@@ -61,6 +61,9 @@ __global__ void __launch_bounds__(BS) k_eval(EvalArgs A) {
     __shared__ real s_C[2][NC];
     __shared__ real s_pw[3][P + 1];
     __shared__ real s_x[BS], s_y[BS], s_z[BS], s_mu[BS];
+    // low parts of the staged positions (FP32 only): x - s_leaf = hi + lo
+    __shared__ real s_xl[sizeof(real) == 4 ? BS : 1], s_yl[sizeof(real) == 4 ? BS : 1], s_zl[sizeof(real) == 4 ? BS : 1];
+    constexpr bool split = sizeof(real) == 4;
     __shared__ int s_j[BS];
     const real *Ch = static_cast<const real *>(A.Ch);
     const int tid = threadIdx.x;
@@ -108,9 +111,8 @@ __global__ void __launch_bounds__(BS) k_eval(EvalArgs A) {
                                            static_cast<real>(c_ifact[ab] * c_ifact[bb] * c_ifact[cb2]);
                             acc += s_C[cb][cidx(a + ab, b + bb, c + cb2)] * w;
                         }
-                real rn = real(1);
-                for (int k = 0; k < n; k++) rn *= ratio;
-                s_C[cb ^ 1][i] = Ch[(size_t)cc * NC + i] + rn * acc;
+                for (int k = 0; k < n; k++) acc *= ratio;   // (rho_c/rho_p)^n applied to the small factor first
+                s_C[cb ^ 1][i] = Ch[(size_t)cc * NC + i] + acc;
             }
             cb ^= 1;
             __syncthreads();
@@ -123,12 +125,17 @@ __global__ void __launch_bounds__(BS) k_eval(EvalArgs A) {
             const int ti = t0 + tid;
             const bool act = ti < cnt;
             const int i = f + ti;
-            real px = 0, py = 0, pz = 0, ax = 0, ay = 0, az = 0;
+            real px = 0, py = 0, pz = 0, pxl = 0, pyl = 0, pzl = 0, ax = 0, ay = 0, az = 0;
             if (act) {
                 const double dx = A.x[i] - lsx, dy = A.y[i] - lsy, dz = A.z[i] - lsz;
                 px = static_cast<real>(dx);
                 py = static_cast<real>(dy);
                 pz = static_cast<real>(dz);
+                if (split) {
+                    pxl = static_cast<real>(dx - static_cast<double>(px));
+                    pyl = static_cast<real>(dy - static_cast<double>(py));
+                    pzl = static_cast<real>(dz - static_cast<double>(pz));
+                }
                 const real hx = static_cast<real>(dx * irho), hy = static_cast<real>(dy * irho),
                            hz = static_cast<real>(dz * irho);
                 real wx[P], wy[P], wz[P];
@@ -163,9 +170,16 @@ __global__ void __launch_bounds__(BS) k_eval(EvalArgs A) {
                     __syncthreads();
                     if (tid < sc - j0) {
                         const int j = sf + j0 + tid;
-                        s_x[tid] = static_cast<real>(A.x[j] - lsx);
-                        s_y[tid] = static_cast<real>(A.y[j] - lsy);
-                        s_z[tid] = static_cast<real>(A.z[j] - lsz);
+                        const double qx = A.x[j] - lsx, qy = A.y[j] - lsy, qz = A.z[j] - lsz;
+                        const real hx = static_cast<real>(qx), hy = static_cast<real>(qy), hz = static_cast<real>(qz);
+                        s_x[tid] = hx;
+                        s_y[tid] = hy;
+                        s_z[tid] = hz;
+                        if (split) {
+                            s_xl[tid] = static_cast<real>(qx - static_cast<double>(hx));
+                            s_yl[tid] = static_cast<real>(qy - static_cast<double>(hy));
+                            s_zl[tid] = static_cast<real>(qz - static_cast<double>(hz));
+                        }
                         s_mu[tid] = static_cast<real>(A.G * A.m[j]);
                         s_j[tid] = j;
                     }
@@ -173,9 +187,14 @@ __global__ void __launch_bounds__(BS) k_eval(EvalArgs A) {
                     if (act) {
                         const int lim = min(BS, sc - j0);
                         for (int k = 0; k < lim; k++) {
-                            const real dx = s_x[k] - px, dy = s_y[k] - py, dz = s_z[k] - pz;
+                            real dx = s_x[k] - px, dy = s_y[k] - py, dz = s_z[k] - pz;
+                            if (split) {   // (hi_j - hi_i) + (lo_j - lo_i): separation to ~1e-7 relative
+                                dx += s_xl[k] - pxl;
+                                dy += s_yl[k] - pyl;
+                                dz += s_zl[k] - pzl;
+                            }
                             const real r2 = dx * dx + dy * dy + dz * dz;
-                            if (s_j[k] != i && r2 > real(0)) {
+                            if (s_j[k] != i && r2 > (split ? real(1e-30) : real(0))) {
                                 const real inv = rsqrt_real(r2);
                                 const real f3 = s_mu[k] * inv * inv * inv;
                                 ax += dx * f3;

@@ -249,7 +249,15 @@ ExtForce external(ncorp_ctx *c, double t) {
     return e;
 }
 
-void reset_ctl(ncorp_ctx *c) { NCORP_CUDA_CHECK(cudaMemsetAsync(c->ctl, 0, sizeof(Ctrl), c->stream)); }
+// Clears the error word and the per-call counters; the tree description
+// (cell and leaf counts, levels, root cube) of a resident tree is kept.
+void reset_ctl(ncorp_ctx *c) {
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->err, 0, sizeof(int), c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_found, 0, sizeof(int), c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_tests, 0, sizeof(long long), c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_snap, 0, sizeof(int), c->stream));
+}
 
 int finish(ncorp_ctx *c) {
     NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
@@ -272,6 +280,8 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
 
 void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual) {
     const bool mixed = c->cfg.precision == NCORP_MIXED;
+    c->grav_p = p;
+    c->grav_mixed = mixed;
     launch_climb_gravity(c, S, p, mixed, c->cfg.G, theta);
     launch_walk(c, true);
     launch_directed_lists(c);
@@ -645,6 +655,69 @@ int ncorp_tree_export(ncorp_ctx *c, int64_t *order, uint64_t *keys, double *root
         if (k > 0 && ggeo && (c->tree_kind & 1)) pack(ggeo, {C.M, C.sx, C.sy, C.sz, C.rmax, C.rcrit});
         if (k > 0 && cgeo && (c->tree_kind & 2)) pack(cgeo, {C.bx, C.by, C.bz, C.bmax, C.bcrit});
         if (nc > cap) return fail(c, NCORP_EOVERFLOW, "%d cells, room for %lld", nc, (long long)cap);
+        return NCORP_OK;
+    })
+}
+
+int ncorp_expansions(ncorp_ctx *c, double *mult, double *local, double *rho, int64_t cap, int64_t *n_cells, int *p) {
+    if (!c || cap < 0) return NCORP_EINVAL;
+    if (c->grav_p <= 0 || !(c->tree_kind & 1)) return fail(c, NCORP_ESTATE, "no gravity evaluation yet");
+    NCORP_API_BODY(c, {
+        const int P = c->grav_p;
+        const int nm = num_m(P), nc_ = num_c(P);
+        const int ncell = std::min(c->ctl_h->n_cells, c->cells.cap);
+        const int k = static_cast<int>(std::min<int64_t>(cap, ncell));
+        if (n_cells) *n_cells = ncell;
+        if (p) *p = P;
+        std::vector<double> r(std::max(k, 1));
+        if (k > 0) NCORP_CUDA_CHECK(cudaMemcpy(r.data(), c->cells.rho, sizeof(double) * k, cudaMemcpyDeviceToHost));
+        auto fetch = [&](const void *src, int w) {
+            std::vector<double> out(static_cast<size_t>(k) * w);
+            if (c->grav_mixed) {
+                std::vector<float> f(out.size());
+                if (k > 0) NCORP_CUDA_CHECK(cudaMemcpy(f.data(), src, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+                for (size_t i = 0; i < f.size(); i++) out[i] = f[i];
+            } else if (k > 0) {
+                NCORP_CUDA_CHECK(cudaMemcpy(out.data(), src, sizeof(double) * out.size(), cudaMemcpyDeviceToHost));
+            }
+            return out;
+        };
+        // exponents of the packed components
+        auto exps = [](int idx, int &a, int &b, int &cc) {
+            int n = 0;
+            while (off(n + 1) <= idx) n++;
+            int rem = idx - off(n), kk = 0;
+            while (tri(kk + 1) <= rem) kk++;
+            cc = rem - tri(kk);
+            b = kk - cc;
+            a = n - kk;
+        };
+        if (mult) {
+            std::vector<double> M = fetch(c->cells.Mh, nm);
+            for (int i = 0; i < k; i++)
+                for (int j = 0; j < nm; j++) {
+                    int a, b, cc;
+                    exps(j == 0 ? 0 : j + 3, a, b, cc);
+                    double f = 1.0 / inv_mfact(a, b, cc);
+                    for (int t = 0; t < a + b + cc; t++) f *= r[i];
+                    M[static_cast<size_t>(i) * nm + j] *= f;
+                }
+            NCORP_CUDA_CHECK(cudaMemcpy(mult, M.data(), sizeof(double) * M.size(), cudaMemcpyDefault));
+        }
+        if (local) {
+            std::vector<double> Cl = fetch(c->cells.Ch, nc_);
+            for (int i = 0; i < k; i++)
+                for (int j = 0; j < nc_; j++) {
+                    int a, b, cc;
+                    exps(j + 1, a, b, cc);
+                    double f = 1.0;
+                    for (int t = 0; t < a + b + cc; t++) f /= r[i];
+                    Cl[static_cast<size_t>(i) * nc_ + j] *= f;
+                }
+            NCORP_CUDA_CHECK(cudaMemcpy(local, Cl.data(), sizeof(double) * Cl.size(), cudaMemcpyDefault));
+        }
+        if (rho && k > 0) NCORP_CUDA_CHECK(cudaMemcpy(rho, r.data(), sizeof(double) * k, cudaMemcpyDefault));
+        if (ncell > cap) return fail(c, NCORP_EOVERFLOW, "%d cells, room for %lld", ncell, (long long)cap);
         return NCORP_OK;
     })
 }

@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     for (int lev = 0; lev < MAX_LEVEL; lev++) {
         const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
         if (ls >= le) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->max_level = lev;
         const int ncl = le - ls;
         const int chunk = (ncl + gridDim.x - 1) / gridDim.x;
         const int cb = min(le, ls + blockIdx.x * chunk), ce = min(le, cb + chunk);
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
         if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
             A.ctl->level_start[lev + 2] = s_base;
             A.ctl->n_cells = s_base;
+            if (s_base > le) A.ctl->max_level = lev + 1;
         }
         if (!grid_sync(A.ctl)) return;
     }
@@ -236,6 +236,13 @@ __device__ __forceinline__ double cell_side(const Ctrl *ctl, int lev) {
     double h = ctl->root[3];
     for (int k = 0; k < lev; k++) h = dmul(h, 0.5);
     return h;
+}
+
+// Power-of-two scale of a cell's expansions: >= r_max (so |x - s|/rho <= 1)
+// and >= side/256, so that the scale ratios met in M2M, M2L and L2L stay
+// below 2^(level difference + 8) even for one-moonlet cells (r_max ~ 0).
+__device__ __forceinline__ double cell_scale(const Ctrl *ctl, int lev, double rmax) {
+    return pow2_ceil(fmax(rmax, cell_side(ctl, lev) * 0x1p-8));
 }
 
 // ---------------------------------------------------------------------------
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(256) k_climb_gravity(ClimbArgs A) {
         const int lev = A.level[c];
         const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
         if (cap < rmax) rmax = cap;
-        const double rho = rmax > 0.0 ? pow2_ceil(rmax) : cell_side(A.ctl, lev);
+        const double rho = cell_scale(A.ctl, lev, rmax);
         A.M[c] = M;
         A.sx[c] = sx;
         A.sy[c] = sy;
@@ -423,7 +430,7 @@ __global__ void __launch_bounds__(256) k_climb_gravity(ClimbArgs A) {
             const int lev = A.level[c];
             const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
             if (cap < rmax) rmax = cap;
-            const double rho = rmax > 0.0 ? pow2_ceil(rmax) : cell_side(A.ctl, lev);
+            const double rho = cell_scale(A.ctl, lev, rmax);
             A.M[c] = M;
             A.sx[c] = sx;
             A.sy[c] = sy;

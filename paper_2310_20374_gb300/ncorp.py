@@ -66,12 +66,13 @@ def load(path: str | None = None):
     L.ncorp_get_state.argtypes = [vp, vp, vp]
     L.ncorp_stats.argtypes = [vp, C.POINTER(i64), ip]
     L.ncorp_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
+    L.ncorp_expansions.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(ip)]
     L.ncorp_free.argtypes = [vp]
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
-                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export"):
+                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -167,6 +168,24 @@ def ncorp_tree_export(ctx, order=None, keys=None, root=None, cells=None, ggeo=No
     if st not in (NCORP_OK, NCORP_EOVERFLOW):
         _check(ctx, st)
     return int(nc.value)
+
+
+def ncorp_expansions(ctx, mult=None, local=None, rho=None, cap=0):
+    """Returns (n_cells, p); fills the given [cap][...] float64 arrays."""
+    nc = C.c_int64(0)
+    pp = C.c_int(0)
+    st = load().ncorp_expansions(ctx, _ptr(mult), _ptr(local), _ptr(rho), int(cap), C.byref(nc), C.byref(pp))
+    if st not in (NCORP_OK, NCORP_EOVERFLOW):
+        _check(ctx, st)
+    return int(nc.value), int(pp.value)
+
+
+def num_m(p):
+    return 1 if p < 2 else p * (p + 1) * (p + 2) // 6 - 3
+
+
+def num_c(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6 - 1
 
 
 def ncorp_free(ctx):

@@ -6,6 +6,8 @@ Tolerances (relative, per moonlet, on the mutual acceleration): 1e-11 for
 the FP64 path and 2e-5 for the mixed FP32/FP64 path, against the oracle's
 falcON at the same p, theta_min, leaf size and thresholds.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -307,3 +309,60 @@ def test_context_grows_beyond_initial_capacity():
         ncorp.ncorp_free(ctx)
     ref, _ = oracle.falcon_accel(oracle.params(p=3, theta=0.5, leaf_size=16), d["pos"], d["mass"])
     assert rel_err(mut, ref).max() <= FP64_TOL
+
+
+# ------------------------------------------------- per-stage expansion parity
+def _oracle_multi(P, pos, mass):
+    M, Cc = oracle.expansions(P, pos, mass)
+    p = P.p
+    Mm = [np.concatenate([oracle.full_to_multi(row[oracle.off(n):oracle.off(n + 1)], n) for n in range(p) if n != 1])
+          for row in M]
+    Cm = [np.concatenate([oracle.full_to_multi(row[oracle.off(n):oracle.off(n + 1)], n) for n in range(1, p + 1)])
+          for row in Cc]
+    return np.array(Mm), np.array(Cm)
+
+
+@pytest.mark.parametrize("p,prec,tol", [(4, ncorp.NCORP_FP64, 1e-12), (6, ncorp.NCORP_FP64, 1e-12),
+                                        (6, ncorp.NCORP_MIXED, 3e-5)])
+def test_multipoles_and_m2l_sums_match_oracle(p, prec, tol):
+    """P2M + M2M (Eq. multipole_moment, App. C) and the M2L sums of each cell
+    (Eq. phi_expanded) against the oracle's full-tensor versions."""
+    n, s = 4000, 24
+    grav = (64, 8, 64)
+    d = diskgen.make_disk(n, 81 + p)
+    ctx = make_ctx(n, precision=prec, s=s, grav=grav)
+    try:
+        gpu_accel(ctx, d, p, 0.5)
+        cap = 4 * n
+        mult = np.zeros((cap, ncorp.num_m(p)))
+        loc = np.zeros((cap, ncorp.num_c(p)))
+        rho = np.zeros(cap)
+        nc, pp = ncorp.ncorp_expansions(ctx, mult, loc, rho, cap)
+    finally:
+        ncorp.ncorp_free(ctx)
+    P = oracle.params(p=p, theta=0.5, leaf_size=s, gravity_thresholds=grav)
+    Mo, Co = _oracle_multi(P, d["pos"], d["mass"])
+    assert nc == len(Mo) and pp == p
+    mult, loc, rho = mult[:nc], loc[:nc], rho[:nc]
+    assert np.isfinite(mult).all() and np.isfinite(loc).all()
+    # compare in the scaled representation M_beta/(beta! rho^|beta|) and C_alpha rho^|alpha|, in which every
+    # component of a cell is bounded by its mass (multipoles) or by its largest component (locals)
+    em, ec = [], []
+    for n_, (lo, hi) in [(0, (0, 1))] + [(k, (ncorp.num_m(k), ncorp.num_m(k + 1))) for k in range(2, p)]:
+        f = np.array([1.0 / np.prod([math.factorial(e) for e in ab]) for ab in _exps(n_)])
+        w = f[None, :] / rho[:, None] ** n_
+        em.append(np.abs(mult[:, lo:hi] - Mo[:, lo:hi]) * w / Mo[:, :1])
+    Cs_g, Cs_o = [], []
+    for m in range(1, p + 1):
+        lo, hi = ncorp.num_c(m - 1), ncorp.num_c(m)
+        Cs_g.append(loc[:, lo:hi] * rho[:, None] ** m)
+        Cs_o.append(Co[:, lo:hi] * rho[:, None] ** m)
+    Cg, Cr = np.hstack(Cs_g), np.hstack(Cs_o)
+    has = np.abs(Cr).max(axis=1) > 0
+    ec = np.abs(Cg[has] - Cr[has]) / np.abs(Cr[has]).max(axis=1, keepdims=True)
+    assert max(e.max() for e in em) <= tol
+    assert ec.max() <= tol * 10
+
+
+def _exps(n):
+    return [(n - k, k - c, c) for k in range(n + 1) for c in range(k + 1)]
