@@ -33,6 +33,8 @@ struct CollideArgs {
     const int *self;
     const int *first, *count;
     const double *x, *y, *z, *vx, *vy, *vz, *R;
+    const float4 *hi4, *lo4;
+    const float *rc;           // R + dt |v| rounded up to FP32
     const int *perm;
     double dt;
     uint64_t *pairs;
@@ -56,25 +58,69 @@ __device__ __forceinline__ void test_and_emit(const CollideArgs &A, int u, int v
     }
 }
 
-__global__ void k_collide(CollideArgs A) {
+// A pair can only collide within the step if |dr| <= R1 + R2 + dt |dv| <= rc1 + rc2
+// (rc = R + dt |v|).  The separation is evaluated from the double-float
+// positions (relative error ~1e-7) and compared with (rc1 + rc2)^2 (1 + 2^-10);
+// only pairs inside that bound reach the exact FP64 test, so the pair set is
+// the one the FP64 test alone gives.
+__device__ __forceinline__ bool may_touch(const float4 &h, const float4 &l, float r, const float4 &th,
+                                          const float4 &tl, float tr) {
+    const float dx = (h.x - th.x) + (l.x - tl.x);
+    const float dy = (h.y - th.y) + (l.y - tl.y);
+    const float dz = (h.z - th.z) + (l.z - tl.z);
+    const float s = r + tr;
+    return dx * dx + dy * dy + dz * dz <= s * s * (1.0f + 0x1p-10f);
+}
+
+constexpr int COL_WARPS = 8;
+
+// Warp per direct item (a leaf with itself, or a pair of leaves): the source
+// leaf is staged in shared memory 32 moonlets at a time, every lane owns up to
+// two target moonlets.
+__global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
+    __shared__ float4 s_h[COL_WARPS][32], s_l[COL_WARPS][32];
+    __shared__ float s_r[COL_WARPS][32];
     if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     long long tests = 0;
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ns + np; w += nwarps) {
+        int ct, cs;
         if (w < ns) {
-            const int c = A.self[w];
-            const int f = A.first[c], cnt = A.count[c];
-            for (int u = lane; u < cnt; u += 32)
-                for (int v = u + 1; v < cnt; v++) test_and_emit(A, f + u, f + v);
-            if (lane == 0) tests += static_cast<long long>(cnt) * (cnt - 1) / 2;
+            ct = cs = A.self[w];
         } else {
             const int2 e = A.p2p[w - ns];
-            const int fa = A.first[e.x], ca = A.count[e.x], fb = A.first[e.y], cb = A.count[e.y];
-            for (int u = lane; u < ca; u += 32)
-                for (int v = 0; v < cb; v++) test_and_emit(A, fa + u, fb + v);
-            if (lane == 0) tests += static_cast<long long>(ca) * cb;
+            ct = e.x;
+            cs = e.y;
+        }
+        const bool self = ct == cs;
+        const int ft = A.first[ct], nt = A.count[ct], fs = A.first[cs], nsrc = A.count[cs];
+        if (lane == 0) tests += self ? static_cast<long long>(nt) * (nt - 1) / 2 : static_cast<long long>(nt) * nsrc;
+        for (int t0 = 0; t0 < nt; t0 += 64) {
+            const int u0 = t0 + lane, u1 = u0 + 32;
+            const bool a0 = u0 < nt, a1 = u1 < nt;
+            float4 th0 = make_float4(0, 0, 0, 0), tl0 = th0, th1 = th0, tl1 = th0;
+            float tr0 = 0.f, tr1 = 0.f;
+            if (a0) { th0 = A.hi4[ft + u0]; tl0 = A.lo4[ft + u0]; tr0 = A.rc[ft + u0]; }
+            if (a1) { th1 = A.hi4[ft + u1]; tl1 = A.lo4[ft + u1]; tr1 = A.rc[ft + u1]; }
+            for (int j0 = 0; j0 < nsrc; j0 += 32) {
+                const int lim = min(32, nsrc - j0);
+                __syncwarp();
+                if (lane < lim) {
+                    s_h[wl][lane] = A.hi4[fs + j0 + lane];
+                    s_l[wl][lane] = A.lo4[fs + j0 + lane];
+                    s_r[wl][lane] = A.rc[fs + j0 + lane];
+                }
+                __syncwarp();
+                for (int k = 0; k < lim; k++) {
+                    const int v = j0 + k;
+                    const float4 h = s_h[wl][k], l = s_l[wl][k];
+                    const float r = s_r[wl][k];
+                    if (a0 && (!self || v > u0) && may_touch(h, l, r, th0, tl0, tr0)) test_and_emit(A, ft + u0, fs + v);
+                    if (a1 && (!self || v > u1) && may_touch(h, l, r, th1, tl1, tr1)) test_and_emit(A, ft + u1, fs + v);
+                }
+            }
         }
     }
     if (lane == 0 && tests)
@@ -87,6 +133,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.p2p = c->wl.p2p; A.self = c->wl.self;
     A.first = c->cells.first; A.count = c->cells.count;
     A.x = P.x; A.y = P.y; A.z = P.z; A.vx = vx; A.vy = vy; A.vz = vz; A.R = P.R;
+    A.hi4 = P.hi4; A.lo4 = P.lo4; A.rc = c->rcf;
     A.perm = P.perm;
     A.dt = dt;
     A.pairs = c->pairs;
@@ -94,7 +141,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.self_cap = c->wl.self_cap;
     A.p2p_cap = c->wl.p2p_cap;
     A.ctl = c->ctl;
-    k_collide<<<8 * c->num_sms, 256, 0, c->stream>>>(A);
+    k_collide<<<4 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A);
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

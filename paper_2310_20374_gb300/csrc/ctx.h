@@ -19,6 +19,8 @@ struct ParticleSet {
     int *perm = nullptr;                                   // caller index of each moonlet
     uint32_t *qx = nullptr, *qy = nullptr, *qz = nullptr; // quantised coordinates
     uint64_t *key = nullptr;                               // Hilbert key
+    float4 *hi4 = nullptr;    // (x, y, z) rounded to FP32, and mu = G m
+    float4 *lo4 = nullptr;    // (x, y, z) - hi, rounded to FP32 (double-float position)
 };
 
 struct Cells {
@@ -70,8 +72,10 @@ struct ncorp_ctx {
 
     ncorp::ParticleSet A, B, Cset;   // A: resident state; B: scratch (half-kicked v, drifted x); Cset: next order
     double *amx = nullptr, *amy = nullptr, *amz = nullptr;   // mutual acceleration (tree order)
+    float *rcf = nullptr;            // R + dt |v| per moonlet (collision search), rounded up
     uint64_t *key_alt = nullptr;
     uint32_t *idx = nullptr, *idx_alt = nullptr;
+    int *work_counter = nullptr;     // dynamic work distribution of persistent kernels
     int *tile_hist = nullptr;
     int tile_hist_cap = 0;
     int *scan_tmp = nullptr;
@@ -112,7 +116,7 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
                     int bits);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx);
+                   const uint32_t *idx, double G);
 void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total);
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 

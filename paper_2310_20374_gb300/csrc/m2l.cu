@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
     const int E = min(A.ctl->n_m2l_dir, A.dir_cap);
     const int T = gridDim.x * blockDim.x;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int per = (E + T - 1) / T;
+    const int per = max((E + T - 1) / T, 16);   // runs of >= 16 entries: one flush per target run
     const int e0 = min(E, t * per), e1 = min(E, e0 + per);
     real acc[NC];
 #pragma unroll

@@ -60,11 +60,14 @@ void alloc_set(ParticleSet &S, size_t n) {
     dalloc(S.perm, n);
     dalloc(S.qx, n); dalloc(S.qy, n); dalloc(S.qz, n);
     dalloc(S.key, n);
+    dalloc(S.hi4, n);
+    dalloc(S.lo4, n);
 }
 
 void free_set(ParticleSet &S) {
     dfree(S.x); dfree(S.y); dfree(S.z); dfree(S.vx); dfree(S.vy); dfree(S.vz); dfree(S.m); dfree(S.R);
     dfree(S.ax); dfree(S.ay); dfree(S.az); dfree(S.perm); dfree(S.qx); dfree(S.qy); dfree(S.qz); dfree(S.key);
+    dfree(S.hi4); dfree(S.lo4);
 }
 
 void ensure_particles(ncorp_ctx *c, int64_t n) {
@@ -74,6 +77,7 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
     alloc_set(c->B, cap);
     alloc_set(c->Cset, cap);
     dalloc(c->amx, cap); dalloc(c->amy, cap); dalloc(c->amz, cap);
+    dalloc(c->rcf, cap);
     dalloc(c->key_alt, cap);
     dalloc(c->idx, cap); dalloc(c->idx_alt, cap);
     dalloc(c->stage, 3 * cap);
@@ -274,7 +278,7 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
     view.x = sx.x; view.y = sx.y; view.z = sx.z;
     view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
     view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
-    launch_gather(c, view, view, dst, n, c->idx);
+    launch_gather(c, view, view, dst, n, c->idx, c->cfg.G);
     launch_build(c, dst, n, c->s);
 }
 
@@ -372,6 +376,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
         if (!coop) throw CudaError(cudaErrorNotSupported, "cooperative launch unsupported", __FILE__, __LINE__);
         dalloc(c->ctl, 1);
+        dalloc(c->work_counter, 4);
         NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
         std::memset(c->ctl_h, 0, sizeof(Ctrl));
         NCORP_CUDA_CHECK(cudaMemset(c->ctl, 0, sizeof(Ctrl)));
@@ -730,7 +735,7 @@ void ncorp_free(ncorp_ctx *c) {
     free_set(c->A);
     free_set(c->B);
     free_set(c->Cset);
-    dfree(c->amx); dfree(c->amy); dfree(c->amz);
+    dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->rcf);
     dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
     dfree(c->tile_hist); dfree(c->scan_tmp); dfree(c->stage); dfree(c->stage2);
     Cells &C = c->cells;
@@ -743,6 +748,7 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
     dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
     dfree(c->ctl);
+    dfree(c->work_counter);
     if (c->ctl_h) cudaFreeHost(c->ctl_h);
     delete c;
 }

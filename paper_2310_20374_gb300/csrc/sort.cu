@@ -384,7 +384,9 @@ struct GatherArgs {
     double *ox, *oy, *oz, *ovx, *ovy, *ovz, *om, *oR;
     int *operm;
     uint32_t *oqx, *oqy, *oqz;
+    float4 *hi4, *lo4;
     const uint32_t *idx;
+    double G;
     int n;
 };
 
@@ -403,11 +405,17 @@ __global__ void k_gather(GatherArgs g) {
         g.oqx[i] = g.qx[j];
         g.oqy[i] = g.qy[j];
         g.oqz[i] = g.qz[j];
+        // double-float copy of the position: x = hi + lo with both parts FP32
+        const double X = g.x[j], Y = g.y[j], Z = g.z[j];
+        const float hx = static_cast<float>(X), hy = static_cast<float>(Y), hz = static_cast<float>(Z);
+        g.hi4[i] = make_float4(hx, hy, hz, static_cast<float>(g.G * g.m[j]));
+        g.lo4[i] = make_float4(static_cast<float>(X - static_cast<double>(hx)), static_cast<float>(Y - static_cast<double>(hy)),
+                               static_cast<float>(Z - static_cast<double>(hz)), 0.0f);
     }
 }
 
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx) {
+                   const uint32_t *idx, double G) {
     GatherArgs g;
     g.x = src_xv.x; g.y = src_xv.y; g.z = src_xv.z;
     g.vx = src_xv.vx; g.vy = src_xv.vy; g.vz = src_xv.vz;
@@ -417,7 +425,9 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     g.ovx = dst.vx; g.ovy = dst.vy; g.ovz = dst.vz;
     g.om = dst.m; g.oR = dst.R; g.operm = dst.perm;
     g.oqx = dst.qx; g.oqy = dst.qy; g.oqz = dst.qz;
+    g.hi4 = dst.hi4; g.lo4 = dst.lo4;
     g.idx = idx;
+    g.G = G;
     g.n = n;
     k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g);
     NCORP_CUDA_CHECK(cudaGetLastError());

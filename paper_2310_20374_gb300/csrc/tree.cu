@@ -247,8 +247,12 @@ __device__ __forceinline__ double cell_scale(const Ctrl *ctl, int lev, double rm
 
 // ---------------------------------------------------------------------------
 // Gravity climb: warp per leaf, bottom-up through per-cell arrival counters
-// (the last child to finish climbs to its parent; no waiting).  Lane 0 does
-// the geometry sequentially; all lanes share the multipole coefficients.
+// (the last child to finish climbs to its parent; nothing waits).  The centre
+// of mass is summed by lane 0 in key order from moonlets staged in shared
+// memory (the order fixes the rounding, so the result is reproducible bit for
+// bit); maxima are order-free and are reduced across the warp.  Multipoles:
+// P2M with one moonlet per lane and a warp reduction; M2M (App. C) with one
+// child per lane and a warp reduction.
 // ---------------------------------------------------------------------------
 struct ClimbArgs {
     const double *x, *y, *z, *m;
@@ -257,194 +261,247 @@ struct ClimbArgs {
     uint32_t *cx, *cy, *cz;
     double *M, *sx, *sy, *sz, *rmax, *rcrit, *rho;
     void *Mh;
+    float *rcf;
     const int *leaves;
     const Ctrl *ctl;
     double G, dt, theta;
 };
 
+constexpr int CLIMB_WARPS = 4;
+
+struct ClimbShared {
+    double a[32], b[32], c[32], d[32], e[32];
+};
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum_r(real v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// acc[midx(beta)] += mu d^beta for orders 0 and 2..P-1
 template <int P, typename real>
-__device__ void p2m_leaf(const ClimbArgs &A, int c, double sx, double sy, double sz, double rho, real *Mh) {
-    constexpr int NM = num_m(P);
-    const int lane = threadIdx.x & 31;
-    const int f = A.first[c], cnt = A.count[c];
-    const double irho = 1.0 / rho;   // exact: rho is a power of two
-    real acc[(NM + 31) / 32];
-    int ex[(NM + 31) / 32][3];
+__device__ __forceinline__ void p2m_add(real dx, real dy, real dz, real mu, real *acc) {
+    real px[P], py[P], pz[P];
+    px[0] = py[0] = pz[0] = real(1);
 #pragma unroll
-    for (int r = 0; r < (NM + 31) / 32; r++) {
-        acc[r] = real(0);
-        const int j = lane + 32 * r;
-        const int si = j == 0 ? 0 : j + 3;
-        ex[r][0] = j < NM ? c_exp.e[si][0] : 0;
-        ex[r][1] = j < NM ? c_exp.e[si][1] : 0;
-        ex[r][2] = j < NM ? c_exp.e[si][2] : 0;
+    for (int k = 1; k < P; k++) {
+        px[k] = px[k - 1] * dx;
+        py[k] = py[k - 1] * dy;
+        pz[k] = pz[k - 1] * dz;
     }
-    for (int k0 = 0; k0 < cnt; k0 += 32) {
-        real dx = 0, dy = 0, dz = 0, mu = 0;
-        if (k0 + lane < cnt) {
-            const int k = f + k0 + lane;
-            dx = static_cast<real>(dmul(dsub(A.x[k], sx), irho));
-            dy = static_cast<real>(dmul(dsub(A.y[k], sy), irho));
-            dz = static_cast<real>(dmul(dsub(A.z[k], sz), irho));
-            mu = static_cast<real>(A.G * A.m[k]);
-        }
-        const int lim = min(32, cnt - k0);
-        for (int t = 0; t < lim; t++) {
-            const real px = __shfl_sync(0xffffffffu, dx, t), py = __shfl_sync(0xffffffffu, dy, t);
-            const real pz = __shfl_sync(0xffffffffu, dz, t), pm = __shfl_sync(0xffffffffu, mu, t);
+    acc[0] += mu;
 #pragma unroll
-            for (int r = 0; r < (NM + 31) / 32; r++) {
-                real v = pm;
-                for (int i = 0; i < ex[r][0]; i++) v *= px;
-                for (int i = 0; i < ex[r][1]; i++) v *= py;
-                for (int i = 0; i < ex[r][2]; i++) v *= pz;
-                acc[r] += v;
+    for (int n = 2; n < P; n++)
+#pragma unroll
+        for (int k = 0; k <= n; k++)
+#pragma unroll
+            for (int c = 0; c <= k; c++) acc[midx(n - k, k - c, c)] += mu * px[n - k] * py[k - c] * pz[c];
+}
+
+// out[alpha] += sum_{gamma <= alpha, |gamma| != 1} l^(alpha-gamma)/(alpha-gamma)! r^|gamma| m[gamma],
+// l = (s_child - s_parent)/rho_parent, r = rho_child/rho_parent
+template <int P, typename real>
+__device__ __forceinline__ void m2m_add(const real *m, real lx, real ly, real lz, real r, real *out) {
+    real px[P], py[P], pz[P], pr[P];
+    px[0] = py[0] = pz[0] = pr[0] = real(1);
+#pragma unroll
+    for (int k = 1; k < P; k++) {
+        px[k] = px[k - 1] * lx;
+        py[k] = py[k - 1] * ly;
+        pz[k] = pz[k - 1] * lz;
+        pr[k] = pr[k - 1] * r;
+    }
+#pragma unroll
+    for (int n = 0; n < P; n++) {
+        if (n == 1) continue;
+#pragma unroll
+        for (int k = 0; k <= n; k++)
+#pragma unroll
+            for (int c = 0; c <= k; c++) {
+                const int a = n - k, b = k - c;
+                real acc = real(0);
+#pragma unroll
+                for (int ga = 0; ga <= a; ga++)
+#pragma unroll
+                    for (int gb = 0; gb <= b; gb++)
+#pragma unroll
+                        for (int gc = 0; gc <= c; gc++) {
+                            const int gn = ga + gb + gc;
+                            if (gn == 1) continue;
+                            acc += static_cast<real>(inv_mfact(a - ga, b - gb, c - gc)) * px[a - ga] * py[b - gb] *
+                                   pz[c - gc] * pr[gn] * m[midx(ga, gb, gc)];
+                        }
+                out[midx(a, b, c)] += acc;
             }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < (NM + 31) / 32; r++) {
-        const int j = lane + 32 * r;
-        if (j < NM) {
-            const real inv = static_cast<real>(c_ifact[ex[r][0]] * c_ifact[ex[r][1]] * c_ifact[ex[r][2]]);
-            Mh[(size_t)c * NM + j] = acc[r] * inv;
-        }
     }
 }
 
-// M-hat_alpha(P) = sum_children sum_{gamma <= alpha, |gamma| != 1}
-//   (-Lambda/rho_P)^(alpha-gamma)/(alpha-gamma)! (rho_c/rho_P)^|gamma| M-hat_gamma(child),
-// Lambda = s_P - s_child  (App. C with the binomial expansion in multi-index form)
 template <int P, typename real>
-__device__ void m2m_parent(const ClimbArgs &A, int pc, double sx, double sy, double sz, double rho, real *Mh) {
+__device__ __forceinline__ void store_reduced(real *acc, real *dst, int lane) {
     constexpr int NM = num_m(P);
-    const int lane = threadIdx.x & 31;
-    const int c0 = A.child0[pc], nch = A.nchild[pc];
-    const double irho = 1.0 / rho;
-    for (int j = lane; j < NM; j += 32) {
-        const int si = j == 0 ? 0 : j + 3;
-        const int a = c_exp.e[si][0], b = c_exp.e[si][1], cc = c_exp.e[si][2];
-        real acc = 0;
-        for (int ch = c0; ch < c0 + nch; ch++) {
-            const real lx = static_cast<real>(-dmul(dsub(sx, __ldcg(&A.sx[ch])), irho));
-            const real ly = static_cast<real>(-dmul(dsub(sy, __ldcg(&A.sy[ch])), irho));
-            const real lz = static_cast<real>(-dmul(dsub(sz, __ldcg(&A.sz[ch])), irho));
-            const real ratio = static_cast<real>(__ldcg(&A.rho[ch]) * irho);
-            const real *Mc = Mh + (size_t)ch * NM;
-            for (int ga = 0; ga <= a; ga++)
-                for (int gb = 0; gb <= b; gb++)
-                    for (int gc = 0; gc <= cc; gc++) {
-                        const int gn = ga + gb + gc;
-                        if (gn == 1) continue;
-                        const real mg = __ldcg(&Mc[midx(ga, gb, gc)]);
-                        real t = static_cast<real>(c_ifact[a - ga] * c_ifact[b - gb] * c_ifact[cc - gc]) * mg;
-                        for (int i = 0; i < a - ga; i++) t *= lx;
-                        for (int i = 0; i < b - gb; i++) t *= ly;
-                        for (int i = 0; i < cc - gc; i++) t *= lz;
-                        for (int i = 0; i < gn; i++) t *= ratio;
-                        acc += t;
-                    }
-        }
-        Mh[(size_t)pc * NM + j] = acc;
+#pragma unroll
+    for (int j = 0; j < NM; j++) {
+        const real v = warp_sum_r(acc[j]);
+        if (lane == (j & 31)) dst[j] = v;
     }
 }
 
 template <int P, typename real>
-__global__ void __launch_bounds__(256) k_climb_gravity(ClimbArgs A) {
+__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A) {
+    constexpr int NM = num_m(P);
+    __shared__ ClimbShared sh_all[CLIMB_WARPS];
     if (aborted(A.ctl)) return;
+    ClimbShared &S = sh_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     real *Mh = static_cast<real *>(A.Mh);
     for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
-    int c = A.leaves[gw];
-    // ---- leaf geometry (lane 0, sequential in key order)
-    double gsx = 0, gsy = 0, gsz = 0, grho = 1;
-    if (lane == 0) {
+        int c = A.leaves[gw];
+        // ---- leaf: centre of mass summed in key order by lane 0
         const int f = A.first[c], cnt = A.count[c];
         double M = 0, sx = 0, sy = 0, sz = 0;
-        for (int k = f; k < f + cnt; k++) {
-            const double m = A.m[k];
-            M = dadd(M, m);
-            sx = dadd(sx, dmul(m, A.x[k]));
-            sy = dadd(sy, dmul(m, A.y[k]));
-            sz = dadd(sz, dmul(m, A.z[k]));
-        }
-        sx = ddiv(sx, M);
-        sy = ddiv(sy, M);
-        sz = ddiv(sz, M);
-        double rmax = 0;
-        for (int k = f; k < f + cnt; k++) {
-            const double r = dnorm3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz));
-            if (r > rmax) rmax = r;
-        }
-        const int lev = A.level[c];
-        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
-        if (cap < rmax) rmax = cap;
-        const double rho = cell_scale(A.ctl, lev, rmax);
-        A.M[c] = M;
-        A.sx[c] = sx;
-        A.sy[c] = sy;
-        A.sz[c] = sz;
-        A.rmax[c] = rmax;
-        A.rho[c] = rho;
-        gsx = sx; gsy = sy; gsz = sz; grho = rho;
-    }
-    gsx = __shfl_sync(0xffffffffu, gsx, 0);
-    gsy = __shfl_sync(0xffffffffu, gsy, 0);
-    gsz = __shfl_sync(0xffffffffu, gsz, 0);
-    grho = __shfl_sync(0xffffffffu, grho, 0);
-    p2m_leaf<P, real>(A, c, gsx, gsy, gsz, grho, Mh);
-    // ---- climb
-    while (true) {
-        __threadfence();
-        __syncwarp();
-        int pc = A.parent[c];
-        if (pc < 0) break;
-        int last = 0;
-        if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (!last) break;
-        __threadfence();
-        c = pc;
-        if (lane == 0) {
-            const int c0 = A.child0[c], nch = A.nchild[c];
-            double M = 0, sx = 0, sy = 0, sz = 0;
-            for (int ch = c0; ch < c0 + nch; ch++) {
-                const double mc = __ldcg(&A.M[ch]);
-                M = dadd(M, mc);
-                sx = dadd(sx, dmul(mc, __ldcg(&A.sx[ch])));
-                sy = dadd(sy, dmul(mc, __ldcg(&A.sy[ch])));
-                sz = dadd(sz, dmul(mc, __ldcg(&A.sz[ch])));
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int lim = min(32, cnt - k0);
+            __syncwarp();
+            if (lane < lim) {
+                S.a[lane] = A.x[f + k0 + lane];
+                S.b[lane] = A.y[f + k0 + lane];
+                S.c[lane] = A.z[f + k0 + lane];
+                S.d[lane] = A.m[f + k0 + lane];
             }
+            __syncwarp();
+            if (lane == 0)
+                for (int k = 0; k < lim; k++) {
+                    const double m = S.d[k];
+                    M = dadd(M, m);
+                    sx = dadd(sx, dmul(m, S.a[k]));
+                    sy = dadd(sy, dmul(m, S.b[k]));
+                    sz = dadd(sz, dmul(m, S.c[k]));
+                }
+        }
+        if (lane == 0) {
             sx = ddiv(sx, M);
             sy = ddiv(sy, M);
             sz = ddiv(sz, M);
-            double rmax = 0;
-            for (int ch = c0; ch < c0 + nch; ch++) {
-                const double r = dadd(__ldcg(&A.rmax[ch]), dnorm3(dsub(__ldcg(&A.sx[ch]), sx),
-                                                                   dsub(__ldcg(&A.sy[ch]), sy),
-                                                                   dsub(__ldcg(&A.sz[ch]), sz)));
-                if (r > rmax) rmax = r;
-            }
-            const int lev = A.level[c];
-            const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
-            if (cap < rmax) rmax = cap;
-            const double rho = cell_scale(A.ctl, lev, rmax);
+        }
+        M = __shfl_sync(0xffffffffu, M, 0);
+        sx = __shfl_sync(0xffffffffu, sx, 0);
+        sy = __shfl_sync(0xffffffffu, sy, 0);
+        sz = __shfl_sync(0xffffffffu, sz, 0);
+        double rmax = 0;
+        for (int k = lane; k < cnt; k += 32)
+            rmax = fmax(rmax, dnorm3(dsub(A.x[f + k], sx), dsub(A.y[f + k], sy), dsub(A.z[f + k], sz)));
+        rmax = warp_max(rmax);
+        const int lev = A.level[c];
+        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        double rho = cell_scale(A.ctl, lev, rmax);
+        if (lane == 0) {
             A.M[c] = M;
             A.sx[c] = sx;
             A.sy[c] = sy;
             A.sz[c] = sz;
             A.rmax[c] = rmax;
             A.rho[c] = rho;
-            gsx = sx; gsy = sy; gsz = sz; grho = rho;
         }
-        gsx = __shfl_sync(0xffffffffu, gsx, 0);
-        gsy = __shfl_sync(0xffffffffu, gsy, 0);
-        gsz = __shfl_sync(0xffffffffu, gsz, 0);
-        grho = __shfl_sync(0xffffffffu, grho, 0);
-        m2m_parent<P, real>(A, c, gsx, gsy, gsz, grho, Mh);
-    }
+        {   // P2M (Eq. multipole_moment), scaled: M-hat_beta = sum mu (d/rho)^beta / beta!
+            real acc[NM];
+#pragma unroll
+            for (int j = 0; j < NM; j++) acc[j] = real(0);
+            const double irho = 1.0 / rho;
+            for (int k = lane; k < cnt; k += 32)
+                p2m_add<P, real>(static_cast<real>((A.x[f + k] - sx) * irho), static_cast<real>((A.y[f + k] - sy) * irho),
+                                 static_cast<real>((A.z[f + k] - sz) * irho), static_cast<real>(A.G * A.m[f + k]), acc);
+#pragma unroll
+            for (int n = 0; n < P; n++) {
+                if (n == 1) continue;
+#pragma unroll
+                for (int k = 0; k <= n; k++)
+#pragma unroll
+                    for (int cc = 0; cc <= k; cc++)
+                        acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
+            }
+            store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
+        }
+        // ---- climb
+        while (true) {
+            __threadfence();
+            __syncwarp();
+            const int pc = A.parent[c];
+            if (pc < 0) break;
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) break;
+            __threadfence();
+            c = pc;
+            const int c0 = A.child0[c], nch = A.nchild[c];
+            if (lane < nch) {
+                S.a[lane] = __ldcg(&A.M[c0 + lane]);
+                S.b[lane] = __ldcg(&A.sx[c0 + lane]);
+                S.c[lane] = __ldcg(&A.sy[c0 + lane]);
+                S.d[lane] = __ldcg(&A.sz[c0 + lane]);
+                S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
+            }
+            __syncwarp();
+            double M2 = 0, px = 0, py = 0, pz = 0;
+            if (lane == 0) {
+                for (int ch = 0; ch < nch; ch++) {
+                    const double mc = S.a[ch];
+                    M2 = dadd(M2, mc);
+                    px = dadd(px, dmul(mc, S.b[ch]));
+                    py = dadd(py, dmul(mc, S.c[ch]));
+                    pz = dadd(pz, dmul(mc, S.d[ch]));
+                }
+                px = ddiv(px, M2);
+                py = ddiv(py, M2);
+                pz = ddiv(pz, M2);
+            }
+            M2 = __shfl_sync(0xffffffffu, M2, 0);
+            px = __shfl_sync(0xffffffffu, px, 0);
+            py = __shfl_sync(0xffffffffu, py, 0);
+            pz = __shfl_sync(0xffffffffu, pz, 0);
+            double rm = 0;
+            if (lane < nch) rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
+            rm = warp_max(rm);
+            const int plev = A.level[c];
+            const double pcap = corner_distance(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz);
+            if (pcap < rm) rm = pcap;
+            const double prho = cell_scale(A.ctl, plev, rm);
+            if (lane == 0) {
+                A.M[c] = M2;
+                A.sx[c] = px;
+                A.sy[c] = py;
+                A.sz[c] = pz;
+                A.rmax[c] = rm;
+                A.rho[c] = prho;
+            }
+            {   // M2M (App. C), one child per lane
+                real acc[NM];
+#pragma unroll
+                for (int j = 0; j < NM; j++) acc[j] = real(0);
+                if (lane < nch) {
+                    const int ch = c0 + lane;
+                    real mc[NM];
+#pragma unroll
+                    for (int j = 0; j < NM; j++) mc[j] = __ldcg(&Mh[(size_t)ch * NM + j]);
+                    const double ip = 1.0 / prho;
+                    m2m_add<P, real>(mc, static_cast<real>((S.b[lane] - px) * ip), static_cast<real>((S.c[lane] - py) * ip),
+                                     static_cast<real>((S.d[lane] - pz) * ip),
+                                     static_cast<real>(__ldcg(&A.rho[ch]) * ip), acc);
+                }
+                store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
+            }
+        }
     }
 }
 
@@ -481,8 +538,7 @@ __global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__
 
 template <int P, typename real>
 static void climb_gravity_t(ncorp_ctx *c, const ClimbArgs &A) {
-    const int block = 256;
-    k_climb_gravity<P, real><<<8 * c->num_sms, block, 0, c->stream>>>(A);
+    k_climb_gravity<P, real><<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A);
 }
 
 void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
@@ -515,79 +571,120 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
 }
 
 // ---------------------------------------------------------------------------
-// Collision climb: thread per leaf, bottom-up.  s-bar is the mean moonlet
-// position (children weighted by their moonlet counts), r_max as above, and
-// r_crit = r_max + max over children of (r_crit - r_max), a moonlet's being
-// R + dt |v|.
+// Collision climb: warp per leaf, bottom-up.  s-bar is the mean moonlet
+// position (children weighted by their moonlet counts), summed by lane 0 in
+// key order; r_max as above; r_crit = r_max + max over children of
+// (r_crit - r_max), a moonlet's being R + dt |v| (also stored, rounded up to
+// FP32, for the pair prefilter).
 // ---------------------------------------------------------------------------
-__global__ void k_climb_collision(ClimbArgs A) {
+__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs A) {
+    __shared__ ClimbShared sh_all[CLIMB_WARPS];
     if (aborted(A.ctl)) return;
+    ClimbShared &S = sh_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
-    int c = A.leaves[t];
-    {
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
+        int c = A.leaves[gw];
         const int f = A.first[c], cnt = A.count[c];
         double sx = 0, sy = 0, sz = 0;
-        for (int k = f; k < f + cnt; k++) {
-            sx = dadd(sx, A.x[k]);
-            sy = dadd(sy, A.y[k]);
-            sz = dadd(sz, A.z[k]);
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int lim = min(32, cnt - k0);
+            __syncwarp();
+            if (lane < lim) {
+                S.a[lane] = A.x[f + k0 + lane];
+                S.b[lane] = A.y[f + k0 + lane];
+                S.c[lane] = A.z[f + k0 + lane];
+            }
+            __syncwarp();
+            if (lane == 0)
+                for (int k = 0; k < lim; k++) {
+                    sx = dadd(sx, S.a[k]);
+                    sy = dadd(sy, S.b[k]);
+                    sz = dadd(sz, S.c[k]);
+                }
         }
-        const double w = static_cast<double>(cnt);
-        sx = ddiv(sx, w);
-        sy = ddiv(sy, w);
-        sz = ddiv(sz, w);
+        if (lane == 0) {
+            const double w = static_cast<double>(cnt);
+            sx = ddiv(sx, w);
+            sy = ddiv(sy, w);
+            sz = ddiv(sz, w);
+        }
+        sx = __shfl_sync(0xffffffffu, sx, 0);
+        sy = __shfl_sync(0xffffffffu, sy, 0);
+        sz = __shfl_sync(0xffffffffu, sz, 0);
         double rmax = 0, ex = 0;
-        for (int k = f; k < f + cnt; k++) {
-            const double r = dnorm3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz));
-            if (r > rmax) rmax = r;
-            const double e = dadd(A.R[k], dmul(A.dt, dnorm3(A.vx[k], A.vy[k], A.vz[k])));
-            if (e > ex) ex = e;
+        for (int k = lane; k < cnt; k += 32) {
+            const int i = f + k;
+            rmax = fmax(rmax, dnorm3(dsub(A.x[i], sx), dsub(A.y[i], sy), dsub(A.z[i], sz)));
+            const double e = dadd(A.R[i], dmul(A.dt, dnorm3(A.vx[i], A.vy[i], A.vz[i])));
+            ex = fmax(ex, e);
+            A.rcf[i] = __double2float_ru(e);
         }
+        rmax = warp_max(rmax);
+        ex = warp_max(ex);
         const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
         if (cap < rmax) rmax = cap;
-        A.sx[c] = sx;
-        A.sy[c] = sy;
-        A.sz[c] = sz;
-        A.rmax[c] = rmax;
-        A.rcrit[c] = dadd(rmax, ex);
-    }
-    while (true) {
-        __threadfence();
-        const int pc = A.parent[c];
-        if (pc < 0) break;
-        if (atomicAdd(&A.arrive[pc], 1) != A.nchild[pc] - 1) break;
-        __threadfence();
-        c = pc;
-        const int c0 = A.child0[c], nch = A.nchild[c];
-        double sx = 0, sy = 0, sz = 0;
-        for (int ch = c0; ch < c0 + nch; ch++) {
-            const double w = static_cast<double>(A.count[ch]);
-            sx = dadd(sx, dmul(w, __ldcg(&A.sx[ch])));
-            sy = dadd(sy, dmul(w, __ldcg(&A.sy[ch])));
-            sz = dadd(sz, dmul(w, __ldcg(&A.sz[ch])));
+        if (lane == 0) {
+            A.sx[c] = sx;
+            A.sy[c] = sy;
+            A.sz[c] = sz;
+            A.rmax[c] = rmax;
+            A.rcrit[c] = dadd(rmax, ex);
         }
-        const double w = static_cast<double>(A.count[c]);
-        sx = ddiv(sx, w);
-        sy = ddiv(sy, w);
-        sz = ddiv(sz, w);
-        double rmax = 0, ex = 0;
-        for (int ch = c0; ch < c0 + nch; ch++) {
-            const double rm = __ldcg(&A.rmax[ch]);
-            const double r = dadd(rm, dnorm3(dsub(__ldcg(&A.sx[ch]), sx), dsub(__ldcg(&A.sy[ch]), sy),
-                                             dsub(__ldcg(&A.sz[ch]), sz)));
-            if (r > rmax) rmax = r;
-            const double e = dsub(__ldcg(&A.rcrit[ch]), rm);
-            if (e > ex) ex = e;
+        while (true) {
+            __threadfence();
+            __syncwarp();
+            const int pc = A.parent[c];
+            if (pc < 0) break;
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) break;
+            __threadfence();
+            c = pc;
+            const int c0 = A.child0[c], nch = A.nchild[c];
+            if (lane < nch) {
+                S.a[lane] = static_cast<double>(A.count[c0 + lane]);
+                S.b[lane] = __ldcg(&A.sx[c0 + lane]);
+                S.c[lane] = __ldcg(&A.sy[c0 + lane]);
+                S.d[lane] = __ldcg(&A.sz[c0 + lane]);
+                S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
+            }
+            __syncwarp();
+            double px = 0, py = 0, pz = 0;
+            if (lane == 0) {
+                for (int ch = 0; ch < nch; ch++) {
+                    const double w = S.a[ch];
+                    px = dadd(px, dmul(w, S.b[ch]));
+                    py = dadd(py, dmul(w, S.c[ch]));
+                    pz = dadd(pz, dmul(w, S.d[ch]));
+                }
+                const double w = static_cast<double>(A.count[c]);
+                px = ddiv(px, w);
+                py = ddiv(py, w);
+                pz = ddiv(pz, w);
+            }
+            px = __shfl_sync(0xffffffffu, px, 0);
+            py = __shfl_sync(0xffffffffu, py, 0);
+            pz = __shfl_sync(0xffffffffu, pz, 0);
+            double rm = 0, e2 = 0;
+            if (lane < nch) {
+                rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
+                e2 = dsub(__ldcg(&A.rcrit[c0 + lane]), S.e[lane]);
+            }
+            rm = warp_max(rm);
+            e2 = warp_max(e2);
+            const double pcap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py, pz);
+            if (pcap < rm) rm = pcap;
+            if (lane == 0) {
+                A.sx[c] = px;
+                A.sy[c] = py;
+                A.sz[c] = pz;
+                A.rmax[c] = rm;
+                A.rcrit[c] = dadd(rm, e2);
+            }
         }
-        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
-        if (cap < rmax) rmax = cap;
-        A.sx[c] = sx;
-        A.sy[c] = sy;
-        A.sz[c] = sz;
-        A.rmax[c] = rmax;
-        A.rcrit[c] = dadd(rmax, ex);
-    }
     }
 }
 
@@ -599,9 +696,9 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
-    A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt;
+    A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_climb_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
+    k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A);
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
