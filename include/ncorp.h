@@ -163,9 +163,10 @@ int ncorp_tree_export(ncorp_ctx *ctx, int64_t *order, uint64_t *keys, double *ro
  *   mult  [cap][nm]: multipole moments M_beta = sum_i mu_i (x_i - s)^beta of
  *         Eq. multipole_moment in symmetric multi-index form, orders 0 and
  *         2..p-1 (nm = 1 for p = 1, else p(p+1)(p+2)/6 - 3)
- *   local [cap][nc]: the M2L sums C_alpha of Eq. phi_expanded accumulated on
- *         each cell by the walk, before the descent, orders 1..p
- *         (nc = (p+1)(p+2)(p+3)/6 - 1)
+ *   local [cap][nc]: the complete local expansion C_alpha of each cell: the
+ *         M2L sums of Eq. phi_expanded the walk gave the cell, plus its
+ *         ancestors' translated to its centre by the descent (Eq. shifting),
+ *         orders 1..p (nc = (p+1)(p+2)(p+3)/6 - 1)
  *   rho   [cap]: the cell's power-of-two scale
  * Within order n the components run over k = 0..n, c = 0..k with
  * (a, b, c) = (n-k, k-c, c) the powers of (x, y, z).  *p receives p.

@@ -34,8 +34,8 @@
  * including (a,a); "well separated" as (rcA+rcB)^2 <= |sA-sB|^2; no
  * softening; collision pruning with a 2^-40 relative margin; the corner
  * cap computed on the cell cube widened by L*2^-48; the moonlet mean of
- * Eq. center weighted by child counts; theta(M) solved by 64 bisection
- * steps without libm.
+ * Eq. center weighted by child counts; theta(M) solved by 12 bisection
+ * steps and 4 Newton steps without libm.
  */
 #include <math.h>
 #include <stdint.h>
@@ -149,8 +149,11 @@ void or_keys(int64_t n, const double *pos, double root[4], uint32_t *q, uint64_t
 /* ------------------------------------------------------------------------ */
 /* Opening angle theta(M) (Dehnen 2002, Eq. 13):                            */
 /*   theta^5/(1-theta)^2 = [theta_min^5/(1-theta_min)^2] (M/M_tot)^(-1/3),  */
-/* i.e. f(theta) = theta^15 M - K^3 M_tot (1-theta)^6 = 0, monotone on      */
-/* [theta_min, 1); 64 bisection steps with + - x only.                      */
+/* i.e. the root in [theta_min, 1) of the increasing                         */
+/*   f(theta) = theta^15 M - K^3 M_tot (1-theta)^6:                          */
+/* 12 bisection steps, then 4 Newton steps kept inside the final bracket,    */
+/* with + - x / only (no libm), so that any IEEE implementation evaluating   */
+/* the same expressions in the same order gets the same bits.                */
 /* ------------------------------------------------------------------------ */
 double or_theta(double M, double Mtot, double theta_min)
 {
@@ -160,14 +163,26 @@ double or_theta(double M, double Mtot, double theta_min)
     double K3 = (K * K) * K;
     double rhs = K3 * Mtot;
     double lo = theta_min, hi = 1.0;
-    for (int it = 0; it < 64; it++) {
+    for (int it = 0; it < 12; it++) {
         double mid = (lo + hi) * 0.5;
         double m2 = mid * mid, m3 = m2 * mid, m6 = m3 * m3, m12 = m6 * m6, m15 = m12 * m3;
         double w = 1.0 - mid, w2 = w * w, w3 = w2 * w, w6 = w3 * w3;
         double f = m15 * M - rhs * w6;
         if (f > 0.0) hi = mid; else lo = mid;
     }
-    return hi;
+    double th = (lo + hi) * 0.5;
+    for (int it = 0; it < 4; it++) {
+        double w = 1.0 - th;
+        double q2 = th * th, q3 = q2 * th, q6 = q3 * q3, q12 = q6 * q6, q14 = q12 * q2, q15 = q14 * th;
+        double w2 = w * w, w3 = w2 * w, w5 = w3 * w2, w6 = w3 * w3;
+        double f = q15 * M - rhs * w6;
+        double fp = (15.0 * q14) * M + (6.0 * rhs) * w5;
+        double nt = th - f / fp;
+        if (nt < lo) nt = lo;
+        if (nt > hi) nt = hi;
+        th = nt;
+    }
+    return th;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -899,10 +914,12 @@ int or_falcon_accel(const or_params *P, int64_t n, const double *pos, const doub
     return 0;
 }
 
-/* Per-cell expansions for parity of the multipole stages: after the climb and
- * the walk (before the descent), cells in level-major order; M: packed full
- * tensors of orders 0..p-1 (OFF(p) values per cell), C: the M2L sums of orders
- * 0..p (OFF(p+1) values per cell, order 0 unused).  Returns the cell count. */
+/* Per-cell expansions for parity of the multipole stages: after the climb,
+ * the walk and the descent, cells in level-major order; M: packed full tensors
+ * of orders 0..p-1 (OFF(p) values per cell), C: the complete local expansion
+ * of each cell (its M2L sums plus its ancestors' translated to its centre),
+ * orders 0..p (OFF(p+1) values per cell, order 0 unused).  Returns the cell
+ * count. */
 int64_t or_expansions(const or_params *P, int64_t n, const double *pos, const double *mass,
                       double *Mout, double *Cout, int64_t cap)
 {
@@ -915,6 +932,7 @@ int64_t or_expansions(const or_params *P, int64_t n, const double *pos, const do
     climb_gravity(&T, T.rootn);
     finish_gravity(&T);
     tree_walk(&T, T.rootn, T.rootn, 1);
+    descend(&T, T.rootn);
     Node **sorted = (Node **)malloc(sizeof(Node *) * T.nnodes);
     memcpy(sorted, T.nodes, sizeof(Node *) * T.nnodes);
     qsort(sorted, (size_t)T.nnodes, sizeof(Node *), cmp_node);

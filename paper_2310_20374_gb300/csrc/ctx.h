@@ -31,6 +31,12 @@ struct Cells {
     double *M = nullptr, *sx = nullptr, *sy = nullptr, *sz = nullptr, *rmax = nullptr, *rcrit = nullptr,
            *rho = nullptr;                                 // gravity climb
     double *bx = nullptr, *by = nullptr, *bz = nullptr, *bmax = nullptr, *bcrit = nullptr;  // collision climb
+    // FP32 copies for the walk's first test and the FP32 kernels:
+    float4 *gh = nullptr;     // gravity centre rounded to FP32 (xyz), r_crit rounded to FP32 (w)
+    float4 *gl = nullptr;     // centre - hi (xyz), rho (w, exact power of two)
+    float4 *shift = nullptr;  // (s_cell - s_parent)/rho_parent (xyz), rho_cell/rho_parent (w)
+    float4 *bh = nullptr;     // collision centre hi (xyz), collision r_crit (w)
+    float4 *bl = nullptr;     // collision centre lo (xyz)
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
     void *Ch = nullptr;       // [cap][num_c(p)] local coefficients (float or double)
     int *leaves = nullptr;    // leaf cell ids

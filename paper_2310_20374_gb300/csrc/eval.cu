@@ -47,6 +47,7 @@ __constant__ ExpTable2 c_exp2 = make_exp_table2();
 struct EvalArgs {
     const int *leaves, *level, *parent, *first, *count;
     const double *sx, *sy, *sz, *rho;
+    const float4 *gh, *gl, *shift;
     const void *Ch;
     const int *p2p_off, *p2p_src;
     int p2p_dir_cap;
@@ -62,13 +63,13 @@ struct EvalArgs {
 
 constexpr int EVAL_WARPS = 4;   // warps per block
 
+constexpr int EVAL_BUF = 128;   // staged source moonlets per warp
+
 template <int P, typename real>
 struct EvalShared {
     static constexpr int NC = num_c(P);
-    real C[2][NC];
-    real pw[3][P + 1];
-    int path[MAX_LEVEL + 2];
-    float4 h[32], l[32];                     // FP32 path: staged sources (hi + mu, lo)
+    real C[1][NC];
+    float4 h[EVAL_BUF], l[EVAL_BUF];         // FP32 path: staged sources (hi + mu, lo)
     double dx[32], dy[32], dz[32], dm[32];   // FP64 path
 };
 
@@ -139,10 +140,209 @@ __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tree descent (Sect. 3.4.3): level by level from the root, every cell adds
+// its parent's (already complete) local expansion translated to its own
+// centre.  One cooperative launch; a warp per cell, lanes over the output
+// coefficients; the cell's C-hat is overwritten with the complete expansion.
+// ---------------------------------------------------------------------------
+struct DescendArgs {
+    const int *parent;
+    const float4 *shift;
+    const double *sx, *sy, *sz, *rho;
+    void *Ch;
+    Ctrl *ctl;
+};
+
 template <int P, typename real>
-__global__ void __launch_bounds__(32 * EVAL_WARPS) k_eval(EvalArgs A) {
+__global__ void __launch_bounds__(256) k_descend(DescendArgs A) {
     constexpr int NC = num_c(P);
     constexpr bool f32 = std::is_same<real, float>::value;
+    __shared__ real s_C[8][NC];
+    __shared__ real s_pw[8][3][P + 1];
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    real *Ch = static_cast<real *>(A.Ch);
+    volatile Ctrl *vc = A.ctl;
+    const int maxl = vc->max_level;
+    for (int lev = 1; lev <= maxl; lev++) {
+        const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
+        for (int c = ls + gw; c < le; c += nwarps) {
+            const int pc = A.parent[c];
+            for (int i = lane; i < NC; i += 32) s_C[wl][i] = __ldcg(&Ch[(size_t)pc * NC + i]);
+            real ratio;
+            if constexpr (f32) {
+                const float4 sh = A.shift[c];
+                ratio = sh.w;
+                if (lane < 3) {
+                    const float h = lane == 0 ? sh.x : (lane == 1 ? sh.y : sh.z);
+                    float pw = 1.0f;
+                    for (int k = 0; k <= P; k++) {
+                        s_pw[wl][lane][k] = pw;
+                        pw *= h;
+                    }
+                }
+            } else {
+                const double iprho = 1.0 / A.rho[pc];
+                ratio = A.rho[c] * iprho;
+                if (lane < 3) {
+                    const double dv = lane == 0 ? A.sx[c] - A.sx[pc] : (lane == 1 ? A.sy[c] - A.sy[pc] : A.sz[c] - A.sz[pc]);
+                    const real h = dv * iprho;
+                    real pw = real(1);
+                    for (int k = 0; k <= P; k++) {
+                        s_pw[wl][lane][k] = pw;
+                        pw *= h;
+                    }
+                }
+            }
+            __syncwarp();
+            for (int i = lane; i < NC; i += 32) {
+                const int a = c_exp2.e[i + 1][0], b = c_exp2.e[i + 1][1], cc = c_exp2.e[i + 1][2];
+                const int n = a + b + cc;
+                real acc = real(0);
+                for (int nb = 0; nb <= P - n; nb++)
+                    for (int kb = 0; kb <= nb; kb++)
+                        for (int c2 = 0; c2 <= kb; c2++) {
+                            const int ab = nb - kb, bb = kb - c2;
+                            const real w = s_pw[wl][0][ab] * s_pw[wl][1][bb] * s_pw[wl][2][c2] *
+                                           static_cast<real>(c_ifact[ab] * c_ifact[bb] * c_ifact[c2]);
+                            acc += s_C[wl][cidx(a + ab, b + bb, cc + c2)] * w;
+                        }
+                for (int k = 0; k < n; k++) acc *= ratio;   // (rho_c/rho_p)^n applied to the small factor first
+                Ch[(size_t)c * NC + i] += acc;
+            }
+            __syncwarp();
+        }
+        if (!grid_sync(A.ctl)) return;
+    }
+}
+
+// Near field of one group of targets (NT per lane) from the leaf's direct
+// list: source leaves are taken four at a time, their moonlets staged into
+// the warp's buffer, and every lane sums over the whole buffer.
+template <int NT>
+__device__ __forceinline__ void p2p_list_f32(const EvalArgs &A, float4 *bh, float4 *bl, int s0, int s1, int lane,
+                                             const float4 *th, const float4 *tl, float *ax, float *ay, float *az) {
+    for (int si = s0; si < s1; si += 4) {
+        const int nc = min(4, s1 - si);
+        int fst = 0, cn = 0;
+        if (lane < nc) {
+            const int src = A.p2p_src[si + lane];
+            fst = A.first[src];
+            cn = A.count[src];
+        }
+        int f[4], o[4], total = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            f[q] = __shfl_sync(0xffffffffu, fst, q);
+            o[q] = total;
+            total += __shfl_sync(0xffffffffu, cn, q);
+        }
+        for (int w0 = 0; w0 < total; w0 += EVAL_BUF) {
+            const int lim = min(EVAL_BUF, total - w0);
+            __syncwarp();
+            for (int t = lane; t < EVAL_BUF; t += 32) {
+                const int g = w0 + t;
+                if (t < lim) {
+                    const int q = g >= o[3] ? 3 : (g >= o[2] ? 2 : (g >= o[1] ? 1 : 0));
+                    const int jj = f[q] + g - o[q];
+                    bh[t] = A.hi4[jj];
+                    bl[t] = A.lo4[jj];
+                } else if (t < ((lim + 7) & ~7)) {   // pad to a multiple of 8 with mu = 0 far away
+                    bh[t] = make_float4(1e18f, 0.f, 0.f, 0.f);
+                    bl[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncwarp();
+            const int lim8 = (lim + 7) & ~7;
+            for (int k = 0; k < lim8; k += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float4 h = bh[k + u], l = bl[k + u];
+#pragma unroll
+                    for (int t = 0; t < NT; t++) p2p_f32(h, l, th[t], tl[t], ax[t], ay[t], az[t]);
+                }
+            }
+        }
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void p2p_list_f64(const EvalArgs &A, double *bx, double *by, double *bz, double *bm,
+                                             int s0, int s1, int lane, const double *X, const double *Y,
+                                             const double *Z, double *ax, double *ay, double *az) {
+    for (int si = s0; si < s1; si++) {
+        const int src = A.p2p_src[si];
+        const int sf = A.first[src], sc = A.count[src];
+        for (int j0 = 0; j0 < sc; j0 += 32) {
+            const int lim = min(32, sc - j0);
+            __syncwarp();
+            if (lane < lim) {
+                const int j = sf + j0 + lane;
+                bx[lane] = A.x[j];
+                by[lane] = A.y[j];
+                bz[lane] = A.z[j];
+                bm[lane] = A.G * A.m[j];
+            }
+            __syncwarp();
+            for (int k = 0; k < lim; k++)
+#pragma unroll
+                for (int t = 0; t < NT; t++) p2p_f64(bx[k], by[k], bz[k], bm[k], X[t], Y[t], Z[t], ax[t], ay[t], az[t]);
+        }
+    }
+}
+
+// L2P + near field + external forces for the targets f + t0 + lane + 32 t, t < NT
+template <int P, typename real, int NT>
+__device__ __forceinline__ void eval_targets(const EvalArgs &A, EvalShared<P, real> &S, const real *C, int leaf, int f,
+                                             int cnt, int t0, int lane, int s0, int s1) {
+    constexpr bool f32 = std::is_same<real, float>::value;
+    const float4 lgh = A.gh[leaf], lgl = A.gl[leaf];
+    const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
+    real ax[NT], ay[NT], az[NT];
+    double X[NT], Y[NT], Z[NT];
+    float4 th[NT], tl[NT];
+    bool act[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const int ti = t0 + lane + 32 * t;
+        act[t] = ti < cnt;
+        const int i = f + (act[t] ? ti : 0);
+        ax[t] = ay[t] = az[t] = real(0);
+        X[t] = A.x[i]; Y[t] = A.y[i]; Z[t] = A.z[i];
+        th[t] = A.hi4[i];
+        tl[t] = A.lo4[i];
+        if constexpr (f32) {
+            l2p<P, real>(C, ((th[t].x - lgh.x) + (tl[t].x - lgl.x)) * irf, ((th[t].y - lgh.y) + (tl[t].y - lgl.y)) * irf,
+                         ((th[t].z - lgh.z) + (tl[t].z - lgl.z)) * irf, ax[t], ay[t], az[t]);
+            ax[t] *= irf; ay[t] *= irf; az[t] *= irf;
+        } else {
+            const double irho = 1.0 / A.rho[leaf];
+            l2p<P, real>(C, (X[t] - A.sx[leaf]) * irho, (Y[t] - A.sy[leaf]) * irho, (Z[t] - A.sz[leaf]) * irho, ax[t],
+                         ay[t], az[t]);
+            ax[t] *= irho; ay[t] *= irho; az[t] *= irho;
+        }
+    }
+    if constexpr (f32) p2p_list_f32<NT>(A, S.h, S.l, s0, s1, lane, th, tl, ax, ay, az);
+    else p2p_list_f64<NT>(A, S.dx, S.dy, S.dz, S.dm, s0, s1, lane, X, Y, Z, ax, ay, az);
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        if (!act[t]) continue;
+        const int i = f + t0 + lane + 32 * t;
+        double ex, ey, ez;
+        external_force(A.ext, X[t], Y[t], Z[t], ex, ey, ez);
+        const double mx = ax[t], my = ay[t], mz = az[t];
+        A.ax[i] = mx + ex;
+        A.ay[i] = my + ey;
+        A.az[i] = mz + ez;
+        if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
+    }
+}
+
+template <int P, typename real>
+__global__ void __launch_bounds__(32 * EVAL_WARPS, 4) k_eval(EvalArgs A) {
+    constexpr int NC = num_c(P);
     __shared__ EvalShared<P, real> sh_all[EVAL_WARPS];
     if (aborted(A.ctl)) return;
     EvalShared<P, real> &S = sh_all[threadIdx.x >> 5];
@@ -155,139 +355,30 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS) k_eval(EvalArgs A) {
         li = __shfl_sync(0xffffffffu, li, 0);
         if (li >= nl) break;
         const int leaf = A.leaves[li];
-        // ---- ancestor chain and descent
-        if (lane == 0) {
-            int c = leaf;
-            for (int d = A.level[leaf]; d >= 0; d--) {
-                S.path[d] = c;
-                c = A.parent[c];
-            }
-        }
         __syncwarp();
-        const int depth = A.level[leaf];
-        for (int i = lane; i < NC; i += 32) S.C[0][i] = Ch[(size_t)S.path[0] * NC + i];
-        int cb = 0;
+        for (int i = lane; i < NC; i += 32) S.C[0][i] = Ch[(size_t)leaf * NC + i];   // complete after the descent
         __syncwarp();
-        for (int d = 1; d <= depth; d++) {
-            const int pc = S.path[d - 1], cc = S.path[d];
-            const double iprho = 1.0 / A.rho[pc];
-            if (lane < 3) {
-                const double dv = lane == 0 ? A.sx[cc] - A.sx[pc] : (lane == 1 ? A.sy[cc] - A.sy[pc] : A.sz[cc] - A.sz[pc]);
-                const real h = static_cast<real>(dv * iprho);
-                real pw = real(1);
-                for (int k = 0; k <= P; k++) {
-                    S.pw[lane][k] = pw;
-                    pw *= h;
-                }
-            }
-            __syncwarp();
-            const real ratio = static_cast<real>(A.rho[cc] * iprho);
-            for (int i = lane; i < NC; i += 32) {
-                const int a = c_exp2.e[i + 1][0], b = c_exp2.e[i + 1][1], c = c_exp2.e[i + 1][2];
-                const int n = a + b + c;
-                real acc = real(0);
-                for (int nb = 0; nb <= P - n; nb++)
-                    for (int kb = 0; kb <= nb; kb++)
-                        for (int c2 = 0; c2 <= kb; c2++) {
-                            const int ab = nb - kb, bb = kb - c2;
-                            const real w = S.pw[0][ab] * S.pw[1][bb] * S.pw[2][c2] *
-                                           static_cast<real>(c_ifact[ab] * c_ifact[bb] * c_ifact[c2]);
-                            acc += S.C[cb][cidx(a + ab, b + bb, c + c2)] * w;
-                        }
-                for (int k = 0; k < n; k++) acc *= ratio;   // (rho_c/rho_p)^n applied to the small factor first
-                S.C[cb ^ 1][i] = Ch[(size_t)cc * NC + i] + acc;
-            }
-            cb ^= 1;
-            __syncwarp();
-        }
-        const real *C = S.C[cb];
-        // ---- moonlets of the leaf, two per lane
         const int f = A.first[leaf], cnt = A.count[leaf];
-        const double lsx = A.sx[leaf], lsy = A.sy[leaf], lsz = A.sz[leaf];
-        const double irho = 1.0 / A.rho[leaf];
         const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
-        for (int t0 = 0; t0 < cnt; t0 += 64) {
-            const int i0 = f + t0 + lane, i1 = i0 + 32;
-            const bool act0 = t0 + lane < cnt, act1 = t0 + lane + 32 < cnt;
-            real ax0 = 0, ay0 = 0, az0 = 0, ax1 = 0, ay1 = 0, az1 = 0;
-            float4 th0 = make_float4(0, 0, 0, 0), tl0 = th0, th1 = th0, tl1 = th0;
-            double X0 = 0, Y0 = 0, Z0 = 0, X1 = 0, Y1 = 0, Z1 = 0;
-            if (act0) {
-                X0 = A.x[i0]; Y0 = A.y[i0]; Z0 = A.z[i0];
-                l2p<P, real>(C, static_cast<real>((X0 - lsx) * irho), static_cast<real>((Y0 - lsy) * irho),
-                             static_cast<real>((Z0 - lsz) * irho), ax0, ay0, az0);
-                if (f32) { th0 = A.hi4[i0]; tl0 = A.lo4[i0]; }
-            }
-            if (act1) {
-                X1 = A.x[i1]; Y1 = A.y[i1]; Z1 = A.z[i1];
-                l2p<P, real>(C, static_cast<real>((X1 - lsx) * irho), static_cast<real>((Y1 - lsy) * irho),
-                             static_cast<real>((Z1 - lsz) * irho), ax1, ay1, az1);
-                if (f32) { th1 = A.hi4[i1]; tl1 = A.lo4[i1]; }
-            }
-            {
-                const real ir = static_cast<real>(irho);
-                ax0 *= ir; ay0 *= ir; az0 *= ir;
-                ax1 *= ir; ay1 *= ir; az1 *= ir;
-            }
-            for (int si = s0; si < s1; si++) {
-                const int src = A.p2p_src[si];
-                const int sf = A.first[src], sc = A.count[src];
-                for (int j0 = 0; j0 < sc; j0 += 32) {
-                    const int lim = min(32, sc - j0);
-                    __syncwarp();
-                    if (lane < lim) {
-                        const int j = sf + j0 + lane;
-                        if (f32) {
-                            S.h[lane] = A.hi4[j];
-                            S.l[lane] = A.lo4[j];
-                        } else {
-                            S.dx[lane] = A.x[j];
-                            S.dy[lane] = A.y[j];
-                            S.dz[lane] = A.z[j];
-                            S.dm[lane] = A.G * A.m[j];
-                        }
-                    }
-                    __syncwarp();
-                    if constexpr (f32) {
-                        for (int k = 0; k < lim; k++) {
-                            const float4 h = S.h[k], l = S.l[k];
-                            p2p_f32(h, l, th0, tl0, ax0, ay0, az0);
-                            p2p_f32(h, l, th1, tl1, ax1, ay1, az1);
-                        }
-                    } else {
-                        for (int k = 0; k < lim; k++) {
-                            const double jx = S.dx[k], jy = S.dy[k], jz = S.dz[k], mu = S.dm[k];
-                            p2p_f64(jx, jy, jz, mu, X0, Y0, Z0, ax0, ay0, az0);
-                            p2p_f64(jx, jy, jz, mu, X1, Y1, Z1, ax1, ay1, az1);
-                        }
-                    }
-                }
-            }
-            if (act0) {
-                double ex, ey, ez;
-                external_force(A.ext, X0, Y0, Z0, ex, ey, ez);
-                const double mx = ax0, my = ay0, mz = az0;
-                A.ax[i0] = mx + ex;
-                A.ay[i0] = my + ey;
-                A.az[i0] = mz + ez;
-                if (A.amx) { A.amx[i0] = mx; A.amy[i0] = my; A.amz[i0] = mz; }
-            }
-            if (act1) {
-                double ex, ey, ez;
-                external_force(A.ext, X1, Y1, Z1, ex, ey, ez);
-                const double mx = ax1, my = ay1, mz = az1;
-                A.ax[i1] = mx + ex;
-                A.ay[i1] = my + ey;
-                A.az[i1] = mz + ez;
-                if (A.amx) { A.amx[i1] = mx; A.amy[i1] = my; A.amz[i1] = mz; }
-            }
+        if (cnt <= 32) {
+            eval_targets<P, real, 1>(A, S, S.C[0], leaf, f, cnt, 0, lane, s0, s1);
+        } else {
+            for (int t0 = 0; t0 < cnt; t0 += 64) eval_targets<P, real, 2>(A, S, S.C[0], leaf, f, cnt, t0, lane, s0, s1);
         }
         __syncwarp();
     }
 }
 
 template <int P, typename real>
-static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
+static void eval_t(ncorp_ctx *c, const EvalArgs &A, DescendArgs D) {
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void *>(k_descend<P, real>), 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    void *args[] = {&D};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_descend<P, real>),
+                                                 dim3(per_sm * c->num_sms), dim3(256), args, 0, c->stream));
     k_eval<P, real><<<8 * c->num_sms, 32 * EVAL_WARPS, 0, c->stream>>>(A);
 }
 
@@ -296,6 +387,7 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     EvalArgs A;
     A.leaves = C.leaves; A.level = C.level; A.parent = C.parent; A.first = C.first; A.count = C.count;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
+    A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
     A.Ch = C.Ch;
     A.p2p_off = c->wl.p2p_off; A.p2p_src = c->wl.p2p_src; A.p2p_dir_cap = c->wl.p2p_dir_cap;
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;
@@ -309,10 +401,14 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     A.work = c->work_counter;
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
+    DescendArgs D;
+    D.parent = C.parent; D.shift = C.shift; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
+    D.Ch = C.Ch; D.ctl = c->ctl;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
 #define NCORP_EVAL_CASE(PP)                      \
     case PP:                                     \
-        if (mixed) eval_t<PP, float>(c, A);      \
-        else eval_t<PP, double>(c, A);           \
+        if (mixed) eval_t<PP, float>(c, A, D);   \
+        else eval_t<PP, double>(c, A, D);        \
         break;
     switch (p) {
         NCORP_EVAL_CASE(1)

@@ -55,6 +55,7 @@ struct M2LArgs {
     const int2 *dir;
     int dir_cap;
     const double *sx, *sy, *sz, *rho;
+    const float4 *gh, *gl;
     const void *Mh;
     void *Ch;
     const Ctrl *ctl;
@@ -80,8 +81,11 @@ __global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
     int cur = -1;
     double irho = 1.0;
     double tx = 0, ty = 0, tz = 0;
+    float4 th = make_float4(0, 0, 0, 1), tl = th;
+    float irf = 1.0f;
+    constexpr bool f32 = sizeof(real) == 4;
     auto flush = [&]() {
-        const real f = static_cast<real>(irho);
+        const real f = f32 ? static_cast<real>(irf) : static_cast<real>(irho);
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             atomic_add_real(&Ch[(size_t)cur * NC + i], acc[i] * f);
@@ -93,16 +97,31 @@ __global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
         if (d.x != cur) {
             if (cur >= 0) flush();
             cur = d.x;
-            irho = 1.0 / A.rho[cur];
-            tx = A.sx[cur];
-            ty = A.sy[cur];
-            tz = A.sz[cur];
+            if constexpr (f32) {
+                th = A.gh[cur];
+                tl = A.gl[cur];
+                irf = 1.0f / tl.w;   // exact: rho is a power of two
+            } else {
+                irho = 1.0 / A.rho[cur];
+                tx = A.sx[cur];
+                ty = A.sy[cur];
+                tz = A.sz[cur];
+            }
         }
         const int src = d.y;
-        const real ux = static_cast<real>((tx - A.sx[src]) * irho);
-        const real uy = static_cast<real>((ty - A.sy[src]) * irho);
-        const real uz = static_cast<real>((tz - A.sz[src]) * irho);
-        const real q = static_cast<real>(-A.rho[src] * irho);   // -rho_B / rho_A
+        real ux, uy, uz, q;
+        if constexpr (f32) {   // separation from double-float centres, no FP64 work
+            const float4 sh = A.gh[src], sl = A.gl[src];
+            ux = ((th.x - sh.x) + (tl.x - sl.x)) * irf;
+            uy = ((th.y - sh.y) + (tl.y - sl.y)) * irf;
+            uz = ((th.z - sh.z) + (tl.z - sl.z)) * irf;
+            q = -sl.w * irf;   // -rho_B / rho_A
+        } else {
+            ux = (tx - A.sx[src]) * irho;
+            uy = (ty - A.sy[src]) * irho;
+            uz = (tz - A.sz[src]) * irho;
+            q = -A.rho[src] * irho;
+        }
         real D[ND];
         green_derivatives<P, real>(ux, uy, uz, D);
         const real *Ms = Mh + (size_t)src * NM;
@@ -149,6 +168,7 @@ void launch_m2l(ncorp_ctx *c, int p, bool mixed) {
     A.dir = c->wl.m2l_dir;
     A.dir_cap = c->wl.m2l_dir_cap;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
+    A.gh = C.gh; A.gl = C.gl;
     A.Mh = C.Mh;
     A.Ch = C.Ch;
     A.ctl = c->ctl;

@@ -95,6 +95,7 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.M, cap); dalloc(C.sx, cap); dalloc(C.sy, cap); dalloc(C.sz, cap);
     dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
     dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
+    dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.shift, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
     double *mh = nullptr, *ch = nullptr;
     dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
     dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
@@ -742,7 +743,7 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
     dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
     dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
-    dfree(C.bcrit); dfree(C.Mh); dfree(C.Ch); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.shift); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
     WalkLists &W = c->wl;
     dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
     dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);

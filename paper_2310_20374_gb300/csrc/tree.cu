@@ -213,29 +213,20 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
 // Corner cap (Sect. 3.4.2): distance from s to the farthest corner of the
 // cell's cube, the cube widened by L 2^-48 on each side.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double corner_distance(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz,
-                                                  double sx, double sy, double sz) {
-    const double L = ctl->root[3];
-    double h = L;
-    for (int k = 0; k < lev; k++) h = dmul(h, 0.5);
-    const double eps = dmul(L, 0x1p-48);
-    const uint32_t cc[3] = {cx, cy, cz};
-    const double s[3] = {sx, sy, sz};
-    double d[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const double lo = dadd(ctl->root[k], dmul(static_cast<double>(cc[k]), h));
-        const double a = dsub(s[k], dsub(lo, eps));
-        const double b = dsub(dadd(dadd(lo, h), eps), s[k]);
-        d[k] = a > b ? a : b;
-    }
-    return dnorm3(d[0], d[1], d[2]);
+__device__ __forceinline__ double cell_side(const Ctrl *ctl, int lev) { return ldexp(ctl->root[3], -lev); }
+
+__device__ __forceinline__ double corner_axis(const Ctrl *ctl, int k, double h, uint32_t c, double s) {
+    const double eps = dmul(ctl->root[3], 0x1p-48);
+    const double lo = dadd(ctl->root[k], dmul(static_cast<double>(c), h));
+    const double a = dsub(s, dsub(lo, eps));
+    const double b = dsub(dadd(dadd(lo, h), eps), s);
+    return a > b ? a : b;
 }
 
-__device__ __forceinline__ double cell_side(const Ctrl *ctl, int lev) {
-    double h = ctl->root[3];
-    for (int k = 0; k < lev; k++) h = dmul(h, 0.5);
-    return h;
+__device__ __forceinline__ double corner_distance(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz,
+                                                  double sx, double sy, double sz) {
+    const double h = cell_side(ctl, lev);
+    return dnorm3(corner_axis(ctl, 0, h, cx, sx), corner_axis(ctl, 1, h, cy, sy), corner_axis(ctl, 2, h, cz, sz));
 }
 
 // Power-of-two scale of a cell's expansions: >= r_max (so |x - s|/rho <= 1)
@@ -245,21 +236,32 @@ __device__ __forceinline__ double cell_scale(const Ctrl *ctl, int lev, double rm
     return pow2_ceil(fmax(rmax, cell_side(ctl, lev) * 0x1p-8));
 }
 
+// FP32 double-float copy of a centre: hi = fl32(s), lo = fl32(s - hi)
+__device__ __forceinline__ void split3(double x, double y, double z, float4 &hi, float4 &lo) {
+    hi.x = static_cast<float>(x);
+    hi.y = static_cast<float>(y);
+    hi.z = static_cast<float>(z);
+    lo.x = static_cast<float>(x - static_cast<double>(hi.x));
+    lo.y = static_cast<float>(y - static_cast<double>(hi.y));
+    lo.z = static_cast<float>(z - static_cast<double>(hi.z));
+}
+
 // ---------------------------------------------------------------------------
-// Gravity climb: warp per leaf, bottom-up through per-cell arrival counters
-// (the last child to finish climbs to its parent; nothing waits).  The centre
-// of mass is summed by lane 0 in key order from moonlets staged in shared
-// memory (the order fixes the rounding, so the result is reproducible bit for
-// bit); maxima are order-free and are reduced across the warp.  Multipoles:
-// P2M with one moonlet per lane and a warp reduction; M2M (App. C) with one
-// child per lane and a warp reduction.
+// Climbs.  GB300 executes an FP64 warp instruction in the same time whatever
+// the number of active lanes, so the sequential, order-fixed FP64 sums that
+// make the geometry reproducible bit for bit are spread one cell per thread
+// (leaves) or one sum per lane (parents), never run on a single lane.
+// r_max of a leaf is sqrt(max_i |x_i - s|^2): a correctly rounded square root
+// is non-decreasing, so this equals max_i sqrt(|x_i - s|^2) exactly.
 // ---------------------------------------------------------------------------
 struct ClimbArgs {
     const double *x, *y, *z, *m;
+    const float4 *hi4, *lo4;
     const double *vx, *vy, *vz, *R;
     int *first, *count, *child0, *nchild, *parent, *level, *arrive;
     uint32_t *cx, *cy, *cz;
     double *M, *sx, *sy, *sz, *rmax, *rcrit, *rho;
+    float4 *gh, *gl, *shift;
     void *Mh;
     float *rcf;
     const int *leaves;
@@ -284,6 +286,46 @@ __device__ __forceinline__ real warp_sum_r(real v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ---- gravity leaves: one thread per leaf (Eqs. expansion_center, rmax_2, corner cap)
+__global__ void k_leaf_gravity(ClimbArgs A) {
+    if (aborted(A.ctl)) return;
+    const int n_leaves = A.ctl->n_leaves;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
+        const int c = A.leaves[t];
+        const int f = A.first[c], cnt = A.count[c];
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int k = f; k < f + cnt; k++) {
+            const double m = A.m[k];
+            M = dadd(M, m);
+            sx = dadd(sx, dmul(m, A.x[k]));
+            sy = dadd(sy, dmul(m, A.y[k]));
+            sz = dadd(sz, dmul(m, A.z[k]));
+        }
+        sx = ddiv(sx, M);
+        sy = ddiv(sy, M);
+        sz = ddiv(sz, M);
+        double d2 = 0;
+        for (int k = f; k < f + cnt; k++) d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+        double rmax = dsqrt(d2);
+        const int lev = A.level[c];
+        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        const double rho = cell_scale(A.ctl, lev, rmax);
+        A.M[c] = M;
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rho[c] = rho;
+        float4 hi, lo;
+        split3(sx, sy, sz, hi, lo);
+        hi.w = 0.f;
+        lo.w = static_cast<float>(rho);
+        A.gh[c] = hi;
+        A.gl[c] = lo;
+    }
 }
 
 // acc[midx(beta)] += mu d^beta for orders 0 and 2..P-1
@@ -354,8 +396,43 @@ __device__ __forceinline__ void store_reduced(real *acc, real *dst, int lane) {
     }
 }
 
+// Parent geometry with the warp: lane 0 sums the masses and lanes 1..3 the
+// mass-weighted coordinates, each in child order (as a sequential sum would);
+// lanes 1..3 divide; one lane per child forms r_max,c + |s_c - s|; one lane
+// per axis the corner distance.  Children are staged in S (a = M or count,
+// b, c, d = centre, e = r_max).  weights_are_mass: gravity (M) or collisions
+// (moonlet counts, divisor = the cell's count).
+__device__ __forceinline__ void parent_centre(const ClimbShared &S, int nch, int lane, bool weights_are_mass,
+                                              double cnt_parent, double &M, double &px, double &py, double &pz) {
+    double acc = 0;
+    if (lane < 4) {
+        const double *coord = lane == 1 ? S.b : (lane == 2 ? S.c : S.d);
+        for (int ch = 0; ch < nch; ch++) {
+            const double w = S.a[ch];
+            acc = lane == 0 ? dadd(acc, w) : dadd(acc, dmul(w, coord[ch]));
+        }
+    }
+    M = __shfl_sync(0xffffffffu, acc, 0);
+    const double div = weights_are_mass ? M : cnt_parent;
+    double q = (lane >= 1 && lane < 4) ? ddiv(acc, div) : 0.0;
+    px = __shfl_sync(0xffffffffu, q, 1);
+    py = __shfl_sync(0xffffffffu, q, 2);
+    pz = __shfl_sync(0xffffffffu, q, 3);
+}
+
+__device__ __forceinline__ double corner_warp(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz, double sx,
+                                              double sy, double sz, int lane) {
+    const double h = cell_side(ctl, lev);
+    double d = 0;
+    if (lane < 3) d = corner_axis(ctl, lane, h, lane == 0 ? cx : (lane == 1 ? cy : cz), lane == 0 ? sx : (lane == 1 ? sy : sz));
+    const double d0 = __shfl_sync(0xffffffffu, d, 0), d1 = __shfl_sync(0xffffffffu, d, 1),
+                 d2 = __shfl_sync(0xffffffffu, d, 2);
+    return dnorm3(d0, d1, d2);
+}
+
+// ---- gravity: P2M at the leaves, then parents (geometry, M2M, children's descent shifts)
 template <int P, typename real>
-__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A) {
+__global__ void __launch_bounds__(32 * CLIMB_WARPS, 4) k_climb_gravity(ClimbArgs A) {
     constexpr int NM = num_m(P);
     __shared__ ClimbShared sh_all[CLIMB_WARPS];
     if (aborted(A.ctl)) return;
@@ -366,61 +443,24 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A)
     real *Mh = static_cast<real *>(A.Mh);
     for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
         int c = A.leaves[gw];
-        // ---- leaf: centre of mass summed in key order by lane 0
-        const int f = A.first[c], cnt = A.count[c];
-        double M = 0, sx = 0, sy = 0, sz = 0;
-        for (int k0 = 0; k0 < cnt; k0 += 32) {
-            const int lim = min(32, cnt - k0);
-            __syncwarp();
-            if (lane < lim) {
-                S.a[lane] = A.x[f + k0 + lane];
-                S.b[lane] = A.y[f + k0 + lane];
-                S.c[lane] = A.z[f + k0 + lane];
-                S.d[lane] = A.m[f + k0 + lane];
-            }
-            __syncwarp();
-            if (lane == 0)
-                for (int k = 0; k < lim; k++) {
-                    const double m = S.d[k];
-                    M = dadd(M, m);
-                    sx = dadd(sx, dmul(m, S.a[k]));
-                    sy = dadd(sy, dmul(m, S.b[k]));
-                    sz = dadd(sz, dmul(m, S.c[k]));
-                }
-        }
-        if (lane == 0) {
-            sx = ddiv(sx, M);
-            sy = ddiv(sy, M);
-            sz = ddiv(sz, M);
-        }
-        M = __shfl_sync(0xffffffffu, M, 0);
-        sx = __shfl_sync(0xffffffffu, sx, 0);
-        sy = __shfl_sync(0xffffffffu, sy, 0);
-        sz = __shfl_sync(0xffffffffu, sz, 0);
-        double rmax = 0;
-        for (int k = lane; k < cnt; k += 32)
-            rmax = fmax(rmax, dnorm3(dsub(A.x[f + k], sx), dsub(A.y[f + k], sy), dsub(A.z[f + k], sz)));
-        rmax = warp_max(rmax);
-        const int lev = A.level[c];
-        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
-        if (cap < rmax) rmax = cap;
-        double rho = cell_scale(A.ctl, lev, rmax);
-        if (lane == 0) {
-            A.M[c] = M;
-            A.sx[c] = sx;
-            A.sy[c] = sy;
-            A.sz[c] = sz;
-            A.rmax[c] = rmax;
-            A.rho[c] = rho;
-        }
         {   // P2M (Eq. multipole_moment), scaled: M-hat_beta = sum mu (d/rho)^beta / beta!
+            const int f = A.first[c], cnt = A.count[c];
+            const float4 gh = A.gh[c], gl = A.gl[c];
+            const float ir = 1.0f / gl.w;
             real acc[NM];
 #pragma unroll
             for (int j = 0; j < NM; j++) acc[j] = real(0);
-            const double irho = 1.0 / rho;
-            for (int k = lane; k < cnt; k += 32)
-                p2m_add<P, real>(static_cast<real>((A.x[f + k] - sx) * irho), static_cast<real>((A.y[f + k] - sy) * irho),
-                                 static_cast<real>((A.z[f + k] - sz) * irho), static_cast<real>(A.G * A.m[f + k]), acc);
+            for (int k = lane; k < cnt; k += 32) {
+                if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
+                    const float4 h = A.hi4[f + k], l = A.lo4[f + k];
+                    p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
+                                     ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
+                } else {
+                    const double irho = 1.0 / A.rho[c];
+                    p2m_add<P, real>((A.x[f + k] - A.sx[c]) * irho, (A.y[f + k] - A.sy[c]) * irho,
+                                     (A.z[f + k] - A.sz[c]) * irho, A.G * A.m[f + k], acc);
+                }
+            }
 #pragma unroll
             for (int n = 0; n < P; n++) {
                 if (n == 1) continue;
@@ -453,28 +493,13 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A)
                 S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
             }
             __syncwarp();
-            double M2 = 0, px = 0, py = 0, pz = 0;
-            if (lane == 0) {
-                for (int ch = 0; ch < nch; ch++) {
-                    const double mc = S.a[ch];
-                    M2 = dadd(M2, mc);
-                    px = dadd(px, dmul(mc, S.b[ch]));
-                    py = dadd(py, dmul(mc, S.c[ch]));
-                    pz = dadd(pz, dmul(mc, S.d[ch]));
-                }
-                px = ddiv(px, M2);
-                py = ddiv(py, M2);
-                pz = ddiv(pz, M2);
-            }
-            M2 = __shfl_sync(0xffffffffu, M2, 0);
-            px = __shfl_sync(0xffffffffu, px, 0);
-            py = __shfl_sync(0xffffffffu, py, 0);
-            pz = __shfl_sync(0xffffffffu, pz, 0);
+            double M2, px, py, pz;
+            parent_centre(S, nch, lane, true, 0.0, M2, px, py, pz);
             double rm = 0;
             if (lane < nch) rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
             rm = warp_max(rm);
             const int plev = A.level[c];
-            const double pcap = corner_distance(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz);
+            const double pcap = corner_warp(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
             if (pcap < rm) rm = pcap;
             const double prho = cell_scale(A.ctl, plev, rm);
             if (lane == 0) {
@@ -484,6 +509,19 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A)
                 A.sz[c] = pz;
                 A.rmax[c] = rm;
                 A.rho[c] = prho;
+                float4 hi, lo;
+                split3(px, py, pz, hi, lo);
+                hi.w = 0.f;
+                lo.w = static_cast<float>(prho);
+                A.gh[c] = hi;
+                A.gl[c] = lo;
+            }
+            const double ip = 1.0 / prho;   // exact: prho is a power of two
+            if (lane < nch) {   // descent shift of each child (used by L2L)
+                const double crho = __ldcg(&A.rho[c0 + lane]);
+                A.shift[c0 + lane] = make_float4(static_cast<float>((S.b[lane] - px) * ip),
+                                                 static_cast<float>((S.c[lane] - py) * ip),
+                                                 static_cast<float>((S.d[lane] - pz) * ip), static_cast<float>(crho * ip));
             }
             {   // M2M (App. C), one child per lane
                 real acc[NM];
@@ -494,7 +532,6 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A)
                     real mc[NM];
 #pragma unroll
                     for (int j = 0; j < NM; j++) mc[j] = __ldcg(&Mh[(size_t)ch * NM + j]);
-                    const double ip = 1.0 / prho;
                     m2m_add<P, real>(mc, static_cast<real>((S.b[lane] - px) * ip), static_cast<real>((S.c[lane] - py) * ip),
                                      static_cast<real>((S.d[lane] - pz) * ip),
                                      static_cast<real>(__ldcg(&A.rho[ch]) * ip), acc);
@@ -506,8 +543,9 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_gravity(ClimbArgs A)
 }
 
 // theta(M) of Dehnen (2002) Eq. 13: theta^5/(1-theta)^2 = K (M/M_tot)^(-1/3),
-// K = theta_min^5/(1-theta_min)^2, solved as f(theta) = theta^15 M -
-// K^3 M_tot (1-theta)^6 = 0 by 64 bisection steps on [theta_min, 1).
+// K = theta_min^5/(1-theta_min)^2, i.e. the root in [theta_min, 1) of the
+// increasing f(theta) = theta^15 M - K^3 M_tot (1-theta)^6: 12 bisection
+// steps, then 4 Newton steps kept inside the final bracket (+ - x / only).
 __device__ double theta_of(double M, double Mtot, double tmin) {
     const double t2 = dmul(tmin, tmin), t4 = dmul(t2, t2), t5 = dmul(t4, tmin);
     const double u = dsub(1.0, tmin), u2 = dmul(u, u);
@@ -515,7 +553,7 @@ __device__ double theta_of(double M, double Mtot, double tmin) {
     const double K3 = dmul(dmul(K, K), K);
     const double rhs = dmul(K3, Mtot);
     double lo = tmin, hi = 1.0;
-    for (int it = 0; it < 64; it++) {
+    for (int it = 0; it < 12; it++) {
         const double mid = dmul(dadd(lo, hi), 0.5);
         const double m2 = dmul(mid, mid), m3 = dmul(m2, mid), m6 = dmul(m3, m3), m12 = dmul(m6, m6),
                      m15 = dmul(m12, m3);
@@ -524,16 +562,32 @@ __device__ double theta_of(double M, double Mtot, double tmin) {
         if (f > 0.0) hi = mid;
         else lo = mid;
     }
-    return hi;
+    double th = dmul(dadd(lo, hi), 0.5);
+    for (int it = 0; it < 4; it++) {
+        const double w = dsub(1.0, th);
+        const double q2 = dmul(th, th), q3 = dmul(q2, th), q6 = dmul(q3, q3), q12 = dmul(q6, q6),
+                     q14 = dmul(q12, q2), q15 = dmul(q14, th);
+        const double w2 = dmul(w, w), w3 = dmul(w2, w), w5 = dmul(w3, w2), w6 = dmul(w3, w3);
+        const double f = dsub(dmul(q15, M), dmul(rhs, w6));
+        const double fp = dadd(dmul(dmul(15.0, q14), M), dmul(dmul(6.0, rhs), w5));
+        double nt = dsub(th, ddiv(f, fp));
+        if (nt < lo) nt = lo;
+        if (nt > hi) nt = hi;
+        th = nt;
+    }
+    return th;
 }
 
 __global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__ rmax, double *__restrict__ rcrit,
-                        const Ctrl *ctl, int cap, double tmin) {
+                        float4 *gh, const Ctrl *ctl, int cap, double tmin) {
     if (aborted(ctl)) return;
     const int nc = min(ctl->n_cells, cap);
     const double Mtot = M[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-        rcrit[i] = ddiv(rmax[i], theta_of(M[i], Mtot, tmin));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const double rc = ddiv(rmax[i], theta_of(M[i], Mtot, tmin));
+        rcrit[i] = rc;
+        gh[i].w = static_cast<float>(rc);
+    }
 }
 
 template <int P, typename real>
@@ -544,12 +598,14 @@ static void climb_gravity_t(ncorp_ctx *c, const ClimbArgs &A) {
 void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
     Cells &C = c->cells;
     ClimbArgs A{};
-    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.hi4 = P.hi4; A.lo4 = P.lo4;
     A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.M = C.M; A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rmax = C.rmax; A.rcrit = C.rcrit; A.rho = C.rho;
+    A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
     A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
+    k_leaf_gravity<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
 #define NCORP_CLIMB_CASE(PP)                                             \
     case PP:                                                             \
         if (mixed) climb_gravity_t<PP, float>(c, A);                     \
@@ -566,17 +622,57 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     }
 #undef NCORP_CLIMB_CASE
     NCORP_CUDA_CHECK(cudaGetLastError());
-    k_rcrit<<<grid_for(C.cap, 256, 8 * c->num_sms), 256, 0, c->stream>>>(C.M, C.rmax, C.rcrit, c->ctl, C.cap, theta);
+    k_rcrit<<<grid_for(C.cap, 64, 16 * c->num_sms), 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta);
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
-// Collision climb: warp per leaf, bottom-up.  s-bar is the mean moonlet
-// position (children weighted by their moonlet counts), summed by lane 0 in
-// key order; r_max as above; r_crit = r_max + max over children of
-// (r_crit - r_max), a moonlet's being R + dt |v| (also stored, rounded up to
-// FP32, for the pair prefilter).
+// Collision climb (Eqs. center, rmax, rcrit): s-bar is the mean moonlet
+// position (children weighted by their moonlet counts); r_crit = r_max + max
+// over children of (r_crit - r_max), a moonlet's being R + dt |v| (stored,
+// rounded up to FP32, for the pair prefilter).
 // ---------------------------------------------------------------------------
+__global__ void k_leaf_collision(ClimbArgs A) {
+    if (aborted(A.ctl)) return;
+    const int n_leaves = A.ctl->n_leaves;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
+        const int c = A.leaves[t];
+        const int f = A.first[c], cnt = A.count[c];
+        double sx = 0, sy = 0, sz = 0;
+        for (int k = f; k < f + cnt; k++) {
+            sx = dadd(sx, A.x[k]);
+            sy = dadd(sy, A.y[k]);
+            sz = dadd(sz, A.z[k]);
+        }
+        const double w = static_cast<double>(cnt);
+        sx = ddiv(sx, w);
+        sy = ddiv(sy, w);
+        sz = ddiv(sz, w);
+        double d2 = 0, ex = 0;
+        for (int k = f; k < f + cnt; k++) {
+            d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+            const double e = dadd(A.R[k], dmul(A.dt, dnorm3(A.vx[k], A.vy[k], A.vz[k])));
+            ex = fmax(ex, e);
+            A.rcf[k] = __double2float_ru(e);
+        }
+        double rmax = dsqrt(d2);
+        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        if (cap < rmax) rmax = cap;
+        const double rc = dadd(rmax, ex);
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rcrit[c] = rc;
+        float4 hi, lo;
+        split3(sx, sy, sz, hi, lo);
+        hi.w = static_cast<float>(rc);
+        lo.w = 0.f;
+        A.gh[c] = hi;
+        A.gl[c] = lo;
+    }
+}
+
 __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs A) {
     __shared__ ClimbShared sh_all[CLIMB_WARPS];
     if (aborted(A.ctl)) return;
@@ -586,52 +682,6 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs 
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
         int c = A.leaves[gw];
-        const int f = A.first[c], cnt = A.count[c];
-        double sx = 0, sy = 0, sz = 0;
-        for (int k0 = 0; k0 < cnt; k0 += 32) {
-            const int lim = min(32, cnt - k0);
-            __syncwarp();
-            if (lane < lim) {
-                S.a[lane] = A.x[f + k0 + lane];
-                S.b[lane] = A.y[f + k0 + lane];
-                S.c[lane] = A.z[f + k0 + lane];
-            }
-            __syncwarp();
-            if (lane == 0)
-                for (int k = 0; k < lim; k++) {
-                    sx = dadd(sx, S.a[k]);
-                    sy = dadd(sy, S.b[k]);
-                    sz = dadd(sz, S.c[k]);
-                }
-        }
-        if (lane == 0) {
-            const double w = static_cast<double>(cnt);
-            sx = ddiv(sx, w);
-            sy = ddiv(sy, w);
-            sz = ddiv(sz, w);
-        }
-        sx = __shfl_sync(0xffffffffu, sx, 0);
-        sy = __shfl_sync(0xffffffffu, sy, 0);
-        sz = __shfl_sync(0xffffffffu, sz, 0);
-        double rmax = 0, ex = 0;
-        for (int k = lane; k < cnt; k += 32) {
-            const int i = f + k;
-            rmax = fmax(rmax, dnorm3(dsub(A.x[i], sx), dsub(A.y[i], sy), dsub(A.z[i], sz)));
-            const double e = dadd(A.R[i], dmul(A.dt, dnorm3(A.vx[i], A.vy[i], A.vz[i])));
-            ex = fmax(ex, e);
-            A.rcf[i] = __double2float_ru(e);
-        }
-        rmax = warp_max(rmax);
-        ex = warp_max(ex);
-        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
-        if (cap < rmax) rmax = cap;
-        if (lane == 0) {
-            A.sx[c] = sx;
-            A.sy[c] = sy;
-            A.sz[c] = sz;
-            A.rmax[c] = rmax;
-            A.rcrit[c] = dadd(rmax, ex);
-        }
         while (true) {
             __threadfence();
             __syncwarp();
@@ -652,22 +702,8 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs 
                 S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
             }
             __syncwarp();
-            double px = 0, py = 0, pz = 0;
-            if (lane == 0) {
-                for (int ch = 0; ch < nch; ch++) {
-                    const double w = S.a[ch];
-                    px = dadd(px, dmul(w, S.b[ch]));
-                    py = dadd(py, dmul(w, S.c[ch]));
-                    pz = dadd(pz, dmul(w, S.d[ch]));
-                }
-                const double w = static_cast<double>(A.count[c]);
-                px = ddiv(px, w);
-                py = ddiv(py, w);
-                pz = ddiv(pz, w);
-            }
-            px = __shfl_sync(0xffffffffu, px, 0);
-            py = __shfl_sync(0xffffffffu, py, 0);
-            pz = __shfl_sync(0xffffffffu, pz, 0);
+            double Mdummy, px, py, pz;
+            parent_centre(S, nch, lane, false, static_cast<double>(A.count[c]), Mdummy, px, py, pz);
             double rm = 0, e2 = 0;
             if (lane < nch) {
                 rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
@@ -675,14 +711,21 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs 
             }
             rm = warp_max(rm);
             e2 = warp_max(e2);
-            const double pcap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py, pz);
+            const double pcap = corner_warp(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
             if (pcap < rm) rm = pcap;
             if (lane == 0) {
+                const double rc = dadd(rm, e2);
                 A.sx[c] = px;
                 A.sy[c] = py;
                 A.sz[c] = pz;
                 A.rmax[c] = rm;
-                A.rcrit[c] = dadd(rm, e2);
+                A.rcrit[c] = rc;
+                float4 hi, lo;
+                split3(px, py, pz, hi, lo);
+                hi.w = static_cast<float>(rc);
+                lo.w = 0.f;
+                A.gh[c] = hi;
+                A.gl[c] = lo;
             }
         }
     }
@@ -696,8 +739,10 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
+    A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
+    k_leaf_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
     k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A);
     NCORP_CUDA_CHECK(cudaGetLastError());
 }

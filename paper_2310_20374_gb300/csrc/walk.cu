@@ -30,6 +30,7 @@ struct WalkArgs {
     long long n_cs, pre, post;
     const int *count, *child0, *nchild;
     const double *sx, *sy, *sz, *rcrit;
+    const float4 *H, *Lo;      // FP32 centre hi + r_crit, centre lo
     int2 *front0, *front1;
     int *fcount;
     int front_cap;
@@ -114,18 +115,34 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
                     if (prod < A.pre) {
                         direct = true;
                     } else {
-                        const double dx = dsub(A.sx[cA], A.sx[cB]);
-                        const double dy = dsub(A.sy[cA], A.sy[cB]);
-                        const double dz = dsub(A.sz[cA], A.sz[cB]);
-                        const double d2 = dsq3(dx, dy, dz);
+                        // FP32 first: centres as hi + lo pairs give |s_A - s_B|^2 to ~1e-6
+                        // relative and r_crit is rounded once; outside a band of
+                        // +-2^-14 around the threshold the FP32 answer is the FP64 one,
+                        // inside it the exact FP64 test decides.
+                        const float4 ha = A.H[cA], hb = A.H[cB], la = A.Lo[cA], lb = A.Lo[cB];
+                        const float fx = (ha.x - hb.x) + (la.x - lb.x);
+                        const float fy = (ha.y - hb.y) + (la.y - lb.y);
+                        const float fz = (ha.z - hb.z) + (la.z - lb.z);
+                        const float d2f = fx * fx + fy * fy + fz * fz;
+                        const float tf = ha.w + hb.w, t2f = tf * tf;
                         const double rA = A.rcrit[cA], rB = A.rcrit[cB];
                         bool sep;
-                        if (A.gravity) {
-                            const double t = dadd(rA, rB);
-                            sep = dmul(t, t) <= d2;
+                        if (d2f > 1e-30f && d2f > t2f * (1.0f + 0x1p-14f)) {
+                            sep = true;
+                        } else if (d2f > 1e-30f && d2f < t2f * (1.0f - 0x1p-14f)) {
+                            sep = false;
                         } else {
-                            const double t = dmul(dadd(rA, rB), 1.0 + 0x1p-40);
-                            sep = dmul(t, t) < d2;
+                            const double dx = dsub(A.sx[cA], A.sx[cB]);
+                            const double dy = dsub(A.sy[cA], A.sy[cB]);
+                            const double dz = dsub(A.sz[cA], A.sz[cB]);
+                            const double d2 = dsq3(dx, dy, dz);
+                            if (A.gravity) {
+                                const double t = dadd(rA, rB);
+                                sep = dmul(t, t) <= d2;
+                            } else {
+                                const double t = dmul(dadd(rA, rB), 1.0 + 0x1p-40);
+                                sep = dmul(t, t) < d2;
+                            }
                         }
                         if (sep) {
                             if (A.gravity) emit_m2l = 1;
@@ -234,6 +251,8 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     A.sy = gravity ? C.sy : C.by;
     A.sz = gravity ? C.sz : C.bz;
     A.rcrit = gravity ? C.rcrit : C.bcrit;
+    A.H = gravity ? C.gh : C.bh;
+    A.Lo = gravity ? C.gl : C.bl;
     A.front0 = W.front[0]; A.front1 = W.front[1]; A.fcount = W.front_count; A.front_cap = W.front_cap;
     A.m2l = W.m2l; A.m2l_cap = W.m2l_cap;
     A.p2p = W.p2p; A.p2p_cap = W.p2p_cap;

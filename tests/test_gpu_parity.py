@@ -324,9 +324,10 @@ def _oracle_multi(P, pos, mass):
 
 @pytest.mark.parametrize("p,prec,tol", [(4, ncorp.NCORP_FP64, 1e-12), (6, ncorp.NCORP_FP64, 1e-12),
                                         (6, ncorp.NCORP_MIXED, 3e-5)])
-def test_multipoles_and_m2l_sums_match_oracle(p, prec, tol):
-    """P2M + M2M (Eq. multipole_moment, App. C) and the M2L sums of each cell
-    (Eq. phi_expanded) against the oracle's full-tensor versions."""
+def test_multipoles_and_local_expansions_match_oracle(p, prec, tol):
+    """P2M + M2M (Eq. multipole_moment, App. C) and the complete local expansion
+    of each cell (M2L of Eq. phi_expanded + descent of Eq. shifting) against the
+    oracle's full-tensor versions."""
     n, s = 4000, 24
     grav = (64, 8, 64)
     d = diskgen.make_disk(n, 81 + p)
