@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 falcON step: particle-steps/s on the paper-shaped disk.
+
+Workload (one "step" = one full SBAB1 step of Sect. 4.1 through ncorp_step:
+half kick, tree collision search, drift, key sort + octree build, climb with
+P2M/M2M, dual-tree walk, M2L, descent, L2P + near field + external forces,
+half kick): one synthetic moonlet disk of N = 1e5 (seed 2, the recipe of
+paper_2310_20374_gb300/diskgen.py), falcON p = 6, theta_min = 0.5,
+dt = 1e-3, mixed precision (FP32 expansions and near field, FP64 state,
+geometry, keys and collision test).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ncorp,reference}]
+
+N > 1 runs under torchrun: every rank integrates its own replica disk (the
+step has no exchange between disks), the timed region is bracketed by
+barriers and the slowest rank's time is used.  --impl reference times the
+CPU oracle (oracle/, plain C FP64) on the host, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s, falcON p=6 gravity+collisions; p50/p99 step latency mixed-N"
+UNIT = "particle-steps/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070   # SMs x FP32 lanes x 2 (FMA) x max SM clock (GHz) / 1000 -> TFLOP/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ncorp", choices=["ncorp", "reference"])
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--p", type=int, default=6)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_config(a):
+    return {"workload": f"1 disk x {a.n} moonlets per GPU (seed {a.seed}+rank), falcON p={a.p} theta_min={a.theta}, "
+                        f"SBAB1 step dt={a.dt} with tree collision search, {a.precision} precision",
+            "n_per_gpu": a.n, "p": a.p, "theta_min": a.theta, "dt": a.dt, "leaf_size": 64 if a.p >= 6 else 32,
+            "gravity_thresholds": [256, 256, 512] if a.p >= 6 else [64, 8, 64], "collision_thresholds": [12, 0, 16],
+            "precision": a.precision, "l2": "flushed by a 256 MiB device write before every timed step",
+            "parallelism": "replicas (one independent disk per GPU)"}
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2310_20374_gb300 import diskgen, ncorp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+
+    cfgd = workload_config(a)
+    d = diskgen.make_disk(a.n, a.seed + rank)
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED if a.precision == "mixed" else ncorp.NCORP_FP64
+    cfg.leaf_size = cfgd["leaf_size"]
+    cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = cfgd["gravity_thresholds"]
+    cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = cfgd["collision_thresholds"]
+    ctx = ncorp.ncorp_init(cfg, a.n, local, stream.cuda_stream)
+    pos = torch.tensor(d["pos"], device="cuda")
+    vel = torch.tensor(d["vel"], device="cuda")
+    m = torch.tensor(d["mass"], device="cuda")
+    R = torch.tensor(d["radius"], device="cuda")
+    pairs = torch.empty((1 << 16, 2), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        ncorp.ncorp_step(ctx, pos, vel, m, R, a.n, a.p, a.theta, a.dt)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    ncorp.ncorp_profile(ctx, True)
+    sampler = ClockSampler(physical_gpu_index(local))
+    barrier()
+    total_ms, launches, found = 0.0, 0, 0
+    stage = {}
+    interactions, m2l_dir, step_ms = 0, 0, []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        step_ms.append(ms)
+        total_ms += ms
+        st = ncorp.ncorp_stats(ctx)
+        launches += st["launches"]
+        found += st["col_found"]
+        interactions += st["p2p_interactions"]
+        m2l_dir += st["m2l_directed"]
+        for k, v in ncorp.ncorp_stage_times(ctx).items():
+            stage[k] = stage.get(k, 0.0) + v
+    barrier()
+    clocks = sampler.stop()
+    ncorp.ncorp_profile(ctx, False)
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = a.n * a.steps * world / (t_max * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers: every step
+    # copies the state in (positions, velocities, masses, radii), runs the step
+    # from it and copies the new state and the colliding pairs out.
+    hp = torch.tensor(d["pos"]).pin_memory()
+    hv = torch.tensor(d["vel"]).pin_memory()
+    hm = torch.tensor(d["mass"]).pin_memory()
+    hR = torch.tensor(d["radius"]).pin_memory()
+    hpairs = torch.empty((1 << 16, 2), dtype=torch.int64).pin_memory()
+    e2e_steps = max(3, min(a.steps, 10))
+    ncorp.ncorp_reset(ctx)
+    ncorp.ncorp_step(ctx, hp, hv, hm, hR, a.n, a.p, a.theta, a.dt)
+    barrier()
+    t0 = time.perf_counter()
+    npairs = 0
+    for _ in range(e2e_steps):
+        ncorp.ncorp_reset(ctx)
+        ncorp.ncorp_step(ctx, hp, hv, hm, hR, a.n, a.p, a.theta, a.dt)
+        npairs += ncorp.ncorp_collisions(ctx, hpairs, hpairs.shape[0])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": a.n * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": a.n * (24 + 24 + 8 + 8),
+           "d2h_bytes_per_step": a.n * (24 + 24) + 16 * (npairs // e2e_steps),
+           "note": "state uploaded from pinned host memory every step (so the step also recomputes the "
+                   "acceleration of the uploaded state), new state and pairs read back"}
+    ncorp.ncorp_free(ctx)
+
+    # ---- roofline of the dominant kernel (L2P + near field: FP32 ALU bound)
+    eval_ms = stage.get("eval", 0.0) / a.steps
+    nterms = a.p * (a.p + 1) * (a.p + 2) // 6            # multi-indices |beta| <= p-1
+    flops_eval = 40.0 * interactions / a.steps + a.n * (6.0 * nterms + 3 * (a.p - 1))
+    achieved = flops_eval / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_eval (L2P + near-field direct sum + external forces)",
+                "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "flops_per_launch": flops_eval, "avg_launch_ms": round(eval_ms, 4),
+                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4),
+           "p50_step_ms": round(float(np.percentile(step_ms, 50)), 4),
+           "p99_step_ms": round(float(np.percentile(step_ms, 99)), 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
+           "data": "synthetic (seeded moonlet disk shaped like the paper's)", "config": cfgd,
+           "stage_ms_per_step": {k: round(v / a.steps, 4) for k, v in stage.items()},
+           "colliding_pairs_per_step": found / a.steps, "gpu_launches": launches,
+           "clocks": clocks, "e2e": e2e, "roofline": roofline}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, cfgd, d)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- oracle
+def oracle_params(cfgd, a):
+    import oracle
+    return oracle.params(p=a.p, theta=a.theta, leaf_size=cfgd["leaf_size"],
+                         gravity_thresholds=tuple(cfgd["gravity_thresholds"]),
+                         collision_thresholds=tuple(cfgd["collision_thresholds"]))
+
+
+def time_oracle_steps(a, cfgd, d, nsteps):
+    """Wall time of nsteps oracle SBAB1 steps (acceleration of the start state computed untimed)."""
+    import oracle
+    P = oracle_params(cfgd, a)
+    acc0, _ = oracle.falcon_accel(P, d["pos"], d["mass"])
+    acc0 = acc0 + oracle.external_accel(P, d["pos"])
+    t0 = time.perf_counter()
+    oracle.kdk(P, d["pos"], d["vel"], d["mass"], d["radius"], a.dt, nsteps, acc0=acc0)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(a, cfgd, d):
+    import oracle
+    oracle.build()
+    secs = time_oracle_steps(a, cfgd, d, 1)
+    return {"value": round(a.n / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 SBAB1 step of the same {a.n}-moonlet disk (falcON p={a.p} + tree collision search), "
+                      f"plain C FP64 oracle, single thread; acceleration of the start state computed outside "
+                      f"the timing", "seconds": round(secs, 3)}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2310_20374_gb300 import diskgen
+    import oracle
+    oracle.build()
+    cfgd = workload_config(a)
+    # bounded sample: a disk small enough that warmup + steps end within ~2 minutes
+    per_particle_s = 6e-5
+    n = int(min(a.n, max(2000, 120.0 / (per_particle_s * (a.steps + max(a.warmup, 3) + 1)))))
+    d = diskgen.make_disk(n, a.seed)
+    import copy
+    b = copy.copy(a)
+    b.n = n
+    time_oracle_steps(b, cfgd, d, max(a.warmup, 3))
+    secs = time_oracle_steps(b, cfgd, d, a.steps)
+    value = n * a.steps / secs
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": a.steps, "warmup": max(a.warmup, 3), "ms_per_step": round(1e3 * secs / a.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded moonlet disk shaped like the paper's)", "config": cfgd,
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{a.steps} SBAB1 steps of a {n}-moonlet disk from the same generator "
+                                      f"(the workload's disk scaled to keep the run within minutes)"},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

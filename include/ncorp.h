@@ -141,8 +141,26 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_WALK_ITERS  11   /* frontier iterations of the last walk */
 #define NCORP_STAT_M2L_DIRECTED 12  /* directed M2L entries evaluated */
 #define NCORP_STAT_P2P_DIRECTED 13  /* directed leaf-source entries evaluated */
+#define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
 #define NCORP_NSTATS           16
 int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
+
+/* Stage timers.  With profiling on, every call records CUDA events on the
+ * context's stream around its stages and ncorp_stage_times() returns the
+ * device milliseconds each stage took in the last call (summed when a stage
+ * runs more than once).  Off by default; on costs a few event records. */
+#define NCORP_STAGE_SORT     0   /* bounding box, keys, radix sort, gather */
+#define NCORP_STAGE_BUILD    1   /* octree build, leaf list */
+#define NCORP_STAGE_CLIMB    2   /* gravity climb: geometry, P2M, M2M, theta(M), r_crit */
+#define NCORP_STAGE_WALK     3   /* gravity walk and per-target lists */
+#define NCORP_STAGE_M2L      4
+#define NCORP_STAGE_DESCEND  5   /* L2L from the root */
+#define NCORP_STAGE_EVAL     6   /* L2P, near field, external forces */
+#define NCORP_STAGE_COLLIDE  7   /* collision climb, walk and pair test */
+#define NCORP_STAGE_KDK      8   /* kicks, drift, host/device copies of the state */
+#define NCORP_NSTAGES        9
+int ncorp_profile(ncorp_ctx *ctx, int enable);
+int ncorp_stage_times(ncorp_ctx *ctx, double *ms, int n);
 
 /* Diagnostic export of the tree of the last ncorp_accel/ncorp_collide/ncorp_step
  * (level-major cells, Hilbert order within a level), for parity checks.

@@ -141,7 +141,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.self_cap = c->wl.self_cap;
     A.p2p_cap = c->wl.p2p_cap;
     A.ctl = c->ctl;
-    k_collide<<<4 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A);
+    k_collide<<<4 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -161,7 +161,7 @@ void launch_sort_pairs(ncorp_ctx *c, int count) {
 
 void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count) {
     if (count <= 0) return;
-    k_unpack_pairs<<<grid_for(count, 256, 4 * c->num_sms), 256, 0, c->stream>>>(packed, out, count);
+    k_unpack_pairs<<<grid_for(count, 256, 4 * c->num_sms), 256, 0, c->stream>>>(packed, out, count); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -111,6 +111,11 @@ struct ncorp_ctx {
     int64_t stats[NCORP_NSTATS] = {0};
     int tree_kind = 0;               // 1: gravity geometry valid, 2: collision geometry valid (bit mask)
     int grav_p = 0;                  // p of the last gravity evaluation (0: none)
+    int launches = 0;                // kernels launched by the current call
+    bool profile = false;
+    cudaEvent_t ev[NCORP_NSTAGES][8][2] = {};   // up to 8 intervals per stage per call
+    int ev_used[NCORP_NSTAGES] = {0};
+    double stage_ms[NCORP_NSTAGES] = {0};
     bool grav_mixed = false;
 };
 
@@ -138,6 +143,7 @@ void launch_directed_lists(ncorp_ctx *c);
 
 // ---- m2l.cu / eval.cu ----
 void launch_m2l(ncorp_ctx *c, int p, bool mixed);
+void launch_descend(ncorp_ctx *c, int p, bool mixed);
 struct ExtForce {
     double GMc;            // G * central mass
     double star_k;         // G M_star / r_star^3 (0: off)

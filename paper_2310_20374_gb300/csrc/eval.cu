@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS, 4) k_eval(EvalArgs A) {
 }
 
 template <int P, typename real>
-static void eval_t(ncorp_ctx *c, const EvalArgs &A, DescendArgs D) {
+static void descend_t(ncorp_ctx *c, DescendArgs D) {
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, reinterpret_cast<const void *>(k_descend<P, real>), 256, 0));
@@ -379,7 +379,36 @@ static void eval_t(ncorp_ctx *c, const EvalArgs &A, DescendArgs D) {
     void *args[] = {&D};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_descend<P, real>),
                                                  dim3(per_sm * c->num_sms), dim3(256), args, 0, c->stream));
+    c->launches++;
+}
+
+template <int P, typename real>
+static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
     k_eval<P, real><<<8 * c->num_sms, 32 * EVAL_WARPS, 0, c->stream>>>(A);
+    c->launches++;
+}
+
+void launch_descend(ncorp_ctx *c, int p, bool mixed) {
+    Cells &C = c->cells;
+    DescendArgs D;
+    D.parent = C.parent; D.shift = C.shift; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
+    D.Ch = C.Ch; D.ctl = c->ctl;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+#define NCORP_DESC_CASE(PP)                      \
+    case PP:                                     \
+        if (mixed) descend_t<PP, float>(c, D);   \
+        else descend_t<PP, double>(c, D);        \
+        break;
+    switch (p) {
+        NCORP_DESC_CASE(1)
+        NCORP_DESC_CASE(2)
+        NCORP_DESC_CASE(3)
+        NCORP_DESC_CASE(4)
+        NCORP_DESC_CASE(5)
+        NCORP_DESC_CASE(6)
+        default: break;
+    }
+#undef NCORP_DESC_CASE
 }
 
 void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual) {
@@ -401,14 +430,10 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     A.work = c->work_counter;
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
-    DescendArgs D;
-    D.parent = C.parent; D.shift = C.shift; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
-    D.Ch = C.Ch; D.ctl = c->ctl;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
 #define NCORP_EVAL_CASE(PP)                      \
     case PP:                                     \
-        if (mixed) eval_t<PP, float>(c, A, D);   \
-        else eval_t<PP, double>(c, A, D);        \
+        if (mixed) eval_t<PP, float>(c, A);      \
+        else eval_t<PP, double>(c, A);           \
         break;
     switch (p) {
         NCORP_EVAL_CASE(1)

@@ -54,30 +54,30 @@ __global__ void k_drift(const double *__restrict__ x, const double *__restrict__
 static int eg(ncorp_ctx *c, int n) { return grid_for(n, 256, 16 * c->num_sms); }
 
 void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n) {
-    k_aos_to_soa<<<eg(c, n), 256, 0, c->stream>>>(aos, x, y, z, n);
+    k_aos_to_soa<<<eg(c, n), 256, 0, c->stream>>>(aos, x, y, z, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm,
                         double *aos, int n) {
-    k_scatter_aos<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, perm, aos, n);
+    k_scatter_aos<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, perm, aos, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 void launch_scatter_scalar(ncorp_ctx *c, const double *v, const int *perm, double *out, int n) {
-    k_scatter_scalar<<<eg(c, n), 256, 0, c->stream>>>(v, perm, out, n);
+    k_scatter_scalar<<<eg(c, n), 256, 0, c->stream>>>(v, perm, out, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 void launch_kick(ncorp_ctx *c, const double *vx, const double *vy, const double *vz, const double *ax,
                  const double *ay, const double *az, double h, double *ox, double *oy, double *oz, int n) {
-    k_kick<<<eg(c, n), 256, 0, c->stream>>>(vx, vy, vz, ax, ay, az, h, ox, oy, oz, n);
+    k_kick<<<eg(c, n), 256, 0, c->stream>>>(vx, vy, vz, ax, ay, az, h, ox, oy, oz, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 void launch_drift(ncorp_ctx *c, const double *x, const double *y, const double *z, const double *vx,
                   const double *vy, const double *vz, double dt, double *ox, double *oy, double *oz, int n) {
-    k_drift<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, vx, vy, vz, dt, ox, oy, oz, n);
+    k_drift<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, vx, vy, vz, dt, ox, oy, oz, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

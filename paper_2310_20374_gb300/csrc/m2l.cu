@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
 
 template <int P, typename real>
 static void m2l_t(ncorp_ctx *c, const M2LArgs &A) {
-    k_m2l<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A);
+    k_m2l<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
 }
 
 void launch_m2l(ncorp_ctx *c, int p, bool mixed) {

@@ -264,22 +264,67 @@ void reset_ctl(ncorp_ctx *c) {
     NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_snap, 0, sizeof(int), c->stream));
 }
 
+// ---- stage timers (CUDA events on the context's stream, only when profiling)
+void stage_begin(ncorp_ctx *c, int st) {
+    if (!c->profile || c->ev_used[st] >= 8) return;
+    cudaEvent_t &e = c->ev[st][c->ev_used[st]][0];
+    if (!e) NCORP_CUDA_CHECK(cudaEventCreate(&e));
+    NCORP_CUDA_CHECK(cudaEventRecord(e, c->stream));
+}
+
+void stage_end(ncorp_ctx *c, int st) {
+    if (!c->profile || c->ev_used[st] >= 8) return;
+    cudaEvent_t &e = c->ev[st][c->ev_used[st]][1];
+    if (!e) NCORP_CUDA_CHECK(cudaEventCreate(&e));
+    NCORP_CUDA_CHECK(cudaEventRecord(e, c->stream));
+    c->ev_used[st]++;
+}
+
+struct Stage {
+    ncorp_ctx *c;
+    int st;
+    Stage(ncorp_ctx *c_, int st_) : c(c_), st(st_) { stage_begin(c, st); }
+    ~Stage() { stage_end(c, st); }
+};
+
+void begin_call(ncorp_ctx *c) {
+    c->launches = 0;
+    for (int i = 0; i < NCORP_NSTAGES; i++) {
+        c->ev_used[i] = 0;
+        c->stage_ms[i] = 0.0;
+    }
+}
+
 int finish(ncorp_ctx *c) {
     NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
     NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->profile)
+        for (int i = 0; i < NCORP_NSTAGES; i++) {
+            double sum = 0;
+            for (int k = 0; k < c->ev_used[i]; k++) {
+                float ms = 0;
+                NCORP_CUDA_CHECK(cudaEventElapsedTime(&ms, c->ev[i][k][0], c->ev[i][k][1]));
+                sum += ms;
+            }
+            c->stage_ms[i] = sum;
+        }
     return c->ctl_h->err;
 }
 
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
                 int n) {
-    launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
-    radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
-    ParticleSet view = sr;
-    view.x = sx.x; view.y = sx.y; view.z = sx.z;
-    view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
-    view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
-    launch_gather(c, view, view, dst, n, c->idx, c->cfg.G);
+    {
+        Stage st(c, NCORP_STAGE_SORT);
+        launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
+        radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
+        ParticleSet view = sr;
+        view.x = sx.x; view.y = sx.y; view.z = sx.z;
+        view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
+        view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
+        launch_gather(c, view, view, dst, n, c->idx, c->cfg.G);
+    }
+    Stage st(c, NCORP_STAGE_BUILD);
     launch_build(c, dst, n, c->s);
 }
 
@@ -287,14 +332,15 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
     const bool mixed = c->cfg.precision == NCORP_MIXED;
     c->grav_p = p;
     c->grav_mixed = mixed;
-    launch_climb_gravity(c, S, p, mixed, c->cfg.G, theta);
-    launch_walk(c, true);
-    launch_directed_lists(c);
-    launch_m2l(c, p, mixed);
-    launch_eval(c, S, p, mixed, c->cfg.G, external(c, t), want_mutual);
+    { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_gravity(c, S, p, mixed, c->cfg.G, theta); }
+    { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true); launch_directed_lists(c); }
+    { Stage st(c, NCORP_STAGE_M2L); launch_m2l(c, p, mixed); }
+    { Stage st(c, NCORP_STAGE_DESCEND); launch_descend(c, p, mixed); }
+    { Stage st(c, NCORP_STAGE_EVAL); launch_eval(c, S, p, mixed, c->cfg.G, external(c, t), want_mutual); }
 }
 
 void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
+    Stage st(c, NCORP_STAGE_COLLIDE);
     launch_climb_collision(c, S, vx, vy, vz, dt);
     launch_walk(c, false);
     launch_collide(c, S, vx, vy, vz, dt);
@@ -302,6 +348,7 @@ void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const doub
 
 void record_stats(ncorp_ctx *c, bool grav) {
     const Ctrl &h = *c->ctl_h;
+    c->stats[NCORP_STAT_LAUNCHES] = c->launches;
     c->stats[NCORP_STAT_CELLS] = h.n_cells;
     c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
     c->stats[NCORP_STAT_DEPTH] = h.max_level;
@@ -412,6 +459,7 @@ int ncorp_accel(ncorp_ctx *c, const double *positions, const double *masses, int
     if (st) return st;
     if (!positions || !masses || !acc) return fail(c, NCORP_EINVAL, "null pointer");
     NCORP_API_BODY(c, {
+        begin_call(c);
         const int n = static_cast<int>(n64);
         ensure_particles(c, n);
         choose_parameters(c, p);
@@ -454,6 +502,7 @@ int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocitie
     if (!positions || !velocities || !radii) return fail(c, NCORP_EINVAL, "null pointer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NCORP_EINVAL, "dt must be > 0");
     NCORP_API_BODY(c, {
+        begin_call(c);
         const int n = static_cast<int>(n64);
         ensure_particles(c, n);
         if (c->s == 0) choose_parameters(c, 6);
@@ -494,6 +543,7 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
     if (!positions || !velocities || !masses || !radii) return fail(c, NCORP_EINVAL, "null pointer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NCORP_EINVAL, "dt must be > 0");
     NCORP_API_BODY(c, {
+        begin_call(c);
         const int n = static_cast<int>(n64);
         const bool resident = c->have_state && c->tree_valid && c->n == n && c->last_pos == positions &&
                               c->last_vel == velocities && c->last_m == masses && c->last_R == radii &&
@@ -507,6 +557,7 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
             ensure_tree_capacity(c, n);
             reset_ctl(c);
             if (!have) {   // read the caller's state (caller order)
+                Stage st(c, NCORP_STAGE_KDK);
                 ParticleSet &A = c->A;
                 upload_vec(c, positions, A.x, A.y, A.z, n);
                 upload_vec(c, velocities, A.vx, A.vy, A.vz, n);
@@ -521,14 +572,17 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                 gravity(c, c->A, p, theta, c->time, false);
             }
             ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
-            launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n);
+            { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n); }
             if (c->cfg.collisions) collisions(c, A, B.vx, B.vy, B.vz, dt);
-            launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n);
+            { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
             build_tree(c, B, B, A, Cn, n);
             gravity(c, Cn, p, theta, c->time + dt, false);
-            launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n);
-            download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
-            download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
+            {
+                Stage st(c, NCORP_STAGE_KDK);
+                launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n);
+                download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
+                download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
+            }
             int err = finish(c);
             if (!finite_ok(c)) {
                 c->have_state = false;
@@ -728,6 +782,18 @@ int ncorp_expansions(ncorp_ctx *c, double *mult, double *local, double *rho, int
     })
 }
 
+int ncorp_profile(ncorp_ctx *c, int enable) {
+    if (!c) return NCORP_EINVAL;
+    c->profile = enable != 0;
+    return NCORP_OK;
+}
+
+int ncorp_stage_times(ncorp_ctx *c, double *ms, int n) {
+    if (!c || !ms || n < 0) return NCORP_EINVAL;
+    for (int i = 0; i < n && i < NCORP_NSTAGES; i++) ms[i] = c->stage_ms[i];
+    return NCORP_OK;
+}
+
 void ncorp_free(ncorp_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -750,6 +816,10 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
     dfree(c->ctl);
     dfree(c->work_counter);
+    for (int i = 0; i < NCORP_NSTAGES; i++)
+        for (int k = 0; k < 8; k++)
+            for (int e = 0; e < 2; e++)
+                if (c->ev[i][k][e]) cudaEventDestroy(c->ev[i][k][e]);
     if (c->ctl_h) cudaFreeHost(c->ctl_h);
     delete c;
 }

@@ -151,9 +151,9 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
     NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[0], 0xff, 3 * sizeof(unsigned long long), c->stream));
     NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[3], 0x00, 3 * sizeof(unsigned long long), c->stream));
     int g = grid_for(n, 256, 4 * c->num_sms);
-    k_bbox<<<g, 256, 0, c->stream>>>(x, y, z, n, c->ctl);
+    k_bbox<<<g, 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
-    k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz);
+    k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -259,9 +259,9 @@ void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
         c->scan_tmp_cap = nb + 1024;
         NCORP_CUDA_CHECK(cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_cap));
     }
-    k_scan_reduce<<<nb, SCAN_T, 0, c->stream>>>(in, n, c->scan_tmp);
-    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_tmp, nb);
-    k_scan_apply<<<nb, SCAN_T, 0, c->stream>>>(in, out, n, c->scan_tmp, nb, total);
+    k_scan_reduce<<<nb, SCAN_T, 0, c->stream>>>(in, n, c->scan_tmp); c->launches++;
+    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_tmp, nb); c->launches++;
+    k_scan_apply<<<nb, SCAN_T, 0, c->stream>>>(in, out, n, c->scan_tmp, nb, total); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -355,9 +355,9 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
     uint32_t *vi = vals, *vo = vals_alt;
     for (int ps = 0; ps < passes; ps++) {
         int shift = 8 * ps;
-        k_rs_hist<<<ntiles, RS_T, 0, c->stream>>>(ki, n, shift, c->tile_hist, ntiles);
+        k_rs_hist<<<ntiles, RS_T, 0, c->stream>>>(ki, n, shift, c->tile_hist, ntiles); c->launches++;
         scan_exclusive(c, c->tile_hist, c->tile_hist, need, nullptr);
-        k_rs_scatter<<<ntiles, RS_T, 0, c->stream>>>(ki, vi, ko, vo, n, shift, c->tile_hist, ntiles);
+        k_rs_scatter<<<ntiles, RS_T, 0, c->stream>>>(ki, vi, ko, vo, n, shift, c->tile_hist, ntiles); c->launches++;
         NCORP_CUDA_CHECK(cudaGetLastError());
         std::swap(ki, ko);
         std::swap(vi, vo);
@@ -369,7 +369,7 @@ __global__ void k_iota(uint32_t *idx, int n) {
 }
 
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n) {
-    k_iota<<<grid_for(n, 256, 8 * c->num_sms), 256, 0, c->stream>>>(idx, n);
+    k_iota<<<grid_for(n, 256, 8 * c->num_sms), 256, 0, c->stream>>>(idx, n); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -429,7 +429,7 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     g.idx = idx;
     g.G = G;
     g.n = n;
-    k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g);
+    k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -197,15 +197,17 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
     A.level = C.level; A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
     A.parent = C.parent; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.bounds = C.bounds; A.blocksum = C.blocksum; A.ctl = c->ctl;
-    k_build_init<<<1, 1, 0, c->stream>>>(A);
+    k_build_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     const int block = 256;
     int grid = coop_grid(c, reinterpret_cast<const void *>(k_build), block, 0);
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_build), dim3(grid), dim3(block),
                                                  args, 0, c->stream));
+    c->launches++;
     k_collect_leaves<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(C.nchild, c->ctl, C.cap, C.leaves,
                                                                                  &c->ctl->n_leaves);
+    c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -592,7 +594,7 @@ __global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__
 
 template <int P, typename real>
 static void climb_gravity_t(ncorp_ctx *c, const ClimbArgs &A) {
-    k_climb_gravity<P, real><<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A);
+    k_climb_gravity<P, real><<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
 }
 
 void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
@@ -605,7 +607,7 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
     A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_leaf_gravity<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
+    k_leaf_gravity<<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
 #define NCORP_CLIMB_CASE(PP)                                             \
     case PP:                                                             \
         if (mixed) climb_gravity_t<PP, float>(c, A);                     \
@@ -622,7 +624,7 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     }
 #undef NCORP_CLIMB_CASE
     NCORP_CUDA_CHECK(cudaGetLastError());
-    k_rcrit<<<grid_for(C.cap, 64, 16 * c->num_sms), 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta);
+    k_rcrit<<<grid_for(C.cap, 64, 16 * c->num_sms), 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -742,8 +744,8 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_leaf_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A);
-    k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A);
+    k_leaf_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -259,7 +259,7 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     A.self = W.self; A.self_cap = W.self_cap;
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(W.front_count, 0, sizeof(int) * (WALK_MAX_ITERS + 1), c->stream));
-    k_walk_init<<<1, 1, 0, c->stream>>>(A);
+    k_walk_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_walk),
@@ -270,6 +270,7 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
                                                  0, c->stream));
+    c->launches++;
 }
 
 // ---------------------------------------------------------------------------
@@ -347,7 +348,7 @@ void launch_directed_lists(ncorp_ctx *c) {
     NCORP_CUDA_CHECK(cudaMemsetAsync(W.p2p_off, 0, sizeof(int) * n, c->stream));
     const int grid = 4 * c->num_sms;
     k_count_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cnt, W.p2p_off, W.m2l_cap, W.p2p_cap,
-                                               W.self_cap);
+                                               W.self_cap); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     scan_exclusive(c, W.cnt, W.offs, n, nullptr);
     scan_exclusive(c, W.p2p_off, W.p2p_off, n, nullptr);
@@ -355,7 +356,7 @@ void launch_directed_lists(ncorp_ctx *c) {
     NCORP_CUDA_CHECK(cudaMemcpyAsync(W.cnt, W.p2p_off, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream));
     k_scatter_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cursor, W.cnt, W.m2l_dir,
                                                  W.m2l_dir_cap, W.p2p_src, W.p2p_dir_cap, W.m2l_cap, W.p2p_cap,
-                                                 W.self_cap);
+                                                 W.self_cap); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

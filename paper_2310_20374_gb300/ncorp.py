@@ -18,7 +18,8 @@ from . import build as _build
 NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEOUT, NCORP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 NCORP_FP64, NCORP_MIXED = 0, 1
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
-              "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "_14", "_15"]
+              "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "_15"]
+STAGE_NAMES = ["sort", "build", "climb", "walk", "m2l", "descend", "eval", "collide", "kdk"]
 HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
 
 
@@ -67,12 +68,14 @@ def load(path: str | None = None):
     L.ncorp_stats.argtypes = [vp, C.POINTER(i64), ip]
     L.ncorp_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
     L.ncorp_expansions.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(ip)]
+    L.ncorp_profile.argtypes = [vp, ip]
+    L.ncorp_stage_times.argtypes = [vp, C.POINTER(dbl), ip]
     L.ncorp_free.argtypes = [vp]
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
-                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions"):
+                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -186,6 +189,16 @@ def num_m(p):
 
 def num_c(p):
     return (p + 1) * (p + 2) * (p + 3) // 6 - 1
+
+
+def ncorp_profile(ctx, enable=True):
+    return _check(ctx, load().ncorp_profile(ctx, int(bool(enable))))
+
+
+def ncorp_stage_times(ctx) -> dict:
+    arr = (C.c_double * len(STAGE_NAMES))()
+    _check(ctx, load().ncorp_stage_times(ctx, arr, len(STAGE_NAMES)))
+    return dict(zip(STAGE_NAMES, (float(v) for v in arr)))
 
 
 def ncorp_free(ctx):
