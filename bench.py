@@ -35,13 +35,13 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s, falcON p=6 gravity+collisions; p50/p99 step latency mixed-N"
 UNIT = "particle-steps/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070   # SMs x FP32 lanes x 2 (FMA) x max SM clock (GHz) / 1000 -> TFLOP/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 (FMA) x max SM clock (GHz) -> TFLOP/s
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ncorp", choices=["ncorp", "reference"])
     ap.add_argument("--n", type=int, default=100_000)
@@ -82,7 +82,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -169,6 +169,7 @@ def run_gpu(a):
     sampler = ClockSampler(physical_gpu_index(local))
     barrier()
     total_ms, launches, found = 0.0, 0, 0
+    last_stats = {}
     stage = {}
     interactions, m2l_dir, step_ms = 0, 0, []
     for _ in range(a.steps):
@@ -185,6 +186,7 @@ def run_gpu(a):
         total_ms += ms
         st = ncorp.ncorp_stats(ctx)
         launches += st["launches"]
+        last_stats = st
         found += st["col_found"]
         interactions += st["p2p_interactions"]
         m2l_dir += st["m2l_directed"]
@@ -231,16 +233,26 @@ def run_gpu(a):
                    "acceleration of the uploaded state), new state and pairs read back"}
     ncorp.ncorp_free(ctx)
 
-    # ---- roofline of the dominant kernel (L2P + near field: FP32 ALU bound)
+    # ---- roofline of the dominant kernel (L2P + near field: FP32 ALU bound).
+    # Algorithmic FLOPs per step: 24 per directed moonlet pair of the near field
+    # (9 adds for the double-float separation, 3 mul + 2 add for r^2, rsqrt, 3 mul
+    # for mu/r^3, 3 FMA into the sums; every unordered pair counted by the walk
+    # is evaluated in both directions) plus, per moonlet, the L2P gradient of a
+    # p-order expansion: 3 FMA (6 FLOPs) per multi-index of order < p, plus the
+    # p-1 powers of each coordinate offset.
     eval_ms = stage.get("eval", 0.0) / a.steps
     nterms = a.p * (a.p + 1) * (a.p + 2) // 6            # multi-indices |beta| <= p-1
-    flops_eval = 40.0 * interactions / a.steps + a.n * (6.0 * nterms + 3 * (a.p - 1))
+    directed = 2.0 * interactions / a.steps
+    flops_eval = 24.0 * directed + a.n * (6.0 * nterms + 3 * (a.p - 1))
     achieved = flops_eval / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_eval (L2P + near-field direct sum + external forces)",
                 "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                "flops_per_launch": flops_eval, "avg_launch_ms": round(eval_ms, 4),
-                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+                "flops_per_launch": flops_eval, "directed_pairs_per_launch": directed,
+                "avg_launch_ms": round(eval_ms, 4),
+                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 FP32 lanes x 2 FLOPs x 2.07 GHz (not measured)"}
+    last = {k: last_stats[k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self",
+                                      "p2p_interactions", "col_pairs", "col_tests")}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4),
@@ -250,7 +262,7 @@ def run_gpu(a):
            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
            "data": "synthetic (seeded moonlet disk shaped like the paper's)", "config": cfgd,
            "stage_ms_per_step": {k: round(v / a.steps, 4) for k, v in stage.items()},
-           "colliding_pairs_per_step": found / a.steps, "gpu_launches": launches,
+           "colliding_pairs_per_step": found / a.steps, "tree_stats_last_step": last, "gpu_launches": launches,
            "clocks": clocks, "e2e": e2e, "roofline": roofline}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, cfgd, d)

@@ -38,7 +38,8 @@ struct Cells {
     float4 *bh = nullptr;     // collision centre hi (xyz), collision r_crit (w)
     float4 *bl = nullptr;     // collision centre lo (xyz)
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
-    void *Ch = nullptr;       // [cap][num_c(p)] local coefficients (float or double)
+    void *Ch = nullptr;       // [cap][num_c(p)] local coefficients of the cell's own M2L (float or double)
+    void *Cf = nullptr;       // [cap][num_c(p)] complete local expansion after the descent
     int *leaves = nullptr;    // leaf cell ids
     int *bounds = nullptr;    // [cap][9] scratch of the build
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels

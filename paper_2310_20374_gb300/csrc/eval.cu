@@ -1,21 +1,15 @@
-// eval.cu -- tree descent and evaluation at the moonlets: L2L from the root
-// to each leaf and L2P (Eq. shifting), the direct ("brute force") gravity of
-// the leaf's near-field list, and the central-body / distant-star forces
-// (App. B.1, B.3).
+// eval.cu -- tree descent and evaluation at the moonlets: the complete local
+// expansion of every cell (Sect. 3.4.3, Eq. shifting), L2P at the moonlets,
+// the direct ("brute force") gravity of each leaf's near-field list, and the
+// central-body / distant-star forces (App. B.1, B.3).
 //
-// One warp per leaf, leaves handed out dynamically.  The descent of Sect.
-// 3.4.3 (a cell adds its parent's C translated to its own centre, from the
-// root down) is followed along the leaf's ancestor chain:
-//   C-hat_alpha(child) = C-hat_alpha(child, own M2L)
-//       + (rho_c/rho_p)^|alpha| sum_beta C-hat_{alpha+beta}(parent) (delta/rho_p)^beta / beta!,
-//   delta = s_child - s_parent,
-// which is Eq. shifting over symmetric multi-indices in scaled form.  Then
-// every moonlet of the leaf gets
+// Evaluation: one warp per leaf, leaves handed out dynamically.  Every
+// moonlet of the leaf gets
 //   a = (1/rho) sum_{|beta| <= p-1} C-hat_{e_k+beta} (d/rho)^beta / beta!,  d = x - s_leaf,
 // plus sum_j mu_j (x_j - x)/|x_j - x|^3 over the moonlets of its direct list
 // (mu_j = G m_j; coincident pairs, the moonlet itself included, are skipped),
-// plus the external forces in FP64.  Each lane owns two moonlets and builds
-// their sums in registers; they are written once.
+// plus the external forces in FP64.  Each lane owns one or two moonlets and
+// builds their sums in registers; they are written once.
 //
 // Mixed precision: the direct sum reads every position as an FP32 pair
 // (hi, lo) with x = hi + lo; (hi_j - hi_i) + (lo_j - lo_i) gives the
@@ -48,7 +42,7 @@ struct EvalArgs {
     const int *leaves, *level, *parent, *first, *count;
     const double *sx, *sy, *sz, *rho;
     const float4 *gh, *gl, *shift;
-    const void *Ch;
+    const void *Cf;   // complete local expansions
     const int *p2p_off, *p2p_src;
     int p2p_dir_cap;
     const double *x, *y, *z, *m;
@@ -59,18 +53,6 @@ struct EvalArgs {
     double *amx, *amy, *amz;
     int *work;
     const Ctrl *ctl;
-};
-
-constexpr int EVAL_WARPS = 4;   // warps per block
-
-constexpr int EVAL_BUF = 128;   // staged source moonlets per warp
-
-template <int P, typename real>
-struct EvalShared {
-    static constexpr int NC = num_c(P);
-    real C[1][NC];
-    float4 h[EVAL_BUF], l[EVAL_BUF];         // FP32 path: staged sources (hi + mu, lo)
-    double dx[32], dy[32], dz[32], dm[32];   // FP64 path
 };
 
 template <int P, typename real>
@@ -112,19 +94,19 @@ __device__ __forceinline__ void external_force(const ExtForce &E, double X, doub
     }
 }
 
+// One near-field pair, FP32: the separation from the (hi, lo) pairs, then
+// mu_j d / |d|^3; a coincident pair (r^2 = 0, the moonlet itself) adds 0.
 __device__ __forceinline__ void p2p_f32(const float4 &h, const float4 &l, const float4 &th, const float4 &tl, float &ax,
                                         float &ay, float &az) {
     const float dx = (h.x - th.x) + (l.x - tl.x);
     const float dy = (h.y - th.y) + (l.y - tl.y);
     const float dz = (h.z - th.z) + (l.z - tl.z);
     const float r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 > 1e-30f) {
-        const float inv = rsqrtf(r2);
-        const float f3 = h.w * inv * inv * inv;
-        ax += dx * f3;
-        ay += dy * f3;
-        az += dz * f3;
-    }
+    const float inv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float f3 = h.w * inv * inv * inv;
+    ax += dx * f3;
+    ay += dy * f3;
+    az += dz * f3;
 }
 
 __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double mu, double X, double Y, double Z,
@@ -141,259 +123,330 @@ __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double 
 }
 
 // ---------------------------------------------------------------------------
-// Tree descent (Sect. 3.4.3): level by level from the root, every cell adds
-// its parent's (already complete) local expansion translated to its own
-// centre.  One cooperative launch; a warp per cell, lanes over the output
-// coefficients; the cell's C-hat is overwritten with the complete expansion.
+// Tree descent (Sect. 3.4.3).  The descent adds to every cell its parent's
+// complete local expansion translated to the cell's centre, from the root
+// down.  A translation (Eq. shifting) re-expands a polynomial of degree p
+// about a new point, which is exact, and translations compose, so the
+// complete expansion of cell c is the sum of the own M2L expansions of c and
+// of all its ancestors a, each translated straight from s_a to s_c:
+//   C-hat_alpha(c) = C-hat_alpha(c, own)
+//       + sum_a (rho_c/rho_a)^|alpha| sum_beta C-hat_{alpha+beta}(a, own) (h_a)^beta / beta!,
+//   h_a = (s_c - s_a)/rho_a.
+// Every cell is thus independent of the others: one warp per cell, lanes
+// over the output coefficients, with no level-by-level barrier.  The result
+// goes to Cf (Ch keeps the own M2L sums).
+//
+// The inner sum factorises over the axes (beta! = bx! by! bz!), so a
+// translation is done as three one-dimensional shifts, along x, y, z in
+// turn: D_gamma = sum_k C_{gamma + k e_axis} h_axis^k / k!, with
+// coefficients beyond order p taken as zero.
 // ---------------------------------------------------------------------------
 struct DescendArgs {
     const int *parent;
-    const float4 *shift;
+    const float4 *gh, *gl;
     const double *sx, *sy, *sz, *rho;
-    void *Ch;
-    Ctrl *ctl;
+    const void *Ch;
+    void *Cf;
+    const Ctrl *ctl;
 };
 
+constexpr int DESC_WARPS = 8;
+
+// Index of (a, b, c) + k e_axis in the order-1.. storage, for an output of
+// order n with kk = b + c.
+template <int AXIS>
+__device__ __forceinline__ int shifted_index(int n, int kk, int c, int k) {
+    const int m = n + k;
+    const int t = AXIS == 0 ? kk : kk + k;
+    return m * (m + 1) * (m + 2) / 6 + t * (t + 1) / 2 + c + (AXIS == 2 ? k : 0) - 1;
+}
+
+template <int P, int AXIS, typename real>
+__device__ __forceinline__ real shift_axis(const real *src, const real (&w)[P + 1], int n, int kk, int c) {
+    real s = src[shifted_index<AXIS>(n, kk, c, 0)];
+#pragma unroll
+    for (int k = 1; k <= P - 1; k++)
+        if (k <= P - n) s += src[shifted_index<AXIS>(n, kk, c, k)] * w[k];
+    return s;
+}
+
 template <int P, typename real>
-__global__ void __launch_bounds__(256) k_descend(DescendArgs A) {
+__global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
     constexpr int NC = num_c(P);
+    constexpr int PER = (NC + 31) / 32;
     constexpr bool f32 = std::is_same<real, float>::value;
-    __shared__ real s_C[8][NC];
-    __shared__ real s_pw[8][3][P + 1];
+    __shared__ real s_A[DESC_WARPS][NC];
+    __shared__ real s_B[DESC_WARPS][NC];
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    real *Ch = static_cast<real *>(A.Ch);
-    volatile Ctrl *vc = A.ctl;
-    const int maxl = vc->max_level;
-    for (int lev = 1; lev <= maxl; lev++) {
-        const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
-        for (int c = ls + gw; c < le; c += nwarps) {
-            const int pc = A.parent[c];
-            for (int i = lane; i < NC; i += 32) s_C[wl][i] = __ldcg(&Ch[(size_t)pc * NC + i]);
-            real ratio;
-            if constexpr (f32) {
-                const float4 sh = A.shift[c];
-                ratio = sh.w;
-                if (lane < 3) {
-                    const float h = lane == 0 ? sh.x : (lane == 1 ? sh.y : sh.z);
-                    float pw = 1.0f;
-                    for (int k = 0; k <= P; k++) {
-                        s_pw[wl][lane][k] = pw;
-                        pw *= h;
-                    }
-                }
-            } else {
-                const double iprho = 1.0 / A.rho[pc];
-                ratio = A.rho[c] * iprho;
-                if (lane < 3) {
-                    const double dv = lane == 0 ? A.sx[c] - A.sx[pc] : (lane == 1 ? A.sy[c] - A.sy[pc] : A.sz[c] - A.sz[pc]);
-                    const real h = dv * iprho;
-                    real pw = real(1);
-                    for (int k = 0; k <= P; k++) {
-                        s_pw[wl][lane][k] = pw;
-                        pw *= h;
-                    }
-                }
-            }
-            __syncwarp();
-            for (int i = lane; i < NC; i += 32) {
-                const int a = c_exp2.e[i + 1][0], b = c_exp2.e[i + 1][1], cc = c_exp2.e[i + 1][2];
-                const int n = a + b + cc;
-                real acc = real(0);
-                for (int nb = 0; nb <= P - n; nb++)
-                    for (int kb = 0; kb <= nb; kb++)
-                        for (int c2 = 0; c2 <= kb; c2++) {
-                            const int ab = nb - kb, bb = kb - c2;
-                            const real w = s_pw[wl][0][ab] * s_pw[wl][1][bb] * s_pw[wl][2][c2] *
-                                           static_cast<real>(c_ifact[ab] * c_ifact[bb] * c_ifact[c2]);
-                            acc += s_C[wl][cidx(a + ab, b + bb, cc + c2)] * w;
-                        }
-                for (int k = 0; k < n; k++) acc *= ratio;   // (rho_c/rho_p)^n applied to the small factor first
-                Ch[(size_t)c * NC + i] += acc;
-            }
-            __syncwarp();
-        }
-        if (!grid_sync(A.ctl)) return;
+    const real *Ch = static_cast<const real *>(A.Ch);
+    real *Cf = static_cast<real *>(A.Cf);
+    real *sa = s_A[wl], *sb = s_B[wl];
+    const int ncells = A.ctl->n_cells;
+    int on[PER], okk[PER], oc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int i = lane + 32 * k;
+        const int e = i < NC ? i + 1 : 1;
+        const int a0 = c_exp2.e[e][0], b0 = c_exp2.e[e][1], c0 = c_exp2.e[e][2];
+        on[k] = a0 + b0 + c0;
+        okk[k] = b0 + c0;
+        oc[k] = c0;
     }
-}
-
-// Near field of one group of targets (NT per lane) from the leaf's direct
-// list: source leaves are taken four at a time, their moonlets staged into
-// the warp's buffer, and every lane sums over the whole buffer.
-template <int NT>
-__device__ __forceinline__ void p2p_list_f32(const EvalArgs &A, float4 *bh, float4 *bl, int s0, int s1, int lane,
-                                             const float4 *th, const float4 *tl, float *ax, float *ay, float *az) {
-    for (int si = s0; si < s1; si += 4) {
-        const int nc = min(4, s1 - si);
-        int fst = 0, cn = 0;
-        if (lane < nc) {
-            const int src = A.p2p_src[si + lane];
-            fst = A.first[src];
-            cn = A.count[src];
+    for (int c = gw; c < ncells; c += nwarps) {
+        real acc[PER];
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = lane + 32 * k;
+            acc[k] = i < NC ? Ch[(size_t)c * NC + i] : real(0);
         }
-        int f[4], o[4], total = 0;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            f[q] = __shfl_sync(0xffffffffu, fst, q);
-            o[q] = total;
-            total += __shfl_sync(0xffffffffu, cn, q);
-        }
-        for (int w0 = 0; w0 < total; w0 += EVAL_BUF) {
-            const int lim = min(EVAL_BUF, total - w0);
-            __syncwarp();
-            for (int t = lane; t < EVAL_BUF; t += 32) {
-                const int g = w0 + t;
-                if (t < lim) {
-                    const int q = g >= o[3] ? 3 : (g >= o[2] ? 2 : (g >= o[1] ? 1 : 0));
-                    const int jj = f[q] + g - o[q];
-                    bh[t] = A.hi4[jj];
-                    bl[t] = A.lo4[jj];
-                } else if (t < ((lim + 7) & ~7)) {   // pad to a multiple of 8 with mu = 0 far away
-                    bh[t] = make_float4(1e18f, 0.f, 0.f, 0.f);
-                    bl[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            __syncwarp();
-            const int lim8 = (lim + 7) & ~7;
-            for (int k = 0; k < lim8; k += 8) {
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const float4 h = bh[k + u], l = bl[k + u];
-#pragma unroll
-                    for (int t = 0; t < NT; t++) p2p_f32(h, l, th[t], tl[t], ax[t], ay[t], az[t]);
-                }
-            }
-        }
-    }
-}
-
-template <int NT>
-__device__ __forceinline__ void p2p_list_f64(const EvalArgs &A, double *bx, double *by, double *bz, double *bm,
-                                             int s0, int s1, int lane, const double *X, const double *Y,
-                                             const double *Z, double *ax, double *ay, double *az) {
-    for (int si = s0; si < s1; si++) {
-        const int src = A.p2p_src[si];
-        const int sf = A.first[src], sc = A.count[src];
-        for (int j0 = 0; j0 < sc; j0 += 32) {
-            const int lim = min(32, sc - j0);
-            __syncwarp();
-            if (lane < lim) {
-                const int j = sf + j0 + lane;
-                bx[lane] = A.x[j];
-                by[lane] = A.y[j];
-                bz[lane] = A.z[j];
-                bm[lane] = A.G * A.m[j];
-            }
-            __syncwarp();
-            for (int k = 0; k < lim; k++)
-#pragma unroll
-                for (int t = 0; t < NT; t++) p2p_f64(bx[k], by[k], bz[k], bm[k], X[t], Y[t], Z[t], ax[t], ay[t], az[t]);
-        }
-    }
-}
-
-// L2P + near field + external forces for the targets f + t0 + lane + 32 t, t < NT
-template <int P, typename real, int NT>
-__device__ __forceinline__ void eval_targets(const EvalArgs &A, EvalShared<P, real> &S, const real *C, int leaf, int f,
-                                             int cnt, int t0, int lane, int s0, int s1) {
-    constexpr bool f32 = std::is_same<real, float>::value;
-    const float4 lgh = A.gh[leaf], lgl = A.gl[leaf];
-    const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
-    real ax[NT], ay[NT], az[NT];
-    double X[NT], Y[NT], Z[NT];
-    float4 th[NT], tl[NT];
-    bool act[NT];
-#pragma unroll
-    for (int t = 0; t < NT; t++) {
-        const int ti = t0 + lane + 32 * t;
-        act[t] = ti < cnt;
-        const int i = f + (act[t] ? ti : 0);
-        ax[t] = ay[t] = az[t] = real(0);
-        X[t] = A.x[i]; Y[t] = A.y[i]; Z[t] = A.z[i];
-        th[t] = A.hi4[i];
-        tl[t] = A.lo4[i];
+        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+        double csx = 0.0, csy = 0.0, csz = 0.0, crho = 0.0;
         if constexpr (f32) {
-            l2p<P, real>(C, ((th[t].x - lgh.x) + (tl[t].x - lgl.x)) * irf, ((th[t].y - lgh.y) + (tl[t].y - lgl.y)) * irf,
-                         ((th[t].z - lgh.z) + (tl[t].z - lgl.z)) * irf, ax[t], ay[t], az[t]);
-            ax[t] *= irf; ay[t] *= irf; az[t] *= irf;
+            ch = A.gh[c];
+            cl = A.gl[c];
         } else {
-            const double irho = 1.0 / A.rho[leaf];
-            l2p<P, real>(C, (X[t] - A.sx[leaf]) * irho, (Y[t] - A.sy[leaf]) * irho, (Z[t] - A.sz[leaf]) * irho, ax[t],
-                         ay[t], az[t]);
-            ax[t] *= irho; ay[t] *= irho; az[t] *= irho;
+            csx = A.sx[c]; csy = A.sy[c]; csz = A.sz[c]; crho = A.rho[c];
+        }
+        for (int a = A.parent[c]; a >= 0; a = A.parent[a]) {
+            __syncwarp();
+            for (int i = lane; i < NC; i += 32) sa[i] = Ch[(size_t)a * NC + i];
+            real hx, hy, hz, ratio;
+            if constexpr (f32) {
+                const float4 ah = A.gh[a], al = A.gl[a];
+                const float ir = 1.0f / al.w;   // exact: rho is a power of two
+                ratio = cl.w * ir;
+                hx = ((ch.x - ah.x) + (cl.x - al.x)) * ir;
+                hy = ((ch.y - ah.y) + (cl.y - al.y)) * ir;
+                hz = ((ch.z - ah.z) + (cl.z - al.z)) * ir;
+            } else {
+                const double iar = 1.0 / A.rho[a];
+                ratio = crho * iar;
+                hx = (csx - A.sx[a]) * iar;
+                hy = (csy - A.sy[a]) * iar;
+                hz = (csz - A.sz[a]) * iar;
+            }
+            real wx[P + 1], wy[P + 1], wz[P + 1];
+            wx[0] = wy[0] = wz[0] = real(1);
+#pragma unroll
+            for (int k = 1; k <= P; k++) {
+                wx[k] = wx[k - 1] * hx;
+                wy[k] = wy[k - 1] * hy;
+                wz[k] = wz[k - 1] * hz;
+            }
+#pragma unroll
+            for (int k = 2; k <= P; k++) {
+                const real f = static_cast<real>(c_ifact[k]);
+                wx[k] *= f; wy[k] *= f; wz[k] *= f;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PER; k++)
+                if (lane + 32 * k < NC) sb[lane + 32 * k] = shift_axis<P, 0>(sa, wx, on[k], okk[k], oc[k]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PER; k++)
+                if (lane + 32 * k < NC) sa[lane + 32 * k] = shift_axis<P, 1>(sb, wy, on[k], okk[k], oc[k]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PER; k++) {
+                if (lane + 32 * k >= NC) continue;
+                real s = shift_axis<P, 2>(sa, wz, on[k], okk[k], oc[k]);
+                for (int q = 0; q < on[k]; q++) s *= ratio;   // (rho_c/rho_a)^n, exact powers of two
+                acc[k] += s;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = lane + 32 * k;
+            if (i < NC) Cf[(size_t)c * NC + i] = acc[k];
         }
     }
-    if constexpr (f32) p2p_list_f32<NT>(A, S.h, S.l, s0, s1, lane, th, tl, ax, ay, az);
-    else p2p_list_f64<NT>(A, S.dx, S.dy, S.dz, S.dm, s0, s1, lane, X, Y, Z, ax, ay, az);
-#pragma unroll
-    for (int t = 0; t < NT; t++) {
-        if (!act[t]) continue;
-        const int i = f + t0 + lane + 32 * t;
-        double ex, ey, ez;
-        external_force(A.ext, X[t], Y[t], Z[t], ex, ey, ez);
-        const double mx = ax[t], my = ay[t], mz = az[t];
-        A.ax[i] = mx + ex;
-        A.ay[i] = my + ey;
-        A.az[i] = mz + ez;
-        if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
-    }
 }
+
+// ---------------------------------------------------------------------------
+// Evaluation kernel: one block of EV_THREADS threads per leaf, leaves handed
+// out dynamically.  The leaf's m targets (taken EV_THREADS at a time if the
+// leaf is larger) occupy T = pow2ceil(m) slots, and the block's threads form
+// G = EV_THREADS / T groups: thread (g, t) sums the staged sources
+// k = g, g + G, g + 2G, ... for target t, so a leaf of a few moonlets keeps
+// all lanes busy.  The G partial sums of a target are then added in group
+// order (the result does not depend on timing).  The direct list is staged
+// EV_BUF moonlets at a time, cutting source leaves where the buffer ends.
+// ---------------------------------------------------------------------------
+constexpr int EV_THREADS = 128;
+constexpr int EV_BUF = 512;
 
 template <int P, typename real>
-__global__ void __launch_bounds__(32 * EVAL_WARPS, 4) k_eval(EvalArgs A) {
+struct EvShared {
+    static constexpr int NC = num_c(P);
+    __align__(16) unsigned char buf[EV_BUF * 32];   // FP32: float4 hi[EV_BUF] (xyz, mu), lo[EV_BUF]
+                                                    // FP64: double x, y, z, mu [EV_BUF]
+    real C[NC];
+    real red[3][EV_THREADS];
+    int lfirst[32], lpre[32];
+    int leaf, total, next_si, next_soff;
+};
+
+template <int P, typename real>
+__global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
     constexpr int NC = num_c(P);
-    __shared__ EvalShared<P, real> sh_all[EVAL_WARPS];
+    constexpr bool f32 = std::is_same<real, float>::value;
+    __shared__ EvShared<P, real> S;
     if (aborted(A.ctl)) return;
-    EvalShared<P, real> &S = sh_all[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const real *Ch = static_cast<const real *>(A.Ch);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const real *Cf = static_cast<const real *>(A.Cf);
     const int nl = A.ctl->n_leaves;
+    float4 *sh = reinterpret_cast<float4 *>(S.buf), *sl = sh + EV_BUF;
+    double *bx = reinterpret_cast<double *>(S.buf), *by = bx + EV_BUF, *bz = by + EV_BUF, *bm = bz + EV_BUF;
     while (true) {
-        int li = 0;
-        if (lane == 0) li = atomicAdd(A.work, 1);
-        li = __shfl_sync(0xffffffffu, li, 0);
+        __syncthreads();
+        if (tid == 0) S.leaf = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int li = S.leaf;
         if (li >= nl) break;
         const int leaf = A.leaves[li];
-        __syncwarp();
-        for (int i = lane; i < NC; i += 32) S.C[0][i] = Ch[(size_t)leaf * NC + i];   // complete after the descent
-        __syncwarp();
+        for (int i = tid; i < NC; i += EV_THREADS) S.C[i] = Cf[(size_t)leaf * NC + i];
+        __syncthreads();
         const int f = A.first[leaf], cnt = A.count[leaf];
         const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
-        if (cnt <= 32) {
-            eval_targets<P, real, 1>(A, S, S.C[0], leaf, f, cnt, 0, lane, s0, s1);
-        } else {
-            for (int t0 = 0; t0 < cnt; t0 += 64) eval_targets<P, real, 2>(A, S, S.C[0], leaf, f, cnt, t0, lane, s0, s1);
+        for (int t0 = 0; t0 < cnt; t0 += EV_THREADS) {
+            const int m = min(EV_THREADS, cnt - t0);
+            int T = 1;
+            while (T < m) T <<= 1;
+            const int G = EV_THREADS / T, tt = tid & (T - 1), g = tid / T;
+            const bool act = tt < m;
+            const int i = f + t0 + (act ? tt : 0);
+            const float4 th = A.hi4[i], tl = A.lo4[i];
+            const double X = A.x[i], Y = A.y[i], Z = A.z[i];
+            real ax = real(0), ay = real(0), az = real(0);
+            int si = s0, soff = 0;
+            while (si < s1) {
+                __syncthreads();
+                if (warp == 0) {
+                    const int idx = si + lane;
+                    int fst = 0, c = 0;
+                    if (idx < s1) {
+                        const int src = A.p2p_src[idx];
+                        fst = A.first[src];
+                        c = A.count[src];
+                    }
+                    if (lane == 0) { fst += soff; c -= soff; }
+                    int inc = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += v;
+                    }
+                    const int exc = inc - c;
+                    const int total = min(EV_BUF, __shfl_sync(0xffffffffu, inc, 31));
+                    S.lfirst[lane] = fst;
+                    S.lpre[lane] = exc;
+                    // source leaves consumed completely; the next one may be cut
+                    const unsigned done = __ballot_sync(0xffffffffu, idx < s1 && inc <= total);
+                    const int L = __popc(done);
+                    const int excL = __shfl_sync(0xffffffffu, exc, L & 31);
+                    if (lane == 0) {
+                        S.total = total;
+                        S.next_si = si + L;
+                        S.next_soff = (L < 32 && si + L < s1) ? (L == 0 ? soff : 0) + (total - excL) : 0;
+                    }
+                }
+                __syncthreads();
+                const int total = S.total;
+                for (int t = tid; t < total; t += EV_THREADS) {
+                    int q = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1)
+                        if (S.lpre[q + st] <= t) q += st;
+                    const int jj = S.lfirst[q] + t - S.lpre[q];
+                    if constexpr (f32) {
+                        sh[t] = A.hi4[jj];
+                        sl[t] = A.lo4[jj];
+                    } else {
+                        bx[t] = A.x[jj];
+                        by[t] = A.y[jj];
+                        bz[t] = A.z[jj];
+                        bm[t] = A.G * A.m[jj];
+                    }
+                }
+                si = S.next_si;
+                soff = S.next_soff;
+                __syncthreads();
+                if constexpr (f32) {
+#pragma unroll 4
+                    for (int k = g; k < total; k += G) p2p_f32(sh[k], sl[k], th, tl, ax, ay, az);
+                } else {
+#pragma unroll 2
+                    for (int k = g; k < total; k += G) p2p_f64(bx[k], by[k], bz[k], bm[k], X, Y, Z, ax, ay, az);
+                }
+            }
+            if (G > 1) {
+                __syncthreads();
+                S.red[0][tid] = ax;
+                S.red[1][tid] = ay;
+                S.red[2][tid] = az;
+                __syncthreads();
+                if (g == 0) {
+                    ax = ay = az = real(0);
+                    for (int q = 0; q < G; q++) {
+                        ax += S.red[0][q * T + tt];
+                        ay += S.red[1][q * T + tt];
+                        az += S.red[2][q * T + tt];
+                    }
+                }
+            }
+            if (g == 0 && act) {
+                // L2P of the leaf's complete local expansion (Eq. shifting at the moonlet)
+                real lx = real(0), ly = real(0), lz = real(0);
+                if constexpr (f32) {
+                    const float4 lgh = A.gh[leaf], lgl = A.gl[leaf];
+                    const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
+                    l2p<P, real>(S.C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
+                                 ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
+                    lx *= irf; ly *= irf; lz *= irf;
+                } else {
+                    const double irho = 1.0 / A.rho[leaf];
+                    l2p<P, real>(S.C, (X - A.sx[leaf]) * irho, (Y - A.sy[leaf]) * irho, (Z - A.sz[leaf]) * irho, lx, ly,
+                                 lz);
+                    lx *= irho; ly *= irho; lz *= irho;
+                }
+                double ex, ey, ez;
+                external_force(A.ext, X, Y, Z, ex, ey, ez);
+                const double mx = static_cast<double>(lx + ax), my = static_cast<double>(ly + ay),
+                             mz = static_cast<double>(lz + az);
+                A.ax[i] = mx + ex;
+                A.ay[i] = my + ey;
+                A.az[i] = mz + ez;
+                if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
+            }
         }
-        __syncwarp();
     }
 }
 
 template <int P, typename real>
 static void descend_t(ncorp_ctx *c, DescendArgs D) {
-    int per_sm = 0;
-    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, reinterpret_cast<const void *>(k_descend<P, real>), 256, 0));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;
-    void *args[] = {&D};
-    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_descend<P, real>),
-                                                 dim3(per_sm * c->num_sms), dim3(256), args, 0, c->stream));
+    k_descend<P, real><<<8 * c->num_sms, 32 * DESC_WARPS, 0, c->stream>>>(D);
     c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 template <int P, typename real>
 static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
-    k_eval<P, real><<<8 * c->num_sms, 32 * EVAL_WARPS, 0, c->stream>>>(A);
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void *>(k_eval<P, real>), EV_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_eval<P, real><<<per_sm * c->num_sms, EV_THREADS, 0, c->stream>>>(A);
     c->launches++;
 }
 
 void launch_descend(ncorp_ctx *c, int p, bool mixed) {
     Cells &C = c->cells;
     DescendArgs D;
-    D.parent = C.parent; D.shift = C.shift; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
-    D.Ch = C.Ch; D.ctl = c->ctl;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    D.parent = C.parent; D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
+    D.Ch = C.Ch; D.Cf = C.Cf; D.ctl = c->ctl;
 #define NCORP_DESC_CASE(PP)                      \
     case PP:                                     \
         if (mixed) descend_t<PP, float>(c, D);   \
@@ -417,7 +470,7 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     A.leaves = C.leaves; A.level = C.level; A.parent = C.parent; A.first = C.first; A.count = C.count;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
     A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
-    A.Ch = C.Ch;
+    A.Cf = C.Cf;
     A.p2p_off = c->wl.p2p_off; A.p2p_src = c->wl.p2p_src; A.p2p_dir_cap = c->wl.p2p_dir_cap;
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;
     A.hi4 = P.hi4; A.lo4 = P.lo4;

@@ -96,13 +96,16 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
     dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
     dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.shift, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
-    double *mh = nullptr, *ch = nullptr;
+    double *mh = nullptr, *ch = nullptr, *cf = nullptr;
     dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
     dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
+    dalloc(cf, static_cast<size_t>(cap) * num_c(MAXP));
     if (C.Mh) cudaFree(C.Mh);
     if (C.Ch) cudaFree(C.Ch);
+    if (C.Cf) cudaFree(C.Cf);
     C.Mh = mh;
     C.Ch = ch;
+    C.Cf = cf;
     dalloc(C.leaves, cap);
     dalloc(C.bounds, static_cast<size_t>(cap) * 9);
     dalloc(C.blocksum, 8192);
@@ -765,7 +768,7 @@ int ncorp_expansions(ncorp_ctx *c, double *mult, double *local, double *rho, int
             NCORP_CUDA_CHECK(cudaMemcpy(mult, M.data(), sizeof(double) * M.size(), cudaMemcpyDefault));
         }
         if (local) {
-            std::vector<double> Cl = fetch(c->cells.Ch, nc_);
+            std::vector<double> Cl = fetch(c->cells.Cf, nc_);
             for (int i = 0; i < k; i++)
                 for (int j = 0; j < nc_; j++) {
                     int a, b, cc;
@@ -809,7 +812,7 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
     dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
     dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
-    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.shift); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.shift); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
     WalkLists &W = c->wl;
     dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
     dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
