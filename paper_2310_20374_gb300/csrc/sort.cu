@@ -266,84 +266,132 @@ void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort of (uint64 key, uint32 value), 8-bit digits.  Each pass: tile
-// histograms, a scan of the digit-major histogram table, and a stable scatter.
+// LSD radix sort of (uint64 key, uint32 value), 8-bit digits, all passes in
+// one cooperative launch.  Each pass: per-tile digit histograms (digit-major
+// table), a grid barrier, prefix sums along each digit's row (one warp per
+// row) and the rows' totals, a barrier, each block's scan of the 256 totals
+// (digit starts), and the stable scatter; a barrier ends the pass.
 // Stability inside a tile comes from warp-synchronous ranking: each warp owns
 // a contiguous slice of the tile and walks it 32 keys at a time, ranking equal
 // digits with __match_any_sync; warps are then ordered by a per-digit prefix.
 // ---------------------------------------------------------------------------
-constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_SLICE = RS_TILE / RS_W;
+constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_SLICE = RS_TILE / RS_W;
 
-__global__ void k_rs_hist(const uint64_t *__restrict__ keys, int n, int shift, int *__restrict__ hist, int ntiles) {
-    __shared__ int s_cnt[256];
-    s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    long long base = static_cast<long long>(blockIdx.x) * RS_TILE;
-    for (int k = 0; k < RS_I; k++) {
-        long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
-        if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 0xffu], 1);
-    }
-    __syncthreads();
-    hist[threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
-}
+struct RadixArgs {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    int n, ntiles, passes;
+    int *hist;     // [256][ntiles]
+    int *rowsum;   // [256]
+    Ctrl *ctl;
+};
 
-__global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
-                             const int *__restrict__ offs, int ntiles) {
+__global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     __shared__ int s_cnt[RS_W][256];
+    __shared__ int s_start[256];
+    __shared__ int s_warp[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
-    __syncwarp();
-    const long long base = static_cast<long long>(blockIdx.x) * RS_TILE + static_cast<long long>(w) * RS_SLICE;
+    const int gw = blockIdx.x * RS_W + w, nwarps = gridDim.x * RS_W;
     const unsigned lt = (1u << lane) - 1u;
-    uint64_t kk[RS_I];
-    uint32_t vv[RS_I];
-    int rank[RS_I];
-#pragma unroll
-    for (int r = 0; r < RS_I; r++) {
-        long long i = base + r * 32 + lane;
-        bool ok = i < n;
-        kk[r] = ok ? kin[i] : 0ull;
-        vv[r] = ok ? vin[i] : 0u;
-        int d = ok ? static_cast<int>((kk[r] >> shift) & 0xffu) : 256 + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int before = ok ? s_cnt[w][d] : 0;
-        rank[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (ok && (__ffs(peers) - 1) == lane) s_cnt[w][d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {   // exclusive prefix over warps, per digit
-        int d = threadIdx.x;
-        int acc = 0;
-        for (int ww = 0; ww < RS_W; ww++) {
-            int t = s_cnt[ww][d];
-            s_cnt[ww][d] = acc;
-            acc += t;
+    const int n = A.n, ntiles = A.ntiles;
+    for (int ps = 0; ps < A.passes; ps++) {
+        const int shift = 8 * ps;
+        const uint64_t *kin = (ps & 1) ? A.k1 : A.k0;
+        const uint32_t *vin = (ps & 1) ? A.v1 : A.v0;
+        uint64_t *kout = (ps & 1) ? A.k0 : A.k1;
+        uint32_t *vout = (ps & 1) ? A.v0 : A.v1;
+        // 1. tile histograms
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            s_start[threadIdx.x] = 0;
+            __syncthreads();
+            const long long base = static_cast<long long>(tile) * RS_TILE;
+            for (int k = 0; k < RS_I; k++) {
+                const long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
+                if (i < n) atomicAdd(&s_start[(__ldcg(&kin[i]) >> shift) & 0xffu], 1);
+            }
+            __syncthreads();
+            A.hist[threadIdx.x * ntiles + tile] = s_start[threadIdx.x];
+            __syncthreads();
         }
-    }
-    __syncthreads();
+        if (!grid_sync(A.ctl)) return;
+        // 2. exclusive prefix along each digit's row, row totals
+        for (int row = gw; row < 256; row += nwarps) {
+            int carry = 0;
+            for (int t0 = 0; t0 < ntiles; t0 += 32) {
+                const int t = t0 + lane;
+                const int v = t < ntiles ? __ldcg(&A.hist[row * ntiles + t]) : 0;
+                int inc = v;
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
-        long long i = base + r * 32 + lane;
-        if (i < n) {
-            int d = static_cast<int>((kk[r] >> shift) & 0xffu);
-            int pos = offs[d * ntiles + blockIdx.x] + s_cnt[w][d] + rank[r];
-            kout[pos] = kk[r];
-            vout[pos] = vv[r];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                if (t < ntiles) A.hist[row * ntiles + t] = carry + inc - v;
+                carry += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) A.rowsum[row] = carry;
         }
+        if (!grid_sync(A.ctl)) return;
+        // 3. digit starts
+        s_start[threadIdx.x] = block_excl_scan(__ldcg(&A.rowsum[threadIdx.x]), s_warp, nullptr);
+        __syncthreads();
+        // 4. stable scatter
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
+            __syncwarp();
+            const long long base = static_cast<long long>(tile) * RS_TILE + static_cast<long long>(w) * RS_SLICE;
+            uint64_t kk[RS_I];
+            uint32_t vv[RS_I];
+            int rank[RS_I];
+#pragma unroll
+            for (int r = 0; r < RS_I; r++) {
+                const long long i = base + r * 32 + lane;
+                const bool ok = i < n;
+                kk[r] = ok ? __ldcg(&kin[i]) : 0ull;
+                vv[r] = ok ? __ldcg(&vin[i]) : 0u;
+                const int d = ok ? static_cast<int>((kk[r] >> shift) & 0xffu) : 256 + lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int before = ok ? s_cnt[w][d] : 0;
+                rank[r] = before + __popc(peers & lt);
+                __syncwarp();
+                if (ok && (__ffs(peers) - 1) == lane) s_cnt[w][d] = before + __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            {   // exclusive prefix over warps, per digit
+                const int d = threadIdx.x;
+                int acc = 0;
+                for (int ww = 0; ww < RS_W; ww++) {
+                    const int t = s_cnt[ww][d];
+                    s_cnt[ww][d] = acc;
+                    acc += t;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < RS_I; r++) {
+                const long long i = base + r * 32 + lane;
+                if (i < n) {
+                    const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
+                    const int pos = s_start[d] + __ldcg(&A.hist[d * ntiles + tile]) + s_cnt[w][d] + rank[r];
+                    kout[pos] = kk[r];
+                    vout[pos] = vv[r];
+                }
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(A.ctl)) return;
     }
 }
 
 // Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
-// the key are significant (a multiple of 8 passes is rounded up; an even
-// number of passes leaves the result in the input buffers).
+// the key are significant (rounded up to an even number of 8-bit passes, so
+// the result ends in the input buffers).
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
                     int bits) {
     if (n <= 1) return;
-    int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int need = 256 * ntiles;
+    const int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const int need = 256 * ntiles + 256;
     if (c->tile_hist_cap < need) {
         if (c->tile_hist) cudaFree(c->tile_hist);
         c->tile_hist_cap = need + 4096;
@@ -351,17 +399,21 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
     }
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
-    uint64_t *ki = keys, *ko = keys_alt;
-    uint32_t *vi = vals, *vo = vals_alt;
-    for (int ps = 0; ps < passes; ps++) {
-        int shift = 8 * ps;
-        k_rs_hist<<<ntiles, RS_T, 0, c->stream>>>(ki, n, shift, c->tile_hist, ntiles); c->launches++;
-        scan_exclusive(c, c->tile_hist, c->tile_hist, need, nullptr);
-        k_rs_scatter<<<ntiles, RS_T, 0, c->stream>>>(ki, vi, ko, vo, n, shift, c->tile_hist, ntiles); c->launches++;
-        NCORP_CUDA_CHECK(cudaGetLastError());
-        std::swap(ki, ko);
-        std::swap(vi, vo);
-    }
+    RadixArgs A;
+    A.k0 = keys; A.k1 = keys_alt; A.v0 = vals; A.v1 = vals_alt;
+    A.n = n; A.ntiles = ntiles; A.passes = passes;
+    A.hist = c->tile_hist; A.rowsum = c->tile_hist + 256 * ntiles; A.ctl = c->ctl;
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
+                                                                   RS_T, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int grid = std::min(ntiles, per_sm * c->num_sms);
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    void *args[] = {&A};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args,
+                                                 0, c->stream));
+    c->launches++;
 }
 
 __global__ void k_iota(uint32_t *idx, int n) {

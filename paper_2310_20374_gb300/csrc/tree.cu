@@ -290,43 +290,91 @@ __device__ __forceinline__ real warp_sum_r(real v) {
     return v;
 }
 
-// ---- gravity leaves: one thread per leaf (Eqs. expansion_center, rmax_2, corner cap)
-__global__ void k_leaf_gravity(ClimbArgs A) {
+// ---- leaves: eight leaves per warp, four lanes per leaf.  The centre's
+// sums run in the oracle's order, one sum per lane (q = 0: the weights,
+// q = 1..3: the weighted coordinates), so a warp instruction advances 32
+// independent sums; the maxima over the moonlets are exact in any order and
+// are split over the four lanes.
+constexpr int LEAF_GROUP = 8;
+
+struct LeafSlot {
+    int sub, q, base, t, c, f, cnt;
+    bool valid;
+};
+
+__device__ __forceinline__ LeafSlot leaf_slot(const ClimbArgs &A, int gw, int lane, int n_leaves) {
+    LeafSlot L;
+    L.sub = lane >> 2;
+    L.q = lane & 3;
+    L.base = lane & ~3;
+    L.t = gw * LEAF_GROUP + L.sub;
+    L.valid = L.t < n_leaves;
+    L.c = L.valid ? A.leaves[L.t] : 0;
+    L.f = L.valid ? A.first[L.c] : 0;
+    L.cnt = L.valid ? A.count[L.c] : 0;
+    return L;
+}
+
+__device__ __forceinline__ double quad_max(double v) {
+    v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    return fmax(v, __shfl_xor_sync(0xffffffffu, v, 2));
+}
+
+// Corner cap of the leaf (lanes q = 0..2 take one axis each), returned on every lane of the quad.
+__device__ __forceinline__ double quad_corner(const ClimbArgs &A, const LeafSlot &L, double sx, double sy, double sz) {
+    double d = 0.0;
+    if (L.valid && L.q < 3) {
+        const int lev = A.level[L.c];
+        const double h = cell_side(A.ctl, lev);
+        d = corner_axis(A.ctl, L.q, h, L.q == 0 ? A.cx[L.c] : (L.q == 1 ? A.cy[L.c] : A.cz[L.c]),
+                        L.q == 0 ? sx : (L.q == 1 ? sy : sz));
+    }
+    const double d0 = __shfl_sync(0xffffffffu, d, L.base), d1 = __shfl_sync(0xffffffffu, d, L.base + 1),
+                 d2 = __shfl_sync(0xffffffffu, d, L.base + 2);
+    return dnorm3(d0, d1, d2);
+}
+
+// ---- gravity leaves (Eqs. expansion_center, rmax_2, corner cap)
+__global__ void __launch_bounds__(64) k_leaf_gravity(ClimbArgs A) {
     if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
-        const int c = A.leaves[t];
-        const int f = A.first[c], cnt = A.count[c];
-        double M = 0, sx = 0, sy = 0, sz = 0;
-        for (int k = f; k < f + cnt; k++) {
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw * LEAF_GROUP < n_leaves; gw += nwarps) {
+        const LeafSlot L = leaf_slot(A, gw, lane, n_leaves);
+        const double *coord = L.q == 1 ? A.x : (L.q == 2 ? A.y : A.z);
+        double acc = 0.0;
+        for (int k = L.f; k < L.f + L.cnt; k++) {
             const double m = A.m[k];
-            M = dadd(M, m);
-            sx = dadd(sx, dmul(m, A.x[k]));
-            sy = dadd(sy, dmul(m, A.y[k]));
-            sz = dadd(sz, dmul(m, A.z[k]));
+            acc = L.q == 0 ? dadd(acc, m) : dadd(acc, dmul(m, coord[k]));
         }
-        sx = ddiv(sx, M);
-        sy = ddiv(sy, M);
-        sz = ddiv(sz, M);
-        double d2 = 0;
-        for (int k = f; k < f + cnt; k++) d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+        const double M = __shfl_sync(0xffffffffu, acc, L.base);
+        const double sq = L.q == 0 ? M : ddiv(acc, M);
+        const double sx = __shfl_sync(0xffffffffu, sq, L.base + 1), sy = __shfl_sync(0xffffffffu, sq, L.base + 2),
+                     sz = __shfl_sync(0xffffffffu, sq, L.base + 3);
+        double d2 = 0.0;
+        for (int k = L.f + L.q; k < L.f + L.cnt; k += 4)
+            d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+        d2 = quad_max(d2);
         double rmax = dsqrt(d2);
-        const int lev = A.level[c];
-        const double cap = corner_distance(A.ctl, lev, A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        const double cap = quad_corner(A, L, sx, sy, sz);
         if (cap < rmax) rmax = cap;
-        const double rho = cell_scale(A.ctl, lev, rmax);
-        A.M[c] = M;
-        A.sx[c] = sx;
-        A.sy[c] = sy;
-        A.sz[c] = sz;
-        A.rmax[c] = rmax;
-        A.rho[c] = rho;
-        float4 hi, lo;
-        split3(sx, sy, sz, hi, lo);
-        hi.w = 0.f;
-        lo.w = static_cast<float>(rho);
-        A.gh[c] = hi;
-        A.gl[c] = lo;
+        if (L.valid && L.q == 0) {
+            const int c = L.c;
+            const double rho = cell_scale(A.ctl, A.level[c], rmax);
+            A.M[c] = M;
+            A.sx[c] = sx;
+            A.sy[c] = sy;
+            A.sz[c] = sz;
+            A.rmax[c] = rmax;
+            A.rho[c] = rho;
+            float4 hi, lo;
+            split3(sx, sy, sz, hi, lo);
+            hi.w = 0.f;
+            lo.w = static_cast<float>(rho);
+            A.gh[c] = hi;
+            A.gl[c] = lo;
+        }
     }
 }
 
@@ -607,7 +655,7 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
     A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_leaf_gravity<<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_leaf_gravity<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
 #define NCORP_CLIMB_CASE(PP)                                             \
     case PP:                                                             \
         if (mixed) climb_gravity_t<PP, float>(c, A);                     \
@@ -634,44 +682,47 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
 // over children of (r_crit - r_max), a moonlet's being R + dt |v| (stored,
 // rounded up to FP32, for the pair prefilter).
 // ---------------------------------------------------------------------------
-__global__ void k_leaf_collision(ClimbArgs A) {
+__global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
     if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_leaves; t += gridDim.x * blockDim.x) {
-        const int c = A.leaves[t];
-        const int f = A.first[c], cnt = A.count[c];
-        double sx = 0, sy = 0, sz = 0;
-        for (int k = f; k < f + cnt; k++) {
-            sx = dadd(sx, A.x[k]);
-            sy = dadd(sy, A.y[k]);
-            sz = dadd(sz, A.z[k]);
-        }
-        const double w = static_cast<double>(cnt);
-        sx = ddiv(sx, w);
-        sy = ddiv(sy, w);
-        sz = ddiv(sz, w);
-        double d2 = 0, ex = 0;
-        for (int k = f; k < f + cnt; k++) {
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw * LEAF_GROUP < n_leaves; gw += nwarps) {
+        const LeafSlot L = leaf_slot(A, gw, lane, n_leaves);
+        const double *coord = L.q == 0 ? A.x : (L.q == 1 ? A.y : A.z);
+        double acc = 0.0;
+        if (L.q < 3)
+            for (int k = L.f; k < L.f + L.cnt; k++) acc = dadd(acc, coord[k]);
+        const double sq = L.q < 3 ? ddiv(acc, static_cast<double>(L.cnt)) : 0.0;
+        const double sx = __shfl_sync(0xffffffffu, sq, L.base), sy = __shfl_sync(0xffffffffu, sq, L.base + 1),
+                     sz = __shfl_sync(0xffffffffu, sq, L.base + 2);
+        double d2 = 0.0, ex = 0.0;
+        for (int k = L.f + L.q; k < L.f + L.cnt; k += 4) {
             d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
             const double e = dadd(A.R[k], dmul(A.dt, dnorm3(A.vx[k], A.vy[k], A.vz[k])));
             ex = fmax(ex, e);
             A.rcf[k] = __double2float_ru(e);
         }
+        d2 = quad_max(d2);
+        ex = quad_max(ex);
         double rmax = dsqrt(d2);
-        const double cap = corner_distance(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], sx, sy, sz);
+        const double cap = quad_corner(A, L, sx, sy, sz);
         if (cap < rmax) rmax = cap;
-        const double rc = dadd(rmax, ex);
-        A.sx[c] = sx;
-        A.sy[c] = sy;
-        A.sz[c] = sz;
-        A.rmax[c] = rmax;
-        A.rcrit[c] = rc;
-        float4 hi, lo;
-        split3(sx, sy, sz, hi, lo);
-        hi.w = static_cast<float>(rc);
-        lo.w = 0.f;
-        A.gh[c] = hi;
-        A.gl[c] = lo;
+        if (L.valid && L.q == 0) {
+            const int c = L.c;
+            const double rc = dadd(rmax, ex);
+            A.sx[c] = sx;
+            A.sy[c] = sy;
+            A.sz[c] = sz;
+            A.rmax[c] = rmax;
+            A.rcrit[c] = rc;
+            float4 hi, lo;
+            split3(sx, sy, sz, hi, lo);
+            hi.w = static_cast<float>(rc);
+            lo.w = 0.f;
+            A.gh[c] = hi;
+            A.gl[c] = lo;
+        }
     }
 }
 
@@ -744,7 +795,7 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_leaf_collision<<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_leaf_collision<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
     k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
