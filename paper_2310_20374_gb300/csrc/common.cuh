@@ -97,6 +97,7 @@ struct Ctrl {
     int n_self;            // leaves interacting with themselves
     int n_found;           // colliding pairs found
     int walk_iters;
+    int n_items;           // multipole work items (cell, chunk)
     int n_m2l_dir;
     int n_p2p_dir;
     unsigned bar_count;

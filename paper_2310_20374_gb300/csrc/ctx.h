@@ -34,12 +34,15 @@ struct Cells {
     // FP32 copies for the walk's first test and the FP32 kernels:
     float4 *gh = nullptr;     // gravity centre rounded to FP32 (xyz), r_crit rounded to FP32 (w)
     float4 *gl = nullptr;     // centre - hi (xyz), rho (w, exact power of two)
-    float4 *shift = nullptr;  // (s_cell - s_parent)/rho_parent (xyz), rho_cell/rho_parent (w)
     float4 *bh = nullptr;     // collision centre hi (xyz), collision r_crit (w)
     float4 *bl = nullptr;     // collision centre lo (xyz)
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
     void *Ch = nullptr;       // [cap][num_c(p)] local coefficients of the cell's own M2L (float or double)
     void *Cf = nullptr;       // [cap][num_c(p)] complete local expansion after the descent
+    void *part = nullptr;     // [item_cap][num_m(p)] multipole sums of cell chunks
+    int2 *items = nullptr;    // [item_cap] multipole work items (cell, chunk)
+    int *item_base = nullptr; // [cap] first work item of each cell
+    int item_cap = 0;
     int *leaves = nullptr;    // leaf cell ids
     int *bounds = nullptr;    // [cap][9] scratch of the build
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels
@@ -59,6 +62,7 @@ struct WalkLists {
 };
 
 constexpr int WALK_MAX_ITERS = 96;
+constexpr int P2M_ITEM_CHUNK = 512;   // moonlets per multipole work item
 
 }  // namespace ncorp
 

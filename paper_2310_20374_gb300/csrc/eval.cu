@@ -41,7 +41,7 @@ __constant__ ExpTable2 c_exp2 = make_exp_table2();
 struct EvalArgs {
     const int *leaves, *level, *parent, *first, *count;
     const double *sx, *sy, *sz, *rho;
-    const float4 *gh, *gl, *shift;
+    const float4 *gh, *gl;
     const void *Cf;   // complete local expansions
     const int *p2p_off, *p2p_src;
     int p2p_dir_cap;
@@ -469,7 +469,7 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     EvalArgs A;
     A.leaves = C.leaves; A.level = C.level; A.parent = C.parent; A.first = C.first; A.count = C.count;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
-    A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
+    A.gh = C.gh; A.gl = C.gl;
     A.Cf = C.Cf;
     A.p2p_off = c->wl.p2p_off; A.p2p_src = c->wl.p2p_src; A.p2p_dir_cap = c->wl.p2p_dir_cap;
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;

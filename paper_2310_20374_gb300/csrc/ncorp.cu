@@ -95,7 +95,8 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.M, cap); dalloc(C.sx, cap); dalloc(C.sy, cap); dalloc(C.sz, cap);
     dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
     dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
-    dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.shift, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
+    dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
+    dalloc(C.item_base, cap);
     double *mh = nullptr, *ch = nullptr, *cf = nullptr;
     dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
     dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
@@ -166,9 +167,24 @@ void choose_parameters(ncorp_ctx *c, int p) {
     }
 }
 
+// Multipole work items: one per cell plus one per further P2M_ITEM_CHUNK
+// moonlets of the cell; a moonlet lies in at most MAX_LEVEL + 1 cells.
+void ensure_items(ncorp_ctx *c) {
+    Cells &C = c->cells;
+    const int64_t want = C.cap + (static_cast<int64_t>(MAX_LEVEL + 1) * c->n_cap) / P2M_ITEM_CHUNK + 64;
+    if (C.item_cap >= want) return;
+    dalloc(C.items, static_cast<size_t>(want));
+    double *part = nullptr;
+    dalloc(part, static_cast<size_t>(want) * num_m(MAXP));
+    if (C.part) cudaFree(C.part);
+    C.part = part;
+    C.item_cap = static_cast<int>(want);
+}
+
 void ensure_tree_capacity(ncorp_ctx *c, int n) {
     int want = std::max(4096, 4 * (n / std::max(1, c->s)) + 1024);
     if (c->cells.cap < want) alloc_cells(c, want);
+    ensure_items(c);
     const int cc = c->cells.cap;
     int front = std::max(1 << 16, 48 * cc), m2l = std::max(1 << 16, 64 * cc), p2p = std::max(1 << 16, 48 * cc);
     if (c->wl.front_cap < front || c->wl.m2l_cap < m2l || c->wl.p2p_cap < p2p || c->wl.self_cap < cc)
@@ -183,6 +199,7 @@ bool grow_after(ncorp_ctx *c, int err) {
     bool grew = false;
     if (err & ERR_CELLS) {
         alloc_cells(c, std::max(2 * c->cells.cap, c->ctl_h->n_cells + 1024));
+        ensure_items(c);
         grew = true;
     }
     WalkLists &W = c->wl;
@@ -812,7 +829,7 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
     dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
     dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
-    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.shift); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
     WalkLists &W = c->wl;
     dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
     dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);

@@ -263,7 +263,7 @@ struct ClimbArgs {
     int *first, *count, *child0, *nchild, *parent, *level, *arrive;
     uint32_t *cx, *cy, *cz;
     double *M, *sx, *sy, *sz, *rmax, *rcrit, *rho;
-    float4 *gh, *gl, *shift;
+    float4 *gh, *gl;
     void *Mh;
     float *rcf;
     const int *leaves;
@@ -398,44 +398,6 @@ __device__ __forceinline__ void p2m_add(real dx, real dy, real dz, real mu, real
             for (int c = 0; c <= k; c++) acc[midx(n - k, k - c, c)] += mu * px[n - k] * py[k - c] * pz[c];
 }
 
-// out[alpha] += sum_{gamma <= alpha, |gamma| != 1} l^(alpha-gamma)/(alpha-gamma)! r^|gamma| m[gamma],
-// l = (s_child - s_parent)/rho_parent, r = rho_child/rho_parent
-template <int P, typename real>
-__device__ __forceinline__ void m2m_add(const real *m, real lx, real ly, real lz, real r, real *out) {
-    real px[P], py[P], pz[P], pr[P];
-    px[0] = py[0] = pz[0] = pr[0] = real(1);
-#pragma unroll
-    for (int k = 1; k < P; k++) {
-        px[k] = px[k - 1] * lx;
-        py[k] = py[k - 1] * ly;
-        pz[k] = pz[k - 1] * lz;
-        pr[k] = pr[k - 1] * r;
-    }
-#pragma unroll
-    for (int n = 0; n < P; n++) {
-        if (n == 1) continue;
-#pragma unroll
-        for (int k = 0; k <= n; k++)
-#pragma unroll
-            for (int c = 0; c <= k; c++) {
-                const int a = n - k, b = k - c;
-                real acc = real(0);
-#pragma unroll
-                for (int ga = 0; ga <= a; ga++)
-#pragma unroll
-                    for (int gb = 0; gb <= b; gb++)
-#pragma unroll
-                        for (int gc = 0; gc <= c; gc++) {
-                            const int gn = ga + gb + gc;
-                            if (gn == 1) continue;
-                            acc += static_cast<real>(inv_mfact(a - ga, b - gb, c - gc)) * px[a - ga] * py[b - gb] *
-                                   pz[c - gc] * pr[gn] * m[midx(ga, gb, gc)];
-                        }
-                out[midx(a, b, c)] += acc;
-            }
-    }
-}
-
 template <int P, typename real>
 __device__ __forceinline__ void store_reduced(real *acc, real *dst, int lane) {
     constexpr int NM = num_m(P);
@@ -480,49 +442,17 @@ __device__ __forceinline__ double corner_warp(const Ctrl *ctl, int lev, uint32_t
     return dnorm3(d0, d1, d2);
 }
 
-// ---- gravity: P2M at the leaves, then parents (geometry, M2M, children's descent shifts)
-template <int P, typename real>
-__global__ void __launch_bounds__(32 * CLIMB_WARPS, 4) k_climb_gravity(ClimbArgs A) {
-    constexpr int NM = num_m(P);
+// ---- gravity geometry of the parents (Eqs. expansion_center, rmax_2, corner
+// cap): the last child to finish carries the climb to its parent.
+__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_geometry(ClimbArgs A) {
     __shared__ ClimbShared sh_all[CLIMB_WARPS];
     if (aborted(A.ctl)) return;
     ClimbShared &S = sh_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    real *Mh = static_cast<real *>(A.Mh);
     for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
         int c = A.leaves[gw];
-        {   // P2M (Eq. multipole_moment), scaled: M-hat_beta = sum mu (d/rho)^beta / beta!
-            const int f = A.first[c], cnt = A.count[c];
-            const float4 gh = A.gh[c], gl = A.gl[c];
-            const float ir = 1.0f / gl.w;
-            real acc[NM];
-#pragma unroll
-            for (int j = 0; j < NM; j++) acc[j] = real(0);
-            for (int k = lane; k < cnt; k += 32) {
-                if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
-                    const float4 h = A.hi4[f + k], l = A.lo4[f + k];
-                    p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
-                                     ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
-                } else {
-                    const double irho = 1.0 / A.rho[c];
-                    p2m_add<P, real>((A.x[f + k] - A.sx[c]) * irho, (A.y[f + k] - A.sy[c]) * irho,
-                                     (A.z[f + k] - A.sz[c]) * irho, A.G * A.m[f + k], acc);
-                }
-            }
-#pragma unroll
-            for (int n = 0; n < P; n++) {
-                if (n == 1) continue;
-#pragma unroll
-                for (int k = 0; k <= n; k++)
-#pragma unroll
-                    for (int cc = 0; cc <= k; cc++)
-                        acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
-            }
-            store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
-        }
-        // ---- climb
         while (true) {
             __threadfence();
             __syncwarp();
@@ -551,8 +481,8 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS, 4) k_climb_gravity(ClimbArgs
             const int plev = A.level[c];
             const double pcap = corner_warp(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
             if (pcap < rm) rm = pcap;
-            const double prho = cell_scale(A.ctl, plev, rm);
             if (lane == 0) {
+                const double prho = cell_scale(A.ctl, plev, rm);
                 A.M[c] = M2;
                 A.sx[c] = px;
                 A.sy[c] = py;
@@ -566,28 +496,107 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS, 4) k_climb_gravity(ClimbArgs
                 A.gh[c] = hi;
                 A.gl[c] = lo;
             }
-            const double ip = 1.0 / prho;   // exact: prho is a power of two
-            if (lane < nch) {   // descent shift of each child (used by L2L)
-                const double crho = __ldcg(&A.rho[c0 + lane]);
-                A.shift[c0 + lane] = make_float4(static_cast<float>((S.b[lane] - px) * ip),
-                                                 static_cast<float>((S.c[lane] - py) * ip),
-                                                 static_cast<float>((S.d[lane] - pz) * ip), static_cast<float>(crho * ip));
-            }
-            {   // M2M (App. C), one child per lane
-                real acc[NM];
+        }
+    }
+}
+
+// ---- multipoles (Eq. multipole_moment, scaled: M-hat_beta = sum mu (d/rho)^beta / beta!).
+// In exact arithmetic the M2M translation of App. C gives a parent the sum
+// of its moonlets' moments about its own centre, so every cell takes that
+// sum directly from its moonlets: no level waits for the one below.  A cell
+// is cut into chunks of P2M_CHUNK consecutive moonlets, one warp per chunk;
+// a cell of several chunks adds their sums in chunk order.
+constexpr int P2M_CHUNK = P2M_ITEM_CHUNK;
+
+struct P2MArgs {
+    const double *x, *y, *z, *m;
+    const float4 *hi4, *lo4;
+    const int *first, *count;
+    const double *sx, *sy, *sz, *rho;
+    const float4 *gh, *gl;
+    void *Mh;
+    void *part;        // [item_cap][num_m(p)]
+    int2 *items;       // (cell, chunk)
+    int *item_base;    // first item of each cell
+    int item_cap;
+    double G;
+    Ctrl *ctl;
+};
+
+__global__ void k_p2m_alloc(P2MArgs A) {
+    if (aborted(A.ctl)) return;
+    const int nc = A.ctl->n_cells;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const int nch = (A.count[i] + P2M_CHUNK - 1) / P2M_CHUNK;
+        const int base = atomicAdd(&A.ctl->n_items, nch);
+        A.item_base[i] = base;
+        if (base + nch > A.item_cap) {
+            atomicOr(&A.ctl->err, ERR_CELLS);
+            continue;
+        }
+        for (int j = 0; j < nch; j++) A.items[base + j] = make_int2(i, j);
+    }
+}
+
+template <int P, typename real>
+__global__ void __launch_bounds__(128) k_p2m(P2MArgs A) {
+    constexpr int NM = num_m(P);
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nitems = min(A.ctl->n_items, A.item_cap);
+    real *Mh = static_cast<real *>(A.Mh), *part = static_cast<real *>(A.part);
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
+        const int2 ij = A.items[it];
+        const int c = ij.x, cnt = A.count[c];
+        const int f = A.first[c] + ij.y * P2M_CHUNK, e = min(A.first[c] + cnt, f + P2M_CHUNK);
+        real acc[NM];
 #pragma unroll
-                for (int j = 0; j < NM; j++) acc[j] = real(0);
-                if (lane < nch) {
-                    const int ch = c0 + lane;
-                    real mc[NM];
-#pragma unroll
-                    for (int j = 0; j < NM; j++) mc[j] = __ldcg(&Mh[(size_t)ch * NM + j]);
-                    m2m_add<P, real>(mc, static_cast<real>((S.b[lane] - px) * ip), static_cast<real>((S.c[lane] - py) * ip),
-                                     static_cast<real>((S.d[lane] - pz) * ip),
-                                     static_cast<real>(__ldcg(&A.rho[ch]) * ip), acc);
-                }
-                store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
+        for (int j = 0; j < NM; j++) acc[j] = real(0);
+        if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
+            const float4 gh = A.gh[c], gl = A.gl[c];
+            const float ir = 1.0f / gl.w;   // exact: rho is a power of two
+            for (int k = f + lane; k < e; k += 32) {
+                const float4 h = A.hi4[k], l = A.lo4[k];
+                p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
+                                 ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
             }
+        } else {
+            const double irho = 1.0 / A.rho[c], sx = A.sx[c], sy = A.sy[c], sz = A.sz[c];
+            for (int k = f + lane; k < e; k += 32)
+                p2m_add<P, real>((A.x[k] - sx) * irho, (A.y[k] - sy) * irho, (A.z[k] - sz) * irho, A.G * A.m[k], acc);
+        }
+#pragma unroll
+        for (int n = 0; n < P; n++) {
+            if (n == 1) continue;
+#pragma unroll
+            for (int k = 0; k <= n; k++)
+#pragma unroll
+                for (int cc = 0; cc <= k; cc++)
+                    acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
+        }
+        const bool single = cnt <= P2M_CHUNK;
+        store_reduced<P, real>(acc, single ? Mh + (size_t)c * NM : part + (size_t)it * NM, lane);
+    }
+}
+
+template <int P, typename real>
+__global__ void k_p2m_finish(P2MArgs A) {
+    constexpr int NM = num_m(P);
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nc = A.ctl->n_cells;
+    real *Mh = static_cast<real *>(A.Mh);
+    const real *part = static_cast<const real *>(A.part);
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nwarps) {
+        const int nch = (A.count[c] + P2M_CHUNK - 1) / P2M_CHUNK;
+        if (nch <= 1) continue;
+        const int base = A.item_base[c];
+        for (int j = lane; j < NM; j += 32) {
+            real s = real(0);
+            for (int q = 0; q < nch; q++) s += part[(size_t)(base + q) * NM + j];
+            Mh[(size_t)c * NM + j] = s;
         }
     }
 }
@@ -628,12 +637,17 @@ __device__ double theta_of(double M, double Mtot, double tmin) {
     return th;
 }
 
+// One FP64 warp instruction costs the same whatever the number of active
+// lanes, so theta(M) is spread eight cells to a warp over many warps.
 __global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__ rmax, double *__restrict__ rcrit,
                         float4 *gh, const Ctrl *ctl, int cap, double tmin) {
     if (aborted(ctl)) return;
     const int nc = min(ctl->n_cells, cap);
     const double Mtot = M[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= 8) return;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8 + lane; i < nc; i += nwarps * 8) {
         const double rc = ddiv(rmax[i], theta_of(M[i], Mtot, tmin));
         rcrit[i] = rc;
         gh[i].w = static_cast<float>(rc);
@@ -641,8 +655,9 @@ __global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__
 }
 
 template <int P, typename real>
-static void climb_gravity_t(ncorp_ctx *c, const ClimbArgs &A) {
-    k_climb_gravity<P, real><<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
+static void p2m_t(ncorp_ctx *c, const P2MArgs &A) {
+    k_p2m<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_p2m_finish<P, real><<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
 }
 
 void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
@@ -652,27 +667,37 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild; A.parent = C.parent;
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.M = C.M; A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rmax = C.rmax; A.rcrit = C.rcrit; A.rho = C.rho;
-    A.gh = C.gh; A.gl = C.gl; A.shift = C.shift;
+    A.gh = C.gh; A.gl = C.gl;
     A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
     k_leaf_gravity<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
-#define NCORP_CLIMB_CASE(PP)                                             \
-    case PP:                                                             \
-        if (mixed) climb_gravity_t<PP, float>(c, A);                     \
-        else climb_gravity_t<PP, double>(c, A);                          \
+    k_climb_geometry<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
+    k_rcrit<<<16 * c->num_sms, 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+
+    P2MArgs B;
+    B.x = P.x; B.y = P.y; B.z = P.z; B.m = P.m; B.hi4 = P.hi4; B.lo4 = P.lo4;
+    B.first = C.first; B.count = C.count;
+    B.sx = C.sx; B.sy = C.sy; B.sz = C.sz; B.rho = C.rho; B.gh = C.gh; B.gl = C.gl;
+    B.Mh = C.Mh; B.part = C.part; B.items = C.items; B.item_base = C.item_base; B.item_cap = C.item_cap;
+    B.G = G; B.ctl = c->ctl;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_items, 0, sizeof(int), c->stream));
+    k_p2m_alloc<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(B); c->launches++;
+#define NCORP_P2M_CASE(PP)                     \
+    case PP:                                   \
+        if (mixed) p2m_t<PP, float>(c, B);     \
+        else p2m_t<PP, double>(c, B);          \
         break;
     switch (p) {
-        NCORP_CLIMB_CASE(1)
-        NCORP_CLIMB_CASE(2)
-        NCORP_CLIMB_CASE(3)
-        NCORP_CLIMB_CASE(4)
-        NCORP_CLIMB_CASE(5)
-        NCORP_CLIMB_CASE(6)
+        NCORP_P2M_CASE(1)
+        NCORP_P2M_CASE(2)
+        NCORP_P2M_CASE(3)
+        NCORP_P2M_CASE(4)
+        NCORP_P2M_CASE(5)
+        NCORP_P2M_CASE(6)
         default: break;
     }
-#undef NCORP_CLIMB_CASE
-    NCORP_CUDA_CHECK(cudaGetLastError());
-    k_rcrit<<<grid_for(C.cap, 64, 16 * c->num_sms), 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta); c->launches++;
+#undef NCORP_P2M_CASE
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
