@@ -252,7 +252,8 @@ def run_gpu(a):
                 "avg_launch_ms": round(eval_ms, 4),
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 FP32 lanes x 2 FLOPs x 2.07 GHz (not measured)"}
     last = {k: last_stats[k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self",
-                                      "p2p_interactions", "col_pairs", "col_tests")}
+                                      "p2p_interactions", "walk_iters", "col_pairs", "col_self", "col_tests",
+                                      "col_iters")}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4),

@@ -142,6 +142,7 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_M2L_DIRECTED 12  /* directed M2L entries evaluated */
 #define NCORP_STAT_P2P_DIRECTED 13  /* directed leaf-source entries evaluated */
 #define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
+#define NCORP_STAT_COL_ITERS   15   /* frontier iterations of the collision walk */
 #define NCORP_NSTATS           16
 int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
 

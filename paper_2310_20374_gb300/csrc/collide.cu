@@ -74,12 +74,16 @@ __device__ __forceinline__ bool may_touch(const float4 &h, const float4 &l, floa
 
 constexpr int COL_WARPS = 8;
 
-// Warp per direct item (a leaf with itself, or a pair of leaves): the source
-// leaf is staged in shared memory 32 moonlets at a time, every lane owns up to
-// two target moonlets.
+// Warp per direct item (a leaf with itself, or a pair of leaves).  The
+// source leaf is staged COL_STAGE moonlets at a time; the item's targets are
+// taken 32 at a time, m of them occupying T = pow2ceil(m) lanes, and the
+// warp's lanes form G = 32 / T groups: lane (g, t) tests target t against the
+// staged sources k = g, g + G, ...  so small leaves keep the lanes busy.
+constexpr int COL_STAGE = 64;
+
 __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
-    __shared__ float4 s_h[COL_WARPS][32], s_l[COL_WARPS][32];
-    __shared__ float s_r[COL_WARPS][32];
+    __shared__ float4 s_h[COL_WARPS][COL_STAGE], s_l[COL_WARPS][COL_STAGE];
+    __shared__ float s_r[COL_WARPS][COL_STAGE];
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
@@ -97,28 +101,31 @@ __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
         const bool self = ct == cs;
         const int ft = A.first[ct], nt = A.count[ct], fs = A.first[cs], nsrc = A.count[cs];
         if (lane == 0) tests += self ? static_cast<long long>(nt) * (nt - 1) / 2 : static_cast<long long>(nt) * nsrc;
-        for (int t0 = 0; t0 < nt; t0 += 64) {
-            const int u0 = t0 + lane, u1 = u0 + 32;
-            const bool a0 = u0 < nt, a1 = u1 < nt;
-            float4 th0 = make_float4(0, 0, 0, 0), tl0 = th0, th1 = th0, tl1 = th0;
-            float tr0 = 0.f, tr1 = 0.f;
-            if (a0) { th0 = A.hi4[ft + u0]; tl0 = A.lo4[ft + u0]; tr0 = A.rc[ft + u0]; }
-            if (a1) { th1 = A.hi4[ft + u1]; tl1 = A.lo4[ft + u1]; tr1 = A.rc[ft + u1]; }
-            for (int j0 = 0; j0 < nsrc; j0 += 32) {
-                const int lim = min(32, nsrc - j0);
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            const int m = min(32, nt - t0);
+            int lg = 0;
+            while ((1 << lg) < m) lg++;
+            const int T = 1 << lg, G = 32 >> lg, tt = lane & (T - 1), g = lane >> lg;
+            const int u = t0 + tt;
+            const bool act = tt < m;
+            float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+            float tr = 0.f;
+            if (act) { th = A.hi4[ft + u]; tl = A.lo4[ft + u]; tr = A.rc[ft + u]; }
+            for (int j0 = 0; j0 < nsrc; j0 += COL_STAGE) {
+                const int lim = min(COL_STAGE, nsrc - j0);
                 __syncwarp();
-                if (lane < lim) {
-                    s_h[wl][lane] = A.hi4[fs + j0 + lane];
-                    s_l[wl][lane] = A.lo4[fs + j0 + lane];
-                    s_r[wl][lane] = A.rc[fs + j0 + lane];
+                for (int k = lane; k < lim; k += 32) {
+                    s_h[wl][k] = A.hi4[fs + j0 + k];
+                    s_l[wl][k] = A.lo4[fs + j0 + k];
+                    s_r[wl][k] = A.rc[fs + j0 + k];
                 }
                 __syncwarp();
-                for (int k = 0; k < lim; k++) {
-                    const int v = j0 + k;
-                    const float4 h = s_h[wl][k], l = s_l[wl][k];
-                    const float r = s_r[wl][k];
-                    if (a0 && (!self || v > u0) && may_touch(h, l, r, th0, tl0, tr0)) test_and_emit(A, ft + u0, fs + v);
-                    if (a1 && (!self || v > u1) && may_touch(h, l, r, th1, tl1, tr1)) test_and_emit(A, ft + u1, fs + v);
+                if (act) {
+                    for (int k = g; k < lim; k += G) {
+                        const int v = j0 + k;
+                        if ((!self || v > u) && may_touch(s_h[wl][k], s_l[wl][k], s_r[wl][k], th, tl, tr))
+                            test_and_emit(A, ft + u, fs + v);
+                    }
                 }
             }
         }

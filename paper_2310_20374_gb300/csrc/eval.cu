@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
 // G = EV_THREADS / T groups: thread (g, t) sums the staged sources
 // k = g, g + G, g + 2G, ... for target t, so a leaf of a few moonlets keeps
 // all lanes busy.  The G partial sums of a target are then added in group
-// order (the result does not depend on timing).  The direct list is staged
+// order.  The direct list is staged
 // EV_BUF moonlets at a time, cutting source leaves where the buffer ends.
 // ---------------------------------------------------------------------------
 constexpr int EV_THREADS = 128;

@@ -380,11 +380,13 @@ void record_stats(ncorp_ctx *c, bool grav) {
         c->stats[NCORP_STAT_P2P_INTER] = h.n_inter;
         c->stats[NCORP_STAT_M2L_DIRECTED] = h.n_m2l_dir;
         c->stats[NCORP_STAT_P2P_DIRECTED] = h.n_p2p_dir;
-    } else {
-        c->stats[NCORP_STAT_COL_PAIRS] = h.dec_pairs;
-        c->stats[NCORP_STAT_COL_SELF] = h.dec_self;
+    }
+    if (!grav || c->cfg.collisions) {
+        c->stats[NCORP_STAT_COL_PAIRS] = h.col_pairs;
+        c->stats[NCORP_STAT_COL_SELF] = h.col_self;
         c->stats[NCORP_STAT_COL_TESTS] = h.n_tests;
         c->stats[NCORP_STAT_COL_FOUND] = h.n_found;
+        c->stats[NCORP_STAT_COL_ITERS] = h.col_iters;
     }
 }
 

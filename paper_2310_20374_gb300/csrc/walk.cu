@@ -234,6 +234,11 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.ctl->walk_iters = it;
+        if (!A.gravity) {
+            A.ctl->col_pairs = A.ctl->dec_pairs;
+            A.ctl->col_self = A.ctl->dec_self;
+            A.ctl->col_iters = it;
+        }
         if (it >= WALK_MAX_ITERS) atomicOr(&A.ctl->err, ERR_FRONTIER);
     }
 }
