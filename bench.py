@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s, falcON p=6 gravity+collisions; p50/p99 step latency mixed-N"
 UNIT = "particle-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 (FMA) x max SM clock (GHz) -> TFLOP/s
+# DRAM bytes (read + write) of one k_eval launch on this workload, from one ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
+# set to None whenever the kernel changes until it is captured again.
+EVAL_DRAM_BYTES_PER_LAUNCH = 8.32e6
 
 
 def parse():
@@ -247,7 +251,7 @@ def run_gpu(a):
     achieved = flops_eval / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_eval (L2P + near-field direct sum + external forces)",
                 "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": EVAL_DRAM_BYTES_PER_LAUNCH,
                 "flops_per_launch": flops_eval, "directed_pairs_per_launch": directed,
                 "avg_launch_ms": round(eval_ms, 4),
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 FP32 lanes x 2 FLOPs x 2.07 GHz (not measured)"}
