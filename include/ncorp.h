@@ -144,6 +144,9 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
 #define NCORP_STAT_COL_ITERS   15   /* frontier iterations of the collision walk */
 #define NCORP_NSTATS           16
+
+/* Writes min(n_stats, NCORP_NSTATS) counters of the last call (slots above)
+ * to host memory stats[].  NCORP_EINVAL if ctx or stats is NULL. */
 int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
 
 /* Stage timers.  With profiling on, every call records CUDA events on the
@@ -152,15 +155,21 @@ int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
  * runs more than once).  Off by default; on costs a few event records. */
 #define NCORP_STAGE_SORT     0   /* bounding box, keys, radix sort, gather */
 #define NCORP_STAGE_BUILD    1   /* octree build, leaf list */
-#define NCORP_STAGE_CLIMB    2   /* gravity climb: geometry, P2M, M2M, theta(M), r_crit */
+#define NCORP_STAGE_CLIMB    2   /* gravity climb: geometry, theta(M), r_crit, multipoles */
 #define NCORP_STAGE_WALK     3   /* gravity walk and per-target lists */
 #define NCORP_STAGE_M2L      4
-#define NCORP_STAGE_DESCEND  5   /* L2L from the root */
+#define NCORP_STAGE_DESCEND  5   /* complete local expansions (Eq. shifting from the ancestors) */
 #define NCORP_STAGE_EVAL     6   /* L2P, near field, external forces */
 #define NCORP_STAGE_COLLIDE  7   /* collision climb, walk and pair test */
 #define NCORP_STAGE_KDK      8   /* kicks, drift, host/device copies of the state */
 #define NCORP_NSTAGES        9
+
+/* Turns the stage timers on (enable != 0) or off.  NCORP_EINVAL if ctx is NULL. */
 int ncorp_profile(ncorp_ctx *ctx, int enable);
+
+/* Writes min(n, NCORP_NSTAGES) stage times of the last call, in milliseconds,
+ * to host memory ms[] (zeros while profiling is off).  NCORP_EINVAL if ctx or
+ * ms is NULL or n < 0. */
 int ncorp_stage_times(ncorp_ctx *ctx, double *ms, int n);
 
 /* Diagnostic export of the tree of the last ncorp_accel/ncorp_collide/ncorp_step
@@ -199,6 +208,42 @@ void ncorp_free(ncorp_ctx *ctx);
 
 /* Message of the last failure on ctx (static storage owned by ctx; never NULL). */
 const char *ncorp_last_error(const ncorp_ctx *ctx);
+
+/* Largest n accepted by ncorp_hilbert_sort_static. */
+#define NCORP_STATIC_MAX_N 65536
+
+/* Hilbert keys of n moonlets and their stable sort, without allocating any
+ * memory: the key and sort stages of a step (root cube, 21-bit quantisation
+ * and 63-bit 3-D Hilbert keys of Sect. 3.4.6, then the stable radix sort by
+ * (key, index)).  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory once they are set up (a fixed
+ * device-memory budget, or a loop in which the implicit synchronisation of
+ * cudaMalloc/cudaFree is not acceptable), and needs no context.
+ *   positions [n][3] double, device memory of the current device (read)
+ *   keys      [n] uint64, device (written): sorted keys, ascending
+ *   order     [n] int64, device (written): order[i] = the index (row of
+ *             positions) of the moonlet with the i-th smallest key; equal keys
+ *             keep increasing index order
+ *   cuda_stream: the stream the work is enqueued on (NULL: legacy default);
+ *             the call synchronises it before returning, to read the status.
+ * Results are bit-identical to the keys and order that ncorp_tree_export
+ * reports after ncorp_accel on the same positions.
+ * Scratch: one file-scope device array per device, sized for
+ * NCORP_STATIC_MAX_N moonlets (about 3.4 MB); nothing is allocated or freed.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make one call on each
+ * device before any stream capture that is to contain this function.
+ * The array keeps the contents of the last call; each call first resets the
+ * parts that must start at zero (bounding-box accumulators, status word,
+ * barrier counter) and overwrites everything else before reading it.
+ * Calls whose device work overlaps (from several streams or host threads on
+ * the same device) share that array and race: serialise them.
+ * Errors: NCORP_EINVAL if n < 1, n > NCORP_STATIC_MAX_N, a pointer is NULL or
+ * not device memory of the current device (all before any device work), or a
+ * position is not finite; NCORP_ETIMEOUT if the sort's grid barrier timed
+ * out; NCORP_ECUDA if a CUDA call failed. */
+int ncorp_hilbert_sort_static(const double *positions, int64_t n, uint64_t *keys, int64_t *order,
+                              void *cuda_stream);
 
 #ifdef __cplusplus
 }

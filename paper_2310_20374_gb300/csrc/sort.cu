@@ -8,7 +8,9 @@
 // position) with a stable radix sort, so that every cell of every level owns
 // a contiguous range of moonlets and consecutive cells of a level are
 // consecutive along the curve.
+#include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 #include "ctx.h"
 
@@ -485,4 +487,129 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free keys + sort (ncorp_hilbert_sort_static): the same kernels
+// as the step's key and sort stages, with every scratch buffer in one
+// file-scope device array.
+// ---------------------------------------------------------------------------
+constexpr int STATIC_MAX_N = NCORP_STATIC_MAX_N;
+constexpr int STATIC_TILES = (STATIC_MAX_N + RS_TILE - 1) / RS_TILE;
+
+struct StaticScratch {
+    Ctrl ctl;                          // bounding box, status word, barrier
+    double x[STATIC_MAX_N], y[STATIC_MAX_N], z[STATIC_MAX_N];
+    uint64_t key_alt[STATIC_MAX_N];
+    uint32_t idx[STATIC_MAX_N], idx_alt[STATIC_MAX_N];
+    uint32_t qx[STATIC_MAX_N], qy[STATIC_MAX_N], qz[STATIC_MAX_N];
+    int hist[256 * STATIC_TILES + 256];
+};
+
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+__global__ void k_static_reset(StaticScratch *S) {
+    Ctrl &c = S->ctl;
+    c.err = 0;
+    c.bar_count = 0;
+    for (int k = 0; k < 3; k++) {
+        c.bbox[k] = ~0ull;
+        c.bbox[3 + k] = 0ull;
+    }
+}
+
+__global__ void k_static_split(const double *__restrict__ pos, StaticScratch *S, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        S->x[i] = pos[3 * i];
+        S->y[i] = pos[3 * i + 1];
+        S->z[i] = pos[3 * i + 2];
+    }
+}
+
+__global__ void k_static_order(const StaticScratch *S, int64_t *order, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        order[i] = static_cast<int64_t>(S->idx[i]);
+}
+
+struct StaticDevice {
+    StaticScratch *ptr = nullptr;
+    int num_sms = 0;
+    int radix_per_sm = 0;
+};
+
+static std::mutex g_static_mutex;
+static StaticDevice g_static_dev[128];
+
+// Per-device set-up, done once with the device current.
+static cudaError_t static_setup(int dev, StaticDevice &out) {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    StaticDevice &d = g_static_dev[dev];
+    if (!d.ptr) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix), RS_T, 0);
+        if (e != cudaSuccess) return e;
+        d.num_sms = sms;
+        d.radix_per_sm = std::max(1, std::min(per_sm, 2));
+        d.ptr = static_cast<StaticScratch *>(p);
+    }
+    out = d;
+    return cudaSuccess;
+}
+
+static bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace ncorp
+
+extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, uint64_t *keys, int64_t *order,
+                                         void *cuda_stream) {
+    using namespace ncorp;
+    if (n64 < 1 || n64 > STATIC_MAX_N || !positions || !keys || !order) return NCORP_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return NCORP_ECUDA;
+    if (!on_device(positions, dev) || !on_device(keys, dev) || !on_device(order, dev)) return NCORP_EINVAL;
+    StaticDevice d;
+    if (static_setup(dev, d) != cudaSuccess) return NCORP_ECUDA;
+    const int n = static_cast<int>(n64);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    StaticScratch *S = d.ptr;
+    const int g = std::max(1, std::min((n + 255) / 256, 4 * d.num_sms));
+    k_static_reset<<<1, 1, 0, s>>>(S);
+    k_static_split<<<g, 256, 0, s>>>(positions, S, n);
+    k_bbox<<<g, 256, 0, s>>>(S->x, S->y, S->z, n, &S->ctl);
+    k_keys<<<g, 256, 0, s>>>(S->x, S->y, S->z, n, &S->ctl, keys, S->idx, S->qx, S->qy, S->qz);
+    if (cudaGetLastError() != cudaSuccess) return NCORP_ECUDA;
+    if (n > 1) {
+        RadixArgs A;
+        A.k0 = keys; A.k1 = S->key_alt; A.v0 = S->idx; A.v1 = S->idx_alt;
+        A.n = n;
+        A.ntiles = (n + RS_TILE - 1) / RS_TILE;
+        A.passes = 8;   // 3 x 21 key bits, rounded up to an even number of 8-bit passes
+        A.hist = S->hist;
+        A.rowsum = S->hist + 256 * A.ntiles;
+        A.ctl = &S->ctl;
+        const int grid = std::min(A.ntiles, d.radix_per_sm * d.num_sms);
+        void *args[] = {&A};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args, 0, s) !=
+            cudaSuccess)
+            return NCORP_ECUDA;
+    }
+    k_static_order<<<g, 256, 0, s>>>(S, order, n);
+    if (cudaGetLastError() != cudaSuccess) return NCORP_ECUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, &S->ctl.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NCORP_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NCORP_ECUDA;
+    if (err & ERR_NONFINITE) return NCORP_EINVAL;
+    if (err & ERR_TIMEOUT) return NCORP_ETIMEOUT;
+    return NCORP_OK;
+}

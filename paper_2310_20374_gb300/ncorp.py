@@ -70,12 +70,14 @@ def load(path: str | None = None):
     L.ncorp_expansions.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(ip)]
     L.ncorp_profile.argtypes = [vp, ip]
     L.ncorp_stage_times.argtypes = [vp, C.POINTER(dbl), ip]
+    L.ncorp_hilbert_sort_static.argtypes = [vp, i64, vp, vp, vp]
     L.ncorp_free.argtypes = [vp]
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
-                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times"):
+                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
+                 "ncorp_hilbert_sort_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -199,6 +201,20 @@ def ncorp_stage_times(ctx) -> dict:
     arr = (C.c_double * len(STAGE_NAMES))()
     _check(ctx, load().ncorp_stage_times(ctx, arr, len(STAGE_NAMES)))
     return dict(zip(STAGE_NAMES, (float(v) for v in arr)))
+
+
+NCORP_STATIC_MAX_N = 65536
+
+
+def ncorp_hilbert_sort_static(positions, n, keys, order, stream=None):
+    """Allocation-free keys + stable sort (device arrays only); raises NcorpError on failure."""
+    st = load().ncorp_hilbert_sort_static(_ptr(positions), int(n), _ptr(keys), _ptr(order), _ptr(stream))
+    if st != NCORP_OK:
+        why = {NCORP_EINVAL: f"invalid argument (n must be 1..{NCORP_STATIC_MAX_N}, arrays device memory of the "
+                             f"current device, positions finite)",
+               NCORP_ETIMEOUT: "grid barrier timed out", NCORP_ECUDA: "CUDA call failed"}.get(st, "")
+        raise NcorpError(st, why)
+    return st
 
 
 def ncorp_free(ctx):

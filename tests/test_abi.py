@@ -3,6 +3,7 @@ every function include/ncorp.h declares, and rejects bad arguments before any
 device work."""
 import ctypes as C
 import os
+import re
 import subprocess
 
 import pytest
@@ -57,5 +58,6 @@ def test_header_documents_every_entry_point():
     with open(ncorp.HEADER) as f:
         text = f.read()
     for name in ncorp.declared_functions():
-        i = text.index(name + "(")
-        assert "/*" in text[max(0, i - 1500):i], f"{name} has no comment"
+        m = re.search(r"^(?:const )?[a-z_0-9]+ \**" + name + r"\(", text, re.M)   # the declaration line
+        assert m, f"{name} has no declaration line"
+        assert text[:m.start()].rstrip().endswith("*/"), f"{name} has no comment right above it"
