@@ -209,6 +209,72 @@ void ncorp_free(ncorp_ctx *ctx);
 /* Message of the last failure on ctx (static storage owned by ctx; never NULL). */
 const char *ncorp_last_error(const ncorp_ctx *ctx);
 
+/* ---- Batches: many independent disks on one GPU ----------------------------
+ * A batch owns one resident state per disk and advances all of them together:
+ * ncorp_batch_run enqueues the steps of every disk on a pool of CUDA streams
+ * and waits once, so the kernels of different disks overlap on the GPU.  Each
+ * disk is integrated exactly as by ncorp_step (the same SBAB1 step of
+ * Sect. 4.1 with the falcON forces and the collision search of Sect. 3.1).
+ * A batch is not thread-safe: call it from one host thread at a time. */
+typedef struct ncorp_batch ncorp_batch;
+
+/* Creates an empty batch on the current CUDA device; every disk uses cfg
+ * (copied).  hbm_budget_bytes caps the device memory the batch's disks may
+ * take (0: no cap); cuda_stream is the caller's stream: ncorp_batch_run starts
+ * after the work queued on it so far, and work queued on it later starts after
+ * the run.  NCORP_EINVAL for NULL arguments or an invalid precision. */
+int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Adds a disk of n moonlets: positions/velocities [n][3], masses/radii [n],
+ * host or device arrays (copied; the caller keeps ownership); p, theta and
+ * dt as for ncorp_step, fixed for the disk.  Computes the disk's tree and
+ * acceleration (one synchronous force evaluation).  *disk_id receives the
+ * disk's id (unique within the batch).  Errors: NCORP_EINVAL (arguments,
+ * non-finite input), NCORP_ENOMEM (allocation failed, or the disk would exceed
+ * the batch's device-memory budget), NCORP_ECUDA, NCORP_EOVERFLOW,
+ * NCORP_ETIMEOUT; on error no disk is added. */
+int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *velocities, const double *masses,
+                         const double *radii, int64_t n, int p, double theta, double dt, int32_t *disk_id);
+
+/* Advances every disk by n_steps SBAB1 steps (Sect. 4.1) and waits for them.
+ * If an internal buffer of some disk overflowed during the run, that disk is
+ * rerun from its state at the start of the run one synchronous step at a
+ * time with grown buffers (counted in NCORP_BATCH_FALLBACKS).  The colliding
+ * pairs of each disk's last step are kept for ncorp_batch_collisions.
+ * Errors: NCORP_EINVAL (n_steps < 0, non-finite state), NCORP_ECUDA,
+ * NCORP_ETIMEOUT, NCORP_EOVERFLOW. */
+int ncorp_batch_run(ncorp_batch *b, int n_steps);
+
+/* Copies a disk's current state, in the order it was given, into
+ * positions/velocities [n][3] (host or device).  NCORP_EINVAL for an unknown id. */
+int ncorp_batch_get_state(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities);
+
+/* Colliding pairs of a disk's last step, as ncorp_collisions gives them. */
+int ncorp_batch_collisions(ncorp_batch *b, int32_t disk_id, int64_t *pairs, int64_t cap, int64_t *n_pairs);
+
+/* Removes a disk and releases its device memory; if positions and
+ * velocities are given (both or neither), the disk's final state is copied
+ * there first, as by ncorp_batch_get_state.  NCORP_EINVAL for an unknown id. */
+int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities);
+
+/* Batch counters (int64 slots): */
+#define NCORP_BATCH_DISKS      0   /* disks in the batch */
+#define NCORP_BATCH_MOONLETS   1   /* moonlets over all disks */
+#define NCORP_BATCH_BYTES      2   /* device bytes taken by the disks */
+#define NCORP_BATCH_STREAMS    3   /* streams the disks are spread over */
+#define NCORP_BATCH_FALLBACKS  4   /* disk reruns after a buffer overflow, since creation */
+#define NCORP_BATCH_LAUNCHES   5   /* kernels launched by the last run */
+#define NCORP_BATCH_NINFO      6
+
+/* Writes min(n_info, NCORP_BATCH_NINFO) batch counters to host memory info[]. */
+int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info);
+
+/* Releases the batch and all its disks (NULL is ignored). */
+void ncorp_batch_free(ncorp_batch *b);
+
+/* Message of the last failure of a batch call (never NULL). */
+const char *ncorp_batch_last_error(const ncorp_batch *b);
+
 /* Largest n accepted by ncorp_hilbert_sort_static. */
 #define NCORP_STATIC_MAX_N 65536
 

@@ -64,6 +64,11 @@ struct WalkLists {
 constexpr int WALK_MAX_ITERS = 96;
 constexpr int P2M_ITEM_CHUNK = 512;   // moonlets per multipole work item
 
+// Grid of a cooperative launch: the given blocks per SM, capped by the
+// context's limit so that the cooperative grids of contexts driven on
+// concurrent streams fit on the device together.
+inline int coop_blocks(const ncorp_ctx *c, int per_sm);
+
 }  // namespace ncorp
 
 struct ncorp_ctx {
@@ -71,6 +76,7 @@ struct ncorp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    int coop_max = 0;               // cap on cooperative grid sizes (0: none); set when contexts run concurrently
     char err[512] = {0};
 
     int64_t n_cap = 0;
@@ -195,3 +201,9 @@ inline int grid_for(int n, int block, int max_blocks = 1 << 20) {
 }
 
 }  // namespace ncorp
+
+inline int ncorp::coop_blocks(const ncorp_ctx *c, int per_sm) {
+    int g = per_sm * c->num_sms;
+    if (c->coop_max > 0 && g > c->coop_max) g = c->coop_max;
+    return g < 1 ? 1 : g;
+}

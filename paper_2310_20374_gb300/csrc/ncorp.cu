@@ -366,6 +366,21 @@ void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const doub
     launch_collide(c, S, vx, vy, vz, dt);
 }
 
+// One SBAB1 step of the resident state A (its tree and acceleration valid):
+// half kick, collision search on A's tree, drift, new tree, gravity, half
+// kick.  The new state is left in Cset (not yet swapped with A), nothing is
+// copied to the caller and nothing waits: the caller reads the status.
+void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt) {
+    const double h = 0.5 * dt;
+    ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
+    { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n); }
+    if (c->cfg.collisions) collisions(c, A, B.vx, B.vy, B.vz, dt);
+    { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
+    build_tree(c, B, B, A, Cn, n);
+    gravity(c, Cn, p, theta, c->time + dt, false);
+    { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n); }
+}
+
 void record_stats(ncorp_ctx *c, bool grav) {
     const Ctrl &h = *c->ctl_h;
     c->stats[NCORP_STAT_LAUNCHES] = c->launches;
@@ -572,7 +587,6 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                               c->last_p == p && c->last_theta == theta;
         ensure_particles(c, n);
         choose_parameters(c, p);
-        const double h = 0.5 * dt;
         bool have = resident && c->have_state;
         bool tree = resident;
         for (int attempt = 0;; attempt++) {
@@ -593,15 +607,10 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                 std::swap(c->A, c->Cset);
                 gravity(c, c->A, p, theta, c->time, false);
             }
-            ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
-            { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n); }
-            if (c->cfg.collisions) collisions(c, A, B.vx, B.vy, B.vz, dt);
-            { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
-            build_tree(c, B, B, A, Cn, n);
-            gravity(c, Cn, p, theta, c->time + dt, false);
+            enqueue_kdk(c, n, p, theta, dt);
             {
                 Stage st(c, NCORP_STAGE_KDK);
-                launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n);
+                ParticleSet &Cn = c->Cset;
                 download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
                 download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
             }
@@ -849,6 +858,341 @@ void ncorp_free(ncorp_ctx *c) {
 const char *ncorp_last_error(const ncorp_ctx *c) {
     if (!c) return "null context";
     return c->err[0] ? c->err : "no error";
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches of independent disks.  Every disk keeps its own context (state,
+// tree, lists); the batch drives the contexts on a pool of streams, enqueuing
+// the steps of all disks before it waits once, so that the disks' kernels
+// overlap on the GPU.  The cooperative grids of every context are capped so
+// that those of all streams fit on the device at the same time.
+// ===========================================================================
+namespace {
+
+constexpr int BATCH_STREAMS = 8;
+
+struct BatchDisk {
+    int32_t id = 0;
+    ncorp_ctx *c = nullptr;
+    int64_t n = 0;
+    int p = 0;
+    double theta = 0.5, dt = 0.0;
+    int stream = 0;
+    double *pos = nullptr, *vel = nullptr, *m = nullptr, *R = nullptr;   // owned, caller order
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ncorp_batch {
+    ncorp_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t user = nullptr;
+    size_t budget = 0, used = 0;
+    cudaStream_t pool[BATCH_STREAMS] = {};
+    int64_t load[BATCH_STREAMS] = {};
+    cudaEvent_t ev_start = nullptr, ev_done[BATCH_STREAMS] = {};
+    std::vector<BatchDisk> disks;
+    int32_t next_id = 0;
+    int64_t fallbacks = 0;
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+int batch_fail(ncorp_batch *b, int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+BatchDisk *find_disk(ncorp_batch *b, int32_t id) {
+    for (auto &d : b->disks)
+        if (d.id == id) return &d;
+    return nullptr;
+}
+
+void release_disk(BatchDisk &d) {
+    if (d.c) ncorp_free(d.c);
+    d.c = nullptr;
+    dfree(d.pos); dfree(d.vel); dfree(d.m); dfree(d.R);
+}
+
+// Tree and acceleration of the disk's initial state (what the first
+// ncorp_step of a context computes before stepping), with the usual growth
+// and retry; leaves the context resident.
+int prime_disk(ncorp_ctx *c, BatchDisk &d) {
+    const int n = static_cast<int>(d.n);
+    ensure_particles(c, n);
+    choose_parameters(c, d.p);
+    for (int attempt = 0;; attempt++) {
+        begin_call(c);
+        ensure_tree_capacity(c, n);
+        reset_ctl(c);
+        ParticleSet &A = c->A;
+        upload_vec(c, d.pos, A.x, A.y, A.z, n);
+        upload_vec(c, d.vel, A.vx, A.vy, A.vz, n);
+        upload_scalar(c, d.m, A.m, n);
+        upload_scalar(c, d.R, A.R, n);
+        launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+        build_tree(c, c->A, c->A, c->A, c->Cset, n);
+        std::swap(c->A, c->Cset);
+        gravity(c, c->A, d.p, d.theta, c->time, false);
+        const int err = finish(c);
+        if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
+        if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+        if (err == 0) break;
+        if (attempt >= MAX_RETRIES || !grow_after(c, err))
+            return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+    }
+    c->n = n;
+    c->have_state = true;
+    c->tree_valid = true;
+    c->tree_kind = 1;
+    c->last_pos = d.pos;
+    c->last_vel = d.vel;
+    c->last_m = d.m;
+    c->last_R = d.R;
+    c->last_p = d.p;
+    c->last_theta = d.theta;
+    c->n_found = 0;
+    return NCORP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_budget_bytes, void *cuda_stream) {
+    if (!out || !cfg) return NCORP_EINVAL;
+    *out = nullptr;
+    if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
+    ncorp_batch *b = new (std::nothrow) ncorp_batch();
+    if (!b) return NCORP_ENOMEM;
+    b->cfg = *cfg;
+    b->budget = hbm_budget_bytes;
+    b->user = static_cast<cudaStream_t>(cuda_stream);
+    bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
+              cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int s = 0; ok && s < BATCH_STREAMS; s++)
+        ok = cudaStreamCreateWithFlags(&b->pool[s], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_done[s], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        ncorp_batch_free(b);
+        return NCORP_ECUDA;
+    }
+    *out = b;
+    return NCORP_OK;
+}
+
+int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *velocities, const double *masses,
+                         const double *radii, int64_t n, int p, double theta, double dt, int32_t *disk_id) {
+    if (!b) return NCORP_EINVAL;
+    if (!positions || !velocities || !masses || !radii || !disk_id)
+        return batch_fail(b, NCORP_EINVAL, "null pointer");
+    if (n < 1 || n > (int64_t(1) << 30)) return batch_fail(b, NCORP_EINVAL, "n = %lld out of range", (long long)n);
+    if (p < 1 || p > MAXP) return batch_fail(b, NCORP_EINVAL, "p = %d outside 1..6", p);
+    if (!(theta > 0.0 && theta < 1.0)) return batch_fail(b, NCORP_EINVAL, "theta = %g outside (0, 1)", theta);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return batch_fail(b, NCORP_EINVAL, "dt must be > 0");
+    if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, NCORP_ECUDA, "cudaSetDevice failed");
+    int s = 0;
+    for (int k = 1; k < BATCH_STREAMS; k++)
+        if (b->load[k] < b->load[s]) s = k;
+    BatchDisk d;
+    d.id = b->next_id;
+    d.n = n;
+    d.p = p;
+    d.theta = theta;
+    d.dt = dt;
+    d.stream = s;
+    size_t free0 = 0, free1 = 0, total = 0;
+    cudaMemGetInfo(&free0, &total);
+    int st = ncorp_init(&d.c, &b->cfg, n, b->device, b->pool[s]);
+    if (st != NCORP_OK) return batch_fail(b, st, "context for disk of %lld moonlets: allocation failed", (long long)n);
+    d.c->coop_max = std::max(8, 2 * b->num_sms / BATCH_STREAMS);
+    try {
+        dalloc(d.pos, 3 * n);
+        dalloc(d.vel, 3 * n);
+        dalloc(d.m, n);
+        dalloc(d.R, n);
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, cudaMemcpyDefault, b->pool[s]));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.vel, velocities, sizeof(double) * 3 * n, cudaMemcpyDefault, b->pool[s]));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.m, masses, sizeof(double) * n, cudaMemcpyDefault, b->pool[s]));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.R, radii, sizeof(double) * n, cudaMemcpyDefault, b->pool[s]));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(b->pool[s]));
+    } catch (const CudaError &e) {
+        release_disk(d);
+        return batch_fail(b, e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA, "%s: %s", e.expr,
+                          cudaGetErrorString(e.code));
+    }
+    cudaMemGetInfo(&free1, &total);
+    d.bytes = free0 > free1 ? free0 - free1 : 0;
+    if (b->budget && b->used + d.bytes > b->budget) {
+        release_disk(d);
+        return batch_fail(b, NCORP_ENOMEM, "device-memory budget exceeded: %zu + %zu > %zu bytes", b->used, d.bytes,
+                          b->budget);
+    }
+    try {
+        st = prime_disk(d.c, d);
+    } catch (const CudaError &e) {
+        st = fail(d.c, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
+    }
+    if (st != NCORP_OK) {
+        batch_fail(b, st, "disk of %lld moonlets: %s", (long long)n, ncorp_last_error(d.c));
+        release_disk(d);
+        return st;
+    }
+    b->used += d.bytes;
+    b->load[s] += n;
+    b->disks.push_back(d);
+    b->next_id++;
+    *disk_id = d.id;
+    return NCORP_OK;
+}
+
+int ncorp_batch_run(ncorp_batch *b, int n_steps) {
+    if (!b) return NCORP_EINVAL;
+    if (n_steps < 0) return batch_fail(b, NCORP_EINVAL, "n_steps < 0");
+    if (n_steps == 0 || b->disks.empty()) return NCORP_OK;
+    std::vector<double> t0(b->disks.size());
+    b->launches = 0;
+    try {
+        NCORP_CUDA_CHECK(cudaSetDevice(b->device));
+        NCORP_CUDA_CHECK(cudaEventRecord(b->ev_start, b->user));
+        for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamWaitEvent(b->pool[s], b->ev_start, 0));
+        for (size_t i = 0; i < b->disks.size(); i++) {
+            BatchDisk &d = b->disks[i];
+            ncorp_ctx *c = d.c;
+            c->stream = b->pool[d.stream];
+            t0[i] = c->time;
+            begin_call(c);
+            choose_parameters(c, d.p);
+            // state at the start of the run, kept in the disk's own arrays for a rerun
+            download_vec(c, c->A.x, c->A.y, c->A.z, c->A.perm, d.pos, static_cast<int>(d.n), c->stage);
+            download_vec(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, d.vel, static_cast<int>(d.n), c->stage2);
+            reset_ctl(c);
+        }
+        for (int k = 0; k < n_steps; k++)
+            for (auto &d : b->disks) {
+                ncorp_ctx *c = d.c;
+                NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_found, 0, sizeof(int), c->stream));
+                enqueue_kdk(c, static_cast<int>(d.n), d.p, d.theta, d.dt);
+                std::swap(c->A, c->Cset);
+                c->time += d.dt;
+            }
+        for (auto &d : b->disks)
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(d.c->ctl_h, d.c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, d.c->stream));
+        for (int s = 0; s < BATCH_STREAMS; s++) {
+            NCORP_CUDA_CHECK(cudaEventRecord(b->ev_done[s], b->pool[s]));
+            NCORP_CUDA_CHECK(cudaStreamWaitEvent(b->user, b->ev_done[s], 0));
+        }
+        for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamSynchronize(b->pool[s]));
+    } catch (const CudaError &e) {
+        for (auto &d : b->disks) {
+            d.c->have_state = false;
+            d.c->tree_valid = false;
+        }
+        return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
+    }
+    for (size_t i = 0; i < b->disks.size(); i++) {
+        BatchDisk &d = b->disks[i];
+        ncorp_ctx *c = d.c;
+        b->launches += c->launches;
+        const int err = c->ctl_h->err;
+        if (err == 0) {
+            c->n_found = c->cfg.collisions ? c->ctl_h->n_found : 0;
+            c->pairs_sorted = false;
+            record_stats(c, true);
+            c->stats[NCORP_STAT_COL_FOUND] = c->n_found;
+            continue;
+        }
+        // A list overflowed or a barrier gave up in some step: rerun this disk's
+        // steps from the saved state, one synchronous step at a time (buffers
+        // grow as needed).
+        b->fallbacks++;
+        c->time = t0[i];
+        c->have_state = false;
+        c->tree_valid = false;
+        for (int k = 0; k < n_steps; k++) {
+            const int st = ncorp_step(c, d.pos, d.vel, d.m, d.R, d.n, d.p, d.theta, d.dt);
+            if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", d.id, ncorp_last_error(c));
+        }
+    }
+    return NCORP_OK;
+}
+
+int ncorp_batch_get_state(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities) {
+    if (!b) return NCORP_EINVAL;
+    BatchDisk *d = find_disk(b, disk_id);
+    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    const int st = ncorp_get_state(d->c, positions, velocities);
+    if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
+    return NCORP_OK;
+}
+
+int ncorp_batch_collisions(ncorp_batch *b, int32_t disk_id, int64_t *pairs, int64_t cap, int64_t *n_pairs) {
+    if (!b) return NCORP_EINVAL;
+    BatchDisk *d = find_disk(b, disk_id);
+    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    const int st = ncorp_collisions(d->c, pairs, cap, n_pairs);
+    if (st != NCORP_OK && st != NCORP_EOVERFLOW) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
+    return st;
+}
+
+int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities) {
+    if (!b) return NCORP_EINVAL;
+    BatchDisk *d = find_disk(b, disk_id);
+    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    if ((positions == nullptr) != (velocities == nullptr))
+        return batch_fail(b, NCORP_EINVAL, "give both output arrays or neither");
+    if (positions) {
+        const int st = ncorp_get_state(d->c, positions, velocities);
+        if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
+    }
+    cudaSetDevice(b->device);
+    b->used -= std::min(b->used, d->bytes);
+    b->load[d->stream] -= d->n;
+    release_disk(*d);
+    b->disks.erase(b->disks.begin() + (d - b->disks.data()));
+    return NCORP_OK;
+}
+
+int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info) {
+    if (!b || !info || n_info < 0) return NCORP_EINVAL;
+    int64_t moonlets = 0;
+    for (const auto &d : b->disks) moonlets += d.n;
+    const int64_t v[NCORP_BATCH_NINFO] = {static_cast<int64_t>(b->disks.size()), moonlets,
+                                          static_cast<int64_t>(b->used), BATCH_STREAMS, b->fallbacks, b->launches};
+    for (int i = 0; i < n_info && i < NCORP_BATCH_NINFO; i++) info[i] = v[i];
+    return NCORP_OK;
+}
+
+void ncorp_batch_free(ncorp_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    for (auto &d : b->disks) release_disk(d);
+    b->disks.clear();
+    for (int s = 0; s < BATCH_STREAMS; s++) {
+        if (b->pool[s]) {
+            cudaStreamSynchronize(b->pool[s]);
+            cudaStreamDestroy(b->pool[s]);
+        }
+        if (b->ev_done[s]) cudaEventDestroy(b->ev_done[s]);
+    }
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    delete b;
+}
+
+const char *ncorp_batch_last_error(const ncorp_batch *b) {
+    if (!b) return "null batch";
+    return b->err[0] ? b->err : "no error";
 }
 
 }  // extern "C"

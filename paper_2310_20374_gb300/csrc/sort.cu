@@ -410,7 +410,7 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
                                                                    RS_T, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    const int grid = std::min(ntiles, per_sm * c->num_sms);
+    const int grid = std::min(ntiles, coop_blocks(c, per_sm));
     NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args,

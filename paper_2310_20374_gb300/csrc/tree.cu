@@ -185,7 +185,7 @@ static int coop_grid(ncorp_ctx *c, const void *kernel, int block, size_t smem) {
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    return per_sm * c->num_sms;
+    return coop_blocks(c, per_sm);
 }
 
 void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {

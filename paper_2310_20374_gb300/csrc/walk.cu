@@ -271,7 +271,7 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
                                                                    256, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    const int grid = per_sm * c->num_sms;
+    const int grid = coop_blocks(c, per_sm);
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
                                                  0, c->stream));

@@ -71,13 +71,25 @@ def load(path: str | None = None):
     L.ncorp_profile.argtypes = [vp, ip]
     L.ncorp_stage_times.argtypes = [vp, C.POINTER(dbl), ip]
     L.ncorp_hilbert_sort_static.argtypes = [vp, i64, vp, vp, vp]
+    L.ncorp_batch_create.argtypes = [C.POINTER(vp), C.POINTER(ncorp_config), C.c_size_t, vp]
+    L.ncorp_batch_add_disk.argtypes = [vp, vp, vp, vp, vp, i64, ip, dbl, dbl, C.POINTER(C.c_int32)]
+    L.ncorp_batch_run.argtypes = [vp, ip]
+    L.ncorp_batch_get_state.argtypes = [vp, C.c_int32, vp, vp]
+    L.ncorp_batch_collisions.argtypes = [vp, C.c_int32, vp, i64, C.POINTER(i64)]
+    L.ncorp_batch_remove_disk.argtypes = [vp, C.c_int32, vp, vp]
+    L.ncorp_batch_info.argtypes = [vp, C.POINTER(i64), ip]
+    L.ncorp_batch_free.argtypes = [vp]
+    L.ncorp_batch_free.restype = None
+    L.ncorp_batch_last_error.argtypes = [vp]
+    L.ncorp_batch_last_error.restype = C.c_char_p
     L.ncorp_free.argtypes = [vp]
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
                  "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
-                 "ncorp_hilbert_sort_static"):
+                 "ncorp_hilbert_sort_static", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
+                 "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -204,6 +216,64 @@ def ncorp_stage_times(ctx) -> dict:
 
 
 NCORP_STATIC_MAX_N = 65536
+BATCH_INFO_NAMES = ["disks", "moonlets", "bytes", "streams", "fallbacks", "launches"]
+
+
+def _bcheck(b, st, ok=(NCORP_OK,)):
+    if st not in ok:
+        msg = load().ncorp_batch_last_error(b)
+        raise NcorpError(st, msg.decode() if msg else "")
+    return st
+
+
+def ncorp_batch_create(cfg: ncorp_config, hbm_budget_bytes: int = 0, stream=None):
+    h = C.c_void_p()
+    st = load().ncorp_batch_create(C.byref(h), C.byref(cfg), int(hbm_budget_bytes), _ptr(stream))
+    if st != NCORP_OK:
+        raise NcorpError(st, "ncorp_batch_create failed")
+    return h
+
+
+def ncorp_batch_add_disk(b, positions, velocities, masses, radii, n, p, theta, dt) -> int:
+    did = C.c_int32(-1)
+    _bcheck(b, load().ncorp_batch_add_disk(b, _ptr(positions), _ptr(velocities), _ptr(masses), _ptr(radii), int(n),
+                                           int(p), float(theta), float(dt), C.byref(did)))
+    return int(did.value)
+
+
+def ncorp_batch_run(b, n_steps):
+    return _bcheck(b, load().ncorp_batch_run(b, int(n_steps)))
+
+
+def ncorp_batch_get_state(b, disk_id, positions, velocities):
+    return _bcheck(b, load().ncorp_batch_get_state(b, int(disk_id), _ptr(positions), _ptr(velocities)))
+
+
+def ncorp_batch_collisions(b, disk_id, pairs, cap):
+    found = C.c_int64(0)
+    _bcheck(b, load().ncorp_batch_collisions(b, int(disk_id), _ptr(pairs), int(cap), C.byref(found)),
+            ok=(NCORP_OK, NCORP_EOVERFLOW))
+    return int(found.value)
+
+
+def ncorp_batch_remove_disk(b, disk_id, positions=None, velocities=None):
+    return _bcheck(b, load().ncorp_batch_remove_disk(b, int(disk_id), _ptr(positions), _ptr(velocities)))
+
+
+def ncorp_batch_info(b) -> dict:
+    arr = (C.c_int64 * len(BATCH_INFO_NAMES))()
+    _bcheck(b, load().ncorp_batch_info(b, arr, len(BATCH_INFO_NAMES)))
+    return dict(zip(BATCH_INFO_NAMES, (int(v) for v in arr)))
+
+
+def ncorp_batch_free(b):
+    if b:
+        load().ncorp_batch_free(b)
+
+
+def ncorp_batch_last_error(b) -> str:
+    m = load().ncorp_batch_last_error(b)
+    return m.decode() if m else ""
 
 
 def ncorp_hilbert_sort_static(positions, n, keys, order, stream=None):

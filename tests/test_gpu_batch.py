@@ -1,0 +1,149 @@
+"""Batches of independent disks (ncorp_batch_*), needs a GB300.
+
+Every disk of a batch must evolve as the same disk stepped alone with
+ncorp_step: the batch only changes how the work is scheduled (streams,
+cooperative grid sizes), so FP64 states agree to rounding of the M2L sums
+(whose atomics add in a different order) and the colliding pairs are the same.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_20374_gb300 import diskgen, ncorp
+
+pytestmark = pytest.mark.gpu
+
+DISKS = [  # n, p, theta, dt, seed, dense ring
+    (3000, 3, 0.5, 2e-2, 61, True),
+    (7000, 4, 0.6, 2e-3, 62, False),
+    (1500, 6, 0.5, 2e-2, 63, True),
+    (12000, 3, 0.5, 5e-4, 64, False),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def make_disk(n, seed, dense):
+    if dense:
+        return diskgen.make_disk(n, seed, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
+    return diskgen.make_disk(n, seed)
+
+
+def config(precision=ncorp.NCORP_FP64):
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = precision
+    cfg.leaf_size = 24
+    return cfg
+
+
+def single_disk_run(d, p, theta, dt, steps):
+    n = len(d["pos"])
+    ctx = ncorp.ncorp_init(config(), n, 0, torch.cuda.current_stream().cuda_stream)
+    pos = torch.tensor(d["pos"], device="cuda")
+    vel = torch.tensor(d["vel"], device="cuda")
+    m = torch.tensor(d["mass"], device="cuda")
+    R = torch.tensor(d["radius"], device="cuda")
+    try:
+        for _ in range(steps):
+            ncorp.ncorp_step(ctx, pos, vel, m, R, n, p, theta, dt)
+        pairs = np.zeros((1 << 14, 2), dtype=np.int64)
+        k = ncorp.ncorp_collisions(ctx, pairs, len(pairs))
+    finally:
+        ncorp.ncorp_free(ctx)
+    return pos.cpu().numpy(), vel.cpu().numpy(), pairs[:k]
+
+
+def test_batch_disks_evolve_as_single_disks():
+    disks = [make_disk(n, seed, dense) for n, _, _, _, seed, dense in DISKS]
+    b = ncorp.ncorp_batch_create(config(), 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        ids = []
+        for i, ((n, p, theta, dt, _, _), d) in enumerate(zip(DISKS, disks)):
+            # host arrays for some disks, device arrays for others
+            if i % 2:
+                args = (d["pos"], d["vel"], d["mass"], d["radius"])
+            else:
+                args = tuple(torch.tensor(d[k], device="cuda") for k in ("pos", "vel", "mass", "radius"))
+            ids.append(ncorp.ncorp_batch_add_disk(b, *args, n, p, theta, dt))
+        assert len(set(ids)) == len(ids)
+        ncorp.ncorp_batch_run(b, 3)
+        ncorp.ncorp_batch_run(b, 2)
+        info = ncorp.ncorp_batch_info(b)
+        assert info["disks"] == len(DISKS) and info["moonlets"] == sum(x[0] for x in DISKS)
+        assert info["launches"] > 0
+        for (n, p, theta, dt, _, dense), d, did in zip(DISKS, disks, ids):
+            pos = np.zeros((n, 3))
+            vel = np.zeros((n, 3))
+            ncorp.ncorp_batch_get_state(b, did, pos, vel)
+            pairs = np.zeros((1 << 14, 2), dtype=np.int64)
+            k = ncorp.ncorp_batch_collisions(b, did, pairs, len(pairs))
+            xs, vs, ps = single_disk_run(d, p, theta, dt, 5)
+            np.testing.assert_allclose(pos, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+            np.testing.assert_allclose(vel, vs, rtol=0, atol=1e-11 * np.abs(vs).max())
+            assert np.array_equal(pairs[:k], ps)
+            if dense:
+                assert k > 0
+        # removing a disk returns its state and leaves the others running
+        out_p = torch.zeros((DISKS[0][0], 3), dtype=torch.float64, device="cuda")
+        out_v = torch.zeros_like(out_p)
+        ncorp.ncorp_batch_remove_disk(b, ids[0], out_p, out_v)
+        xs, vs, _ = single_disk_run(disks[0], *DISKS[0][1:4], 5)
+        np.testing.assert_allclose(out_p.cpu().numpy(), xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+        ncorp.ncorp_batch_run(b, 1)
+        assert ncorp.ncorp_batch_info(b)["disks"] == len(DISKS) - 1
+    finally:
+        ncorp.ncorp_batch_free(b)
+
+
+def test_batch_mixed_precision_runs_and_matches_single_disk():
+    n, p, theta, dt = 20000, 6, 0.5, 1e-3
+    d = diskgen.make_disk(n, 65)
+    b = ncorp.ncorp_batch_create(config(ncorp.NCORP_MIXED), 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        did = ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], n, p, theta, dt)
+        did2 = ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], n, p, theta, dt)
+        ncorp.ncorp_batch_run(b, 4)
+        pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+        pos2, vel2 = np.zeros((n, 3)), np.zeros((n, 3))
+        ncorp.ncorp_batch_get_state(b, did, pos, vel)
+        ncorp.ncorp_batch_get_state(b, did2, pos2, vel2)
+    finally:
+        ncorp.ncorp_batch_free(b)
+    ctx = ncorp.ncorp_init(config(ncorp.NCORP_MIXED), n, 0, torch.cuda.current_stream().cuda_stream)
+    xs, vs = d["pos"].copy(), d["vel"].copy()
+    try:
+        for _ in range(4):
+            ncorp.ncorp_step(ctx, xs, vs, d["mass"], d["radius"], n, p, theta, dt)
+    finally:
+        ncorp.ncorp_free(ctx)
+    # the mutual acceleration differs by ~1e-6 relative between runs (FP32 sums in another order)
+    for x, v in ((pos, vel), (pos2, vel2)):
+        np.testing.assert_allclose(x, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+        np.testing.assert_allclose(v, vs, rtol=0, atol=1e-10 * np.abs(vs).max())
+
+
+def test_batch_rejections():
+    d = diskgen.make_disk(2000, 66)
+    b = ncorp.ncorp_batch_create(config(), 1 << 20, torch.cuda.current_stream().cuda_stream)   # 1 MiB budget
+    try:
+        with pytest.raises(ncorp.NcorpError) as e:
+            ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], 2000, 3, 0.5, 1e-3)
+        assert e.value.code == ncorp.NCORP_ENOMEM and "budget" in str(e.value)
+        assert ncorp.ncorp_batch_info(b)["disks"] == 0
+        for bad in ((0, 3, 0.5, 1e-3), (2000, 7, 0.5, 1e-3), (2000, 3, 1.0, 1e-3), (2000, 3, 0.5, 0.0)):
+            with pytest.raises(ncorp.NcorpError) as e:
+                ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], *bad)
+            assert e.value.code == ncorp.NCORP_EINVAL
+        with pytest.raises(ncorp.NcorpError) as e:
+            ncorp.ncorp_batch_remove_disk(b, 12345)
+        assert e.value.code == ncorp.NCORP_EINVAL
+        with pytest.raises(ncorp.NcorpError):
+            ncorp.ncorp_batch_run(b, -1)
+        ncorp.ncorp_batch_run(b, 3)   # empty batch: nothing to do
+    finally:
+        ncorp.ncorp_batch_free(b)
