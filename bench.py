@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="disk", choices=["disk", "ensemble", "serving"],
+                    help="disk: one disk per GPU (default); ensemble: 64 disks of mixed size per GPU in one batch; "
+                         "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="serving: length of the arrival window")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
     return ap.parse_args()
 
 
@@ -335,10 +340,177 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------- batches
+def ensemble_sizes(k, lo, hi, seed):
+    """k disk sizes log-uniform in [lo, hi] (seeded)."""
+    u = np.random.default_rng(seed).random(k)
+    return np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))).astype(np.int64)
+
+
+def batch_common(a):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2310_20374_gb300 import ncorp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED if a.precision == "mixed" else ncorp.NCORP_FP64
+    return torch, dist, ncorp, cfg, rank, world, local
+
+
+def run_ensemble(a):
+    """64 disks per GPU, N log-uniform in [1e3, 2e5], seeds 100..163 (+ 64 rank), p = 6, theta_min = 0.5,
+    advanced together by ncorp_batch_run; value = moonlet-steps of all disks / time."""
+    torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
+    from paper_2310_20374_gb300 import diskgen
+    stream = torch.cuda.current_stream()
+    sizes = ensemble_sizes(64, 1e3, 2e5, 100 + rank)
+    b = ncorp.ncorp_batch_create(cfg, 0, stream.cuda_stream)
+    for k, n in enumerate(sizes):
+        d = diskgen.make_disk(int(n), 100 + 64 * rank + k)
+        args = [torch.tensor(d[f], device="cuda") for f in ("pos", "vel", "mass", "radius")]
+        ncorp.ncorp_batch_add_disk(b, *args, int(n), a.p, a.theta, a.dt)
+    total = int(sizes.sum())
+    ncorp.ncorp_batch_run(b, max(a.warmup, 3))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(physical_gpu_index(local))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ncorp.ncorp_batch_run(b, a.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier()
+    clocks = sampler.stop()
+    info = ncorp.ncorp_batch_info(b)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    # end to end: states read back to host memory after the run (state stays resident between runs)
+    hp = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
+    hv = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
+    t0 = time.perf_counter()
+    ncorp.ncorp_batch_run(b, a.steps)
+    for k in range(len(sizes)):
+        ncorp.ncorp_batch_get_state(b, k, hp[k], hv[k])
+    e2e_s = time.perf_counter() - t0
+    ncorp.ncorp_batch_free(b)
+    value = total * a.steps * world / (t_max * 1e-3)
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
+           "data": "synthetic (seeded moonlet disks shaped like the paper's)",
+           "config": {"workload": f"64 disks per GPU, N log-uniform in [1e3, 2e5] (total {total} moonlets), "
+                                  f"falcON p={a.p} theta_min={a.theta}, {a.steps} SBAB1 steps dt={a.dt} with collision "
+                                  f"search, {a.precision} precision, one ncorp_batch_run",
+                      "moonlets_per_gpu": total, "disks_per_gpu": 64,
+                      "l2": "inputs larger than L2 (about 1 kB of state and tree per moonlet)",
+                      "parallelism": "replicas (one batch of 64 disks per GPU)"},
+           "gpu_launches": info["launches"], "clocks": clocks,
+           "e2e": {"value": round(total * a.steps * world / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": int(48 * total / a.steps),
+                   "note": "host wall time of ncorp_batch_run plus reading every disk's state back to pinned host "
+                           "memory once per run (per-step bytes averaged)"}}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_serving(a):
+    """Disks arrive as a Poisson stream (rate r per s over the window), N log-uniform in [1e3, 1e6], p uniform in
+    {3, 4, 6}, theta_min = 0.5, each integrated for 100 steps; every tick advances all active disks one step.
+    Reports the p50/p99 of the step latency seen by the disks and the aggregate moonlet-steps/s."""
+    torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
+    from paper_2310_20374_gb300 import diskgen
+    rng = np.random.default_rng(500 + rank)
+    arrivals = []
+    t = rng.exponential(1.0 / a.serve_rate)
+    while t < a.serve_seconds:
+        arrivals.append(t)
+        t += rng.exponential(1.0 / a.serve_rate)
+    sizes = ensemble_sizes(len(arrivals), 1e3, 1e6, 600 + rank)
+    ps = rng.choice([3, 4, 6], size=len(arrivals))
+    # inputs are generated before the clock starts (they stand in for requests already in host memory)
+    disks = [diskgen.make_disk(int(n), 700 + k) for k, n in enumerate(sizes)]
+    stream = torch.cuda.current_stream()
+    free_b, _ = torch.cuda.mem_get_info()
+    b = ncorp.ncorp_batch_create(cfg, int(0.8 * free_b), stream.cuda_stream)   # admission: 80% of free HBM
+    active = {}           # disk id -> [request index, steps left]
+    lat, wait, work, nxt = [], [], 0, 0
+    start = time.perf_counter()
+    while nxt < len(arrivals) or active:
+        now = time.perf_counter() - start
+        while nxt < len(arrivals) and arrivals[nxt] <= now:
+            d = disks[nxt]
+            try:
+                did = ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], int(sizes[nxt]),
+                                                 int(ps[nxt]), a.theta, a.dt)
+            except ncorp.NcorpError as e:
+                if e.code != ncorp.NCORP_ENOMEM or not active:
+                    raise
+                break     # memory budget full: the request waits for a disk to leave
+            wait.append(time.perf_counter() - start - arrivals[nxt])
+            active[did] = [nxt, 100]
+            nxt += 1
+        if not active:
+            time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+            continue
+        t0 = time.perf_counter()
+        ncorp.ncorp_batch_run(b, 1)
+        dt_tick = time.perf_counter() - t0
+        for did, v in list(active.items()):
+            lat.append(dt_tick)
+            work += int(sizes[v[0]])
+            v[1] -= 1
+            if v[1] == 0:
+                ncorp.ncorp_batch_remove_disk(b, did)
+                del active[did]
+    wall = time.perf_counter() - start
+    ncorp.ncorp_batch_free(b)
+    lat_ms = np.array(lat) * 1e3
+    out = {"metric": METRIC, "value": round(work / wall, 1), "unit": UNIT, "n_gpus": world,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
+           "data": "synthetic (seeded moonlet disks shaped like the paper's)",
+           "config": {"workload": f"serving: Poisson arrivals at {a.serve_rate}/s for {a.serve_seconds} s "
+                                  f"({len(arrivals)} disks), N log-uniform in [1e3, 1e6], p in {{3,4,6}}, "
+                                  f"theta_min={a.theta}, 100 SBAB1 steps each, dt={a.dt}, {a.precision} precision",
+                      "requests": len(arrivals), "moonlet_steps": work},
+           "p50_step_ms": round(float(np.percentile(lat_ms, 50)), 3),
+           "p99_step_ms": round(float(np.percentile(lat_ms, 99)), 3),
+           "admission_wait_ms_p50": round(float(np.percentile(np.array(wait) * 1e3, 50)), 3),
+           "admission_wait_ms_p99": round(float(np.percentile(np.array(wait) * 1e3, 99)), 3),
+           "wall_s": round(wall, 2), "offered_moonlet_steps_per_s": round(float(sizes.sum()) * 100 / a.serve_seconds, 1)}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "ensemble":
+        run_ensemble(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_gpu(a)
 
