@@ -61,6 +61,17 @@ struct WalkLists {
     int *p2p_src = nullptr;       // source leaf of each directed entry
 };
 
+// One tree with everything a walk over it produces: cells, walk lists and
+// the control block (tree description, counters, error word).  A context
+// holds two, so that the collision search on the tree of x_n can run while
+// the tree of x_{n+1} is built and walked.
+struct TreeSet {
+    Cells cells;
+    WalkLists wl;
+    Ctrl *ctl = nullptr;      // device
+    Ctrl *ctl_h = nullptr;    // pinned host mirror
+};
+
 constexpr int WALK_MAX_ITERS = 96;
 constexpr int P2M_ITEM_CHUNK = 512;   // moonlets per multipole work item
 
@@ -109,6 +120,11 @@ struct ncorp_ctx {
 
     ncorp::Ctrl *ctl = nullptr;      // device
     ncorp::Ctrl *ctl_h = nullptr;    // pinned host mirror
+    ncorp::TreeSet alt;              // the other tree set (cells, wl, ctl above are the current one)
+    cudaStream_t side = nullptr;     // stream of the collision search while the next tree is built
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int *err_acc = nullptr;          // device: error words of tree sets recycled during a call
+    int *err_acc_h = nullptr;        // pinned host mirror
 
     // resident-state bookkeeping
     bool have_state = false;         // A holds a state

@@ -194,6 +194,36 @@ void ensure_tree_capacity(ncorp_ctx *c, int n) {
     if (c->pair_cap < pc) alloc_pairs(c, pc);
 }
 
+// The current tree set (cells, wl, ctl, ctl_h) and the other one trade places.
+void swap_sets(ncorp_ctx *c) {
+    std::swap(c->cells, c->alt.cells);
+    std::swap(c->wl, c->alt.wl);
+    std::swap(c->ctl, c->alt.ctl);
+    std::swap(c->ctl_h, c->alt.ctl_h);
+}
+
+// Runs f with the other tree set as the current one (the resident flags
+// describe the current tree and are left as they were).
+template <class F>
+void on_alt(ncorp_ctx *c, F f) {
+    const bool tv = c->tree_valid;
+    swap_sets(c);
+    try {
+        f();
+    } catch (...) {
+        swap_sets(c);
+        c->tree_valid = tv;
+        throw;
+    }
+    swap_sets(c);
+    c->tree_valid = tv;
+}
+
+void ensure_both_capacities(ncorp_ctx *c, int n) {
+    ensure_tree_capacity(c, n);
+    on_alt(c, [&] { ensure_tree_capacity(c, n); });
+}
+
 // grows whatever overflowed; returns false if nothing can be grown
 bool grow_after(ncorp_ctx *c, int err) {
     bool grew = false;
@@ -275,14 +305,25 @@ ExtForce external(ncorp_ctx *c, double t) {
 }
 
 // Clears the error word and the per-call counters; the tree description
-// (cell and leaf counts, levels, root cube) of a resident tree is kept.
-void reset_ctl(ncorp_ctx *c) {
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->err, 0, sizeof(int), c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_found, 0, sizeof(int), c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_tests, 0, sizeof(long long), c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_snap, 0, sizeof(int), c->stream));
+// (cell and leaf counts, levels, root cube) of a resident tree is kept.  With
+// fold, the cleared error word is first or-ed into the context's accumulator
+// (a tree set recycled in the middle of a call keeps its errors visible).
+__global__ void k_reset_ctl(Ctrl *ctl, int *acc) {
+    if (acc) *acc |= ctl->err;
+    ctl->err = 0;
+    ctl->n_found = 0;
+    ctl->n_tests = 0;
+    ctl->bar_count = 0;
+    ctl->bar_snap = 0;
 }
+
+void reset_ctl(ncorp_ctx *c, bool fold = false) {
+    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, fold ? c->err_acc : nullptr);
+    c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void clear_err_acc(ncorp_ctx *c) { NCORP_CUDA_CHECK(cudaMemsetAsync(c->err_acc, 0, sizeof(int), c->stream)); }
 
 // ---- stage timers (CUDA events on the context's stream, only when profiling)
 void stage_begin(ncorp_ctx *c, int st) {
@@ -315,8 +356,14 @@ void begin_call(ncorp_ctx *c) {
     }
 }
 
-int finish(ncorp_ctx *c) {
+// Waits for the call's work and returns its error word: the current tree
+// set's, and with both also the other set's and the accumulator's.
+int finish(ncorp_ctx *c, bool both = false) {
     NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    if (both) {
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(c->alt.ctl_h, c->alt.ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(c->err_acc_h, c->err_acc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
     NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
     if (c->profile)
         for (int i = 0; i < NCORP_NSTAGES; i++) {
@@ -328,7 +375,7 @@ int finish(ncorp_ctx *c) {
             }
             c->stage_ms[i] = sum;
         }
-    return c->ctl_h->err;
+    return c->ctl_h->err | (both ? (c->alt.ctl_h->err | *c->err_acc_h) : 0);
 }
 
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
@@ -366,23 +413,58 @@ void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const doub
     launch_collide(c, S, vx, vy, vz, dt);
 }
 
-// One SBAB1 step of the resident state A (its tree and acceleration valid):
-// half kick, collision search on A's tree, drift, new tree, gravity, half
-// kick.  The new state is left in Cset (not yet swapped with A), nothing is
-// copied to the caller and nothing waits: the caller reads the status.
-void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt) {
+constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision walk beside the gravity pipeline
+
+// One SBAB1 step of the resident state A (its tree, in the current tree set,
+// and its acceleration valid): half kick, collision search on A's tree, drift,
+// tree of the new positions in the other tree set, gravity, half kick.  With
+// overlap, the collision search runs on the context's side stream while the
+// main stream drifts, sorts, builds and walks the new tree (the two touch
+// disjoint buffers); its cooperative grids are kept small enough that both
+// streams' cooperative kernels fit on the device together.  On return the
+// tree sets have traded places (the current one describes the new positions)
+// and the new state is in Cset (not yet swapped with A); nothing is copied to
+// the caller and nothing waits: the caller reads the status.
+void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overlap) {
     const double h = 0.5 * dt;
     ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
     { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n); }
-    if (c->cfg.collisions) collisions(c, A, B.vx, B.vy, B.vz, dt);
+    const bool side = overlap && c->cfg.collisions;
+    if (c->cfg.collisions) {
+        if (side) {
+            cudaStream_t main = c->stream;
+            const int cap = c->coop_max;
+            NCORP_CUDA_CHECK(cudaEventRecord(c->ev_fork, main));
+            NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            c->stream = c->side;
+            c->coop_max = cap > 0 ? std::min(cap, COLLISION_SIDE_BLOCKS) : COLLISION_SIDE_BLOCKS;
+            try {
+                collisions(c, A, B.vx, B.vy, B.vz, dt);
+                NCORP_CUDA_CHECK(cudaEventRecord(c->ev_join, c->side));
+            } catch (...) {
+                c->stream = main;
+                c->coop_max = cap;
+                throw;
+            }
+            c->stream = main;
+            c->coop_max = cap;
+        } else {
+            collisions(c, A, B.vx, B.vy, B.vz, dt);
+        }
+    }
+    swap_sets(c);
+    reset_ctl(c, true);
     { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
     build_tree(c, B, B, A, Cn, n);
     gravity(c, Cn, p, theta, c->time + dt, false);
+    if (side) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n); }
 }
 
-void record_stats(ncorp_ctx *c, bool grav) {
+// col: the control block of the tree the collision search ran on (NULL: the current one)
+void record_stats(ncorp_ctx *c, bool grav, const Ctrl *col = nullptr) {
     const Ctrl &h = *c->ctl_h;
+    const Ctrl &hc = col ? *col : h;
     c->stats[NCORP_STAT_LAUNCHES] = c->launches;
     c->stats[NCORP_STAT_CELLS] = h.n_cells;
     c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
@@ -397,11 +479,11 @@ void record_stats(ncorp_ctx *c, bool grav) {
         c->stats[NCORP_STAT_P2P_DIRECTED] = h.n_p2p_dir;
     }
     if (!grav || c->cfg.collisions) {
-        c->stats[NCORP_STAT_COL_PAIRS] = h.col_pairs;
-        c->stats[NCORP_STAT_COL_SELF] = h.col_self;
-        c->stats[NCORP_STAT_COL_TESTS] = h.n_tests;
-        c->stats[NCORP_STAT_COL_FOUND] = h.n_found;
-        c->stats[NCORP_STAT_COL_ITERS] = h.col_iters;
+        c->stats[NCORP_STAT_COL_PAIRS] = hc.col_pairs;
+        c->stats[NCORP_STAT_COL_SELF] = hc.col_self;
+        c->stats[NCORP_STAT_COL_TESTS] = hc.n_tests;
+        c->stats[NCORP_STAT_COL_FOUND] = hc.n_found;
+        c->stats[NCORP_STAT_COL_ITERS] = hc.col_iters;
     }
 }
 
@@ -460,14 +542,24 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         int coop = 0;
         NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
         if (!coop) throw CudaError(cudaErrorNotSupported, "cooperative launch unsupported", __FILE__, __LINE__);
-        dalloc(c->ctl, 1);
+        for (int set = 0; set < 2; set++) {
+            dalloc(c->ctl, 1);
+            NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
+            std::memset(c->ctl_h, 0, sizeof(Ctrl));
+            NCORP_CUDA_CHECK(cudaMemset(c->ctl, 0, sizeof(Ctrl)));
+            swap_sets(c);
+        }
         dalloc(c->work_counter, 4);
-        NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
-        std::memset(c->ctl_h, 0, sizeof(Ctrl));
-        NCORP_CUDA_CHECK(cudaMemset(c->ctl, 0, sizeof(Ctrl)));
+        dalloc(c->err_acc, 1);
+        NCORP_CUDA_CHECK(cudaMemset(c->err_acc, 0, sizeof(int)));
+        NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->err_acc_h), sizeof(int)));
+        *c->err_acc_h = 0;
+        NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         ensure_particles(c, n_max);
         choose_parameters(c, 6);
-        ensure_tree_capacity(c, static_cast<int>(n_max));
+        ensure_both_capacities(c, static_cast<int>(n_max));
     } catch (const CudaError &e) {
         int code = (e.code == cudaErrorMemoryAllocation) ? NCORP_ENOMEM : NCORP_ECUDA;
         ncorp_free(c);
@@ -590,8 +682,10 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
         bool have = resident && c->have_state;
         bool tree = resident;
         for (int attempt = 0;; attempt++) {
-            ensure_tree_capacity(c, n);
+            ensure_both_capacities(c, n);
             reset_ctl(c);
+            on_alt(c, [&] { reset_ctl(c); });
+            clear_err_acc(c);
             if (!have) {   // read the caller's state (caller order)
                 Stage st(c, NCORP_STAGE_KDK);
                 ParticleSet &A = c->A;
@@ -607,15 +701,17 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                 std::swap(c->A, c->Cset);
                 gravity(c, c->A, p, theta, c->time, false);
             }
-            enqueue_kdk(c, n, p, theta, dt);
+            enqueue_kdk(c, n, p, theta, dt, true);
             {
                 Stage st(c, NCORP_STAGE_KDK);
                 ParticleSet &Cn = c->Cset;
                 download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
                 download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
             }
-            int err = finish(c);
-            if (!finite_ok(c)) {
+            const int err = finish(c, true);
+            // the current tree set now holds the new tree, the other one A's tree
+            const int e_new = c->ctl_h->err, e_old = c->alt.ctl_h->err, e_acc = *c->err_acc_h;
+            if (err & ERR_NONFINITE) {
                 c->have_state = false;
                 c->tree_valid = false;
                 return fail(c, NCORP_EINVAL, "non-finite position");
@@ -627,15 +723,18 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
             }
             if (err == 0) break;
             // A was not written: rerun from it with larger buffers (its tree is rebuilt)
+            swap_sets(c);
             have = true;
             tree = false;
-            if (attempt >= MAX_RETRIES || !grow_after(c, err)) {
+            bool grew = grow_after(c, e_old | e_acc);
+            on_alt(c, [&] { grew = grow_after(c, e_new | e_acc) || grew; });
+            if (attempt >= MAX_RETRIES || !grew) {
                 c->tree_valid = false;
                 return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
             }
         }
         if (c->cfg.collisions) {
-            c->n_found = c->ctl_h->n_found;
+            c->n_found = c->alt.ctl_h->n_found;
             c->pairs_sorted = false;
         } else {
             c->n_found = 0;
@@ -652,7 +751,7 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
         c->last_R = radii;
         c->last_p = p;
         c->last_theta = theta;
-        record_stats(c, true);
+        record_stats(c, true, c->alt.ctl_h);
         c->stats[NCORP_STAT_COL_FOUND] = c->n_found;
         return NCORP_OK;
     })
@@ -830,28 +929,42 @@ void ncorp_free(ncorp_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->side) cudaStreamSynchronize(c->side);
     free_set(c->A);
     free_set(c->B);
     free_set(c->Cset);
     dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->rcf);
     dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
     dfree(c->tile_hist); dfree(c->scan_tmp); dfree(c->stage); dfree(c->stage2);
-    Cells &C = c->cells;
-    dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
-    dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
-    dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
-    dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
-    WalkLists &W = c->wl;
-    dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
-    dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
+    for (int set = 0; set < 2; set++) {
+        Cells &C = c->cells;
+        dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
+        dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
+        dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
+        dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf);
+        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+        WalkLists &W = c->wl;
+        dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
+        dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
+        dfree(c->ctl);
+        if (c->ctl_h) cudaFreeHost(c->ctl_h);
+        c->ctl_h = nullptr;
+        swap_sets(c);
+    }
     dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
-    dfree(c->ctl);
+    dfree(c->err_acc);
+    if (c->err_acc_h) cudaFreeHost(c->err_acc_h);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     dfree(c->work_counter);
     for (int i = 0; i < NCORP_NSTAGES; i++)
         for (int k = 0; k < 8; k++)
             for (int e = 0; e < 2; e++)
                 if (c->ev[i][k][e]) cudaEventDestroy(c->ev[i][k][e]);
-    if (c->ctl_h) cudaFreeHost(c->ctl_h);
     delete c;
 }
 
@@ -933,7 +1046,7 @@ int prime_disk(ncorp_ctx *c, BatchDisk &d) {
     choose_parameters(c, d.p);
     for (int attempt = 0;; attempt++) {
         begin_call(c);
-        ensure_tree_capacity(c, n);
+        ensure_both_capacities(c, n);
         reset_ctl(c);
         ParticleSet &A = c->A;
         upload_vec(c, d.pos, A.x, A.y, A.z, n);
@@ -1078,17 +1191,22 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
             download_vec(c, c->A.x, c->A.y, c->A.z, c->A.perm, d.pos, static_cast<int>(d.n), c->stage);
             download_vec(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, d.vel, static_cast<int>(d.n), c->stage2);
             reset_ctl(c);
+            on_alt(c, [&] { reset_ctl(c); });
+            clear_err_acc(c);
         }
         for (int k = 0; k < n_steps; k++)
             for (auto &d : b->disks) {
                 ncorp_ctx *c = d.c;
-                NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_found, 0, sizeof(int), c->stream));
-                enqueue_kdk(c, static_cast<int>(d.n), d.p, d.theta, d.dt);
+                enqueue_kdk(c, static_cast<int>(d.n), d.p, d.theta, d.dt, false);
                 std::swap(c->A, c->Cset);
                 c->time += d.dt;
             }
-        for (auto &d : b->disks)
-            NCORP_CUDA_CHECK(cudaMemcpyAsync(d.c->ctl_h, d.c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, d.c->stream));
+        for (auto &d : b->disks) {
+            ncorp_ctx *c = d.c;
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(c->alt.ctl_h, c->alt.ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(c->err_acc_h, c->err_acc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        }
         for (int s = 0; s < BATCH_STREAMS; s++) {
             NCORP_CUDA_CHECK(cudaEventRecord(b->ev_done[s], b->pool[s]));
             NCORP_CUDA_CHECK(cudaStreamWaitEvent(b->user, b->ev_done[s], 0));
@@ -1105,11 +1223,11 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
         BatchDisk &d = b->disks[i];
         ncorp_ctx *c = d.c;
         b->launches += c->launches;
-        const int err = c->ctl_h->err;
+        const int err = c->ctl_h->err | c->alt.ctl_h->err | *c->err_acc_h;
         if (err == 0) {
-            c->n_found = c->cfg.collisions ? c->ctl_h->n_found : 0;
+            c->n_found = c->cfg.collisions ? c->alt.ctl_h->n_found : 0;
             c->pairs_sorted = false;
-            record_stats(c, true);
+            record_stats(c, true, c->alt.ctl_h);
             c->stats[NCORP_STAT_COL_FOUND] = c->n_found;
             continue;
         }
