@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 (FMA) x
 # DRAM bytes (read + write) of one k_eval launch on this workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # set to None whenever the kernel changes until it is captured again.
-EVAL_DRAM_BYTES_PER_LAUNCH = 8.32e6
+EVAL_DRAM_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -242,23 +242,20 @@ def run_gpu(a):
                    "acceleration of the uploaded state), new state and pairs read back"}
     ncorp.ncorp_free(ctx)
 
-    # ---- roofline of the dominant kernel (L2P + near field: FP32 ALU bound).
-    # Algorithmic FLOPs per step: 24 per directed moonlet pair of the near field
-    # (9 adds for the double-float separation, 3 mul + 2 add for r^2, rsqrt, 3 mul
-    # for mu/r^3, 3 FMA into the sums; every unordered pair counted by the walk
-    # is evaluated in both directions) plus, per moonlet, the L2P gradient of a
-    # p-order expansion: 3 FMA (6 FLOPs) per multi-index of order < p, plus the
-    # p-1 powers of each coordinate offset.
-    eval_ms = stage.get("eval", 0.0) / a.steps
-    nterms = a.p * (a.p + 1) * (a.p + 2) // 6            # multi-indices |beta| <= p-1
+    # ---- roofline of the dominant kernel (the near-field direct sums, k_eval: FP32 ALU bound).
+    # Algorithmic FLOPs per launch: 24 per directed moonlet pair (9 adds for the
+    # double-float separation, 3 mul + 2 add for r^2, rsqrt, 3 mul for mu/r^3,
+    # 3 FMA into the sums); every unordered pair counted by the walk is
+    # evaluated from both sides.
+    near_ms = stage.get("near", 0.0) / a.steps
     directed = 2.0 * interactions / a.steps
-    flops_eval = 24.0 * directed + a.n * (6.0 * nterms + 3 * (a.p - 1))
-    achieved = flops_eval / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_eval (L2P + near-field direct sum + external forces)",
+    flops_near = 24.0 * directed
+    achieved = flops_near / (near_ms * 1e-3) / 1e12 if near_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_eval (near-field direct sums per leaf)",
                 "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": EVAL_DRAM_BYTES_PER_LAUNCH,
-                "flops_per_launch": flops_eval, "directed_pairs_per_launch": directed,
-                "avg_launch_ms": round(eval_ms, 4),
+                "flops_per_launch": flops_near, "directed_pairs_per_launch": directed,
+                "avg_launch_ms": round(near_ms, 4),
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 FP32 lanes x 2 FLOPs x 2.07 GHz (not measured)"}
     last = {k: last_stats[k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self",
                                       "p2p_interactions", "walk_iters", "col_pairs", "col_self", "col_tests",

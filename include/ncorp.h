@@ -155,14 +155,15 @@ int ncorp_stats(ncorp_ctx *ctx, int64_t *stats, int n_stats);
  * runs more than once).  Off by default; on costs a few event records. */
 #define NCORP_STAGE_SORT     0   /* bounding box, keys, radix sort, gather */
 #define NCORP_STAGE_BUILD    1   /* octree build, leaf list */
-#define NCORP_STAGE_CLIMB    2   /* gravity climb: geometry, theta(M), r_crit, multipoles */
+#define NCORP_STAGE_CLIMB    2   /* gravity climb: geometry, theta(M), r_crit; multipoles beside them */
 #define NCORP_STAGE_WALK     3   /* gravity walk and per-target lists */
 #define NCORP_STAGE_M2L      4
 #define NCORP_STAGE_DESCEND  5   /* complete local expansions (Eq. shifting from the ancestors) */
-#define NCORP_STAGE_EVAL     6   /* L2P, near field, external forces */
+#define NCORP_STAGE_EVAL     6   /* L2P of the local expansions, external forces */
 #define NCORP_STAGE_COLLIDE  7   /* collision climb, walk and pair test */
 #define NCORP_STAGE_KDK      8   /* kicks, drift, host/device copies of the state */
-#define NCORP_NSTAGES        9
+#define NCORP_STAGE_NEAR     9   /* near-field direct sums (beside M2L and the descent) */
+#define NCORP_NSTAGES       10
 
 /* Turns the stage timers on (enable != 0) or off.  NCORP_EINVAL if ctx is NULL. */
 int ncorp_profile(ncorp_ctx *ctx, int enable);

@@ -123,6 +123,8 @@ struct ncorp_ctx {
     ncorp::TreeSet alt;              // the other tree set (cells, wl, ctl above are the current one)
     cudaStream_t side = nullptr;     // stream of the collision search while the next tree is built
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side2 = nullptr;    // stream of the multipoles and the near field inside a gravity evaluation
+    cudaEvent_t ev_geo = nullptr, ev_p2m = nullptr, ev_lists = nullptr, ev_near = nullptr;
     int *err_acc = nullptr;          // device: error words of tree sets recycled during a call
     int *err_acc_h = nullptr;        // pinned host mirror
 
@@ -160,13 +162,14 @@ void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 
 // ---- tree.cu ----
 void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s);
-void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta);
+void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta);
+void launch_rcrit(ncorp_ctx *c, double theta);
+void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
 void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
                             const double *vz, double dt);
 
 // ---- walk.cu ----
 void launch_walk(ncorp_ctx *c, bool gravity);
-void launch_directed_lists(ncorp_ctx *c);
 
 // ---- m2l.cu / eval.cu ----
 void launch_m2l(ncorp_ctx *c, int p, bool mixed);
@@ -177,7 +180,8 @@ struct ExtForce {
     double sx, sy, sz;     // star position
     double inv_rs2;        // 1 / r_star^2
 };
-void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual);
+void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
+void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual);
 
 // ---- collide.cu ----
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,

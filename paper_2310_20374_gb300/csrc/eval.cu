@@ -3,13 +3,14 @@
 // the direct ("brute force") gravity of each leaf's near-field list, and the
 // central-body / distant-star forces (App. B.1, B.3).
 //
-// Evaluation: one warp per leaf, leaves handed out dynamically.  Every
-// moonlet of the leaf gets
+// Evaluation in two kernels, so that the near field (which needs only the
+// direct lists) can run while M2L and the descent produce the local
+// expansions.  k_eval: every moonlet gets
+//   sum_j mu_j (x_j - x)/|x_j - x|^3 over the moonlets of its leaf's direct list
+// (mu_j = G m_j; coincident pairs, the moonlet itself included, are skipped).
+// k_far: it adds
 //   a = (1/rho) sum_{|beta| <= p-1} C-hat_{e_k+beta} (d/rho)^beta / beta!,  d = x - s_leaf,
-// plus sum_j mu_j (x_j - x)/|x_j - x|^3 over the moonlets of its direct list
-// (mu_j = G m_j; coincident pairs, the moonlet itself included, are skipped),
-// plus the external forces in FP64.  Each lane owns one or two moonlets and
-// builds their sums in registers; they are written once.
+// from its leaf's complete local expansion, and the external forces in FP64.
 //
 // Mixed precision: the direct sum reads every position as an FP32 pair
 // (hi, lo) with x = hi + lo; (hi_j - hi_i) + (lo_j - lo_i) gives the
@@ -51,6 +52,7 @@ struct EvalArgs {
     ExtForce ext;
     double *ax, *ay, *az;
     double *amx, *amy, *amz;
+    double *nx, *ny, *nz;     // near-field sums per moonlet (tree order)
     int *work;
     const Ctrl *ctl;
 };
@@ -280,10 +282,8 @@ constexpr int EV_BUF = 512;
 
 template <int P, typename real>
 struct EvShared {
-    static constexpr int NC = num_c(P);
     __align__(16) unsigned char buf[EV_BUF * 32];   // FP32: float4 hi[EV_BUF] (xyz, mu), lo[EV_BUF]
                                                     // FP64: double x, y, z, mu [EV_BUF]
-    real C[NC];
     real red[3][EV_THREADS];
     int lfirst[32], lpre[32];
     int leaf, total, next_si, next_soff;
@@ -291,12 +291,10 @@ struct EvShared {
 
 template <int P, typename real>
 __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
-    constexpr int NC = num_c(P);
     constexpr bool f32 = std::is_same<real, float>::value;
     __shared__ EvShared<P, real> S;
     if (aborted(A.ctl)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const real *Cf = static_cast<const real *>(A.Cf);
     const int nl = A.ctl->n_leaves;
     float4 *sh = reinterpret_cast<float4 *>(S.buf), *sl = sh + EV_BUF;
     double *bx = reinterpret_cast<double *>(S.buf), *by = bx + EV_BUF, *bz = by + EV_BUF, *bm = bz + EV_BUF;
@@ -307,8 +305,6 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
         const int li = S.leaf;
         if (li >= nl) break;
         const int leaf = A.leaves[li];
-        for (int i = tid; i < NC; i += EV_THREADS) S.C[i] = Cf[(size_t)leaf * NC + i];
-        __syncthreads();
         const int f = A.first[leaf], cnt = A.count[leaf];
         const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
         for (int t0 = 0; t0 < cnt; t0 += EV_THREADS) {
@@ -398,29 +394,68 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
                 }
             }
             if (g == 0 && act) {
-                // L2P of the leaf's complete local expansion (Eq. shifting at the moonlet)
-                real lx = real(0), ly = real(0), lz = real(0);
-                if constexpr (f32) {
-                    const float4 lgh = A.gh[leaf], lgl = A.gl[leaf];
-                    const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
-                    l2p<P, real>(S.C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
-                                 ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
-                    lx *= irf; ly *= irf; lz *= irf;
-                } else {
-                    const double irho = 1.0 / A.rho[leaf];
-                    l2p<P, real>(S.C, (X - A.sx[leaf]) * irho, (Y - A.sy[leaf]) * irho, (Z - A.sz[leaf]) * irho, lx, ly,
-                                 lz);
-                    lx *= irho; ly *= irho; lz *= irho;
-                }
-                double ex, ey, ez;
-                external_force(A.ext, X, Y, Z, ex, ey, ez);
-                const double mx = static_cast<double>(lx + ax), my = static_cast<double>(ly + ay),
-                             mz = static_cast<double>(lz + az);
-                A.ax[i] = mx + ex;
-                A.ay[i] = my + ey;
-                A.az[i] = mz + ez;
-                if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
+                A.nx[i] = static_cast<double>(ax);
+                A.ny[i] = static_cast<double>(ay);
+                A.nz[i] = static_cast<double>(az);
             }
+        }
+    }
+}
+
+// L2P of each leaf's complete local expansion (Eq. shifting at the moonlet),
+// plus the near-field sums and the external forces: one warp per leaf, the
+// expansion staged in shared memory, lanes over the leaf's moonlets.
+constexpr int FAR_WARPS = 8;
+
+template <int P, typename real>
+__global__ void __launch_bounds__(32 * FAR_WARPS) k_far(EvalArgs A) {
+    constexpr int NC = num_c(P);
+    constexpr bool f32 = std::is_same<real, float>::value;
+    __shared__ real s_C[FAR_WARPS][NC];
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const real *Cf = static_cast<const real *>(A.Cf);
+    const int nl = A.ctl->n_leaves;
+    real *C = s_C[wl];
+    for (int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < nl; li += nwarps) {
+        const int leaf = A.leaves[li];
+        __syncwarp();
+        for (int k = lane; k < NC; k += 32) C[k] = Cf[(size_t)leaf * NC + k];
+        __syncwarp();
+        const int f = A.first[leaf], cnt = A.count[leaf];
+        float4 lgh = make_float4(0.f, 0.f, 0.f, 0.f), lgl = lgh;
+        double sx = 0.0, sy = 0.0, sz = 0.0, irho = 0.0;
+        if constexpr (f32) {
+            lgh = A.gh[leaf];
+            lgl = A.gl[leaf];
+        } else {
+            irho = 1.0 / A.rho[leaf];
+            sx = A.sx[leaf]; sy = A.sy[leaf]; sz = A.sz[leaf];
+        }
+        for (int t = lane; t < cnt; t += 32) {
+            const int i = f + t;
+            const double X = A.x[i], Y = A.y[i], Z = A.z[i];
+            real lx = real(0), ly = real(0), lz = real(0);
+            if constexpr (f32) {
+                const float4 th = A.hi4[i], tl = A.lo4[i];
+                const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
+                l2p<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
+                             ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
+                lx *= irf; ly *= irf; lz *= irf;
+            } else {
+                l2p<P, real>(C, (X - sx) * irho, (Y - sy) * irho, (Z - sz) * irho, lx, ly, lz);
+                lx *= irho; ly *= irho; lz *= irho;
+            }
+            double ex, ey, ez;
+            external_force(A.ext, X, Y, Z, ex, ey, ez);
+            const double mx = static_cast<double>(lx + static_cast<real>(A.nx[i]));
+            const double my = static_cast<double>(ly + static_cast<real>(A.ny[i]));
+            const double mz = static_cast<double>(lz + static_cast<real>(A.nz[i]));
+            A.ax[i] = mx + ex;
+            A.ay[i] = my + ey;
+            A.az[i] = mz + ez;
+            if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
         }
     }
 }
@@ -439,6 +474,12 @@ static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
         &per_sm, reinterpret_cast<const void *>(k_eval<P, real>), EV_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     k_eval<P, real><<<per_sm * c->num_sms, EV_THREADS, 0, c->stream>>>(A);
+    c->launches++;
+}
+
+template <int P, typename real>
+static void far_t(ncorp_ctx *c, const EvalArgs &A) {
+    k_far<P, real><<<4 * c->num_sms, 32 * FAR_WARPS, 0, c->stream>>>(A);
     c->launches++;
 }
 
@@ -464,7 +505,7 @@ void launch_descend(ncorp_ctx *c, int p, bool mixed) {
 #undef NCORP_DESC_CASE
 }
 
-void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual) {
+static EvalArgs eval_args(ncorp_ctx *c, const ParticleSet &P, double G, ExtForce ext, bool want_mutual) {
     Cells &C = c->cells;
     EvalArgs A;
     A.leaves = C.leaves; A.level = C.level; A.parent = C.parent; A.first = C.first; A.count = C.count;
@@ -480,8 +521,14 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     A.amx = want_mutual ? c->amx : nullptr;
     A.amy = want_mutual ? c->amy : nullptr;
     A.amz = want_mutual ? c->amz : nullptr;
+    A.nx = c->amx; A.ny = c->amy; A.nz = c->amz;   // the far kernel overwrites them in place
     A.work = c->work_counter;
     A.ctl = c->ctl;
+    return A;
+}
+
+void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G) {
+    const EvalArgs A = eval_args(c, P, G, ExtForce{}, false);
     NCORP_CUDA_CHECK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
 #define NCORP_EVAL_CASE(PP)                      \
     case PP:                                     \
@@ -498,6 +545,26 @@ void launch_eval(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
         default: break;
     }
 #undef NCORP_EVAL_CASE
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual) {
+    const EvalArgs A = eval_args(c, P, G, ext, want_mutual);
+#define NCORP_FAR_CASE(PP)                       \
+    case PP:                                     \
+        if (mixed) far_t<PP, float>(c, A);       \
+        else far_t<PP, double>(c, A);            \
+        break;
+    switch (p) {
+        NCORP_FAR_CASE(1)
+        NCORP_FAR_CASE(2)
+        NCORP_FAR_CASE(3)
+        NCORP_FAR_CASE(4)
+        NCORP_FAR_CASE(5)
+        NCORP_FAR_CASE(6)
+        default: break;
+    }
+#undef NCORP_FAR_CASE
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -395,15 +395,52 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
     launch_build(c, dst, n, c->s);
 }
 
+// Runs body with c->stream set to s (launchers enqueue on c->stream).
+template <class F>
+void on_stream(ncorp_ctx *c, cudaStream_t s, F body) {
+    cudaStream_t main = c->stream;
+    c->stream = s;
+    try {
+        body();
+    } catch (...) {
+        c->stream = main;
+        throw;
+    }
+    c->stream = main;
+}
+
+// Gravity of the tree in the current set.  Two streams: the main one runs the
+// geometry climb, theta(M), the walk (with its lists), M2L, the descent and
+// the far-field evaluation; the second one runs the multipoles (which need
+// only the centres) beside theta(M) and the walk, then the near field (which
+// needs only the lists) beside M2L and the descent.
 void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual) {
     const bool mixed = c->cfg.precision == NCORP_MIXED;
+    const double G = c->cfg.G;
     c->grav_p = p;
     c->grav_mixed = mixed;
-    { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_gravity(c, S, p, mixed, c->cfg.G, theta); }
-    { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true); launch_directed_lists(c); }
+    { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_geometry(c, S, G, theta); }
+    NCORP_CUDA_CHECK(cudaEventRecord(c->ev_geo, c->stream));
+    NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_geo, 0));
+    on_stream(c, c->side2, [&] {
+        Stage st(c, NCORP_STAGE_CLIMB);
+        launch_multipoles(c, S, p, mixed, G);
+        NCORP_CUDA_CHECK(cudaEventRecord(c->ev_p2m, c->stream));
+    });
+    { Stage st(c, NCORP_STAGE_CLIMB); launch_rcrit(c, theta); }
+    { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true); }
+    NCORP_CUDA_CHECK(cudaEventRecord(c->ev_lists, c->stream));
+    NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_lists, 0));
+    on_stream(c, c->side2, [&] {
+        Stage st(c, NCORP_STAGE_NEAR);
+        launch_near(c, S, p, mixed, G);
+        NCORP_CUDA_CHECK(cudaEventRecord(c->ev_near, c->stream));
+    });
+    NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_p2m, 0));
     { Stage st(c, NCORP_STAGE_M2L); launch_m2l(c, p, mixed); }
     { Stage st(c, NCORP_STAGE_DESCEND); launch_descend(c, p, mixed); }
-    { Stage st(c, NCORP_STAGE_EVAL); launch_eval(c, S, p, mixed, c->cfg.G, external(c, t), want_mutual); }
+    NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_near, 0));
+    { Stage st(c, NCORP_STAGE_EVAL); launch_far(c, S, p, mixed, G, external(c, t), want_mutual); }
 }
 
 void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
@@ -557,6 +594,9 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&c->ev_geo, &c->ev_p2m, &c->ev_lists, &c->ev_near})
+            NCORP_CUDA_CHECK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         ensure_particles(c, n_max);
         choose_parameters(c, 6);
         ensure_both_capacities(c, static_cast<int>(n_max));
@@ -930,6 +970,7 @@ void ncorp_free(ncorp_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->side2) cudaStreamSynchronize(c->side2);
     free_set(c->A);
     free_set(c->B);
     free_set(c->Cset);
@@ -960,6 +1001,12 @@ void ncorp_free(ncorp_ctx *c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side2) {
+        cudaStreamSynchronize(c->side2);
+        cudaStreamDestroy(c->side2);
+    }
+    for (cudaEvent_t e : {c->ev_geo, c->ev_p2m, c->ev_lists, c->ev_near})
+        if (e) cudaEventDestroy(e);
     dfree(c->work_counter);
     for (int i = 0; i < NCORP_NSTAGES; i++)
         for (int k = 0; k < 8; k++)

@@ -660,7 +660,7 @@ static void p2m_t(ncorp_ctx *c, const P2MArgs &A) {
     k_p2m_finish<P, real><<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
 }
 
-void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, double theta) {
+void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta) {
     Cells &C = c->cells;
     ClimbArgs A{};
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.hi4 = P.hi4; A.lo4 = P.lo4;
@@ -672,9 +672,17 @@ void launch_climb_gravity(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed,
     NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
     k_leaf_gravity<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
     k_climb_geometry<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_rcrit(ncorp_ctx *c, double theta) {
+    Cells &C = c->cells;
     k_rcrit<<<16 * c->num_sms, 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
+}
 
+void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G) {
+    Cells &C = c->cells;
     P2MArgs B;
     B.x = P.x; B.y = P.y; B.z = P.z; B.m = P.m; B.hi4 = P.hi4; B.lo4 = P.lo4;
     B.first = C.first; B.count = C.count;

@@ -40,6 +40,10 @@ struct WalkArgs {
     int p2p_cap;
     int *self;
     int self_cap;
+    // per-target lists (gravity): counting sort by target cell
+    int *cnt, *offs, *cursor, *p2p_off, *p2p_src;
+    int2 *m2l_dir;
+    int m2l_dir_cap, p2p_dir_cap;
     Ctrl *ctl;
 };
 
@@ -64,9 +68,113 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
+// Exclusive prefix sums of x[0, n) by one block, written to o1 (and o2 if
+// given; either may be x itself).  Every thread takes a contiguous run.
+__device__ void block_scan_array(const int *x, int *o1, int *o2, int n, int *s_tmp) {
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = T >> 5;
+    const int per = (n + T - 1) / T, b = min(n, t * per), e = min(n, b + per);
+    int sum = 0;
+    for (int i = b; i < e; i++) sum += __ldcg(&x[i]);
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_tmp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = lane < nw ? s_tmp[lane] : 0;
+        int wi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        if (lane < nw) s_tmp[lane] = wi - v;
+    }
+    __syncthreads();
+    int run = s_tmp[wid] + incl - sum;
+    for (int i = b; i < e; i++) {
+        const int v = __ldcg(&x[i]);
+        o1[i] = run;
+        if (o2) o2[i] = run;
+        run += v;
+    }
+    __syncthreads();
+}
+
+// Directed lists from the walk's output (gravity): M2L (A, B) gives A <- B
+// and B <- A grouped by target; leaf pairs give A <- B and B <- A, self
+// leaves A <- A, grouped by target leaf.  Counting sort: counts, prefix sums,
+// scatter (entries of one target in arrival order).
+__device__ void walk_lists(const WalkArgs &A, int *s_tmp) {
+    const int nm = min(A.ctl->n_m2l, A.m2l_cap), np = min(A.ctl->n_p2p, A.p2p_cap),
+              ns = min(A.ctl->n_self, A.self_cap);
+    const int nc = A.ctl->n_cells + 1;
+    const int stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = t0; i < nm + np + ns; i += stride) {
+        if (i < nm) {
+            const int2 e = __ldcg(&A.m2l[i]);
+            atomicAdd(&A.cnt[e.x], 1);
+            atomicAdd(&A.cnt[e.y], 1);
+        } else if (i < nm + np) {
+            const int2 e = __ldcg(&A.p2p[i - nm]);
+            atomicAdd(&A.p2p_off[e.x], 1);
+            atomicAdd(&A.p2p_off[e.y], 1);
+        } else {
+            atomicAdd(&A.p2p_off[__ldcg(&A.self[i - nm - np])], 1);
+        }
+    }
+    if (!grid_sync(A.ctl)) return;
+    if (blockIdx.x == 0) {
+        block_scan_array(A.cnt, A.offs, A.cursor, nc, s_tmp);       // M2L: offsets and cursors
+        block_scan_array(A.p2p_off, A.p2p_off, A.cnt, nc, s_tmp);   // P2P: offsets (in place), cursors in cnt
+        if (threadIdx.x == 0) {
+            A.ctl->n_m2l_dir = 2 * nm;
+            A.ctl->n_p2p_dir = 2 * np + ns;
+        }
+    }
+    if (!grid_sync(A.ctl)) return;
+    for (int i = t0; i < nm + np + ns; i += stride) {
+        if (i < nm) {
+            const int2 e = __ldcg(&A.m2l[i]);
+            const int a = atomicAdd(&A.cursor[e.x], 1), b = atomicAdd(&A.cursor[e.y], 1);
+            if (a < A.m2l_dir_cap && b < A.m2l_dir_cap) {
+                A.m2l_dir[a] = make_int2(e.x, e.y);
+                A.m2l_dir[b] = make_int2(e.y, e.x);
+            } else {
+                atomicOr(&A.ctl->err, ERR_DIRECTED);
+            }
+        } else if (i < nm + np) {
+            const int2 e = __ldcg(&A.p2p[i - nm]);
+            const int a = atomicAdd(&A.cnt[e.x], 1), b = atomicAdd(&A.cnt[e.y], 1);
+            if (a < A.p2p_dir_cap && b < A.p2p_dir_cap) {
+                A.p2p_src[a] = e.y;
+                A.p2p_src[b] = e.x;
+            } else {
+                atomicOr(&A.ctl->err, ERR_DIRECTED);
+            }
+        } else {
+            const int s = __ldcg(&A.self[i - nm - np]);
+            const int a = atomicAdd(&A.cnt[s], 1);
+            if (a < A.p2p_dir_cap) A.p2p_src[a] = s;
+            else atomicOr(&A.ctl->err, ERR_DIRECTED);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
+    __shared__ int s_tmp[33];
     const int lane = threadIdx.x & 31;
     if (aborted(A.ctl)) return;
+    if (A.gravity) {   // list counters, zeroed before the first barrier of the walk
+        const int nc = A.ctl->n_cells + 1;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+            A.cnt[i] = 0;
+            A.p2p_off[i] = 0;
+        }
+    }
     volatile int *vcount = A.fcount;
     int it = 0;
     for (; it < WALK_MAX_ITERS; it++) {
@@ -232,6 +340,8 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
         if (!grid_sync(A.ctl)) return;
         if (barrier_aborted(A.ctl)) { it++; break; }
     }
+    // the generation count and the barrier snapshot are the same in every block
+    if (A.gravity && it < WALK_MAX_ITERS && !barrier_aborted(A.ctl)) walk_lists(A, s_tmp);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.ctl->walk_iters = it;
         if (!A.gravity) {
@@ -262,6 +372,8 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     A.m2l = W.m2l; A.m2l_cap = W.m2l_cap;
     A.p2p = W.p2p; A.p2p_cap = W.p2p_cap;
     A.self = W.self; A.self_cap = W.self_cap;
+    A.cnt = W.cnt; A.offs = W.offs; A.cursor = W.cursor; A.p2p_off = W.p2p_off; A.p2p_src = W.p2p_src;
+    A.m2l_dir = W.m2l_dir; A.m2l_dir_cap = W.m2l_dir_cap; A.p2p_dir_cap = W.p2p_dir_cap;
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(W.front_count, 0, sizeof(int) * (WALK_MAX_ITERS + 1), c->stream));
     k_walk_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
@@ -276,93 +388,6 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
                                                  0, c->stream));
     c->launches++;
-}
-
-// ---------------------------------------------------------------------------
-// Per-target lists (counting sort by target).
-//   M2L: every well-separated pair (A, B) gives the directed entries A <- B
-//        and B <- A, grouped by target cell.
-//   P2P: every leaf pair gives A <- B and B <- A, every self leaf A <- A,
-//        grouped by target leaf (offsets indexed by cell id).
-// ---------------------------------------------------------------------------
-__global__ void k_count_lists(const int2 *__restrict__ m2l, const int2 *__restrict__ p2p, const int *__restrict__ self,
-                              const Ctrl *ctl, int *cnt_m2l, int *cnt_p2p, int m2l_cap, int p2p_cap, int self_cap) {
-    if (aborted(ctl)) return;
-    const int nm = min(ctl->n_m2l, m2l_cap), np = min(ctl->n_p2p, p2p_cap), ns = min(ctl->n_self, self_cap);
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + np + ns; i += stride) {
-        if (i < nm) {
-            const int2 e = m2l[i];
-            atomicAdd(&cnt_m2l[e.x], 1);
-            atomicAdd(&cnt_m2l[e.y], 1);
-        } else if (i < nm + np) {
-            const int2 e = p2p[i - nm];
-            atomicAdd(&cnt_p2p[e.x], 1);
-            atomicAdd(&cnt_p2p[e.y], 1);
-        } else {
-            atomicAdd(&cnt_p2p[self[i - nm - np]], 1);
-        }
-    }
-}
-
-__global__ void k_scatter_lists(const int2 *__restrict__ m2l, const int2 *__restrict__ p2p,
-                                const int *__restrict__ self, Ctrl *ctl, int *cur_m2l, int *cur_p2p, int2 *m2l_dir,
-                                int m2l_dir_cap, int *p2p_src, int p2p_dir_cap, int m2l_cap, int p2p_cap,
-                                int self_cap) {
-    if (aborted(ctl)) return;
-    const int nm = min(ctl->n_m2l, m2l_cap), np = min(ctl->n_p2p, p2p_cap), ns = min(ctl->n_self, self_cap);
-    const int stride = gridDim.x * blockDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->n_m2l_dir = 2 * nm;
-        ctl->n_p2p_dir = 2 * np + ns;
-    }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm + np + ns; i += stride) {
-        if (i < nm) {
-            const int2 e = m2l[i];
-            const int a = atomicAdd(&cur_m2l[e.x], 1), b = atomicAdd(&cur_m2l[e.y], 1);
-            if (a < m2l_dir_cap && b < m2l_dir_cap) {
-                m2l_dir[a] = make_int2(e.x, e.y);
-                m2l_dir[b] = make_int2(e.y, e.x);
-            } else {
-                atomicOr(&ctl->err, ERR_DIRECTED);
-            }
-        } else if (i < nm + np) {
-            const int2 e = p2p[i - nm];
-            const int a = atomicAdd(&cur_p2p[e.x], 1), b = atomicAdd(&cur_p2p[e.y], 1);
-            if (a < p2p_dir_cap && b < p2p_dir_cap) {
-                p2p_src[a] = e.y;
-                p2p_src[b] = e.x;
-            } else {
-                atomicOr(&ctl->err, ERR_DIRECTED);
-            }
-        } else {
-            const int s = self[i - nm - np];
-            const int a = atomicAdd(&cur_p2p[s], 1);
-            if (a < p2p_dir_cap) p2p_src[a] = s;
-            else atomicOr(&ctl->err, ERR_DIRECTED);
-        }
-    }
-}
-
-void launch_directed_lists(ncorp_ctx *c) {
-    Cells &C = c->cells;
-    WalkLists &W = c->wl;
-    const int n = C.cap + 1;
-    // cnt (m2l) uses W.cnt, (p2p) uses W.cursor as scratch counts
-    NCORP_CUDA_CHECK(cudaMemsetAsync(W.cnt, 0, sizeof(int) * n, c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(W.p2p_off, 0, sizeof(int) * n, c->stream));
-    const int grid = 4 * c->num_sms;
-    k_count_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cnt, W.p2p_off, W.m2l_cap, W.p2p_cap,
-                                               W.self_cap); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
-    scan_exclusive(c, W.cnt, W.offs, n, nullptr);
-    scan_exclusive(c, W.p2p_off, W.p2p_off, n, nullptr);
-    NCORP_CUDA_CHECK(cudaMemcpyAsync(W.cursor, W.offs, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream));
-    NCORP_CUDA_CHECK(cudaMemcpyAsync(W.cnt, W.p2p_off, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream));
-    k_scatter_lists<<<grid, 256, 0, c->stream>>>(W.m2l, W.p2p, W.self, c->ctl, W.cursor, W.cnt, W.m2l_dir,
-                                                 W.m2l_dir_cap, W.p2p_src, W.p2p_dir_cap, W.m2l_cap, W.p2p_cap,
-                                                 W.self_cap); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 }  // namespace ncorp
