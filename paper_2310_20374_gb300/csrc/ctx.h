@@ -45,6 +45,8 @@ struct Cells {
     int item_cap = 0;
     int *leaves = nullptr;    // leaf cell ids
     int *bounds = nullptr;    // [cap][9] scratch of the build
+    int *maker = nullptr;     // [cap] scratch of the build: block that made the cell
+    int *before = nullptr;    // [cap] scratch of the build: children of its maker's earlier cells
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels
 };
 

@@ -110,6 +110,8 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.leaves, cap);
     dalloc(C.bounds, static_cast<size_t>(cap) * 9);
     dalloc(C.blocksum, 8192);
+    dalloc(C.maker, cap);
+    dalloc(C.before, cap);
     WalkLists &W = c->wl;
     dalloc(W.cnt, cap + 1); dalloc(W.offs, cap + 1); dalloc(W.cursor, cap + 1); dalloc(W.p2p_off, cap + 1);
     C.cap = cap;
@@ -983,7 +985,7 @@ void ncorp_free(ncorp_ctx *c) {
         dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
         dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
         dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf);
-        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum);
+        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before);
         WalkLists &W = c->wl;
         dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
         dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);

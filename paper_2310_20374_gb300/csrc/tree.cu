@@ -42,12 +42,21 @@ __device__ __forceinline__ int lower_bound_u64(const uint64_t *__restrict__ a, i
 }
 
 // ---------------------------------------------------------------------------
-// Build: one cooperative launch, one pass per level.  Phase 1 (warp per cell
-// of the level): a cell with more than s moonlets finds the boundaries of its
-// octants by binary search on the next 3 key bits (the Hilbert digit of the
-// child), so the non-empty children come out in Hilbert order.  Phase 2: a
-// grid-wide exclusive scan of the children counts places the children of the
-// level contiguously after it, in the order of their parents.
+// Build: one cooperative launch, one grid barrier per level.  The cells of a
+// level are shared evenly among the blocks.  Per level, a block
+//   1. places the children of its cells: a cell's children follow the level
+//      in the order of their parents, at
+//        level end + (children of the cells made by blocks before the cell's
+//        maker) + (children of the cells its maker made before it),
+//      both terms published before the barrier; then writes them;
+//   2. for each child it made with more than s moonlets, finds the
+//      boundaries of its octants on the next 3 key bits (the Hilbert digit of
+//      the grandchild), so the children of every cell come out in Hilbert
+//      order, and publishes, for the next level, the running count of
+//      grandchildren over the cells it made and its total.
+// Octant boundaries: boundary o (o = 1..7) is the first moonlet whose key is
+// >= (prefix, o); four lanes search for it together, cutting the range in
+// five per round.
 // ---------------------------------------------------------------------------
 struct BuildArgs {
     const uint64_t *key;
@@ -56,6 +65,7 @@ struct BuildArgs {
     int *level, *first, *count, *child0, *nchild, *parent;
     uint32_t *cx, *cy, *cz;
     int *bounds, *blocksum;
+    int *maker, *before;    // per cell: the block that made it, children of its maker's earlier cells
     Ctrl *ctl;
 };
 
@@ -67,6 +77,8 @@ __global__ void k_build_init(BuildArgs A) {
     A.nchild[0] = 0;
     A.parent[0] = -1;
     A.cx[0] = A.cy[0] = A.cz[0] = 0;
+    A.maker[0] = 0;
+    A.before[0] = 0;
     A.ctl->level_start[0] = 0;
     A.ctl->level_start[1] = 1;
     A.ctl->n_cells = 1;
@@ -75,71 +87,159 @@ __global__ void k_build_init(BuildArgs A) {
     A.ctl->bar_count = 0;
 }
 
+// Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
+// bounds[c][0..8] (b_0 = f, b_8 = f + cnt), and its number of non-empty
+// octants (returned on every lane).  Called by a whole warp.
+__device__ int octant_bounds(const BuildArgs &A, int c, int f, int cnt, int lev, int lane) {
+    const uint64_t pref = __ldg(&A.key[f]) >> (63 - 3 * lev);
+    const int shift = 60 - 3 * lev;
+    const int grp = lane >> 2, j = lane & 3;           // boundary o = grp + 1 for grp < 7
+    const bool searching = grp < 7;
+    const uint64_t target = ((pref << 3) | static_cast<uint64_t>(grp + 1)) << shift;
+    int lo = f, hi = f + cnt;                          // the boundary lies in [lo, hi]
+    while (true) {
+        const bool wide = searching && hi - lo > 4;
+        if (!__any_sync(0xffffffffu, wide)) break;
+        bool less = false;
+        int sj = 0;
+        if (wide) {
+            sj = lo + static_cast<int>((static_cast<long long>(hi - lo) * (j + 1)) / 5);
+            less = __ldg(&A.key[sj]) < target;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, less);
+        const int cl = __popc((bal >> (4 * grp)) & 0xfu);    // samples below the target (monotone)
+        const int s_lo = __shfl_sync(0xffffffffu, sj, (lane & ~3) + max(cl - 1, 0));
+        const int s_hi = __shfl_sync(0xffffffffu, sj, (lane & ~3) + min(cl, 3));
+        if (wide) {
+            const int nlo = cl > 0 ? s_lo + 1 : lo;
+            const int nhi = cl < 4 ? s_hi : hi;
+            lo = nlo;
+            hi = nhi;
+        }
+    }
+    const bool below = searching && lo + j < hi && __ldg(&A.key[lo + j]) < target;
+    const unsigned bal = __ballot_sync(0xffffffffu, below);
+    const int b_o = lo + __popc((bal >> (4 * grp)) & 0xfu);
+    // lane k < 9 holds b_k: b_0 = f, b_1..b_7 from the groups, b_8 = f + cnt
+    const int from_grp = __shfl_sync(0xffffffffu, b_o, 4 * max(lane - 1, 0));
+    const int b = lane == 0 ? f : (lane < 8 ? from_grp : f + cnt);
+    const int bn = __shfl_down_sync(0xffffffffu, b, 1);
+    const unsigned ne = __ballot_sync(0xffffffffu, lane < 8 && bn > b);
+    if (lane < 9) A.bounds[(size_t)c * 9 + lane] = b;
+    return __popc(ne);
+}
+
+// For the cells [cb, ce) this block made (level lev): octant bounds, children
+// counts, and the running count over them (before[]); returns the total.
+__device__ int made_cells(const BuildArgs &A, int cb, int ce, int lev, int *s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = cb + wid; c < ce; c += nw) {
+        if (c >= A.cap) break;
+        const int cnt = __ldcg(&A.count[c]), f = __ldcg(&A.first[c]);
+        int nch = 0;
+        if (cnt > A.s && lev < MAX_LEVEL) nch = octant_bounds(A, c, f, cnt, lev, lane);
+        if (lane == 0) A.nchild[c] = nch;
+    }
+    __syncthreads();
+    int run = 0;
+    if (wid == 0) {
+        for (int c0 = cb; c0 < ce; c0 += 32) {
+            const int c = c0 + lane;
+            const int v = (c < ce && c < A.cap) ? __ldcg(&A.nchild[c]) : 0;
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (c < ce && c < A.cap) {
+                A.before[c] = run + incl - v;
+                A.maker[c] = blockIdx.x;
+            }
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) s_red[0] = run;
+    }
+    __syncthreads();
+    const int t = s_red[0];
+    __syncthreads();
+    return t;
+}
+
 __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __shared__ int s_red[32];
-    __shared__ int s_base;
+    __shared__ int s_pre[4097];      // children made by blocks before each block (grid <= 4096)
+    __shared__ int s_lo, s_hi;
     volatile Ctrl *vc = A.ctl;
+    const int G = gridDim.x;
+    {
+        const int t = made_cells(A, 0, blockIdx.x == 0 ? 1 : 0, 0, s_red);
+        if (threadIdx.x == 0) A.blocksum[blockIdx.x] = t;
+    }
+    if (!grid_sync(A.ctl)) return;
     for (int lev = 0; lev < MAX_LEVEL; lev++) {
         const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
         if (ls >= le) break;
-        const int ncl = le - ls;
-        const int chunk = (ncl + gridDim.x - 1) / gridDim.x;
-        const int cb = min(le, ls + blockIdx.x * chunk), ce = min(le, cb + chunk);
-        // ---- phase 1: octant boundaries
-        int wsum = 0;
-        for (int c = cb + wid; c < ce; c += nw) {
-            const int cnt = c < A.cap ? __ldcg(&A.count[c]) : 0, f = c < A.cap ? __ldcg(&A.first[c]) : 0;
-            int nch = 0;
-            if (cnt > A.s && c < A.cap) {
-                const uint64_t pref = A.key[f] >> (63 - 3 * lev);
-                const int shift = 60 - 3 * lev;
-                int b = f + cnt;
-                if (lane < 8) b = lower_bound_u64(A.key, f, f + cnt, ((pref << 3) | (uint64_t)lane) << shift);
-                const int bn = __shfl_down_sync(0xffffffffu, b, 1);
-                const unsigned mask = __ballot_sync(0xffffffffu, lane < 8 && bn > b);
-                nch = __popc(mask);
-                if (lane < 9) A.bounds[(size_t)c * 9 + lane] = b;
+        const int *bsum = A.blocksum + (lev & 1) * G;
+        // prefix of the published totals (every block computes it; each thread a run of them)
+        {
+            const int T = blockDim.x, per = (G + T - 1) / T;
+            const int b0 = min(G, (int)threadIdx.x * per), b1 = min(G, b0 + per);
+            int sum = 0;
+            for (int b = b0; b < b1; b++) sum += ((volatile const int *)bsum)[b];
+            int incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
             }
-            if (lane == 0 && c < A.cap) A.nchild[c] = nch;
-            wsum += nch;
-        }
-        if (lane == 0) s_red[wid] = wsum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < nw; w++) t += s_red[w];
-            A.blocksum[blockIdx.x] = t;
-        }
-        if (!grid_sync(A.ctl)) return;
-        // ---- phase 2: place the children of this level
-        if (wid == 0) {
-            int t = 0;
-            for (int b = lane; b < (int)blockIdx.x; b += 32) t += ((volatile int *)A.blocksum)[b];
-            t = warp_sum(t);
-            int run = le + t;
-            for (int c0 = cb; c0 < ce; c0 += 32) {
-                const int c = c0 + lane;
-                const int v = (c < ce && c < A.cap) ? ((volatile int *)A.nchild)[c] : 0;
-                int incl = v;
+            if (lane == 31) s_red[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const int v = lane < nw ? s_red[lane] : 0;
+                int wi = v;
                 for (int o = 1; o < 32; o <<= 1) {
-                    int u = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += u;
+                    const int u = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= o) wi += u;
                 }
-                if (c < ce && c < A.cap) A.child0[c] = v > 0 ? run + incl - v : -1;
-                run += __shfl_sync(0xffffffffu, incl, 31);
+                if (lane < nw) s_red[lane] = wi - v;
+                if (lane == nw - 1) s_pre[G] = wi;
             }
-            if (lane == 0) s_base = run;
+            __syncthreads();
+            int run = s_red[wid] + incl - sum;
+            for (int b = b0; b < b1; b++) {
+                const int v = ((volatile const int *)bsum)[b];
+                s_pre[b] = run;
+                run += v;
+            }
         }
         __syncthreads();
+        const int total = s_pre[G];
+        // this block's share of the level, and the children it will make
+        const int ncl = le - ls;
+        const int chunk = (ncl + G - 1) / G;
+        const int cb = min(le, ls + (int)blockIdx.x * chunk), ce = min(le, cb + chunk);
+        if (threadIdx.x == 0) {
+            s_lo = 1 << 30;
+            s_hi = -1;
+        }
+        __syncthreads();
+        // ---- 1. place and write the children of the block's cells
         for (int c = cb + wid; c < ce; c += nw) {
             if (c >= A.cap) break;
-            const int nch = ((volatile int *)A.nchild)[c];
-            if (nch == 0) continue;
-            const int c0 = ((volatile int *)A.child0)[c];
-            int b = 0, bn = 0;
-            if (lane < 9) b = ((volatile int *)A.bounds)[(size_t)c * 9 + lane];
-            bn = __shfl_down_sync(0xffffffffu, b, 1);
+            const int nch = __ldcg(&A.nchild[c]);
+            if (nch == 0) {
+                if (lane == 0) A.child0[c] = -1;
+                continue;
+            }
+            const int c0 = le + s_pre[__ldcg(&A.maker[c])] + __ldcg(&A.before[c]);
+            if (lane == 0) {
+                A.child0[c] = c0;
+                atomicMin(&s_lo, c0);
+                atomicMax(&s_hi, c0 + nch);
+            }
+            int b = 0;
+            if (lane < 9) b = __ldcg(&A.bounds[(size_t)c * 9 + lane]);
+            const int bn = __shfl_down_sync(0xffffffffu, b, 1);
             const bool ne = lane < 8 && bn > b;
             const unsigned mask = __ballot_sync(0xffffffffu, ne);
             if (ne) {
@@ -160,10 +260,17 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
                 }
             }
         }
-        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-            A.ctl->level_start[lev + 2] = s_base;
-            A.ctl->n_cells = s_base;
-            if (s_base > le) A.ctl->max_level = lev + 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            A.ctl->level_start[lev + 2] = le + total;
+            A.ctl->n_cells = le + total;
+            if (total > 0) A.ctl->max_level = lev + 1;
+        }
+        __syncthreads();
+        // ---- 2. the children this block made (a contiguous range): bounds, running counts
+        const int mb = s_hi >= 0 ? s_lo : 0, me = s_hi >= 0 ? s_hi : 0;
+        {
+            const int t = made_cells(A, mb, me, lev + 1, s_red);
+            if (threadIdx.x == 0) A.blocksum[((lev + 1) & 1) * G + blockIdx.x] = t;
         }
         if (!grid_sync(A.ctl)) return;
     }
@@ -196,11 +303,13 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
     A.n = n; A.s = s; A.cap = C.cap;
     A.level = C.level; A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
     A.parent = C.parent; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
-    A.bounds = C.bounds; A.blocksum = C.blocksum; A.ctl = c->ctl;
+    A.bounds = C.bounds; A.blocksum = C.blocksum; A.maker = C.maker; A.before = C.before; A.ctl = c->ctl;
     k_build_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     const int block = 256;
-    int grid = coop_grid(c, reinterpret_cast<const void *>(k_build), block, 0);
+    // about one block per thousand moonlets (a level holds at most ~n/s*8 cells): enough warps for the
+    // widest level, and few blocks at small n so that the per-level barriers stay short
+    int grid = std::min(coop_grid(c, reinterpret_cast<const void *>(k_build), block, 0), std::max(16, n / 1024));
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_build), dim3(grid), dim3(block),
                                                  args, 0, c->stream));
