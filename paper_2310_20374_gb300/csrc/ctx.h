@@ -106,8 +106,9 @@ struct ncorp_ctx {
     uint64_t *key_alt = nullptr;
     uint32_t *idx = nullptr, *idx_alt = nullptr;
     int *work_counter = nullptr;     // dynamic work distribution of persistent kernels
-    int *tile_hist = nullptr;
+    int *tile_hist = nullptr;        // radix sort: status words and digit histograms
     int tile_hist_cap = 0;
+    unsigned radix_epoch = 0;        // radix sort calls so far
     int *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
     double *stage = nullptr;         // [n][3] AoS staging

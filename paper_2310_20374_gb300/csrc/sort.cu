@@ -269,75 +269,75 @@ void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------------------
 // LSD radix sort of (uint64 key, uint32 value), 8-bit digits, all passes in
-// one cooperative launch.  Each pass: per-tile digit histograms (digit-major
-// table), a grid barrier, prefix sums along each digit's row (one warp per
-// row) and the rows' totals, a barrier, each block's scan of the 256 totals
-// (digit starts), and the stable scatter; a barrier ends the pass.
-// Stability inside a tile comes from warp-synchronous ranking: each warp owns
-// a contiguous slice of the tile and walks it 32 keys at a time, ranking equal
-// digits with __match_any_sync; warps are then ordered by a per-digit prefix.
+// one cooperative launch.  A first sweep counts the digits of every pass at
+// once (global histograms, hence the digit starts of each pass).  Then each
+// pass ranks every tile's keys locally (stable, warp-synchronous with
+// __match_any_sync: each warp owns a contiguous slice of the tile, warps are
+// ordered by a per-digit prefix), and finds, per digit, how many keys of the
+// tiles before it carry the digit by decoupled look-back (Merrill & Garland,
+// "Single-pass parallel prefix scan with decoupled look-back", 2016): a tile
+// publishes its own count, reads its predecessors' words eight at a time
+// back to the nearest published running total, then publishes its own
+// running total.  A status word holds (tag, kind, value); the tag names the
+// sort call and the pass, so words of other passes or calls are never
+// mistaken for this one's and nothing has to be cleared.  Waits are bounded:
+// a wait that runs out sets ERR_TIMEOUT and the call fails.  One grid
+// barrier ends each pass.
 // ---------------------------------------------------------------------------
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_SLICE = RS_TILE / RS_W;
+constexpr int RS_MAX_PASSES = 8;
+constexpr unsigned long long RS_AGG = 0ull, RS_INC = 1ull << 31;   // kind bit of a status word
 
 struct RadixArgs {
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
     int n, ntiles, passes;
-    int *hist;     // [256][ntiles]
-    int *rowsum;   // [256]
+    unsigned long long *status;   // [ntiles][256]: tag << 32 | kind << 31 | value
+    int *ghist;                   // [RS_MAX_PASSES][256], zero on entry
+    unsigned epoch;               // distinct for every sort call on these buffers
     Ctrl *ctl;
 };
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
 
 __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     __shared__ int s_cnt[RS_W][256];
     __shared__ int s_start[256];
+    __shared__ int s_excl[256];
     __shared__ int s_warp[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gw = blockIdx.x * RS_W + w, nwarps = gridDim.x * RS_W;
     const unsigned lt = (1u << lane) - 1u;
     const int n = A.n, ntiles = A.ntiles;
+    // ---- 0. digit counts of every pass (s_cnt reused as [8][256])
+    {
+        int *s_h = &s_cnt[0][0];
+        for (int i = threadIdx.x; i < RS_MAX_PASSES * 256; i += RS_T) s_h[i] = 0;
+        __syncthreads();
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const long long base = static_cast<long long>(tile) * RS_TILE;
+            for (int k = 0; k < RS_I; k++) {
+                const long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
+                if (i < n) {
+                    const uint64_t key = A.k0[i];
+                    for (int p = 0; p < A.passes; p++) atomicAdd(&s_h[p * 256 + ((key >> (8 * p)) & 0xffu)], 1);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < A.passes * 256; i += RS_T)
+            if (s_h[i]) atomicAdd(&A.ghist[i], s_h[i]);
+    }
+    if (!grid_sync(A.ctl)) return;
     for (int ps = 0; ps < A.passes; ps++) {
         const int shift = 8 * ps;
         const uint64_t *kin = (ps & 1) ? A.k1 : A.k0;
         const uint32_t *vin = (ps & 1) ? A.v1 : A.v0;
         uint64_t *kout = (ps & 1) ? A.k0 : A.k1;
         uint32_t *vout = (ps & 1) ? A.v0 : A.v1;
-        // 1. tile histograms
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            s_start[threadIdx.x] = 0;
-            __syncthreads();
-            const long long base = static_cast<long long>(tile) * RS_TILE;
-            for (int k = 0; k < RS_I; k++) {
-                const long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
-                if (i < n) atomicAdd(&s_start[(__ldcg(&kin[i]) >> shift) & 0xffu], 1);
-            }
-            __syncthreads();
-            A.hist[threadIdx.x * ntiles + tile] = s_start[threadIdx.x];
-            __syncthreads();
-        }
-        if (!grid_sync(A.ctl)) return;
-        // 2. exclusive prefix along each digit's row, row totals
-        for (int row = gw; row < 256; row += nwarps) {
-            int carry = 0;
-            for (int t0 = 0; t0 < ntiles; t0 += 32) {
-                const int t = t0 + lane;
-                const int v = t < ntiles ? __ldcg(&A.hist[row * ntiles + t]) : 0;
-                int inc = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int u = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += u;
-                }
-                if (t < ntiles) A.hist[row * ntiles + t] = carry + inc - v;
-                carry += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            if (lane == 0) A.rowsum[row] = carry;
-        }
-        if (!grid_sync(A.ctl)) return;
-        // 3. digit starts
-        s_start[threadIdx.x] = block_excl_scan(__ldcg(&A.rowsum[threadIdx.x]), s_warp, nullptr);
-        __syncthreads();
-        // 4. stable scatter
+        const unsigned long long tag = static_cast<unsigned long long>(A.epoch * RS_MAX_PASSES + ps) << 32;
+        s_start[threadIdx.x] = block_excl_scan(__ldcg(&A.ghist[ps * 256 + threadIdx.x]), s_warp, nullptr);
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
             __syncwarp();
@@ -360,13 +360,49 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
                 __syncwarp();
             }
             __syncthreads();
-            {   // exclusive prefix over warps, per digit
+            {
                 const int d = threadIdx.x;
-                int acc = 0;
+                int acc = 0;   // exclusive prefix over warps; acc ends as the tile's count of digit d
                 for (int ww = 0; ww < RS_W; ww++) {
                     const int t = s_cnt[ww][d];
                     s_cnt[ww][d] = acc;
                     acc += t;
+                }
+                unsigned long long *st = A.status + static_cast<size_t>(tile) * 256 + d;
+                if (tile == 0) {
+                    *reinterpret_cast<volatile unsigned long long *>(st) = tag | RS_INC | static_cast<unsigned>(acc);
+                    s_excl[d] = 0;
+                } else {
+                    *reinterpret_cast<volatile unsigned long long *>(st) = tag | RS_AGG | static_cast<unsigned>(acc);
+                    // look back, eight predecessors at a time, to the nearest running total
+                    int excl = 0, t = tile - 1;
+                    bool done = false;
+                    while (!done) {
+                        const int m = min(8, t + 1);
+                        unsigned long long wv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            wv[u] = u < m ? ld_status(A.status + static_cast<size_t>(t - u) * 256 + d) : 0ull;
+                        for (int u = 0; u < m && !done; u++) {
+                            long long spins = 0;
+                            while ((wv[u] & 0xffffffff00000000ull) != tag) {
+                                if (++spins > (1ll << 22)) {
+                                    atomicOr(&A.ctl->err, ERR_TIMEOUT);
+                                    wv[u] = tag | RS_INC;
+                                    break;
+                                }
+                                __nanosleep(32);
+                                wv[u] = ld_status(A.status + static_cast<size_t>(t - u) * 256 + d);
+                            }
+                            excl += static_cast<int>(wv[u] & 0x7fffffffull);
+                            if (wv[u] & RS_INC) done = true;
+                        }
+                        t -= m;
+                        if (t < 0) done = true;
+                    }
+                    *reinterpret_cast<volatile unsigned long long *>(st) =
+                        tag | RS_INC | static_cast<unsigned>(excl + acc);
+                    s_excl[d] = excl;
                 }
             }
             __syncthreads();
@@ -375,14 +411,14 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
                 const long long i = base + r * 32 + lane;
                 if (i < n) {
                     const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
-                    const int pos = s_start[d] + __ldcg(&A.hist[d * ntiles + tile]) + s_cnt[w][d] + rank[r];
+                    const int pos = s_start[d] + s_excl[d] + s_cnt[w][d] + rank[r];
                     kout[pos] = kk[r];
                     vout[pos] = vv[r];
                 }
             }
             __syncthreads();
         }
-        if (!grid_sync(A.ctl)) return;
+        if (ps + 1 < A.passes && !grid_sync(A.ctl)) return;
     }
 }
 
@@ -393,18 +429,23 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
                     int bits) {
     if (n <= 1) return;
     const int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    const int need = 256 * ntiles + 256;
+    const int need = 2 * 256 * ntiles + RS_MAX_PASSES * 256;   // status words (2 ints each), histograms
     if (c->tile_hist_cap < need) {
         if (c->tile_hist) cudaFree(c->tile_hist);
         c->tile_hist_cap = need + 4096;
         NCORP_CUDA_CHECK(cudaMalloc(&c->tile_hist, sizeof(int) * c->tile_hist_cap));
+        NCORP_CUDA_CHECK(cudaMemsetAsync(c->tile_hist, 0, sizeof(int) * c->tile_hist_cap, c->stream));
     }
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
     RadixArgs A;
     A.k0 = keys; A.k1 = keys_alt; A.v0 = vals; A.v1 = vals_alt;
     A.n = n; A.ntiles = ntiles; A.passes = passes;
-    A.hist = c->tile_hist; A.rowsum = c->tile_hist + 256 * ntiles; A.ctl = c->ctl;
+    A.status = reinterpret_cast<unsigned long long *>(c->tile_hist);
+    A.ghist = c->tile_hist + 2 * 256 * ntiles;
+    A.epoch = ++c->radix_epoch;
+    A.ctl = c->ctl;
+    NCORP_CUDA_CHECK(cudaMemsetAsync(A.ghist, 0, sizeof(int) * RS_MAX_PASSES * 256, c->stream));
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
                                                                    RS_T, 0));
@@ -501,12 +542,14 @@ struct StaticScratch {
     uint64_t key_alt[STATIC_MAX_N];
     uint32_t idx[STATIC_MAX_N], idx_alt[STATIC_MAX_N];
     uint32_t qx[STATIC_MAX_N], qy[STATIC_MAX_N], qz[STATIC_MAX_N];
-    int hist[256 * STATIC_TILES + 256];
+    unsigned long long status[256 * STATIC_TILES];
+    int ghist[RS_MAX_PASSES * 256];
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
 __global__ void k_static_reset(StaticScratch *S) {
+    for (int i = 0; i < RS_MAX_PASSES * 256; i++) S->ghist[i] = 0;
     Ctrl &c = S->ctl;
     c.err = 0;
     c.bar_count = 0;
@@ -533,6 +576,7 @@ struct StaticDevice {
     StaticScratch *ptr = nullptr;
     int num_sms = 0;
     int radix_per_sm = 0;
+    unsigned epoch = 0;     // sort calls so far (tags the status words of each call)
 };
 
 static std::mutex g_static_mutex;
@@ -556,6 +600,7 @@ static cudaError_t static_setup(int dev, StaticDevice &out) {
         d.radix_per_sm = std::max(1, std::min(per_sm, 2));
         d.ptr = static_cast<StaticScratch *>(p);
     }
+    d.epoch++;   // a new tag for this call's sort
     out = d;
     return cudaSuccess;
 }
@@ -595,8 +640,9 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
         A.n = n;
         A.ntiles = (n + RS_TILE - 1) / RS_TILE;
         A.passes = 8;   // 3 x 21 key bits, rounded up to an even number of 8-bit passes
-        A.hist = S->hist;
-        A.rowsum = S->hist + 256 * A.ntiles;
+        A.status = S->status;
+        A.ghist = S->ghist;
+        A.epoch = d.epoch;
         A.ctl = &S->ctl;
         const int grid = std::min(A.ntiles, d.radix_per_sm * d.num_sms);
         void *args[] = {&A};
