@@ -270,10 +270,9 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
 // ---------------------------------------------------------------------------
 // Evaluation kernel: one block of EV_THREADS threads per leaf, leaves handed
 // out dynamically.  The leaf's m targets (taken EV_THREADS at a time if the
-// leaf is larger) occupy T = pow2ceil(m) slots, and the block's threads form
-// G = EV_THREADS / T groups: thread (g, t) sums the staged sources
-// k = g, g + G, g + 2G, ... for target t, so a leaf of a few moonlets keeps
-// all lanes busy.  The G partial sums of a target are then added in group
+// leaf is larger) are taken by G = floor(EV_THREADS / m) groups of m threads:
+// thread (g, t) sums the staged sources k = g, g + G, g + 2G, ... for target
+// t, so a leaf of a few moonlets keeps the lanes busy.  The G partial sums of a target are then added in group
 // order.  The direct list is staged
 // EV_BUF moonlets at a time, cutting source leaves where the buffer ends.
 // ---------------------------------------------------------------------------
@@ -309,10 +308,8 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
         const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
         for (int t0 = 0; t0 < cnt; t0 += EV_THREADS) {
             const int m = min(EV_THREADS, cnt - t0);
-            int T = 1;
-            while (T < m) T <<= 1;
-            const int G = EV_THREADS / T, tt = tid & (T - 1), g = tid / T;
-            const bool act = tt < m;
+            const int G = EV_THREADS / m, g = tid / m, tt = tid - g * m;
+            const bool act = g < G;   // the last EV_THREADS - G m threads only help with staging
             const int i = f + t0 + (act ? tt : 0);
             const float4 th = A.hi4[i], tl = A.lo4[i];
             const double X = A.x[i], Y = A.y[i], Z = A.z[i];
@@ -370,12 +367,14 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
                 si = S.next_si;
                 soff = S.next_soff;
                 __syncthreads();
-                if constexpr (f32) {
+                if (act) {
+                    if constexpr (f32) {
 #pragma unroll 4
-                    for (int k = g; k < total; k += G) p2p_f32(sh[k], sl[k], th, tl, ax, ay, az);
-                } else {
+                        for (int k = g; k < total; k += G) p2p_f32(sh[k], sl[k], th, tl, ax, ay, az);
+                    } else {
 #pragma unroll 2
-                    for (int k = g; k < total; k += G) p2p_f64(bx[k], by[k], bz[k], bm[k], X, Y, Z, ax, ay, az);
+                        for (int k = g; k < total; k += G) p2p_f64(bx[k], by[k], bz[k], bm[k], X, Y, Z, ax, ay, az);
+                    }
                 }
             }
             if (G > 1) {
@@ -387,9 +386,9 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
                 if (g == 0) {
                     ax = ay = az = real(0);
                     for (int q = 0; q < G; q++) {
-                        ax += S.red[0][q * T + tt];
-                        ay += S.red[1][q * T + tt];
-                        az += S.red[2][q * T + tt];
+                        ax += S.red[0][q * m + tt];
+                        ay += S.red[1][q * m + tt];
+                        az += S.red[2][q * m + tt];
                     }
                 }
             }
