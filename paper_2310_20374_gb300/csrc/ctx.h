@@ -94,6 +94,7 @@ struct ncorp_ctx {
 
     int64_t n_cap = 0;
     int n = 0;
+    int cur_n = 0;                  // moonlets of the tree being built or walked
     int p = 0;
     double theta = 0.5;
     int s = 0;

@@ -383,6 +383,7 @@ int finish(ncorp_ctx *c, bool both = false) {
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
                 int n) {
+    c->cur_n = n;
     {
         Stage st(c, NCORP_STAGE_SORT);
         launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);

@@ -200,9 +200,26 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
             int split_kind = 0;       // 0 none, 1 self-split of cA, 2 split cA against cB, 3 split cB against cA
             bool split_forced = false;
             long long dpair = 0, dself = 0, inter = 0;
+            // every cell field this lane may need, loaded in one round
+            int nA = 0, nB = 0, chA = 0, chB = 0, c0A = 0, c0B = 0;
+            float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha, la = ha, lb = ha;
+            double rA = 0.0, rB = 0.0;
             if (valid) {
-                const int nA = A.count[cA], nB = A.count[cB];
-                const bool leafA = A.nchild[cA] == 0, leafB = A.nchild[cB] == 0;
+                nA = __ldg(&A.count[cA]);
+                nB = __ldg(&A.count[cB]);
+                chA = __ldg(&A.nchild[cA]);
+                chB = __ldg(&A.nchild[cB]);
+                c0A = __ldg(&A.child0[cA]);
+                c0B = __ldg(&A.child0[cB]);
+                ha = __ldg(&A.H[cA]);
+                hb = __ldg(&A.H[cB]);
+                la = __ldg(&A.Lo[cA]);
+                lb = __ldg(&A.Lo[cB]);
+                rA = __ldg(&A.rcrit[cA]);
+                rB = __ldg(&A.rcrit[cB]);
+            }
+            if (valid) {
+                const bool leafA = chA == 0, leafB = chB == 0;
                 if (cA == cB) {
                     if (forced || nA <= A.n_cs || leafA) {
                         if (!forced) {
@@ -227,13 +244,11 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
                         // relative and r_crit is rounded once; outside a band of
                         // +-2^-14 around the threshold the FP32 answer is the FP64 one,
                         // inside it the exact FP64 test decides.
-                        const float4 ha = A.H[cA], hb = A.H[cB], la = A.Lo[cA], lb = A.Lo[cB];
                         const float fx = (ha.x - hb.x) + (la.x - lb.x);
                         const float fy = (ha.y - hb.y) + (la.y - lb.y);
                         const float fz = (ha.z - hb.z) + (la.z - lb.z);
                         const float d2f = fx * fx + fy * fy + fz * fz;
                         const float tf = ha.w + hb.w, t2f = tf * tf;
-                        const double rA = A.rcrit[cA], rB = A.rcrit[cB];
                         bool sep;
                         if (d2f > 1e-30f && d2f > t2f * (1.0f + 0x1p-14f)) {
                             sep = true;
@@ -282,57 +297,70 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
                 if (inter) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_inter),
                                      static_cast<unsigned long long>(inter));
             }
-            // outputs
-            {
-                const int slot = warp_append(&A.ctl->n_m2l, emit_m2l);
-                if (emit_m2l) {
-                    if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
-                    else atomicOr(&A.ctl->err, ERR_M2L);
-                }
+            // outputs: one atomic per list per warp, the four issued together
+            int c0 = 0, nch = 0, k = 0;
+            if (split_kind == 1) {
+                c0 = c0A;
+                nch = chA;
+                k = nch * (nch + 1) / 2;
+            } else if (split_kind == 2) {
+                c0 = c0A;
+                nch = chA;
+                k = nch;
+            } else if (split_kind == 3) {
+                c0 = c0B;
+                nch = chB;
+                k = nch;
             }
-            {
-                const int slot = warp_append(&A.ctl->n_p2p, emit_p2p);
-                if (emit_p2p) {
-                    if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
-                    else atomicOr(&A.ctl->err, ERR_P2P);
-                }
+            const unsigned bm = __ballot_sync(0xffffffffu, emit_m2l), bp = __ballot_sync(0xffffffffu, emit_p2p),
+                           bs = __ballot_sync(0xffffffffu, emit_self);
+            int kin = k;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, kin, o);
+                if (lane >= o) kin += v;
             }
-            {
-                const int slot = warp_append(&A.ctl->n_self, emit_self);
-                if (emit_self) {
-                    if (slot < A.self_cap) A.self[slot] = cA;
-                    else atomicOr(&A.ctl->err, ERR_P2P);
-                }
+            const int ktot = __shfl_sync(0xffffffffu, kin, 31);
+            int base_m = 0, base_p = 0, base_s = 0, base_f = 0;
+            if (lane == 0) {
+                if (bm) base_m = atomicAdd(&A.ctl->n_m2l, __popc(bm));
+                if (bp) base_p = atomicAdd(&A.ctl->n_p2p, __popc(bp));
+                if (bs) base_s = atomicAdd(&A.ctl->n_self, __popc(bs));
+                if (ktot) base_f = atomicAdd(ncount, ktot);
             }
-            {
-                int k = 0, c0 = 0, nch = 0;
-                if (split_kind == 1) {
-                    c0 = A.child0[cA];
-                    nch = A.nchild[cA];
-                    k = nch * (nch + 1) / 2;
-                } else if (split_kind == 2) {
-                    c0 = A.child0[cA];
-                    nch = A.nchild[cA];
-                    k = nch;
-                } else if (split_kind == 3) {
-                    c0 = A.child0[cB];
-                    nch = A.nchild[cB];
-                    k = nch;
-                }
-                int slot = warp_append(ncount, k);
-                if (k > 0) {
-                    if (slot + k > A.front_cap) {
-                        atomicOr(&A.ctl->err, ERR_FRONTIER);
+            base_m = __shfl_sync(0xffffffffu, base_m, 0);
+            base_p = __shfl_sync(0xffffffffu, base_p, 0);
+            base_s = __shfl_sync(0xffffffffu, base_s, 0);
+            base_f = __shfl_sync(0xffffffffu, base_f, 0);
+            const unsigned lt = (1u << lane) - 1u;
+            if (emit_m2l) {
+                const int slot = base_m + __popc(bm & lt);
+                if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
+                else atomicOr(&A.ctl->err, ERR_M2L);
+            }
+            if (emit_p2p) {
+                const int slot = base_p + __popc(bp & lt);
+                if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
+                else atomicOr(&A.ctl->err, ERR_P2P);
+            }
+            if (emit_self) {
+                const int slot = base_s + __popc(bs & lt);
+                if (slot < A.self_cap) A.self[slot] = cA;
+                else atomicOr(&A.ctl->err, ERR_P2P);
+            }
+            if (k > 0) {
+                int slot = base_f + kin - k;
+                if (slot + k > A.front_cap) {
+                    atomicOr(&A.ctl->err, ERR_FRONTIER);
+                } else {
+                    const int fl = split_forced ? FORCED : 0;
+                    if (split_kind == 1) {
+                        for (int a = 0; a < nch; a++)
+                            for (int b = a; b < nch; b++) nxt[slot++] = make_int2(c0 + a, (c0 + b) | fl);
+                    } else if (split_kind == 2) {
+                        for (int a = 0; a < nch; a++) nxt[slot++] = make_int2(c0 + a, cB | fl);
                     } else {
-                        const int fl = split_forced ? FORCED : 0;
-                        if (split_kind == 1) {
-                            for (int a = 0; a < nch; a++)
-                                for (int b = a; b < nch; b++) nxt[slot++] = make_int2(c0 + a, (c0 + b) | fl);
-                        } else if (split_kind == 2) {
-                            for (int a = 0; a < nch; a++) nxt[slot++] = make_int2(c0 + a, cB | fl);
-                        } else {
-                            for (int b = 0; b < nch; b++) nxt[slot++] = make_int2(cA, (c0 + b) | fl);
-                        }
+                        for (int b = 0; b < nch; b++) nxt[slot++] = make_int2(cA, (c0 + b) | fl);
                     }
                 }
             }
@@ -383,7 +411,8 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
                                                                    256, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    const int grid = coop_blocks(c, per_sm);
+    // about one block per 640 moonlets (frontiers peak near a third of n pairs), 32 to the cooperative limit
+    const int grid = std::min(coop_blocks(c, per_sm), std::max(32, c->cur_n / 640));
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
                                                  0, c->stream));
