@@ -102,7 +102,7 @@ struct Ctrl {
     int n_p2p_dir;
     unsigned bar_count;
     unsigned bar_gen;
-    int bar_snap;          // error word as seen by the last block to reach the latest barrier
+    int walk_abort[3];     // walk: overflow seen in generation g, slot g mod 3
     long long dec_pairs;   // walk decisions: direct cell pairs
     long long dec_self;    // walk decisions: direct self cells
     long long n_inter;     // direct particle pairs (unordered)
@@ -133,39 +133,49 @@ __device__ __forceinline__ bool aborted(const Ctrl *ctl) {
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------
 // Every block must be resident (cudaLaunchCooperativeKernel guarantees it or
-// fails).  A wait that exceeds ~2 s sets ERR_TIMEOUT and returns false; the
-// kernels then leave their loops, so no launch can hang.
-__device__ __forceinline__ bool grid_sync(Ctrl *ctl) {
+// fails).  The arrival counter only grows within a launch (it is zeroed before
+// the launch): barrier k of the launch is passed when it reaches (k + 1) times
+// the grid size.  Each block's thread 0 adds its arrival with release
+// semantics and polls with acquire semantics, so the writes of the whole
+// block before the barrier (ordered by __syncthreads) are visible to every
+// block after it.  A wait longer than about a second sets ERR_TIMEOUT and
+// returns false; the kernels then leave, so no launch can hang.  `passed`
+// counts the grid-size steps of the barriers this block has passed.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl *ctl, unsigned &passed) {
     __syncthreads();
     __shared__ int s_ok;
+    passed += gridDim.x;
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &ctl->bar_gen;
-        unsigned g = *gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            ctl->bar_snap = *((volatile int *)&ctl->err);
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > (1ll << 25)) { atomicOr(&ctl->err, ERR_TIMEOUT); break; }
-                __nanosleep(64);
+        red_release_add_u32(&ctl->bar_count, 1u);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(&ctl->bar_count) - passed) < 0; spins++) {
+            if ((spins & 255u) == 255u && global_ns() - t0 > 1000000000ull) {
+                atomicOr(&ctl->err, ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
-        s_ok = (*((volatile int *)&ctl->err) & ERR_TIMEOUT) == 0;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-// Error word captured when the latest barrier completed: identical for every
-// block until the next barrier, so loop exits decided from it are uniform.
-__device__ __forceinline__ bool barrier_aborted(const Ctrl *ctl) {
-    return (*reinterpret_cast<const volatile int *>(&ctl->bar_snap) & ERR_ABORT_MASK) != 0;
 }
 
 // ---- warp helpers -----------------------------------------------------------

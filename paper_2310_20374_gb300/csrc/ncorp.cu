@@ -316,7 +316,6 @@ __global__ void k_reset_ctl(Ctrl *ctl, int *acc) {
     ctl->n_found = 0;
     ctl->n_tests = 0;
     ctl->bar_count = 0;
-    ctl->bar_snap = 0;
 }
 
 void reset_ctl(ncorp_ctx *c, bool fold = false) {

@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int n = A.n, ntiles = A.ntiles;
+    unsigned bar = 0;
     // ---- 0. digit counts of every pass (s_cnt reused as [8][256])
     {
         int *s_h = &s_cnt[0][0];
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
         for (int i = threadIdx.x; i < A.passes * 256; i += RS_T)
             if (s_h[i]) atomicAdd(&A.ghist[i], s_h[i]);
     }
-    if (!grid_sync(A.ctl)) return;
+    if (!grid_sync(A.ctl, bar)) return;
     for (int ps = 0; ps < A.passes; ps++) {
         const int shift = 8 * ps;
         const uint64_t *kin = (ps & 1) ? A.k1 : A.k0;
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
             }
             __syncthreads();
         }
-        if (ps + 1 < A.passes && !grid_sync(A.ctl)) return;
+        if (ps + 1 < A.passes && !grid_sync(A.ctl, bar)) return;
     }
 }
 

@@ -172,11 +172,12 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     __shared__ int s_lo, s_hi;
     volatile Ctrl *vc = A.ctl;
     const int G = gridDim.x;
+    unsigned bar = 0;
     {
         const int t = made_cells(A, 0, blockIdx.x == 0 ? 1 : 0, 0, s_red);
         if (threadIdx.x == 0) A.blocksum[blockIdx.x] = t;
     }
-    if (!grid_sync(A.ctl)) return;
+    if (!grid_sync(A.ctl, bar)) return;
     for (int lev = 0; lev < MAX_LEVEL; lev++) {
         const int ls = vc->level_start[lev], le = vc->level_start[lev + 1];
         if (ls >= le) break;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
             const int t = made_cells(A, mb, me, lev + 1, s_red);
             if (threadIdx.x == 0) A.blocksum[((lev + 1) & 1) * G + blockIdx.x] = t;
         }
-        if (!grid_sync(A.ctl)) return;
+        if (!grid_sync(A.ctl, bar)) return;
     }
 }
 

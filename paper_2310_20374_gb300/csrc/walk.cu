@@ -60,6 +60,7 @@ __global__ void k_walk_init(WalkArgs A) {
     A.ctl->n_inter = 0;
     A.ctl->walk_iters = 0;
     A.ctl->bar_count = 0;
+    A.ctl->walk_abort[0] = A.ctl->walk_abort[1] = A.ctl->walk_abort[2] = 0;
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
@@ -108,7 +109,7 @@ __device__ void block_scan_array(const int *x, int *o1, int *o2, int n, int *s_t
 // and B <- A grouped by target; leaf pairs give A <- B and B <- A, self
 // leaves A <- A, grouped by target leaf.  Counting sort: counts, prefix sums,
 // scatter (entries of one target in arrival order).
-__device__ void walk_lists(const WalkArgs &A, int *s_tmp) {
+__device__ void walk_lists(const WalkArgs &A, int *s_tmp, unsigned &bar) {
     const int nm = min(A.ctl->n_m2l, A.m2l_cap), np = min(A.ctl->n_p2p, A.p2p_cap),
               ns = min(A.ctl->n_self, A.self_cap);
     const int nc = A.ctl->n_cells + 1;
@@ -126,7 +127,7 @@ __device__ void walk_lists(const WalkArgs &A, int *s_tmp) {
             atomicAdd(&A.p2p_off[__ldcg(&A.self[i - nm - np])], 1);
         }
     }
-    if (!grid_sync(A.ctl)) return;
+    if (!grid_sync(A.ctl, bar)) return;
     if (blockIdx.x == 0) {
         block_scan_array(A.cnt, A.offs, A.cursor, nc, s_tmp);       // M2L: offsets and cursors
         block_scan_array(A.p2p_off, A.p2p_off, A.cnt, nc, s_tmp);   // P2P: offsets (in place), cursors in cnt
@@ -135,7 +136,7 @@ __device__ void walk_lists(const WalkArgs &A, int *s_tmp) {
             A.ctl->n_p2p_dir = 2 * np + ns;
         }
     }
-    if (!grid_sync(A.ctl)) return;
+    if (!grid_sync(A.ctl, bar)) return;
     for (int i = t0; i < nm + np + ns; i += stride) {
         if (i < nm) {
             const int2 e = __ldcg(&A.m2l[i]);
@@ -176,10 +177,12 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
         }
     }
     volatile int *vcount = A.fcount;
+    unsigned bar = 0;
     int it = 0;
     for (; it < WALK_MAX_ITERS; it++) {
         const int nf = min(vcount[it], A.front_cap);
         if (nf == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->walk_abort[(it + 1) % 3] = 0;   // slot of the next generation
         const int2 *cur = (it & 1) ? A.front1 : A.front0;
         int2 *nxt = (it & 1) ? A.front0 : A.front1;
         int *ncount = A.fcount + it + 1;
@@ -336,22 +339,23 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
             if (emit_m2l) {
                 const int slot = base_m + __popc(bm & lt);
                 if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
-                else atomicOr(&A.ctl->err, ERR_M2L);
+                else { atomicOr(&A.ctl->err, ERR_M2L); A.ctl->walk_abort[it % 3] = 1; }
             }
             if (emit_p2p) {
                 const int slot = base_p + __popc(bp & lt);
                 if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
-                else atomicOr(&A.ctl->err, ERR_P2P);
+                else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
             }
             if (emit_self) {
                 const int slot = base_s + __popc(bs & lt);
                 if (slot < A.self_cap) A.self[slot] = cA;
-                else atomicOr(&A.ctl->err, ERR_P2P);
+                else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
             }
             if (k > 0) {
                 int slot = base_f + kin - k;
                 if (slot + k > A.front_cap) {
                     atomicOr(&A.ctl->err, ERR_FRONTIER);
+                    A.ctl->walk_abort[it % 3] = 1;
                 } else {
                     const int fl = split_forced ? FORCED : 0;
                     if (split_kind == 1) {
@@ -365,11 +369,12 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
                 }
             }
         }
-        if (!grid_sync(A.ctl)) return;
-        if (barrier_aborted(A.ctl)) { it++; break; }
+        if (!grid_sync(A.ctl, bar)) return;
+        // overflow in this generation (slot it mod 3: identical for every block after the barrier)
+        if (((volatile int *)A.ctl->walk_abort)[it % 3]) { it++; break; }
     }
     // the generation count and the barrier snapshot are the same in every block
-    if (A.gravity && it < WALK_MAX_ITERS && !barrier_aborted(A.ctl)) walk_lists(A, s_tmp);
+    if (A.gravity && it < WALK_MAX_ITERS && !((volatile int *)A.ctl->walk_abort)[(it + 2) % 3]) walk_lists(A, s_tmp, bar);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.ctl->walk_iters = it;
         if (!A.gravity) {
