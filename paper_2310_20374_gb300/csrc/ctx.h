@@ -167,7 +167,6 @@ void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 // ---- tree.cu ----
 void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s);
 void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta);
-void launch_rcrit(ncorp_ctx *c, double theta);
 void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
 void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
                             const double *vz, double dt);

@@ -412,10 +412,10 @@ void on_stream(ncorp_ctx *c, cudaStream_t s, F body) {
 }
 
 // Gravity of the tree in the current set.  Two streams: the main one runs the
-// geometry climb, theta(M), the walk (with its lists), M2L, the descent and
-// the far-field evaluation; the second one runs the multipoles (which need
-// only the centres) beside theta(M) and the walk, then the near field (which
-// needs only the lists) beside M2L and the descent.
+// geometry climb (with theta(M)), the walk (with its lists), M2L, the descent
+// and the far-field evaluation; the second one runs the multipoles beside the
+// walk, then the near field (which needs only the lists) beside M2L and the
+// descent.
 void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual) {
     const bool mixed = c->cfg.precision == NCORP_MIXED;
     const double G = c->cfg.G;
@@ -429,7 +429,6 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
         launch_multipoles(c, S, p, mixed, G);
         NCORP_CUDA_CHECK(cudaEventRecord(c->ev_p2m, c->stream));
     });
-    { Stage st(c, NCORP_STAGE_CLIMB); launch_rcrit(c, theta); }
     { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true); }
     NCORP_CUDA_CHECK(cudaEventRecord(c->ev_lists, c->stream));
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_lists, 0));

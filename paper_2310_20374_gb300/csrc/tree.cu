@@ -377,11 +377,13 @@ struct ClimbArgs {
     void *Mh;
     float *rcf;
     const int *leaves;
-    const Ctrl *ctl;
+    Ctrl *ctl;
     double G, dt, theta;
+    int cap;
 };
 
 constexpr int CLIMB_WARPS = 4;
+constexpr int CLIMB_WARPS_COOP = 8;
 
 struct ClimbShared {
     double a[32], b[32], c[32], d[32], e[32];
@@ -444,47 +446,42 @@ __device__ __forceinline__ double quad_corner(const ClimbArgs &A, const LeafSlot
     return dnorm3(d0, d1, d2);
 }
 
-// ---- gravity leaves (Eqs. expansion_center, rmax_2, corner cap)
-__global__ void __launch_bounds__(64) k_leaf_gravity(ClimbArgs A) {
-    if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31;
-    const int n_leaves = A.ctl->n_leaves;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw * LEAF_GROUP < n_leaves; gw += nwarps) {
-        const LeafSlot L = leaf_slot(A, gw, lane, n_leaves);
-        const double *coord = L.q == 1 ? A.x : (L.q == 2 ? A.y : A.z);
-        double acc = 0.0;
-        for (int k = L.f; k < L.f + L.cnt; k++) {
-            const double m = A.m[k];
-            acc = L.q == 0 ? dadd(acc, m) : dadd(acc, dmul(m, coord[k]));
-        }
-        const double M = __shfl_sync(0xffffffffu, acc, L.base);
-        const double sq = L.q == 0 ? M : ddiv(acc, M);
-        const double sx = __shfl_sync(0xffffffffu, sq, L.base + 1), sy = __shfl_sync(0xffffffffu, sq, L.base + 2),
-                     sz = __shfl_sync(0xffffffffu, sq, L.base + 3);
-        double d2 = 0.0;
-        for (int k = L.f + L.q; k < L.f + L.cnt; k += 4)
-            d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
-        d2 = quad_max(d2);
-        double rmax = dsqrt(d2);
-        const double cap = quad_corner(A, L, sx, sy, sz);
-        if (cap < rmax) rmax = cap;
-        if (L.valid && L.q == 0) {
-            const int c = L.c;
-            const double rho = cell_scale(A.ctl, A.level[c], rmax);
-            A.M[c] = M;
-            A.sx[c] = sx;
-            A.sy[c] = sy;
-            A.sz[c] = sz;
-            A.rmax[c] = rmax;
-            A.rho[c] = rho;
-            float4 hi, lo;
-            split3(sx, sy, sz, hi, lo);
-            hi.w = 0.f;
-            lo.w = static_cast<float>(rho);
-            A.gh[c] = hi;
-            A.gl[c] = lo;
-        }
+// ---- gravity leaves (Eqs. expansion_center, rmax_2, corner cap): the
+// group of LEAF_GROUP leaves of warp-group gw.
+__device__ __forceinline__ void leaf_gravity_group(const ClimbArgs &A, int gw, int lane, int n_leaves) {
+    const LeafSlot L = leaf_slot(A, gw, lane, n_leaves);
+    const double *coord = L.q == 1 ? A.x : (L.q == 2 ? A.y : A.z);
+    double acc = 0.0;
+    for (int k = L.f; k < L.f + L.cnt; k++) {
+        const double m = A.m[k];
+        acc = L.q == 0 ? dadd(acc, m) : dadd(acc, dmul(m, coord[k]));
+    }
+    const double M = __shfl_sync(0xffffffffu, acc, L.base);
+    const double sq = L.q == 0 ? M : ddiv(acc, M);
+    const double sx = __shfl_sync(0xffffffffu, sq, L.base + 1), sy = __shfl_sync(0xffffffffu, sq, L.base + 2),
+                 sz = __shfl_sync(0xffffffffu, sq, L.base + 3);
+    double d2 = 0.0;
+    for (int k = L.f + L.q; k < L.f + L.cnt; k += 4)
+        d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+    d2 = quad_max(d2);
+    double rmax = dsqrt(d2);
+    const double cap = quad_corner(A, L, sx, sy, sz);
+    if (cap < rmax) rmax = cap;
+    if (L.valid && L.q == 0) {
+        const int c = L.c;
+        const double rho = cell_scale(A.ctl, A.level[c], rmax);
+        A.M[c] = M;
+        A.sx[c] = sx;
+        A.sy[c] = sy;
+        A.sz[c] = sz;
+        A.rmax[c] = rmax;
+        A.rho[c] = rho;
+        float4 hi, lo;
+        split3(sx, sy, sz, hi, lo);
+        hi.w = 0.f;
+        lo.w = static_cast<float>(rho);
+        A.gh[c] = hi;
+        A.gl[c] = lo;
     }
 }
 
@@ -552,62 +549,42 @@ __device__ __forceinline__ double corner_warp(const Ctrl *ctl, int lev, uint32_t
     return dnorm3(d0, d1, d2);
 }
 
-// ---- gravity geometry of the parents (Eqs. expansion_center, rmax_2, corner
-// cap): the last child to finish carries the climb to its parent.
-__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_geometry(ClimbArgs A) {
-    __shared__ ClimbShared sh_all[CLIMB_WARPS];
-    if (aborted(A.ctl)) return;
-    ClimbShared &S = sh_all[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int n_leaves = A.ctl->n_leaves;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
-        int c = A.leaves[gw];
-        while (true) {
-            __threadfence();
-            __syncwarp();
-            const int pc = A.parent[c];
-            if (pc < 0) break;
-            int last = 0;
-            if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (!last) break;
-            __threadfence();
-            c = pc;
-            const int c0 = A.child0[c], nch = A.nchild[c];
-            if (lane < nch) {
-                S.a[lane] = __ldcg(&A.M[c0 + lane]);
-                S.b[lane] = __ldcg(&A.sx[c0 + lane]);
-                S.c[lane] = __ldcg(&A.sy[c0 + lane]);
-                S.d[lane] = __ldcg(&A.sz[c0 + lane]);
-                S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
-            }
-            __syncwarp();
-            double M2, px, py, pz;
-            parent_centre(S, nch, lane, true, 0.0, M2, px, py, pz);
-            double rm = 0;
-            if (lane < nch) rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
-            rm = warp_max(rm);
-            const int plev = A.level[c];
-            const double pcap = corner_warp(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
-            if (pcap < rm) rm = pcap;
-            if (lane == 0) {
-                const double prho = cell_scale(A.ctl, plev, rm);
-                A.M[c] = M2;
-                A.sx[c] = px;
-                A.sy[c] = py;
-                A.sz[c] = pz;
-                A.rmax[c] = rm;
-                A.rho[c] = prho;
-                float4 hi, lo;
-                split3(px, py, pz, hi, lo);
-                hi.w = 0.f;
-                lo.w = static_cast<float>(prho);
-                A.gh[c] = hi;
-                A.gl[c] = lo;
-            }
-        }
+// ---- gravity geometry of a parent from its children (Eqs. expansion_center,
+// rmax_2, corner cap), by one warp.
+__device__ __forceinline__ void parent_gravity(const ClimbArgs &A, int c, ClimbShared &S, int lane) {
+    const int c0 = A.child0[c], nch = A.nchild[c];
+    if (lane < nch) {
+        S.a[lane] = __ldcg(&A.M[c0 + lane]);
+        S.b[lane] = __ldcg(&A.sx[c0 + lane]);
+        S.c[lane] = __ldcg(&A.sy[c0 + lane]);
+        S.d[lane] = __ldcg(&A.sz[c0 + lane]);
+        S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
     }
+    __syncwarp();
+    double M2, px, py, pz;
+    parent_centre(S, nch, lane, true, 0.0, M2, px, py, pz);
+    double rm = 0;
+    if (lane < nch) rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
+    rm = warp_max(rm);
+    const int plev = A.level[c];
+    const double pcap = corner_warp(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
+    if (pcap < rm) rm = pcap;
+    if (lane == 0) {
+        const double prho = cell_scale(A.ctl, plev, rm);
+        A.M[c] = M2;
+        A.sx[c] = px;
+        A.sy[c] = py;
+        A.sz[c] = pz;
+        A.rmax[c] = rm;
+        A.rho[c] = prho;
+        float4 hi, lo;
+        split3(px, py, pz, hi, lo);
+        hi.w = 0.f;
+        lo.w = static_cast<float>(prho);
+        A.gh[c] = hi;
+        A.gl[c] = lo;
+    }
+    __syncwarp();
 }
 
 // ---- multipoles (Eq. multipole_moment, scaled: M-hat_beta = sum mu (d/rho)^beta / beta!).
@@ -747,21 +724,38 @@ __device__ double theta_of(double M, double Mtot, double tmin) {
     return th;
 }
 
-// One FP64 warp instruction costs the same whatever the number of active
-// lanes, so theta(M) is spread eight cells to a warp over many warps.
-__global__ void k_rcrit(const double *__restrict__ M, const double *__restrict__ rmax, double *__restrict__ rcrit,
-                        float4 *gh, const Ctrl *ctl, int cap, double tmin) {
-    if (aborted(ctl)) return;
-    const int nc = min(ctl->n_cells, cap);
-    const double Mtot = M[0];
+// ---- gravity geometry in one cooperative launch: the leaves, then the
+// parents level by level from the deepest (each needs its children's), then
+// theta(M) and r_crit = r_max / theta (which need the root's mass).  One FP64
+// warp instruction costs the same whatever the number of active lanes, so the
+// leaves go eight to a warp with four lanes each, theta(M) eight cells to a
+// warp, and the parents one to a warp over as many warps as there are.
+__global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A) {
+    __shared__ ClimbShared sh_all[CLIMB_WARPS_COOP];
+    if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31;
-    if (lane >= 8) return;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8 + lane; i < nc; i += nwarps * 8) {
-        const double rc = ddiv(rmax[i], theta_of(M[i], Mtot, tmin));
-        rcrit[i] = rc;
-        gh[i].w = static_cast<float>(rc);
+    ClimbShared &S = sh_all[threadIdx.x >> 5];
+    // warps numbered across the blocks first, so that consecutive work items land on different SMs
+    const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned bar = 0;
+    const int n_leaves = A.ctl->n_leaves;
+    for (int gw = gw0; gw * LEAF_GROUP < n_leaves; gw += nwarps) leaf_gravity_group(A, gw, lane, n_leaves);
+    if (!grid_sync(A.ctl, bar)) return;
+    const int maxl = A.ctl->max_level;
+    for (int lev = maxl - 1; lev >= 0; lev--) {
+        const int ls = A.ctl->level_start[lev], le = A.ctl->level_start[lev + 1];
+        for (int c = ls + gw0; c < le; c += nwarps)
+            if (A.nchild[c] > 0) parent_gravity(A, c, S, lane);
+        if (!grid_sync(A.ctl, bar)) return;
     }
+    const int nc = min(A.ctl->n_cells, A.cap);
+    const double Mtot = __ldcg(&A.M[0]);
+    if (lane < 8)
+        for (int i = gw0 * 8 + lane; i < nc; i += nwarps * 8) {
+            const double rc = ddiv(__ldcg(&A.rmax[i]), theta_of(__ldcg(&A.M[i]), Mtot, A.theta));
+            A.rcrit[i] = rc;
+            A.gh[i].w = static_cast<float>(rc);
+        }
 }
 
 template <int P, typename real>
@@ -778,17 +772,16 @@ void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double 
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.M = C.M; A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rmax = C.rmax; A.rcrit = C.rcrit; A.rho = C.rho;
     A.gh = C.gh; A.gl = C.gl;
-    A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
-    k_leaf_gravity<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
-    k_climb_geometry<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
-}
-
-void launch_rcrit(ncorp_ctx *c, double theta) {
-    Cells &C = c->cells;
-    k_rcrit<<<16 * c->num_sms, 64, 0, c->stream>>>(C.M, C.rmax, C.rcrit, C.gh, c->ctl, C.cap, theta); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
+    A.Mh = C.Mh; A.leaves = C.leaves; A.ctl = c->ctl; A.G = G; A.theta = theta; A.cap = C.cap;
+    const int block = 32 * CLIMB_WARPS_COOP;
+    // every SM: the FP64 work of the leaves and of theta(M) is bound by the FP64 units of the
+    // sub-partitions, so it is spread over all of them
+    const int grid = coop_grid(c, reinterpret_cast<const void *>(k_geometry), block, 0);
+    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    void *args[] = {&A};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_geometry), dim3(grid), dim3(block),
+                                                 args, 0, c->stream));
+    c->launches++;
 }
 
 void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G) {
