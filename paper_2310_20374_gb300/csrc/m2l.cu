@@ -16,12 +16,14 @@
 // so that the per-entry sum needs no alpha-dependent factor and the 1/rho_A is
 // applied once per target.
 //
-// Work layout: the directed entries (target, source) are grouped by target;
-// each thread takes a contiguous run of entries, keeps the target's
-// coefficients in registers while the target does not change, and adds them
-// to the target's C-hat with one atomic per coefficient when it does.  Both
-// directions of a pair are evaluated (A <- B and B <- A), which is the
-// symmetric treatment of Sect. 3.4.3 split into its two halves.
+// Work layout: the directed entries (target, source) are grouped by target.
+// One warp per target cell: the lanes take the target's sources in turn, each
+// accumulating the target's coefficients in registers; a butterfly reduction
+// then leaves the sums on every lane, and each lane stores its share of the
+// coefficients (the warp owns the target, so no atomics are needed; targets
+// without entries get zeros).  Both directions of a pair are evaluated
+// (A <- B and B <- A), which is the symmetric treatment of Sect. 3.4.3 split
+// into its two halves.
 #include "ctx.h"
 
 namespace ncorp {
@@ -53,6 +55,7 @@ __device__ __forceinline__ void green_derivatives(real ux, real uy, real uz, rea
 
 struct M2LArgs {
     const int2 *dir;
+    const int *offs;    // [n_cells + 1]: entries of target c are dir[offs[c], offs[c + 1])
     int dir_cap;
     const double *sx, *sy, *sz, *rho;
     const float4 *gh, *gl;
@@ -61,119 +64,114 @@ struct M2LArgs {
     const Ctrl *ctl;
 };
 
-__device__ __forceinline__ void atomic_add_real(float *p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add_real(double *p, double v) { atomicAdd(p, v); }
+constexpr int M2L_WARPS = 4;
 
 template <int P, typename real>
-__global__ void __launch_bounds__(128) k_m2l(M2LArgs A) {
+__global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l(M2LArgs A) {
     constexpr int NM = num_m(P), NC = num_c(P), ND = num_d(P);
+    constexpr bool f32 = sizeof(real) == 4;
     const real *__restrict__ Mh = static_cast<const real *>(A.Mh);
     real *Ch = static_cast<real *>(A.Ch);
     if (aborted(A.ctl)) return;
-    const int E = min(A.ctl->n_m2l_dir, A.dir_cap);
-    const int T = gridDim.x * blockDim.x;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int per = max((E + T - 1) / T, 16);   // runs of >= 16 entries: one flush per target run
-    const int e0 = min(E, t * per), e1 = min(E, e0 + per);
-    real acc[NC];
+    const int lane = threadIdx.x & 31;
+    // warps numbered across the blocks first, so that neighbouring targets land on different SMs
+    const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = A.ctl->n_cells;
+    for (int c = gw0; c < ncells; c += nwarps) {
+        const int e0 = min(__ldg(&A.offs[c]), A.dir_cap), e1 = min(__ldg(&A.offs[c + 1]), A.dir_cap);
+        real acc[NC];
 #pragma unroll
-    for (int i = 0; i < NC; i++) acc[i] = real(0);
-    int cur = -1;
-    double irho = 1.0;
-    double tx = 0, ty = 0, tz = 0;
-    float4 th = make_float4(0, 0, 0, 1), tl = th;
-    float irf = 1.0f;
-    constexpr bool f32 = sizeof(real) == 4;
-    auto flush = [&]() {
-        const real f = f32 ? static_cast<real>(irf) : static_cast<real>(irho);
-#pragma unroll
-        for (int i = 0; i < NC; i++) {
-            atomic_add_real(&Ch[(size_t)cur * NC + i], acc[i] * f);
-            acc[i] = real(0);
-        }
-    };
-    for (int e = e0; e < e1; e++) {
-        const int2 d = A.dir[e];
-        if (d.x != cur) {
-            if (cur >= 0) flush();
-            cur = d.x;
+        for (int i = 0; i < NC; i++) acc[i] = real(0);
+        double irho = 1.0, tx = 0.0, ty = 0.0, tz = 0.0;
+        float4 th = make_float4(0.f, 0.f, 0.f, 1.f), tl = th;
+        float irf = 1.0f;
+        if (e1 > e0) {
             if constexpr (f32) {
-                th = A.gh[cur];
-                tl = A.gl[cur];
+                th = A.gh[c];
+                tl = A.gl[c];
                 irf = 1.0f / tl.w;   // exact: rho is a power of two
             } else {
-                irho = 1.0 / A.rho[cur];
-                tx = A.sx[cur];
-                ty = A.sy[cur];
-                tz = A.sz[cur];
+                irho = 1.0 / A.rho[c];
+                tx = A.sx[c];
+                ty = A.sy[c];
+                tz = A.sz[c];
             }
         }
-        const int src = d.y;
-        real ux, uy, uz, q;
-        if constexpr (f32) {   // separation from double-float centres, no FP64 work
-            const float4 sh = A.gh[src], sl = A.gl[src];
-            ux = ((th.x - sh.x) + (tl.x - sl.x)) * irf;
-            uy = ((th.y - sh.y) + (tl.y - sl.y)) * irf;
-            uz = ((th.z - sh.z) + (tl.z - sl.z)) * irf;
-            q = -sl.w * irf;   // -rho_B / rho_A
-        } else {
-            ux = (tx - A.sx[src]) * irho;
-            uy = (ty - A.sy[src]) * irho;
-            uz = (tz - A.sz[src]) * irho;
-            q = -A.rho[src] * irho;
-        }
-        real D[ND];
-        green_derivatives<P, real>(ux, uy, uz, D);
-        const real *Ms = Mh + (size_t)src * NM;
-        real qn = real(1);
-#pragma unroll
-        for (int nb = 0; nb < P; nb++) {
-            if (nb == 1) {
-                qn *= q;
-                continue;
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int src = A.dir[e].y;
+            real ux, uy, uz, q;
+            if constexpr (f32) {   // separation from double-float centres, no FP64 work
+                const float4 sh = A.gh[src], sl = A.gl[src];
+                ux = ((th.x - sh.x) + (tl.x - sl.x)) * irf;
+                uy = ((th.y - sh.y) + (tl.y - sl.y)) * irf;
+                uz = ((th.z - sh.z) + (tl.z - sl.z)) * irf;
+                q = -sl.w * irf;   // -rho_B / rho_A
+            } else {
+                ux = (tx - A.sx[src]) * irho;
+                uy = (ty - A.sy[src]) * irho;
+                uz = (tz - A.sz[src]) * irho;
+                q = -A.rho[src] * irho;
             }
+            real D[ND];
+            green_derivatives<P, real>(ux, uy, uz, D);
+            const real *Ms = Mh + (size_t)src * NM;
+            real qn = real(1);
 #pragma unroll
-            for (int kb = 0; kb <= nb; kb++) {
+            for (int nb = 0; nb < P; nb++) {
+                if (nb == 1) {
+                    qn *= q;
+                    continue;
+                }
 #pragma unroll
-                for (int cb = 0; cb <= kb; cb++) {
-                    const int ab = nb - kb, bb = kb - cb;
-                    const real w = qn * __ldg(&Ms[midx(ab, bb, cb)]);
+                for (int kb = 0; kb <= nb; kb++) {
 #pragma unroll
-                    for (int na = 1; na <= P - nb; na++) {
+                    for (int cb = 0; cb <= kb; cb++) {
+                        const int ab = nb - kb, bb = kb - cb;
+                        const real w = qn * __ldg(&Ms[midx(ab, bb, cb)]);
 #pragma unroll
-                        for (int ka = 0; ka <= na; ka++) {
+                        for (int na = 1; na <= P - nb; na++) {
 #pragma unroll
-                            for (int ca = 0; ca <= ka; ca++) {
-                                const int aa = na - ka, ba = ka - ca;
-                                acc[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
+                            for (int ka = 0; ka <= na; ka++) {
+#pragma unroll
+                                for (int ca = 0; ca <= ka; ca++) {
+                                    const int aa = na - ka, ba = ka - ca;
+                                    acc[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
+                                }
                             }
                         }
                     }
                 }
+                qn *= q;
             }
-            qn *= q;
+        }
+        // sums over the lanes (the same on every lane), scaled by 1/rho_A; lane l stores l, l + 32, ...
+        const real f = f32 ? static_cast<real>(irf) : static_cast<real>(irho);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            real v = acc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((i & 31) == lane) Ch[(size_t)c * NC + i] = v * f;
         }
     }
-    if (cur >= 0) flush();
 }
 
 template <int P, typename real>
 static void m2l_t(ncorp_ctx *c, const M2LArgs &A) {
-    k_m2l<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_m2l<P, real><<<8 * c->num_sms, 32 * M2L_WARPS, 0, c->stream>>>(A); c->launches++;
 }
 
 void launch_m2l(ncorp_ctx *c, int p, bool mixed) {
     Cells &C = c->cells;
     M2LArgs A;
     A.dir = c->wl.m2l_dir;
+    A.offs = c->wl.offs;
     A.dir_cap = c->wl.m2l_dir_cap;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
     A.gh = C.gh; A.gl = C.gl;
     A.Mh = C.Mh;
     A.Ch = C.Ch;
     A.ctl = c->ctl;
-    const size_t esz = mixed ? sizeof(float) : sizeof(double);
-    NCORP_CUDA_CHECK(cudaMemsetAsync(C.Ch, 0, esz * num_c(p) * C.cap, c->stream));
 #define NCORP_M2L_CASE(PP)                       \
     case PP:                                     \
         if (mixed) m2l_t<PP, float>(c, A);       \
