@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
             }
 #pragma unroll
             for (int k = 2; k <= P; k++) {
-                const real f = static_cast<real>(c_ifact[k]);
+                const real f = static_cast<real>(ifact(k));   // compile-time constant (k unrolled)
                 wx[k] *= f; wy[k] *= f; wz[k] *= f;
             }
             __syncwarp();
