@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 (FMA) x
 # DRAM bytes (read + write) of one k_eval launch on this workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # set to None whenever the kernel changes until it is captured again.
-EVAL_DRAM_BYTES_PER_LAUNCH = None
+EVAL_DRAM_BYTES_PER_LAUNCH = 4.41e6
 
 
 def parse():
