@@ -271,12 +271,12 @@ void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
 // LSD radix sort of (uint64 key, uint32 value), 8-bit digits, all passes in
 // one cooperative launch.  A first sweep counts the digits of every pass at
 // once (global histograms, hence the digit starts of each pass).  Then each
-// pass ranks every tile's keys locally (stable, warp-synchronous with
-// __match_any_sync: each warp owns a contiguous slice of the tile, warps are
-// ordered by a per-digit prefix), and finds, per digit, how many keys of the
+// pass ranks every tile's keys locally (stable, warp-synchronous: the lanes
+// holding equal digits are found with one ballot per digit bit; each warp owns
+// a contiguous slice of the tile, warps are ordered by a per-digit prefix), and finds, per digit, how many keys of the
 // tiles before it carry the digit by decoupled look-back (Merrill & Garland,
 // "Single-pass parallel prefix scan with decoupled look-back", 2016): a tile
-// publishes its own count, reads its predecessors' words eight at a time
+// publishes its own count, reads its predecessors' words sixteen at a time
 // back to the nearest published running total, then publishes its own
 // running total.  A status word holds (tag, kind, value); the tag names the
 // sort call and the pass, so words of other passes or calls are never
@@ -347,13 +347,25 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
             uint32_t vv[RS_I];
             int rank[RS_I];
 #pragma unroll
+            for (int r = 0; r < RS_I; r++) {   // all loads first: they are in flight together
+                const long long i = base + r * 32 + lane;
+                kk[r] = i < n ? __ldcg(&kin[i]) : 0ull;
+                vv[r] = i < n ? __ldcg(&vin[i]) : 0u;
+            }
+#pragma unroll
             for (int r = 0; r < RS_I; r++) {
                 const long long i = base + r * 32 + lane;
                 const bool ok = i < n;
-                kk[r] = ok ? __ldcg(&kin[i]) : 0ull;
-                vv[r] = ok ? __ldcg(&vin[i]) : 0u;
-                const int d = ok ? static_cast<int>((kk[r] >> shift) & 0xffu) : 256 + lane;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
+                // lanes holding the same digit: one ballot per digit bit (moonlets past n match only themselves)
+                unsigned peers = ok ? __ballot_sync(0xffffffffu, ok) : 0u;
+#pragma unroll
+                for (int bit = 0; bit < 8; bit++) {
+                    const bool set = (d >> bit) & 1;
+                    const unsigned m = __ballot_sync(0xffffffffu, set);
+                    peers &= set ? m : ~m;
+                }
+                if (!ok) peers = 1u << lane;
                 const int before = ok ? s_cnt[w][d] : 0;
                 rank[r] = before + __popc(peers & lt);
                 __syncwarp();
@@ -375,14 +387,14 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
                     s_excl[d] = 0;
                 } else {
                     *reinterpret_cast<volatile unsigned long long *>(st) = tag | RS_AGG | static_cast<unsigned>(acc);
-                    // look back, eight predecessors at a time, to the nearest running total
+                    // look back, sixteen predecessors at a time, to the nearest running total
                     int excl = 0, t = tile - 1;
                     bool done = false;
                     while (!done) {
-                        const int m = min(8, t + 1);
-                        unsigned long long wv[8];
+                        const int m = min(16, t + 1);
+                        unsigned long long wv[16];
 #pragma unroll
-                        for (int u = 0; u < 8; u++)
+                        for (int u = 0; u < 16; u++)
                             wv[u] = u < m ? ld_status(A.status + static_cast<size_t>(t - u) * 256 + d) : 0ull;
                         for (int u = 0; u < m && !done; u++) {
                             long long spins = 0;
