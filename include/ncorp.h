@@ -97,6 +97,16 @@ int ncorp_set_stream(ncorp_ctx *ctx, void *cuda_stream);
 int ncorp_step(ncorp_ctx *ctx, double *positions, double *velocities, const double *masses,
                const double *radii, int64_t n, int p, double theta, double dt);
 
+/* Enables (enable != 0, the default) or disables CUDA graphs for resident
+ * steps.  A resident ncorp_step (same arrays, n, p, theta as the previous
+ * call) makes the same launches every other call, so it is captured once per
+ * buffer rotation into a CUDA graph (at most two kept per context) and
+ * replayed; results are identical to the directly launched step.  Steps with
+ * a distant star, steps timed by ncorp_profile and retries after a buffer
+ * overflow are always launched directly.  Disabling waits for the context's
+ * stream and frees the cached graphs.  Errors: NCORP_EINVAL, NCORP_ECUDA. */
+int ncorp_set_graphs(ncorp_ctx *ctx, int enable);
+
 /* Forgets the resident state, so the next ncorp_step re-reads its inputs. */
 int ncorp_reset(ncorp_ctx *ctx);
 
@@ -143,7 +153,8 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_P2P_DIRECTED 13  /* directed leaf-source entries evaluated */
 #define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
 #define NCORP_STAT_COL_ITERS   15   /* frontier iterations of the collision walk */
-#define NCORP_NSTATS           16
+#define NCORP_STAT_GRAPH       16   /* 1 if the last ncorp_step ran as a replayed (or just captured) CUDA graph */
+#define NCORP_NSTATS           17
 
 /* Writes min(n_stats, NCORP_NSTATS) counters of the last call (slots above)
  * to host memory stats[].  NCORP_EINVAL if ctx or stats is NULL. */

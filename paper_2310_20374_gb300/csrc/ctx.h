@@ -82,7 +82,22 @@ constexpr int P2M_ITEM_CHUNK = 512;   // moonlets per multipole work item
 // concurrent streams fit on the device together.
 inline int coop_blocks(const ncorp_ctx *c, int per_sm);
 
+// Every device (re)allocation of the library bumps this counter; a captured
+// step graph is valid only for the value it was captured under.
+unsigned long long alloc_generation();
+void bump_alloc_generation();
+void ensure_radix_scratch(ncorp_ctx *c, int n);
+
 }  // namespace ncorp
+
+// A captured CUDA graph of one resident step (see ncorp_step) and the host
+// state it was captured for.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *key[6] = {};
+    long long nums[10] = {};
+    int launches = 0;
+};
 
 struct ncorp_ctx {
     ncorp_config cfg;
@@ -109,7 +124,6 @@ struct ncorp_ctx {
     int *work_counter = nullptr;     // dynamic work distribution of persistent kernels
     int *tile_hist = nullptr;        // radix sort: status words and digit histograms
     int tile_hist_cap = 0;
-    unsigned radix_epoch = 0;        // radix sort calls so far
     int *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
     double *stage = nullptr;         // [n][3] AoS staging
@@ -145,6 +159,11 @@ struct ncorp_ctx {
     int tree_kind = 0;               // 1: gravity geometry valid, 2: collision geometry valid (bit mask)
     int grav_p = 0;                  // p of the last gravity evaluation (0: none)
     int launches = 0;                // kernels launched by the current call
+    StepGraph graphs[2];             // resident steps alternate between two buffer rotations
+    int graph_next = 0;
+    bool graphs_on = true;           // ncorp_set_graphs
+    bool graph_used = false;         // the last call ran a step graph
+    cudaStream_t gstream = nullptr;  // stream the step graphs are captured on
     bool profile = false;
     cudaEvent_t ev[NCORP_NSTAGES][8][2] = {};   // up to 8 intervals per stage per call
     int ev_used[NCORP_NSTAGES] = {0};

@@ -12,6 +12,7 @@
 // A is never written during a step, so a step whose lists overflowed is rerun
 // from it with larger buffers.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -21,6 +22,10 @@
 #include "ctx.h"
 
 using namespace ncorp;
+
+static std::atomic<unsigned long long> g_alloc_gen{0};
+unsigned long long ncorp::alloc_generation() { return g_alloc_gen.load(); }
+void ncorp::bump_alloc_generation() { g_alloc_gen++; }
 
 namespace {
 
@@ -36,6 +41,7 @@ int fail(ncorp_ctx *c, int code, const char *fmt, ...) {
 
 template <typename T>
 void dalloc(T *&p, size_t count) {
+    g_alloc_gen++;
     if (p) cudaFree(p);
     p = nullptr;
     if (count == 0) count = 1;
@@ -194,6 +200,7 @@ void ensure_tree_capacity(ncorp_ctx *c, int n) {
                     std::max(cc, c->wl.self_cap));
     int pc = std::max(1 << 16, 4 * n);
     if (c->pair_cap < pc) alloc_pairs(c, pc);
+    ensure_radix_scratch(c, std::max(n, pc));
 }
 
 // The current tree set (cells, wl, ctl, ctl_h) and the other one trade places.
@@ -351,6 +358,7 @@ struct Stage {
 
 void begin_call(ncorp_ctx *c) {
     c->launches = 0;
+    c->graph_used = false;
     for (int i = 0; i < NCORP_NSTAGES; i++) {
         c->ev_used[i] = 0;
         c->stage_ms[i] = 0.0;
@@ -504,6 +512,7 @@ void record_stats(ncorp_ctx *c, bool grav, const Ctrl *col = nullptr) {
     const Ctrl &h = *c->ctl_h;
     const Ctrl &hc = col ? *col : h;
     c->stats[NCORP_STAT_LAUNCHES] = c->launches;
+    c->stats[NCORP_STAT_GRAPH] = c->graph_used ? 1 : 0;
     c->stats[NCORP_STAT_CELLS] = h.n_cells;
     c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
     c->stats[NCORP_STAT_DEPTH] = h.max_level;
@@ -533,6 +542,109 @@ int check_common(ncorp_ctx *c, int64_t n, int p, double theta) {
     if (p < 1 || p > MAXP) return fail(c, NCORP_EINVAL, "p = %d outside 1..6", p);
     if (!(theta > 0.0 && theta < 1.0)) return fail(c, NCORP_EINVAL, "theta = %g outside (0, 1)", theta);
     return NCORP_OK;
+}
+
+// ---- CUDA graphs of resident steps ------------------------------------------
+// A resident step (state, tree and acceleration already on the device) makes
+// the same launches with the same arguments every other call: the two tree
+// sets and the two particle sets trade places once per step.  Such a step is
+// captured once per rotation into a CUDA graph and then replayed, which takes
+// the host's launch overhead out of the step and lets the device start
+// dependent launches back to back.  A graph is valid for everything its
+// launches read from the host: the buffer pointers (and the allocation
+// generation, which every device (re)allocation bumps), n, p, theta, dt, the
+// precision, the collision switch, the cooperative grid cap and whether the
+// caller's arrays are on the device.  The star's position depends on the time,
+// so steps with a star are never captured.
+
+void step_graph_key(ncorp_ctx *c, const double *pos, const double *vel, int n, int p, double theta, double dt,
+                    bool dev_x, bool dev_v, StepGraph &k) {
+    const void *ptrs[6] = {pos, vel, c->A.x, c->Cset.x, c->ctl, c->alt.ctl};
+    long long tb, db;
+    std::memcpy(&tb, &theta, sizeof tb);
+    std::memcpy(&db, &dt, sizeof db);
+    const long long nums[10] = {n, p, tb, db, static_cast<long long>(alloc_generation()), c->cfg.precision,
+                                c->cfg.collisions, (dev_x ? 2 : 0) | (dev_v ? 1 : 0), c->coop_max, c->num_sms};
+    std::memcpy(k.key, ptrs, sizeof ptrs);
+    std::memcpy(k.nums, nums, sizeof nums);
+}
+
+bool same_key(const StepGraph &a, const StepGraph &b) {
+    return std::memcmp(a.key, b.key, sizeof a.key) == 0 && std::memcmp(a.nums, b.nums, sizeof a.nums) == 0;
+}
+
+void drop_graph(StepGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = StepGraph{};
+}
+
+// The device work of one resident step up to the scatter of the new state
+// into the caller's order (into the caller's arrays when they are on the
+// device, else into the staging buffers).
+void resident_step_body(ncorp_ctx *c, double *pos, double *vel, int n, int p, double theta, double dt, bool dev_x,
+                        bool dev_v) {
+    reset_ctl(c);
+    on_alt(c, [&] { reset_ctl(c); });
+    clear_err_acc(c);
+    enqueue_kdk(c, n, p, theta, dt, true);
+    Stage st(c, NCORP_STAGE_KDK);
+    ParticleSet &Cn = c->Cset;
+    launch_scatter_aos(c, Cn.x, Cn.y, Cn.z, Cn.perm, dev_x ? pos : c->stage, n);
+    launch_scatter_aos(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, dev_v ? vel : c->stage2, n);
+}
+
+// Enqueues a resident step on c->stream through a cached graph (capturing it
+// first if no cached graph fits).  Host side effects are those of the direct
+// path: the tree sets trade places.  Returns false, with nothing enqueued and
+// the host state unchanged, if the step could not be captured.
+bool resident_step_graph(ncorp_ctx *c, double *pos, double *vel, int n, int p, double theta, double dt, bool dev_x,
+                         bool dev_v) {
+    StepGraph want;
+    step_graph_key(c, pos, vel, n, p, theta, dt, dev_x, dev_v, want);
+    for (StepGraph &g : c->graphs)
+        if (g.exec && same_key(g, want)) {
+            NCORP_CUDA_CHECK(cudaGraphLaunch(g.exec, c->stream));
+            swap_sets(c);
+            c->cur_n = n;
+            c->grav_p = p;
+            c->grav_mixed = c->cfg.precision == NCORP_MIXED;
+            c->launches += g.launches;
+            return true;
+        }
+    if (!c->gstream) NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    const Ctrl *ctl0 = c->ctl;
+    const int launches0 = c->launches;
+    cudaStream_t main = c->stream;
+    cudaGraph_t graph = nullptr;
+    NCORP_CUDA_CHECK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed));
+    c->stream = c->gstream;
+    bool ok = true;
+    try {
+        resident_step_body(c, pos, vel, n, p, theta, dt, dev_x, dev_v);
+    } catch (const CudaError &) {
+        ok = false;
+    }
+    c->stream = main;
+    const cudaError_t end = cudaStreamEndCapture(c->gstream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (ok && end == cudaSuccess && graph) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    else ok = false;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (c->ctl != ctl0) swap_sets(c);
+        c->launches = launches0;
+        return false;
+    }
+    NCORP_CUDA_CHECK(cudaGraphLaunch(exec, main));
+    StepGraph &slot = c->graphs[c->graph_next];
+    c->graph_next ^= 1;
+    drop_graph(slot);
+    slot = want;
+    slot.exec = exec;
+    slot.launches = c->launches - launches0;
+    return true;
 }
 
 constexpr int MAX_RETRIES = 6;
@@ -613,6 +725,18 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
 int ncorp_set_stream(ncorp_ctx *c, void *cuda_stream) {
     if (!c) return NCORP_EINVAL;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return NCORP_OK;
+}
+
+int ncorp_set_graphs(ncorp_ctx *c, int enable) {
+    if (!c) return NCORP_EINVAL;
+    c->graphs_on = enable != 0;
+    if (!c->graphs_on) {
+        NCORP_API_BODY(c, {
+            NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+            for (StepGraph &g : c->graphs) drop_graph(g);
+        })
+    }
     return NCORP_OK;
 }
 
@@ -724,26 +848,37 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
         bool tree = resident;
         for (int attempt = 0;; attempt++) {
             ensure_both_capacities(c, n);
-            reset_ctl(c);
-            on_alt(c, [&] { reset_ctl(c); });
-            clear_err_acc(c);
-            if (!have) {   // read the caller's state (caller order)
-                Stage st(c, NCORP_STAGE_KDK);
-                ParticleSet &A = c->A;
-                upload_vec(c, positions, A.x, A.y, A.z, n);
-                upload_vec(c, velocities, A.vx, A.vy, A.vz, n);
-                upload_scalar(c, masses, A.m, n);
-                upload_scalar(c, radii, A.R, n);
-                launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
-                tree = false;
+            c->graph_used = false;
+            if (attempt == 0 && have && tree && c->graphs_on && !c->profile && c->cfg.star_mass == 0.0) {
+                const bool dev_x = is_device_ptr(c, positions), dev_v = is_device_ptr(c, velocities);
+                c->graph_used = resident_step_graph(c, positions, velocities, n, p, theta, dt, dev_x, dev_v);
+                if (c->graph_used && !dev_x)
+                    NCORP_CUDA_CHECK(cudaMemcpyAsync(positions, c->stage, sizeof(double) * 3 * n,
+                                                     cudaMemcpyDeviceToHost, c->stream));
+                if (c->graph_used && !dev_v)
+                    NCORP_CUDA_CHECK(cudaMemcpyAsync(velocities, c->stage2, sizeof(double) * 3 * n,
+                                                     cudaMemcpyDeviceToHost, c->stream));
             }
-            if (!tree) {   // tree and acceleration of the current positions
-                build_tree(c, c->A, c->A, c->A, c->Cset, n);
-                std::swap(c->A, c->Cset);
-                gravity(c, c->A, p, theta, c->time, false);
-            }
-            enqueue_kdk(c, n, p, theta, dt, true);
-            {
+            if (!c->graph_used) {
+                reset_ctl(c);
+                on_alt(c, [&] { reset_ctl(c); });
+                clear_err_acc(c);
+                if (!have) {   // read the caller's state (caller order)
+                    Stage st(c, NCORP_STAGE_KDK);
+                    ParticleSet &A = c->A;
+                    upload_vec(c, positions, A.x, A.y, A.z, n);
+                    upload_vec(c, velocities, A.vx, A.vy, A.vz, n);
+                    upload_scalar(c, masses, A.m, n);
+                    upload_scalar(c, radii, A.R, n);
+                    launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+                    tree = false;
+                }
+                if (!tree) {   // tree and acceleration of the current positions
+                    build_tree(c, c->A, c->A, c->A, c->Cset, n);
+                    std::swap(c->A, c->Cset);
+                    gravity(c, c->A, p, theta, c->time, false);
+                }
+                enqueue_kdk(c, n, p, theta, dt, true);
                 Stage st(c, NCORP_STAGE_KDK);
                 ParticleSet &Cn = c->Cset;
                 download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
@@ -1008,6 +1143,8 @@ void ncorp_free(ncorp_ctx *c) {
     }
     for (cudaEvent_t e : {c->ev_geo, c->ev_p2m, c->ev_lists, c->ev_near})
         if (e) cudaEventDestroy(e);
+    for (StepGraph &g : c->graphs) drop_graph(g);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     dfree(c->work_counter);
     for (int i = 0; i < NCORP_NSTAGES; i++)
         for (int k = 0; k < 8; k++)

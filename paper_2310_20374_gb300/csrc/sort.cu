@@ -260,6 +260,7 @@ void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
         if (c->scan_tmp) cudaFree(c->scan_tmp);
         c->scan_tmp_cap = nb + 1024;
         NCORP_CUDA_CHECK(cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_cap));
+        bump_alloc_generation();
     }
     k_scan_reduce<<<nb, SCAN_T, 0, c->stream>>>(in, n, c->scan_tmp); c->launches++;
     k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_tmp, nb); c->launches++;
@@ -294,7 +295,7 @@ struct RadixArgs {
     int n, ntiles, passes;
     unsigned long long *status;   // [ntiles][256]: tag << 32 | kind << 31 | value
     int *ghist;                   // [RS_MAX_PASSES][256], zero on entry
-    unsigned epoch;               // distinct for every sort call on these buffers
+    unsigned *epoch;              // device counter: this call's tag base, advanced by the call
     Ctrl *ctl;
 };
 
@@ -311,6 +312,8 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     const unsigned lt = (1u << lane) - 1u;
     const int n = A.n, ntiles = A.ntiles;
     unsigned bar = 0;
+    // every block reads the call's epoch before the first barrier; block 0 advances it after
+    const unsigned epoch = *reinterpret_cast<volatile unsigned *>(A.epoch);
     // ---- 0. digit counts of every pass (s_cnt reused as [8][256])
     {
         int *s_h = &s_cnt[0][0];
@@ -331,13 +334,14 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
             if (s_h[i]) atomicAdd(&A.ghist[i], s_h[i]);
     }
     if (!grid_sync(A.ctl, bar)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.epoch = epoch + 1;
     for (int ps = 0; ps < A.passes; ps++) {
         const int shift = 8 * ps;
         const uint64_t *kin = (ps & 1) ? A.k1 : A.k0;
         const uint32_t *vin = (ps & 1) ? A.v1 : A.v0;
         uint64_t *kout = (ps & 1) ? A.k0 : A.k1;
         uint32_t *vout = (ps & 1) ? A.v0 : A.v1;
-        const unsigned long long tag = static_cast<unsigned long long>(A.epoch * RS_MAX_PASSES + ps) << 32;
+        const unsigned long long tag = static_cast<unsigned long long>((epoch + 1) * RS_MAX_PASSES + ps) << 32;
         s_start[threadIdx.x] = block_excl_scan(__ldcg(&A.ghist[ps * 256 + threadIdx.x]), s_warp, nullptr);
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
@@ -357,8 +361,9 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
                 const long long i = base + r * 32 + lane;
                 const bool ok = i < n;
                 const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
-                // lanes holding the same digit: one ballot per digit bit (moonlets past n match only themselves)
-                unsigned peers = ok ? __ballot_sync(0xffffffffu, ok) : 0u;
+                // lanes holding the same digit: one ballot per digit bit, every lane of the warp taking part
+                // in every ballot (lanes past n start from the mask of valid lanes and keep only themselves)
+                unsigned peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
                 for (int bit = 0; bit < 8; bit++) {
                     const bool set = (d >> bit) & 1;
@@ -438,17 +443,24 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
 // Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
 // the key are significant (rounded up to an even number of 8-bit passes, so
 // the result ends in the input buffers).
+void ensure_radix_scratch(ncorp_ctx *c, int n) {
+    const int ntiles = std::max(1, (n + RS_TILE - 1) / RS_TILE);
+    const int need = 2 * 256 * ntiles + RS_MAX_PASSES * 256 + 1;   // status words (2 ints each), histograms, epoch
+    if (c->tile_hist_cap < need) {
+        if (c->tile_hist) cudaFree(c->tile_hist);
+        c->tile_hist = nullptr;
+        c->tile_hist_cap = need + 4096;
+        NCORP_CUDA_CHECK(cudaMalloc(&c->tile_hist, sizeof(int) * c->tile_hist_cap));
+        NCORP_CUDA_CHECK(cudaMemset(c->tile_hist, 0, sizeof(int) * c->tile_hist_cap));
+        bump_alloc_generation();
+    }
+}
+
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
                     int bits) {
     if (n <= 1) return;
     const int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    const int need = 2 * 256 * ntiles + RS_MAX_PASSES * 256;   // status words (2 ints each), histograms
-    if (c->tile_hist_cap < need) {
-        if (c->tile_hist) cudaFree(c->tile_hist);
-        c->tile_hist_cap = need + 4096;
-        NCORP_CUDA_CHECK(cudaMalloc(&c->tile_hist, sizeof(int) * c->tile_hist_cap));
-        NCORP_CUDA_CHECK(cudaMemsetAsync(c->tile_hist, 0, sizeof(int) * c->tile_hist_cap, c->stream));
-    }
+    ensure_radix_scratch(c, n);
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
     RadixArgs A;
@@ -456,7 +468,7 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
     A.n = n; A.ntiles = ntiles; A.passes = passes;
     A.status = reinterpret_cast<unsigned long long *>(c->tile_hist);
     A.ghist = c->tile_hist + 2 * 256 * ntiles;
-    A.epoch = ++c->radix_epoch;
+    A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + c->tile_hist_cap - 1);
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(A.ghist, 0, sizeof(int) * RS_MAX_PASSES * 256, c->stream));
     int per_sm = 0;
@@ -557,6 +569,7 @@ struct StaticScratch {
     uint32_t qx[STATIC_MAX_N], qy[STATIC_MAX_N], qz[STATIC_MAX_N];
     unsigned long long status[256 * STATIC_TILES];
     int ghist[RS_MAX_PASSES * 256];
+    unsigned epoch;                   // radix sort calls so far (tags the status words)
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
@@ -589,7 +602,6 @@ struct StaticDevice {
     StaticScratch *ptr = nullptr;
     int num_sms = 0;
     int radix_per_sm = 0;
-    unsigned epoch = 0;     // sort calls so far (tags the status words of each call)
 };
 
 static std::mutex g_static_mutex;
@@ -613,7 +625,6 @@ static cudaError_t static_setup(int dev, StaticDevice &out) {
         d.radix_per_sm = std::max(1, std::min(per_sm, 2));
         d.ptr = static_cast<StaticScratch *>(p);
     }
-    d.epoch++;   // a new tag for this call's sort
     out = d;
     return cudaSuccess;
 }
@@ -655,7 +666,7 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
         A.passes = 8;   // 3 x 21 key bits, rounded up to an even number of 8-bit passes
         A.status = S->status;
         A.ghist = S->ghist;
-        A.epoch = d.epoch;
+        A.epoch = &S->epoch;
         A.ctl = &S->ctl;
         const int grid = std::min(A.ntiles, d.radix_per_sm * d.num_sms);
         void *args[] = {&A};

@@ -18,7 +18,8 @@ from . import build as _build
 NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEOUT, NCORP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 NCORP_FP64, NCORP_MIXED = 0, 1
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
-              "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters"]
+              "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters",
+              "graph"]
 STAGE_NAMES = ["sort", "build", "climb", "walk", "m2l", "descend", "eval", "collide", "kdk", "near"]
 HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
 
@@ -61,6 +62,7 @@ def load(path: str | None = None):
     L.ncorp_set_stream.argtypes = [vp, vp]
     L.ncorp_step.argtypes = [vp, vp, vp, vp, vp, i64, ip, dbl, dbl]
     L.ncorp_reset.argtypes = [vp]
+    L.ncorp_set_graphs.argtypes = [vp, ip]
     L.ncorp_collisions.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.ncorp_accel.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
     L.ncorp_collide.argtypes = [vp, vp, vp, vp, i64, dbl]
@@ -86,7 +88,7 @@ def load(path: str | None = None):
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
-    for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_collisions", "ncorp_accel",
+    for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
                  "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
                  "ncorp_hilbert_sort_static", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
                  "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
@@ -150,6 +152,10 @@ def ncorp_reset(ctx):
     return _check(ctx, load().ncorp_reset(ctx))
 
 
+def ncorp_set_graphs(ctx, enable):
+    return _check(ctx, load().ncorp_set_graphs(ctx, 1 if enable else 0))
+
+
 def ncorp_collisions(ctx, pairs, cap):
     """Fills pairs [cap][2] int64; returns the total number found."""
     found = C.c_int64(0)
@@ -173,8 +179,8 @@ def ncorp_get_state(ctx, positions, velocities):
 
 
 def ncorp_stats(ctx) -> dict:
-    arr = (C.c_int64 * 16)()
-    _check(ctx, load().ncorp_stats(ctx, arr, 16))
+    arr = (C.c_int64 * len(STAT_NAMES))()
+    _check(ctx, load().ncorp_stats(ctx, arr, len(STAT_NAMES)))
     return {k: int(v) for k, v in zip(STAT_NAMES, arr) if not k.startswith("_")}
 
 
