@@ -75,6 +75,9 @@ void ncorp_config_default(ncorp_config *cfg);
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream); the
  * context allocates its own device workspace (it grows on demand).
+ * The environment variable NCORP_RADIX_EPOCH_LIMIT (an integer >= 1, read
+ * here) lowers the number of radix sorts after which the context's sort
+ * scratch is cleared (default 2^28); it exists to test that path.
  * Errors: NCORP_EINVAL (null out/cfg, n_max < 1, bad config), NCORP_ECUDA,
  * NCORP_ENOMEM. */
 int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream);

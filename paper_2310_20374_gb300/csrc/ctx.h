@@ -87,6 +87,7 @@ inline int coop_blocks(const ncorp_ctx *c, int per_sm);
 unsigned long long alloc_generation();
 void bump_alloc_generation();
 void ensure_radix_scratch(ncorp_ctx *c, int n);
+unsigned radix_epoch_limit();
 
 }  // namespace ncorp
 
@@ -122,8 +123,9 @@ struct ncorp_ctx {
     uint64_t *key_alt = nullptr;
     uint32_t *idx = nullptr, *idx_alt = nullptr;
     int *work_counter = nullptr;     // dynamic work distribution of persistent kernels
-    int *tile_hist = nullptr;        // radix sort: status words and digit histograms
+    int *tile_hist = nullptr;        // radix sort: digit histograms, epoch, status words
     int tile_hist_cap = 0;
+    unsigned radix_epoch_limit = 0;  // radix tag epochs before the status words are cleared
     int *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
     double *stage = nullptr;         // [n][3] AoS staging

@@ -686,6 +686,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->time = cfg->t0;
+    c->radix_epoch_limit = radix_epoch_limit();
     try {
         NCORP_CUDA_CHECK(cudaSetDevice(device));
         NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));

@@ -10,6 +10,7 @@
 // consecutive along the curve.
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
 #include <mutex>
 
 #include "ctx.h"
@@ -294,10 +295,16 @@ struct RadixArgs {
     uint32_t *v0, *v1;
     int n, ntiles, passes;
     unsigned long long *status;   // [ntiles][256]: tag << 32 | kind << 31 | value
+    long long status_words;       // size of the whole status region (>= ntiles * 256)
     int *ghist;                   // [RS_MAX_PASSES][256], zero on entry
     unsigned *epoch;              // device counter: this call's tag base, advanced by the call
+    unsigned epoch_limit;         // at this epoch the call clears the status region and restarts from 0
     Ctrl *ctl;
 };
+
+// Tags are (epoch + 1) * 8 + pass in 32 bits; well before they would wrap, the
+// sort that reaches the limit clears every status word and restarts the epoch.
+constexpr unsigned RS_EPOCH_LIMIT = 1u << 28;
 
 __device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
     return *reinterpret_cast<const volatile unsigned long long *>(p);
@@ -334,7 +341,8 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
             if (s_h[i]) atomicAdd(&A.ghist[i], s_h[i]);
     }
     if (!grid_sync(A.ctl, bar)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *A.epoch = epoch + 1;
+    const bool wrap = epoch + 1 >= A.epoch_limit;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.epoch = wrap ? 0u : epoch + 1;
     for (int ps = 0; ps < A.passes; ps++) {
         const int shift = 8 * ps;
         const uint64_t *kin = (ps & 1) ? A.k1 : A.k0;
@@ -438,14 +446,39 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
         }
         if (ps + 1 < A.passes && !grid_sync(A.ctl, bar)) return;
     }
+    if (wrap) {   // every look-back of the call is over after this barrier: no status word is read again
+        if (!grid_sync(A.ctl, bar)) return;
+        for (long long i = static_cast<long long>(blockIdx.x) * RS_T + threadIdx.x; i < A.status_words;
+             i += static_cast<long long>(gridDim.x) * RS_T)
+            A.status[i] = 0ull;
+    }
 }
 
 // Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
 // the key are significant (rounded up to an even number of 8-bit passes, so
 // the result ends in the input buffers).
+// The epoch at which a context's sorts clear their status words: the constant
+// above, or a smaller value from NCORP_RADIX_EPOCH_LIMIT (read at context
+// creation; lets a test reach the clearing path in a few calls).
+unsigned radix_epoch_limit() {
+    const char *e = std::getenv("NCORP_RADIX_EPOCH_LIMIT");
+    if (e) {
+        const long long v = std::atoll(e);
+        if (v >= 1 && v <= static_cast<long long>(RS_EPOCH_LIMIT)) return static_cast<unsigned>(v);
+    }
+    return RS_EPOCH_LIMIT;
+}
+
+// Layout of the context's radix scratch (ints): the digit histograms of every
+// pass at [0, 2048), the epoch counter at RS_EPOCH_AT, the tile status words
+// from RS_STATUS_AT on.  The status words never share memory with anything
+// else, so a word left by an earlier sort (of any size) carries an older tag.
+constexpr int RS_EPOCH_AT = RS_MAX_PASSES * 256;
+constexpr int RS_STATUS_AT = RS_MAX_PASSES * 256 + 64;
+
 void ensure_radix_scratch(ncorp_ctx *c, int n) {
     const int ntiles = std::max(1, (n + RS_TILE - 1) / RS_TILE);
-    const int need = 2 * 256 * ntiles + RS_MAX_PASSES * 256 + 1;   // status words (2 ints each), histograms, epoch
+    const int need = RS_STATUS_AT + 2 * 256 * ntiles;   // status words take two ints each
     if (c->tile_hist_cap < need) {
         if (c->tile_hist) cudaFree(c->tile_hist);
         c->tile_hist = nullptr;
@@ -466,9 +499,11 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
     RadixArgs A;
     A.k0 = keys; A.k1 = keys_alt; A.v0 = vals; A.v1 = vals_alt;
     A.n = n; A.ntiles = ntiles; A.passes = passes;
-    A.status = reinterpret_cast<unsigned long long *>(c->tile_hist);
-    A.ghist = c->tile_hist + 2 * 256 * ntiles;
-    A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + c->tile_hist_cap - 1);
+    A.status = reinterpret_cast<unsigned long long *>(c->tile_hist + RS_STATUS_AT);
+    A.status_words = (c->tile_hist_cap - RS_STATUS_AT) / 2;
+    A.ghist = c->tile_hist;
+    A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + RS_EPOCH_AT);
+    A.epoch_limit = c->radix_epoch_limit;
     A.ctl = c->ctl;
     NCORP_CUDA_CHECK(cudaMemsetAsync(A.ghist, 0, sizeof(int) * RS_MAX_PASSES * 256, c->stream));
     int per_sm = 0;
@@ -496,6 +531,12 @@ void launch_iota(ncorp_ctx *c, uint32_t *idx, int n) {
 // ---------------------------------------------------------------------------
 // gather: dst[i] = src[idx[i]] for the state (positions and velocities from
 // src_xv, the rest from src_rest), the caller index and the quantised coords.
+// Ties: the radix sort keeps moonlets with equal keys in their input order
+// (the previous step's tree order), while the order is defined by (key,
+// caller index).  A moonlet inside a run of equal keys therefore goes to the
+// run's first slot plus its rank by caller index within the run; runs are
+// found from the sorted keys (they are rare: equal keys mean the same
+// quantised cell of side L / 2^21).
 // ---------------------------------------------------------------------------
 struct GatherArgs {
     const double *x, *y, *z, *vx, *vy, *vz, *m, *R;
@@ -506,30 +547,42 @@ struct GatherArgs {
     uint32_t *oqx, *oqy, *oqz;
     float4 *hi4, *lo4;
     const uint32_t *idx;
+    const uint64_t *key;   // sorted keys
     double G;
     int n;
 };
 
 __global__ void k_gather(GatherArgs g) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
-        int j = static_cast<int>(g.idx[i]);
-        g.ox[i] = g.x[j];
-        g.oy[i] = g.y[j];
-        g.oz[i] = g.z[j];
-        g.ovx[i] = g.vx[j];
-        g.ovy[i] = g.vy[j];
-        g.ovz[i] = g.vz[j];
-        g.om[i] = g.m[j];
-        g.oR[i] = g.R[j];
-        g.operm[i] = g.perm[j];
-        g.oqx[i] = g.qx[j];
-        g.oqy[i] = g.qy[j];
-        g.oqz[i] = g.qz[j];
+        const int j = static_cast<int>(g.idx[i]);
+        int d = i;
+        const uint64_t k = g.key[i];
+        if ((i > 0 && g.key[i - 1] == k) || (i + 1 < g.n && g.key[i + 1] == k)) {
+            int s = i, e = i + 1;
+            while (s > 0 && g.key[s - 1] == k) s--;
+            while (e < g.n && g.key[e] == k) e++;
+            const int pj = g.perm[j];
+            int r = 0;
+            for (int u = s; u < e; u++) r += g.perm[g.idx[u]] < pj;
+            d = s + r;
+        }
+        g.ox[d] = g.x[j];
+        g.oy[d] = g.y[j];
+        g.oz[d] = g.z[j];
+        g.ovx[d] = g.vx[j];
+        g.ovy[d] = g.vy[j];
+        g.ovz[d] = g.vz[j];
+        g.om[d] = g.m[j];
+        g.oR[d] = g.R[j];
+        g.operm[d] = g.perm[j];
+        g.oqx[d] = g.qx[j];
+        g.oqy[d] = g.qy[j];
+        g.oqz[d] = g.qz[j];
         // double-float copy of the position: x = hi + lo with both parts FP32
         const double X = g.x[j], Y = g.y[j], Z = g.z[j];
         const float hx = static_cast<float>(X), hy = static_cast<float>(Y), hz = static_cast<float>(Z);
-        g.hi4[i] = make_float4(hx, hy, hz, static_cast<float>(g.G * g.m[j]));
-        g.lo4[i] = make_float4(static_cast<float>(X - static_cast<double>(hx)), static_cast<float>(Y - static_cast<double>(hy)),
+        g.hi4[d] = make_float4(hx, hy, hz, static_cast<float>(g.G * g.m[j]));
+        g.lo4[d] = make_float4(static_cast<float>(X - static_cast<double>(hx)), static_cast<float>(Y - static_cast<double>(hy)),
                                static_cast<float>(Z - static_cast<double>(hz)), 0.0f);
     }
 }
@@ -547,6 +600,7 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     g.oqx = dst.qx; g.oqy = dst.qy; g.oqz = dst.qz;
     g.hi4 = dst.hi4; g.lo4 = dst.lo4;
     g.idx = idx;
+    g.key = dst.key;
     g.G = G;
     g.n = n;
     k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g); c->launches++;
@@ -665,8 +719,10 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
         A.ntiles = (n + RS_TILE - 1) / RS_TILE;
         A.passes = 8;   // 3 x 21 key bits, rounded up to an even number of 8-bit passes
         A.status = S->status;
+        A.status_words = 256ll * STATIC_TILES;
         A.ghist = S->ghist;
         A.epoch = &S->epoch;
+        A.epoch_limit = RS_EPOCH_LIMIT;
         A.ctl = &S->ctl;
         const int grid = std::min(A.ntiles, d.radix_per_sm * d.num_sms);
         void *args[] = {&A};

@@ -104,3 +104,23 @@ def test_graph_steps_on_a_side_stream_and_after_toggling():
     np.testing.assert_allclose(x, xr, rtol=0, atol=1e-12 * np.abs(xr).max())
     # FP32 sums in another order: the velocities agree to about the mixed-precision error
     assert np.abs(v - vr).max() <= 1e-6 * np.abs(vr).max()
+
+
+def test_radix_status_clearing_keeps_results(monkeypatch):
+    """The radix sorts tag their look-back status words with a device epoch;
+    at a limit the sort clears the status words and restarts the epoch.  With
+    the limit lowered to 3, the clearing runs every few sorts (in directly
+    launched and replayed steps, and in the colliding-pair sorts) and the
+    results stay those of a context that never reaches it."""
+    d = diskgen.make_disk(30000, 73, a_lo=2.0, a_hi=2.6, r_lo=1e-2, r_hi=3e-2)
+    monkeypatch.setenv("NCORP_RADIX_EPOCH_LIMIT", "3")
+    used_w, st_w, pairs_w = run(d, True, False)
+    monkeypatch.delenv("NCORP_RADIX_EPOCH_LIMIT")
+    used_r, st_r, pairs_r = run(d, True, False)
+    assert used_w == used_r == [0] + [1] * (STEPS - 1)
+    for (xw, vw), (xr, vr) in zip(st_w, st_r):
+        np.testing.assert_allclose(xw, xr, rtol=0, atol=1e-12 * np.abs(xr).max())
+        np.testing.assert_allclose(vw, vr, rtol=0, atol=1e-11 * np.abs(vr).max())
+    assert sum(len(p) for p in pairs_r) > 0
+    for pw, pr in zip(pairs_w, pairs_r):
+        assert np.array_equal(pw, pr)

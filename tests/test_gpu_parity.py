@@ -279,6 +279,49 @@ def test_coincident_and_clustered_moonlets():
     assert np.allclose(mut, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
 
 
+def test_equal_keys_ordered_by_caller_index_after_a_step():
+    """Ties in the key order are broken by caller index (reading c4), also in
+    a step, where the sort's input is the previous tree order: moonlet 0 drifts
+    exactly onto moonlet 1, which preceded it in the tree order of x_0."""
+    rng = np.random.default_rng(9)
+    bg = rng.uniform(-3.9, 3.9, size=(200, 3))
+    bg[0], bg[1] = [-4, -4, -4], [4, 4, 4]          # root cube [-8, 8)^3, cells of side 2^-17
+    h, dt = 2.0 ** -17, 2.0 ** -10
+    target = np.array([0.5, 0.25, 0.125]) + h / 2    # centre of a quantisation cell
+    P = oracle.params(p=3, theta=0.5, leaf_size=8)
+    mass = np.full(202, 1e-30)                       # gravity negligible: the drift is exact
+    for axis in range(3):
+        for sgn in (1.0, -1.0):
+            off = np.zeros(3)
+            off[axis] = sgn * 4 * h
+            pos = np.vstack([target + off, target, bg])
+            keys = oracle.tree_export(P, pos, mass)["keys"]
+            if keys[1] < keys[0]:
+                break
+        if keys[1] < keys[0]:
+            break
+    assert keys[1] < keys[0]
+    vel = np.zeros_like(pos)
+    vel[0] = -off / dt
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_FP64
+    cfg.leaf_size = 8
+    cfg.central_mass = 0.0
+    ctx = ncorp.ncorp_init(cfg, len(pos), 0, torch.cuda.current_stream().cuda_stream)
+    x, v = pos.copy(), vel.copy()
+    try:
+        ncorp.ncorp_step(ctx, x, v, mass, np.full(202, 1e-12), len(pos), 3, 0.5, dt)
+        g = export_tree(ctx, len(pos))
+    finally:
+        ncorp.ncorp_free(ctx)
+    assert np.array_equal(x[0], target) and np.array_equal(x[1], target)
+    o = oracle.tree_export(P, x, mass)
+    assert o["keys"][0] == o["keys"][1]
+    assert np.array_equal(g["order"], o["order"])
+    assert np.array_equal(g["keys"], o["keys"][o["order"]])
+    assert np.array_equal(g["cells"], o["cells"])
+
+
 def test_bad_arguments():
     ctx = make_ctx(16)
     try:
