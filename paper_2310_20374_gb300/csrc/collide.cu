@@ -148,7 +148,9 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.self_cap = c->wl.self_cap;
     A.p2p_cap = c->wl.p2p_cap;
     A.ctl = c->ctl;
-    k_collide<<<4 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
+    // two blocks per SM: the search runs beside the main chain's cooperative kernels, which must find
+    // room on every SM while it runs
+    k_collide<<<2 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

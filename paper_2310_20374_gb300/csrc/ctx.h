@@ -179,7 +179,7 @@ namespace ncorp {
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
                       uint32_t *qx, uint32_t *qy, uint32_t *qz);
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits);
+                    int bits, bool bar_zeroed = false);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
                    const uint32_t *idx, double G);
 void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total);

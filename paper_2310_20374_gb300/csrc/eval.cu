@@ -526,9 +526,9 @@ static EvalArgs eval_args(ncorp_ctx *c, const ParticleSet &P, double G, ExtForce
     return A;
 }
 
+// The work counter was zeroed by the gravity walk's k_walk_init.
 void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G) {
     const EvalArgs A = eval_args(c, P, G, ExtForce{}, false);
-    NCORP_CUDA_CHECK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
 #define NCORP_EVAL_CASE(PP)                      \
     case PP:                                     \
         if (mixed) eval_t<PP, float>(c, A);      \

@@ -313,25 +313,43 @@ ExtForce external(ncorp_ctx *c, double t) {
     return e;
 }
 
-// Clears the error word and the per-call counters; the tree description
-// (cell and leaf counts, levels, root cube) of a resident tree is kept.  With
-// fold, the cleared error word is first or-ed into the context's accumulator
-// (a tree set recycled in the middle of a call keeps its errors visible).
-__global__ void k_reset_ctl(Ctrl *ctl, int *acc) {
-    if (acc) *acc |= ctl->err;
+// Clears the error word and the per-call counters and sets the bounding box
+// to empty; the tree description (cell and leaf counts, levels, root cube)
+// of a resident tree is kept.  With fold, the cleared error word is first
+// or-ed into the context's accumulator (a tree set recycled in the middle of
+// a call keeps its errors visible).  ctl2 (optional) is cleared the same way
+// and clear (optional) is zeroed: one launch resets both tree sets and the
+// accumulator at the start of a step.
+__device__ void reset_one(Ctrl *ctl, int *fold) {
+    if (fold) *fold |= ctl->err;
     ctl->err = 0;
     ctl->n_found = 0;
     ctl->n_tests = 0;
     ctl->bar_count = 0;
+    for (int k = 0; k < 3; k++) {
+        ctl->bbox[k] = ~0ull;
+        ctl->bbox[3 + k] = 0ull;
+    }
+}
+
+__global__ void k_reset_ctl(Ctrl *ctl, Ctrl *ctl2, int *fold, int *clear) {
+    reset_one(ctl, fold);
+    if (ctl2) reset_one(ctl2, nullptr);
+    if (clear) *clear = 0;
 }
 
 void reset_ctl(ncorp_ctx *c, bool fold = false) {
-    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, fold ? c->err_acc : nullptr);
+    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, nullptr, fold ? c->err_acc : nullptr, nullptr);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
-void clear_err_acc(ncorp_ctx *c) { NCORP_CUDA_CHECK(cudaMemsetAsync(c->err_acc, 0, sizeof(int), c->stream)); }
+// Both tree sets and the error accumulator, before a step.
+void reset_ctls(ncorp_ctx *c) {
+    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, c->alt.ctl, nullptr, c->err_acc);
+    c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
 
 // ---- stage timers (CUDA events on the context's stream, only when profiling)
 void stage_begin(ncorp_ctx *c, int st) {
@@ -394,7 +412,7 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
     {
         Stage st(c, NCORP_STAGE_SORT);
         launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
-        radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
+        radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true);
         ParticleSet view = sr;
         view.x = sx.x; view.y = sx.y; view.z = sx.z;
         view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
@@ -583,9 +601,7 @@ void drop_graph(StepGraph &g) {
 // device, else into the staging buffers).
 void resident_step_body(ncorp_ctx *c, double *pos, double *vel, int n, int p, double theta, double dt, bool dev_x,
                         bool dev_v) {
-    reset_ctl(c);
-    on_alt(c, [&] { reset_ctl(c); });
-    clear_err_acc(c);
+    reset_ctls(c);
     enqueue_kdk(c, n, p, theta, dt, true);
     Stage st(c, NCORP_STAGE_KDK);
     ParticleSet &Cn = c->Cset;
@@ -611,7 +627,11 @@ bool resident_step_graph(ncorp_ctx *c, double *pos, double *vel, int n, int p, d
             c->launches += g.launches;
             return true;
         }
-    if (!c->gstream) NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    if (!c->gstream) {   // highest priority: the step's main chain (captured from it) goes first
+        int least = 0, greatest = 0;
+        NCORP_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        NCORP_CUDA_CHECK(cudaStreamCreateWithPriority(&c->gstream, cudaStreamNonBlocking, greatest));
+    }
     const Ctrl *ctl0 = c->ctl;
     const int launches0 = c->launches;
     cudaStream_t main = c->stream;
@@ -627,7 +647,9 @@ bool resident_step_graph(ncorp_ctx *c, double *pos, double *vel, int n, int p, d
     c->stream = main;
     const cudaError_t end = cudaStreamEndCapture(c->gstream, &graph);
     cudaGraphExec_t exec = nullptr;
-    if (ok && end == cudaSuccess && graph) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    // kernel nodes keep the priority of the stream they were captured from
+    if (ok && end == cudaSuccess && graph)
+        ok = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
     else ok = false;
     if (graph) cudaGraphDestroy(graph);
     if (!ok) {
@@ -705,10 +727,14 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         NCORP_CUDA_CHECK(cudaMemset(c->err_acc, 0, sizeof(int)));
         NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->err_acc_h), sizeof(int)));
         *c->err_acc_h = 0;
-        NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        // side streams at the lowest priority: when blocks of both wait for room on the SMs, the main
+        // chain's go first
+        int least = 0, greatest = 0;
+        NCORP_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        NCORP_CUDA_CHECK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, least));
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-        NCORP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+        NCORP_CUDA_CHECK(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, least));
         for (cudaEvent_t *e : {&c->ev_geo, &c->ev_p2m, &c->ev_lists, &c->ev_near})
             NCORP_CUDA_CHECK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         ensure_particles(c, n_max);
@@ -861,9 +887,7 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                                                      cudaMemcpyDeviceToHost, c->stream));
             }
             if (!c->graph_used) {
-                reset_ctl(c);
-                on_alt(c, [&] { reset_ctl(c); });
-                clear_err_acc(c);
+                reset_ctls(c);
                 if (!have) {   // read the caller's state (caller order)
                     Stage st(c, NCORP_STAGE_KDK);
                     ParticleSet &A = c->A;
@@ -1376,9 +1400,7 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
             // state at the start of the run, kept in the disk's own arrays for a rerun
             download_vec(c, c->A.x, c->A.y, c->A.z, c->A.perm, d.pos, static_cast<int>(d.n), c->stage);
             download_vec(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, d.vel, static_cast<int>(d.n), c->stage2);
-            reset_ctl(c);
-            on_alt(c, [&] { reset_ctl(c); });
-            clear_err_acc(c);
+            reset_ctls(c);
         }
         for (int k = 0; k < n_steps; k++)
             for (auto &d : b->disks) {

@@ -20,34 +20,59 @@ namespace ncorp {
 // ---------------------------------------------------------------------------
 // bounding box
 // ---------------------------------------------------------------------------
-__global__ void k_bbox(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                       int n, Ctrl *ctl) {
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+// One block per SM at most; every thread folds its moonlets into running
+// minima and maxima of the order-preserving integer images of the
+// coordinates (integer min/max, no FP64 instruction), the block reduces them
+// in shared memory and adds one atomic per bound.  A coordinate whose
+// exponent field is all ones (infinite or NaN) sets ERR_NONFINITE.
+__global__ void __launch_bounds__(256) k_bbox(const double *__restrict__ x, const double *__restrict__ y,
+                                              const double *__restrict__ z, int n, Ctrl *ctl) {
+    __shared__ unsigned long long s_b[6][8];
+    __shared__ int s_bad;
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
+    if (threadIdx.x == 0) s_bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v[3] = {x[i], y[i], z[i]};
+        const double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            bad |= !isfinite(v[k]);
-            lo[k] = fmin(lo[k], v[k]);
-            hi[k] = fmax(hi[k], v[k]);
+            const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v[k]));
+            bad |= (u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+            const unsigned long long e = ord_encode(v[k]);
+            lo[k] = e < lo[k] ? e : lo[k];
+            hi[k] = e > hi[k] ? e : hi[k];
         }
     }
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[k], o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[k], o);
+            lo[k] = a < lo[k] ? a : lo[k];
+            hi[k] = b > hi[k] ? b : hi[k];
         }
-    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(&ctl->err, ERR_NONFINITE);
-    if (lane_id() == 0) {
+    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) s_bad = 1;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane_id() == 0)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            atomicMin(&ctl->bbox[k], ord_encode(lo[k]));
-            atomicMax(&ctl->bbox[3 + k], ord_encode(hi[k]));
+            s_b[k][w] = lo[k];
+            s_b[3 + k][w] = hi[k];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        unsigned long long r = s_b[k][0];
+        for (int j = 1; j < nw; j++) {
+            const unsigned long long v = s_b[k][j];
+            r = k < 3 ? (v < r ? v : r) : (v > r ? v : r);
+        }
+        if (k < 3) atomicMin(&ctl->bbox[k], r);
+        else atomicMax(&ctl->bbox[k], r);
     }
+    if (threadIdx.x == 0 && s_bad) atomicOr(&ctl->err, ERR_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -119,28 +144,42 @@ __device__ void root_cube(const Ctrl *ctl, double out[4]) {
     out[3] = L;
 }
 
-__device__ __forceinline__ uint32_t quantise(double v, double lo, double scale) {
-    double f = floor(dmul(dsub(v, lo), scale));
-    f = fmax(f, 0.0);
-    f = fmin(f, (double)((1u << KEY_BITS) - 1u));
-    return static_cast<uint32_t>(f);
+// floor(dmul(dsub(v, lo), 2^s)) clamped to [0, 2^21 - 1], with one FP64
+// instruction: the scaling by a power of two is exact, so the floor of the
+// scaled difference is its significand shifted right, done in integers.
+__device__ __forceinline__ uint32_t quantise(double v, double lo, int s) {
+    const double d = dsub(v, lo);
+    const long long u = __double_as_longlong(d);
+    if (u <= 0) return 0u;                                   // d <= 0 (or -0)
+    const int ex = static_cast<int>((u >> 52) & 0x7ff);
+    const unsigned long long m = (static_cast<unsigned long long>(u) & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+    const int sh = 1075 - (ex ? ex : 1) - s;                 // d 2^s = m 2^-sh
+    const unsigned long long q = sh <= 0 ? ~0ull : (sh >= 64 ? 0ull : m >> sh);
+    const unsigned long long qmax = (1u << KEY_BITS) - 1u;
+    return static_cast<uint32_t>(q > qmax ? qmax : q);
 }
 
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                        int n, Ctrl *ctl, uint64_t *__restrict__ key, uint32_t *__restrict__ idx,
                        uint32_t *__restrict__ qx, uint32_t *__restrict__ qy, uint32_t *__restrict__ qz) {
     __shared__ double s_root[4];
+    __shared__ int s_shift;
     if (threadIdx.x == 0) {
         root_cube(ctl, s_root);
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (int k = 0; k < 4; k++) ctl->root[k] = s_root[k];
+            ctl->bar_count = 0;
+        }
+        // L = 2^k exactly: the scale 2^21 / L is 2^(21 - k)
+        s_shift = KEY_BITS - (static_cast<int>((__double_as_longlong(s_root[3]) >> 52) & 0x7ff) - 1023);
     }
     __syncthreads();
-    const double scale = ddiv(static_cast<double>(1u << KEY_BITS), s_root[3]);
+    const int sh = s_shift;
+    const double x0 = s_root[0], y0 = s_root[1], z0 = s_root[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t a = quantise(x[i], s_root[0], scale);
-        uint32_t b = quantise(y[i], s_root[1], scale);
-        uint32_t c = quantise(z[i], s_root[2], scale);
+        const uint32_t a = quantise(x[i], x0, sh);
+        const uint32_t b = quantise(y[i], y0, sh);
+        const uint32_t c = quantise(z[i], z0, sh);
         qx[i] = a;
         qy[i] = b;
         qz[i] = c;
@@ -149,12 +188,11 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     }
 }
 
+// The bounding box in ctl must be empty on entry (k_reset_ctl leaves it so);
+// k_keys also zeroes the grid-barrier counter for the sort that follows.
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
                       uint32_t *qx, uint32_t *qy, uint32_t *qz) {
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[0], 0xff, 3 * sizeof(unsigned long long), c->stream));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bbox[3], 0x00, 3 * sizeof(unsigned long long), c->stream));
-    int g = grid_for(n, 256, 4 * c->num_sms);
-    k_bbox<<<g, 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
+    k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
@@ -296,7 +334,8 @@ struct RadixArgs {
     int n, ntiles, passes;
     unsigned long long *status;   // [ntiles][256]: tag << 32 | kind << 31 | value
     long long status_words;       // size of the whole status region (>= ntiles * 256)
-    int *ghist;                   // [RS_MAX_PASSES][256], zero on entry
+    int *ghist;                   // [2][RS_MAX_PASSES][256]: half (epoch & 1) zero on entry, the other
+                                  // half zeroed by the call for the next one
     unsigned *epoch;              // device counter: this call's tag base, advanced by the call
     unsigned epoch_limit;         // at this epoch the call clears the status region and restarts from 0
     Ctrl *ctl;
@@ -321,6 +360,11 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     unsigned bar = 0;
     // every block reads the call's epoch before the first barrier; block 0 advances it after
     const unsigned epoch = *reinterpret_cast<volatile unsigned *>(A.epoch);
+    int *const ghist = A.ghist + (epoch & 1u) * (RS_MAX_PASSES * 256);
+    {   // the next call's histograms (nobody reads them in this call)
+        int *const nxt = A.ghist + ((epoch + 1u) & 1u) * (RS_MAX_PASSES * 256);
+        for (int i = blockIdx.x * RS_T + threadIdx.x; i < RS_MAX_PASSES * 256; i += gridDim.x * RS_T) nxt[i] = 0;
+    }
     // ---- 0. digit counts of every pass (s_cnt reused as [8][256])
     {
         int *s_h = &s_cnt[0][0];
@@ -338,7 +382,7 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
         }
         __syncthreads();
         for (int i = threadIdx.x; i < A.passes * 256; i += RS_T)
-            if (s_h[i]) atomicAdd(&A.ghist[i], s_h[i]);
+            if (s_h[i]) atomicAdd(&ghist[i], s_h[i]);
     }
     if (!grid_sync(A.ctl, bar)) return;
     const bool wrap = epoch + 1 >= A.epoch_limit;
@@ -350,7 +394,7 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
         uint64_t *kout = (ps & 1) ? A.k0 : A.k1;
         uint32_t *vout = (ps & 1) ? A.v0 : A.v1;
         const unsigned long long tag = static_cast<unsigned long long>((epoch + 1) * RS_MAX_PASSES + ps) << 32;
-        s_start[threadIdx.x] = block_excl_scan(__ldcg(&A.ghist[ps * 256 + threadIdx.x]), s_warp, nullptr);
+        s_start[threadIdx.x] = block_excl_scan(__ldcg(&ghist[ps * 256 + threadIdx.x]), s_warp, nullptr);
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
             __syncwarp();
@@ -451,12 +495,15 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
         for (long long i = static_cast<long long>(blockIdx.x) * RS_T + threadIdx.x; i < A.status_words;
              i += static_cast<long long>(gridDim.x) * RS_T)
             A.status[i] = 0ull;
+        for (int i = blockIdx.x * RS_T + threadIdx.x; i < RS_MAX_PASSES * 256; i += gridDim.x * RS_T)
+            ghist[i] = 0;   // the next call (epoch 0) takes the first half
     }
 }
 
 // Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
 // the key are significant (rounded up to an even number of 8-bit passes, so
-// the result ends in the input buffers).
+// the result ends in the input buffers).  bar_zeroed: the caller's stream has
+// already zeroed ctl->bar_count since the last cooperative kernel.
 // The epoch at which a context's sorts clear their status words: the constant
 // above, or a smaller value from NCORP_RADIX_EPOCH_LIMIT (read at context
 // creation; lets a test reach the clearing path in a few calls).
@@ -469,12 +516,12 @@ unsigned radix_epoch_limit() {
     return RS_EPOCH_LIMIT;
 }
 
-// Layout of the context's radix scratch (ints): the digit histograms of every
-// pass at [0, 2048), the epoch counter at RS_EPOCH_AT, the tile status words
-// from RS_STATUS_AT on.  The status words never share memory with anything
+// Layout of the context's radix scratch (ints): two sets of digit histograms
+// of every pass at [0, 4096), the epoch counter at RS_EPOCH_AT, the tile
+// status words from RS_STATUS_AT on.  The status words never share memory with anything
 // else, so a word left by an earlier sort (of any size) carries an older tag.
-constexpr int RS_EPOCH_AT = RS_MAX_PASSES * 256;
-constexpr int RS_STATUS_AT = RS_MAX_PASSES * 256 + 64;
+constexpr int RS_EPOCH_AT = 2 * RS_MAX_PASSES * 256;
+constexpr int RS_STATUS_AT = 2 * RS_MAX_PASSES * 256 + 64;
 
 void ensure_radix_scratch(ncorp_ctx *c, int n) {
     const int ntiles = std::max(1, (n + RS_TILE - 1) / RS_TILE);
@@ -490,7 +537,7 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
 }
 
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits) {
+                    int bits, bool bar_zeroed) {
     if (n <= 1) return;
     const int ntiles = (n + RS_TILE - 1) / RS_TILE;
     ensure_radix_scratch(c, n);
@@ -505,14 +552,13 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
     A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + RS_EPOCH_AT);
     A.epoch_limit = c->radix_epoch_limit;
     A.ctl = c->ctl;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(A.ghist, 0, sizeof(int) * RS_MAX_PASSES * 256, c->stream));
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
                                                                    RS_T, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
     const int grid = std::min(ntiles, coop_blocks(c, per_sm));
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    if (!bar_zeroed) NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args,
                                                  0, c->stream));
@@ -622,14 +668,14 @@ struct StaticScratch {
     uint32_t idx[STATIC_MAX_N], idx_alt[STATIC_MAX_N];
     uint32_t qx[STATIC_MAX_N], qy[STATIC_MAX_N], qz[STATIC_MAX_N];
     unsigned long long status[256 * STATIC_TILES];
-    int ghist[RS_MAX_PASSES * 256];
+    int ghist[2 * RS_MAX_PASSES * 256];
     unsigned epoch;                   // radix sort calls so far (tags the status words)
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
 __global__ void k_static_reset(StaticScratch *S) {
-    for (int i = 0; i < RS_MAX_PASSES * 256; i++) S->ghist[i] = 0;
+    for (int i = 0; i < 2 * RS_MAX_PASSES * 256; i++) S->ghist[i] = 0;
     Ctrl &c = S->ctl;
     c.err = 0;
     c.bar_count = 0;

@@ -62,7 +62,7 @@ struct BuildArgs {
     const uint64_t *key;
     const uint32_t *qx, *qy, *qz;
     int n, s, cap;
-    int *level, *first, *count, *child0, *nchild, *parent;
+    int *level, *first, *count, *child0, *nchild, *parent, *arrive;
     uint32_t *cx, *cy, *cz;
     int *bounds, *blocksum;
     int *maker, *before;    // per cell: the block that made it, children of its maker's earlier cells
@@ -84,7 +84,9 @@ __global__ void k_build_init(BuildArgs A) {
     A.ctl->n_cells = 1;
     A.ctl->max_level = 0;
     A.ctl->n_leaves = 0;
+    A.ctl->n_items = 0;     // multipole work items of this tree (k_p2m_alloc)
     A.ctl->bar_count = 0;
+    A.arrive[0] = 0;        // arrival counters of the collision climb, zeroed as cells are made
 }
 
 // Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
                     A.child0[ci] = -1;
                     A.nchild[ci] = 0;
                     A.parent[ci] = c;
+                    A.arrive[ci] = 0;
                     A.cx[ci] = A.qx[b] >> sh;
                     A.cy[ci] = A.qy[b] >> sh;
                     A.cz[ci] = A.qz[b] >> sh;
@@ -277,7 +280,9 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     }
 }
 
-__global__ void k_collect_leaves(const int *__restrict__ nchild, const Ctrl *ctl, int cap, int *leaves, int *n_leaves) {
+// Also zeroes the grid-barrier counter for the cooperative kernel that follows.
+__global__ void k_collect_leaves(const int *__restrict__ nchild, Ctrl *ctl, int cap, int *leaves, int *n_leaves) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bar_count = 0;
     if (aborted(ctl)) return;
     const int nc = min(ctl->n_cells, cap);
     for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {
@@ -305,6 +310,7 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
     A.level = C.level; A.first = C.first; A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
     A.parent = C.parent; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.bounds = C.bounds; A.blocksum = C.blocksum; A.maker = C.maker; A.before = C.before; A.ctl = c->ctl;
+    A.arrive = C.arrive;
     k_build_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     const int block = 256;
@@ -760,7 +766,7 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A)
 
 template <int P, typename real>
 static void p2m_t(ncorp_ctx *c, const P2MArgs &A) {
-    k_p2m<P, real><<<8 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
+    k_p2m<P, real><<<2 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
     k_p2m_finish<P, real><<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
 }
 
@@ -777,8 +783,7 @@ void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double 
     // every SM: the FP64 work of the leaves and of theta(M) is bound by the FP64 units of the
     // sub-partitions, so it is spread over all of them
     const int grid = coop_grid(c, reinterpret_cast<const void *>(k_geometry), block, 0);
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
-    void *args[] = {&A};
+    void *args[] = {&A};   // ctl->bar_count was zeroed by k_collect_leaves
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_geometry), dim3(grid), dim3(block),
                                                  args, 0, c->stream));
     c->launches++;
@@ -792,7 +797,6 @@ void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, do
     B.sx = C.sx; B.sy = C.sy; B.sz = C.sz; B.rho = C.rho; B.gh = C.gh; B.gl = C.gl;
     B.Mh = C.Mh; B.part = C.part; B.items = C.items; B.item_base = C.item_base; B.item_cap = C.item_cap;
     B.G = G; B.ctl = c->ctl;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->n_items, 0, sizeof(int), c->stream));
     k_p2m_alloc<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(B); c->launches++;
 #define NCORP_P2M_CASE(PP)                     \
     case PP:                                   \
@@ -930,9 +934,8 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
     A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(C.arrive, 0, sizeof(int) * C.cap, c->stream));
     k_leaf_collision<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
-    k_climb_collision<<<8 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
+    k_climb_collision<<<4 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -44,14 +44,19 @@ struct WalkArgs {
     int *cnt, *offs, *cursor, *p2p_off, *p2p_src;
     int2 *m2l_dir;
     int m2l_dir_cap, p2p_dir_cap;
+    int *work;                 // gravity: the near-field kernel's work counter, zeroed by k_walk_init
     Ctrl *ctl;
 };
 
 constexpr int FORCED = static_cast<int>(0x80000000u);
 
+// One thread: the root pair, zeroed frontier counts and counters, and (for
+// gravity) the work counter of the near-field kernel that reads the lists.
 __global__ void k_walk_init(WalkArgs A) {
     A.front0[0] = make_int2(0, 0);
+    for (int i = 1; i <= WALK_MAX_ITERS; i++) A.fcount[i] = 0;
     A.fcount[0] = 1;
+    if (A.work) *A.work = 0;
     A.ctl->n_m2l = 0;
     A.ctl->n_p2p = 0;
     A.ctl->n_self = 0;
@@ -407,8 +412,8 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     A.self = W.self; A.self_cap = W.self_cap;
     A.cnt = W.cnt; A.offs = W.offs; A.cursor = W.cursor; A.p2p_off = W.p2p_off; A.p2p_src = W.p2p_src;
     A.m2l_dir = W.m2l_dir; A.m2l_dir_cap = W.m2l_dir_cap; A.p2p_dir_cap = W.p2p_dir_cap;
+    A.work = gravity ? c->work_counter : nullptr;
     A.ctl = c->ctl;
-    NCORP_CUDA_CHECK(cudaMemsetAsync(W.front_count, 0, sizeof(int) * (WALK_MAX_ITERS + 1), c->stream));
     k_walk_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     int per_sm = 0;
