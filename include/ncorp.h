@@ -157,7 +157,9 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
 #define NCORP_STAT_COL_ITERS   15   /* frontier iterations of the collision walk */
 #define NCORP_STAT_GRAPH       16   /* 1 if the last ncorp_step ran as a replayed (or just captured) CUDA graph */
-#define NCORP_NSTATS           17
+#define NCORP_STAT_SORT_PATH   17   /* key sort of the last tree: 1 nearly-sorted merge (steps), 0 radix sort,
+                                       -1 radix sort after the merge found the kept keys out of order */
+#define NCORP_NSTATS           18
 
 /* Writes min(n_stats, NCORP_NSTATS) counters of the last call (slots above)
  * to host memory stats[].  NCORP_EINVAL if ctx or stats is NULL. */

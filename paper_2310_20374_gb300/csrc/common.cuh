@@ -98,6 +98,7 @@ struct Ctrl {
     int n_found;           // colliding pairs found
     int walk_iters;
     int n_items;           // multipole work items (cell, chunk)
+    int resort_ok;         // the last key sort took the nearly-sorted path (1) or the radix sort
     int n_m2l_dir;
     int n_p2p_dir;
     unsigned bar_count;

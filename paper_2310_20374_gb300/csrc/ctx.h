@@ -88,6 +88,10 @@ unsigned long long alloc_generation();
 void bump_alloc_generation();
 void ensure_radix_scratch(ncorp_ctx *c, int n);
 unsigned radix_epoch_limit();
+void sort_near_sorted(ncorp_ctx *c, uint64_t *keys, uint32_t *idx, uint64_t *keys_alt, uint32_t *idx_alt, int n,
+                      int bits);
+constexpr int RESORT_MOVERS_CAP = 4096;   // movers of the nearly-sorted key sort (RS_MOVERS_MAX)
+constexpr int RESORT_BLOCKS_CAP = 4096;
 
 }  // namespace ncorp
 
@@ -121,6 +125,9 @@ struct ncorp_ctx {
     double *amx = nullptr, *amy = nullptr, *amz = nullptr;   // mutual acceleration (tree order)
     float *rcf = nullptr;            // R + dt |v| per moonlet (collision search), rounded up
     uint64_t *key_alt = nullptr;
+    uint64_t *resort_mkey = nullptr;   // nearly-sorted key sort: movers and per-block counts
+    uint32_t *resort_midx = nullptr;
+    int *resort_bcount = nullptr;
     uint32_t *idx = nullptr, *idx_alt = nullptr;
     int *work_counter = nullptr;     // dynamic work distribution of persistent kernels
     int *tile_hist = nullptr;        // radix sort: digit histograms, epoch, status words

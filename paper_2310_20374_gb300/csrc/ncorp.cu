@@ -86,6 +86,11 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
     dalloc(c->rcf, cap);
     dalloc(c->key_alt, cap);
     dalloc(c->idx, cap); dalloc(c->idx_alt, cap);
+    if (!c->resort_mkey) {
+        dalloc(c->resort_mkey, 2 * RESORT_MOVERS_CAP);   // input order, then sorted
+        dalloc(c->resort_midx, 2 * RESORT_MOVERS_CAP);
+        dalloc(c->resort_bcount, RESORT_BLOCKS_CAP);
+    }
     dalloc(c->stage, 3 * cap);
     dalloc(c->stage2, 3 * cap);
     c->n_cap = cap;
@@ -326,6 +331,7 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     ctl->n_found = 0;
     ctl->n_tests = 0;
     ctl->bar_count = 0;
+    ctl->resort_ok = 0;
     for (int k = 0; k < 3; k++) {
         ctl->bbox[k] = ~0ull;
         ctl->bbox[3 + k] = 0ull;
@@ -406,13 +412,16 @@ int finish(ncorp_ctx *c, bool both = false) {
 }
 
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
+// near_sorted: the positions are in the previous tree order of nearby
+// positions (a drift), so the keys are nearly sorted.
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
-                int n) {
+                int n, bool near_sorted = false) {
     c->cur_n = n;
     {
         Stage st(c, NCORP_STAGE_SORT);
         launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
-        radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true);
+        if (near_sorted) sort_near_sorted(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
+        else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true);
         ParticleSet view = sr;
         view.x = sx.x; view.y = sx.y; view.z = sx.z;
         view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
@@ -519,7 +528,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
     swap_sets(c);
     reset_ctl(c, true);
     { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
-    build_tree(c, B, B, A, Cn, n);
+    build_tree(c, B, B, A, Cn, n, true);
     gravity(c, Cn, p, theta, c->time + dt, false);
     if (side) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n); }
@@ -531,6 +540,7 @@ void record_stats(ncorp_ctx *c, bool grav, const Ctrl *col = nullptr) {
     const Ctrl &hc = col ? *col : h;
     c->stats[NCORP_STAT_LAUNCHES] = c->launches;
     c->stats[NCORP_STAT_GRAPH] = c->graph_used ? 1 : 0;
+    c->stats[NCORP_STAT_SORT_PATH] = h.resort_ok;
     c->stats[NCORP_STAT_CELLS] = h.n_cells;
     c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
     c->stats[NCORP_STAT_DEPTH] = h.max_level;
@@ -1137,6 +1147,7 @@ void ncorp_free(ncorp_ctx *c) {
     free_set(c->Cset);
     dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->rcf);
     dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
+    dfree(c->resort_mkey); dfree(c->resort_midx); dfree(c->resort_bcount);
     dfree(c->tile_hist); dfree(c->scan_tmp); dfree(c->stage); dfree(c->stage2);
     for (int set = 0; set < 2; set++) {
         Cells &C = c->cells;

@@ -349,7 +349,9 @@ __device__ __forceinline__ unsigned long long ld_status(const unsigned long long
     return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-__global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
+// The whole sort, run by every block of a cooperative grid of any size (256
+// threads per block); bar counts the grid barriers the blocks have passed.
+__device__ void radix_body(const RadixArgs &A, unsigned &bar) {
     __shared__ int s_cnt[RS_W][256];
     __shared__ int s_start[256];
     __shared__ int s_excl[256];
@@ -357,7 +359,6 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int n = A.n, ntiles = A.ntiles;
-    unsigned bar = 0;
     // every block reads the call's epoch before the first barrier; block 0 advances it after
     const unsigned epoch = *reinterpret_cast<volatile unsigned *>(A.epoch);
     int *const ghist = A.ghist + (epoch & 1u) * (RS_MAX_PASSES * 256);
@@ -500,6 +501,11 @@ __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
+    unsigned bar = 0;
+    radix_body(A, bar);
+}
+
 // Sorts keys/vals in place (the alt buffers are scratch); `bits` low bits of
 // the key are significant (rounded up to an even number of 8-bit passes, so
 // the result ends in the input buffers).  bar_zeroed: the caller's stream has
@@ -536,32 +542,240 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
     }
 }
 
-void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits, bool bar_zeroed) {
-    if (n <= 1) return;
-    const int ntiles = (n + RS_TILE - 1) / RS_TILE;
+static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                            int n, int bits) {
     ensure_radix_scratch(c, n);
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
     RadixArgs A;
     A.k0 = keys; A.k1 = keys_alt; A.v0 = vals; A.v1 = vals_alt;
-    A.n = n; A.ntiles = ntiles; A.passes = passes;
+    A.n = n; A.ntiles = (n + RS_TILE - 1) / RS_TILE; A.passes = passes;
     A.status = reinterpret_cast<unsigned long long *>(c->tile_hist + RS_STATUS_AT);
     A.status_words = (c->tile_hist_cap - RS_STATUS_AT) / 2;
     A.ghist = c->tile_hist;
     A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + RS_EPOCH_AT);
     A.epoch_limit = c->radix_epoch_limit;
     A.ctl = c->ctl;
+    return A;
+}
+
+void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
+                    int bits, bool bar_zeroed) {
+    if (n <= 1) return;
+    RadixArgs A = radix_args(c, keys, vals, keys_alt, vals_alt, n, bits);
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
                                                                    RS_T, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    const int grid = std::min(ntiles, coop_blocks(c, per_sm));
+    const int grid = std::min(A.ntiles, coop_blocks(c, per_sm));
     if (!bar_zeroed) NCORP_CUDA_CHECK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
     void *args[] = {&A};
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args,
                                                  0, c->stream));
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Sorting keys that are nearly sorted already.  In a step the keys are
+// computed in the previous step's tree order; a drift moves most moonlets
+// by a small fraction of their spacing, so only a few keys are out of place
+// (at dt = 1e-3 on the 1e5 disk: 627 of 1e5, i.e. n minus the longest
+// sorted subsequence).  One cooperative launch:
+//   1. every key adjacent to a descent (k[i] > k[i+1]) is a "mover", the rest
+//      are "stayers"; per-block counts;
+//   2. stayers and movers are compacted in input order (stayer keys and
+//      indices into the radix sort's scratch arrays, movers into a small
+//      buffer);
+//   3. the stayers are checked to be sorted, and the movers are placed by
+//      rank (the count of movers with a smaller key, one warp per mover);
+//   4. the two sorted sequences are merged: a stayer goes to its rank among
+//      the stayers plus the number of movers with a smaller key, a mover to
+//      its rank among the movers plus the number of stayers with a key not
+//      larger than its own.
+// The result is sorted by key (equal keys in any order: the gather ranks
+// them by caller index).  If there are more than RS_MOVERS_MAX movers or
+// the stayers are not sorted, nothing has been written to the keys or the
+// index (the index must be the identity on entry) and the same launch sorts
+// them with the full radix sort; ctl->resort_ok tells which path ran (1
+// fast, 0 or -1 radix).
+// ---------------------------------------------------------------------------
+constexpr int RS_MOVERS_MAX = RESORT_MOVERS_CAP;
+constexpr int RS_SAMPLES = 2048;     // stayer keys sampled into shared memory for the movers' searches
+constexpr int RZ_T = 256;
+
+struct ResortArgs {
+    RadixArgs radix;      // the full sort of the same arrays (its alt buffers are the stayer scratch)
+    uint64_t *key;        // [n] in: keys in input order; out: sorted
+    uint32_t *idx;        // [n] in: identity; out: input index of every sorted key
+    uint64_t *s_key;      // [n] scratch: stayer keys
+    uint32_t *s_idx;      // [n] scratch: stayer input indices
+    uint64_t *m_key;      // [RS_MOVERS_MAX] movers in input order
+    uint32_t *m_idx;
+    uint64_t *m_key2;     // [RS_MOVERS_MAX] movers sorted by key
+    uint32_t *m_idx2;
+    int *bcount;          // [gridDim.x] movers per block
+    int n;
+    Ctrl *ctl;
+};
+
+__device__ __forceinline__ bool is_mover(const uint64_t *k, int i, int n) {
+    const uint64_t v = k[i];
+    return (i > 0 && k[i - 1] > v) || (i + 1 < n && v > k[i + 1]);
+}
+
+__global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
+    extern __shared__ unsigned long long rz_smem[];
+    __shared__ int s_warp[33];
+    const int n = A.n, G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+    const int chunk = (n + G - 1) / G, c0 = min(n, b * chunk), c1 = min(n, c0 + chunk);
+    unsigned bar = 0;
+    if (b == 0 && t == 0) A.ctl->resort_ok = 0;
+    // ---- 1. movers per block
+    int mine = 0;
+    for (int i = c0 + t; i < c1; i += RZ_T) mine += is_mover(A.key, i, n) ? 1 : 0;
+    int cnt = 0;
+    block_excl_scan(mine, s_warp, &cnt);
+    if (t == 0) A.bcount[b] = cnt;
+    if (!grid_sync(A.ctl, bar)) return;
+    // ---- 2. prefix over the blocks, total; compaction in input order
+    int before = 0, total = 0;
+    for (int j = t; j < G; j += RZ_T) {
+        const int v = __ldcg(&A.bcount[j]);
+        total += v;
+        if (j < b) before += v;
+    }
+    block_excl_scan(before, s_warp, &before);
+    block_excl_scan(total, s_warp, &total);
+    if (total > RS_MOVERS_MAX) {           // uniform: every block computed the same total
+        radix_body(A.radix, bar);
+        return;
+    }
+    const int nm = total, ns = n - nm;
+    {
+        int mb = before, sb = c0 - before;   // this block's first mover and stayer slots
+        for (int base = c0; base < c1; base += RZ_T) {
+            const int i = base + t;
+            const bool ok = i < c1;
+            const bool mv = ok && is_mover(A.key, i, n);
+            int tot_m = 0;
+            const int rm = block_excl_scan(mv ? 1 : 0, s_warp, &tot_m);
+            const int nok = min(RZ_T, c1 - base);
+            if (mv) {
+                A.m_key[mb + rm] = A.key[i];
+                A.m_idx[mb + rm] = static_cast<uint32_t>(i);
+            } else if (ok) {
+                const int rs = t - rm;
+                A.s_key[sb + rs] = A.key[i];
+                A.s_idx[sb + rs] = static_cast<uint32_t>(i);
+            }
+            mb += tot_m;
+            sb += nok - tot_m;
+        }
+    }
+    if (!grid_sync(A.ctl, bar)) return;
+    // ---- 3. stayers sorted?  movers sorted by rank: a mover's place is the number of movers with a
+    // smaller key, or an equal key and a smaller slot; one warp per mover, the keys in shared memory
+    {
+        bool bad = false;
+        for (int p = b * RZ_T + t; p + 1 < ns; p += G * RZ_T) bad |= __ldcg(&A.s_key[p]) > __ldcg(&A.s_key[p + 1]);
+        if (__syncthreads_or(bad) && t == 0) A.ctl->resort_ok = -1;
+    }
+    {
+        unsigned long long *mk = rz_smem;
+        for (int q = t; q < nm; q += RZ_T) mk[q] = __ldcg(&A.m_key[q]);
+        __syncthreads();
+        const int lane = t & 31, gw = (b * RZ_T + t) >> 5, nwarps = (G * RZ_T) >> 5;
+        for (int q = gw; q < nm; q += nwarps) {
+            const unsigned long long v = mk[q];
+            int r = 0;
+            for (int j = lane; j < nm; j += 32) {
+                const unsigned long long u = mk[j];
+                r += (u < v || (u == v && j < q)) ? 1 : 0;
+            }
+            r = warp_sum(r);
+            if (lane == 0) {
+                A.m_key2[r] = v;
+                A.m_idx2[r] = __ldcg(&A.m_idx[q]);
+            }
+        }
+    }
+    if (!grid_sync(A.ctl, bar)) return;
+    if (*reinterpret_cast<volatile int *>(&A.ctl->resort_ok) != 0) {   // stayers out of order (uniform)
+        radix_body(A.radix, bar);
+        return;
+    }
+    // ---- 4. merge
+    unsigned long long *mk = rz_smem;                   // movers' keys
+    unsigned long long *smp = rz_smem + RS_MOVERS_MAX;  // every step-th stayer key
+    const int step = max(1, (ns + RS_SAMPLES - 1) / RS_SAMPLES), nsmp = (ns + step - 1) / step;
+    __syncthreads();   // the rank phase's reads of rz_smem are over in this block
+    for (int q = t; q < nm; q += RZ_T) mk[q] = __ldcg(&A.m_key2[q]);
+    for (int q = t; q < nsmp; q += RZ_T) smp[q] = __ldcg(&A.s_key[q * step]);
+    __syncthreads();
+    for (int p = b * RZ_T + t; p < ns; p += G * RZ_T) {
+        const unsigned long long v = __ldcg(&A.s_key[p]);
+        int lo = 0, hi = nm;                        // movers with a key < v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (mk[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        A.key[p + lo] = v;
+        A.idx[p + lo] = __ldcg(&A.s_idx[p]);
+    }
+    // movers: one warp each; the sample search brackets the stayers with a key <= v, the warp counts
+    // them inside the bracket
+    const int lane = t & 31, gw = (b * RZ_T + t) >> 5, nwarps = (G * RZ_T) >> 5;
+    for (int q = gw; q < nm; q += nwarps) {
+        const unsigned long long v = mk[q];
+        int lo = 0, hi = nsmp;                      // samples with a key <= v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (smp[mid] <= v) lo = mid + 1;
+            else hi = mid;
+        }
+        // stayers [0, (lo - 1) step] have keys <= v; the count ends in [(lo - 1) step + 1, lo step]
+        int r = lo == 0 ? 0 : (lo - 1) * step + 1;
+        const int e = min(ns, lo * step);
+        for (int base = r; base < e; base += 32) {
+            const int p = base + lane;
+            const bool le = p < e && __ldcg(&A.s_key[p]) <= v;
+            r += __popc(__ballot_sync(0xffffffffu, le));
+        }
+        if (lane == 0) {
+            A.key[q + r] = v;
+            A.idx[q + r] = __ldcg(&A.m_idx2[q]);
+        }
+    }
+    if (b == 0 && t == 0) A.ctl->resort_ok = 1;
+}
+
+// Sorts keys (with idx = identity on entry) like radix_sort_u64 with the
+// key bits of a Hilbert key, taking the fast path above when the keys are
+// nearly sorted.  ctl->bar_count must be zero on entry (k_keys zeroes it).
+void sort_near_sorted(ncorp_ctx *c, uint64_t *keys, uint32_t *idx, uint64_t *keys_alt, uint32_t *idx_alt, int n,
+                      int bits) {
+    if (n <= 1) return;
+    ResortArgs A;
+    A.radix = radix_args(c, keys, idx, keys_alt, idx_alt, n, bits);
+    A.key = keys; A.idx = idx;
+    A.s_key = keys_alt; A.s_idx = idx_alt;
+    A.m_key = c->resort_mkey; A.m_idx = c->resort_midx; A.bcount = c->resort_bcount;
+    A.m_key2 = c->resort_mkey + RESORT_MOVERS_CAP; A.m_idx2 = c->resort_midx + RESORT_MOVERS_CAP;
+    A.n = n;
+    A.ctl = c->ctl;
+    const size_t smem = sizeof(unsigned long long) * (RS_MOVERS_MAX + RS_SAMPLES);
+    NCORP_CUDA_CHECK(cudaFuncSetAttribute(reinterpret_cast<const void *>(k_resort),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    // about 512 keys per block (short compaction loops), at most one block per SM: the collision
+    // search's kernels run beside this launch, and a second block of this size would not fit with
+    // them on an SM (the launch would wait for them to drain); the fallback runs with the same grid
+    const int want = std::max((n + 511) / 512, A.radix.ntiles);
+    const int grid = std::max(1, std::min({coop_blocks(c, 1), want, RESORT_BLOCKS_CAP}));
+    void *args[] = {&A};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resort), dim3(grid), dim3(RZ_T),
+                                                 args, smem, c->stream));
     c->launches++;
 }
 

@@ -19,7 +19,7 @@ NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEO
 NCORP_FP64, NCORP_MIXED = 0, 1
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
               "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters",
-              "graph"]
+              "graph", "sort_path"]
 STAGE_NAMES = ["sort", "build", "climb", "walk", "m2l", "descend", "eval", "collide", "kdk", "near"]
 HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
 
