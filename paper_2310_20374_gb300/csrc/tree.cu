@@ -555,29 +555,60 @@ __device__ __forceinline__ double corner_warp(const Ctrl *ctl, int lev, uint32_t
     return dnorm3(d0, d1, d2);
 }
 
-// ---- gravity geometry of a parent from its children (Eqs. expansion_center,
-// rmax_2, corner cap), by one warp.
-__device__ __forceinline__ void parent_gravity(const ClimbArgs &A, int c, ClimbShared &S, int lane) {
-    const int c0 = A.child0[c], nch = A.nchild[c];
-    if (lane < nch) {
-        S.a[lane] = __ldcg(&A.M[c0 + lane]);
-        S.b[lane] = __ldcg(&A.sx[c0 + lane]);
-        S.c[lane] = __ldcg(&A.sy[c0 + lane]);
-        S.d[lane] = __ldcg(&A.sz[c0 + lane]);
-        S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
+// ---- gravity geometry of parents from their children (Eqs. expansion_center,
+// rmax_2, corner cap), four parents per warp, eight lanes each (a parent has
+// at most eight children), so that one FP64 warp instruction advances four
+// parents.  Lane j of a group holds child j; lanes
+// j = 0..3 form the centre's sums over the children in child order (lane 0
+// the mass, as w * 1 = w exactly, lanes 1..3 the weighted coordinates).  c is
+// the group's parent, -1 for none; every lane of the warp calls this.
+constexpr int PARENT_GROUP = 4;
+
+__device__ __forceinline__ void parent_gravity_group(const ClimbArgs &A, int c, int lane) {
+    const int j = lane & 7, base = lane & ~7;
+    const bool valid = c >= 0;
+    const int c0 = valid ? A.child0[c] : 0, nch = valid ? A.nchild[c] : 0;
+    double cm = 0.0, csx = 0.0, csy = 0.0, csz = 0.0, crm = 0.0;
+    if (j < nch) {
+        cm = __ldcg(&A.M[c0 + j]);
+        csx = __ldcg(&A.sx[c0 + j]);
+        csy = __ldcg(&A.sy[c0 + j]);
+        csz = __ldcg(&A.sz[c0 + j]);
+        crm = __ldcg(&A.rmax[c0 + j]);
     }
-    __syncwarp();
-    double M2, px, py, pz;
-    parent_centre(S, nch, lane, true, 0.0, M2, px, py, pz);
-    double rm = 0;
-    if (lane < nch) rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
-    rm = warp_max(rm);
-    const int plev = A.level[c];
-    const double pcap = corner_warp(A.ctl, plev, A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
+    double acc = 0.0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ch++) {
+        const double w = __shfl_sync(0xffffffffu, cm, base + ch);
+        const double bx = __shfl_sync(0xffffffffu, csx, base + ch);
+        const double by = __shfl_sync(0xffffffffu, csy, base + ch);
+        const double bz = __shfl_sync(0xffffffffu, csz, base + ch);
+        const double coord = j == 1 ? bx : (j == 2 ? by : (j == 3 ? bz : 1.0));
+        const double t = dmul(w, coord);
+        if (ch < nch) acc = dadd(acc, t);
+    }
+    const double M = __shfl_sync(0xffffffffu, acc, base);
+    const double q = ddiv(acc, M);
+    const double px = __shfl_sync(0xffffffffu, q, base + 1), py = __shfl_sync(0xffffffffu, q, base + 2),
+                 pz = __shfl_sync(0xffffffffu, q, base + 3);
+    double rm = 0.0;
+    if (j < nch) rm = dadd(crm, dnorm3(dsub(csx, px), dsub(csy, py), dsub(csz, pz)));
+    rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, 1));
+    rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, 2));
+    rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, 4));
+    const int plev = valid ? A.level[c] : 0;
+    double d = 0.0;
+    if (valid && j < 3) {
+        const double h = cell_side(A.ctl, plev);
+        d = corner_axis(A.ctl, j, h, j == 0 ? A.cx[c] : (j == 1 ? A.cy[c] : A.cz[c]), j == 0 ? px : (j == 1 ? py : pz));
+    }
+    const double d0 = __shfl_sync(0xffffffffu, d, base), d1 = __shfl_sync(0xffffffffu, d, base + 1),
+                 d2 = __shfl_sync(0xffffffffu, d, base + 2);
+    const double pcap = dnorm3(d0, d1, d2);
     if (pcap < rm) rm = pcap;
-    if (lane == 0) {
+    if (valid && j == 0) {
         const double prho = cell_scale(A.ctl, plev, rm);
-        A.M[c] = M2;
+        A.M[c] = M;
         A.sx[c] = px;
         A.sy[c] = py;
         A.sz[c] = pz;
@@ -590,7 +621,6 @@ __device__ __forceinline__ void parent_gravity(const ClimbArgs &A, int c, ClimbS
         A.gh[c] = hi;
         A.gl[c] = lo;
     }
-    __syncwarp();
 }
 
 // ---- multipoles (Eq. multipole_moment, scaled: M-hat_beta = sum mu (d/rho)^beta / beta!).
@@ -734,13 +764,11 @@ __device__ double theta_of(double M, double Mtot, double tmin) {
 // parents level by level from the deepest (each needs its children's), then
 // theta(M) and r_crit = r_max / theta (which need the root's mass).  One FP64
 // warp instruction costs the same whatever the number of active lanes, so the
-// leaves go eight to a warp with four lanes each, theta(M) eight cells to a
-// warp, and the parents one to a warp over as many warps as there are.
+// leaves go eight to a warp with four lanes each, theta(M) 32 cells to a
+// warp, and the parents four to a warp with eight lanes each.
 __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A) {
-    __shared__ ClimbShared sh_all[CLIMB_WARPS_COOP];
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31;
-    ClimbShared &S = sh_all[threadIdx.x >> 5];
     // warps numbered across the blocks first, so that consecutive work items land on different SMs
     const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned bar = 0;
@@ -750,18 +778,24 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A)
     const int maxl = A.ctl->max_level;
     for (int lev = maxl - 1; lev >= 0; lev--) {
         const int ls = A.ctl->level_start[lev], le = A.ctl->level_start[lev + 1];
-        for (int c = ls + gw0; c < le; c += nwarps)
-            if (A.nchild[c] > 0) parent_gravity(A, c, S, lane);
+        for (int g = gw0; ls + g * PARENT_GROUP < le; g += nwarps) {
+            const int cc = ls + g * PARENT_GROUP + (lane >> 3);
+            const int c = (cc < le && A.nchild[cc] > 0) ? cc : -1;
+            if (__any_sync(0xffffffffu, c >= 0)) parent_gravity_group(A, c, lane);
+        }
         if (!grid_sync(A.ctl, bar)) return;
     }
     const int nc = min(A.ctl->n_cells, A.cap);
     const double Mtot = __ldcg(&A.M[0]);
-    if (lane < 8)
-        for (int i = gw0 * 8 + lane; i < nc; i += nwarps * 8) {
+    // theta(M): every lane one cell; the dependent FP64 chain of a warp bounds this phase, so fewer,
+    // fuller warps (at most one per sub-partition) finish first
+    {
+        for (int i = gw0 * 32 + lane; i < nc; i += nwarps * 32) {
             const double rc = ddiv(__ldcg(&A.rmax[i]), theta_of(__ldcg(&A.M[i]), Mtot, A.theta));
             A.rcrit[i] = rc;
             A.gh[i].w = static_cast<float>(rc);
         }
+    }
 }
 
 template <int P, typename real>
