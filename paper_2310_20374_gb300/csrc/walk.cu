@@ -74,78 +74,145 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
-// Exclusive prefix sums of x[0, n) by one block, written to o1 (and o2 if
-// given; either may be x itself).  Every thread takes a contiguous run.
-__device__ void block_scan_array(const int *x, int *o1, int *o2, int n, int *s_tmp) {
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = T >> 5;
-    const int per = (n + T - 1) / T, b = min(n, t * per), e = min(n, b + per);
-    int sum = 0;
-    for (int i = b; i < e; i++) sum += __ldcg(&x[i]);
-    int incl = sum;
+// Exclusive prefix of v over the block; *total receives the block's sum.
+__device__ int block_prefix(int v, int *s_tmp, int *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
     }
+    __syncthreads();
     if (lane == 31) s_tmp[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        const int v = lane < nw ? s_tmp[lane] : 0;
-        int wi = v;
+        const int w = lane < nw ? s_tmp[lane] : 0;
+        int wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += u;
         }
-        if (lane < nw) s_tmp[lane] = wi - v;
+        if (lane < nw) s_tmp[lane] = wi - w;
+        if (lane == 31) s_tmp[32] = wi;
     }
     __syncthreads();
-    int run = s_tmp[wid] + incl - sum;
-    for (int i = b; i < e; i++) {
-        const int v = __ldcg(&x[i]);
-        o1[i] = run;
-        if (o2) o2[i] = run;
-        run += v;
-    }
-    __syncthreads();
+    const int r = s_tmp[wid] + incl - v;
+    if (total) *total = s_tmp[32];
+    return r;
+}
+
+// One end of a walk entry: the target's counter, key = 2 target + (0: M2L
+// list, 1: direct list), -1 for none.  Lanes of a warp holding the same key
+// are served by one atomic (entries of a split arrive together, so a target
+// often appears several times in a warp); returns the lane's slot.
+__device__ __forceinline__ int aggregated_add(int *m2l_ctr, int *p2p_ctr, int key) {
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int at = 0;
+    if (key >= 0 && lane == leader) at = atomicAdd((key & 1) ? &p2p_ctr[key >> 1] : &m2l_ctr[key >> 1], __popc(peers));
+    at = __shfl_sync(0xffffffffu, at, leader);
+    return at + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Directed lists from the walk's output (gravity): M2L (A, B) gives A <- B
 // and B <- A grouped by target; leaf pairs give A <- B and B <- A, self
-// leaves A <- A, grouped by target leaf.  Counting sort: counts, prefix sums,
-// scatter (entries of one target in arrival order).
+// leaves A <- A, grouped by target leaf.  Counting sort: counts (warp-
+// aggregated atomics), prefix sums over all blocks (chunk sums, a barrier,
+// chunk scans), scatter (aggregated again: entries of one target in an order
+// set by the atomics).  The frontier buffers, idle after the walk, hold the
+// chunk sums.
 __device__ void walk_lists(const WalkArgs &A, int *s_tmp, unsigned &bar) {
     const int nm = min(A.ctl->n_m2l, A.m2l_cap), np = min(A.ctl->n_p2p, A.p2p_cap),
               ns = min(A.ctl->n_self, A.self_cap);
-    const int nc = A.ctl->n_cells + 1;
-    const int stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = t0; i < nm + np + ns; i += stride) {
+    const int nc = A.ctl->n_cells + 1, total = nm + np + ns;
+    const int lane = threadIdx.x & 31;
+    const int wbase = (blockIdx.x * blockDim.x + threadIdx.x - lane), wstride = gridDim.x * blockDim.x;
+    for (int base = wbase; base < total; base += wstride) {
+        const int i = base + lane;
+        int k0 = -1, k1 = -1;
         if (i < nm) {
             const int2 e = __ldcg(&A.m2l[i]);
-            atomicAdd(&A.cnt[e.x], 1);
-            atomicAdd(&A.cnt[e.y], 1);
+            k0 = 2 * e.x;
+            k1 = 2 * e.y;
         } else if (i < nm + np) {
             const int2 e = __ldcg(&A.p2p[i - nm]);
-            atomicAdd(&A.p2p_off[e.x], 1);
-            atomicAdd(&A.p2p_off[e.y], 1);
-        } else {
-            atomicAdd(&A.p2p_off[__ldcg(&A.self[i - nm - np])], 1);
+            k0 = 2 * e.x + 1;
+            k1 = 2 * e.y + 1;
+        } else if (i < total) {
+            k0 = 2 * __ldcg(&A.self[i - nm - np]) + 1;
+        }
+        aggregated_add(A.cnt, A.p2p_off, k0);
+        aggregated_add(A.cnt, A.p2p_off, k1);
+    }
+    if (!grid_sync(A.ctl, bar)) return;
+    // chunk sums of both count arrays
+    int *bs = reinterpret_cast<int *>(A.front0);   // [2][gridDim.x]
+    const int G = gridDim.x, ch = (nc + G - 1) / G;
+    const int c0 = min(nc, static_cast<int>(blockIdx.x) * ch), c1 = min(nc, c0 + ch);
+    {
+        int sm = 0, sp = 0;
+        for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+            sm += __ldcg(&A.cnt[i]);
+            sp += __ldcg(&A.p2p_off[i]);
+        }
+        int tm = 0, tp = 0;
+        block_prefix(sm, s_tmp, &tm);
+        block_prefix(sp, s_tmp, &tp);
+        if (threadIdx.x == 0) {
+            bs[blockIdx.x] = tm;
+            bs[G + blockIdx.x] = tp;
         }
     }
     if (!grid_sync(A.ctl, bar)) return;
-    if (blockIdx.x == 0) {
-        block_scan_array(A.cnt, A.offs, A.cursor, nc, s_tmp);       // M2L: offsets and cursors
-        block_scan_array(A.p2p_off, A.p2p_off, A.cnt, nc, s_tmp);   // P2P: offsets (in place), cursors in cnt
-        if (threadIdx.x == 0) {
+    {
+        int pm = 0, pp = 0;
+        for (int b = threadIdx.x; b < static_cast<int>(blockIdx.x); b += blockDim.x) {
+            pm += __ldcg(&bs[b]);
+            pp += __ldcg(&bs[G + b]);
+        }
+        block_prefix(pm, s_tmp, &pm);
+        block_prefix(pp, s_tmp, &pp);
+        for (int t0 = c0; t0 < c1; t0 += blockDim.x) {
+            const int i = t0 + threadIdx.x;
+            const bool ok = i < c1;
+            const int vm = ok ? __ldcg(&A.cnt[i]) : 0, vp = ok ? __ldcg(&A.p2p_off[i]) : 0;
+            int sm = 0, sp = 0;
+            const int xm = block_prefix(vm, s_tmp, &sm), xp = block_prefix(vp, s_tmp, &sp);
+            if (ok) {
+                A.offs[i] = pm + xm;      // M2L: offsets and cursors
+                A.cursor[i] = pm + xm;
+                A.p2p_off[i] = pp + xp;   // direct: offsets (in place), cursors in cnt
+                A.cnt[i] = pp + xp;
+            }
+            pm += sm;
+            pp += sp;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
             A.ctl->n_m2l_dir = 2 * nm;
             A.ctl->n_p2p_dir = 2 * np + ns;
         }
     }
     if (!grid_sync(A.ctl, bar)) return;
-    for (int i = t0; i < nm + np + ns; i += stride) {
+    for (int base = wbase; base < total; base += wstride) {
+        const int i = base + lane;
+        int k0 = -1, k1 = -1;
+        int2 e = make_int2(0, 0);
         if (i < nm) {
-            const int2 e = __ldcg(&A.m2l[i]);
-            const int a = atomicAdd(&A.cursor[e.x], 1), b = atomicAdd(&A.cursor[e.y], 1);
+            e = __ldcg(&A.m2l[i]);
+            k0 = 2 * e.x;
+            k1 = 2 * e.y;
+        } else if (i < nm + np) {
+            e = __ldcg(&A.p2p[i - nm]);
+            k0 = 2 * e.x + 1;
+            k1 = 2 * e.y + 1;
+        } else if (i < total) {
+            e.x = e.y = __ldcg(&A.self[i - nm - np]);
+            k0 = 2 * e.x + 1;
+        }
+        const int a = aggregated_add(A.cursor, A.cnt, k0), b = aggregated_add(A.cursor, A.cnt, k1);
+        if (i < nm) {
             if (a < A.m2l_dir_cap && b < A.m2l_dir_cap) {
                 A.m2l_dir[a] = make_int2(e.x, e.y);
                 A.m2l_dir[b] = make_int2(e.y, e.x);
@@ -153,26 +220,213 @@ __device__ void walk_lists(const WalkArgs &A, int *s_tmp, unsigned &bar) {
                 atomicOr(&A.ctl->err, ERR_DIRECTED);
             }
         } else if (i < nm + np) {
-            const int2 e = __ldcg(&A.p2p[i - nm]);
-            const int a = atomicAdd(&A.cnt[e.x], 1), b = atomicAdd(&A.cnt[e.y], 1);
             if (a < A.p2p_dir_cap && b < A.p2p_dir_cap) {
                 A.p2p_src[a] = e.y;
                 A.p2p_src[b] = e.x;
             } else {
                 atomicOr(&A.ctl->err, ERR_DIRECTED);
             }
-        } else {
-            const int s = __ldcg(&A.self[i - nm - np]);
-            const int a = atomicAdd(&A.cnt[s], 1);
-            if (a < A.p2p_dir_cap) A.p2p_src[a] = s;
+        } else if (i < total) {
+            if (a < A.p2p_dir_cap) A.p2p_src[a] = e.x;
             else atomicOr(&A.ctl->err, ERR_DIRECTED);
+        }
+    }
+}
+
+// One generation of the walk: the pairs cur[0, nf) of generation it, taken
+// a warp of 32 at a time from warp offset first in steps of stride threads;
+// outcomes appended to the lists and children pairs to the next frontier.
+__device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int nf, int first, int stride) {
+    const int lane = threadIdx.x & 31;
+    const int2 *cur = (it & 1) ? A.front1 : A.front0;
+    int2 *nxt = (it & 1) ? A.front0 : A.front1;
+    int *ncount = A.fcount + it + 1;
+    for (int base = first; base < nf; base += stride) {
+        const int i = base + lane;
+        const bool valid = i < nf;
+        int cA = 0, cB = 0;
+        bool forced = false;
+        if (valid) {
+            const int2 e = __ldcg(&cur[i]);
+            cA = e.x;
+            cB = e.y & 0x7fffffff;
+            forced = (e.y & FORCED) != 0;
+        }
+        // outcome of this lane
+        int emit_m2l = 0, emit_p2p = 0, emit_self = 0;
+        int split_kind = 0;       // 0 none, 1 self-split of cA, 2 split cA against cB, 3 split cB against cA
+        bool split_forced = false;
+        long long dpair = 0, dself = 0, inter = 0;
+        // every cell field this lane may need, loaded in one round
+        int nA = 0, nB = 0, chA = 0, chB = 0, c0A = 0, c0B = 0;
+        float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha, la = ha, lb = ha;
+        double rA = 0.0, rB = 0.0;
+        if (valid) {
+            nA = __ldg(&A.count[cA]);
+            nB = __ldg(&A.count[cB]);
+            chA = __ldg(&A.nchild[cA]);
+            chB = __ldg(&A.nchild[cB]);
+            c0A = __ldg(&A.child0[cA]);
+            c0B = __ldg(&A.child0[cB]);
+            ha = __ldg(&A.H[cA]);
+            hb = __ldg(&A.H[cB]);
+            la = __ldg(&A.Lo[cA]);
+            lb = __ldg(&A.Lo[cB]);
+            rA = __ldg(&A.rcrit[cA]);
+            rB = __ldg(&A.rcrit[cB]);
+        }
+        if (valid) {
+            const bool leafA = chA == 0, leafB = chB == 0;
+            if (cA == cB) {
+                if (forced || nA <= A.n_cs || leafA) {
+                    if (!forced) {
+                        dself = 1;
+                        inter = static_cast<long long>(nA) * (nA - 1) / 2;
+                    }
+                    if (leafA) emit_self = 1;
+                    else { split_kind = 1; split_forced = true; }
+                } else {
+                    split_kind = 1;
+                }
+            } else if (forced) {
+                if (leafA && leafB) emit_p2p = 1;
+                else { split_kind = leafA ? 3 : 2; split_forced = true; }
+            } else {
+                const long long prod = static_cast<long long>(nA) * nB;
+                bool direct = false;
+                if (prod < A.pre) {
+                    direct = true;
+                } else {
+                    // FP32 first: centres as hi + lo pairs give |s_A - s_B|^2 to ~1e-6
+                    // relative and r_crit is rounded once; outside a band of
+                    // +-2^-14 around the threshold the FP32 answer is the FP64 one,
+                    // inside it the exact FP64 test decides.
+                    const float fx = (ha.x - hb.x) + (la.x - lb.x);
+                    const float fy = (ha.y - hb.y) + (la.y - lb.y);
+                    const float fz = (ha.z - hb.z) + (la.z - lb.z);
+                    const float d2f = fx * fx + fy * fy + fz * fz;
+                    const float tf = ha.w + hb.w, t2f = tf * tf;
+                    bool sep;
+                    if (d2f > 1e-30f && d2f > t2f * (1.0f + 0x1p-14f)) {
+                        sep = true;
+                    } else if (d2f > 1e-30f && d2f < t2f * (1.0f - 0x1p-14f)) {
+                        sep = false;
+                    } else {
+                        const double dx = dsub(A.sx[cA], A.sx[cB]);
+                        const double dy = dsub(A.sy[cA], A.sy[cB]);
+                        const double dz = dsub(A.sz[cA], A.sz[cB]);
+                        const double d2 = dsq3(dx, dy, dz);
+                        if (A.gravity) {
+                            const double t = dadd(rA, rB);
+                            sep = dmul(t, t) <= d2;
+                        } else {
+                            const double t = dmul(dadd(rA, rB), 1.0 + 0x1p-40);
+                            sep = dmul(t, t) < d2;
+                        }
+                    }
+                    if (sep) {
+                        if (A.gravity) emit_m2l = 1;
+                    } else if (prod < A.post || (leafA && leafB)) {
+                        direct = true;
+                    } else if (!leafA && (rA > rB || leafB)) {
+                        split_kind = 2;
+                    } else {
+                        split_kind = 3;
+                    }
+                }
+                if (direct) {
+                    dpair = 1;
+                    inter = prod;
+                    if (leafA && leafB) emit_p2p = 1;
+                    else { split_kind = leafA ? 3 : 2; split_forced = true; }
+                }
+            }
+        }
+        // statistics
+        dpair = warp_sum_ll(dpair);
+        dself = warp_sum_ll(dself);
+        inter = warp_sum_ll(inter);
+        if (lane == 0) {
+            if (dpair) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_pairs),
+                                 static_cast<unsigned long long>(dpair));
+            if (dself) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_self),
+                                 static_cast<unsigned long long>(dself));
+            if (inter) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_inter),
+                                 static_cast<unsigned long long>(inter));
+        }
+        // outputs: one atomic per list per warp, the four issued together
+        int c0 = 0, nch = 0, k = 0;
+        if (split_kind == 1) {
+            c0 = c0A;
+            nch = chA;
+            k = nch * (nch + 1) / 2;
+        } else if (split_kind == 2) {
+            c0 = c0A;
+            nch = chA;
+            k = nch;
+        } else if (split_kind == 3) {
+            c0 = c0B;
+            nch = chB;
+            k = nch;
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, emit_m2l), bp = __ballot_sync(0xffffffffu, emit_p2p),
+                       bs = __ballot_sync(0xffffffffu, emit_self);
+        int kin = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, kin, o);
+            if (lane >= o) kin += v;
+        }
+        const int ktot = __shfl_sync(0xffffffffu, kin, 31);
+        int base_m = 0, base_p = 0, base_s = 0, base_f = 0;
+        if (lane == 0) {
+            if (bm) base_m = atomicAdd(&A.ctl->n_m2l, __popc(bm));
+            if (bp) base_p = atomicAdd(&A.ctl->n_p2p, __popc(bp));
+            if (bs) base_s = atomicAdd(&A.ctl->n_self, __popc(bs));
+            if (ktot) base_f = atomicAdd(ncount, ktot);
+        }
+        base_m = __shfl_sync(0xffffffffu, base_m, 0);
+        base_p = __shfl_sync(0xffffffffu, base_p, 0);
+        base_s = __shfl_sync(0xffffffffu, base_s, 0);
+        base_f = __shfl_sync(0xffffffffu, base_f, 0);
+        const unsigned lt = (1u << lane) - 1u;
+        if (emit_m2l) {
+            const int slot = base_m + __popc(bm & lt);
+            if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
+            else { atomicOr(&A.ctl->err, ERR_M2L); A.ctl->walk_abort[it % 3] = 1; }
+        }
+        if (emit_p2p) {
+            const int slot = base_p + __popc(bp & lt);
+            if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
+            else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
+        }
+        if (emit_self) {
+            const int slot = base_s + __popc(bs & lt);
+            if (slot < A.self_cap) A.self[slot] = cA;
+            else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
+        }
+        if (k > 0) {
+            int slot = base_f + kin - k;
+            if (slot + k > A.front_cap) {
+                atomicOr(&A.ctl->err, ERR_FRONTIER);
+                A.ctl->walk_abort[it % 3] = 1;
+            } else {
+                const int fl = split_forced ? FORCED : 0;
+                if (split_kind == 1) {
+                    for (int a = 0; a < nch; a++)
+                        for (int b = a; b < nch; b++) nxt[slot++] = make_int2(c0 + a, (c0 + b) | fl);
+                } else if (split_kind == 2) {
+                    for (int a = 0; a < nch; a++) nxt[slot++] = make_int2(c0 + a, cB | fl);
+                } else {
+                    for (int b = 0; b < nch; b++) nxt[slot++] = make_int2(cA, (c0 + b) | fl);
+                }
+            }
         }
     }
 }
 
 __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
     __shared__ int s_tmp[33];
-    const int lane = threadIdx.x & 31;
     if (aborted(A.ctl)) return;
     if (A.gravity) {   // list counters, zeroed before the first barrier of the walk
         const int nc = A.ctl->n_cells + 1;
@@ -188,192 +442,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
         const int nf = min(vcount[it], A.front_cap);
         if (nf == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->walk_abort[(it + 1) % 3] = 0;   // slot of the next generation
-        const int2 *cur = (it & 1) ? A.front1 : A.front0;
-        int2 *nxt = (it & 1) ? A.front0 : A.front1;
-        int *ncount = A.fcount + it + 1;
-        const int stride = gridDim.x * blockDim.x;
-        for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nf; base += stride) {
-            const int i = base + lane;
-            const bool valid = i < nf;
-            int cA = 0, cB = 0;
-            bool forced = false;
-            if (valid) {
-                const int2 e = __ldcg(&cur[i]);
-                cA = e.x;
-                cB = e.y & 0x7fffffff;
-                forced = (e.y & FORCED) != 0;
-            }
-            // outcome of this lane
-            int emit_m2l = 0, emit_p2p = 0, emit_self = 0;
-            int split_kind = 0;       // 0 none, 1 self-split of cA, 2 split cA against cB, 3 split cB against cA
-            bool split_forced = false;
-            long long dpair = 0, dself = 0, inter = 0;
-            // every cell field this lane may need, loaded in one round
-            int nA = 0, nB = 0, chA = 0, chB = 0, c0A = 0, c0B = 0;
-            float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha, la = ha, lb = ha;
-            double rA = 0.0, rB = 0.0;
-            if (valid) {
-                nA = __ldg(&A.count[cA]);
-                nB = __ldg(&A.count[cB]);
-                chA = __ldg(&A.nchild[cA]);
-                chB = __ldg(&A.nchild[cB]);
-                c0A = __ldg(&A.child0[cA]);
-                c0B = __ldg(&A.child0[cB]);
-                ha = __ldg(&A.H[cA]);
-                hb = __ldg(&A.H[cB]);
-                la = __ldg(&A.Lo[cA]);
-                lb = __ldg(&A.Lo[cB]);
-                rA = __ldg(&A.rcrit[cA]);
-                rB = __ldg(&A.rcrit[cB]);
-            }
-            if (valid) {
-                const bool leafA = chA == 0, leafB = chB == 0;
-                if (cA == cB) {
-                    if (forced || nA <= A.n_cs || leafA) {
-                        if (!forced) {
-                            dself = 1;
-                            inter = static_cast<long long>(nA) * (nA - 1) / 2;
-                        }
-                        if (leafA) emit_self = 1;
-                        else { split_kind = 1; split_forced = true; }
-                    } else {
-                        split_kind = 1;
-                    }
-                } else if (forced) {
-                    if (leafA && leafB) emit_p2p = 1;
-                    else { split_kind = leafA ? 3 : 2; split_forced = true; }
-                } else {
-                    const long long prod = static_cast<long long>(nA) * nB;
-                    bool direct = false;
-                    if (prod < A.pre) {
-                        direct = true;
-                    } else {
-                        // FP32 first: centres as hi + lo pairs give |s_A - s_B|^2 to ~1e-6
-                        // relative and r_crit is rounded once; outside a band of
-                        // +-2^-14 around the threshold the FP32 answer is the FP64 one,
-                        // inside it the exact FP64 test decides.
-                        const float fx = (ha.x - hb.x) + (la.x - lb.x);
-                        const float fy = (ha.y - hb.y) + (la.y - lb.y);
-                        const float fz = (ha.z - hb.z) + (la.z - lb.z);
-                        const float d2f = fx * fx + fy * fy + fz * fz;
-                        const float tf = ha.w + hb.w, t2f = tf * tf;
-                        bool sep;
-                        if (d2f > 1e-30f && d2f > t2f * (1.0f + 0x1p-14f)) {
-                            sep = true;
-                        } else if (d2f > 1e-30f && d2f < t2f * (1.0f - 0x1p-14f)) {
-                            sep = false;
-                        } else {
-                            const double dx = dsub(A.sx[cA], A.sx[cB]);
-                            const double dy = dsub(A.sy[cA], A.sy[cB]);
-                            const double dz = dsub(A.sz[cA], A.sz[cB]);
-                            const double d2 = dsq3(dx, dy, dz);
-                            if (A.gravity) {
-                                const double t = dadd(rA, rB);
-                                sep = dmul(t, t) <= d2;
-                            } else {
-                                const double t = dmul(dadd(rA, rB), 1.0 + 0x1p-40);
-                                sep = dmul(t, t) < d2;
-                            }
-                        }
-                        if (sep) {
-                            if (A.gravity) emit_m2l = 1;
-                        } else if (prod < A.post || (leafA && leafB)) {
-                            direct = true;
-                        } else if (!leafA && (rA > rB || leafB)) {
-                            split_kind = 2;
-                        } else {
-                            split_kind = 3;
-                        }
-                    }
-                    if (direct) {
-                        dpair = 1;
-                        inter = prod;
-                        if (leafA && leafB) emit_p2p = 1;
-                        else { split_kind = leafA ? 3 : 2; split_forced = true; }
-                    }
-                }
-            }
-            // statistics
-            dpair = warp_sum_ll(dpair);
-            dself = warp_sum_ll(dself);
-            inter = warp_sum_ll(inter);
-            if (lane == 0) {
-                if (dpair) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_pairs),
-                                     static_cast<unsigned long long>(dpair));
-                if (dself) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_self),
-                                     static_cast<unsigned long long>(dself));
-                if (inter) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_inter),
-                                     static_cast<unsigned long long>(inter));
-            }
-            // outputs: one atomic per list per warp, the four issued together
-            int c0 = 0, nch = 0, k = 0;
-            if (split_kind == 1) {
-                c0 = c0A;
-                nch = chA;
-                k = nch * (nch + 1) / 2;
-            } else if (split_kind == 2) {
-                c0 = c0A;
-                nch = chA;
-                k = nch;
-            } else if (split_kind == 3) {
-                c0 = c0B;
-                nch = chB;
-                k = nch;
-            }
-            const unsigned bm = __ballot_sync(0xffffffffu, emit_m2l), bp = __ballot_sync(0xffffffffu, emit_p2p),
-                           bs = __ballot_sync(0xffffffffu, emit_self);
-            int kin = k;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, kin, o);
-                if (lane >= o) kin += v;
-            }
-            const int ktot = __shfl_sync(0xffffffffu, kin, 31);
-            int base_m = 0, base_p = 0, base_s = 0, base_f = 0;
-            if (lane == 0) {
-                if (bm) base_m = atomicAdd(&A.ctl->n_m2l, __popc(bm));
-                if (bp) base_p = atomicAdd(&A.ctl->n_p2p, __popc(bp));
-                if (bs) base_s = atomicAdd(&A.ctl->n_self, __popc(bs));
-                if (ktot) base_f = atomicAdd(ncount, ktot);
-            }
-            base_m = __shfl_sync(0xffffffffu, base_m, 0);
-            base_p = __shfl_sync(0xffffffffu, base_p, 0);
-            base_s = __shfl_sync(0xffffffffu, base_s, 0);
-            base_f = __shfl_sync(0xffffffffu, base_f, 0);
-            const unsigned lt = (1u << lane) - 1u;
-            if (emit_m2l) {
-                const int slot = base_m + __popc(bm & lt);
-                if (slot < A.m2l_cap) A.m2l[slot] = make_int2(cA, cB);
-                else { atomicOr(&A.ctl->err, ERR_M2L); A.ctl->walk_abort[it % 3] = 1; }
-            }
-            if (emit_p2p) {
-                const int slot = base_p + __popc(bp & lt);
-                if (slot < A.p2p_cap) A.p2p[slot] = make_int2(cA, cB);
-                else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
-            }
-            if (emit_self) {
-                const int slot = base_s + __popc(bs & lt);
-                if (slot < A.self_cap) A.self[slot] = cA;
-                else { atomicOr(&A.ctl->err, ERR_P2P); A.ctl->walk_abort[it % 3] = 1; }
-            }
-            if (k > 0) {
-                int slot = base_f + kin - k;
-                if (slot + k > A.front_cap) {
-                    atomicOr(&A.ctl->err, ERR_FRONTIER);
-                    A.ctl->walk_abort[it % 3] = 1;
-                } else {
-                    const int fl = split_forced ? FORCED : 0;
-                    if (split_kind == 1) {
-                        for (int a = 0; a < nch; a++)
-                            for (int b = a; b < nch; b++) nxt[slot++] = make_int2(c0 + a, (c0 + b) | fl);
-                    } else if (split_kind == 2) {
-                        for (int a = 0; a < nch; a++) nxt[slot++] = make_int2(c0 + a, cB | fl);
-                    } else {
-                        for (int b = 0; b < nch; b++) nxt[slot++] = make_int2(cA, (c0 + b) | fl);
-                    }
-                }
-            }
-        }
+        walk_generation(A, it, nf, blockIdx.x * blockDim.x + (threadIdx.x & ~31), gridDim.x * blockDim.x);
         if (!grid_sync(A.ctl, bar)) return;
         // overflow in this generation (slot it mod 3: identical for every block after the barrier)
         if (((volatile int *)A.ctl->walk_abort)[it % 3]) { it++; break; }
