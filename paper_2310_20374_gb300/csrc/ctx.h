@@ -184,7 +184,7 @@ namespace ncorp {
 
 // ---- launchers (sort.cu) ----
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
-                      uint32_t *qx, uint32_t *qy, uint32_t *qz);
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done = false);
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
                     int bits, bool bar_zeroed = false);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
@@ -212,7 +212,8 @@ struct ExtForce {
     double inv_rs2;        // 1 / r_star^2
 };
 void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
-void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual);
+void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual,
+                double kick_h = 0.0);
 
 // ---- collide.cu ----
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
@@ -226,6 +227,17 @@ void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const do
 void launch_scatter_scalar(ncorp_ctx *c, const double *v, const int *perm, double *out, int n);
 void launch_kick(ncorp_ctx *c, const double *vx, const double *vy, const double *vz, const double *ax,
                  const double *ay, const double *az, double h, double *ox, double *oy, double *oz, int n);
+// v' = v + h a, x' = x + dt v' and the bounding box of x' into ctl (which
+// must hold an empty box).
+struct KickDriftArgs {
+    const double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
+    double h, dt;
+    double *ox, *oy, *oz, *ovx, *ovy, *ovz;
+    int n;
+    Ctrl *ctl;
+};
+void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A);
+void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n);
 void launch_drift(ncorp_ctx *c, const double *x, const double *y, const double *z, const double *vx,
                   const double *vy, const double *vz, double dt, double *ox, double *oy, double *oz, int n);
 void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count);

@@ -53,6 +53,8 @@ struct EvalArgs {
     double *ax, *ay, *az;
     double *amx, *amy, *amz;
     double *nx, *ny, *nz;     // near-field sums per moonlet (tree order)
+    double kick_h;            // k_far: v += kick_h a after the evaluation (0: no kick)
+    double *vx, *vy, *vz;
     int *work;
     const Ctrl *ctl;
 };
@@ -81,10 +83,23 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
             }
 }
 
+// 1/r^3 from r^2: an FP32 reciprocal square root refined by two Newton steps
+// in FP64 (the seed's relative error ~2^-22 squares twice, to the FP64
+// rounding level), about a third of the FP64 instructions of a correctly
+// rounded square root and division; outside the FP32 range the direct form.
+__device__ __forceinline__ double inv_r3(double r2) {
+    if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / (r2 * sqrt(r2));
+    double y = static_cast<double>(rsqrtf(static_cast<float>(r2)));
+    const double hr2 = -0.5 * r2;
+    y = y * fma(hr2, y * y, 1.5);
+    y = y * fma(hr2, y * y, 1.5);
+    return y * y * y;
+}
+
 __device__ __forceinline__ void external_force(const ExtForce &E, double X, double Y, double Z, double &ex, double &ey,
                                                double &ez) {
     const double r2 = X * X + Y * Y + Z * Z;
-    const double fc = -E.GMc / (r2 * sqrt(r2));
+    const double fc = -E.GMc * inv_r3(r2);
     ex = fc * X;
     ey = fc * Y;
     ez = fc * Z;
@@ -451,10 +466,16 @@ __global__ void __launch_bounds__(32 * FAR_WARPS) k_far(EvalArgs A) {
             const double mx = static_cast<double>(lx + static_cast<real>(A.nx[i]));
             const double my = static_cast<double>(ly + static_cast<real>(A.ny[i]));
             const double mz = static_cast<double>(lz + static_cast<real>(A.nz[i]));
-            A.ax[i] = mx + ex;
-            A.ay[i] = my + ey;
-            A.az[i] = mz + ez;
+            const double gx = mx + ex, gy = my + ey, gz = mz + ez;
+            A.ax[i] = gx;
+            A.ay[i] = gy;
+            A.az[i] = gz;
             if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
+            if (A.kick_h != 0.0) {   // the step's closing half kick, as k_kick computes it
+                A.vx[i] = dadd(A.vx[i], dmul(A.kick_h, gx));
+                A.vy[i] = dadd(A.vy[i], dmul(A.kick_h, gy));
+                A.vz[i] = dadd(A.vz[i], dmul(A.kick_h, gz));
+            }
         }
     }
 }
@@ -523,6 +544,8 @@ static EvalArgs eval_args(ncorp_ctx *c, const ParticleSet &P, double G, ExtForce
     A.nx = c->amx; A.ny = c->amy; A.nz = c->amz;   // the far kernel overwrites them in place
     A.work = c->work_counter;
     A.ctl = c->ctl;
+    A.kick_h = 0.0;
+    A.vx = A.vy = A.vz = nullptr;
     return A;
 }
 
@@ -547,8 +570,11 @@ void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
-void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual) {
-    const EvalArgs A = eval_args(c, P, G, ext, want_mutual);
+void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual,
+                double kick_h) {
+    EvalArgs A = eval_args(c, P, G, ext, want_mutual);
+    A.kick_h = kick_h;
+    A.vx = P.vx; A.vy = P.vy; A.vz = P.vz;
 #define NCORP_FAR_CASE(PP)                       \
     case PP:                                     \
         if (mixed) far_t<PP, float>(c, A);       \

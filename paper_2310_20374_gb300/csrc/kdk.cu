@@ -51,6 +51,83 @@ __global__ void k_drift(const double *__restrict__ x, const double *__restrict__
     }
 }
 
+// Half kick, drift and the bounding box of the drifted positions in one
+// pass (the step's opening): v' = v + h a, x' = x + dt v', and the box of x'
+// folded as in k_bbox (integer images, one atomic per bound per block).
+__global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
+    __shared__ unsigned long long s_b[6][8];
+    __shared__ int s_bad;
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+    bool bad = false;
+    if (threadIdx.x == 0) s_bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+        const double vx = dadd(A.vx[i], dmul(A.h, A.ax[i]));
+        const double vy = dadd(A.vy[i], dmul(A.h, A.ay[i]));
+        const double vz = dadd(A.vz[i], dmul(A.h, A.az[i]));
+        A.ovx[i] = vx;
+        A.ovy[i] = vy;
+        A.ovz[i] = vz;
+        const double v[3] = {dadd(A.x[i], dmul(A.dt, vx)), dadd(A.y[i], dmul(A.dt, vy)), dadd(A.z[i], dmul(A.dt, vz))};
+        A.ox[i] = v[0];
+        A.oy[i] = v[1];
+        A.oz[i] = v[2];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v[k]));
+            bad |= (u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+            const unsigned long long e = ord_encode(v[k]);
+            lo[k] = e < lo[k] ? e : lo[k];
+            hi[k] = e > hi[k] ? e : hi[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[k], o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[k], o);
+            lo[k] = a < lo[k] ? a : lo[k];
+            hi[k] = b > hi[k] ? b : hi[k];
+        }
+    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) s_bad = 1;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane_id() == 0)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            s_b[k][w] = lo[k];
+            s_b[3 + k][w] = hi[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        unsigned long long r = s_b[k][0];
+        for (int j = 1; j < nw; j++) {
+            const unsigned long long v = s_b[k][j];
+            r = k < 3 ? (v < r ? v : r) : (v > r ? v : r);
+        }
+        if (k < 3) atomicMin(&A.ctl->bbox[k], r);
+        else atomicMax(&A.ctl->bbox[k], r);
+    }
+    if (threadIdx.x == 0 && s_bad) atomicOr(&A.ctl->err, ERR_NONFINITE);
+}
+
+// Positions and velocities to the caller's order in one pass.
+__global__ void k_scatter_state(const double *__restrict__ x, const double *__restrict__ y,
+                                const double *__restrict__ z, const double *__restrict__ vx,
+                                const double *__restrict__ vy, const double *__restrict__ vz,
+                                const int *__restrict__ perm, double *__restrict__ pos, double *__restrict__ vel, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int u = perm[i];
+        pos[3 * u] = x[i];
+        pos[3 * u + 1] = y[i];
+        pos[3 * u + 2] = z[i];
+        vel[3 * u] = vx[i];
+        vel[3 * u + 1] = vy[i];
+        vel[3 * u + 2] = vz[i];
+    }
+}
+
 static int eg(ncorp_ctx *c, int n) { return grid_for(n, 256, 16 * c->num_sms); }
 
 void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n) {
@@ -72,6 +149,17 @@ void launch_scatter_scalar(ncorp_ctx *c, const double *v, const int *perm, doubl
 void launch_kick(ncorp_ctx *c, const double *vx, const double *vy, const double *vz, const double *ax,
                  const double *ay, const double *az, double h, double *ox, double *oy, double *oz, int n) {
     k_kick<<<eg(c, n), 256, 0, c->stream>>>(vx, vy, vz, ax, ay, az, h, ox, oy, oz, n); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A) {
+    k_kick_drift<<<grid_for(A.n, 256, c->num_sms), 256, 0, c->stream>>>(A); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n) {
+    k_scatter_state<<<eg(c, n), 256, 0, c->stream>>>(S.x, S.y, S.z, S.vx, S.vy, S.vz, S.perm, pos, vel, n);
+    c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

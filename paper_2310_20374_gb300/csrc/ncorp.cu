@@ -415,11 +415,11 @@ int finish(ncorp_ctx *c, bool both = false) {
 // near_sorted: the positions are in the previous tree order of nearby
 // positions (a drift), so the keys are nearly sorted.
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
-                int n, bool near_sorted = false) {
+                int n, bool near_sorted = false, bool bbox_done = false) {
     c->cur_n = n;
     {
         Stage st(c, NCORP_STAGE_SORT);
-        launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz);
+        launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz, bbox_done);
         if (near_sorted) sort_near_sorted(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
         else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true);
         ParticleSet view = sr;
@@ -451,7 +451,8 @@ void on_stream(ncorp_ctx *c, cudaStream_t s, F body) {
 // and the far-field evaluation; the second one runs the multipoles beside the
 // walk, then the near field (which needs only the lists) beside M2L and the
 // descent.
-void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual) {
+// kick_h != 0: the evaluation also applies the closing half kick v += kick_h a.
+void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual, double kick_h = 0.0) {
     const bool mixed = c->cfg.precision == NCORP_MIXED;
     const double G = c->cfg.G;
     c->grav_p = p;
@@ -476,7 +477,7 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
     { Stage st(c, NCORP_STAGE_M2L); launch_m2l(c, p, mixed); }
     { Stage st(c, NCORP_STAGE_DESCEND); launch_descend(c, p, mixed); }
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_near, 0));
-    { Stage st(c, NCORP_STAGE_EVAL); launch_far(c, S, p, mixed, G, external(c, t), want_mutual); }
+    { Stage st(c, NCORP_STAGE_EVAL); launch_far(c, S, p, mixed, G, external(c, t), want_mutual, kick_h); }
 }
 
 void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
@@ -501,7 +502,20 @@ constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision
 void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overlap) {
     const double h = 0.5 * dt;
     ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
-    { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, A.vx, A.vy, A.vz, A.ax, A.ay, A.az, h, B.vx, B.vy, B.vz, n); }
+    // the other tree set becomes the new tree's: cleared (its errors kept) before the kick-drift
+    // kernel folds the drifted positions' bounding box into its control block
+    on_alt(c, [&] { reset_ctl(c, true); });
+    {
+        Stage st(c, NCORP_STAGE_KDK);
+        KickDriftArgs K;
+        K.x = A.x; K.y = A.y; K.z = A.z; K.vx = A.vx; K.vy = A.vy; K.vz = A.vz;
+        K.ax = A.ax; K.ay = A.ay; K.az = A.az;
+        K.h = h; K.dt = dt;
+        K.ox = B.x; K.oy = B.y; K.oz = B.z; K.ovx = B.vx; K.ovy = B.vy; K.ovz = B.vz;
+        K.n = n;
+        K.ctl = c->alt.ctl;
+        launch_kick_drift(c, K);
+    }
     const bool side = overlap && c->cfg.collisions;
     if (c->cfg.collisions) {
         if (side) {
@@ -526,12 +540,9 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         }
     }
     swap_sets(c);
-    reset_ctl(c, true);
-    { Stage st(c, NCORP_STAGE_KDK); launch_drift(c, A.x, A.y, A.z, B.vx, B.vy, B.vz, dt, B.x, B.y, B.z, n); }
-    build_tree(c, B, B, A, Cn, n, true);
-    gravity(c, Cn, p, theta, c->time + dt, false);
+    build_tree(c, B, B, A, Cn, n, true, true);
+    gravity(c, Cn, p, theta, c->time + dt, false, h);   // with the closing half kick
     if (side) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-    { Stage st(c, NCORP_STAGE_KDK); launch_kick(c, Cn.vx, Cn.vy, Cn.vz, Cn.ax, Cn.ay, Cn.az, h, Cn.vx, Cn.vy, Cn.vz, n); }
 }
 
 // col: the control block of the tree the collision search ran on (NULL: the current one)
@@ -615,8 +626,7 @@ void resident_step_body(ncorp_ctx *c, double *pos, double *vel, int n, int p, do
     enqueue_kdk(c, n, p, theta, dt, true);
     Stage st(c, NCORP_STAGE_KDK);
     ParticleSet &Cn = c->Cset;
-    launch_scatter_aos(c, Cn.x, Cn.y, Cn.z, Cn.perm, dev_x ? pos : c->stage, n);
-    launch_scatter_aos(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, dev_v ? vel : c->stage2, n);
+    launch_scatter_state(c, Cn, dev_x ? pos : c->stage, dev_v ? vel : c->stage2, n);
 }
 
 // Enqueues a resident step on c->stream through a cached graph (capturing it

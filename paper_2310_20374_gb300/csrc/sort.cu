@@ -188,12 +188,16 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     }
 }
 
-// The bounding box in ctl must be empty on entry (k_reset_ctl leaves it so);
-// k_keys also zeroes the grid-barrier counter for the sort that follows.
+// The bounding box in ctl must be empty on entry (k_reset_ctl leaves it so),
+// or already hold the positions' box (bbox_done: the step's kick-drift kernel
+// folds it); k_keys also zeroes the grid-barrier counter for the sort that
+// follows.
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
-                      uint32_t *qx, uint32_t *qy, uint32_t *qz) {
-    k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done) {
+    if (!bbox_done) {
+        k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
+        NCORP_CUDA_CHECK(cudaGetLastError());
+    }
     k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
