@@ -68,6 +68,21 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def slowest_rank(dist, value, world, device="cuda"):
+    """Max over the ranks of a per-rank time: the replicas' aggregate runs as long as the slowest rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, world, seconds):
+    """Whole-job particle-steps/s of `world` independent replicas timed by the slowest one."""
+    return units_per_rank * steps * world / seconds
+
+
 def workload_config(a):
     return {"workload": f"1 disk x {a.n} moonlets per GPU (seed {a.seed}+rank), falcON p={a.p} theta_min={a.theta}, "
                         f"SBAB1 step dt={a.dt} with tree collision search, {a.precision} precision",
@@ -213,12 +228,8 @@ def run_gpu(a):
         for k, v in ncorp.ncorp_stage_times(ctx).items():
             stage[k] = stage.get(k, 0.0) + v
     ncorp.ncorp_profile(ctx, False)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = a.n * a.steps * world / (t_max * 1e-3)
+    t_max = slowest_rank(dist, total_ms, world)
+    value = replica_throughput(a.n, a.steps, world, t_max * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers: every step
     # copies the state in (positions, velocities, masses, radii), runs the step
@@ -239,12 +250,8 @@ def run_gpu(a):
         ncorp.ncorp_step(ctx, hp, hv, hm, hR, a.n, a.p, a.theta, a.dt)
         npairs += ncorp.ncorp_collisions(ctx, hpairs, hpairs.shape[0])
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": a.n * e2e_steps * world / e2e_s, "unit": UNIT,
+    e2e_s = slowest_rank(dist, time.perf_counter() - t0, world)
+    e2e = {"value": replica_throughput(a.n, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": a.n * (24 + 24 + 8 + 8),
            "d2h_bytes_per_step": a.n * (24 + 24) + 16 * (npairs // e2e_steps),
            "note": "state uploaded from pinned host memory every step (so the step also recomputes the "
@@ -404,11 +411,7 @@ def run_ensemble(a):
     barrier()
     clocks = sampler.stop()
     info = ncorp.ncorp_batch_info(b)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = slowest_rank(dist, ms, world)
     # end to end: states read back to host memory after the run (state stays resident between runs)
     hp = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
     hv = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
@@ -416,9 +419,9 @@ def run_ensemble(a):
     ncorp.ncorp_batch_run(b, a.steps)
     for k in range(len(sizes)):
         ncorp.ncorp_batch_get_state(b, k, hp[k], hv[k])
-    e2e_s = time.perf_counter() - t0
+    e2e_s = slowest_rank(dist, time.perf_counter() - t0, world)
     ncorp.ncorp_batch_free(b)
-    value = total * a.steps * world / (t_max * 1e-3)
+    value = replica_throughput(total, a.steps, world, t_max * 1e-3)
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
@@ -430,7 +433,7 @@ def run_ensemble(a):
                       "l2": "inputs larger than L2 (about 1 kB of state and tree per moonlet)",
                       "parallelism": "replicas (one batch of 64 disks per GPU)"},
            "gpu_launches": info["launches"], "clocks": clocks,
-           "e2e": {"value": round(total * a.steps * world / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+           "e2e": {"value": round(replica_throughput(total, a.steps, world, e2e_s), 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": int(48 * total / a.steps),
                    "note": "host wall time of ncorp_batch_run plus reading every disk's state back to pinned host "
                            "memory once per run (per-step bytes averaged)"}}
