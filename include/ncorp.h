@@ -56,7 +56,8 @@ typedef struct ncorp_ctx ncorp_ctx;
 typedef struct {
     double G;                 /* gravitational constant */
     double central_mass;      /* M_c (App. B.1) */
-    double central_radius;    /* R_c (informational; collisions with the central body are not searched) */
+    double central_radius;    /* R_c: radius of the equatorial bulge term (collisions with the central body
+                                 are not searched) */
     int leaf_size;            /* s: cells with more than s moonlets are split (Sect. 3.4.1); 0 = default for p */
     int n_cs, n_cc_pre, n_cc_post;  /* gravity TreeWalk thresholds (Sect. 3.4.5); all 0 = defaults for p */
     int c_cs, c_cc_pre, c_cc_post;  /* collision TreeWalk thresholds; all 0 = 12, 0, 16 (Sect. 4.2) */
@@ -66,10 +67,15 @@ typedef struct {
     double star_a;            /* star orbital radius */
     double star_obliquity;    /* obliquity epsilon of the central body (radians) */
     double t0;                /* initial time (sets the star's longitude n t) */
+    double central_J2;        /* J2 of the central body's equatorial bulge (App. B.2): adds
+                                 G M_c R_c^2 J2 / r^5 [(15 z^2 - 3 r^2) / (2 r^2) r - 3 z k] to every
+                                 moonlet's acceleration, k = the frame's z axis (the body's rotation
+                                 axis); 0 disables.  For a fluid body rotating at Omega,
+                                 J2 = Omega^2 / (2 G M_c / R_c^3). */
 } ncorp_config;
 
 /* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
- * NCORP_MIXED, collisions on, no star. */
+ * NCORP_MIXED, collisions on, no star, no bulge (J2 = 0). */
 void ncorp_config_default(ncorp_config *cfg);
 
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.

@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("n_cs", C.c_int64), ("n_cc_pre", C.c_int64), ("n_cc_post", C.c_int64),
                 ("c_cs", C.c_int64), ("c_cc_pre", C.c_int64), ("c_cc_post", C.c_int64),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
-                ("time", C.c_double), ("m2m_direct", C.c_int), ("brute_collisions", C.c_int)]
+                ("time", C.c_double), ("m2m_direct", C.c_int), ("brute_collisions", C.c_int),
+                ("central_radius", C.c_double), ("central_J2", C.c_double)]
 
 
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
@@ -113,7 +114,8 @@ def default_gravity_thresholds(p: int):
 
 def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresholds=None,
            collision_thresholds=(12, 0, 16), star=None, time=0.0, m2m_direct=False,
-           brute_collisions=False) -> Params:
+           brute_collisions=False, bulge=None) -> Params:
+    """bulge: (R_c, J2) of the central body's equatorial bulge (App. B.2), None = no bulge."""
     g = gravity_thresholds if gravity_thresholds is not None else default_gravity_thresholds(p)
     P = Params()
     P.G, P.central_mass, P.p, P.theta_min, P.leaf_size = G, central_mass, int(p), theta, int(leaf_size)
@@ -124,6 +126,8 @@ def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresh
     P.time = time
     P.m2m_direct = int(bool(m2m_direct))
     P.brute_collisions = int(bool(brute_collisions))
+    if bulge:
+        P.central_radius, P.central_J2 = bulge
     return P
 
 

@@ -55,6 +55,7 @@ typedef struct {
     double star_mass, star_a, star_obliquity, time; /* App. B.3; star_mass = 0 disables */
     int m2m_direct;         /* 1: parent multipoles by direct P2M over all members */
     int brute_collisions;   /* KDK: 1 = brute force pairs, 0 = tree */
+    double central_radius, central_J2;   /* App. B.2 equatorial bulge; J2 = 0 disables */
 } or_params;
 
 /* statistics, int64 slots */
@@ -417,7 +418,10 @@ static void star_position(const or_params *P, double t, double rs[3])
     rs[2] = P->star_a * sin(lam) * sin(P->star_obliquity);
 }
 
-/* central mass (App. B.1) + optional quadrupole star tide (App. B.3), added into acc */
+/* central mass (App. B.1) + optional equatorial bulge of the central body
+ * (App. B.2: a = G M_c R_c^2 J2 / r^5 [ (15 z^2 - 3 r^2) / (2 r^2) r - 3 z k ],
+ * k the body's rotation axis = the frame's z axis) + optional quadrupole star
+ * tide (App. B.3), added into acc */
 void or_external_accel(const or_params *P, int64_t n, const double *pos, double t, double *acc)
 {
     double rs[3] = {0, 0, 0}, rs2 = 0.0, ks = 0.0;
@@ -433,6 +437,13 @@ void or_external_accel(const or_params *P, int64_t n, const double *pos, double 
         double r = sqrt(r2);
         double f = -(P->G * P->central_mass) / (r2 * r);
         for (int k = 0; k < 3; k++) acc[3 * i + k] += f * x[k];
+        if (P->central_J2 != 0.0) {
+            double q = P->G * P->central_mass * P->central_radius * P->central_radius * P->central_J2 / (r2 * r2 * r);
+            double z2 = x[2] * x[2];
+            double radial = q * (15.0 * z2 - 3.0 * r2) / (2.0 * r2);
+            for (int k = 0; k < 3; k++) acc[3 * i + k] += radial * x[k];
+            acc[3 * i + 2] -= 3.0 * q * x[2];
+        }
         if (star) {
             double c = 3.0 * dot3(x, rs) / rs2;
             for (int k = 0; k < 3; k++) acc[3 * i + k] -= ks * (x[k] - c * rs[k]);

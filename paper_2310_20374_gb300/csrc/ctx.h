@@ -210,6 +210,7 @@ struct ExtForce {
     double star_k;         // G M_star / r_star^3 (0: off)
     double sx, sy, sz;     // star position
     double inv_rs2;        // 1 / r_star^2
+    double bulge;          // G M_c R_c^2 J2 of the equatorial bulge (0: off)
 };
 void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
 void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual,

@@ -83,26 +83,37 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
             }
 }
 
-// 1/r^3 from r^2: an FP32 reciprocal square root refined by two Newton steps
+// 1/r from r^2: an FP32 reciprocal square root refined by two Newton steps
 // in FP64 (the seed's relative error ~2^-22 squares twice, to the FP64
-// rounding level), about a third of the FP64 instructions of a correctly
-// rounded square root and division; outside the FP32 range the direct form.
-__device__ __forceinline__ double inv_r3(double r2) {
-    if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / (r2 * sqrt(r2));
+// rounding level): with 1/r^3 = y^3 and 1/r^5 = y^5 about a third of the FP64
+// instructions of correctly rounded square roots and divisions; outside the
+// FP32 range the direct form.
+__device__ __forceinline__ double inv_r(double r2) {
+    if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / sqrt(r2);
     double y = static_cast<double>(rsqrtf(static_cast<float>(r2)));
     const double hr2 = -0.5 * r2;
     y = y * fma(hr2, y * y, 1.5);
     y = y * fma(hr2, y * y, 1.5);
-    return y * y * y;
+    return y;
 }
 
+// Central body (App. B.1), its equatorial bulge (App. B.2, k = z axis) and the
+// distant star's tide (App. B.3), in FP64.
 __device__ __forceinline__ void external_force(const ExtForce &E, double X, double Y, double Z, double &ex, double &ey,
                                                double &ez) {
     const double r2 = X * X + Y * Y + Z * Z;
-    const double fc = -E.GMc * inv_r3(r2);
+    const double y = inv_r(r2), y2 = y * y, y3 = y2 * y;
+    const double fc = -E.GMc * y3;
     ex = fc * X;
     ey = fc * Y;
     ez = fc * Z;
+    if (E.bulge != 0.0) {
+        const double q = E.bulge * y3 * y2;   // G M_c R_c^2 J2 / r^5
+        const double radial = q * (15.0 * Z * Z - 3.0 * r2) * (0.5 * y2);
+        ex += radial * X;
+        ey += radial * Y;
+        ez += radial * Z - 3.0 * q * Z;
+    }
     if (E.star_k != 0.0) {
         const double c3 = 3.0 * (X * E.sx + Y * E.sy + Z * E.sz) * E.inv_rs2;
         ex -= E.star_k * (X - c3 * E.sx);

@@ -304,6 +304,7 @@ ExtForce external(ncorp_ctx *c, double t) {
     ExtForce e{};
     const ncorp_config &g = c->cfg;
     e.GMc = g.G * g.central_mass;
+    e.bulge = g.G * g.central_mass * g.central_radius * g.central_radius * g.central_J2;
     if (g.star_mass != 0.0) {
         const double a = g.star_a;
         const double nsun = std::sqrt(g.G * g.star_mass / (a * a * a));

@@ -36,7 +36,7 @@ class ncorp_config(C.Structure):
                 ("c_cs", C.c_int), ("c_cc_pre", C.c_int), ("c_cc_post", C.c_int),
                 ("precision", C.c_int), ("collisions", C.c_int),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
-                ("t0", C.c_double)]
+                ("t0", C.c_double), ("central_J2", C.c_double)]
 
 
 _lib = None

@@ -36,7 +36,7 @@ def test_config_default(lib):
     cfg = ncorp.ncorp_config_default()
     assert cfg.G == 1.0 and cfg.central_mass == 1.0 and cfg.central_radius == 1.0
     assert cfg.precision == ncorp.NCORP_MIXED and cfg.collisions == 1
-    assert cfg.leaf_size == 0 and cfg.star_mass == 0.0
+    assert cfg.leaf_size == 0 and cfg.star_mass == 0.0 and cfg.central_J2 == 0.0
 
 
 def test_bad_arguments_rejected_without_device_work(lib):

@@ -28,8 +28,11 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
 
 
-def make_ctx(n_max, precision=ncorp.NCORP_FP64, s=16, grav=(64, 8, 64), col=(12, 0, 16), collisions=1, star=None):
+def make_ctx(n_max, precision=ncorp.NCORP_FP64, s=16, grav=(64, 8, 64), col=(12, 0, 16), collisions=1, star=None,
+             bulge=None):
     cfg = ncorp.ncorp_config_default()
+    if bulge:
+        cfg.central_radius, cfg.central_J2 = bulge
     cfg.precision = precision
     cfg.leaf_size = s
     cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = grav
@@ -166,6 +169,37 @@ def test_star_tide_and_central_force():
     P = oracle.params(p=3, star=star)
     ext = oracle.external_accel(P, d["pos"], 0.0)
     np.testing.assert_allclose(acc - mut, ext, rtol=1e-13, atol=1e-18)
+
+
+def test_equatorial_bulge_and_star():
+    """External forces with the central body's bulge (App. B.2) and the star
+    (App. B.3) together, FP64: the acceleration minus the mutual part is the
+    oracle's external acceleration; three KDK steps (the later ones replayed
+    from a graph) follow the oracle's."""
+    n, dt = 2000, 2e-3
+    d = diskgen.make_disk(n, 42)
+    star, bulge = (3.3e5, 2.3e4, 0.41), (1.0, 1.08e-3)
+    ctx = make_ctx(n, s=16, star=star, bulge=bulge)
+    try:
+        acc, mut, _ = gpu_accel(ctx, d, 3, 0.5)
+    finally:
+        ncorp.ncorp_free(ctx)
+    P = oracle.params(p=3, star=star, bulge=bulge, leaf_size=16, gravity_thresholds=(64, 8, 64))
+    ext = oracle.external_accel(P, d["pos"], 0.0)
+    np.testing.assert_allclose(acc - mut, ext, rtol=1e-13, atol=1e-18)
+    no_bulge = oracle.external_accel(oracle.params(p=3, star=star), d["pos"], 0.0)
+    assert np.abs(ext - no_bulge).max() > 1e-7 * np.abs(ext).max()   # the term is there
+    ctx = make_ctx(n, s=16, bulge=bulge)
+    x, v = d["pos"].copy(), d["vel"].copy()
+    try:
+        for _ in range(3):
+            ncorp.ncorp_step(ctx, x, v, d["mass"], d["radius"], n, 3, 0.5, dt)
+    finally:
+        ncorp.ncorp_free(ctx)
+    Pk = oracle.params(p=3, bulge=bulge, leaf_size=16, gravity_thresholds=(64, 8, 64))
+    xo, vo, _, _ = oracle.kdk(Pk, d["pos"], d["vel"], d["mass"], d["radius"], dt, 3)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-13 * np.abs(xo).max())
+    np.testing.assert_allclose(v, vo, rtol=0, atol=1e-12 * np.abs(vo).max())
 
 
 # ------------------------------------------------------------- collisions

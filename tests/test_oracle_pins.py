@@ -382,3 +382,57 @@ def test_external_forces(oracle_lib):
     a = oracle_lib.external_accel(P, np.array([[0.5, 0.0, 0.0], [0.0, 0.5, 0.0]]), 0.0)
     np.testing.assert_allclose(a[0], [2 * 5.0 * 0.5 / 40.0 ** 3, 0, 0], rtol=1e-14, atol=1e-20)
     np.testing.assert_allclose(a[1], [0, -5.0 * 0.5 / 40.0 ** 3, 0], rtol=1e-14, atol=1e-20)
+
+
+# ---------------------------------------------------------------- equatorial bulge (App. B.2)
+def _bulge_only(oracle, P_bulge, x):
+    """The bulge term: with and without it, minus (so only to ~1e-16 of the central force)."""
+    return oracle.external_accel(P_bulge, x) - oracle.external_accel(oracle.params(), x)
+
+
+def test_bulge_closed_forms_on_the_equator_and_the_pole(oracle_lib):
+    """In the equatorial plane the bulge adds -(3/2) G M R^2 J2 / r^4 along r (a
+    stronger pull), on the axis +3 G M R^2 J2 / r^4 along z (a weaker one)."""
+    oracle = oracle_lib
+    R, J2 = 1.3, 1.08e-3
+    P = oracle.params(bulge=(R, J2))
+    for r in (2.0, 3.7):
+        a = _bulge_only(oracle, P, np.array([[r, 0.0, 0.0], [0.0, 0.0, r], [0.0, 0.0, -r]]))
+        k = R * R * J2 / r ** 4
+        np.testing.assert_allclose(a[0], [-1.5 * k, 0, 0], rtol=1e-11, atol=1e-20)
+        np.testing.assert_allclose(a[1], [0, 0, 3.0 * k], rtol=1e-11, atol=1e-20)
+        np.testing.assert_allclose(a[2], [0, 0, -3.0 * k], rtol=1e-11, atol=1e-20)
+
+
+def test_bulge_is_the_gradient_of_the_quadrupole_potential(oracle_lib):
+    """a = grad Phi with Phi = -G M R^2 J2 P2(z/r) / r^3 (sign convention
+    a = grad Phi, Phi = +G M / r for the central mass), by central differences."""
+    oracle = oracle_lib
+    R, J2, GM = 0.9, 2.0e-3, 1.0
+    P = oracle.params(bulge=(R, J2))
+
+    def phi(x):
+        r = np.linalg.norm(x)
+        mu = x[2] / r
+        return -GM * R * R * J2 * 0.5 * (3 * mu * mu - 1) / r ** 3
+
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(20, 3)) * 2 + np.array([3.0, 0, 0])
+    a = _bulge_only(oracle, P, x)
+    h = 1e-5
+    for i in range(len(x)):
+        g = [(phi(x[i] + h * e) - phi(x[i] - h * e)) / (2 * h) for e in np.eye(3)]
+        np.testing.assert_allclose(a[i], g, rtol=1e-7, atol=1e-12 * np.abs(g).max())
+
+
+def test_bulge_symmetries(oracle_lib):
+    """Axisymmetric about z (a rotation of x, y rotates a_x, a_y) and odd in z for a_z."""
+    oracle = oracle_lib
+    P = oracle.params(bulge=(1.0, 1e-3))
+    x = np.array([[2.1, 0.4, 0.3]])
+    c, s = np.cos(0.7), np.sin(0.7)
+    Rz = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+    a = _bulge_only(oracle, P, x)[0]
+    np.testing.assert_allclose(_bulge_only(oracle, P, (Rz @ x[0])[None])[0], Rz @ a, rtol=1e-11, atol=1e-20)
+    m = np.array([[1.0, 1.0, -1.0]])
+    np.testing.assert_allclose(_bulge_only(oracle, P, x * m)[0], a * m[0], rtol=1e-11, atol=1e-20)
