@@ -133,8 +133,6 @@ struct ncorp_ctx {
     int *tile_hist = nullptr;        // radix sort: digit histograms, epoch, status words
     int tile_hist_cap = 0;
     unsigned radix_epoch_limit = 0;  // radix tag epochs before the status words are cleared
-    int *scan_tmp = nullptr;
-    int scan_tmp_cap = 0;
     double *stage = nullptr;         // [n][3] AoS staging
     double *stage2 = nullptr;
 
@@ -189,7 +187,6 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
                     int bits, bool bar_zeroed = false);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
                    const uint32_t *idx, double G);
-void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total);
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 
 // ---- tree.cu ----
@@ -225,9 +222,6 @@ void launch_sort_pairs(ncorp_ctx *c, int count);
 void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n);
 void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm,
                         double *aos, int n);
-void launch_scatter_scalar(ncorp_ctx *c, const double *v, const int *perm, double *out, int n);
-void launch_kick(ncorp_ctx *c, const double *vx, const double *vy, const double *vz, const double *ax,
-                 const double *ay, const double *az, double h, double *ox, double *oy, double *oz, int n);
 // v' = v + h a, x' = x + dt v' and the bounding box of x' into ctl (which
 // must hold an empty box).
 struct KickDriftArgs {
@@ -239,8 +233,6 @@ struct KickDriftArgs {
 };
 void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A);
 void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n);
-void launch_drift(ncorp_ctx *c, const double *x, const double *y, const double *z, const double *vx,
-                  const double *vy, const double *vz, double dt, double *ox, double *oy, double *oz, int n);
 void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count);
 
 // host-side error helper used by every launcher

@@ -1159,7 +1159,7 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->rcf);
     dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
     dfree(c->resort_mkey); dfree(c->resort_midx); dfree(c->resort_bcount);
-    dfree(c->tile_hist); dfree(c->scan_tmp); dfree(c->stage); dfree(c->stage2);
+    dfree(c->tile_hist); dfree(c->stage); dfree(c->stage2);
     for (int set = 0; set < 2; set++) {
         Cells &C = c->cells;
         dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);

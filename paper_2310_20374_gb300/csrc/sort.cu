@@ -1,13 +1,13 @@
-// sort.cu -- root cube, quantisation, 3-D Hilbert keys, LSD radix sort of the
-// keys, gather of the moonlet state into key order, and exclusive scans.
+// sort.cu -- root cube, quantisation, 3-D Hilbert keys, their sort (LSD
+// radix sort, or the merge of the few out-of-place keys of a step), and the
+// gather of the moonlet state into key order.
 //
 // Sect. 3.4.6: cells of a level are ordered along a 3-D Hilbert curve and
 // moonlets are inserted in the Hilbert order of their leaves.  Here every
 // moonlet gets the 63-bit Hilbert index of its quantised position (21 bits
-// per axis inside the root cube) and the state is sorted by (key, previous
-// position) with a stable radix sort, so that every cell of every level owns
-// a contiguous range of moonlets and consecutive cells of a level are
-// consecutive along the curve.
+// per axis inside the root cube) and the state is sorted by (key, caller
+// index), so that every cell of every level owns a contiguous range of
+// moonlets and consecutive cells of a level are consecutive along the curve.
 #include <algorithm>
 #include <cfloat>
 #include <cstdlib>
@@ -202,11 +202,6 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
-// ---------------------------------------------------------------------------
-// Exclusive scan of int arrays: block sums, scan of the sums, block scans.
-// ---------------------------------------------------------------------------
-constexpr int SCAN_T = 512, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
-
 __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int incl = v;
@@ -233,82 +228,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
     if (total) *total = s_warp[32];
     __syncthreads();
     return res;
-}
-
-__global__ void k_scan_reduce(const int *__restrict__ in, int n, int *__restrict__ bsum) {
-    __shared__ int s_warp[33];
-    long long base = static_cast<long long>(blockIdx.x) * SCAN_TILE;
-    int sum = 0;
-    for (int k = 0; k < SCAN_I; k++) {
-        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
-        if (i < n) sum += in[i];
-    }
-    int tot;
-    block_excl_scan(sum, s_warp, &tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-}
-
-__global__ void k_scan_top(int *bsum, int nb) {
-    __shared__ int s_warp[33];
-    __shared__ int s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
-        int i = b0 + threadIdx.x;
-        int v = i < nb ? bsum[i] : 0;
-        int tot;
-        int ex = block_excl_scan(v, s_warp, &tot);
-        if (i < nb) bsum[i] = ex + s_carry;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) bsum[nb] = s_carry;
-}
-
-__global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, int n, const int *__restrict__ bsum,
-                             int nb, int *total) {
-    __shared__ int s_warp[33];
-    __shared__ int s_tile[SCAN_TILE];
-    long long base = static_cast<long long>(blockIdx.x) * SCAN_TILE;
-    for (int k = 0; k < SCAN_I; k++) {
-        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
-        s_tile[k * SCAN_T + threadIdx.x] = i < n ? in[i] : 0;
-    }
-    __syncthreads();
-    int v[SCAN_I], sum = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_I; k++) {
-        v[k] = s_tile[threadIdx.x * SCAN_I + k];
-        sum += v[k];
-    }
-    int ex = block_excl_scan(sum, s_warp, nullptr) + bsum[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < SCAN_I; k++) {
-        s_tile[threadIdx.x * SCAN_I + k] = ex;
-        ex += v[k];
-    }
-    __syncthreads();
-    for (int k = 0; k < SCAN_I; k++) {
-        long long i = base + static_cast<long long>(k) * SCAN_T + threadIdx.x;
-        if (i < n) out[i] = s_tile[k * SCAN_T + threadIdx.x];
-    }
-    if (total && blockIdx.x == 0 && threadIdx.x == 0) *total = bsum[nb];
-}
-
-void scan_exclusive(ncorp_ctx *c, const int *in, int *out, int n, int *total) {
-    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb < 1) nb = 1;
-    if (c->scan_tmp_cap < nb + 1) {
-        if (c->scan_tmp) cudaFree(c->scan_tmp);
-        c->scan_tmp_cap = nb + 1024;
-        NCORP_CUDA_CHECK(cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_cap));
-        bump_alloc_generation();
-    }
-    k_scan_reduce<<<nb, SCAN_T, 0, c->stream>>>(in, n, c->scan_tmp); c->launches++;
-    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_tmp, nb); c->launches++;
-    k_scan_apply<<<nb, SCAN_T, 0, c->stream>>>(in, out, n, c->scan_tmp, nb, total); c->launches++;
-    NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
