@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("c_cs", C.c_int64), ("c_cc_pre", C.c_int64), ("c_cc_post", C.c_int64),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
                 ("time", C.c_double), ("m2m_direct", C.c_int), ("brute_collisions", C.c_int),
-                ("central_radius", C.c_double), ("central_J2", C.c_double)]
+                ("central_radius", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double)]
 
 
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
@@ -90,6 +90,8 @@ def lib():
             L.or_collide_pair.restype = C.c_int
             L.or_collide_brute.argtypes = [i64, _dp, _dp, _dp, dbl, _ip, i64]
             L.or_collide_brute.restype = i64
+            L.or_resolve.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, _ip, i64, _opt(_ip)]
+            L.or_resolve.restype = i64
             L.or_falcon_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
             L.or_falcon_accel.restype = C.c_int
             L.or_collide_tree.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
@@ -99,7 +101,8 @@ def lib():
             L.or_tree_export.restype = i64
             L.or_expansions.argtypes = [PP, i64, _dp, _dp, _opt(_dp), _opt(_dp), i64]
             L.or_expansions.restype = i64
-            L.or_kdk.argtypes = [PP, i64, _dp, _dp, _dp, _dp, dbl, C.c_int, _opt(_dp), _opt(_dp), _ip, i64]
+            L.or_kdk.argtypes = [PP, i64, _dp, _dp, _dp, _dp, dbl, C.c_int, _opt(_dp), _opt(_dp), _ip, i64,
+                                 _opt(_ip)]
             L.or_kdk.restype = i64
             _lib = L
     return _lib
@@ -114,8 +117,9 @@ def default_gravity_thresholds(p: int):
 
 def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresholds=None,
            collision_thresholds=(12, 0, 16), star=None, time=0.0, m2m_direct=False,
-           brute_collisions=False, bulge=None) -> Params:
-    """bulge: (R_c, J2) of the central body's equatorial bulge (App. B.2), None = no bulge."""
+           brute_collisions=False, bulge=None, resolve_f=0.0) -> Params:
+    """bulge: (R_c, J2) of the central body's equatorial bulge (App. B.2), None = no bulge.
+    resolve_f: 0 = colliding pairs are only reported; 1 <= f <= 2 = kdk() resolves them (Sect. 5)."""
     g = gravity_thresholds if gravity_thresholds is not None else default_gravity_thresholds(p)
     P = Params()
     P.G, P.central_mass, P.p, P.theta_min, P.leaf_size = G, central_mass, int(p), theta, int(leaf_size)
@@ -128,6 +132,7 @@ def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresh
     P.brute_collisions = int(bool(brute_collisions))
     if bulge:
         P.central_radius, P.central_J2 = bulge
+    P.resolve_f = float(resolve_f)
     return P
 
 
@@ -258,6 +263,17 @@ def collide_tree(P: Params, pos, vel, rad, dt, cap=1 << 16):
     return out[:n], dict(zip(STAT_NAMES, (int(v) for v in st)))
 
 
+def resolve(pos, vel, mass, rad, f, pairs):
+    """Resolves colliding pairs (rows i < j) of one step (Sect. 5.1-5.2); returns (positions the drift
+    starts from, new velocities, per-pair resolved flags)."""
+    pos, vel = _f64(pos).copy(), _f64(vel).copy()
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    done = np.zeros(max(len(pr), 1), dtype=np.int64)
+    lib().or_resolve(len(pos), pos.reshape(-1), vel.reshape(-1), _f64(mass), _f64(rad), float(f),
+                     pr.reshape(-1) if len(pr) else np.zeros(2, dtype=np.int64), len(pr), done)
+    return pos, vel, done[:len(pr)].astype(bool)
+
+
 def tree_export(P: Params, pos, mass=None, vel=None, rad=None, dt=0.0):
     """Canonical order, keys, root, cells[k,7], gravity geometry[k,6], collision geometry[k,5]."""
     pos = _f64(pos)
@@ -305,13 +321,17 @@ def full_to_multi(T, order):
     return np.array(out)
 
 
-def kdk(P: Params, pos, vel, mass, rad, dt, nsteps, acc0=None, cap=1 << 16):
-    """Runs nsteps KDK steps; returns (pos, vel, acc, pairs[k,3] as (step, i, j))."""
+def kdk(P: Params, pos, vel, mass, rad, dt, nsteps, acc0=None, cap=1 << 16, info=None):
+    """Runs nsteps KDK steps; returns (pos, vel, acc, pairs[k,3] as (step, i, j)).  With a dict as
+    info, info["resolved"] receives the number of resolved impacts (-1: the pair buffer overflowed)."""
     pos, vel = _f64(pos).copy(), _f64(vel).copy()
     n = len(pos)
     acc = np.zeros((max(n, 1), 3))
     out = np.zeros((cap, 3), dtype=np.int64)
     a0 = None if acc0 is None else _f64(acc0).reshape(-1)
+    res = np.zeros(1, dtype=np.int64)
     tot = lib().or_kdk(C.byref(P), n, pos.reshape(-1), vel.reshape(-1), _f64(mass), _f64(rad), float(dt),
-                       int(nsteps), a0, acc.reshape(-1), out.reshape(-1), cap)
+                       int(nsteps), a0, acc.reshape(-1), out.reshape(-1), cap, res)
+    if info is not None:
+        info["resolved"] = int(res[0])
     return pos, vel, acc[:n], out[:min(tot, cap)]

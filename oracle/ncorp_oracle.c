@@ -27,6 +27,7 @@
  *   - the dual tree walk (Algorithm TreeWalk, Sect. 3.4.5)           pinned
  *   - the collision predicate (Sect. 3.1), brute force and tree-based  pinned
  *   - the SBAB1 kick-drift-kick step with merged kicks (Sect. 4.1)    pinned
+ *   - elastic and inelastic collision resolution (Sect. 5.1, 5.2)     pinned
  *
  * Readings of points the paper leaves open (numbered as in the design
  * notes): root cube and quantisation; Skilling's Hilbert curve; ties in the
@@ -35,7 +36,9 @@
  * softening; collision pruning with a 2^-40 relative margin; the corner
  * cap computed on the cell cube widened by L*2^-48; the moonlet mean of
  * Eq. center weighted by child counts; theta(M) solved by 12 bisection
- * steps and 4 Newton steps without libm.
+ * steps and 4 Newton steps without libm; one impact per moonlet per step,
+ * pairs resolved in increasing (dt_c, i, j), the rest of the step travelled
+ * at the new velocity.
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,6 +59,7 @@ typedef struct {
     int m2m_direct;         /* 1: parent multipoles by direct P2M over all members */
     int brute_collisions;   /* KDK: 1 = brute force pairs, 0 = tree */
     double central_radius, central_J2;   /* App. B.2 equatorial bulge; J2 = 0 disables */
+    double resolve_f;       /* KDK: 0 = pairs reported only; 1..2 = resolved with this f (Sect. 5) */
 } or_params;
 
 /* statistics, int64 slots */
@@ -456,8 +460,9 @@ void or_external_accel(const or_params *P, int64_t n, const double *pos, double 
 /* Delta = (dr.dv)^2 + dv^2 ((R1+R2)^2 - dr^2), dt_c = -(dr.dv + sqrt(Delta))/dv^2, */
 /* collision iff Delta >= 0 and 0 <= dt_c <= dt.                            */
 /* ------------------------------------------------------------------------ */
-int or_collide_pair(const double x1[3], const double v1[3], double R1,
-                    const double x2[3], const double v2[3], double R2, double dt)
+/* Time of impact: returns 1 and *tc when Delta >= 0 and dv^2 != 0. */
+static int impact_time(const double x1[3], const double v1[3], double R1,
+                       const double x2[3], const double v2[3], double R2, double *tc)
 {
     double dx = x1[0] - x2[0], dy = x1[1] - x2[1], dz = x1[2] - x2[2];
     double ux = v1[0] - v2[0], uy = v1[1] - v2[1], uz = v1[2] - v2[2];
@@ -468,7 +473,15 @@ int or_collide_pair(const double x1[3], const double v1[3], double R1,
     double Rs = R1 + R2;
     double Delta = b * b + dv2 * (Rs * Rs - dr2);
     if (Delta < 0.0) return 0;
-    double tc = -(b + sqrt(Delta)) / dv2;
+    *tc = -(b + sqrt(Delta)) / dv2;
+    return 1;
+}
+
+int or_collide_pair(const double x1[3], const double v1[3], double R1,
+                    const double x2[3], const double v2[3], double R2, double dt)
+{
+    double tc;
+    if (!impact_time(x1, v1, R1, x2, v2, R2, &tc)) return 0;
     return tc >= 0.0 && tc <= dt;
 }
 
@@ -483,6 +496,87 @@ int64_t or_collide_brute(int64_t n, const double *pos, const double *vel, const 
                 found++;
             }
     return found;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Collision resolution (Sect. 5.1 and 5.2).  The two moonlets of a pair     */
+/* (1, 2) = (i, j), i < j, move in straight lines to the impact at dt_c (the */
+/* root of the predicate above), where, with dr = r1 - r2 and dv = v1 - v2   */
+/* taken at the impact,                                                      */
+/*   J = alpha (dr.dv) dr,  alpha = f m1 m2 / ((m1 + m2)(R1 + R2)^2),        */
+/*   v1' = v1 - J / m1,     v2' = v2 + J / m2                                 */
+/* (Eq. velocity_prediction; f = 2 is Eq. alpha_el, 1 <= f <= 2 Eq. alpha). */
+/* The rest of the step is travelled at v': the position the drift starts    */
+/* from becomes x + dt_c (v - v'), so that the drift x + dt v' lands on      */
+/* (x + dt_c v) + (dt - dt_c) v' up to rounding.                             */
+/* The paper does not say what happens to a moonlet found in several pairs   */
+/* of one step.  Reading: pairs are taken in increasing (dt_c, i, j) and a   */
+/* pair is resolved only if neither moonlet was resolved before it in the    */
+/* step, so a moonlet has at most one impact per step, its earliest.         */
+/* ------------------------------------------------------------------------ */
+typedef struct { double tc; int64_t i, j, k; } Impact;
+
+static int cmp_impact(const void *a, const void *b)
+{
+    const Impact *p = (const Impact *)a, *q = (const Impact *)b;
+    if (p->tc != q->tc) return p->tc < q->tc ? -1 : 1;
+    if (p->i != q->i) return p->i < q->i ? -1 : 1;
+    if (p->j != q->j) return p->j < q->j ? -1 : 1;
+    return 0;
+}
+
+static void resolve_pair(double *pos, double *vel, const double *mass, const double *rad, double f,
+                         int64_t i, int64_t j, double tc)
+{
+    double *x1 = pos + 3 * i, *x2 = pos + 3 * j, *v1 = vel + 3 * i, *v2 = vel + 3 * j;
+    double m1 = mass[i], m2 = mass[j];
+    double Rs = rad[i] + rad[j];
+    double dr[3], dv[3];
+    for (int k = 0; k < 3; k++) {
+        dr[k] = (x1[k] + tc * v1[k]) - (x2[k] + tc * v2[k]);
+        dv[k] = v1[k] - v2[k];
+    }
+    double alpha = ((f * m1) * m2) / ((m1 + m2) * (Rs * Rs));
+    double c = alpha * dot3(dr, dv);
+    for (int k = 0; k < 3; k++) {
+        double J = c * dr[k];
+        double w1 = v1[k] - J / m1, w2 = v2[k] + J / m2;
+        x1[k] = x1[k] + tc * (v1[k] - w1);
+        x2[k] = x2[k] + tc * (v2[k] - w2);
+        v1[k] = w1;
+        v2[k] = w2;
+    }
+}
+
+/* Resolves the colliding pairs (rows (i, j), i < j) of one step in place:  */
+/* velocities become v', positions the drift's starting points.  done[k]    */
+/* (nullable) tells whether pair k was resolved.  Returns how many were.    */
+int64_t or_resolve(int64_t n, double *pos, double *vel, const double *mass, const double *rad, double f,
+                   const int64_t *pairs, int64_t npairs, int64_t *done)
+{
+    Impact *im = (Impact *)malloc(sizeof(Impact) * (npairs > 0 ? npairs : 1));
+    unsigned char *used = (unsigned char *)calloc(n > 0 ? n : 1, 1);
+    int64_t m = 0, count = 0;
+    for (int64_t k = 0; k < npairs; k++) {
+        int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+        double tc;
+        if (done) done[k] = 0;
+        if (i < 0 || j >= n || i >= j) continue;
+        if (!impact_time(pos + 3 * i, vel + 3 * i, rad[i], pos + 3 * j, vel + 3 * j, rad[j], &tc)) continue;
+        im[m].tc = tc; im[m].i = i; im[m].j = j; im[m].k = k;
+        m++;
+    }
+    qsort(im, (size_t)m, sizeof(Impact), cmp_impact);
+    for (int64_t q = 0; q < m; q++) {
+        if (used[im[q].i] || used[im[q].j]) continue;
+        used[im[q].i] = used[im[q].j] = 1;
+        resolve_pair(pos, vel, mass, rad, f, im[q].i, im[q].j, im[q].tc);
+        if (done) done[im[q].k] = 1;
+        count++;
+    }
+    free(im);
+    free(used);
+    return count;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1036,16 +1130,19 @@ int64_t or_tree_export(const or_params *P, int64_t n, const double *pos, const d
  * acc0: acceleration at the input positions (mutual + external), or NULL to
  * compute it.  Each step: v += dt/2 a; search collisions on (x, v); x += dt v;
  * a = falcON + external at the new x and time t + dt; v += dt/2 a.
- * Collision pairs of step k are stored with a leading step index:
- * rows (k, i, j).  The final acceleration is left in acc_out. */
+ * With P->resolve_f > 0 the pairs are resolved (or_resolve) between the
+ * search and the drift.  Collision pairs of step k are stored with a leading
+ * step index: rows (k, i, j).  The final acceleration is left in acc_out;
+ * *resolved (nullable) receives the number of resolved impacts, or -1 when
+ * a step found more pairs than cap (then nothing more is resolved). */
 int64_t or_kdk(const or_params *P0, int64_t n, double *pos, double *vel, const double *mass,
                const double *rad, double dt, int nsteps, const double *acc0, double *acc_out,
-               int64_t *pairs, int64_t cap)
+               int64_t *pairs, int64_t cap, int64_t *resolved)
 {
     or_params P = *P0;
     double *a = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
     int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * 2 * (cap > 0 ? cap : 1));
-    int64_t total = 0;
+    int64_t total = 0, nres = 0;
     if (acc0) memcpy(a, acc0, sizeof(double) * 3 * n);
     else {
         or_falcon_accel(&P, n, pos, mass, a, NULL);
@@ -1062,6 +1159,10 @@ int64_t or_kdk(const or_params *P0, int64_t n, double *pos, double *vel, const d
             }
             total++;
         }
+        if (P.resolve_f > 0.0 && nres >= 0) {
+            if (found > cap) nres = -1;
+            else nres += or_resolve(n, pos, vel, mass, rad, P.resolve_f, tmp, found, NULL);
+        }
         for (int64_t i = 0; i < 3 * n; i++) pos[i] = pos[i] + dt * vel[i];
         P.time = P.time + dt;
         or_falcon_accel(&P, n, pos, mass, a, NULL);
@@ -1069,6 +1170,7 @@ int64_t or_kdk(const or_params *P0, int64_t n, double *pos, double *vel, const d
         for (int64_t i = 0; i < 3 * n; i++) vel[i] = vel[i] + h * a[i];
     }
     if (acc_out) memcpy(acc_out, a, sizeof(double) * 3 * n);
+    if (resolved) *resolved = nres;
     free(a);
     free(tmp);
     return total;
