@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--resolve-f", type=float, default=0.0,
+                    help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="disk", choices=["disk", "ensemble", "serving"],
                     help="disk: one disk per GPU (default); ensemble: 64 disks of mixed size per GPU in one batch; "
@@ -84,12 +86,14 @@ def replica_throughput(units_per_rank, steps, world, seconds):
 
 
 def workload_config(a):
+    res = f", collisions resolved with f={a.resolve_f}" if a.resolve_f else ""
     return {"workload": f"1 disk x {a.n} moonlets per GPU (seed {a.seed}+rank), falcON p={a.p} theta_min={a.theta}, "
-                        f"SBAB1 step dt={a.dt} with tree collision search, {a.precision} precision",
+                        f"SBAB1 step dt={a.dt} with tree collision search{res}, {a.precision} precision",
             "n_per_gpu": a.n, "p": a.p, "theta_min": a.theta, "dt": a.dt, "leaf_size": 64 if a.p >= 6 else 32,
             "gravity_thresholds": [256, 256, 512] if a.p >= 6 else [64, 8, 64], "collision_thresholds": [12, 0, 16],
             "precision": a.precision, "l2": "flushed by a 256 MiB device write before every timed step",
-            "parallelism": "replicas (one independent disk per GPU)"}
+            "parallelism": "replicas (one independent disk per GPU)",
+            **({"resolve_f": a.resolve_f} if a.resolve_f else {})}
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -171,6 +175,7 @@ def run_gpu(a):
     cfg.leaf_size = cfgd["leaf_size"]
     cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = cfgd["gravity_thresholds"]
     cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = cfgd["collision_thresholds"]
+    cfg.resolve_f = a.resolve_f
     ctx = ncorp.ncorp_init(cfg, a.n, local, stream.cuda_stream)
     pos = torch.tensor(d["pos"], device="cuda")
     vel = torch.tensor(d["vel"], device="cuda")
@@ -302,7 +307,7 @@ def oracle_params(cfgd, a):
     import oracle
     return oracle.params(p=a.p, theta=a.theta, leaf_size=cfgd["leaf_size"],
                          gravity_thresholds=tuple(cfgd["gravity_thresholds"]),
-                         collision_thresholds=tuple(cfgd["collision_thresholds"]))
+                         collision_thresholds=tuple(cfgd["collision_thresholds"]), resolve_f=a.resolve_f)
 
 
 def time_oracle_steps(a, cfgd, d, nsteps):

@@ -72,10 +72,19 @@ typedef struct {
                                  moonlet's acceleration, k = the frame's z axis (the body's rotation
                                  axis); 0 disables.  For a fluid body rotating at Omega,
                                  J2 = Omega^2 / (2 G M_c / R_c^3). */
+    double resolve_f;         /* collision resolution in ncorp_step (Sect. 5.1, 5.2): 0 = colliding pairs are
+                                 only reported; 1 <= f <= 2 = each is resolved at its impact time by the
+                                 impulse J = alpha (dr.dv) dr, alpha = f m1 m2 / ((m1 + m2)(R1 + R2)^2)
+                                 (f = 2 elastic, f = 1 the most inelastic), and the moonlets travel the rest
+                                 of the step at their new velocities.  A moonlet takes at most one impact
+                                 per step: pairs are resolved in increasing (impact time, i, j) and a pair
+                                 with a moonlet already resolved in the step is reported but not resolved.
+                                 The search then runs before the drift instead of beside it.  Other values:
+                                 NCORP_EINVAL at ncorp_init. */
 } ncorp_config;
 
 /* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
- * NCORP_MIXED, collisions on, no star, no bulge (J2 = 0). */
+ * NCORP_MIXED, collisions on (reported, not resolved), no star, no bulge (J2 = 0). */
 void ncorp_config_default(ncorp_config *cfg);
 
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
@@ -165,7 +174,8 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_GRAPH       16   /* 1 if the last ncorp_step ran as a replayed (or just captured) CUDA graph */
 #define NCORP_STAT_SORT_PATH   17   /* key sort of the last tree: 1 nearly-sorted merge (steps), 0 radix sort,
                                        -1 radix sort after the merge found the kept keys out of order */
-#define NCORP_NSTATS           18
+#define NCORP_STAT_RESOLVED    18   /* impacts resolved by the last ncorp_step (resolve_f > 0) */
+#define NCORP_NSTATS           19
 
 /* Writes min(n_stats, NCORP_NSTATS) counters of the last call (slots above)
  * to host memory stats[].  NCORP_EINVAL if ctx or stats is NULL. */

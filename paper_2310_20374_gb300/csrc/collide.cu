@@ -1,5 +1,6 @@
 // collide.cu -- the pairwise collision test of Sect. 3.1 over the direct lists
-// of the collision walk, and the sorting of the colliding pairs.
+// of the collision walk, the resolution of the colliding pairs (Sect. 5.1,
+// 5.2) and the sorting of the pairs for output.
 //
 // Straight-line trajectories over the step: with dr = r1 - r2, dv = v1 - v2,
 //   Delta = (dr.dv)^2 + dv^2 ((R1 + R2)^2 - dr^2),
@@ -12,9 +13,10 @@
 
 namespace ncorp {
 
-__device__ __forceinline__ bool collide_test(double x1, double y1, double z1, double u1, double v1, double w1,
-                                             double R1, double x2, double y2, double z2, double u2, double v2,
-                                             double w2, double R2, double dt) {
+// Impact time of the straight-line trajectories: false when dv = 0 or Delta < 0.
+__device__ __forceinline__ bool impact_time(double x1, double y1, double z1, double u1, double v1, double w1,
+                                            double R1, double x2, double y2, double z2, double u2, double v2,
+                                            double w2, double R2, double &tc) {
     const double dx = dsub(x1, x2), dy = dsub(y1, y2), dz = dsub(z1, z2);
     const double ux = dsub(u1, u2), uy = dsub(v1, v2), uz = dsub(w1, w2);
     const double b = dadd(dadd(dmul(dx, ux), dmul(dy, uy)), dmul(dz, uz));
@@ -24,7 +26,15 @@ __device__ __forceinline__ bool collide_test(double x1, double y1, double z1, do
     const double Rs = dadd(R1, R2);
     const double Delta = dadd(dmul(b, b), dmul(dv2, dsub(dmul(Rs, Rs), dr2)));
     if (Delta < 0.0) return false;
-    const double tc = ddiv(-dadd(b, dsqrt(Delta)), dv2);
+    tc = ddiv(-dadd(b, dsqrt(Delta)), dv2);
+    return true;
+}
+
+__device__ __forceinline__ bool collide_test(double x1, double y1, double z1, double u1, double v1, double w1,
+                                             double R1, double x2, double y2, double z2, double u2, double v2,
+                                             double w2, double R2, double dt) {
+    double tc;
+    if (!impact_time(x1, y1, z1, u1, v1, w1, R1, x2, y2, z2, u2, v2, w2, R2, tc)) return false;
     return tc >= 0.0 && tc <= dt;
 }
 
@@ -38,6 +48,7 @@ struct CollideArgs {
     const int *perm;
     double dt;
     uint64_t *pairs;
+    int2 *where;               // nullable: the pair's positions in this order (lower caller index first)
     int cap, self_cap, p2p_cap;
     Ctrl *ctl;
 };
@@ -51,9 +62,10 @@ __device__ __forceinline__ void test_and_emit(const CollideArgs &A, int u, int v
     if (collide_test(A.x[a], A.y[a], A.z[a], A.vx[a], A.vy[a], A.vz[a], A.R[a], A.x[b], A.y[b], A.z[b], A.vx[b],
                      A.vy[b], A.vz[b], A.R[b], A.dt)) {
         const int slot = atomicAdd(&A.ctl->n_found, 1);
-        if (slot < A.cap)
+        if (slot < A.cap) {
             A.pairs[slot] = (static_cast<unsigned long long>(A.perm[a]) << 32) | static_cast<unsigned>(A.perm[b]);
-        else
+            if (A.where) A.where[slot] = make_int2(a, b);
+        } else
             atomicOr(&A.ctl->err, ERR_PAIRS);
     }
 }
@@ -144,6 +156,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.perm = P.perm;
     A.dt = dt;
     A.pairs = c->pairs;
+    A.where = c->cfg.resolve_f > 0.0 ? c->pair_where : nullptr;
     A.cap = c->pair_cap;
     A.self_cap = c->wl.self_cap;
     A.p2p_cap = c->wl.p2p_cap;
@@ -152,6 +165,186 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     // room on every SM while it runs
     k_collide<<<2 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Collision resolution (Sect. 5.1 elastic, 5.2 inelastic).  For a pair (1, 2)
+// in increasing caller index, both moonlets travel in straight lines to the
+// impact at t_c, where with dr = r1 - r2 and dv = v1 - v2 taken there
+//   J = alpha (dr.dv) dr,  alpha = f m1 m2 / ((m1 + m2)(R1 + R2)^2),
+//   v1' = v1 - J / m1,     v2' = v2 + J / m2,
+// and the rest of the step is travelled at v': the drift starts from
+// x + t_c (v - v'), i.e. x_new = (x + t_c (v - v')) + dt v'.  Every operation
+// is an exactly rounded FP64 one in a fixed order, so resolved states are
+// reproducible bit for bit.
+//
+// A moonlet takes at most one impact per step: pairs are taken in increasing
+// (t_c, i, j) and a pair is resolved only if neither moonlet was resolved by
+// an earlier pair.  That sequential greedy matching is computed in rounds: in
+// each, every undecided pair whose key is the least of the undecided pairs at
+// both its moonlets is resolved (all earlier pairs there were skipped), then
+// every undecided pair at a moonlet just taken is skipped.  The least
+// undecided pair always wins, so the rounds end, usually after one or two.
+// One block does it all: the pairs of a disk's step are few (ones to tens),
+// and a block needs no grid-wide barrier between the rounds.
+// ---------------------------------------------------------------------------
+constexpr int RES_THREADS = 512;
+enum { RES_UNDECIDED = 0, RES_RESOLVED = 1, RES_SKIPPED = 2 };
+
+struct ResolveArgs {
+    const uint64_t *pairs;     // packed caller indices (i << 32 | j), i < j
+    const int2 *where;         // their positions in the search tree's order
+    const double *x, *y, *z;   // positions at the start of the drift
+    const double *m, *R;
+    double *vx, *vy, *vz;      // half-kicked velocities in, resolved ones out
+    double *ox, *oy, *oz;      // drifted positions, rewritten for resolved moonlets
+    double f, dt;
+    int cap;
+    double *tc;
+    int *state;
+    unsigned long long *node_tc, *node_ij;
+    int *owner;
+    Ctrl *ctl;                 // the search's control block: n_found in, n_resolved out
+    Ctrl *next;                // the new tree's control block: its box is emptied when a moonlet moved
+};
+
+__device__ __forceinline__ unsigned long long tc_key(double tc) {
+    return static_cast<unsigned long long>(__double_as_longlong(tc == 0.0 ? 0.0 : tc));   // -0 sorts as +0
+}
+
+__global__ void __launch_bounds__(RES_THREADS) k_resolve(ResolveArgs A) {
+    __shared__ int s_count;
+    const int found = A.ctl->n_found;
+    // an overflowed search (pairs missing) is rerun by the host with more room: resolve nothing now
+    if (found == 0 || found > A.cap || aborted(A.ctl)) {
+        if (threadIdx.x == 0) A.ctl->n_resolved = 0;
+        return;
+    }
+    if (threadIdx.x == 0) s_count = 0;
+    for (int k = threadIdx.x; k < found; k += blockDim.x) {
+        const int2 w = A.where[k];
+        const int a = w.x, b = w.y;
+        double tc = 0.0;
+        const bool ok = impact_time(A.x[a], A.y[a], A.z[a], A.vx[a], A.vy[a], A.vz[a], A.R[a], A.x[b], A.y[b],
+                                    A.z[b], A.vx[b], A.vy[b], A.vz[b], A.R[b], tc);
+        A.tc[k] = tc;
+        A.state[k] = ok ? RES_UNDECIDED : RES_SKIPPED;
+        A.owner[a] = 0;
+        A.owner[b] = 0;
+    }
+    __syncthreads();
+    for (int round = 0; round <= found; round++) {
+        for (int k = threadIdx.x; k < found; k += blockDim.x) {
+            if (A.state[k] != RES_UNDECIDED) continue;
+            const int2 w = A.where[k];
+            A.node_tc[w.x] = A.node_tc[w.y] = ~0ull;
+            A.node_ij[w.x] = A.node_ij[w.y] = ~0ull;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < found; k += blockDim.x) {
+            if (A.state[k] != RES_UNDECIDED) continue;
+            const int2 w = A.where[k];
+            const unsigned long long t = tc_key(A.tc[k]);
+            atomicMin(&A.node_tc[w.x], t);
+            atomicMin(&A.node_tc[w.y], t);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < found; k += blockDim.x) {
+            if (A.state[k] != RES_UNDECIDED) continue;
+            const int2 w = A.where[k];
+            const unsigned long long t = tc_key(A.tc[k]), ij = A.pairs[k];
+            if (A.node_tc[w.x] == t) atomicMin(&A.node_ij[w.x], ij);
+            if (A.node_tc[w.y] == t) atomicMin(&A.node_ij[w.y], ij);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < found; k += blockDim.x) {
+            if (A.state[k] != RES_UNDECIDED) continue;
+            const int2 w = A.where[k];
+            const unsigned long long t = tc_key(A.tc[k]), ij = A.pairs[k];
+            if (A.node_tc[w.x] == t && A.node_ij[w.x] == ij && A.node_tc[w.y] == t && A.node_ij[w.y] == ij) {
+                // (a duplicated pair would tie with itself: the first copy claims the moonlets)
+                if (atomicCAS(&A.owner[w.x], 0, k + 1) == 0) {
+                    A.owner[w.y] = k + 1;
+                    A.state[k] = RES_RESOLVED;
+                } else {
+                    A.state[k] = RES_SKIPPED;
+                }
+            }
+        }
+        __syncthreads();
+        int left = 0;
+        for (int k = threadIdx.x; k < found; k += blockDim.x) {
+            if (A.state[k] != RES_UNDECIDED) continue;
+            const int2 w = A.where[k];
+            if (A.owner[w.x] || A.owner[w.y]) A.state[k] = RES_SKIPPED;
+            else left = 1;
+        }
+        if (!__syncthreads_or(left)) break;
+    }
+    for (int k = threadIdx.x; k < found; k += blockDim.x) {
+        if (A.state[k] != RES_RESOLVED) continue;
+        const int2 w = A.where[k];
+        const int a = w.x, b = w.y;
+        const double tc = A.tc[k];
+        const double m1 = A.m[a], m2 = A.m[b];
+        const double Rs = dadd(A.R[a], A.R[b]);
+        const double x1[3] = {A.x[a], A.y[a], A.z[a]}, x2[3] = {A.x[b], A.y[b], A.z[b]};
+        const double v1[3] = {A.vx[a], A.vy[a], A.vz[a]}, v2[3] = {A.vx[b], A.vy[b], A.vz[b]};
+        double dr[3], dv[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            dr[d] = dsub(dadd(x1[d], dmul(tc, v1[d])), dadd(x2[d], dmul(tc, v2[d])));
+            dv[d] = dsub(v1[d], v2[d]);
+        }
+        const double alpha = ddiv(dmul(dmul(A.f, m1), m2), dmul(dadd(m1, m2), dmul(Rs, Rs)));
+        const double cj = dmul(alpha, dadd(dadd(dmul(dr[0], dv[0]), dmul(dr[1], dv[1])), dmul(dr[2], dv[2])));
+        double w1[3], w2[3], o1[3], o2[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double J = dmul(cj, dr[d]);
+            w1[d] = dsub(v1[d], ddiv(J, m1));
+            w2[d] = dadd(v2[d], ddiv(J, m2));
+            o1[d] = dadd(dadd(x1[d], dmul(tc, dsub(v1[d], w1[d]))), dmul(A.dt, w1[d]));
+            o2[d] = dadd(dadd(x2[d], dmul(tc, dsub(v2[d], w2[d]))), dmul(A.dt, w2[d]));
+        }
+        A.vx[a] = w1[0]; A.vy[a] = w1[1]; A.vz[a] = w1[2];
+        A.vx[b] = w2[0]; A.vy[b] = w2[1]; A.vz[b] = w2[2];
+        A.ox[a] = o1[0]; A.oy[a] = o1[1]; A.oz[a] = o1[2];
+        A.ox[b] = o2[0]; A.oy[b] = o2[1]; A.oz[b] = o2[2];
+        atomicAdd(&s_count, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        A.ctl->n_resolved = s_count;
+        if (s_count > 0)   // moved moonlets: the drifted positions' box is folded again from scratch
+            for (int d = 0; d < 3; d++) {
+                A.next->bbox[d] = ~0ull;
+                A.next->bbox[3 + d] = 0ull;
+            }
+    }
+}
+
+// S: the searched state (positions at the start of the drift, masses, radii,
+// in the search tree's order); D: the half-kicked velocities and drifted
+// positions in the same order.  Enqueued after the search and before the
+// keys of the drifted positions; the new tree's box is refolded (all blocks
+// of that launch return at once when nothing was resolved).
+void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, double dt) {
+    ResolveArgs A;
+    A.pairs = c->pairs; A.where = c->pair_where;
+    A.x = S.x; A.y = S.y; A.z = S.z; A.m = S.m; A.R = S.R;
+    A.vx = D.vx; A.vy = D.vy; A.vz = D.vz;
+    A.ox = D.x; A.oy = D.y; A.oz = D.z;
+    A.f = c->cfg.resolve_f;
+    A.dt = dt;
+    A.cap = c->pair_cap;
+    A.tc = c->res_tc; A.state = c->res_state;
+    A.node_tc = c->node_tc; A.node_ij = c->node_ij; A.owner = c->node_owner;
+    A.ctl = c->ctl;
+    A.next = c->alt.ctl;
+    k_resolve<<<1, RES_THREADS, 0, c->stream>>>(A); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    launch_bbox_gated(c, D.x, D.y, D.z, n, c->alt.ctl, &c->ctl->n_resolved);
 }
 
 __global__ void k_unpack_pairs(const uint64_t *__restrict__ packed, int64_t *__restrict__ out, int count) {

@@ -96,6 +96,7 @@ struct Ctrl {
     int n_p2p;             // leaf-leaf direct pairs
     int n_self;            // leaves interacting with themselves
     int n_found;           // colliding pairs found
+    int n_resolved;        // colliding pairs resolved (collision resolution on)
     int walk_iters;
     int n_items;           // multipole work items (cell, chunk)
     int resort_ok;         // the last key sort took the nearly-sorted path (1) or the radix sort

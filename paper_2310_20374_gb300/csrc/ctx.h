@@ -142,6 +142,12 @@ struct ncorp_ctx {
     uint64_t *pairs = nullptr, *pairs_alt = nullptr;
     uint32_t *pair_idx = nullptr, *pair_idx_alt = nullptr;
     int64_t *pairs_out = nullptr;
+    // collision resolution (allocated when resolve_f > 0)
+    int2 *pair_where = nullptr;      // per pair: both moonlets' positions in the search tree's order
+    double *res_tc = nullptr;        // per pair: impact time
+    int *res_state = nullptr;        // per pair: undecided, resolved or skipped
+    unsigned long long *node_tc = nullptr, *node_ij = nullptr;   // per moonlet: minima of a matching round
+    int *node_owner = nullptr;       // per moonlet: 1 + the resolved pair holding it, else 0
 
     ncorp::Ctrl *ctl = nullptr;      // device
     ncorp::Ctrl *ctl_h = nullptr;    // pinned host mirror
@@ -214,6 +220,10 @@ void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G,
                 double kick_h = 0.0);
 
 // ---- collide.cu ----
+// the box of (x, y, z) folded into ctl when *gate != 0 (decided on the device)
+void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, Ctrl *ctl,
+                       const int *gate);
+void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, double dt);
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
                     double dt);
 void launch_sort_pairs(ncorp_ctx *c, int count);

@@ -93,6 +93,11 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
     }
     dalloc(c->stage, 3 * cap);
     dalloc(c->stage2, 3 * cap);
+    if (c->cfg.resolve_f > 0.0) {
+        dalloc(c->node_tc, cap);
+        dalloc(c->node_ij, cap);
+        dalloc(c->node_owner, cap);
+    }
     c->n_cap = cap;
     c->have_state = false;
     c->tree_valid = false;
@@ -159,6 +164,11 @@ void alloc_pairs(ncorp_ctx *c, int cap) {
     dalloc(c->pair_idx, cap);
     dalloc(c->pair_idx_alt, cap);
     dalloc(c->pairs_out, 2 * static_cast<size_t>(cap));
+    if (c->cfg.resolve_f > 0.0) {
+        dalloc(c->pair_where, cap);
+        dalloc(c->res_tc, cap);
+        dalloc(c->res_state, cap);
+    }
     c->pair_cap = cap;
 }
 
@@ -330,6 +340,7 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     if (fold) *fold |= ctl->err;
     ctl->err = 0;
     ctl->n_found = 0;
+    ctl->n_resolved = 0;
     ctl->n_tests = 0;
     ctl->bar_count = 0;
     ctl->resort_ok = 0;
@@ -496,7 +507,10 @@ constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision
 // overlap, the collision search runs on the context's side stream while the
 // main stream drifts, sorts, builds and walks the new tree (the two touch
 // disjoint buffers); its cooperative grids are kept small enough that both
-// streams' cooperative kernels fit on the device together.  On return the
+// streams' cooperative kernels fit on the device together.  With collision
+// resolution the search runs on the main stream, followed by the resolution
+// (which rewrites the drift of the moonlets it resolves and refolds the new
+// box), before the keys of the drifted positions.  On return the
 // tree sets have traded places (the current one describes the new positions)
 // and the new state is in Cset (not yet swapped with A); nothing is copied to
 // the caller and nothing waits: the caller reads the status.
@@ -517,7 +531,9 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         K.ctl = c->alt.ctl;
         launch_kick_drift(c, K);
     }
-    const bool side = overlap && c->cfg.collisions;
+    // resolution changes the drift of the moonlets it resolves, so the search then runs before the keys
+    const bool resolve = c->cfg.collisions && c->cfg.resolve_f > 0.0;
+    const bool side = overlap && c->cfg.collisions && !resolve;
     if (c->cfg.collisions) {
         if (side) {
             cudaStream_t main = c->stream;
@@ -538,6 +554,10 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->coop_max = cap;
         } else {
             collisions(c, A, B.vx, B.vy, B.vz, dt);
+            if (resolve) {
+                Stage st(c, NCORP_STAGE_COLLIDE);
+                launch_resolve(c, A, B, n, dt);
+            }
         }
     }
     swap_sets(c);
@@ -553,6 +573,7 @@ void record_stats(ncorp_ctx *c, bool grav, const Ctrl *col = nullptr) {
     c->stats[NCORP_STAT_LAUNCHES] = c->launches;
     c->stats[NCORP_STAT_GRAPH] = c->graph_used ? 1 : 0;
     c->stats[NCORP_STAT_SORT_PATH] = h.resort_ok;
+    c->stats[NCORP_STAT_RESOLVED] = c->cfg.collisions ? hc.n_resolved : 0;
     c->stats[NCORP_STAT_CELLS] = h.n_cells;
     c->stats[NCORP_STAT_LEAVES] = h.n_leaves;
     c->stats[NCORP_STAT_DEPTH] = h.max_level;
@@ -722,6 +743,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
     if (!out || !cfg || n_max < 1) return NCORP_EINVAL;
     if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
     if (!(cfg->G > 0.0) || !(cfg->central_mass >= 0.0) || cfg->leaf_size < 0) return NCORP_EINVAL;
+    if (!(cfg->resolve_f == 0.0 || (cfg->resolve_f >= 1.0 && cfg->resolve_f <= 2.0))) return NCORP_EINVAL;
     *out = nullptr;
     ncorp_ctx *c = new (std::nothrow) ncorp_ctx();
     if (!c) return NCORP_ENOMEM;
@@ -1176,6 +1198,8 @@ void ncorp_free(ncorp_ctx *c) {
         swap_sets(c);
     }
     dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
+    dfree(c->pair_where); dfree(c->res_tc); dfree(c->res_state);
+    dfree(c->node_tc); dfree(c->node_ij); dfree(c->node_owner);
     dfree(c->err_acc);
     if (c->err_acc_h) cudaFreeHost(c->err_acc_h);
     if (c->side) {
@@ -1318,6 +1342,7 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
     if (!out || !cfg) return NCORP_EINVAL;
     *out = nullptr;
     if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
+    if (!(cfg->resolve_f == 0.0 || (cfg->resolve_f >= 1.0 && cfg->resolve_f <= 2.0))) return NCORP_EINVAL;
     ncorp_batch *b = new (std::nothrow) ncorp_batch();
     if (!b) return NCORP_ENOMEM;
     b->cfg = *cfg;

@@ -24,11 +24,14 @@ namespace ncorp {
 // minima and maxima of the order-preserving integer images of the
 // coordinates (integer min/max, no FP64 instruction), the block reduces them
 // in shared memory and adds one atomic per bound.  A coordinate whose
-// exponent field is all ones (infinite or NaN) sets ERR_NONFINITE.
+// exponent field is all ones (infinite or NaN) sets ERR_NONFINITE.  With a
+// gate, the launch does nothing while *gate is 0.
 __global__ void __launch_bounds__(256) k_bbox(const double *__restrict__ x, const double *__restrict__ y,
-                                              const double *__restrict__ z, int n, Ctrl *ctl) {
+                                              const double *__restrict__ z, int n, Ctrl *ctl,
+                                              const int *gate = nullptr) {
     __shared__ unsigned long long s_b[6][8];
     __shared__ int s_bad;
+    if (gate && *gate == 0) return;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
     if (threadIdx.x == 0) s_bad = 0;
@@ -199,6 +202,12 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
         NCORP_CUDA_CHECK(cudaGetLastError());
     }
     k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, Ctrl *ctl,
+                       const int *gate) {
+    k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, ctl, gate); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

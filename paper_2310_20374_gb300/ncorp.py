@@ -19,7 +19,7 @@ NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEO
 NCORP_FP64, NCORP_MIXED = 0, 1
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
               "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters",
-              "graph", "sort_path"]
+              "graph", "sort_path", "resolved"]
 STAGE_NAMES = ["sort", "build", "climb", "walk", "m2l", "descend", "eval", "collide", "kdk", "near"]
 HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
 
@@ -36,7 +36,7 @@ class ncorp_config(C.Structure):
                 ("c_cs", C.c_int), ("c_cc_pre", C.c_int), ("c_cc_post", C.c_int),
                 ("precision", C.c_int), ("collisions", C.c_int),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
-                ("t0", C.c_double), ("central_J2", C.c_double)]
+                ("t0", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double)]
 
 
 _lib = None
