@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("c_cs", C.c_int64), ("c_cc_pre", C.c_int64), ("c_cc_post", C.c_int64),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
                 ("time", C.c_double), ("m2m_direct", C.c_int), ("brute_collisions", C.c_int),
-                ("central_radius", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double)]
+                ("central_radius", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double),
+                ("n_cb_pre", C.c_int64), ("n_cb_post", C.c_int64)]
 
 
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
@@ -94,6 +95,9 @@ def lib():
             L.or_resolve.restype = i64
             L.or_falcon_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
             L.or_falcon_accel.restype = C.c_int
+            L.or_standard_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
+            L.or_standard_accel.restype = C.c_int
+            L.or_m2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
             L.or_collide_tree.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
             L.or_collide_tree.restype = i64
             L.or_tree_export.argtypes = [PP, i64, _dp, _opt(_dp), _opt(_dp), _opt(_dp), dbl,
@@ -117,9 +121,10 @@ def default_gravity_thresholds(p: int):
 
 def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresholds=None,
            collision_thresholds=(12, 0, 16), star=None, time=0.0, m2m_direct=False,
-           brute_collisions=False, bulge=None, resolve_f=0.0) -> Params:
+           brute_collisions=False, bulge=None, resolve_f=0.0, standard_thresholds=(6, 16)) -> Params:
     """bulge: (R_c, J2) of the central body's equatorial bulge (App. B.2), None = no bulge.
-    resolve_f: 0 = colliding pairs are only reported; 1 <= f <= 2 = kdk() resolves them (Sect. 5)."""
+    resolve_f: 0 = colliding pairs are only reported; 1 <= f <= 2 = kdk() resolves them (Sect. 5).
+    standard_thresholds: (N_cb,pre, N_cb,post) of Algorithm StandardTree (Sect. 3.4.4; 6 and 16 in Sect. 4.2)."""
     g = gravity_thresholds if gravity_thresholds is not None else default_gravity_thresholds(p)
     P = Params()
     P.G, P.central_mass, P.p, P.theta_min, P.leaf_size = G, central_mass, int(p), theta, int(leaf_size)
@@ -133,6 +138,7 @@ def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresh
     if bulge:
         P.central_radius, P.central_J2 = bulge
     P.resolve_f = float(resolve_f)
+    P.n_cb_pre, P.n_cb_post = (int(v) for v in standard_thresholds)
     return P
 
 
@@ -236,6 +242,24 @@ def falcon_accel(P: Params, pos, mass):
     st = np.zeros(16, dtype=np.int64)
     lib().or_falcon_accel(C.byref(P), n, pos.reshape(-1), _f64(mass), out.reshape(-1), st)
     return out[:n], dict(zip(STAT_NAMES, (int(v) for v in st)))
+
+
+def standard_accel(P: Params, pos, mass):
+    """Mutual acceleration by the standard tree code (Algorithm StandardTree), and its counters
+    (m2l = moonlet-cell expansions, p2p_pairs = brute-force moonlet-cell interactions)."""
+    pos = _f64(pos)
+    n = len(pos)
+    out = np.zeros((max(n, 1), 3))
+    st = np.zeros(16, dtype=np.int64)
+    lib().or_standard_accel(C.byref(P), n, pos.reshape(-1), _f64(mass), out.reshape(-1), st)
+    return out[:n], dict(zip(STAT_NAMES, (int(v) for v in st)))
+
+
+def m2p(p, x, sB, MB):
+    """C^(1) at x of the expansion MB (packed full tensors, orders 0..p-1) about sB."""
+    out = np.zeros(3)
+    lib().or_m2p(int(p), _f64(x), _f64(sB), _f64(MB), out)
+    return out
 
 
 # ---- collisions -------------------------------------------------------------------

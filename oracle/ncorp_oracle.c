@@ -25,6 +25,8 @@
  *     (Eq. phi_expanded and the A<->B relation of Sect. 3.4.3), L2L/L2P
  *     (Eq. shifting) with full 3^n tensors (no symmetric compression)  pinned
  *   - the dual tree walk (Algorithm TreeWalk, Sect. 3.4.5)           pinned
+ *   - the standard tree code (Algorithm StandardTree, Sect. 3.4.4)
+ *     with M2P (the m = 1 term of Eq. phi_expanded at a point)        pinned
  *   - the collision predicate (Sect. 3.1), brute force and tree-based  pinned
  *   - the SBAB1 kick-drift-kick step with merged kicks (Sect. 4.1)    pinned
  *   - elastic and inelastic collision resolution (Sect. 5.1, 5.2)     pinned
@@ -60,6 +62,7 @@ typedef struct {
     int brute_collisions;   /* KDK: 1 = brute force pairs, 0 = tree */
     double central_radius, central_J2;   /* App. B.2 equatorial bulge; J2 = 0 disables */
     double resolve_f;       /* KDK: 0 = pairs reported only; 1..2 = resolved with this f (Sect. 5) */
+    int64_t n_cb_pre, n_cb_post;         /* StandardTree thresholds (Sect. 3.4.4) */
 } or_params;
 
 /* statistics, int64 slots */
@@ -388,6 +391,20 @@ void or_l2p(int p, const double *C, const double s[3], const double x[3], double
     acc[0] += out[0];
     acc[1] += out[1];
     acc[2] += out[2];
+}
+
+/* ---- M2P: the field C^(1) of cell B's expansion at the point x, i.e. the
+ * m = 1 term of Eq. phi_expanded for a target reduced to the point x:
+ *   C^(1)(x) += sum_{n=0}^{p-1} (-1)^n/n! D^(n+1)(x - s_B) . M_B^(n). */
+void or_m2p(int p, const double x[3], const double sB[3], const double *MB, double acc[3])
+{
+    double R[3] = {x[0] - sB[0], x[1] - sB[1], x[2] - sB[2]};
+    static double D[729];
+    for (int n = 0; n <= p - 1; n++) {
+        if (n == 1) continue;
+        or_dtensor(n + 1, R, D);
+        contract(D, 1, n, MB + OFF(n), acc, (n & 1) ? -INV_FACT[n] : INV_FACT[n]);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -959,6 +976,49 @@ static void tree_walk(Tree *T, Node *A, Node *B, int gravity)
     }
 }
 
+/* ---- Algorithm StandardTree (Sect. 3.4.4), gravity, for moonlet a and cell
+ * B: brute force when B holds fewer than N_cb,pre moonlets; the expansion of
+ * B at a (M2P) when a is well separated from B; brute force when B holds
+ * fewer than N_cb,post moonlets or is a leaf; else the children of B in
+ * turn.  A moonlet is a point (r_crit = 0), so "well separated" reads
+ * r_crit,B^2 <= |x_a - s_B|^2, in FP64 in a fixed order; a moonlet at the
+ * centre itself (a one-moonlet cell, r_crit = 0, seen from its own moonlet)
+ * is not, since the expansion is singular there.  Brute force adds the pull
+ * of every moonlet of B on a alone (coincident moonlets, a itself included,
+ * are skipped). */
+static void direct_one(Tree *T, int64_t a, Node *B)
+{
+    const double *xa = T->pos + 3 * a;
+    T->st[ST_P2P_PAIRS]++;
+    for (int64_t v = 0; v < B->n; v++) {
+        int64_t j = T->ord[B->first + v];
+        const double *xj = T->pos + 3 * j;
+        double d[3] = {xa[0] - xj[0], xa[1] - xj[1], xa[2] - xj[2]};
+        double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        T->st[ST_P2P_INTER]++;
+        if (r2 == 0.0) continue;
+        double r = sqrt(r2);
+        double f = T->P->G * T->mass[j] * (1.0 / (r2 * r));
+        for (int k = 0; k < 3; k++) T->acc[3 * a + k] -= f * d[k];
+    }
+}
+
+static void standard_tree(Tree *T, int64_t a, Node *B)
+{
+    const or_params *P = T->P;
+    if (B->n < P->n_cb_pre) { direct_one(T, a, B); return; }
+    const double *xa = T->pos + 3 * a;
+    double d[3] = {xa[0] - B->s[0], xa[1] - B->s[1], xa[2] - B->s[2]};
+    double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    if (d2 > 0.0 && B->rcrit * B->rcrit <= d2) {
+        T->st[ST_M2L]++;
+        or_m2p(P->p, xa, B->s, B->Mt, T->acc + 3 * a);
+        return;
+    }
+    if (B->n < P->n_cb_post || B->nchild == 0) { direct_one(T, a, B); return; }
+    for (int c = 0; c < B->nchild; c++) standard_tree(T, a, B->child[c]);
+}
+
 /* ---- tree descent: L2L from the root, L2P at the leaves (Eq. shifting) */
 static void descend(Tree *T, Node *x)
 {
@@ -1013,6 +1073,28 @@ int or_falcon_accel(const or_params *P, int64_t n, const double *pos, const doub
     finish_gravity(&T);
     tree_walk(&T, T.rootn, T.rootn, 1);
     descend(&T, T.rootn);
+    tree_stats(&T);
+    if (stats) memcpy(stats, T.st, sizeof(T.st));
+    tree_free(&T);
+    return 0;
+}
+
+/* Standard tree code mutual acceleration (Algorithm StandardTree called with
+ * (moonlet a, root) for every moonlet), user order, no external forces.
+ * Stats: ST_M2L counts moonlet-cell expansions (M2P), ST_P2P_PAIRS the
+ * brute-force moonlet-cell interactions, ST_P2P_INTER their moonlet pairs. */
+int or_standard_accel(const or_params *P, int64_t n, const double *pos, const double *mass,
+                      double *acc, int64_t *stats)
+{
+    Tree T;
+    memset(&T, 0, sizeof(T));
+    T.P = P; T.n = n; T.pos = pos; T.mass = mass; T.acc = acc;
+    memset(acc, 0, sizeof(double) * 3 * (n > 0 ? n : 0));
+    if (n <= 0) return 0;
+    tree_build(&T);
+    climb_gravity(&T, T.rootn);
+    finish_gravity(&T);
+    for (int64_t a = 0; a < n; a++) standard_tree(&T, a, T.rootn);
     tree_stats(&T);
     if (stats) memcpy(stats, T.st, sizeof(T.st));
     tree_free(&T);
