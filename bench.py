@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--resolve-f", type=float, default=0.0,
                     help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="disk", choices=["disk", "ensemble", "serving"],
+    ap.add_argument("--workload", default="disk", choices=["disk", "ensemble", "serving", "standard"],
                     help="disk: one disk per GPU (default); ensemble: 64 disks of mixed size per GPU in one batch; "
                          "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="serving: length of the arrival window")
@@ -519,6 +519,64 @@ def run_serving(a):
         dist.destroy_process_group()
 
 
+def run_standard(a):
+    """Force evaluation of one disk by the standard tree code (ncorp_accel_standard) and, on the same disk
+    and context settings, by falcON (ncorp_accel): moonlet accelerations per second of each, inputs resident
+    in HBM, L2 flushed before every evaluation."""
+    torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
+    from paper_2310_20374_gb300 import diskgen
+    stream = torch.cuda.current_stream()
+    d = diskgen.make_disk(a.n, a.seed + rank)
+    ctx = ncorp.ncorp_init(cfg, a.n, local, stream.cuda_stream)
+    pos = torch.tensor(d["pos"], device="cuda")
+    m = torch.tensor(d["mass"], device="cuda")
+    acc = torch.empty_like(pos)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        for _ in range(max(a.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(a.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return slowest_rank(dist, total, world), ncorp.ncorp_stats(ctx)
+
+    sampler = ClockSampler(physical_gpu_index(local))
+    ms_std, st_std = timed(lambda: ncorp.ncorp_accel_standard(ctx, pos, m, a.n, a.p, a.theta, acc))
+    ms_fal, st_fal = timed(lambda: ncorp.ncorp_accel(ctx, pos, m, a.n, a.p, a.theta, acc))
+    clocks = sampler.stop()
+    ncorp.ncorp_free(ctx)
+    unit = "moonlet accelerations/s"
+    value = replica_throughput(a.n, a.steps, world, ms_std * 1e-3)
+    out = {"metric": "moonlet accelerations/s, standard tree code (Algorithm StandardTree) vs falcON",
+           "value": round(value, 1), "unit": unit, "n_gpus": world, "steps": a.steps, "warmup": max(a.warmup, 3),
+           "ms_per_step": round(ms_std / a.steps, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
+           "data": "synthetic (seeded moonlet disk shaped like the paper's)",
+           "config": {"workload": f"1 disk x {a.n} moonlets per GPU (seed {a.seed}+rank), p={a.p} theta_min={a.theta}, "
+                                  f"N_cb,pre={cfg.n_cb_pre} N_cb,post={cfg.n_cb_post}, one force evaluation per step "
+                                  f"(tree build, climb, multipoles, walk, evaluation), {a.precision} precision",
+                      "l2": "flushed by a 256 MiB device write before every timed evaluation",
+                      "parallelism": "replicas (one independent disk per GPU)"},
+           "standard_stats": {k: st_std[k] for k in ("cells", "leaves", "m2l", "p2p_pairs", "p2p_interactions")},
+           "falcon": {"value": round(replica_throughput(a.n, a.steps, world, ms_fal * 1e-3), 1), "unit": unit,
+                      "ms_per_eval": round(ms_fal / a.steps, 4),
+                      "stats": {k: st_fal[k] for k in ("m2l", "p2p_pairs", "p2p_interactions")}},
+           "falcon_speedup": round(ms_std / ms_fal, 2),
+           "gpu_launches": st_std["launches"] * a.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -527,6 +585,8 @@ def main():
         run_ensemble(a)
     elif a.workload == "serving":
         run_serving(a)
+    elif a.workload == "standard":
+        run_standard(a)
     else:
         run_gpu(a)
 

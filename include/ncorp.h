@@ -81,10 +81,13 @@ typedef struct {
                                  with a moonlet already resolved in the step is reported but not resolved.
                                  The search then runs before the drift instead of beside it.  Other values:
                                  NCORP_EINVAL at ncorp_init. */
+    int n_cb_pre, n_cb_post;  /* thresholds N_cb,pre and N_cb,post of the standard tree code
+                                 (ncorp_accel_standard, Algorithm StandardTree, Sect. 3.4.4); >= 0 */
 } ncorp_config;
 
 /* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
- * NCORP_MIXED, collisions on (reported, not resolved), no star, no bulge (J2 = 0). */
+ * NCORP_MIXED, collisions on (reported, not resolved), no star, no bulge (J2 = 0),
+ * standard tree thresholds N_cb,pre = 6 and N_cb,post = 16 (Sect. 4.2). */
 void ncorp_config_default(ncorp_config *cfg);
 
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
@@ -141,6 +144,20 @@ int ncorp_collisions(ncorp_ctx *ctx, int64_t *pairs, int64_t cap, int64_t *n_pai
  * Invalidates the resident step state.  Errors as ncorp_step. */
 int ncorp_accel(ncorp_ctx *ctx, const double *positions, const double *masses, int64_t n, int p,
                 double theta, double *acc, double *acc_mutual);
+
+/* Accelerations by the standard tree code (Algorithm StandardTree, Sect.
+ * 3.4.4) on the same tree, geometry (r_crit = r_max / theta(M)) and
+ * multipoles as ncorp_accel: every moonlet a is walked from the root; a cell
+ * B with fewer than n_cb_pre moonlets is summed directly, a cell well
+ * separated from a (r_crit,B^2 <= |x_a - s_B|^2, zero distance excluded)
+ * contributes its order-p expansion at a, a cell with fewer than n_cb_post
+ * moonlets or a leaf is summed directly, any other is opened.  acc / acc_mutual
+ * as for ncorp_accel.  Counters: NCORP_STAT_M2L = moonlet-cell expansions,
+ * NCORP_STAT_P2P_PAIRS = direct moonlet-cell sums, NCORP_STAT_P2P_INTER =
+ * their moonlet pairs.  ncorp_expansions then exports multipoles only
+ * (local != NULL: NCORP_ESTATE).  Errors as ncorp_accel. */
+int ncorp_accel_standard(ncorp_ctx *ctx, const double *positions, const double *masses, int64_t n, int p,
+                         double theta, double *acc, double *acc_mutual);
 
 /* Collision search alone (Sect. 3.1, tree climb for collisions of Sect.
  * 3.4.2, Algorithm TreeWalk) on the given positions and velocities over a

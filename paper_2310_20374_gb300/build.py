@@ -37,9 +37,10 @@ def _headers():
         [os.path.join(ROOT, "include", "ncorp.h")]
 
 
-# Per-file flags.  eval.cu: single-precision denormals flushed to zero (no
-# value below 1e-38 matters to its sums), so rsqrtf needs no denormal fix-up.
-FILE_FLAGS = {"eval.cu": ["-ftz=true"]}
+# Per-file flags.  eval.cu, standard.cu: single-precision denormals flushed to
+# zero (no value below 1e-38 matters to their sums), so rsqrtf needs no
+# denormal fix-up.
+FILE_FLAGS = {"eval.cu": ["-ftz=true"], "standard.cu": ["-ftz=true"]}
 
 
 def _compile(src: str, extra: list[str]) -> str:

@@ -111,6 +111,7 @@ struct Ctrl {
     long long n_tests;     // collision tests
     long long col_pairs;   // collision walk: direct cell pairs
     long long col_self;    // collision walk: direct self cells
+    long long n_m2p;       // standard tree code: moonlet-cell expansions
     int col_iters;         // collision walk: generations
     unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
     double root[4];        // x_lo, y_lo, z_lo, L

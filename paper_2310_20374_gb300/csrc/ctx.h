@@ -171,6 +171,7 @@ struct ncorp_ctx {
     int64_t stats[NCORP_NSTATS] = {0};
     int tree_kind = 0;               // 1: gravity geometry valid, 2: collision geometry valid (bit mask)
     int grav_p = 0;                  // p of the last gravity evaluation (0: none)
+    bool grav_local = false;         // the last gravity evaluation made local expansions (falcON)
     int launches = 0;                // kernels launched by the current call
     StepGraph graphs[2];             // resident steps alternate between two buffer rotations
     int graph_next = 0;
@@ -207,7 +208,8 @@ void launch_walk(ncorp_ctx *c, bool gravity);
 
 // ---- m2l.cu / eval.cu ----
 void launch_m2l(ncorp_ctx *c, int p, bool mixed);
-void launch_descend(ncorp_ctx *c, int p, bool mixed);
+// complete local expansions of the leaves, or of every cell (all_cells)
+void launch_descend(ncorp_ctx *c, int p, bool mixed, bool all_cells = false);
 struct ExtForce {
     double GMc;            // G * central mass
     double star_k;         // G M_star / r_star^3 (0: off)
@@ -216,6 +218,10 @@ struct ExtForce {
     double bulge;          // G M_c R_c^2 J2 of the equatorial bulge (0: off)
 };
 void launch_near(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
+// Algorithm StandardTree for the moonlets of S (tree order) on the current tree, whose geometry and
+// multipoles are computed: S.ax = mutual + external, amx = mutual (want_mutual)
+void launch_standard(ncorp_ctx *c, const ParticleSet &S, int n, int p, bool mixed, double G, ExtForce ext,
+                     bool want_mutual, int pre, int post);
 void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G, ExtForce ext, bool want_mutual,
                 double kick_h = 0.0);
 

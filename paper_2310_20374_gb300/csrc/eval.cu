@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "ctx.h"
+#include "fields.cuh"
 
 namespace ncorp {
 
@@ -83,73 +84,6 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
             }
 }
 
-// 1/r from r^2: an FP32 reciprocal square root refined by two Newton steps
-// in FP64 (the seed's relative error ~2^-22 squares twice, to the FP64
-// rounding level): with 1/r^3 = y^3 and 1/r^5 = y^5 about a third of the FP64
-// instructions of correctly rounded square roots and divisions; outside the
-// FP32 range the direct form.
-__device__ __forceinline__ double inv_r(double r2) {
-    if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / sqrt(r2);
-    double y = static_cast<double>(rsqrtf(static_cast<float>(r2)));
-    const double hr2 = -0.5 * r2;
-    y = y * fma(hr2, y * y, 1.5);
-    y = y * fma(hr2, y * y, 1.5);
-    return y;
-}
-
-// Central body (App. B.1), its equatorial bulge (App. B.2, k = z axis) and the
-// distant star's tide (App. B.3), in FP64.
-__device__ __forceinline__ void external_force(const ExtForce &E, double X, double Y, double Z, double &ex, double &ey,
-                                               double &ez) {
-    const double r2 = X * X + Y * Y + Z * Z;
-    const double y = inv_r(r2), y2 = y * y, y3 = y2 * y;
-    const double fc = -E.GMc * y3;
-    ex = fc * X;
-    ey = fc * Y;
-    ez = fc * Z;
-    if (E.bulge != 0.0) {
-        const double q = E.bulge * y3 * y2;   // G M_c R_c^2 J2 / r^5
-        const double radial = q * (15.0 * Z * Z - 3.0 * r2) * (0.5 * y2);
-        ex += radial * X;
-        ey += radial * Y;
-        ez += radial * Z - 3.0 * q * Z;
-    }
-    if (E.star_k != 0.0) {
-        const double c3 = 3.0 * (X * E.sx + Y * E.sy + Z * E.sz) * E.inv_rs2;
-        ex -= E.star_k * (X - c3 * E.sx);
-        ey -= E.star_k * (Y - c3 * E.sy);
-        ez -= E.star_k * (Z - c3 * E.sz);
-    }
-}
-
-// One near-field pair, FP32: the separation from the (hi, lo) pairs, then
-// mu_j d / |d|^3; a coincident pair (r^2 = 0, the moonlet itself) adds 0.
-__device__ __forceinline__ void p2p_f32(const float4 &h, const float4 &l, const float4 &th, const float4 &tl, float &ax,
-                                        float &ay, float &az) {
-    const float dx = (h.x - th.x) + (l.x - tl.x);
-    const float dy = (h.y - th.y) + (l.y - tl.y);
-    const float dz = (h.z - th.z) + (l.z - tl.z);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float inv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-    const float f3 = h.w * inv * inv * inv;
-    ax += dx * f3;
-    ay += dy * f3;
-    az += dz * f3;
-}
-
-__device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double mu, double X, double Y, double Z,
-                                        double &ax, double &ay, double &az) {
-    const double dx = jx - X, dy = jy - Y, dz = jz - Z;
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 > 0.0) {
-        const double inv = 1.0 / sqrt(r2);
-        const double f3 = mu * inv * inv * inv;
-        ax += dx * f3;
-        ay += dy * f3;
-        az += dz * f3;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Tree descent (Sect. 3.4.3).  The descent adds to every cell its parent's
 // complete local expansion translated to the cell's centre, from the root
@@ -162,7 +96,8 @@ __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double 
 //   h_a = (s_c - s_a)/rho_a.
 // Every cell is thus independent of the others: one warp per cell, lanes
 // over the output coefficients, with no level-by-level barrier.  The result
-// goes to Cf (Ch keeps the own M2L sums).
+// goes to Cf (Ch keeps the own M2L sums).  A step needs the leaves' only
+// (L2P evaluates at the leaves): the other cells are completed on request.
 //
 // The inner sum factorises over the axes (beta! = bx! by! bz!), so a
 // translation is done as three one-dimensional shifts, along x, y, z in
@@ -171,6 +106,7 @@ __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double 
 // ---------------------------------------------------------------------------
 struct DescendArgs {
     const int *parent;
+    const int *leaves;         // the cells to complete: the leaves (L2P needs only theirs), or all when null
     const float4 *gh, *gl;
     const double *sx, *sy, *sz, *rho;
     const void *Ch;
@@ -211,7 +147,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
     const real *Ch = static_cast<const real *>(A.Ch);
     real *Cf = static_cast<real *>(A.Cf);
     real *sa = s_A[wl], *sb = s_B[wl];
-    const int ncells = A.ctl->n_cells;
+    const int nitems = A.leaves ? A.ctl->n_leaves : A.ctl->n_cells;
     int on[PER], okk[PER], oc[PER];
 #pragma unroll
     for (int k = 0; k < PER; k++) {
@@ -222,7 +158,8 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
         okk[k] = b0 + c0;
         oc[k] = c0;
     }
-    for (int c = gw; c < ncells; c += nwarps) {
+    for (int item = gw; item < nitems; item += nwarps) {
+        const int c = A.leaves ? A.leaves[item] : item;
         real acc[PER];
 #pragma unroll
         for (int k = 0; k < PER; k++) {
@@ -514,10 +451,11 @@ static void far_t(ncorp_ctx *c, const EvalArgs &A) {
     c->launches++;
 }
 
-void launch_descend(ncorp_ctx *c, int p, bool mixed) {
+void launch_descend(ncorp_ctx *c, int p, bool mixed, bool all_cells) {
     Cells &C = c->cells;
     DescendArgs D;
-    D.parent = C.parent; D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
+    D.parent = C.parent;
+    D.leaves = all_cells ? nullptr : C.leaves; D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
     D.Ch = C.Ch; D.Cf = C.Cf; D.ctl = c->ctl;
 #define NCORP_DESC_CASE(PP)                      \
     case PP:                                     \

@@ -25,33 +25,9 @@
 // (A <- B and B <- A), which is the symmetric treatment of Sect. 3.4.3 split
 // into its two halves.
 #include "ctx.h"
+#include "fields.cuh"
 
 namespace ncorp {
-
-template <int P, typename real>
-__device__ __forceinline__ void green_derivatives(real ux, real uy, real uz, real *D) {
-    const real r2 = ux * ux + uy * uy + uz * uz;
-    const real ir2 = real(1) / r2;
-    D[0] = sqrt(ir2);
-#pragma unroll
-    for (int n = 1; n <= P; n++) {
-#pragma unroll
-        for (int k = 0; k <= n; k++) {
-#pragma unroll
-            for (int c = 0; c <= k; c++) {
-                const int a = n - k, b = k - c;
-                real s1 = real(0), s2 = real(0);
-                if (a >= 1) s1 += real(a) * ux * D[sidx(a - 1, b, c)];
-                if (b >= 1) s1 += real(b) * uy * D[sidx(a, b - 1, c)];
-                if (c >= 1) s1 += real(c) * uz * D[sidx(a, b, c - 1)];
-                if (a >= 2) s2 += real(a * (a - 1)) * D[sidx(a - 2, b, c)];
-                if (b >= 2) s2 += real(b * (b - 1)) * D[sidx(a, b - 2, c)];
-                if (c >= 2) s2 += real(c * (c - 1)) * D[sidx(a, b, c - 2)];
-                D[sidx(a, b, c)] = -(real(2 * n - 1) * s1 + real(n - 1) * s2) * (ir2 * real(1.0 / n));
-            }
-        }
-    }
-}
 
 struct M2LArgs {
     const int2 *dir;

@@ -342,6 +342,9 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     ctl->n_found = 0;
     ctl->n_resolved = 0;
     ctl->n_tests = 0;
+    ctl->dec_pairs = 0;
+    ctl->n_inter = 0;
+    ctl->n_m2p = 0;
     ctl->bar_count = 0;
     ctl->resort_ok = 0;
     for (int k = 0; k < 3; k++) {
@@ -469,6 +472,7 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
     const double G = c->cfg.G;
     c->grav_p = p;
     c->grav_mixed = mixed;
+    c->grav_local = true;
     { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_geometry(c, S, G, theta); }
     NCORP_CUDA_CHECK(cudaEventRecord(c->ev_geo, c->stream));
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_geo, 0));
@@ -490,6 +494,20 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
     { Stage st(c, NCORP_STAGE_DESCEND); launch_descend(c, p, mixed); }
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_near, 0));
     { Stage st(c, NCORP_STAGE_EVAL); launch_far(c, S, p, mixed, G, external(c, t), want_mutual, kick_h); }
+}
+
+// Gravity of the tree in the current set by the standard tree code: the
+// geometry climb (with theta(M)), the multipoles, then one walk per moonlet.
+void gravity_standard(ncorp_ctx *c, ParticleSet &S, int n, int p, double theta, double t, bool want_mutual) {
+    const bool mixed = c->cfg.precision == NCORP_MIXED;
+    const double G = c->cfg.G;
+    c->grav_p = p;
+    c->grav_mixed = mixed;
+    c->grav_local = false;
+    { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_geometry(c, S, G, theta); }
+    { Stage st(c, NCORP_STAGE_CLIMB); launch_multipoles(c, S, p, mixed, G); }
+    Stage st(c, NCORP_STAGE_EVAL);
+    launch_standard(c, S, n, p, mixed, G, external(c, t), want_mutual, c->cfg.n_cb_pre, c->cfg.n_cb_post);
 }
 
 void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
@@ -737,6 +755,8 @@ void ncorp_config_default(ncorp_config *cfg) {
     cfg->central_radius = 1.0;
     cfg->precision = NCORP_MIXED;
     cfg->collisions = 1;
+    cfg->n_cb_pre = 6;
+    cfg->n_cb_post = 16;
 }
 
 int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream) {
@@ -744,6 +764,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
     if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
     if (!(cfg->G > 0.0) || !(cfg->central_mass >= 0.0) || cfg->leaf_size < 0) return NCORP_EINVAL;
     if (!(cfg->resolve_f == 0.0 || (cfg->resolve_f >= 1.0 && cfg->resolve_f <= 2.0))) return NCORP_EINVAL;
+    if (cfg->n_cb_pre < 0 || cfg->n_cb_post < 0) return NCORP_EINVAL;
     *out = nullptr;
     ncorp_ctx *c = new (std::nothrow) ncorp_ctx();
     if (!c) return NCORP_ENOMEM;
@@ -855,6 +876,54 @@ int ncorp_accel(ncorp_ctx *c, const double *positions, const double *masses, int
         c->n = n;
         c->tree_kind = 1;
         record_stats(c, true);
+        return NCORP_OK;
+    })
+}
+
+int ncorp_accel_standard(ncorp_ctx *c, const double *positions, const double *masses, int64_t n64, int p,
+                         double theta, double *acc, double *acc_mutual) {
+    int st = check_common(c, n64, p, theta);
+    if (st) return st;
+    if (!positions || !masses || !acc) return fail(c, NCORP_EINVAL, "null pointer");
+    NCORP_API_BODY(c, {
+        begin_call(c);
+        const int n = static_cast<int>(n64);
+        ensure_particles(c, n);
+        choose_parameters(c, p);
+        c->have_state = false;
+        c->tree_valid = false;
+        for (int attempt = 0;; attempt++) {
+            ensure_tree_capacity(c, n);
+            reset_ctl(c);
+            ParticleSet &A = c->A;
+            upload_vec(c, positions, A.x, A.y, A.z, n);
+            upload_scalar(c, masses, A.m, n);
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vx, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vy, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.vz, 0, sizeof(double) * n, c->stream));
+            NCORP_CUDA_CHECK(cudaMemsetAsync(A.R, 0, sizeof(double) * n, c->stream));
+            launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+            build_tree(c, A, A, A, c->Cset, n);
+            std::swap(c->A, c->Cset);
+            gravity_standard(c, c->A, n, p, theta, c->time, acc_mutual != nullptr);
+            download_vec(c, c->A.ax, c->A.ay, c->A.az, c->A.perm, acc, n, c->stage);
+            if (acc_mutual) download_vec(c, c->amx, c->amy, c->amz, c->A.perm, acc_mutual, n, c->stage2);
+            int err = finish(c);
+            if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
+            if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+            if (err == 0) break;
+            if (attempt >= MAX_RETRIES || !grow_after(c, err))
+                return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+        }
+        c->n = n;
+        c->tree_kind = 1;
+        record_stats(c, true);
+        const Ctrl &h = *c->ctl_h;
+        c->stats[NCORP_STAT_M2L] = h.n_m2p;
+        c->stats[NCORP_STAT_P2P_SELF] = 0;
+        c->stats[NCORP_STAT_M2L_DIRECTED] = 0;
+        c->stats[NCORP_STAT_P2P_DIRECTED] = 0;
+        c->stats[NCORP_STAT_WALK_ITERS] = 0;
         return NCORP_OK;
     })
 }
@@ -1138,7 +1207,12 @@ int ncorp_expansions(ncorp_ctx *c, double *mult, double *local, double *rho, int
                 }
             NCORP_CUDA_CHECK(cudaMemcpy(mult, M.data(), sizeof(double) * M.size(), cudaMemcpyDefault));
         }
+        if (local && !c->grav_local)
+            return fail(c, NCORP_ESTATE, "the last evaluation (standard tree code) made no local expansions");
         if (local) {
+            // the evaluation completed the leaves' expansions only: complete every cell's now
+            launch_descend(c, P, c->grav_mixed, true);
+            NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
             std::vector<double> Cl = fetch(c->cells.Cf, nc_);
             for (int i = 0; i < k; i++)
                 for (int j = 0; j < nc_; j++) {

@@ -306,10 +306,13 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
                     const float fz = (ha.z - hb.z) + (la.z - lb.z);
                     const float d2f = fx * fx + fy * fy + fz * fz;
                     const float tf = ha.w + hb.w, t2f = tf * tf;
+                    // (the hi + lo pairs carry an absolute error ~2^-47 |s|: separations below
+                    // ~2^-26 |s| go to FP64)
+                    const float fl = (fabsf(ha.x) + fabsf(ha.y) + fabsf(ha.z)) * 0x1p-26f, fl2 = fl * fl + 1e-30f;
                     bool sep;
-                    if (d2f > 1e-30f && d2f > t2f * (1.0f + 0x1p-14f)) {
+                    if (d2f > fl2 && d2f > t2f * (1.0f + 0x1p-14f)) {
                         sep = true;
-                    } else if (d2f > 1e-30f && d2f < t2f * (1.0f - 0x1p-14f)) {
+                    } else if (d2f > fl2 && d2f < t2f * (1.0f - 0x1p-14f)) {
                         sep = false;
                     } else {
                         const double dx = dsub(A.sx[cA], A.sx[cB]);

@@ -36,7 +36,8 @@ class ncorp_config(C.Structure):
                 ("c_cs", C.c_int), ("c_cc_pre", C.c_int), ("c_cc_post", C.c_int),
                 ("precision", C.c_int), ("collisions", C.c_int),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
-                ("t0", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double)]
+                ("t0", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double),
+                ("n_cb_pre", C.c_int), ("n_cb_post", C.c_int)]
 
 
 _lib = None
@@ -65,6 +66,7 @@ def load(path: str | None = None):
     L.ncorp_set_graphs.argtypes = [vp, ip]
     L.ncorp_collisions.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.ncorp_accel.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
+    L.ncorp_accel_standard.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
     L.ncorp_collide.argtypes = [vp, vp, vp, vp, i64, dbl]
     L.ncorp_get_state.argtypes = [vp, vp, vp]
     L.ncorp_stats.argtypes = [vp, C.POINTER(i64), ip]
@@ -89,7 +91,7 @@ def load(path: str | None = None):
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
-                 "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
+                 "ncorp_accel_standard", "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
                  "ncorp_hilbert_sort_static", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
                  "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
         getattr(L, name).restype = C.c_int
@@ -168,6 +170,11 @@ def ncorp_collisions(ctx, pairs, cap):
 def ncorp_accel(ctx, positions, masses, n, p, theta, acc, acc_mutual=None):
     return _check(ctx, load().ncorp_accel(ctx, _ptr(positions), _ptr(masses), int(n), int(p), float(theta),
                                           _ptr(acc), _ptr(acc_mutual)))
+
+
+def ncorp_accel_standard(ctx, positions, masses, n, p, theta, acc, acc_mutual=None):
+    return _check(ctx, load().ncorp_accel_standard(ctx, _ptr(positions), _ptr(masses), int(n), int(p),
+                                                   float(theta), _ptr(acc), _ptr(acc_mutual)))
 
 
 def ncorp_collide(ctx, positions, velocities, radii, n, dt):

@@ -38,6 +38,7 @@ def test_config_default(lib):
     assert cfg.precision == ncorp.NCORP_MIXED and cfg.collisions == 1
     assert cfg.leaf_size == 0 and cfg.star_mass == 0.0 and cfg.central_J2 == 0.0
     assert cfg.resolve_f == 0.0
+    assert (cfg.n_cb_pre, cfg.n_cb_post) == (6, 16)
 
 
 def test_bad_arguments_rejected_without_device_work(lib):
@@ -53,6 +54,10 @@ def test_bad_arguments_rejected_without_device_work(lib):
         bad.resolve_f = f
         assert lib.ncorp_init(C.byref(h), C.byref(bad), 10, 0, None) == ncorp.NCORP_EINVAL
         assert lib.ncorp_batch_create(C.byref(h), C.byref(bad), 0, None) == ncorp.NCORP_EINVAL
+    bad = ncorp.ncorp_config_default()
+    bad.n_cb_pre = -1
+    assert lib.ncorp_init(C.byref(h), C.byref(bad), 10, 0, None) == ncorp.NCORP_EINVAL
+    assert lib.ncorp_accel_standard(None, None, None, 10, 3, 0.5, None, None) == ncorp.NCORP_EINVAL
     assert lib.ncorp_step(None, None, None, None, None, 10, 3, 0.5, 1e-3) == ncorp.NCORP_EINVAL
     assert lib.ncorp_accel(None, None, None, 10, 3, 0.5, None, None) == ncorp.NCORP_EINVAL
     assert lib.ncorp_collisions(None, None, 0, None) == ncorp.NCORP_EINVAL
