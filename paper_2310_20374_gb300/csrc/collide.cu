@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
 }
 
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
-                    double dt) {
+                    double dt, bool wide) {
     CollideArgs A;
     A.p2p = c->wl.p2p; A.self = c->wl.self;
     A.first = c->cells.first; A.count = c->cells.count;
@@ -161,9 +161,9 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.self_cap = c->wl.self_cap;
     A.p2p_cap = c->wl.p2p_cap;
     A.ctl = c->ctl;
-    // two blocks per SM: the search runs beside the main chain's cooperative kernels, which must find
-    // room on every SM while it runs
-    k_collide<<<2 * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
+    // two blocks per SM beside the main chain (its cooperative kernels must find room on every SM
+    // while the search runs); four (the register file's limit) when nothing else runs
+    k_collide<<<(wide ? 4 : 2) * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -231,7 +231,7 @@ void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const dou
                        const int *gate);
 void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, double dt);
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
-                    double dt);
+                    double dt, bool wide);
 void launch_sort_pairs(ncorp_ctx *c, int count);
 
 // ---- kdk.cu ----

@@ -510,11 +510,13 @@ void gravity_standard(ncorp_ctx *c, ParticleSet &S, int n, int p, double theta, 
     launch_standard(c, S, n, p, mixed, G, external(c, t), want_mutual, c->cfg.n_cb_pre, c->cfg.n_cb_post);
 }
 
-void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt) {
+// wide: nothing else runs on the device meanwhile (the pair test takes every SM)
+void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt,
+                bool wide) {
     Stage st(c, NCORP_STAGE_COLLIDE);
     launch_climb_collision(c, S, vx, vy, vz, dt);
     launch_walk(c, false);
-    launch_collide(c, S, vx, vy, vz, dt);
+    launch_collide(c, S, vx, vy, vz, dt, wide);
 }
 
 constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision walk beside the gravity pipeline
@@ -561,7 +563,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->stream = c->side;
             c->coop_max = cap > 0 ? std::min(cap, COLLISION_SIDE_BLOCKS) : COLLISION_SIDE_BLOCKS;
             try {
-                collisions(c, A, B.vx, B.vy, B.vz, dt);
+                collisions(c, A, B.vx, B.vy, B.vz, dt, false);
                 NCORP_CUDA_CHECK(cudaEventRecord(c->ev_join, c->side));
             } catch (...) {
                 c->stream = main;
@@ -571,7 +573,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->stream = main;
             c->coop_max = cap;
         } else {
-            collisions(c, A, B.vx, B.vy, B.vz, dt);
+            collisions(c, A, B.vx, B.vy, B.vz, dt, overlap);   // (overlap false: a batch's streams share the GPU)
             if (resolve) {
                 Stage st(c, NCORP_STAGE_COLLIDE);
                 launch_resolve(c, A, B, n, dt);
@@ -952,7 +954,7 @@ int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocitie
             launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
             build_tree(c, A, A, A, c->Cset, n);
             std::swap(c->A, c->Cset);
-            collisions(c, c->A, c->A.vx, c->A.vy, c->A.vz, dt);
+            collisions(c, c->A, c->A.vx, c->A.vy, c->A.vz, dt, true);
             int err = finish(c);
             if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
             if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
