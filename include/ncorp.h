@@ -79,7 +79,8 @@ typedef struct {
                                  of the step at their new velocities.  A moonlet takes at most one impact
                                  per step: pairs are resolved in increasing (impact time, i, j) and a pair
                                  with a moonlet already resolved in the step is reported but not resolved.
-                                 The search then runs before the drift instead of beside it.  Other values:
+                                 The search still runs beside the new tree's build; a step that resolved an
+                                 impact builds that tree again from the resolved drift.  Other values:
                                  NCORP_EINVAL at ncorp_init. */
     int n_cb_pre, n_cb_post;  /* thresholds N_cb,pre and N_cb,post of the standard tree code
                                  (ncorp_accel_standard, Algorithm StandardTree, Sect. 3.4.4); >= 0 */

@@ -205,7 +205,6 @@ struct ResolveArgs {
     unsigned long long *node_tc, *node_ij;
     int *owner;
     Ctrl *ctl;                 // the search's control block: n_found in, n_resolved out
-    Ctrl *next;                // the new tree's control block: its box is emptied when a moonlet moved
 };
 
 __device__ __forceinline__ unsigned long long tc_key(double tc) {
@@ -314,22 +313,16 @@ __global__ void __launch_bounds__(RES_THREADS) k_resolve(ResolveArgs A) {
         atomicAdd(&s_count, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        A.ctl->n_resolved = s_count;
-        if (s_count > 0)   // moved moonlets: the drifted positions' box is folded again from scratch
-            for (int d = 0; d < 3; d++) {
-                A.next->bbox[d] = ~0ull;
-                A.next->bbox[3 + d] = 0ull;
-            }
-    }
+    if (threadIdx.x == 0) A.ctl->n_resolved = s_count;
 }
 
 // S: the searched state (positions at the start of the drift, masses, radii,
 // in the search tree's order); D: the half-kicked velocities and drifted
-// positions in the same order.  Enqueued after the search and before the
-// keys of the drifted positions; the new tree's box is refolded (all blocks
-// of that launch return at once when nothing was resolved).
+// positions in the same order, rewritten for the resolved moonlets.  The
+// count goes to the search's control block (n_resolved), where the caller's
+// gated launches read it.
 void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, double dt) {
+    (void)n;
     ResolveArgs A;
     A.pairs = c->pairs; A.where = c->pair_where;
     A.x = S.x; A.y = S.y; A.z = S.z; A.m = S.m; A.R = S.R;
@@ -341,10 +334,8 @@ void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, d
     A.tc = c->res_tc; A.state = c->res_state;
     A.node_tc = c->node_tc; A.node_ij = c->node_ij; A.owner = c->node_owner;
     A.ctl = c->ctl;
-    A.next = c->alt.ctl;
     k_resolve<<<1, RES_THREADS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
-    launch_bbox_gated(c, D.x, D.y, D.z, n, c->alt.ctl, &c->ctl->n_resolved);
 }
 
 __global__ void k_unpack_pairs(const uint64_t *__restrict__ packed, int64_t *__restrict__ out, int count) {

@@ -188,16 +188,18 @@ struct ncorp_ctx {
 namespace ncorp {
 
 // ---- launchers (sort.cu) ----
+// gate (nullable): a device counter read by every launched kernel, which does nothing while it is 0
+// (a step's tree is rebuilt only when its collision resolution moved a moonlet)
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
-                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done = false);
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done = false, const int *gate = nullptr);
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits, bool bar_zeroed = false);
+                    int bits, bool bar_zeroed = false, const int *gate = nullptr);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx, double G);
+                   const uint32_t *idx, double G, const int *gate = nullptr);
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 
 // ---- tree.cu ----
-void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s);
+void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *gate = nullptr);
 void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta);
 void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
 void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
@@ -226,7 +228,7 @@ void launch_far(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G,
                 double kick_h = 0.0);
 
 // ---- collide.cu ----
-// the box of (x, y, z) folded into ctl when *gate != 0 (decided on the device)
+// the box of (x, y, z) emptied and folded again into ctl when *gate != 0 (decided on the device)
 void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, Ctrl *ctl,
                        const int *gate);
 void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, double dt);

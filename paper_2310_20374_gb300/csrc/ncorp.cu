@@ -429,22 +429,23 @@ int finish(ncorp_ctx *c, bool both = false) {
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
 // near_sorted: the positions are in the previous tree order of nearby
 // positions (a drift), so the keys are nearly sorted.
+// gate (nullable, radix sort only): every kernel does nothing while *gate is 0.
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
-                int n, bool near_sorted = false, bool bbox_done = false) {
+                int n, bool near_sorted = false, bool bbox_done = false, const int *gate = nullptr) {
     c->cur_n = n;
     {
         Stage st(c, NCORP_STAGE_SORT);
-        launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz, bbox_done);
+        launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz, bbox_done, gate);
         if (near_sorted) sort_near_sorted(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
-        else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true);
+        else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true, gate);
         ParticleSet view = sr;
         view.x = sx.x; view.y = sx.y; view.z = sx.z;
         view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
         view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
-        launch_gather(c, view, view, dst, n, c->idx, c->cfg.G);
+        launch_gather(c, view, view, dst, n, c->idx, c->cfg.G, gate);
     }
     Stage st(c, NCORP_STAGE_BUILD);
-    launch_build(c, dst, n, c->s);
+    launch_build(c, dst, n, c->s, gate);
 }
 
 // Runs body with c->stream set to s (launchers enqueue on c->stream).
@@ -528,9 +529,13 @@ constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision
 // main stream drifts, sorts, builds and walks the new tree (the two touch
 // disjoint buffers); its cooperative grids are kept small enough that both
 // streams' cooperative kernels fit on the device together.  With collision
-// resolution the search runs on the main stream, followed by the resolution
-// (which rewrites the drift of the moonlets it resolves and refolds the new
-// box), before the keys of the drifted positions.  On return the
+// resolution the side stream also resolves the pairs it found, which
+// rewrites the drift of the resolved moonlets while the main stream may be
+// reading it: after the new tree is built the main stream joins the side
+// stream, and if anything was resolved (a device counter) it folds the box
+// and builds the tree again from the resolved drift (gated launches that
+// return at once otherwise).  Without overlap (batches) the search and the
+// resolution run before the keys.  On return the
 // tree sets have traded places (the current one describes the new positions)
 // and the new state is in Cset (not yet swapped with A); nothing is copied to
 // the caller and nothing waits: the caller reads the status.
@@ -551,9 +556,8 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         K.ctl = c->alt.ctl;
         launch_kick_drift(c, K);
     }
-    // resolution changes the drift of the moonlets it resolves, so the search then runs before the keys
     const bool resolve = c->cfg.collisions && c->cfg.resolve_f > 0.0;
-    const bool side = overlap && c->cfg.collisions && !resolve;
+    const bool side = overlap && c->cfg.collisions;
     if (c->cfg.collisions) {
         if (side) {
             cudaStream_t main = c->stream;
@@ -564,6 +568,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->coop_max = cap > 0 ? std::min(cap, COLLISION_SIDE_BLOCKS) : COLLISION_SIDE_BLOCKS;
             try {
                 collisions(c, A, B.vx, B.vy, B.vz, dt, false);
+                if (resolve) launch_resolve(c, A, B, n, dt);   // may rewrite the drift the main stream reads
                 NCORP_CUDA_CHECK(cudaEventRecord(c->ev_join, c->side));
             } catch (...) {
                 c->stream = main;
@@ -573,17 +578,30 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->stream = main;
             c->coop_max = cap;
         } else {
-            collisions(c, A, B.vx, B.vy, B.vz, dt, overlap);   // (overlap false: a batch's streams share the GPU)
+            collisions(c, A, B.vx, B.vy, B.vz, dt, false);   // (no overlap: a batch's streams share the GPU)
             if (resolve) {
                 Stage st(c, NCORP_STAGE_COLLIDE);
                 launch_resolve(c, A, B, n, dt);
+                // the drifted box again, if a moonlet's drift changed (the new tree set's control block)
+                launch_bbox_gated(c, B.x, B.y, B.z, n, c->alt.ctl, &c->ctl->n_resolved);
             }
         }
     }
     swap_sets(c);
     build_tree(c, B, B, A, Cn, n, true, true);
+    if (side && resolve) {
+        // The tree above was built beside the search from the unresolved drift.  A step that resolved an
+        // impact builds it again from the resolved one; otherwise these launches return at once.
+        NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        const int *moved = &c->alt.ctl->n_resolved;   // the search's control block
+        {
+            Stage st(c, NCORP_STAGE_SORT);
+            launch_bbox_gated(c, B.x, B.y, B.z, n, c->ctl, moved);
+        }
+        build_tree(c, B, B, A, Cn, n, false, true, moved);
+    }
     gravity(c, Cn, p, theta, c->time + dt, false, h);   // with the closing half kick
-    if (side) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (side && !resolve) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
 }
 
 // col: the control block of the tree the collision search ran on (NULL: the current one)

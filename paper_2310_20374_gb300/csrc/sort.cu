@@ -164,9 +164,11 @@ __device__ __forceinline__ uint32_t quantise(double v, double lo, int s) {
 
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                        int n, Ctrl *ctl, uint64_t *__restrict__ key, uint32_t *__restrict__ idx,
-                       uint32_t *__restrict__ qx, uint32_t *__restrict__ qy, uint32_t *__restrict__ qz) {
+                       uint32_t *__restrict__ qx, uint32_t *__restrict__ qy, uint32_t *__restrict__ qz,
+                       const int *gate = nullptr) {
     __shared__ double s_root[4];
     __shared__ int s_shift;
+    if (gate && *gate == 0) return;
     if (threadIdx.x == 0) {
         root_cube(ctl, s_root);
         if (blockIdx.x == 0) {
@@ -196,17 +198,28 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
 // folds it); k_keys also zeroes the grid-barrier counter for the sort that
 // follows.
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
-                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done) {
+                      uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done, const int *gate) {
     if (!bbox_done) {
-        k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl); c->launches++;
+        k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, gate); c->launches++;
         NCORP_CUDA_CHECK(cudaGetLastError());
     }
-    k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz); c->launches++;
+    k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz,
+                                                                       gate);
+    c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+__global__ void k_bbox_reset(Ctrl *ctl, const int *gate) {
+    if (*gate == 0) return;
+    for (int d = 0; d < 3; d++) {
+        ctl->bbox[d] = ~0ull;
+        ctl->bbox[3 + d] = 0ull;
+    }
 }
 
 void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, Ctrl *ctl,
                        const int *gate) {
+    k_bbox_reset<<<1, 1, 0, c->stream>>>(ctl, gate); c->launches++;
     k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, ctl, gate); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
@@ -271,6 +284,7 @@ struct RadixArgs {
     unsigned *epoch;              // device counter: this call's tag base, advanced by the call
     unsigned epoch_limit;         // at this epoch the call clears the status region and restarts from 0
     Ctrl *ctl;
+    const int *gate;              // k_radix: nothing to do while *gate is 0 (null: always sort)
 };
 
 // Tags are (epoch + 1) * 8 + pass in 32 bits; well before they would wrap, the
@@ -434,6 +448,7 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
 }
 
 __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
+    if (A.gate && *A.gate == 0) return;   // every block returns before the first barrier
     unsigned bar = 0;
     radix_body(A, bar);
 }
@@ -488,13 +503,15 @@ static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64
     A.epoch = reinterpret_cast<unsigned *>(c->tile_hist + RS_EPOCH_AT);
     A.epoch_limit = c->radix_epoch_limit;
     A.ctl = c->ctl;
+    A.gate = nullptr;
     return A;
 }
 
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits, bool bar_zeroed) {
+                    int bits, bool bar_zeroed, const int *gate) {
     if (n <= 1) return;
     RadixArgs A = radix_args(c, keys, vals, keys_alt, vals_alt, n, bits);
+    A.gate = gate;
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
                                                                    RS_T, 0));
@@ -742,9 +759,11 @@ struct GatherArgs {
     const uint64_t *key;   // sorted keys
     double G;
     int n;
+    const int *gate;       // nothing to do while *gate is 0 (null: always)
 };
 
 __global__ void k_gather(GatherArgs g) {
+    if (g.gate && *g.gate == 0) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
         const int j = static_cast<int>(g.idx[i]);
         int d = i;
@@ -780,8 +799,9 @@ __global__ void k_gather(GatherArgs g) {
 }
 
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx, double G) {
+                   const uint32_t *idx, double G, const int *gate) {
     GatherArgs g;
+    g.gate = gate;
     g.x = src_xv.x; g.y = src_xv.y; g.z = src_xv.z;
     g.vx = src_xv.vx; g.vy = src_xv.vy; g.vz = src_xv.vz;
     g.m = src_rest.m; g.R = src_rest.R; g.perm = src_rest.perm;
@@ -916,6 +936,7 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
         A.epoch = &S->epoch;
         A.epoch_limit = RS_EPOCH_LIMIT;
         A.ctl = &S->ctl;
+        A.gate = nullptr;
         const int grid = std::min(A.ntiles, d.radix_per_sm * d.num_sms);
         void *args[] = {&A};
         if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_radix), dim3(grid), dim3(RS_T), args, 0, s) !=

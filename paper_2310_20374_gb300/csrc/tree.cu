@@ -67,9 +67,11 @@ struct BuildArgs {
     int *bounds, *blocksum;
     int *maker, *before;    // per cell: the block that made it, children of its maker's earlier cells
     Ctrl *ctl;
+    const int *gate;        // nothing to do while *gate is 0 (null: always build)
 };
 
 __global__ void k_build_init(BuildArgs A) {
+    if (A.gate && *A.gate == 0) return;
     A.level[0] = 0;
     A.first[0] = 0;
     A.count[0] = A.n;
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     volatile Ctrl *vc = A.ctl;
     const int G = gridDim.x;
     unsigned bar = 0;
+    if (A.gate && *A.gate == 0) return;   // every block returns before the first barrier
     {
         const int t = made_cells(A, 0, blockIdx.x == 0 ? 1 : 0, 0, s_red);
         if (threadIdx.x == 0) A.blocksum[blockIdx.x] = t;
@@ -281,7 +284,9 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
 }
 
 // Also zeroes the grid-barrier counter for the cooperative kernel that follows.
-__global__ void k_collect_leaves(const int *__restrict__ nchild, Ctrl *ctl, int cap, int *leaves, int *n_leaves) {
+__global__ void k_collect_leaves(const int *__restrict__ nchild, Ctrl *ctl, int cap, int *leaves, int *n_leaves,
+                                 const int *gate) {
+    if (gate && *gate == 0) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bar_count = 0;
     if (aborted(ctl)) return;
     const int nc = min(ctl->n_cells, cap);
@@ -301,9 +306,10 @@ static int coop_grid(ncorp_ctx *c, const void *kernel, int block, size_t smem) {
     return coop_blocks(c, per_sm);
 }
 
-void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
+void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *gate) {
     Cells &C = c->cells;
     BuildArgs A;
+    A.gate = gate;
     A.key = P.key;
     A.qx = P.qx; A.qy = P.qy; A.qz = P.qz;
     A.n = n; A.s = s; A.cap = C.cap;
@@ -322,7 +328,7 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s) {
                                                  args, 0, c->stream));
     c->launches++;
     k_collect_leaves<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(C.nchild, c->ctl, C.cap, C.leaves,
-                                                                                 &c->ctl->n_leaves);
+                                                                                 &c->ctl->n_leaves, gate);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
