@@ -176,8 +176,10 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_CELLS        0
 #define NCORP_STAT_LEAVES       1
 #define NCORP_STAT_DEPTH        2
-#define NCORP_STAT_M2L          3   /* well-separated cell pairs (gravity walk) */
-#define NCORP_STAT_P2P_PAIRS    4   /* cell pairs treated directly (gravity walk decisions) */
+#define NCORP_STAT_M2L          3   /* well-separated cell pairs (gravity walk); moonlet-cell expansions
+                                       after ncorp_accel_standard */
+#define NCORP_STAT_P2P_PAIRS    4   /* cell pairs treated directly (gravity walk decisions); direct
+                                       moonlet-cell sums after ncorp_accel_standard */
 #define NCORP_STAT_P2P_SELF     5   /* cells treated directly with themselves (gravity) */
 #define NCORP_STAT_P2P_INTER    6   /* particle pairs summed directly (gravity, unordered) */
 #define NCORP_STAT_COL_PAIRS    7   /* cell pairs searched directly (collision walk decisions) */

@@ -72,3 +72,45 @@ def test_header_documents_every_entry_point():
         m = re.search(r"^(?:const )?[a-z_0-9]+ \**" + name + r"\(", text, re.M)   # the declaration line
         assert m, f"{name} has no declaration line"
         assert text[:m.start()].rstrip().endswith("*/"), f"{name} has no comment right above it"
+
+
+# ---- the ctypes binding and the oracle wrapper against the C declarations they mirror
+_CTYPES = {"double": C.c_double, "int": C.c_int, "int64_t": C.c_int64}
+
+
+def _struct_fields(text, name):
+    """[(field, ctypes type)] of `typedef struct { ... } name;` in C source text."""
+    m = re.search(r"typedef struct \{(.*?)\}\s*" + name + ";", text, re.S)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        out += [(n.strip(), _CTYPES[ctype]) for n in names.split(",")]
+    return out
+
+
+def test_config_struct_matches_the_header():
+    text = open(ncorp.HEADER).read()
+    assert [(n, t) for n, t in ncorp.ncorp_config._fields_] == _struct_fields(text, "ncorp_config")
+
+
+def test_stat_and_stage_slots_match_the_header():
+    text = open(ncorp.HEADER).read()
+    stats = {n: int(i) for n, i in re.findall(r"#define NCORP_STAT_(\w+)\s+(\d+)", text)}
+    assert int(re.search(r"#define NCORP_NSTATS\s+(\d+)", text).group(1)) == len(ncorp.STAT_NAMES) == len(stats)
+    for name, i in stats.items():
+        assert ncorp.STAT_NAMES[i] == name.lower().replace("p2p_inter", "p2p_interactions"), (name, i)
+    stages = {n: int(i) for n, i in re.findall(r"#define NCORP_STAGE_(\w+)\s+(\d+)", text)}
+    assert int(re.search(r"#define NCORP_NSTAGES\s+(\d+)", text).group(1)) == len(ncorp.STAGE_NAMES) == len(stages)
+    for name, i in stages.items():
+        assert ncorp.STAGE_NAMES[i] == name.lower(), (name, i)
+
+
+def test_oracle_params_match_its_c_struct():
+    import oracle
+    text = open(os.path.join(os.path.dirname(oracle.__file__), "ncorp_oracle.c")).read()
+    assert [(n, t) for n, t in oracle.Params._fields_] == _struct_fields(text, "or_params")
