@@ -80,7 +80,9 @@ typedef struct {
                                  per step: pairs are resolved in increasing (impact time, i, j) and a pair
                                  with a moonlet already resolved in the step is reported but not resolved.
                                  The search still runs beside the new tree's build; a step that resolved an
-                                 impact builds that tree again from the resolved drift.  Other values:
+                                 impact builds that tree again from the resolved drift.  Resolved moonlets
+                                 need positive masses (v' = v -+ J/m): a massless one makes the step fail
+                                 with NCORP_EINVAL (non-finite position).  Other values of resolve_f:
                                  NCORP_EINVAL at ncorp_init. */
     int n_cb_pre, n_cb_post;  /* thresholds N_cb,pre and N_cb,post of the standard tree code
                                  (ncorp_accel_standard, Algorithm StandardTree, Sect. 3.4.4); >= 0 */
