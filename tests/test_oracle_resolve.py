@@ -192,3 +192,22 @@ def test_kdk_without_resolution_is_unchanged():
     assert len(p0) > 0
     np.testing.assert_allclose(x0, xd, rtol=0, atol=1e-14)
     np.testing.assert_allclose(v0, vel, rtol=0, atol=1e-14)
+
+
+def test_self_gravitating_clump_with_resolution_conserves_momentum():
+    """falcON's mutual forces come in equal and opposite pairs (symmetric M2L
+    and P2P) and every impulse is +-J: with no central body the total momentum
+    of a self-gravitating clump with impacts stays at its initial value."""
+    rng = np.random.default_rng(8)
+    n = 400
+    pos = rng.uniform(-1.0, 1.0, (n, 3))
+    vel = rng.normal(size=(n, 3)) * 0.3
+    m = rng.uniform(0.5, 2.0, n) * 1e-4
+    R = rng.uniform(0.03, 0.08, n)
+    P = oracle.params(p=4, theta=0.5, leaf_size=8, G=1.0, central_mass=0.0, resolve_f=1.5)
+    info = {}
+    x, v, _, pairs = oracle.kdk(P, pos, vel, m, R, 0.02, 5, info=info)
+    assert info["resolved"] > 20 and len(pairs) >= info["resolved"]
+    p0, p1 = m @ vel, m @ v
+    assert np.abs(p1 - p0).max() <= 1e-12 * (m @ np.linalg.norm(vel, axis=1))
+    assert np.all(np.isfinite(x)) and not np.array_equal(v, vel)
