@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
                 ("time", C.c_double), ("m2m_direct", C.c_int), ("brute_collisions", C.c_int),
                 ("central_radius", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double),
-                ("n_cb_pre", C.c_int64), ("n_cb_post", C.c_int64)]
+                ("n_cb_pre", C.c_int64), ("n_cb_post", C.c_int64),
+                ("c_cb_pre", C.c_int64), ("c_cb_post", C.c_int64)]
 
 
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
@@ -100,6 +101,8 @@ def lib():
             L.or_m2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
             L.or_collide_tree.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
             L.or_collide_tree.restype = i64
+            L.or_collide_standard.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
+            L.or_collide_standard.restype = i64
             L.or_tree_export.argtypes = [PP, i64, _dp, _opt(_dp), _opt(_dp), _opt(_dp), dbl,
                                          _opt(_ip), _opt(_up), _opt(_dp), _opt(_ip), _opt(_dp), _opt(_dp), i64]
             L.or_tree_export.restype = i64
@@ -121,10 +124,12 @@ def default_gravity_thresholds(p: int):
 
 def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresholds=None,
            collision_thresholds=(12, 0, 16), star=None, time=0.0, m2m_direct=False,
-           brute_collisions=False, bulge=None, resolve_f=0.0, standard_thresholds=(6, 16)) -> Params:
+           brute_collisions=False, bulge=None, resolve_f=0.0, standard_thresholds=(6, 16),
+           standard_collision_thresholds=(0, 16)) -> Params:
     """bulge: (R_c, J2) of the central body's equatorial bulge (App. B.2), None = no bulge.
     resolve_f: 0 = colliding pairs are only reported; 1 <= f <= 2 = kdk() resolves them (Sect. 5).
-    standard_thresholds: (N_cb,pre, N_cb,post) of Algorithm StandardTree (Sect. 3.4.4; 6 and 16 in Sect. 4.2)."""
+    standard_thresholds: (N_cb,pre, N_cb,post) of Algorithm StandardTree (Sect. 3.4.4; 6 and 16 in Sect. 4.2),
+    and standard_collision_thresholds the same for its collision search (0 and 16 in Sect. 4.2)."""
     g = gravity_thresholds if gravity_thresholds is not None else default_gravity_thresholds(p)
     P = Params()
     P.G, P.central_mass, P.p, P.theta_min, P.leaf_size = G, central_mass, int(p), theta, int(leaf_size)
@@ -139,6 +144,7 @@ def params(p=3, theta=0.5, leaf_size=17, G=1.0, central_mass=1.0, gravity_thresh
         P.central_radius, P.central_J2 = bulge
     P.resolve_f = float(resolve_f)
     P.n_cb_pre, P.n_cb_post = (int(v) for v in standard_thresholds)
+    P.c_cb_pre, P.c_cb_post = (int(v) for v in standard_collision_thresholds)
     return P
 
 
@@ -296,6 +302,18 @@ def resolve(pos, vel, mass, rad, f, pairs):
     lib().or_resolve(len(pos), pos.reshape(-1), vel.reshape(-1), _f64(mass), _f64(rad), float(f),
                      pr.reshape(-1) if len(pr) else np.zeros(2, dtype=np.int64), len(pr), done)
     return pos, vel, done[:len(pr)].astype(bool)
+
+
+def collide_standard(P: Params, pos, vel, rad, dt, cap=1 << 16):
+    """Colliding pairs found by the standard tree code's collision search, and its counters."""
+    pos, vel = _f64(pos), _f64(vel)
+    out = np.zeros((cap, 2), dtype=np.int64)
+    st = np.zeros(16, dtype=np.int64)
+    n = lib().or_collide_standard(C.byref(P), len(pos), pos.reshape(-1), vel.reshape(-1), _f64(rad), float(dt),
+                                  out.reshape(-1), cap, st)
+    if n > cap:
+        return collide_standard(P, pos, vel, rad, dt, cap=int(n))
+    return out[:n], dict(zip(STAT_NAMES, (int(v) for v in st)))
 
 
 def tree_export(P: Params, pos, mass=None, vel=None, rad=None, dt=0.0):

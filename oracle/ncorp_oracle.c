@@ -26,7 +26,8 @@
  *     (Eq. shifting) with full 3^n tensors (no symmetric compression)  pinned
  *   - the dual tree walk (Algorithm TreeWalk, Sect. 3.4.5)           pinned
  *   - the standard tree code (Algorithm StandardTree, Sect. 3.4.4)
- *     with M2P (the m = 1 term of Eq. phi_expanded at a point)        pinned
+ *     with M2P (the m = 1 term of Eq. phi_expanded at a point), and
+ *     its collision search                                            pinned
  *   - the collision predicate (Sect. 3.1), brute force and tree-based  pinned
  *   - the SBAB1 kick-drift-kick step with merged kicks (Sect. 4.1)    pinned
  *   - elastic and inelastic collision resolution (Sect. 5.1, 5.2)     pinned
@@ -62,7 +63,8 @@ typedef struct {
     int brute_collisions;   /* KDK: 1 = brute force pairs, 0 = tree */
     double central_radius, central_J2;   /* App. B.2 equatorial bulge; J2 = 0 disables */
     double resolve_f;       /* KDK: 0 = pairs reported only; 1..2 = resolved with this f (Sect. 5) */
-    int64_t n_cb_pre, n_cb_post;         /* StandardTree thresholds (Sect. 3.4.4) */
+    int64_t n_cb_pre, n_cb_post;         /* StandardTree thresholds (Sect. 3.4.4), gravity */
+    int64_t c_cb_pre, c_cb_post;         /* StandardTree thresholds, collision search */
 } or_params;
 
 /* statistics, int64 slots */
@@ -1019,6 +1021,38 @@ static void standard_tree(Tree *T, int64_t a, Node *B)
     for (int c = 0; c < B->nchild; c++) standard_tree(T, a, B->child[c]);
 }
 
+/* ---- Algorithm StandardTree for collision search (Sect. 3.4.4, the
+ * instructions for collisions): brute force when B holds fewer than
+ * N_cb,pre moonlets; nothing when a is well separated from B; brute force
+ * when B holds fewer than N_cb,post moonlets or is a leaf; else the children.
+ * The moonlet's r_crit is R_a + dt |v_a| (r_max = 0, Eq. rcrit) and pruning
+ * keeps the relative margin of the dual walk:
+ * ((r_crit,a + r_crit,B)(1 + 2^-40))^2 < |x_a - sbar_B|^2.  Brute force
+ * tests a against the moonlets of B with a larger caller index, so each
+ * pair is tested from the walk of its lower index (which reaches it: only
+ * pairs that cannot touch are pruned). */
+static void col_one(Tree *T, int64_t a, Node *B)
+{
+    T->st[ST_COL_PAIRS]++;
+    for (int64_t v = 0; v < B->n; v++) {
+        int64_t j = T->ord[B->first + v];
+        if (j > a) col_pair(T, a, j);
+    }
+}
+
+static void standard_collide(Tree *T, int64_t a, Node *B, double rca)
+{
+    const or_params *P = T->P;
+    if (B->n < P->c_cb_pre) { col_one(T, a, B); return; }
+    const double *xa = T->pos + 3 * a;
+    double d[3] = {xa[0] - B->sb[0], xa[1] - B->sb[1], xa[2] - B->sb[2]};
+    double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    double t = (rca + B->rcrit_c) * (1.0 + 0x1p-40);
+    if (t * t < d2) return;
+    if (B->n < P->c_cb_post || B->nchild == 0) { col_one(T, a, B); return; }
+    for (int c = 0; c < B->nchild; c++) standard_collide(T, a, B->child[c], rca);
+}
+
 /* ---- tree descent: L2L from the root, L2P at the leaves (Eq. shifting) */
 static void descend(Tree *T, Node *x)
 {
@@ -1154,6 +1188,31 @@ int64_t or_collide_tree(const or_params *P, int64_t n, const double *pos, const 
     tree_build(&T);
     climb_collision(&T, T.rootn);
     tree_walk(&T, T.rootn, T.rootn, 0);
+    int64_t found = T.npairs;
+    if (found <= cap) qsort(pairs, (size_t)found, 2 * sizeof(int64_t), cmp_pair);
+    tree_stats(&T);
+    T.st[ST_COL_FOUND] = found;
+    if (stats) memcpy(stats, T.st, sizeof(T.st));
+    tree_free(&T);
+    return found;
+}
+
+/* Collision search by the standard tree code (Algorithm StandardTree called
+ * with (moonlet a, root) for every moonlet); pairs in user indices, i < j,
+ * sorted when they fit.  Stats: ST_COL_PAIRS = brute-force moonlet-cell
+ * interactions, ST_COL_TESTS = pairs tested, ST_COL_FOUND. */
+int64_t or_collide_standard(const or_params *P, int64_t n, const double *pos, const double *vel,
+                            const double *rad, double dt, int64_t *pairs, int64_t cap, int64_t *stats)
+{
+    if (n <= 0) return 0;
+    Tree T;
+    memset(&T, 0, sizeof(T));
+    T.P = P; T.n = n; T.pos = pos; T.vel = vel; T.rad = rad; T.dt = dt;
+    T.pairs = pairs; T.pcap = cap;
+    tree_build(&T);
+    climb_collision(&T, T.rootn);
+    for (int64_t a = 0; a < n; a++)
+        standard_collide(&T, a, T.rootn, rad[a] + dt * norm3(vel + 3 * a));
     int64_t found = T.npairs;
     if (found <= cap) qsort(pairs, (size_t)found, 2 * sizeof(int64_t), cmp_pair);
     tree_stats(&T);

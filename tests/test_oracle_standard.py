@@ -107,3 +107,28 @@ def test_errors_similar_to_falcon():
     e_std = np.median(rel_err(oracle.standard_accel(P, pos, m)[0], ref))
     e_fal = np.median(rel_err(oracle.falcon_accel(P, pos, m)[0], ref))
     assert 0.1 < e_std / e_fal < 10.0, (e_std, e_fal)
+
+
+@pytest.mark.parametrize("thresholds", [(0, 16), (0, 0), (8, 64)])
+def test_standard_collision_search_equals_brute_force(thresholds):
+    """The collision variant of StandardTree prunes only cells no moonlet of
+    which can reach a within the step, and tests each pair from its lower
+    index: the pair set is the brute-force one, on random sets and a dense
+    ring, at any thresholds."""
+    P = oracle.params(p=3, leaf_size=6, standard_collision_thresholds=thresholds)
+    for seed in range(6):
+        rng = np.random.default_rng(100 + seed)
+        n = 300
+        pos = rng.uniform(-1.0, 1.0, (n, 3))
+        vel = rng.normal(size=(n, 3))
+        rad = rng.uniform(0.01, 0.05, n)
+        got, st = oracle.collide_standard(P, pos, vel, rad, 0.05)
+        ref = oracle.collide_brute(pos, vel, rad, 0.05)
+        assert np.array_equal(got, ref)
+        assert st["col_tests"] < n * (n - 1) // 2 or thresholds[0] > n
+    d = diskgen.make_disk(4000, 9, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
+    got, st = oracle.collide_standard(P, d["pos"], d["vel"], d["radius"], 0.05)
+    ref = oracle.collide_brute(d["pos"], d["vel"], d["radius"], 0.05)
+    tree, _ = oracle.collide_tree(P, d["pos"], d["vel"], d["radius"], 0.05)
+    assert len(ref) > 10 and np.array_equal(got, ref) and np.array_equal(tree, ref)
+    assert st["col_tests"] < 4000 * 3999 // 20
