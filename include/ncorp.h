@@ -334,9 +334,10 @@ const char *ncorp_batch_last_error(const ncorp_batch *b);
 #define NCORP_STATIC_MAX_N 65536
 
 /* Hilbert keys of n moonlets and their stable sort, without allocating any
- * memory: the key and sort stages of a step (root cube, 21-bit quantisation
- * and 63-bit 3-D Hilbert keys of Sect. 3.4.6, then the stable radix sort by
- * (key, index)).  The paper has no counterpart: this entry point exists for
+ * memory: the key and sort stages of a step (the root cube around the
+ * bounding box, 21-bit quantisation per axis and a 63-bit 3-D Hilbert key,
+ * then the stable radix sort by (key, index)).  The paper has no
+ * counterpart: this entry point exists for
  * callers that must not allocate device memory once they are set up (a fixed
  * device-memory budget, or a loop in which the implicit synchronisation of
  * cudaMalloc/cudaFree is not acceptable), and needs no context.
@@ -352,8 +353,8 @@ const char *ncorp_batch_last_error(const ncorp_batch *b);
  * Scratch: one file-scope device array per device, sized for
  * NCORP_STATIC_MAX_N moonlets (about 3.4 MB); nothing is allocated or freed.
  * The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make one call on each
- * device before any stream capture that is to contain this function.
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins on the device.
  * The array keeps the contents of the last call; each call first resets the
  * parts that must start at zero (bounding-box accumulators, status word,
  * barrier counter) and overwrites everything else before reading it.

@@ -71,48 +71,92 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            PP = C.POINTER(Params)
-            i64, dbl = C.c_int64, C.c_double
-            L.or_root.argtypes = [i64, _dp, _dp]
-            L.or_hilbert_key.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
-            L.or_hilbert_key.restype = C.c_uint64
-            L.or_keys.argtypes = [i64, _dp, _dp, _u32p, _up]
-            L.or_theta.argtypes = [dbl, dbl, dbl]
-            L.or_theta.restype = dbl
-            L.or_dtensor.argtypes = [C.c_int, _dp, _dp]
-            L.or_p2m.argtypes = [C.c_int, i64, _dp, _dp, _dp, _dp]
-            L.or_m2m.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
-            L.or_m2l.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
-            L.or_l2l.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
-            L.or_l2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
-            L.or_direct_accel.argtypes = [i64, _dp, _dp, dbl, i64, _opt(_ip), _dp]
-            L.or_external_accel.argtypes = [PP, i64, _dp, dbl, _dp]
-            L.or_collide_pair.argtypes = [_dp, _dp, dbl, _dp, _dp, dbl, dbl]
-            L.or_collide_pair.restype = C.c_int
-            L.or_collide_brute.argtypes = [i64, _dp, _dp, _dp, dbl, _ip, i64]
-            L.or_collide_brute.restype = i64
-            L.or_resolve.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, _ip, i64, _opt(_ip)]
-            L.or_resolve.restype = i64
-            L.or_falcon_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
-            L.or_falcon_accel.restype = C.c_int
-            L.or_standard_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
-            L.or_standard_accel.restype = C.c_int
-            L.or_m2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
-            L.or_collide_tree.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
-            L.or_collide_tree.restype = i64
-            L.or_collide_standard.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
-            L.or_collide_standard.restype = i64
-            L.or_tree_export.argtypes = [PP, i64, _dp, _opt(_dp), _opt(_dp), _opt(_dp), dbl,
-                                         _opt(_ip), _opt(_up), _opt(_dp), _opt(_ip), _opt(_dp), _opt(_dp), i64]
-            L.or_tree_export.restype = i64
-            L.or_expansions.argtypes = [PP, i64, _dp, _dp, _opt(_dp), _opt(_dp), i64]
-            L.or_expansions.restype = i64
-            L.or_kdk.argtypes = [PP, i64, _dp, _dp, _dp, _dp, dbl, C.c_int, _opt(_dp), _opt(_dp), _ip, i64,
-                                 _opt(_ip)]
-            L.or_kdk.restype = i64
-            _lib = L
+            _lib = _bind(build())
     return _lib
+
+
+def build_variant(source_text: str, out_dir: str) -> str:
+    """Compiles an edited copy of the oracle's source (tests that plant a
+    mistake in the oracle use this) with the oracle's flags; returns the
+    library path."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "ncorp_oracle_variant.c")
+    with open(src, "w") as f:
+        f.write(source_text)
+    out = os.path.join(out_dir, "libncorp_oracle_variant.so")
+    subprocess.check_call(["gcc", *CFLAGS, src, "-o", out, "-lm"])
+    return out
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+class use_library:
+    """Context manager: every function of this module calls the library at
+    `path` (an oracle variant) instead of the oracle itself."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        build()
+        with _lock:
+            self.saved = _lib
+            _lib = _bind(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
+
+
+def _bind(path):
+    L = C.CDLL(path)
+    PP = C.POINTER(Params)
+    i64, dbl = C.c_int64, C.c_double
+    L.or_root.argtypes = [i64, _dp, _dp]
+    L.or_hilbert_key.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
+    L.or_hilbert_key.restype = C.c_uint64
+    L.or_keys.argtypes = [i64, _dp, _dp, _u32p, _up]
+    L.or_theta.argtypes = [dbl, dbl, dbl]
+    L.or_theta.restype = dbl
+    L.or_dtensor.argtypes = [C.c_int, _dp, _dp]
+    L.or_p2m.argtypes = [C.c_int, i64, _dp, _dp, _dp, _dp]
+    L.or_m2m.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
+    L.or_m2l.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.or_l2l.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
+    L.or_l2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
+    L.or_direct_accel.argtypes = [i64, _dp, _dp, dbl, i64, _opt(_ip), _dp]
+    L.or_external_accel.argtypes = [PP, i64, _dp, dbl, _dp]
+    L.or_collide_pair.argtypes = [_dp, _dp, dbl, _dp, _dp, dbl, dbl]
+    L.or_collide_pair.restype = C.c_int
+    L.or_collide_brute.argtypes = [i64, _dp, _dp, _dp, dbl, _ip, i64]
+    L.or_collide_brute.restype = i64
+    L.or_resolve.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, _ip, i64, _opt(_ip)]
+    L.or_resolve.restype = i64
+    L.or_falcon_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
+    L.or_falcon_accel.restype = C.c_int
+    L.or_standard_accel.argtypes = [PP, i64, _dp, _dp, _dp, _ip]
+    L.or_standard_accel.restype = C.c_int
+    L.or_m2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
+    L.or_collide_tree.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
+    L.or_collide_tree.restype = i64
+    L.or_collide_standard.argtypes = [PP, i64, _dp, _dp, _dp, dbl, _ip, i64, _ip]
+    L.or_collide_standard.restype = i64
+    L.or_tree_export.argtypes = [PP, i64, _dp, _opt(_dp), _opt(_dp), _opt(_dp), dbl,
+                                 _opt(_ip), _opt(_up), _opt(_dp), _opt(_ip), _opt(_dp), _opt(_dp), i64]
+    L.or_tree_export.restype = i64
+    L.or_expansions.argtypes = [PP, i64, _dp, _dp, _opt(_dp), _opt(_dp), i64]
+    L.or_expansions.restype = i64
+    L.or_kdk.argtypes = [PP, i64, _dp, _dp, _dp, _dp, dbl, C.c_int, _opt(_dp), _opt(_dp), _ip, i64,
+                         _opt(_ip)]
+    L.or_kdk.restype = i64
+    return L
 
 
 # Thresholds used in the paper's performance runs (Sect. 4.2): collisions

@@ -919,63 +919,105 @@ static void direct_pair(Tree *T, Node *A, Node *B, int gravity)
         }
 }
 
-/* ---- Algorithm TreeWalk (Sect. 3.4.5), recursive form.
+/* ---- Algorithm TreeWalk (Sect. 3.4.5).
+ * What happens to a pending pair of cells (A, B) is one decision, made by
+ * walk_choice() from the pair alone; the walk itself keeps the pending pairs
+ * on an explicit stack, starting from (root, root).  Children replace their
+ * parent pair in the order the algorithm visits them (pushed in reverse, so
+ * they are taken in order), which gives the same sequence of interactions
+ * as a depth-first recursion.
  * gravity = 1: M2L for well-separated pairs; gravity = 0: collision search,
  * where well-separated pairs are pruned (with a relative margin 2^-40) and
- * every "brute force" branch tests the moonlet pairs. */
-static void tree_walk(Tree *T, Node *A, Node *B, int gravity)
+ * every "brute force" outcome tests the moonlet pairs. */
+typedef enum {
+    WALK_SELF_DIRECT,   /* A == B, few moonlets or a leaf: all pairs inside A */
+    WALK_SELF_OPEN,     /* A == B: every pair (a, b), a <= b, of children */
+    WALK_DIRECT,        /* all pairs of A x B */
+    WALK_FAR,           /* well separated: M2L (gravity) or nothing (collisions) */
+    WALK_OPEN_A,        /* (a, B) for every child a of A */
+    WALK_OPEN_B         /* (A, b) for every child b of B */
+} WalkChoice;
+
+static int well_separated(const Node *A, const Node *B, int gravity)
 {
-    const or_params *P = T->P;
+    if (gravity) {   /* (r_crit,A + r_crit,B)^2 <= |s_A - s_B|^2 */
+        double d[3] = {A->s[0] - B->s[0], A->s[1] - B->s[1], A->s[2] - B->s[2]};
+        double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        double t = A->rcrit + B->rcrit;
+        return t * t <= d2;
+    }
+    double d[3] = {A->sb[0] - B->sb[0], A->sb[1] - B->sb[1], A->sb[2] - B->sb[2]};
+    double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    double t = (A->rcrit_c + B->rcrit_c) * (1.0 + 0x1p-40);
+    return t * t < d2;
+}
+
+static WalkChoice walk_choice(const or_params *P, const Node *A, const Node *B, int gravity)
+{
     int64_t n_cs = gravity ? P->n_cs : P->c_cs;
     int64_t n_pre = gravity ? P->n_cc_pre : P->c_cc_pre;
     int64_t n_post = gravity ? P->n_cc_post : P->c_cc_post;
     int leafA = A->nchild == 0, leafB = B->nchild == 0;
-    if (A == B) {
-        if (A->n <= n_cs || leafA) {
+    if (A == B) return (A->n <= n_cs || leafA) ? WALK_SELF_DIRECT : WALK_SELF_OPEN;
+    int64_t prod = A->n * B->n;
+    if (prod < n_pre) return WALK_DIRECT;
+    if (well_separated(A, B, gravity)) return WALK_FAR;
+    if (prod < n_post || (leafA && leafB)) return WALK_DIRECT;
+    /* split the larger (by r_crit) of the two, never a leaf (reading c5) */
+    double rA = gravity ? A->rcrit : A->rcrit_c, rB = gravity ? B->rcrit : B->rcrit_c;
+    return (!leafA && (rA > rB || leafB)) ? WALK_OPEN_A : WALK_OPEN_B;
+}
+
+typedef struct { Node **a, **b; int64_t top, cap; } PairStack;
+
+static void push_pair(PairStack *S, Node *a, Node *b)
+{
+    if (S->top == S->cap) {
+        S->cap = S->cap ? 2 * S->cap : 256;
+        S->a = (Node **)realloc(S->a, sizeof(Node *) * S->cap);
+        S->b = (Node **)realloc(S->b, sizeof(Node *) * S->cap);
+    }
+    S->a[S->top] = a;
+    S->b[S->top] = b;
+    S->top++;
+}
+
+static void tree_walk(Tree *T, Node *root, int gravity)
+{
+    PairStack S = {NULL, NULL, 0, 0};
+    push_pair(&S, root, root);
+    while (S.top > 0) {
+        S.top--;
+        Node *A = S.a[S.top], *B = S.b[S.top];
+        switch (walk_choice(T->P, A, B, gravity)) {
+        case WALK_SELF_DIRECT:
             T->st[gravity ? ST_P2P_SELF : ST_COL_SELF]++;
             direct_self(T, A, gravity);
-        } else {
-            for (int a = 0; a < A->nchild; a++)
-                for (int b = a; b < A->nchild; b++) tree_walk(T, A->child[a], A->child[b], gravity);
+            break;
+        case WALK_SELF_OPEN:   /* visited in the order (0,0), (0,1), ..., (1,1), ... */
+            for (int a = A->nchild - 1; a >= 0; a--)
+                for (int b = A->nchild - 1; b >= a; b--) push_pair(&S, A->child[a], A->child[b]);
+            break;
+        case WALK_DIRECT:
+            T->st[gravity ? ST_P2P_PAIRS : ST_COL_PAIRS]++;
+            direct_pair(T, A, B, gravity);
+            break;
+        case WALK_FAR:
+            if (gravity) {
+                T->st[ST_M2L]++;
+                or_m2l(T->P->p, A->s, A->Mt, B->s, B->Mt, A->Ct, B->Ct);
+            }
+            break;
+        case WALK_OPEN_A:
+            for (int a = A->nchild - 1; a >= 0; a--) push_pair(&S, A->child[a], B);
+            break;
+        case WALK_OPEN_B:
+            for (int b = B->nchild - 1; b >= 0; b--) push_pair(&S, A, B->child[b]);
+            break;
         }
-        return;
     }
-    int64_t prod = A->n * B->n;
-    if (prod < n_pre) {
-        T->st[gravity ? ST_P2P_PAIRS : ST_COL_PAIRS]++;
-        direct_pair(T, A, B, gravity);
-        return;
-    }
-    int separated;
-    if (gravity) {
-        double d[3] = {A->s[0] - B->s[0], A->s[1] - B->s[1], A->s[2] - B->s[2]};
-        double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-        double t = A->rcrit + B->rcrit;
-        separated = t * t <= d2;
-    } else {
-        double d[3] = {A->sb[0] - B->sb[0], A->sb[1] - B->sb[1], A->sb[2] - B->sb[2]};
-        double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-        double t = (A->rcrit_c + B->rcrit_c) * (1.0 + 0x1p-40);
-        separated = t * t < d2;
-    }
-    if (separated) {
-        if (gravity) {
-            T->st[ST_M2L]++;
-            or_m2l(P->p, A->s, A->Mt, B->s, B->Mt, A->Ct, B->Ct);
-        }
-        return;
-    }
-    if (prod < n_post || (leafA && leafB)) {
-        T->st[gravity ? ST_P2P_PAIRS : ST_COL_PAIRS]++;
-        direct_pair(T, A, B, gravity);
-        return;
-    }
-    double rA = gravity ? A->rcrit : A->rcrit_c, rB = gravity ? B->rcrit : B->rcrit_c;
-    if (!leafA && (rA > rB || leafB)) {
-        for (int a = 0; a < A->nchild; a++) tree_walk(T, A->child[a], B, gravity);
-    } else {
-        for (int b = 0; b < B->nchild; b++) tree_walk(T, A, B->child[b], gravity);
-    }
+    free(S.a);
+    free(S.b);
 }
 
 /* ---- Algorithm StandardTree (Sect. 3.4.4), gravity, for moonlet a and cell
@@ -1105,7 +1147,7 @@ int or_falcon_accel(const or_params *P, int64_t n, const double *pos, const doub
     tree_build(&T);
     climb_gravity(&T, T.rootn);
     finish_gravity(&T);
-    tree_walk(&T, T.rootn, T.rootn, 1);
+    tree_walk(&T, T.rootn, 1);
     descend(&T, T.rootn);
     tree_stats(&T);
     if (stats) memcpy(stats, T.st, sizeof(T.st));
@@ -1152,7 +1194,7 @@ int64_t or_expansions(const or_params *P, int64_t n, const double *pos, const do
     tree_build(&T);
     climb_gravity(&T, T.rootn);
     finish_gravity(&T);
-    tree_walk(&T, T.rootn, T.rootn, 1);
+    tree_walk(&T, T.rootn, 1);
     descend(&T, T.rootn);
     Node **sorted = (Node **)malloc(sizeof(Node *) * T.nnodes);
     memcpy(sorted, T.nodes, sizeof(Node *) * T.nnodes);
@@ -1187,7 +1229,7 @@ int64_t or_collide_tree(const or_params *P, int64_t n, const double *pos, const 
     T.pairs = pairs; T.pcap = cap;
     tree_build(&T);
     climb_collision(&T, T.rootn);
-    tree_walk(&T, T.rootn, T.rootn, 0);
+    tree_walk(&T, T.rootn, 0);
     int64_t found = T.npairs;
     if (found <= cap) qsort(pairs, (size_t)found, 2 * sizeof(int64_t), cmp_pair);
     tree_stats(&T);

@@ -919,11 +919,26 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     StaticScratch *S = d.ptr;
     const int g = std::max(1, std::min((n + 255) / 256, 4 * d.num_sms));
-    k_static_reset<<<1, 1, 0, s>>>(S);
-    k_static_split<<<g, 256, 0, s>>>(positions, S, n);
-    k_bbox<<<g, 256, 0, s>>>(S->x, S->y, S->z, n, &S->ctl);
-    k_keys<<<g, 256, 0, s>>>(S->x, S->y, S->z, n, &S->ctl, keys, S->idx, S->qx, S->qy, S->qz);
-    if (cudaGetLastError() != cudaSuccess) return NCORP_ECUDA;
+    // Launched through cudaLaunchKernel, whose return value is this launch's own
+    // error (cudaGetLastError could report an earlier, unrelated failure).
+    Ctrl *ctl = &S->ctl;
+    double *sx = S->x, *sy = S->y, *sz = S->z;
+    uint32_t *sidx = S->idx, *qx = S->qx, *qy = S->qy, *qz = S->qz;
+    int ni = n;
+    {
+        const int *no_gate = nullptr;
+        void *a_reset[] = {&S};
+        void *a_split[] = {const_cast<double **>(&positions), &S, &ni};
+        void *a_bbox[] = {&sx, &sy, &sz, &ni, &ctl, &no_gate};
+        void *a_keys[] = {&sx, &sy, &sz, &ni, &ctl, &keys, &sidx, &qx, &qy, &qz, &no_gate};
+        if (cudaLaunchKernel(reinterpret_cast<const void *>(k_static_reset), dim3(1), dim3(1), a_reset, 0, s) !=
+                cudaSuccess ||
+            cudaLaunchKernel(reinterpret_cast<const void *>(k_static_split), dim3(g), dim3(256), a_split, 0, s) !=
+                cudaSuccess ||
+            cudaLaunchKernel(reinterpret_cast<const void *>(k_bbox), dim3(g), dim3(256), a_bbox, 0, s) != cudaSuccess ||
+            cudaLaunchKernel(reinterpret_cast<const void *>(k_keys), dim3(g), dim3(256), a_keys, 0, s) != cudaSuccess)
+            return NCORP_ECUDA;
+    }
     if (n > 1) {
         RadixArgs A;
         A.k0 = keys; A.k1 = S->key_alt; A.v0 = S->idx; A.v1 = S->idx_alt;
@@ -943,8 +958,12 @@ extern "C" int ncorp_hilbert_sort_static(const double *positions, int64_t n64, u
             cudaSuccess)
             return NCORP_ECUDA;
     }
-    k_static_order<<<g, 256, 0, s>>>(S, order, n);
-    if (cudaGetLastError() != cudaSuccess) return NCORP_ECUDA;
+    {
+        void *a_order[] = {&S, &order, &ni};
+        if (cudaLaunchKernel(reinterpret_cast<const void *>(k_static_order), dim3(g), dim3(256), a_order, 0, s) !=
+            cudaSuccess)
+            return NCORP_ECUDA;
+    }
     int err = 0;
     if (cudaMemcpyAsync(&err, &S->ctl.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NCORP_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return NCORP_ECUDA;

@@ -120,6 +120,35 @@ def _ptr(a):
     raise TypeError(f"cannot take the address of {type(a)}")
 
 
+_KINDS = {"f8": ("float64",), "i8": ("int64", "uint64"), "i4": ("int32",)}
+
+
+def _arr(a, kind, count, name):
+    """Address of an array argument after checking what can be checked here:
+    a torch tensor or numpy array must have the element type `kind` ("f8":
+    float64, "i8": 8-byte integer), be contiguous and hold at least `count`
+    elements, else NcorpError(NCORP_EINVAL) is raised before the library is
+    called (the library cannot see how large an allocation is).  None and raw
+    integer addresses pass through unchecked."""
+    if a is None or isinstance(a, int):
+        return _ptr(a)
+    if hasattr(a, "data_ptr"):   # torch tensor
+        dt = str(a.dtype).replace("torch.", "")
+        contiguous, size = a.is_contiguous(), a.numel()
+    elif hasattr(a, "ctypes"):   # numpy array
+        dt = str(a.dtype)
+        contiguous, size = bool(a.flags["C_CONTIGUOUS"]), a.size
+    else:
+        return _ptr(a)
+    if dt not in _KINDS[kind]:
+        raise NcorpError(NCORP_EINVAL, f"{name}: element type {dt}, expected {' or '.join(_KINDS[kind])}")
+    if not contiguous:
+        raise NcorpError(NCORP_EINVAL, f"{name}: array is not contiguous")
+    if size < count:
+        raise NcorpError(NCORP_EINVAL, f"{name}: {size} elements, at least {count} needed")
+    return _ptr(a)
+
+
 def _check(ctx, st):
     if st != NCORP_OK:
         msg = load().ncorp_last_error(ctx)
@@ -146,8 +175,10 @@ def ncorp_set_stream(ctx, stream):
 
 
 def ncorp_step(ctx, positions, velocities, masses, radii, n, p, theta, dt):
-    return _check(ctx, load().ncorp_step(ctx, _ptr(positions), _ptr(velocities), _ptr(masses), _ptr(radii),
-                                         int(n), int(p), float(theta), float(dt)))
+    n = int(n)
+    return _check(ctx, load().ncorp_step(ctx, _arr(positions, "f8", 3 * n, "positions"),
+                                         _arr(velocities, "f8", 3 * n, "velocities"), _arr(masses, "f8", n, "masses"),
+                                         _arr(radii, "f8", n, "radii"), n, int(p), float(theta), float(dt)))
 
 
 def ncorp_reset(ctx):
@@ -161,24 +192,32 @@ def ncorp_set_graphs(ctx, enable):
 def ncorp_collisions(ctx, pairs, cap):
     """Fills pairs [cap][2] int64; returns the total number found."""
     found = C.c_int64(0)
-    st = load().ncorp_collisions(ctx, _ptr(pairs), int(cap), C.byref(found))
+    st = load().ncorp_collisions(ctx, _arr(pairs, "i8", 2 * int(cap), "pairs"), int(cap), C.byref(found))
     if st not in (NCORP_OK, NCORP_EOVERFLOW):
         _check(ctx, st)
     return int(found.value)
 
 
 def ncorp_accel(ctx, positions, masses, n, p, theta, acc, acc_mutual=None):
-    return _check(ctx, load().ncorp_accel(ctx, _ptr(positions), _ptr(masses), int(n), int(p), float(theta),
-                                          _ptr(acc), _ptr(acc_mutual)))
+    n = int(n)
+    return _check(ctx, load().ncorp_accel(ctx, _arr(positions, "f8", 3 * n, "positions"),
+                                          _arr(masses, "f8", n, "masses"), n, int(p), float(theta),
+                                          _arr(acc, "f8", 3 * n, "acc"), _arr(acc_mutual, "f8", 3 * n, "acc_mutual")))
 
 
 def ncorp_accel_standard(ctx, positions, masses, n, p, theta, acc, acc_mutual=None):
-    return _check(ctx, load().ncorp_accel_standard(ctx, _ptr(positions), _ptr(masses), int(n), int(p),
-                                                   float(theta), _ptr(acc), _ptr(acc_mutual)))
+    n = int(n)
+    return _check(ctx, load().ncorp_accel_standard(ctx, _arr(positions, "f8", 3 * n, "positions"),
+                                                   _arr(masses, "f8", n, "masses"), n, int(p), float(theta),
+                                                   _arr(acc, "f8", 3 * n, "acc"),
+                                                   _arr(acc_mutual, "f8", 3 * n, "acc_mutual")))
 
 
 def ncorp_collide(ctx, positions, velocities, radii, n, dt):
-    return _check(ctx, load().ncorp_collide(ctx, _ptr(positions), _ptr(velocities), _ptr(radii), int(n), float(dt)))
+    n = int(n)
+    return _check(ctx, load().ncorp_collide(ctx, _arr(positions, "f8", 3 * n, "positions"),
+                                            _arr(velocities, "f8", 3 * n, "velocities"),
+                                            _arr(radii, "f8", n, "radii"), n, float(dt)))
 
 
 def ncorp_get_state(ctx, positions, velocities):
@@ -249,7 +288,10 @@ def ncorp_batch_create(cfg: ncorp_config, hbm_budget_bytes: int = 0, stream=None
 
 def ncorp_batch_add_disk(b, positions, velocities, masses, radii, n, p, theta, dt) -> int:
     did = C.c_int32(-1)
-    _bcheck(b, load().ncorp_batch_add_disk(b, _ptr(positions), _ptr(velocities), _ptr(masses), _ptr(radii), int(n),
+    n = int(n)
+    _bcheck(b, load().ncorp_batch_add_disk(b, _arr(positions, "f8", 3 * n, "positions"),
+                                           _arr(velocities, "f8", 3 * n, "velocities"),
+                                           _arr(masses, "f8", n, "masses"), _arr(radii, "f8", n, "radii"), n,
                                            int(p), float(theta), float(dt), C.byref(did)))
     return int(did.value)
 
@@ -264,7 +306,8 @@ def ncorp_batch_get_state(b, disk_id, positions, velocities):
 
 def ncorp_batch_collisions(b, disk_id, pairs, cap):
     found = C.c_int64(0)
-    _bcheck(b, load().ncorp_batch_collisions(b, int(disk_id), _ptr(pairs), int(cap), C.byref(found)),
+    _bcheck(b, load().ncorp_batch_collisions(b, int(disk_id), _arr(pairs, "i8", 2 * int(cap), "pairs"), int(cap),
+                                             C.byref(found)),
             ok=(NCORP_OK, NCORP_EOVERFLOW))
     return int(found.value)
 
@@ -291,7 +334,9 @@ def ncorp_batch_last_error(b) -> str:
 
 def ncorp_hilbert_sort_static(positions, n, keys, order, stream=None):
     """Allocation-free keys + stable sort (device arrays only); raises NcorpError on failure."""
-    st = load().ncorp_hilbert_sort_static(_ptr(positions), int(n), _ptr(keys), _ptr(order), _ptr(stream))
+    n = int(n)
+    st = load().ncorp_hilbert_sort_static(_arr(positions, "f8", 3 * n, "positions"), n, _arr(keys, "i8", n, "keys"),
+                                          _arr(order, "i8", n, "order"), _ptr(stream))
     if st != NCORP_OK:
         why = {NCORP_EINVAL: f"invalid argument (n must be 1..{NCORP_STATIC_MAX_N}, arrays device memory of the "
                              f"current device, positions finite)",

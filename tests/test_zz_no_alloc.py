@@ -68,3 +68,20 @@ def test_static_sort_rejects_before_device_work():
     with pytest.raises(ncorp.NcorpError) as e:   # non-finite position, found on the device
         ncorp.ncorp_hilbert_sort_static(bad, 8, keys, order)
     assert e.value.code == ncorp.NCORP_EINVAL
+
+
+def test_static_sort_takes_no_device_memory():
+    """After one warm-up call (which may load the module and look up the
+    scratch array), further calls leave the device's free memory unchanged."""
+    n = 30000
+    d = diskgen.make_disk(n, 44)
+    pos = torch.tensor(d["pos"], device="cuda")
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+    ncorp.ncorp_hilbert_sort_static(pos, n, keys, order)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        ncorp.ncorp_hilbert_sort_static(pos, n, keys, order)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
