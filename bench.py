@@ -35,7 +35,6 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s, falcON p=6 gravity+collisions; p50/p99 step latency mixed-N"
 UNIT = "particle-steps/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 (FMA) x max SM clock (GHz) -> TFLOP/s
 # DRAM bytes (read + write) of one k_eval launch on this workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # set to None whenever the kernel changes until it is captured again.
@@ -57,6 +56,9 @@ def parse():
     ap.add_argument("--resolve-f", type=float, default=0.0,
                     help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="disk: time only the requested precision on workload 2 (no FP64/mixed twin, no workload 3)")
+    ap.add_argument("--steps3", type=int, default=100, help="disk: timed steps of workload 3 (N = 1e6)")
     ap.add_argument("--workload", default="disk", choices=["disk", "ensemble", "serving", "standard"],
                     help="disk: one disk per GPU (default); ensemble: 64 disks of mixed size per GPU in one batch; "
                          "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
@@ -92,17 +94,22 @@ def replica_throughput(units_per_rank, steps, world, seconds):
 # written); sort = keys (24 B read, 24 B written), the nearly-sorted merge of
 # (key, index) (36 B), the gather to tree order (~196 B); build = 16 B;
 # climb = the moonlet pass of the geometry and of P2M (2 x 32 B); eval = L2P,
-# near sums, external force and closing kick (~152 B).  FP32-ALU stages:
-# m2l = FLOPs per unordered M2L pair (both directions, one D(R)), by p;
-# near = 24 FLOP per directed moonlet pair; collide = ~15 FLOP per candidate
-# pair of the FP32 prefilter.  walk and descend are latency-bound chains
-# (dependent generations; ancestor translations per leaf): no throughput bound.
+# near sums, external force and closing kick (~152 B).  ALU-bound stages, in
+# the method's own units whatever the kernels evaluate: m2l = FLOPs per
+# unordered well-separated pair (one D(R), both directions), by p; near =
+# 30 FLOPs per unordered moonlet pair of the direct sums (one rsqrt); collide
+# = 30 FLOPs per candidate pair of the collision test.  walk and descend are
+# latency-bound chains (dependent generations; ancestor translations per
+# leaf): no throughput bound.
 STAGE_BYTES_PER_MOONLET = {"kdk": 220.0, "sort": 280.0, "build": 16.0, "climb": 64.0, "eval": 152.0}
 M2L_FLOP_PER_PAIR = {3: 250.0, 4: 700.0, 6: 3200.0}
+NEAR_FLOP_PER_PAIR = 30.0
+COLLIDE_FLOP_PER_TEST = 30.0
 
 
-def stage_rooflines(stage_ms, n, p, m2l_pairs, p2p_inter, col_tests, hbm_gbs, fp32_tflops):
-    """Per-stage fraction of roofline from per-step stage times (ms) and the step's work counters."""
+def stage_rooflines(stage_ms, n, p, m2l_pairs, p2p_inter, col_tests, hbm_gbs, alu_tflops):
+    """Per-stage fraction of roofline from per-step stage times (ms) and the step's work counters;
+    alu_tflops is the measured FMA peak of the precision the ALU stages run in."""
     out = {}
     for st, bpm in STAGE_BYTES_PER_MOONLET.items():
         ms = stage_ms.get(st, 0.0)
@@ -110,15 +117,15 @@ def stage_rooflines(stage_ms, n, p, m2l_pairs, p2p_inter, col_tests, hbm_gbs, fp
             gbs = bpm * n / (ms * 1e-3) / 1e9
             out[st] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
                        "frac": round(gbs / hbm_gbs, 4), "bytes_per_moonlet": bpm}
-    flops = {"near": 24.0 * 2.0 * p2p_inter, "collide": 15.0 * col_tests}
+    flops = {"near": NEAR_FLOP_PER_PAIR * p2p_inter, "collide": COLLIDE_FLOP_PER_TEST * col_tests}
     if p in M2L_FLOP_PER_PAIR:
         flops["m2l"] = M2L_FLOP_PER_PAIR[p] * m2l_pairs
     for st, f in flops.items():
         ms = stage_ms.get(st, 0.0)
         if ms > 0 and f > 0:
             tf = f / (ms * 1e-3) / 1e12
-            out[st] = {"bound": "alu", "achieved": round(tf, 3), "peak": round(fp32_tflops, 1), "unit": "TFLOP/s",
-                       "frac": round(tf / fp32_tflops, 4), "flops_per_step": f}
+            out[st] = {"bound": "alu", "achieved": round(tf, 3), "peak": round(alu_tflops, 2), "unit": "TFLOP/s",
+                       "frac": round(tf / alu_tflops, 4), "flops_per_step": f}
     for st in ("walk", "descend"):
         if stage_ms.get(st, 0.0) > 0:
             out[st] = {"bound": "latency", "ms": round(stage_ms[st], 4)}
@@ -134,13 +141,26 @@ def measured_hbm_gbs(default=6800.0):
         return default
 
 
-def workload_config(a):
+def leaf_size_for(p):
+    return 64 if p >= 6 else (48 if p >= 4 else 32)
+
+
+def thresholds_for(p):
+    return [256, 256, 512] if p >= 6 else [64, 8, 64]
+
+
+def workload_config(a, n=None, seed=None, p=None, theta=None, precision=None):
+    n = a.n if n is None else n
+    seed = a.seed if seed is None else seed
+    p = a.p if p is None else p
+    theta = a.theta if theta is None else theta
+    precision = a.precision if precision is None else precision
     res = f", collisions resolved with f={a.resolve_f}" if a.resolve_f else ""
-    return {"workload": f"1 disk x {a.n} moonlets per GPU (seed {a.seed}+rank), falcON p={a.p} theta_min={a.theta}, "
-                        f"SBAB1 step dt={a.dt} with tree collision search{res}, {a.precision} precision",
-            "n_per_gpu": a.n, "p": a.p, "theta_min": a.theta, "dt": a.dt, "leaf_size": 64 if a.p >= 6 else 32,
-            "gravity_thresholds": [256, 256, 512] if a.p >= 6 else [64, 8, 64], "collision_thresholds": [12, 0, 16],
-            "precision": a.precision, "l2": "flushed by a 256 MiB device write before every timed step",
+    return {"workload": f"1 disk x {n} moonlets per GPU (seed {seed}+rank), falcON p={p} theta_min={theta}, "
+                        f"SBAB1 step dt={a.dt} with tree collision search{res}, {precision} precision",
+            "n_per_gpu": n, "p": p, "theta_min": theta, "dt": a.dt, "leaf_size": leaf_size_for(p),
+            "gravity_thresholds": thresholds_for(p), "collision_thresholds": [12, 0, 16],
+            "precision": precision, "l2": "flushed by a 256 MiB device write before every timed step",
             "parallelism": "replicas (one independent disk per GPU)",
             **({"resolve_f": a.resolve_f} if a.resolve_f else {})}
 
@@ -203,6 +223,118 @@ def physical_gpu_index(local_rank):
 
 
 # ---------------------------------------------------------------------------- GPU arm
+def host_cores():
+    """Cores of this host as the OS reports them (nproc, and lscpu's model line when available)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                             "Socket(s)", "CPU max MHz"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def time_disk(a, ncorp, torch, ctx_args, d, n, p, theta, precision, steps, warmup, prof_steps, local, stream, flush):
+    """Times `steps` resident ncorp_step calls of one disk (L2 flushed before each, CUDA events on the
+    library's stream), then `prof_steps` directly launched steps with the stage timers on.  Returns the
+    per-step times, counters of the last step, summed launches and the stage times per step."""
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED if precision == "mixed" else ncorp.NCORP_FP64
+    cfg.leaf_size = leaf_size_for(p)
+    cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = thresholds_for(p)
+    cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = 12, 0, 16
+    cfg.resolve_f = a.resolve_f
+    ctx = ncorp.ncorp_init(cfg, n, local, stream.cuda_stream)
+    pos = torch.tensor(d["pos"], device="cuda")
+    vel = torch.tensor(d["vel"], device="cuda")
+    m = torch.tensor(d["mass"], device="cuda")
+    R = torch.tensor(d["radius"], device="cuda")
+
+    def step():
+        ncorp.ncorp_step(ctx, pos, vel, m, R, n, p, theta, a.dt)
+
+    try:
+        for _ in range(max(warmup, 3)):
+            step()
+        ctx_args["barrier"]()
+        step_ms, launches, graph_steps, found = [], 0, 0, 0
+        last = {}
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            st = ncorp.ncorp_stats(ctx)
+            launches += st["launches"]
+            graph_steps += st["graph"]
+            found += st["col_found"]
+            last = st
+        ctx_args["barrier"]()
+        # stage times: more steps after the timed region, launched directly (profiled steps are never
+        # replayed from a graph) with CUDA events around every stage on the stream it runs on
+        ncorp.ncorp_profile(ctx, True)
+        stage, prof = {}, {"m2l": 0, "p2p_interactions": 0, "col_tests": 0}
+        for _ in range(prof_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            step()
+            st = ncorp.ncorp_stats(ctx)
+            for k in prof:
+                prof[k] += st[k]
+            for k, v in ncorp.ncorp_stage_times(ctx).items():
+                stage[k] = stage.get(k, 0.0) + v
+        ncorp.ncorp_profile(ctx, False)
+    finally:
+        ncorp.ncorp_free(ctx)
+    return {"step_ms": step_ms, "launches": launches, "graph_steps": graph_steps, "found": found, "last": last,
+            "stage": {k: v / prof_steps for k, v in stage.items()}, "prof": {k: v / prof_steps for k, v in prof.items()},
+            "prof_steps": prof_steps}
+
+
+def near_roofline(t, peak_tflops, precision, traffic):
+    """Roofline of the dominant kernel, the near-field direct sums (k_eval): NEAR_FLOP_PER_PAIR per unordered
+    moonlet pair of the step (the method's count, whatever the kernel evaluates) over the kernel's event-timed
+    duration, against the measured FMA peak of its precision."""
+    near_ms = t["stage"].get("near", 0.0)
+    pairs = t["prof"]["p2p_interactions"]
+    flops = NEAR_FLOP_PER_PAIR * pairs
+    achieved = flops / (near_ms * 1e-3) / 1e12 if near_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": "k_eval (near-field direct sums per leaf)",
+            "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4) if peak_tflops else None, "traffic": traffic,
+            "flops_per_launch": flops, "unordered_pairs_per_launch": pairs, "avg_launch_ms": round(near_ms, 4),
+            "peak_note": f"measured {precision} FMA throughput of this GPU (ncorp_fma_peak, in-bounds FMA chains, "
+                         f"best of 5 launches at the start of this run), 'of measured'"}
+
+
+def summarize(a, t, n, steps, world, dist, hbm, peak_tflops, p):
+    total = sum(t["step_ms"])
+    t_max = slowest_rank(dist, total, world)
+    last = {k: t["last"][k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
+                                      "walk_iters", "col_pairs", "col_self", "col_tests", "col_iters",
+                                      "m2l_directed", "p2p_directed")}
+    return {"value": round(replica_throughput(n, steps, world, t_max * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(t_max / steps, 4),
+            "p50_step_ms": round(float(np.percentile(t["step_ms"], 50)), 4),
+            "p99_step_ms": round(float(np.percentile(t["step_ms"], 99)), 4),
+            "steps": steps, "graph_steps": t["graph_steps"], "gpu_launches": t["launches"],
+            "colliding_pairs_per_step": t["found"] / steps, "tree_stats_last_step": last,
+            "stage_ms_per_step": {k: round(v, 4) for k, v in t["stage"].items()},
+            "stage_note": f"CUDA events around each stage, {t['prof_steps']} directly launched steps after the "
+                          f"timed region",
+            "stage_roofline": stage_rooflines(t["stage"], n, p, t["prof"]["m2l"], t["prof"]["p2p_interactions"],
+                                              t["prof"]["col_tests"], hbm, peak_tflops)}
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -216,21 +348,6 @@ def run_gpu(a):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     __graft_entry__.build()
     stream = torch.cuda.current_stream()
-
-    cfgd = workload_config(a)
-    d = diskgen.make_disk(a.n, a.seed + rank)
-    cfg = ncorp.ncorp_config_default()
-    cfg.precision = ncorp.NCORP_MIXED if a.precision == "mixed" else ncorp.NCORP_FP64
-    cfg.leaf_size = cfgd["leaf_size"]
-    cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = cfgd["gravity_thresholds"]
-    cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = cfgd["collision_thresholds"]
-    cfg.resolve_f = a.resolve_f
-    ctx = ncorp.ncorp_init(cfg, a.n, local, stream.cuda_stream)
-    pos = torch.tensor(d["pos"], device="cuda")
-    vel = torch.tensor(d["vel"], device="cuda")
-    m = torch.tensor(d["mass"], device="cuda")
-    R = torch.tensor(d["radius"], device="cuda")
-    pairs = torch.empty((1 << 16, 2), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -238,63 +355,58 @@ def run_gpu(a):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step():
-        ncorp.ncorp_step(ctx, pos, vel, m, R, a.n, a.p, a.theta, a.dt)
-
-    for _ in range(max(a.warmup, 3)):
-        step()
+    hbm = measured_hbm_gbs()
     sampler = ClockSampler(physical_gpu_index(local))
-    barrier()
-    total_ms, launches, found, graph_steps = 0.0, 0, 0, 0
-    last_stats = {}
-    interactions, m2l_dir, step_ms = 0, 0, []
-    for _ in range(a.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        step_ms.append(ms)
-        total_ms += ms
-        st = ncorp.ncorp_stats(ctx)
-        launches += st["launches"]
-        graph_steps += st["graph"]
-        last_stats = st
-        found += st["col_found"]
-        interactions += st["p2p_interactions"]
-        m2l_dir += st["m2l_directed"]
-    barrier()
+    peaks = {"fp32_tflops": ncorp.ncorp_fma_peak(local, ncorp.NCORP_MIXED, stream.cuda_stream) / 1e12,
+             "fp64_tflops": ncorp.ncorp_fma_peak(local, ncorp.NCORP_FP64, stream.cuda_stream) / 1e12,
+             "hbm_gbs": hbm, "how": "FMA: ncorp_fma_peak (in-bounds FMA chains on every SM, best of 5 ~5 ms "
+                                    "launches, 2 FLOP per FMA); HBM: MEASURED_PEAKS.json copy bandwidth"}
+    peak = peaks["fp32_tflops"] if a.precision == "mixed" else peaks["fp64_tflops"]
+    ctx_args = {"barrier": barrier}
+
+    # ---- the headline: workload 2 (N = 1e5, p = 6, theta_min = 0.5) in the requested precision
+    cfgd = workload_config(a)
+    d = diskgen.make_disk(a.n, a.seed + rank)
+    t = time_disk(a, ncorp, torch, ctx_args, d, a.n, a.p, a.theta, a.precision, a.steps, a.warmup,
+                  min(a.steps, 10), local, stream, flush)
+    head = summarize(a, t, a.n, a.steps, world, dist, hbm, peak, a.p)
+    roofline = near_roofline(t, peak, a.precision, EVAL_DRAM_BYTES_PER_LAUNCH if a.precision == "mixed" else None)
+
+    extra = {}
+    if not a.headline_only:
+        # ---- the same disk in the other precision (FP64 is the paper's arithmetic; workload 2 names both)
+        other = "fp64" if a.precision == "mixed" else "mixed"
+        opeak = peaks["fp64_tflops"] if other == "fp64" else peaks["fp32_tflops"]
+        osteps = max(5, a.steps // 10)
+        t2 = time_disk(a, ncorp, torch, ctx_args, d, a.n, a.p, a.theta, other, osteps, 3, min(osteps, 5),
+                       local, stream, flush)
+        extra[other] = {"config": workload_config(a, precision=other), **summarize(a, t2, a.n, osteps, world, dist,
+                                                                                     hbm, opeak, a.p),
+                        "roofline": near_roofline(t2, opeak, other, None)}
+        # ---- workload 3: N = 1e6 (seed 3), p = 4, theta_min = 0.6, mixed, 100 steps
+        n3 = 1_000_000
+        d3 = diskgen.make_disk(n3, 3 + rank)
+        t3 = time_disk(a, ncorp, torch, ctx_args, d3, n3, 4, 0.6, "mixed", a.steps3, 3, 5, local, stream, flush)
+        extra["config3"] = {"config": workload_config(a, n=n3, seed=3, p=4, theta=0.6, precision="mixed"),
+                            **summarize(a, t3, n3, a.steps3, world, dist, hbm, peaks["fp32_tflops"], 4),
+                            "roofline": near_roofline(t3, peaks["fp32_tflops"], "mixed", None)}
     clocks = sampler.stop()
-    # ---- stage times: a few more steps after the timed region, launched
-    # directly (profiled steps are never replayed from a graph) with CUDA
-    # events around every stage on the stream it runs on.
-    ncorp.ncorp_profile(ctx, True)
-    stage, prof_steps, prof_inter = {}, min(a.steps, 10), 0
-    for _ in range(prof_steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        step()
-        prof_inter += ncorp.ncorp_stats(ctx)["p2p_interactions"]
-        for k, v in ncorp.ncorp_stage_times(ctx).items():
-            stage[k] = stage.get(k, 0.0) + v
-    ncorp.ncorp_profile(ctx, False)
-    t_max = slowest_rank(dist, total_ms, world)
-    value = replica_throughput(a.n, a.steps, world, t_max * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers: every step
     # copies the state in (positions, velocities, masses, radii), runs the step
     # from it and copies the new state and the colliding pairs out.
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED if a.precision == "mixed" else ncorp.NCORP_FP64
+    cfg.leaf_size = cfgd["leaf_size"]
+    cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = cfgd["gravity_thresholds"]
+    cfg.resolve_f = a.resolve_f
+    ctx = ncorp.ncorp_init(cfg, a.n, local, stream.cuda_stream)
     hp = torch.tensor(d["pos"]).pin_memory()
     hv = torch.tensor(d["vel"]).pin_memory()
     hm = torch.tensor(d["mass"]).pin_memory()
     hR = torch.tensor(d["radius"]).pin_memory()
     hpairs = torch.empty((1 << 16, 2), dtype=torch.int64).pin_memory()
     e2e_steps = max(3, min(a.steps, 10))
-    ncorp.ncorp_reset(ctx)
     ncorp.ncorp_step(ctx, hp, hv, hm, hR, a.n, a.p, a.theta, a.dt)
     barrier()
     t0 = time.perf_counter()
@@ -305,50 +417,29 @@ def run_gpu(a):
         npairs += ncorp.ncorp_collisions(ctx, hpairs, hpairs.shape[0])
     barrier()
     e2e_s = slowest_rank(dist, time.perf_counter() - t0, world)
-    e2e = {"value": replica_throughput(a.n, e2e_steps, world, e2e_s), "unit": UNIT,
+    e2e = {"value": round(replica_throughput(a.n, e2e_steps, world, e2e_s), 1), "unit": UNIT,
            "h2d_bytes_per_step": a.n * (24 + 24 + 8 + 8),
            "d2h_bytes_per_step": a.n * (24 + 24) + 16 * (npairs // e2e_steps),
            "note": "state uploaded from pinned host memory every step (so the step also recomputes the "
                    "acceleration of the uploaded state), new state and pairs read back"}
     ncorp.ncorp_free(ctx)
 
-    # ---- roofline of the dominant kernel (the near-field direct sums, k_eval: FP32 ALU bound).
-    # Algorithmic FLOPs per launch: 24 per directed moonlet pair (9 adds for the
-    # double-float separation, 3 mul + 2 add for r^2, rsqrt, 3 mul for mu/r^3,
-    # 3 FMA into the sums); every unordered pair counted by the walk is
-    # evaluated from both sides.
-    near_ms = stage.get("near", 0.0) / prof_steps
-    directed = 2.0 * prof_inter / prof_steps
-    flops_near = 24.0 * directed
-    achieved = flops_near / (near_ms * 1e-3) / 1e12 if near_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_eval (near-field direct sums per leaf)",
-                "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": EVAL_DRAM_BYTES_PER_LAUNCH,
-                "flops_per_launch": flops_near, "directed_pairs_per_launch": directed,
-                "avg_launch_ms": round(near_ms, 4),
-                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 FP32 lanes x 2 FLOPs x 2.07 GHz (not measured)"}
-    last = {k: last_stats[k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self",
-                                      "p2p_interactions", "walk_iters", "col_pairs", "col_self", "col_tests",
-                                      "col_iters")}
-
-    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
-           "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4),
-           "p50_step_ms": round(float(np.percentile(step_ms, 50)), 4),
-           "p99_step_ms": round(float(np.percentile(step_ms, 99)), 4),
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": max(a.warmup, 3), "ms_per_step": head["ms_per_step"],
+           "p50_step_ms": head["p50_step_ms"], "p99_step_ms": head["p99_step_ms"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
            "data": "synthetic (seeded moonlet disk shaped like the paper's)", "config": cfgd,
-           "stage_ms_per_step": {k: round(v / prof_steps, 4) for k, v in stage.items()},
-           "stage_note": f"CUDA events around each stage, {prof_steps} directly launched steps after the timed region",
-           "graph_steps": graph_steps,
-           "colliding_pairs_per_step": found / a.steps, "tree_stats_last_step": last, "gpu_launches": launches,
-           "clocks": clocks, "e2e": e2e, "roofline": roofline,
-           "stage_roofline": stage_rooflines({k: v / prof_steps for k, v in stage.items()}, a.n, a.p,
-                                             last_stats["m2l"], prof_inter / prof_steps, last_stats["col_tests"],
-                                             measured_hbm_gbs(), FP32_PEAK_TFLOPS),
-           "stage_roofline_note": "per stage of one step against the measured HBM copy bandwidth or the FP32 "
-                                  "peak; the working set (~20 MB at N = 1e5) stays in L2, and walk/descend are "
-                                  "latency-bound chains"}
+           "gpu_launches": head["gpu_launches"], "graph_steps": head["graph_steps"],
+           "colliding_pairs_per_step": head["colliding_pairs_per_step"],
+           "tree_stats_last_step": head["tree_stats_last_step"],
+           "stage_ms_per_step": head["stage_ms_per_step"], "stage_note": head["stage_note"],
+           "clocks": clocks, "e2e": e2e, "roofline": roofline, "peaks": peaks,
+           "stage_roofline": head["stage_roofline"],
+           "stage_roofline_note": "per stage of one step against the measured HBM copy bandwidth or the measured "
+                                  "FMA peak of the stage's precision; at N = 1e5 the working set (~20 MB) stays "
+                                  "in L2, and walk/descend are latency-bound chains",
+           **extra}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, cfgd, d)
     if rank == 0:
@@ -376,14 +467,48 @@ def time_oracle_steps(a, cfgd, d, nsteps):
     return time.perf_counter() - t0
 
 
+def _oracle_step_worker(args):
+    """One oracle SBAB1 step of a disk from the generator (runs in a spawned process)."""
+    n, seed, p, theta, dt, leaf, grav, col = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2310_20374_gb300 import diskgen
+    d = diskgen.make_disk(n, seed)
+    P = oracle.params(p=p, theta=theta, leaf_size=leaf, gravity_thresholds=tuple(grav), collision_thresholds=tuple(col))
+    acc0, _ = oracle.falcon_accel(P, d["pos"], d["mass"])
+    acc0 = acc0 + oracle.external_accel(P, d["pos"])
+    t0 = time.perf_counter()
+    oracle.kdk(P, d["pos"], d["vel"], d["mass"], d["radius"], dt, 1, acc0=acc0)
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(a, cfgd, d):
+    """The oracle as it stands on this host: one SBAB1 step of the same disk on one core, and one step of an
+    independent disk per core at once (the all-core figure: disks one per core, SURVEY's CPU baseline)."""
+    import multiprocessing as mp
+
     import oracle
     oracle.build()
     secs = time_oracle_steps(a, cfgd, d, 1)
+    cores = host_cores()
+    ncores = int(cores.get("nproc") or 1)
+    job = [(a.n, a.seed + 1000 + k, a.p, a.theta, a.dt, cfgd["leaf_size"], cfgd["gravity_thresholds"],
+            cfgd["collision_thresholds"]) for k in range(ncores)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        per = pool.map(_oracle_step_worker, job)
+    wall = time.perf_counter() - t0
+    all_core = a.n * ncores / max(per)
     return {"value": round(a.n / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"1 SBAB1 step of the same {a.n}-moonlet disk (falcON p={a.p} + tree collision search), "
                       f"plain C FP64 oracle, single thread; acceleration of the start state computed outside "
-                      f"the timing", "seconds": round(secs, 3)}
+                      f"the timing", "seconds": round(secs, 3),
+            "all_cores": {"value": round(all_core, 1), "unit": UNIT, "cores": ncores,
+                          "sample": f"{ncores} independent {a.n}-moonlet disks, one oracle process per core, one "
+                                    f"step each at once; value = moonlet-steps / the slowest process's step time",
+                          "slowest_s": round(max(per), 3), "fastest_s": round(min(per), 3),
+                          "wall_s_with_setup": round(wall, 2)},
+            "host": cores}
 
 
 def run_reference(a):
@@ -393,10 +518,10 @@ def run_reference(a):
     from paper_2310_20374_gb300 import diskgen
     import oracle
     oracle.build()
-    cfgd = workload_config(a)
     # bounded sample: a disk small enough that warmup + steps end within ~2 minutes
     per_particle_s = 6e-5
     n = int(min(a.n, max(2000, 120.0 / (per_particle_s * (a.steps + max(a.warmup, 3) + 1)))))
+    cfgd = workload_config(a, n=n)
     d = diskgen.make_disk(n, a.seed)
     import copy
     b = copy.copy(a)
@@ -410,7 +535,8 @@ def run_reference(a):
            "data": "synthetic (seeded moonlet disk shaped like the paper's)", "config": cfgd,
            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{a.steps} SBAB1 steps of a {n}-moonlet disk from the same generator "
-                                      f"(the workload's disk scaled to keep the run within minutes)"},
+                                      f"(the workload's {a.n}-moonlet disk scaled down to keep the run within "
+                                      f"minutes)", "host": host_cores()},
            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

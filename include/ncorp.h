@@ -96,9 +96,19 @@ void ncorp_config_default(ncorp_config *cfg);
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream); the
  * context allocates its own device workspace (it grows on demand).
- * The environment variable NCORP_RADIX_EPOCH_LIMIT (an integer >= 1, read
- * here) lowers the number of radix sorts after which the context's sort
- * scratch is cleared (default 2^28); it exists to test that path.
+ * Environment variables read here (all optional):
+ *   NCORP_RADIX_EPOCH_LIMIT (>= 1) lowers the number of radix sorts after
+ *     which the context's sort scratch is cleared (default 2^28);
+ *   NCORP_WAIT_LIMIT_MS (1..60000, default 1000) bounds every device-side
+ *     grid-barrier wait of the context: a wait that runs longer makes the
+ *     call fail with NCORP_ETIMEOUT instead of hanging;
+ *   NCORP_TEST_STALL_STEP=k makes the k-th ncorp_step of the context wait at
+ *     its grid barriers for an arrival that never comes, so that the step
+ *     fails with NCORP_ETIMEOUT after the wait limit;
+ *   NCORP_TEST_LIST_CAP / NCORP_TEST_PAIR_CAP start the walk lists / the
+ *     colliding-pair buffer at that many entries, so that the first step
+ *     that needs more overflows and is rerun with grown buffers.
+ * The last three exist to test the failure paths and are off by default.
  * Errors: NCORP_EINVAL (null out/cfg, n_max < 1, bad config), NCORP_ECUDA,
  * NCORP_ENOMEM. */
 int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream);
@@ -117,6 +127,10 @@ int ncorp_set_stream(ncorp_ctx *ctx, void *cuda_stream);
  * theta and the context was not used by ncorp_accel/ncorp_collide in between;
  * call ncorp_reset() after changing the arrays' contents yourself.
  * The pairs found are kept for ncorp_collisions().
+ * A step whose internal lists overflow is rerun from the resident state with
+ * grown buffers (invisible to the caller).  A step that fails with
+ * NCORP_ETIMEOUT writes nothing to positions/velocities and drops the
+ * resident state, so the next call re-reads the caller's arrays.
  * Errors: NCORP_EINVAL, NCORP_ECUDA, NCORP_ENOMEM, NCORP_ETIMEOUT. */
 int ncorp_step(ncorp_ctx *ctx, double *positions, double *velocities, const double *masses,
                const double *radii, int64_t n, int p, double theta, double dt);
@@ -329,6 +343,16 @@ void ncorp_batch_free(ncorp_batch *b);
 
 /* Message of the last failure of a batch call (never NULL). */
 const char *ncorp_batch_last_error(const ncorp_batch *b);
+
+/* Measured fused multiply-add throughput of device `device`, the peak the
+ * ALU-bound stages are compared with: FP32 (precision = NCORP_MIXED) or FP64
+ * (NCORP_FP64).  Runs independent FMA chains on every SM for about 5 ms, six
+ * times on cuda_stream (the first a warm-up), and writes the best rate in
+ * FLOP/s (2 per FMA) to *flop_per_s.  Allocates and frees a small output
+ * buffer (grid x block elements; every thread writes only its own element).
+ * Errors: NCORP_EINVAL (NULL output, other precision), NCORP_ENOMEM,
+ * NCORP_ECUDA. */
+int ncorp_fma_peak(int device, int precision, void *cuda_stream, double *flop_per_s);
 
 /* Largest n accepted by ncorp_hilbert_sort_static. */
 #define NCORP_STATIC_MAX_N 65536

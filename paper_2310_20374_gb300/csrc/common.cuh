@@ -115,6 +115,9 @@ struct Ctrl {
     int col_iters;         // collision walk: generations
     unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
     double root[4];        // x_lo, y_lo, z_lo, L
+    unsigned long long wait_ns;   // limit of a grid barrier's wait (0: one second); set once per context
+    int stall;             // nonzero: the grid barriers of this tree set wait for one arrival that never
+                           // comes, so each gives up after wait_ns (failure-path tests; cleared per call)
 };
 
 // order-preserving map double -> uint64 (for atomicMin/atomicMax)
@@ -141,9 +144,12 @@ __device__ __forceinline__ bool aborted(const Ctrl *ctl) {
 // the grid size.  Each block's thread 0 adds its arrival with release
 // semantics and polls with acquire semantics, so the writes of the whole
 // block before the barrier (ordered by __syncthreads) are visible to every
-// block after it.  A wait longer than about a second sets ERR_TIMEOUT and
-// returns false; the kernels then leave, so no launch can hang.  `passed`
-// counts the grid-size steps of the barriers this block has passed.
+// block after it.  A wait longer than ctl->wait_ns (one second when 0) sets
+// ERR_TIMEOUT and returns false; the kernels then leave, so no launch can
+// hang.  `passed` counts the grid-size steps of the barriers this block has
+// passed.  With ctl->stall set the barrier also waits for one arrival that
+// no block makes, so every block gives up after the limit (the host-armed
+// failure of the failure-path tests).
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -168,8 +174,10 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctl, unsigned &passed) {
         red_release_add_u32(&ctl->bar_count, 1u);
         int ok = 1;
         const unsigned long long t0 = global_ns();
-        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(&ctl->bar_count) - passed) < 0; spins++) {
-            if ((spins & 255u) == 255u && global_ns() - t0 > 1000000000ull) {
+        const unsigned long long limit = ctl->wait_ns ? ctl->wait_ns : 1000000000ull;
+        const unsigned target = passed + (ctl->stall ? 1u : 0u);
+        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(&ctl->bar_count) - target) < 0; spins++) {
+            if ((spins & 255u) == 255u && global_ns() - t0 > limit) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
                 ok = 0;
                 break;

@@ -133,6 +133,7 @@ struct ncorp_ctx {
     int *tile_hist = nullptr;        // radix sort: digit histograms, epoch, status words
     int tile_hist_cap = 0;
     unsigned radix_epoch_limit = 0;  // radix tag epochs before the status words are cleared
+    bool radix_dirty = false;        // a call timed out: the next sort clears its scratch first
     double *stage = nullptr;         // [n][3] AoS staging
     double *stage2 = nullptr;
 
@@ -179,6 +180,11 @@ struct ncorp_ctx {
     bool graph_used = false;         // the last call ran a step graph
     cudaStream_t gstream = nullptr;  // stream the step graphs are captured on
     bool profile = false;
+    // failure-path test knobs, read from the environment at ncorp_init (all off by default):
+    // list/pair capacities capped until they first overflow, and the ncorp_step call (1-based) whose
+    // grid barriers wait for an arrival that never comes (each gives up after the wait limit)
+    int test_list_cap = 0, test_pair_cap = 0;
+    long long stall_call = 0, step_calls = 0;
     cudaEvent_t ev[NCORP_NSTAGES][8][2] = {};   // up to 8 intervals per stage per call
     int ev_used[NCORP_NSTAGES] = {0};
     double stage_ms[NCORP_NSTAGES] = {0};
@@ -238,8 +244,10 @@ void launch_sort_pairs(ncorp_ctx *c, int count);
 
 // ---- kdk.cu ----
 void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n);
+// abort_a / abort_b (nullable): error words; the scatter writes nothing when either holds an abort flag
+// (a step that timed out or overflowed leaves the caller's arrays as they were)
 void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm,
-                        double *aos, int n);
+                        double *aos, int n, const int *abort_a = nullptr, const int *abort_b = nullptr);
 // v' = v + h a, x' = x + dt v' and the bounding box of x' into ctl (which
 // must hold an empty box).
 struct KickDriftArgs {
@@ -250,7 +258,8 @@ struct KickDriftArgs {
     Ctrl *ctl;
 };
 void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A);
-void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n);
+void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n,
+                          const int *abort_a = nullptr, const int *abort_b = nullptr);
 void launch_unpack_pairs(ncorp_ctx *c, const uint64_t *packed, int64_t *out, int count);
 
 // host-side error helper used by every launcher

@@ -19,8 +19,15 @@ __global__ void k_aos_to_soa(const double *__restrict__ aos, double *x, double *
     }
 }
 
+__device__ __forceinline__ bool scatter_gated(const int *a, const int *b) {
+    return (a && (*reinterpret_cast<const volatile int *>(a) & ERR_ABORT_MASK)) ||
+           (b && (*reinterpret_cast<const volatile int *>(b) & ERR_ABORT_MASK));
+}
+
 __global__ void k_scatter_aos(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                              const int *__restrict__ perm, double *__restrict__ aos, int n) {
+                              const int *__restrict__ perm, double *__restrict__ aos, int n, const int *abort_a,
+                              const int *abort_b) {
+    if (scatter_gated(abort_a, abort_b)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int u = perm[i];
         aos[3 * u] = x[i];
@@ -94,7 +101,9 @@ __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
 __global__ void k_scatter_state(const double *__restrict__ x, const double *__restrict__ y,
                                 const double *__restrict__ z, const double *__restrict__ vx,
                                 const double *__restrict__ vy, const double *__restrict__ vz,
-                                const int *__restrict__ perm, double *__restrict__ pos, double *__restrict__ vel, int n) {
+                                const int *__restrict__ perm, double *__restrict__ pos, double *__restrict__ vel, int n,
+                                const int *abort_a, const int *abort_b) {
+    if (scatter_gated(abort_a, abort_b)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int u = perm[i];
         pos[3 * u] = x[i];
@@ -114,8 +123,8 @@ void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, do
 }
 
 void launch_scatter_aos(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm,
-                        double *aos, int n) {
-    k_scatter_aos<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, perm, aos, n); c->launches++;
+                        double *aos, int n, const int *abort_a, const int *abort_b) {
+    k_scatter_aos<<<eg(c, n), 256, 0, c->stream>>>(x, y, z, perm, aos, n, abort_a, abort_b); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -124,8 +133,10 @@ void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A) {
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
-void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n) {
-    k_scatter_state<<<eg(c, n), 256, 0, c->stream>>>(S.x, S.y, S.z, S.vx, S.vy, S.vz, S.perm, pos, vel, n);
+void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n, const int *abort_a,
+                          const int *abort_b) {
+    k_scatter_state<<<eg(c, n), 256, 0, c->stream>>>(S.x, S.y, S.z, S.vx, S.vy, S.vz, S.perm, pos, vel, n, abort_a,
+                                                     abort_b);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }

@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -210,10 +211,15 @@ void ensure_tree_capacity(ncorp_ctx *c, int n) {
     ensure_items(c);
     const int cc = c->cells.cap;
     int front = std::max(1 << 16, 48 * cc), m2l = std::max(1 << 16, 64 * cc), p2p = std::max(1 << 16, 48 * cc);
+    if (c->test_list_cap > 0) {   // failure-path tests: lists too small until they first overflow
+        m2l = std::min(m2l, c->test_list_cap);
+        p2p = std::min(p2p, c->test_list_cap);
+    }
     if (c->wl.front_cap < front || c->wl.m2l_cap < m2l || c->wl.p2p_cap < p2p || c->wl.self_cap < cc)
         alloc_lists(c, std::max(front, c->wl.front_cap), std::max(m2l, c->wl.m2l_cap), std::max(p2p, c->wl.p2p_cap),
                     std::max(cc, c->wl.self_cap));
     int pc = std::max(1 << 16, 4 * n);
+    if (c->test_pair_cap > 0) pc = std::min(pc, c->test_pair_cap);
     if (c->pair_cap < pc) alloc_pairs(c, pc);
     ensure_radix_scratch(c, std::max(n, pc));
 }
@@ -265,8 +271,12 @@ bool grow_after(ncorp_ctx *c, int err) {
         self = std::max(2 * self, c->ctl_h->n_self + 1024);
         grew = true;
     }
-    if (grew) alloc_lists(c, front, m2l, p2p, self);
+    if (grew) {
+        alloc_lists(c, front, m2l, p2p, self);
+        c->test_list_cap = 0;
+    }
     if (err & ERR_PAIRS) {
+        c->test_pair_cap = 0;
         alloc_pairs(c, std::max(2 * c->pair_cap, c->ctl_h->n_found + 1024));
         grew = true;
     }
@@ -300,12 +310,13 @@ void upload_scalar(ncorp_ctx *c, const double *user, double *dst, int n) {
     NCORP_CUDA_CHECK(cudaMemcpyAsync(dst, user, sizeof(double) * n, cudaMemcpyDefault, c->stream));
 }
 
+// abort_a / abort_b (nullable): error words that stop the write when they hold an abort flag
 void download_vec(ncorp_ctx *c, const double *x, const double *y, const double *z, const int *perm, double *user,
-                  int n, double *stage) {
+                  int n, double *stage, const int *abort_a = nullptr, const int *abort_b = nullptr) {
     if (is_device_ptr(c, user)) {
-        launch_scatter_aos(c, x, y, z, perm, user, n);
+        launch_scatter_aos(c, x, y, z, perm, user, n, abort_a, abort_b);
     } else {
-        launch_scatter_aos(c, x, y, z, perm, stage, n);
+        launch_scatter_aos(c, x, y, z, perm, stage, n, abort_a, abort_b);
         NCORP_CUDA_CHECK(cudaMemcpyAsync(user, stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     }
 }
@@ -347,10 +358,16 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     ctl->n_m2p = 0;
     ctl->bar_count = 0;
     ctl->resort_ok = 0;
+    if (!fold) ctl->stall = 0;   // a set recycled within a call (fold) keeps the call's armed stall
     for (int k = 0; k < 3; k++) {
         ctl->bbox[k] = ~0ull;
         ctl->bbox[3 + k] = 0ull;
     }
+}
+
+__global__ void k_arm_stall(Ctrl *ctl, Ctrl *ctl2) {
+    ctl->stall = 1;
+    ctl2->stall = 1;
 }
 
 __global__ void k_reset_ctl(Ctrl *ctl, Ctrl *ctl2, int *fold, int *clear) {
@@ -423,7 +440,9 @@ int finish(ncorp_ctx *c, bool both = false) {
             }
             c->stage_ms[i] = sum;
         }
-    return c->ctl_h->err | (both ? (c->alt.ctl_h->err | *c->err_acc_h) : 0);
+    const int err = c->ctl_h->err | (both ? (c->alt.ctl_h->err | *c->err_acc_h) : 0);
+    if (err & ERR_TIMEOUT) c->radix_dirty = true;
+    return err;
 }
 
 // keys of (x from sx, v from sv, m/R/perm from sr) -> radix sort -> gather into dst -> build
@@ -686,7 +705,8 @@ void resident_step_body(ncorp_ctx *c, double *pos, double *vel, int n, int p, do
     enqueue_kdk(c, n, p, theta, dt, true);
     Stage st(c, NCORP_STAGE_KDK);
     ParticleSet &Cn = c->Cset;
-    launch_scatter_state(c, Cn, dev_x ? pos : c->stage, dev_v ? vel : c->stage2, n);
+    // a step that aborted (overflow, time-out) writes nothing to the caller's arrays
+    launch_scatter_state(c, Cn, dev_x ? pos : c->stage, dev_v ? vel : c->stage2, n, &c->ctl->err, &c->alt.ctl->err);
 }
 
 // Enqueues a resident step on c->stream through a cached graph (capturing it
@@ -751,6 +771,16 @@ bool resident_step_graph(ncorp_ctx *c, double *pos, double *vel, int n, int p, d
 
 constexpr int MAX_RETRIES = 6;
 
+// integer environment variable, clamped to [lo, hi]; dflt when unset or not a number
+long long env_int(const char *name, long long dflt, long long lo, long long hi) {
+    const char *v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    char *end = nullptr;
+    const long long x = std::strtoll(v, &end, 10);
+    if (end == v) return dflt;
+    return std::min(hi, std::max(lo, x));
+}
+
 #define NCORP_API_BODY(ctxp, ...)                                                               \
     try {                                                                                       \
         NCORP_CUDA_CHECK(cudaSetDevice((ctxp)->device));                                        \
@@ -799,11 +829,21 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         int coop = 0;
         NCORP_CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
         if (!coop) throw CudaError(cudaErrorNotSupported, "cooperative launch unsupported", __FILE__, __LINE__);
+        // Failure-path test knobs (off unless set): NCORP_WAIT_LIMIT_MS bounds every grid barrier's wait
+        // (default 1000), NCORP_TEST_STALL_STEP=k makes the k-th ncorp_step's barriers wait for an arrival
+        // that never comes, NCORP_TEST_LIST_CAP / NCORP_TEST_PAIR_CAP start the walk lists / pair buffer at
+        // that many entries so that they overflow and grow.
+        const unsigned long long wait_ns = static_cast<unsigned long long>(env_int("NCORP_WAIT_LIMIT_MS", 1000, 1,
+                                                                                    60000)) * 1000000ull;
+        c->stall_call = env_int("NCORP_TEST_STALL_STEP", 0, 0, 1 << 30);
+        c->test_list_cap = static_cast<int>(env_int("NCORP_TEST_LIST_CAP", 0, 0, 1 << 30));
+        c->test_pair_cap = static_cast<int>(env_int("NCORP_TEST_PAIR_CAP", 0, 0, 1 << 30));
         for (int set = 0; set < 2; set++) {
             dalloc(c->ctl, 1);
             NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
             std::memset(c->ctl_h, 0, sizeof(Ctrl));
-            NCORP_CUDA_CHECK(cudaMemset(c->ctl, 0, sizeof(Ctrl)));
+            c->ctl_h->wait_ns = wait_ns;
+            NCORP_CUDA_CHECK(cudaMemcpy(c->ctl, c->ctl_h, sizeof(Ctrl), cudaMemcpyHostToDevice));
             swap_sets(c);
         }
         dalloc(c->work_counter, 4);
@@ -1005,10 +1045,11 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
         choose_parameters(c, p);
         bool have = resident && c->have_state;
         bool tree = resident;
+        const bool stall = c->stall_call > 0 && ++c->step_calls == c->stall_call;
         for (int attempt = 0;; attempt++) {
             ensure_both_capacities(c, n);
             c->graph_used = false;
-            if (attempt == 0 && have && tree && c->graphs_on && !c->profile && c->cfg.star_mass == 0.0) {
+            if (attempt == 0 && have && tree && c->graphs_on && !c->profile && c->cfg.star_mass == 0.0 && !stall) {
                 const bool dev_x = is_device_ptr(c, positions), dev_v = is_device_ptr(c, velocities);
                 c->graph_used = resident_step_graph(c, positions, velocities, n, p, theta, dt, dev_x, dev_v);
                 if (c->graph_used && !dev_x)
@@ -1020,6 +1061,11 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
             }
             if (!c->graph_used) {
                 reset_ctls(c);
+                if (stall && attempt == 0) {   // failure-path test: this step's grid barriers give up
+                    k_arm_stall<<<1, 1, 0, c->stream>>>(c->ctl, c->alt.ctl);
+                    c->launches++;
+                    NCORP_CUDA_CHECK(cudaGetLastError());
+                }
                 if (!have) {   // read the caller's state (caller order)
                     Stage st(c, NCORP_STAGE_KDK);
                     ParticleSet &A = c->A;
@@ -1038,8 +1084,10 @@ int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double
                 enqueue_kdk(c, n, p, theta, dt, true);
                 Stage st(c, NCORP_STAGE_KDK);
                 ParticleSet &Cn = c->Cset;
-                download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage);
-                download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2);
+                // nothing is written to the caller's arrays if the step aborted
+                download_vec(c, Cn.x, Cn.y, Cn.z, Cn.perm, positions, n, c->stage, &c->ctl->err, &c->alt.ctl->err);
+                download_vec(c, Cn.vx, Cn.vy, Cn.vz, Cn.perm, velocities, n, c->stage2, &c->ctl->err,
+                             &c->alt.ctl->err);
             }
             const int err = finish(c, true);
             // the current tree set now holds the new tree, the other one A's tree
@@ -1573,6 +1621,7 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
         ncorp_ctx *c = d.c;
         b->launches += c->launches;
         const int err = c->ctl_h->err | c->alt.ctl_h->err | *c->err_acc_h;
+        if (err & ERR_TIMEOUT) c->radix_dirty = true;
         if (err == 0) {
             c->n_found = c->cfg.collisions ? c->alt.ctl_h->n_found : 0;
             c->pairs_sorted = false;

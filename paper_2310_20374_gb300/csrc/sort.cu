@@ -429,8 +429,12 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
                 if (i < n) {
                     const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
                     const int pos = s_start[d] + s_excl[d] + s_cnt[w][d] + rank[r];
-                    kout[pos] = kk[r];
-                    vout[pos] = vv[r];
+                    // always in range for a consistent prefix; a look-back that gave up (ERR_TIMEOUT, the
+                    // call fails) must not write outside the arrays
+                    if (static_cast<unsigned>(pos) < static_cast<unsigned>(n)) {
+                        kout[pos] = kk[r];
+                        vout[pos] = vv[r];
+                    }
                 }
             }
             __syncthreads();
@@ -492,6 +496,13 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
 static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                             int n, int bits) {
     ensure_radix_scratch(c, n);
+    if (c->radix_dirty) {
+        // A sort of an earlier call may have stopped at a timed-out barrier before advancing the epoch,
+        // leaving counts in the histograms the next sort would take as zeroed: start from clean scratch
+        // (epoch 0, zero histograms, status words with tag 0, which no sort uses).
+        NCORP_CUDA_CHECK(cudaMemsetAsync(c->tile_hist, 0, sizeof(int) * c->tile_hist_cap, c->stream));
+        c->radix_dirty = false;
+    }
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
     RadixArgs A;

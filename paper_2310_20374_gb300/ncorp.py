@@ -75,6 +75,7 @@ def load(path: str | None = None):
     L.ncorp_profile.argtypes = [vp, ip]
     L.ncorp_stage_times.argtypes = [vp, C.POINTER(dbl), ip]
     L.ncorp_hilbert_sort_static.argtypes = [vp, i64, vp, vp, vp]
+    L.ncorp_fma_peak.argtypes = [ip, ip, vp, C.POINTER(dbl)]
     L.ncorp_batch_create.argtypes = [C.POINTER(vp), C.POINTER(ncorp_config), C.c_size_t, vp]
     L.ncorp_batch_add_disk.argtypes = [vp, vp, vp, vp, vp, i64, ip, dbl, dbl, C.POINTER(C.c_int32)]
     L.ncorp_batch_run.argtypes = [vp, ip]
@@ -92,7 +93,7 @@ def load(path: str | None = None):
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
                  "ncorp_accel_standard", "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
-                 "ncorp_hilbert_sort_static", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
+                 "ncorp_hilbert_sort_static", "ncorp_fma_peak", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
                  "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -343,6 +344,15 @@ def ncorp_hilbert_sort_static(positions, n, keys, order, stream=None):
                NCORP_ETIMEOUT: "grid barrier timed out", NCORP_ECUDA: "CUDA call failed"}.get(st, "")
         raise NcorpError(st, why)
     return st
+
+
+def ncorp_fma_peak(device=0, precision=NCORP_MIXED, stream=None) -> float:
+    """Measured FMA throughput in FLOP/s: FP32 (NCORP_MIXED) or FP64 (NCORP_FP64)."""
+    out = C.c_double(0.0)
+    st = load().ncorp_fma_peak(int(device), int(precision), _ptr(stream), C.byref(out))
+    if st != NCORP_OK:
+        raise NcorpError(st, "ncorp_fma_peak failed")
+    return float(out.value)
 
 
 def ncorp_free(ctx):

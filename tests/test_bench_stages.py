@@ -23,7 +23,7 @@ STAGES = {"sort": 0.0948, "build": 0.0893, "climb": 0.1651, "walk": 0.1361, "m2l
 
 def test_stage_rooflines_arithmetic():
     n, m2l, inter, tests = 100_000, 137_116, 57_122_097, 22_217_601
-    out = bench.stage_rooflines(STAGES, n, 6, m2l, inter, tests, 6777.6, 80.5)
+    out = bench.stage_rooflines(STAGES, n, 6, m2l, inter, tests, 6777.6, 72.6)
     assert set(out) == set(STAGES)
     kdk = out["kdk"]
     assert kdk["bound"] == "hbm" and kdk["unit"] == "GB/s"
@@ -31,10 +31,12 @@ def test_stage_rooflines_arithmetic():
     assert kdk["achieved"] == pytest.approx(gbs, abs=0.05)
     assert kdk["frac"] == pytest.approx(gbs / 6777.6, abs=1e-4)
     near = out["near"]
-    assert near["bound"] == "alu" and near["flops_per_step"] == 48.0 * inter
-    assert near["achieved"] == pytest.approx(48.0 * inter / 0.1912e-3 / 1e12, abs=1e-3)
+    # the method's own counts (30 FLOPs per unordered direct pair, 3.2e3 per unordered M2L pair at p = 6,
+    # 30 per collision candidate), whatever the kernels evaluate
+    assert near["bound"] == "alu" and near["flops_per_step"] == 30.0 * inter
+    assert near["achieved"] == pytest.approx(30.0 * inter / 0.1912e-3 / 1e12, abs=1e-3)
     assert out["m2l"]["flops_per_step"] == 3200.0 * m2l
-    assert out["collide"]["flops_per_step"] == 15.0 * tests
+    assert out["collide"]["flops_per_step"] == 30.0 * tests
     assert out["walk"] == {"bound": "latency", "ms": 0.1361}
     assert out["descend"]["bound"] == "latency"
     for v in out.values():
@@ -56,3 +58,16 @@ def test_measured_hbm_bandwidth_or_fallback(tmp_path, monkeypatch):
     assert bench.measured_hbm_gbs() == 6800.0
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.5}))
     assert bench.measured_hbm_gbs() == 7000.5
+
+
+def test_near_roofline_counts_unordered_pairs():
+    t = {"stage": {"near": 0.2}, "prof": {"p2p_interactions": 5e7, "m2l": 0, "col_tests": 0}}
+    r = bench.near_roofline(t, 70.0, "mixed", None)
+    assert r["flops_per_launch"] == 30.0 * 5e7
+    assert r["achieved"] == pytest.approx(30.0 * 5e7 / 0.2e-3 / 1e12, abs=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / 70.0, abs=1e-4) and r["traffic"] is None
+
+
+def test_host_cores_reports_nproc():
+    h = bench.host_cores()
+    assert h["nproc"] == os.cpu_count()

@@ -6,11 +6,12 @@
      benchmark's workload, in the launch configuration the benchmark times
      (leaf size 64, thresholds (256, 256, 512), collisions (12, 0, 16)); one
      force evaluation each and one full step in FP64, against the oracle.
-  3. N = 1e6 disk (seed 3), p = 4, theta_min = 0.6, mixed: too large for the
-     oracle's falcON in a test, so the outputs the oracle can produce at this
-     size are compared exactly (keys, order, cells, climb geometry, the
-     colliding pairs) and the accelerations through properties that hold at
-     any size (momentum, error against direct summation on a seeded sample).
+  3. N = 1e6 disk (seed 3), p = 4, theta_min = 0.6, mixed: keys, order,
+     cells, climb geometry and the colliding pairs against the oracle
+     exactly; the mutual accelerations against the oracle's falcON per
+     moonlet (2e-5) with equal walk decision counts (one oracle evaluation
+     at this size takes about 15 s); momentum and the error against direct
+     summation on a seeded sample.
 """
 import numpy as np
 import pytest
@@ -168,6 +169,11 @@ def test_disk_1e6_p4_mixed_tree_collisions_and_accuracy():
     assert st["cells"] == nc
     ref_pairs, _ = oracle.collide_tree(P, d["pos"], d["vel"], d["radius"], dt)
     assert np.array_equal(pairs[:k], ref_pairs)
+    # element-wise parity with the oracle's falcON at the full size, same walk decisions
+    ref, ost = oracle.falcon_accel(P, d["pos"], d["mass"])
+    assert all(st[key] == ost[key] for key in DECISIONS), {key: (st[key], ost[key]) for key in DECISIONS}
+    e = rel_err(mut, ref)
+    assert e.max() <= MIXED_TOL, (e.max(), np.median(e))
     # momentum: the symmetric M2L and the pairwise near field conserve it up to FP32 rounding
     f = d["mass"][:, None] * mut
     assert np.linalg.norm(f.sum(axis=0)) <= 1e-6 * np.linalg.norm(f, axis=1).sum()
