@@ -116,6 +116,7 @@ struct Ctrl {
     unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
     double root[4];        // x_lo, y_lo, z_lo, L
     unsigned long long wait_ns;   // limit of a grid barrier's wait (0: one second); set once per context
+    unsigned desc_epoch;   // epoch of the current descent (advanced by every M2L launch; never reset)
     int stall;             // nonzero: the grid barriers of this tree set wait for one arrival that never
                            // comes, so each gives up after wait_ns (failure-path tests; cleared per call)
 };

@@ -48,6 +48,7 @@ struct Cells {
     int *maker = nullptr;     // [cap] scratch of the build: block that made the cell
     int *before = nullptr;    // [cap] scratch of the build: children of its maker's earlier cells
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels
+    unsigned *done = nullptr; // [cap] descent: epoch in which the cell's complete expansion was written
 };
 
 struct WalkLists {
@@ -216,8 +217,8 @@ void launch_walk(ncorp_ctx *c, bool gravity);
 
 // ---- m2l.cu / eval.cu ----
 void launch_m2l(ncorp_ctx *c, int p, bool mixed);
-// complete local expansions of the leaves, or of every cell (all_cells)
-void launch_descend(ncorp_ctx *c, int p, bool mixed, bool all_cells = false);
+// complete local expansions of every cell (after launch_m2l, which opens the descent's epoch)
+void launch_descend(ncorp_ctx *c, int p, bool mixed);
 struct ExtForce {
     double GMc;            // G * central mass
     double star_k;         // G M_star / r_star^3 (0: off)

@@ -85,33 +85,37 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
 }
 
 // ---------------------------------------------------------------------------
-// Tree descent (Sect. 3.4.3).  The descent adds to every cell its parent's
-// complete local expansion translated to the cell's centre, from the root
-// down.  A translation (Eq. shifting) re-expands a polynomial of degree p
-// about a new point, which is exact, and translations compose, so the
-// complete expansion of cell c is the sum of the own M2L expansions of c and
-// of all its ancestors a, each translated straight from s_a to s_c:
+// Tree descent (Sect. 3.4.3, Eq. shifting): every cell's complete local
+// expansion is its own M2L sum plus its parent's complete expansion
+// translated to the cell's centre,
 //   C-hat_alpha(c) = C-hat_alpha(c, own)
-//       + sum_a (rho_c/rho_a)^|alpha| sum_beta C-hat_{alpha+beta}(a, own) (h_a)^beta / beta!,
-//   h_a = (s_c - s_a)/rho_a.
-// Every cell is thus independent of the others: one warp per cell, lanes
-// over the output coefficients, with no level-by-level barrier.  The result
-// goes to Cf (Ch keeps the own M2L sums).  A step needs the leaves' only
-// (L2P evaluates at the leaves): the other cells are completed on request.
+//       + (rho_c/rho_a)^|alpha| sum_beta C-hat_{alpha+beta}(a) (h)^beta / beta!,
+//   h = (s_c - s_a)/rho_a,  a = parent(c),
+// from the root down: one translation per cell.  The result goes to Cf (Ch
+// keeps the own M2L sums).
 //
-// The inner sum factorises over the axes (beta! = bx! by! bz!), so a
-// translation is done as three one-dimensional shifts, along x, y, z in
-// turn: D_gamma = sum_k C_{gamma + k e_axis} h_axis^k / k!, with
-// coefficients beyond order p taken as zero.
+// One pass, no level barriers: warps claim cells in increasing index order
+// (cells are level-major, so a parent always precedes its children) and a
+// warp waits only for its cell's parent, whose warp claimed it earlier and is
+// therefore running; the earliest unfinished cell always has its parent done,
+// so the pass always advances.  A cell is published by its `done` word (the
+// epoch of this descent, advanced by the M2L launch that precedes it), with
+// release/acquire ordering; the wait is bounded (ERR_TIMEOUT) and gives up as
+// soon as the call has aborted.
+//
+// A translation is done as three one-dimensional shifts, along x, y, z in
+// turn (beta! = bx! by! bz!): D_gamma = sum_k C_{gamma + k e_axis} h_axis^k / k!,
+// with coefficients beyond order p taken as zero.
 // ---------------------------------------------------------------------------
 struct DescendArgs {
     const int *parent;
-    const int *leaves;         // the cells to complete: the leaves (L2P needs only theirs), or all when null
     const float4 *gh, *gl;
     const double *sx, *sy, *sz, *rho;
     const void *Ch;
     void *Cf;
-    const Ctrl *ctl;
+    unsigned *done;            // [cells]: epoch of the descent that completed the cell
+    int *work;                 // claim counter, zeroed by the M2L launch
+    Ctrl *ctl;                 // desc_epoch: this descent's epoch (advanced by the M2L launch)
 };
 
 constexpr int DESC_WARPS = 8;
@@ -134,6 +138,16 @@ __device__ __forceinline__ real shift_axis(const real *src, const real (&w)[P + 
     return s;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32_any(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <int P, typename real>
 __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
     constexpr int NC = num_c(P);
@@ -143,11 +157,12 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
     __shared__ real s_B[DESC_WARPS][NC];
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const real *Ch = static_cast<const real *>(A.Ch);
     real *Cf = static_cast<real *>(A.Cf);
     real *sa = s_A[wl], *sb = s_B[wl];
-    const int nitems = A.leaves ? A.ctl->n_leaves : A.ctl->n_cells;
+    const unsigned ep = *reinterpret_cast<const volatile unsigned *>(&A.ctl->desc_epoch);
+    const unsigned long long limit = A.ctl->wait_ns ? A.ctl->wait_ns : 1000000000ull;
+    const int ncells = A.ctl->n_cells;
     int on[PER], okk[PER], oc[PER];
 #pragma unroll
     for (int k = 0; k < PER; k++) {
@@ -158,28 +173,35 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
         okk[k] = b0 + c0;
         oc[k] = c0;
     }
-    for (int item = gw; item < nitems; item += nwarps) {
-        const int c = A.leaves ? A.leaves[item] : item;
+    while (true) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(A.work, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= ncells) break;
         real acc[PER];
 #pragma unroll
         for (int k = 0; k < PER; k++) {
             const int i = lane + 32 * k;
             acc[k] = i < NC ? Ch[(size_t)c * NC + i] : real(0);
         }
-        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
-        double csx = 0.0, csy = 0.0, csz = 0.0, crho = 0.0;
-        if constexpr (f32) {
-            ch = A.gh[c];
-            cl = A.gl[c];
-        } else {
-            csx = A.sx[c]; csy = A.sy[c]; csz = A.sz[c]; crho = A.rho[c];
-        }
-        for (int a = A.parent[c]; a >= 0; a = A.parent[a]) {
-            __syncwarp();
-            for (int i = lane; i < NC; i += 32) sa[i] = Ch[(size_t)a * NC + i];
+        const int a = A.parent[c];
+        if (a >= 0) {
+            int ok = 1;
+            if (lane == 0) {
+                const unsigned long long t0 = global_ns();
+                for (unsigned spins = 0; ld_acquire_u32_any(&A.done[a]) != ep; spins++) {
+                    if ((spins & 63u) == 63u && (aborted(A.ctl) || global_ns() - t0 > limit)) {
+                        atomicOr(&A.ctl->err, ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+            for (int i = lane; i < NC; i += 32) sa[i] = __ldcg(&Cf[(size_t)a * NC + i]);
             real hx, hy, hz, ratio;
             if constexpr (f32) {
-                const float4 ah = A.gh[a], al = A.gl[a];
+                const float4 ch = A.gh[c], cl = A.gl[c], ah = A.gh[a], al = A.gl[a];
                 const float ir = 1.0f / al.w;   // exact: rho is a power of two
                 ratio = cl.w * ir;
                 hx = ((ch.x - ah.x) + (cl.x - al.x)) * ir;
@@ -187,10 +209,10 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
                 hz = ((ch.z - ah.z) + (cl.z - al.z)) * ir;
             } else {
                 const double iar = 1.0 / A.rho[a];
-                ratio = crho * iar;
-                hx = (csx - A.sx[a]) * iar;
-                hy = (csy - A.sy[a]) * iar;
-                hz = (csz - A.sz[a]) * iar;
+                ratio = A.rho[c] * iar;
+                hx = (A.sx[c] - A.sx[a]) * iar;
+                hy = (A.sy[c] - A.sy[a]) * iar;
+                hz = (A.sz[c] - A.sz[a]) * iar;
             }
             real wx[P + 1], wy[P + 1], wz[P + 1];
             wx[0] = wy[0] = wz[0] = real(1);
@@ -221,11 +243,17 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
                 for (int q = 0; q < on[k]; q++) s *= ratio;   // (rho_c/rho_a)^n, exact powers of two
                 acc[k] += s;
             }
+            __syncwarp();
         }
 #pragma unroll
         for (int k = 0; k < PER; k++) {
             const int i = lane + 32 * k;
             if (i < NC) Cf[(size_t)c * NC + i] = acc[k];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            st_release_u32(&A.done[c], ep);
         }
     }
 }
@@ -430,7 +458,11 @@ __global__ void __launch_bounds__(32 * FAR_WARPS) k_far(EvalArgs A) {
 
 template <int P, typename real>
 static void descend_t(ncorp_ctx *c, DescendArgs D) {
-    k_descend<P, real><<<8 * c->num_sms, 32 * DESC_WARPS, 0, c->stream>>>(D);
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void *>(k_descend<P, real>), 32 * DESC_WARPS, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_descend<P, real><<<per_sm * c->num_sms, 32 * DESC_WARPS, 0, c->stream>>>(D);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
@@ -451,12 +483,12 @@ static void far_t(ncorp_ctx *c, const EvalArgs &A) {
     c->launches++;
 }
 
-void launch_descend(ncorp_ctx *c, int p, bool mixed, bool all_cells) {
+void launch_descend(ncorp_ctx *c, int p, bool mixed) {
     Cells &C = c->cells;
     DescendArgs D;
     D.parent = C.parent;
-    D.leaves = all_cells ? nullptr : C.leaves; D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
-    D.Ch = C.Ch; D.Cf = C.Cf; D.ctl = c->ctl;
+    D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
+    D.Ch = C.Ch; D.Cf = C.Cf; D.done = C.done; D.work = c->work_counter + 1; D.ctl = c->ctl;
 #define NCORP_DESC_CASE(PP)                      \
     case PP:                                     \
         if (mixed) descend_t<PP, float>(c, D);   \

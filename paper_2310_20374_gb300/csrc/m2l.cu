@@ -37,7 +37,8 @@ struct M2LArgs {
     const float4 *gh, *gl;
     const void *Mh;
     void *Ch;
-    const Ctrl *ctl;
+    Ctrl *ctl;
+    int *desc_work;     // the descent's claim counter, zeroed here
 };
 
 constexpr int M2L_WARPS = 4;
@@ -51,6 +52,10 @@ __global__ void __launch_bounds__(32 * M2L_WARPS, 3) k_m2l(M2LArgs A) {
     const real *__restrict__ Mh = static_cast<const real *>(A.Mh);
     real *Ch = static_cast<real *>(A.Ch);
     if (aborted(A.ctl)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // opens the following descent: fresh epoch, claims from 0
+        A.ctl->desc_epoch += 1u;
+        *A.desc_work = 0;
+    }
     const int lane = threadIdx.x & 31;
     // warps numbered across the blocks first, so that neighbouring targets land on different SMs
     const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -150,6 +155,7 @@ void launch_m2l(ncorp_ctx *c, int p, bool mixed) {
     A.Mh = C.Mh;
     A.Ch = C.Ch;
     A.ctl = c->ctl;
+    A.desc_work = c->work_counter + 1;
 #define NCORP_M2L_CASE(PP)                       \
     case PP:                                     \
         if (mixed) m2l_t<PP, float>(c, A);       \

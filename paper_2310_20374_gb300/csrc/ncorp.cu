@@ -129,6 +129,8 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.blocksum, 8192);
     dalloc(C.maker, cap);
     dalloc(C.before, cap);
+    dalloc(C.done, cap);   // descent epochs start at 1: zeroed words never match
+    NCORP_CUDA_CHECK(cudaMemset(C.done, 0, sizeof(unsigned) * cap));
     WalkLists &W = c->wl;
     dalloc(W.cnt, cap + 1); dalloc(W.offs, cap + 1); dalloc(W.cursor, cap + 1); dalloc(W.p2p_off, cap + 1);
     C.cap = cap;
@@ -1277,10 +1279,7 @@ int ncorp_expansions(ncorp_ctx *c, double *mult, double *local, double *rho, int
         }
         if (local && !c->grav_local)
             return fail(c, NCORP_ESTATE, "the last evaluation (standard tree code) made no local expansions");
-        if (local) {
-            // the evaluation completed the leaves' expansions only: complete every cell's now
-            launch_descend(c, P, c->grav_mixed, true);
-            NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        if (local) {   // the evaluation's descent completed every cell's expansion
             std::vector<double> Cl = fetch(c->cells.Cf, nc_);
             for (int i = 0; i < k; i++)
                 for (int j = 0; j < nc_; j++) {
@@ -1330,7 +1329,7 @@ void ncorp_free(ncorp_ctx *c) {
         dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
         dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
         dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf);
-        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before);
+        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
         WalkLists &W = c->wl;
         dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
         dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
