@@ -44,7 +44,7 @@ struct CollideArgs {
     const int *first, *count;
     const double *x, *y, *z, *vx, *vy, *vz, *R;
     const float4 *hi4, *lo4;
-    const float *rc;           // R + dt |v| rounded up to FP32
+    const float4 *cv;          // velocity rounded to FP32 (xyz), R + dt |v| rounded up to FP32 (w)
     const int *perm;
     double dt;
     uint64_t *pairs;
@@ -70,18 +70,38 @@ __device__ __forceinline__ void test_and_emit(const CollideArgs &A, int u, int v
     }
 }
 
-// A pair can only collide within the step if |dr| <= R1 + R2 + dt |dv| <= rc1 + rc2
-// (rc = R + dt |v|).  The separation is evaluated from the double-float
-// positions (relative error ~1e-7) and compared with (rc1 + rc2)^2 (1 + 2^-10);
-// only pairs inside that bound reach the exact FP64 test, so the pair set is
-// the one the FP64 test alone gives.
+// Two FP32 prefilters in front of the exact FP64 test, each keeping every pair
+// the FP64 test can accept, so the pair set is the one the FP64 test alone
+// gives.
+//  1. A pair can only collide within the step if |dr| <= R1 + R2 + dt |dv| <=
+//     rc1 + rc2 (rc = R + dt |v|): the separation from the double-float
+//     positions (relative error ~1e-7) against (rc1 + rc2)^2 (1 + 2^-10).
+//  2. The trajectories come within R1 + R2 of each other at the impact time
+//     dt_c in [0, dt], so the least distance over [0, dt] is at most R1 + R2:
+//     with t* = clamp(-dr.dv / dv^2, 0, dt), |dr + t* dv|^2 against
+//     (R1 + R2)^2 (1 + 2^-10) plus 2^-12 (|dr|^2 + dt^2 |dv|^2).  The margin
+//     exceeds the FP32 evaluation's error (velocities rounded to FP32: ~1e-7
+//     relative; the terms of the quadratic are bounded by that scale) by
+//     orders of magnitude, and the FP64 predicate's rounding likewise.
 __device__ __forceinline__ bool may_touch(const float4 &h, const float4 &l, float r, const float4 &th,
-                                          const float4 &tl, float tr) {
-    const float dx = (h.x - th.x) + (l.x - tl.x);
-    const float dy = (h.y - th.y) + (l.y - tl.y);
-    const float dz = (h.z - th.z) + (l.z - tl.z);
+                                          const float4 &tl, float tr, float &dx, float &dy, float &dz) {
+    dx = (h.x - th.x) + (l.x - tl.x);
+    dy = (h.y - th.y) + (l.y - tl.y);
+    dz = (h.z - th.z) + (l.z - tl.z);
     const float s = r + tr;
     return dx * dx + dy * dy + dz * dz <= s * s * (1.0f + 0x1p-10f);
+}
+
+__device__ __forceinline__ bool may_meet(float dx, float dy, float dz, const float4 &v, const float4 &tv, float Rs,
+                                         float dt) {
+    const float ux = v.x - tv.x, uy = v.y - tv.y, uz = v.z - tv.z;
+    const float b = dx * ux + dy * uy + dz * uz;
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    const float t = u2 > 0.0f ? fminf(fmaxf(-b / u2, 0.0f), dt) : 0.0f;
+    const float ex = dx + t * ux, ey = dy + t * uy, ez = dz + t * uz;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float margin = 0x1p-12f * (d2 + dt * dt * u2) + 1e-30f;
+    return ex * ex + ey * ey + ez * ez <= Rs * Rs * (1.0f + 0x1p-10f) + margin;
 }
 
 constexpr int COL_WARPS = 8;
@@ -94,8 +114,9 @@ constexpr int COL_WARPS = 8;
 constexpr int COL_STAGE = 64;
 
 __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
-    __shared__ float4 s_h[COL_WARPS][COL_STAGE], s_l[COL_WARPS][COL_STAGE];
-    __shared__ float s_r[COL_WARPS][COL_STAGE];
+    __shared__ float4 s_h[COL_WARPS][COL_STAGE], s_l[COL_WARPS][COL_STAGE], s_v[COL_WARPS][COL_STAGE];
+    __shared__ float s_R[COL_WARPS][COL_STAGE];
+    const float dtf = static_cast<float>(A.dt) * (1.0f + 0x1p-20f);
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
@@ -120,22 +141,30 @@ __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
             const int T = 1 << lg, G = 32 >> lg, tt = lane & (T - 1), g = lane >> lg;
             const int u = t0 + tt;
             const bool act = tt < m;
-            float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
-            float tr = 0.f;
-            if (act) { th = A.hi4[ft + u]; tl = A.lo4[ft + u]; tr = A.rc[ft + u]; }
+            float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th, tv = th;
+            float tR = 0.f;
+            if (act) {
+                th = A.hi4[ft + u];
+                tl = A.lo4[ft + u];
+                tv = A.cv[ft + u];
+                tR = static_cast<float>(A.R[ft + u]);
+            }
             for (int j0 = 0; j0 < nsrc; j0 += COL_STAGE) {
                 const int lim = min(COL_STAGE, nsrc - j0);
                 __syncwarp();
                 for (int k = lane; k < lim; k += 32) {
                     s_h[wl][k] = A.hi4[fs + j0 + k];
                     s_l[wl][k] = A.lo4[fs + j0 + k];
-                    s_r[wl][k] = A.rc[fs + j0 + k];
+                    s_v[wl][k] = A.cv[fs + j0 + k];
+                    s_R[wl][k] = static_cast<float>(A.R[fs + j0 + k]);
                 }
                 __syncwarp();
                 if (act) {
                     for (int k = g; k < lim; k += G) {
                         const int v = j0 + k;
-                        if ((!self || v > u) && may_touch(s_h[wl][k], s_l[wl][k], s_r[wl][k], th, tl, tr))
+                        float dx, dy, dz;
+                        if ((!self || v > u) && may_touch(s_h[wl][k], s_l[wl][k], s_v[wl][k].w, th, tl, tv.w, dx, dy, dz) &&
+                            may_meet(dx, dy, dz, s_v[wl][k], tv, (s_R[wl][k] + tR) * (1.0f + 0x1p-20f), dtf))
                             test_and_emit(A, ft + u, fs + v);
                     }
                 }
@@ -152,7 +181,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.p2p = c->wl.p2p; A.self = c->wl.self;
     A.first = c->cells.first; A.count = c->cells.count;
     A.x = P.x; A.y = P.y; A.z = P.z; A.vx = vx; A.vy = vy; A.vz = vz; A.R = P.R;
-    A.hi4 = P.hi4; A.lo4 = P.lo4; A.rc = c->rcf;
+    A.hi4 = P.hi4; A.lo4 = P.lo4; A.cv = c->cv4;
     A.perm = P.perm;
     A.dt = dt;
     A.pairs = c->pairs;

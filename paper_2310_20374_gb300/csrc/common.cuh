@@ -98,7 +98,6 @@ struct Ctrl {
     int n_found;           // colliding pairs found
     int n_resolved;        // colliding pairs resolved (collision resolution on)
     int walk_iters;
-    int n_items;           // multipole work items (cell, chunk)
     int resort_ok;         // the last key sort took the nearly-sorted path (1) or the radix sort
     int n_m2l_dir;
     int n_p2p_dir;
@@ -160,6 +159,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+
+// Acquire-release fence at device scope: orders this thread's earlier memory
+// accesses before its later ones for every thread of the GPU that
+// synchronises with it through an atomic or a flag (much cheaper than the
+// sequentially consistent fence of __threadfence()).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;

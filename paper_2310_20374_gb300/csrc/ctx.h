@@ -26,7 +26,7 @@ struct ParticleSet {
 struct Cells {
     int cap = 0;
     int *level = nullptr, *first = nullptr, *count = nullptr, *child0 = nullptr, *nchild = nullptr,
-        *parent = nullptr, *arrive = nullptr;
+        *parent = nullptr, *arrive = nullptr, *arrive_m = nullptr;   // arrival counters: collision climb, multipoles
     uint32_t *cx = nullptr, *cy = nullptr, *cz = nullptr;
     double *M = nullptr, *sx = nullptr, *sy = nullptr, *sz = nullptr, *rmax = nullptr, *rcrit = nullptr,
            *rho = nullptr;                                 // gravity climb
@@ -39,16 +39,14 @@ struct Cells {
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
     void *Ch = nullptr;       // [cap][num_c(p)] local coefficients of the cell's own M2L (float or double)
     void *Cf = nullptr;       // [cap][num_c(p)] complete local expansion after the descent
-    void *part = nullptr;     // [item_cap][num_m(p)] multipole sums of cell chunks
-    int2 *items = nullptr;    // [item_cap] multipole work items (cell, chunk)
-    int *item_base = nullptr; // [cap] first work item of each cell
-    int item_cap = 0;
     int *leaves = nullptr;    // leaf cell ids
     int *bounds = nullptr;    // [cap][9] scratch of the build
     int *maker = nullptr;     // [cap] scratch of the build: block that made the cell
     int *before = nullptr;    // [cap] scratch of the build: children of its maker's earlier cells
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels
     unsigned *done = nullptr; // [cap] descent: epoch in which the cell's complete expansion was written
+    int *leaf_of = nullptr;   // [leaf_of_cap] leaf of each moonlet of the tree (tree order)
+    int leaf_of_cap = 0;
 };
 
 struct WalkLists {
@@ -76,7 +74,6 @@ struct TreeSet {
 };
 
 constexpr int WALK_MAX_ITERS = 96;
-constexpr int P2M_ITEM_CHUNK = 512;   // moonlets per multipole work item
 
 // Grid of a cooperative launch: the given blocks per SM, capped by the
 // context's limit so that the cooperative grids of contexts driven on
@@ -124,7 +121,8 @@ struct ncorp_ctx {
 
     ncorp::ParticleSet A, B, Cset;   // A: resident state; B: scratch (half-kicked v, drifted x); Cset: next order
     double *amx = nullptr, *amy = nullptr, *amz = nullptr;   // mutual acceleration (tree order)
-    float *rcf = nullptr;            // R + dt |v| per moonlet (collision search), rounded up
+    float4 *cv4 = nullptr;           // collision search, per moonlet: velocity rounded to FP32 (xyz) and
+                                     // R + dt |v| rounded up (w)
     uint64_t *key_alt = nullptr;
     uint64_t *resort_mkey = nullptr;   // nearly-sorted key sort: movers and per-block counts
     uint32_t *resort_midx = nullptr;

@@ -18,6 +18,7 @@
 // pair.
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "ctx.h"
 #include "fields.cuh"
 
@@ -41,7 +42,8 @@ constexpr ExpTable2 make_exp_table2() {
 __constant__ ExpTable2 c_exp2 = make_exp_table2();
 
 struct EvalArgs {
-    const int *leaves, *level, *parent, *first, *count;
+    int n;                     // moonlets of the tree
+    const int *leaves, *level, *parent, *first, *count, *leaf_of;
     const double *sx, *sy, *sz, *rho;
     const float4 *gh, *gl;
     const void *Cf;   // complete local expansions
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
                 }
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+            __syncwarp();   // orders lane 0's acquire before every lane's reads of the parent
             for (int i = lane; i < NC; i += 32) sa[i] = __ldcg(&Cf[(size_t)a * NC + i]);
             real hx, hy, hz, ratio;
             if constexpr (f32) {
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
         }
         __syncwarp();
         if (lane == 0) {
-            __threadfence();
+            fence_acq_rel_gpu();
             st_release_u32(&A.done[c], ep);
         }
     }
@@ -392,66 +395,214 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Near field in mixed precision, one warp per target leaf (claimed
+// dynamically), sources streamed through shared memory by the copy engine.
+//
+// The leaf's direct list is a sequence of source leaves, each a contiguous
+// run of the tree-ordered (hi, lo) arrays (16-byte float4 elements), so a
+// stage of up to NW_STAGE sources is a few bulk copies (cp.async.bulk, one
+// per source-leaf piece and array) completed on the stage's mbarrier.  Each
+// warp owns a ring of two stages: while it sums the sources of one stage the
+// copies of the next are in flight, and no barrier wider than the warp is
+// ever taken.  Targets: a leaf of m <= 64 moonlets at a time; above 32 every
+// lane takes two targets (the sources are read once for both), below it the
+// lanes form G = 32 / T groups of T = pow2ceil(m) lanes that share the
+// stage's sources (k = g, g + G, ...) and add their partial sums at the end
+// (shuffles in a fixed order).
+// ---------------------------------------------------------------------------
+constexpr int NW_WARPS = 4;
+constexpr int NW_STAGE = 128;
+
+struct NearWarpSmem {
+    float4 hi[2][NW_STAGE];
+    float4 lo[2][NW_STAGE];
+    uint64_t bar[2];
+};
+
+// Plans the next stage of the direct list [si, s1) (si advanced past the source leaves taken whole,
+// soff = moonlets of the source leaf at si already taken), arms buffer b's barrier and issues the
+// copies.  Returns the stage's source count (0: the list is exhausted, nothing issued).  All lanes.
+__device__ __forceinline__ int near_issue(const EvalArgs &A, NearWarpSmem &W, int b, int &si, int &soff, int s1,
+                                          int lane) {
+    if (si >= s1) return 0;
+    const int idx = si + lane;
+    int fst = 0, c = 0;
+    if (idx < s1) {
+        const int src = A.p2p_src[idx];
+        fst = A.first[src];
+        c = A.count[src];
+    }
+    if (lane == 0) {
+        fst += soff;
+        c -= soff;
+    }
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const int exc = inc - c;
+    const int tot = min(NW_STAGE, __shfl_sync(0xffffffffu, inc, 31));
+    if (lane == 0) mbar_arrive_expect_tx(&W.bar[b], static_cast<unsigned>(tot) * 32u);
+    __syncwarp();
+    const int take = min(inc, tot) - exc;
+    if (idx < s1 && take > 0) {
+        bulk_g2s(&W.hi[b][exc], &A.hi4[fst], static_cast<unsigned>(take) * 16u, &W.bar[b]);
+        bulk_g2s(&W.lo[b][exc], &A.lo4[fst], static_cast<unsigned>(take) * 16u, &W.bar[b]);
+    }
+    // source leaves taken whole; the next one may be cut where the stage ends
+    const unsigned whole = __ballot_sync(0xffffffffu, idx < s1 && inc <= tot);
+    const int L = __popc(whole);
+    const int excL = __shfl_sync(0xffffffffu, exc, L & 31);
+    soff = (L < 32 && si + L < s1) ? (L == 0 ? soff : 0) + (tot - excL) : 0;
+    si += L;
+    return tot;
+}
+
+// Waits (bounded) for buffer b's copies; false after a time-out (ERR_TIMEOUT set).
+__device__ __forceinline__ bool near_wait(const EvalArgs &A, NearWarpSmem &W, int b, unsigned parity,
+                                          unsigned long long limit, int lane) {
+    int ok = 1;
+    if (lane == 0) {
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(&W.bar[b], parity)) {
+            if (global_ns() - t0 > limit) {
+                atomicOr(const_cast<int *>(&A.ctl->err), ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(32 * NW_WARPS) k_near(EvalArgs A) {
+    __shared__ __align__(128) NearWarpSmem S[NW_WARPS];
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31;
+    NearWarpSmem &W = S[threadIdx.x >> 5];
+    if (lane == 0) {
+        mbar_init(&W.bar[0], 1);
+        mbar_init(&W.bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const unsigned long long limit = A.ctl->wait_ns ? A.ctl->wait_ns : 1000000000ull;
+    const int nl = A.ctl->n_leaves;
+    unsigned phase = 0;   // bit b: parity of the next completion of buffer b
+    int buf = 0;          // the buffer the next stage goes to
+    while (true) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(A.work, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= nl) break;
+        const int leaf = A.leaves[li];
+        const int f = A.first[leaf], cnt = A.count[leaf];
+        const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
+        for (int t0 = 0; t0 < cnt; t0 += 64) {
+            const int m = min(64, cnt - t0);
+            const bool two = m > 32;
+            int lg = 0;
+            while ((1 << lg) < m && lg < 5) lg++;
+            const int T = two ? 32 : (1 << lg), G = 32 / T, tt = lane & (T - 1), g = lane / T;
+            const bool actA = tt < m, actB = two && 32 + lane < m;
+            const int ia = f + t0 + (actA ? tt : 0), ib = f + t0 + (actB ? 32 + lane : 0);
+            const float4 thA = A.hi4[ia], tlA = A.lo4[ia], thB = A.hi4[ib], tlB = A.lo4[ib];
+            float axA = 0.f, ayA = 0.f, azA = 0.f, axB = 0.f, ayB = 0.f, azB = 0.f;
+            int si = s0, soff = 0;
+            __syncwarp();
+            fence_proxy_async();   // the ring was read with ordinary loads before
+            int tot = near_issue(A, W, buf, si, soff, s1, lane);
+            while (tot > 0) {
+                const int nb = buf ^ 1;
+                const int tot_next = near_issue(A, W, nb, si, soff, s1, lane);
+                if (!near_wait(A, W, buf, (phase >> buf) & 1u, limit, lane)) {
+                    if (tot_next > 0) near_wait(A, W, nb, (phase >> nb) & 1u, limit, lane);   // copies in flight
+                    return;
+                }
+                phase ^= 1u << buf;
+                const float4 *H = W.hi[buf], *Lo = W.lo[buf];
+                if (two) {
+#pragma unroll 4
+                    for (int k = 0; k < tot; k++) {
+                        const float4 h = H[k], l = Lo[k];
+                        p2p_f32(h, l, thA, tlA, axA, ayA, azA);
+                        p2p_f32(h, l, thB, tlB, axB, ayB, azB);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = g; k < tot; k += G) p2p_f32(H[k], Lo[k], thA, tlA, axA, ayA, azA);
+                }
+                __syncwarp();
+                fence_proxy_async();   // this buffer's reads are done before it is refilled
+                buf = nb;
+                tot = tot_next;
+            }
+            // partial sums of the groups, added in a fixed order
+            for (int o = T; o < 32; o <<= 1) {
+                axA += __shfl_xor_sync(0xffffffffu, axA, o);
+                ayA += __shfl_xor_sync(0xffffffffu, ayA, o);
+                azA += __shfl_xor_sync(0xffffffffu, azA, o);
+            }
+            if (g == 0 && actA) {
+                A.nx[f + t0 + tt] = static_cast<double>(axA);
+                A.ny[f + t0 + tt] = static_cast<double>(ayA);
+                A.nz[f + t0 + tt] = static_cast<double>(azA);
+            }
+            if (actB) {
+                A.nx[f + t0 + 32 + lane] = static_cast<double>(axB);
+                A.ny[f + t0 + 32 + lane] = static_cast<double>(ayB);
+                A.nz[f + t0 + 32 + lane] = static_cast<double>(azB);
+            }
+        }
+    }
+}
+
 // L2P of each leaf's complete local expansion (Eq. shifting at the moonlet),
-// plus the near-field sums and the external forces: one warp per leaf, the
-// expansion staged in shared memory, lanes over the leaf's moonlets.
-constexpr int FAR_WARPS = 8;
+// plus the near-field sums and the external forces: one thread per moonlet
+// in tree order (the moonlets of a leaf are consecutive, so the threads of a
+// warp read the same few expansions: broadcast loads).
+constexpr int FAR_THREADS = 256;
 
 template <int P, typename real>
-__global__ void __launch_bounds__(32 * FAR_WARPS) k_far(EvalArgs A) {
+__global__ void __launch_bounds__(FAR_THREADS) k_far(EvalArgs A) {
     constexpr int NC = num_c(P);
     constexpr bool f32 = std::is_same<real, float>::value;
-    __shared__ real s_C[FAR_WARPS][NC];
     if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const real *Cf = static_cast<const real *>(A.Cf);
-    const int nl = A.ctl->n_leaves;
-    real *C = s_C[wl];
-    for (int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < nl; li += nwarps) {
-        const int leaf = A.leaves[li];
-        __syncwarp();
-        for (int k = lane; k < NC; k += 32) C[k] = Cf[(size_t)leaf * NC + k];
-        __syncwarp();
-        const int f = A.first[leaf], cnt = A.count[leaf];
-        float4 lgh = make_float4(0.f, 0.f, 0.f, 0.f), lgl = lgh;
-        double sx = 0.0, sy = 0.0, sz = 0.0, irho = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+        const int leaf = __ldg(&A.leaf_of[i]);
+        const real *C = Cf + (size_t)leaf * NC;
+        const double X = A.x[i], Y = A.y[i], Z = A.z[i];
+        real lx = real(0), ly = real(0), lz = real(0);
         if constexpr (f32) {
-            lgh = A.gh[leaf];
-            lgl = A.gl[leaf];
+            const float4 lgh = __ldg(&A.gh[leaf]), lgl = __ldg(&A.gl[leaf]);
+            const float4 th = A.hi4[i], tl = A.lo4[i];
+            const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
+            l2p<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
+                         ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
+            lx *= irf; ly *= irf; lz *= irf;
         } else {
-            irho = 1.0 / A.rho[leaf];
-            sx = A.sx[leaf]; sy = A.sy[leaf]; sz = A.sz[leaf];
+            const double irho = 1.0 / A.rho[leaf];
+            l2p<P, real>(C, (X - A.sx[leaf]) * irho, (Y - A.sy[leaf]) * irho, (Z - A.sz[leaf]) * irho, lx, ly, lz);
+            lx *= irho; ly *= irho; lz *= irho;
         }
-        for (int t = lane; t < cnt; t += 32) {
-            const int i = f + t;
-            const double X = A.x[i], Y = A.y[i], Z = A.z[i];
-            real lx = real(0), ly = real(0), lz = real(0);
-            if constexpr (f32) {
-                const float4 th = A.hi4[i], tl = A.lo4[i];
-                const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
-                l2p<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
-                             ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
-                lx *= irf; ly *= irf; lz *= irf;
-            } else {
-                l2p<P, real>(C, (X - sx) * irho, (Y - sy) * irho, (Z - sz) * irho, lx, ly, lz);
-                lx *= irho; ly *= irho; lz *= irho;
-            }
-            double ex, ey, ez;
-            external_force(A.ext, X, Y, Z, ex, ey, ez);
-            const double mx = static_cast<double>(lx + static_cast<real>(A.nx[i]));
-            const double my = static_cast<double>(ly + static_cast<real>(A.ny[i]));
-            const double mz = static_cast<double>(lz + static_cast<real>(A.nz[i]));
-            const double gx = mx + ex, gy = my + ey, gz = mz + ez;
-            A.ax[i] = gx;
-            A.ay[i] = gy;
-            A.az[i] = gz;
-            if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
-            if (A.kick_h != 0.0) {   // the step's closing half kick, as k_kick computes it
-                A.vx[i] = dadd(A.vx[i], dmul(A.kick_h, gx));
-                A.vy[i] = dadd(A.vy[i], dmul(A.kick_h, gy));
-                A.vz[i] = dadd(A.vz[i], dmul(A.kick_h, gz));
-            }
+        double ex, ey, ez;
+        external_force(A.ext, X, Y, Z, ex, ey, ez);
+        const double mx = static_cast<double>(lx + static_cast<real>(A.nx[i]));
+        const double my = static_cast<double>(ly + static_cast<real>(A.ny[i]));
+        const double mz = static_cast<double>(lz + static_cast<real>(A.nz[i]));
+        const double gx = mx + ex, gy = my + ey, gz = mz + ez;
+        A.ax[i] = gx;
+        A.ay[i] = gy;
+        A.az[i] = gz;
+        if (A.amx) { A.amx[i] = mx; A.amy[i] = my; A.amz[i] = mz; }
+        if (A.kick_h != 0.0) {   // the step's closing half kick, as k_kick computes it
+            A.vx[i] = dadd(A.vx[i], dmul(A.kick_h, gx));
+            A.vy[i] = dadd(A.vy[i], dmul(A.kick_h, gy));
+            A.vz[i] = dadd(A.vz[i], dmul(A.kick_h, gz));
         }
     }
 }
@@ -467,8 +618,21 @@ static void descend_t(ncorp_ctx *c, DescendArgs D) {
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
+static void near_mixed(ncorp_ctx *c, const EvalArgs &A) {
+    int per_sm = 0;
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void *>(k_near), 32 * NW_WARPS, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_near<<<per_sm * c->num_sms, 32 * NW_WARPS, 0, c->stream>>>(A);
+    c->launches++;
+}
+
 template <int P, typename real>
 static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
+    if constexpr (std::is_same<real, float>::value) {   // the mixed path (any p: the near field has no p)
+        near_mixed(c, A);
+        return;
+    }
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, reinterpret_cast<const void *>(k_eval<P, real>), EV_THREADS, 0));
@@ -479,7 +643,7 @@ static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
 
 template <int P, typename real>
 static void far_t(ncorp_ctx *c, const EvalArgs &A) {
-    k_far<P, real><<<4 * c->num_sms, 32 * FAR_WARPS, 0, c->stream>>>(A);
+    k_far<P, real><<<grid_for(A.n, FAR_THREADS, 8 * c->num_sms), FAR_THREADS, 0, c->stream>>>(A);
     c->launches++;
 }
 
@@ -509,7 +673,9 @@ void launch_descend(ncorp_ctx *c, int p, bool mixed) {
 static EvalArgs eval_args(ncorp_ctx *c, const ParticleSet &P, double G, ExtForce ext, bool want_mutual) {
     Cells &C = c->cells;
     EvalArgs A;
+    A.n = c->cur_n;
     A.leaves = C.leaves; A.level = C.level; A.parent = C.parent; A.first = C.first; A.count = C.count;
+    A.leaf_of = C.leaf_of;
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
     A.gh = C.gh; A.gl = C.gl;
     A.Cf = C.Cf;

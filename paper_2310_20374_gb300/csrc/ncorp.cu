@@ -84,7 +84,7 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
     alloc_set(c->B, cap);
     alloc_set(c->Cset, cap);
     dalloc(c->amx, cap); dalloc(c->amy, cap); dalloc(c->amz, cap);
-    dalloc(c->rcf, cap);
+    dalloc(c->cv4, cap);
     dalloc(c->key_alt, cap);
     dalloc(c->idx, cap); dalloc(c->idx_alt, cap);
     if (!c->resort_mkey) {
@@ -107,13 +107,12 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
 void alloc_cells(ncorp_ctx *c, int cap) {
     Cells &C = c->cells;
     dalloc(C.level, cap); dalloc(C.first, cap); dalloc(C.count, cap); dalloc(C.child0, cap);
-    dalloc(C.nchild, cap); dalloc(C.parent, cap); dalloc(C.arrive, cap);
+    dalloc(C.nchild, cap); dalloc(C.parent, cap); dalloc(C.arrive, cap); dalloc(C.arrive_m, cap);
     dalloc(C.cx, cap); dalloc(C.cy, cap); dalloc(C.cz, cap);
     dalloc(C.M, cap); dalloc(C.sx, cap); dalloc(C.sy, cap); dalloc(C.sz, cap);
     dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
     dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
     dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
-    dalloc(C.item_base, cap);
     double *mh = nullptr, *ch = nullptr, *cf = nullptr;
     dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
     dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
@@ -193,24 +192,13 @@ void choose_parameters(ncorp_ctx *c, int p) {
     }
 }
 
-// Multipole work items: one per cell plus one per further P2M_ITEM_CHUNK
-// moonlets of the cell; a moonlet lies in at most MAX_LEVEL + 1 cells.
-void ensure_items(ncorp_ctx *c) {
-    Cells &C = c->cells;
-    const int64_t want = C.cap + (static_cast<int64_t>(MAX_LEVEL + 1) * c->n_cap) / P2M_ITEM_CHUNK + 64;
-    if (C.item_cap >= want) return;
-    dalloc(C.items, static_cast<size_t>(want));
-    double *part = nullptr;
-    dalloc(part, static_cast<size_t>(want) * num_m(MAXP));
-    if (C.part) cudaFree(C.part);
-    C.part = part;
-    C.item_cap = static_cast<int>(want);
-}
-
 void ensure_tree_capacity(ncorp_ctx *c, int n) {
     int want = std::max(4096, 4 * (n / std::max(1, c->s)) + 1024);
     if (c->cells.cap < want) alloc_cells(c, want);
-    ensure_items(c);
+    if (c->cells.leaf_of_cap < n) {
+        dalloc(c->cells.leaf_of, static_cast<size_t>(n));
+        c->cells.leaf_of_cap = n;
+    }
     const int cc = c->cells.cap;
     int front = std::max(1 << 16, 48 * cc), m2l = std::max(1 << 16, 64 * cc), p2p = std::max(1 << 16, 48 * cc);
     if (c->test_list_cap > 0) {   // failure-path tests: lists too small until they first overflow
@@ -261,7 +249,6 @@ bool grow_after(ncorp_ctx *c, int err) {
     bool grew = false;
     if (err & ERR_CELLS) {
         alloc_cells(c, std::max(2 * c->cells.cap, c->ctl_h->n_cells + 1024));
-        ensure_items(c);
         grew = true;
     }
     WalkLists &W = c->wl;
@@ -1319,17 +1306,17 @@ void ncorp_free(ncorp_ctx *c) {
     free_set(c->A);
     free_set(c->B);
     free_set(c->Cset);
-    dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->rcf);
+    dfree(c->amx); dfree(c->amy); dfree(c->amz); dfree(c->cv4);
     dfree(c->key_alt); dfree(c->idx); dfree(c->idx_alt);
     dfree(c->resort_mkey); dfree(c->resort_midx); dfree(c->resort_bcount);
     dfree(c->tile_hist); dfree(c->stage); dfree(c->stage2);
     for (int set = 0; set < 2; set++) {
         Cells &C = c->cells;
         dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
-        dfree(C.arrive); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
+        dfree(C.arrive); dfree(C.arrive_m); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
         dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
         dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf);
-        dfree(C.part); dfree(C.items); dfree(C.item_base); dfree(C.leaves); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
+        dfree(C.leaves); dfree(C.leaf_of); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
         WalkLists &W = c->wl;
         dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
         dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);

@@ -62,7 +62,7 @@ struct BuildArgs {
     const uint64_t *key;
     const uint32_t *qx, *qy, *qz;
     int n, s, cap;
-    int *level, *first, *count, *child0, *nchild, *parent, *arrive;
+    int *level, *first, *count, *child0, *nchild, *parent, *arrive, *arrive_m;
     uint32_t *cx, *cy, *cz;
     int *bounds, *blocksum;
     int *maker, *before;    // per cell: the block that made it, children of its maker's earlier cells
@@ -86,9 +86,9 @@ __global__ void k_build_init(BuildArgs A) {
     A.ctl->n_cells = 1;
     A.ctl->max_level = 0;
     A.ctl->n_leaves = 0;
-    A.ctl->n_items = 0;     // multipole work items of this tree (k_p2m_alloc)
     A.ctl->bar_count = 0;
-    A.arrive[0] = 0;        // arrival counters of the collision climb, zeroed as cells are made
+    A.arrive[0] = 0;        // arrival counters of the collision climb and of the multipoles,
+    A.arrive_m[0] = 0;      // zeroed as cells are made
 }
 
 // Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
                     A.nchild[ci] = 0;
                     A.parent[ci] = c;
                     A.arrive[ci] = 0;
+                    A.arrive_m[ci] = 0;
                     A.cx[ci] = A.qx[b] >> sh;
                     A.cy[ci] = A.qy[b] >> sh;
                     A.cz[ci] = A.qz[b] >> sh;
@@ -283,9 +284,11 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     }
 }
 
-// Also zeroes the grid-barrier counter for the cooperative kernel that follows.
-__global__ void k_collect_leaves(const int *__restrict__ nchild, Ctrl *ctl, int cap, int *leaves, int *n_leaves,
-                                 const int *gate) {
+// The leaf list, and the leaf of every moonlet (leaf_of, tree order).  Also
+// zeroes the grid-barrier counter for the cooperative kernel that follows.
+__global__ void k_collect_leaves(const int *__restrict__ nchild, const int *__restrict__ first,
+                                 const int *__restrict__ count, Ctrl *ctl, int cap, int *leaves, int *n_leaves,
+                                 int *leaf_of, const int *gate) {
     if (gate && *gate == 0) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bar_count = 0;
     if (aborted(ctl)) return;
@@ -294,7 +297,11 @@ __global__ void k_collect_leaves(const int *__restrict__ nchild, Ctrl *ctl, int 
         const int i = base + threadIdx.x;
         const int is_leaf = (i < nc && nchild[i] == 0) ? 1 : 0;
         const int slot = warp_append(n_leaves, is_leaf);
-        if (is_leaf) leaves[slot] = i;
+        if (is_leaf) {
+            leaves[slot] = i;
+            const int f = first[i], e = f + count[i];
+            for (int k = f; k < e; k++) leaf_of[k] = i;
+        }
     }
 }
 
@@ -317,6 +324,7 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *g
     A.parent = C.parent; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.bounds = C.bounds; A.blocksum = C.blocksum; A.maker = C.maker; A.before = C.before; A.ctl = c->ctl;
     A.arrive = C.arrive;
+    A.arrive_m = C.arrive_m;
     k_build_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     const int block = 256;
@@ -327,8 +335,8 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *g
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_build), dim3(grid), dim3(block),
                                                  args, 0, c->stream));
     c->launches++;
-    k_collect_leaves<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(C.nchild, c->ctl, C.cap, C.leaves,
-                                                                                 &c->ctl->n_leaves, gate);
+    k_collect_leaves<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(
+        C.nchild, C.first, C.count, c->ctl, C.cap, C.leaves, &c->ctl->n_leaves, C.leaf_of, gate);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
@@ -387,7 +395,7 @@ struct ClimbArgs {
     double *M, *sx, *sy, *sz, *rmax, *rcrit, *rho;
     float4 *gh, *gl;
     void *Mh;
-    float *rcf;
+    float4 *cv4;
     const int *leaves;
     Ctrl *ctl;
     double G, dt, theta;
@@ -629,105 +637,193 @@ __device__ __forceinline__ void parent_gravity_group(const ClimbArgs &A, int c, 
     }
 }
 
-// ---- multipoles (Eq. multipole_moment, scaled: M-hat_beta = sum mu (d/rho)^beta / beta!).
-// In exact arithmetic the M2M translation of App. C gives a parent the sum
-// of its moonlets' moments about its own centre, so every cell takes that
-// sum directly from its moonlets: no level waits for the one below.  A cell
-// is cut into chunks of P2M_CHUNK consecutive moonlets, one warp per chunk;
-// a cell of several chunks adds their sums in chunk order.
-constexpr int P2M_CHUNK = P2M_ITEM_CHUNK;
-
+// ---- multipoles (Eq. multipole_moment, scaled: M-hat_beta = sum mu (d/rho)^beta / beta!,
+// orders 0 and 2..p-1; the dipole vanishes about the centre of mass).
+// Leaves take the sum over their moonlets (one warp per leaf, lanes over the
+// moonlets, a butterfly sum per coefficient).  A parent takes its children's
+// moments translated to its own centre (the M2M shift of App. C), which in
+// scaled form reads, with delta = (s_c - s_P)/rho_P and r = rho_c/rho_P,
+//   M-hat_P(beta) = sum_children sum_{gamma <= beta, |gamma| != 1}
+//                   M-hat_c(gamma) r^|gamma| delta^(beta - gamma) / (beta - gamma)!
+// (the multinomial expansion of (d_c + delta)^beta / beta!, axis by axis).
+// One launch, no waiting: a warp that has finished a cell adds its arrival to
+// the parent's counter, and the warp that arrives last computes the parent
+// (its children are all done), then goes on up; the children are added in
+// child order, so the result does not depend on who arrives last.
 struct P2MArgs {
     const double *x, *y, *z, *m;
     const float4 *hi4, *lo4;
-    const int *first, *count;
+    const int *first, *count, *child0, *nchild, *parent, *leaves;
+    int *arrive;       // per cell: children whose moments are done (zeroed by the build)
     const double *sx, *sy, *sz, *rho;
     const float4 *gh, *gl;
     void *Mh;
-    void *part;        // [item_cap][num_m(p)]
-    int2 *items;       // (cell, chunk)
-    int *item_base;    // first item of each cell
-    int item_cap;
     double G;
     Ctrl *ctl;
 };
 
-__global__ void k_p2m_alloc(P2MArgs A) {
-    if (aborted(A.ctl)) return;
-    const int nc = A.ctl->n_cells;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        const int nch = (A.count[i] + P2M_CHUNK - 1) / P2M_CHUNK;
-        const int base = atomicAdd(&A.ctl->n_items, nch);
-        A.item_base[i] = base;
-        if (base + nch > A.item_cap) {
-            atomicOr(&A.ctl->err, ERR_CELLS);
-            continue;
-        }
-        for (int j = 0; j < nch; j++) A.items[base + j] = make_int2(i, j);
+constexpr int P2M_WARPS = 4;
+
+template <int P, typename real>
+struct M2MShared {
+    real m[P2M_WARPS][num_m(P) < 1 ? 1 : num_m(P)];
+    real w[P2M_WARPS][3][P];   // delta_axis^k / k!
+    real r[P2M_WARPS][P];      // r^n
+};
+
+// the multi-index (a, b, c) of multipole slot j (orders 0, 2..P-1)
+template <int P>
+__device__ __forceinline__ void m_exps(int j, int &a, int &b, int &c) {
+    a = b = c = 0;
+#pragma unroll
+    for (int n = 0; n < P; n++) {
+        if (n == 1) continue;
+#pragma unroll
+        for (int k = 0; k <= n; k++)
+#pragma unroll
+            for (int cc = 0; cc <= k; cc++)
+                if (midx(n - k, k - cc, cc) == j) {
+                    a = n - k;
+                    b = k - cc;
+                    c = cc;
+                }
     }
 }
 
 template <int P, typename real>
-__global__ void __launch_bounds__(128) k_p2m(P2MArgs A) {
+__device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, int lane, real *Mh) {
     constexpr int NM = num_m(P);
-    if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nitems = min(A.ctl->n_items, A.item_cap);
-    real *Mh = static_cast<real *>(A.Mh), *part = static_cast<real *>(A.part);
-    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int2 ij = A.items[it];
-        const int c = ij.x, cnt = A.count[c];
-        const int f = A.first[c] + ij.y * P2M_CHUNK, e = min(A.first[c] + cnt, f + P2M_CHUNK);
-        real acc[NM];
+    real acc[NM];
 #pragma unroll
-        for (int j = 0; j < NM; j++) acc[j] = real(0);
-        if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
-            const float4 gh = A.gh[c], gl = A.gl[c];
-            const float ir = 1.0f / gl.w;   // exact: rho is a power of two
-            for (int k = f + lane; k < e; k += 32) {
-                const float4 h = A.hi4[k], l = A.lo4[k];
-                p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
-                                 ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
+    for (int j = 0; j < NM; j++) acc[j] = real(0);
+    const int f = A.first[c], e = f + A.count[c];
+    if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
+        const float4 gh = A.gh[c], gl = A.gl[c];
+        const float ir = 1.0f / gl.w;   // exact: rho is a power of two
+        for (int k = f + lane; k < e; k += 32) {
+            const float4 h = A.hi4[k], l = A.lo4[k];
+            p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
+                             ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
+        }
+    } else {
+        const double irho = 1.0 / A.rho[c], sx = A.sx[c], sy = A.sy[c], sz = A.sz[c];
+        for (int k = f + lane; k < e; k += 32)
+            p2m_add<P, real>((A.x[k] - sx) * irho, (A.y[k] - sy) * irho, (A.z[k] - sz) * irho, A.G * A.m[k], acc);
+    }
+#pragma unroll
+    for (int n = 0; n < P; n++) {
+        if (n == 1) continue;
+#pragma unroll
+        for (int k = 0; k <= n; k++)
+#pragma unroll
+            for (int cc = 0; cc <= k; cc++)
+                acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
+    }
+    store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
+}
+
+template <int P, typename real>
+__device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, real> &S, int wl, int pc, int lane,
+                                               real *Mh) {
+    constexpr int NM = num_m(P);
+    constexpr int PER = (NM + 31) / 32;
+    int ea[PER], eb[PER], ec[PER];
+#pragma unroll
+    for (int q = 0; q < PER; q++) m_exps<P>(lane + 32 * q, ea[q], eb[q], ec[q]);
+    real acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; q++) acc[q] = real(0);
+    const int c0 = A.child0[pc], nch = A.nchild[pc];
+    real ipr;
+    if constexpr (sizeof(real) == 4) ipr = 1.0f / A.gl[pc].w;
+    else ipr = 1.0 / A.rho[pc];
+    for (int ch = 0; ch < nch; ch++) {
+        const int c = c0 + ch;
+        __syncwarp();
+        for (int j = lane; j < NM; j += 32) S.m[wl][j] = __ldcg(&Mh[(size_t)c * NM + j]);
+        if (lane < 3) {   // delta^k / k! along axis `lane`
+            real d;
+            if constexpr (sizeof(real) == 4) {
+                const float4 ch_h = A.gh[c], ch_l = A.gl[c], p_h = A.gh[pc], p_l = A.gl[pc];
+                d = lane == 0 ? (ch_h.x - p_h.x) + (ch_l.x - p_l.x)
+                              : (lane == 1 ? (ch_h.y - p_h.y) + (ch_l.y - p_l.y) : (ch_h.z - p_h.z) + (ch_l.z - p_l.z));
+            } else {
+                d = lane == 0 ? A.sx[c] - A.sx[pc] : (lane == 1 ? A.sy[c] - A.sy[pc] : A.sz[c] - A.sz[pc]);
             }
-        } else {
-            const double irho = 1.0 / A.rho[c], sx = A.sx[c], sy = A.sy[c], sz = A.sz[c];
-            for (int k = f + lane; k < e; k += 32)
-                p2m_add<P, real>((A.x[k] - sx) * irho, (A.y[k] - sy) * irho, (A.z[k] - sz) * irho, A.G * A.m[k], acc);
+            d *= ipr;
+            real w = real(1);
+            S.w[wl][lane][0] = w;
+#pragma unroll
+            for (int k = 1; k < P; k++) {
+                w *= d;
+                S.w[wl][lane][k] = w * static_cast<real>(ifact(k));
+            }
+        } else if (lane == 3) {
+            real rr;
+            if constexpr (sizeof(real) == 4) rr = A.gl[c].w * ipr;   // exact: powers of two
+            else rr = A.rho[c] * ipr;
+            real v = real(1);
+#pragma unroll
+            for (int n = 0; n < P; n++) {
+                S.r[wl][n] = v;
+                v *= rr;
+            }
         }
+        __syncwarp();
 #pragma unroll
-        for (int n = 0; n < P; n++) {
-            if (n == 1) continue;
-#pragma unroll
-            for (int k = 0; k <= n; k++)
-#pragma unroll
-                for (int cc = 0; cc <= k; cc++)
-                    acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
+        for (int q = 0; q < PER; q++) {
+            if (lane + 32 * q >= NM) continue;
+            const int a = ea[q], b = eb[q], cz = ec[q];
+            real s = real(0);
+            for (int a2 = 0; a2 <= a; a2++)
+                for (int b2 = 0; b2 <= b; b2++)
+                    for (int c2 = 0; c2 <= cz; c2++) {
+                        const int n2 = a2 + b2 + c2;
+                        if (n2 == 1) continue;
+                        s += S.m[wl][midx(a2, b2, c2)] * S.r[wl][n2] * S.w[wl][0][a - a2] * S.w[wl][1][b - b2] *
+                             S.w[wl][2][cz - c2];
+                    }
+            acc[q] += s;
         }
-        const bool single = cnt <= P2M_CHUNK;
-        store_reduced<P, real>(acc, single ? Mh + (size_t)c * NM : part + (size_t)it * NM, lane);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; q++)
+        if (lane + 32 * q < NM) Mh[(size_t)pc * NM + lane + 32 * q] = acc[q];
+}
+
+template <int P, typename real>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_multipoles(P2MArgs A) {
+    __shared__ M2MShared<P, real> S;
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nl = A.ctl->n_leaves;
+    real *Mh = static_cast<real *>(A.Mh);
+    for (int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < nl; li += nwarps) {
+        int c = A.leaves[li];
+        leaf_moments<P, real>(A, c, lane, Mh);
+        while (true) {   // up the tree while this warp is the last child to finish
+            const int pc = A.parent[c];
+            if (pc < 0) break;
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) {
+                fence_acq_rel_gpu();   // release: this cell's moments before the arrival
+                last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+                if (last) fence_acq_rel_gpu();   // acquire: the other children's moments
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) break;
+            __syncwarp();
+            parent_moments<P, real>(A, S, wl, pc, lane, Mh);
+            c = pc;
+        }
     }
 }
 
 template <int P, typename real>
-__global__ void k_p2m_finish(P2MArgs A) {
-    constexpr int NM = num_m(P);
-    if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nc = A.ctl->n_cells;
-    real *Mh = static_cast<real *>(A.Mh);
-    const real *part = static_cast<const real *>(A.part);
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nwarps) {
-        const int nch = (A.count[c] + P2M_CHUNK - 1) / P2M_CHUNK;
-        if (nch <= 1) continue;
-        const int base = A.item_base[c];
-        for (int j = lane; j < NM; j += 32) {
-            real s = real(0);
-            for (int q = 0; q < nch; q++) s += part[(size_t)(base + q) * NM + j];
-            Mh[(size_t)c * NM + j] = s;
-        }
-    }
+static void p2m_t(ncorp_ctx *c, const P2MArgs &B) {
+    k_multipoles<P, real><<<4 * c->num_sms, 32 * P2M_WARPS, 0, c->stream>>>(B); c->launches++;
 }
 
 // theta(M) of Dehnen (2002) Eq. 13: theta^5/(1-theta)^2 = K (M/M_tot)^(-1/3),
@@ -804,11 +900,6 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A)
     }
 }
 
-template <int P, typename real>
-static void p2m_t(ncorp_ctx *c, const P2MArgs &A) {
-    k_p2m<P, real><<<2 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
-    k_p2m_finish<P, real><<<4 * c->num_sms, 128, 0, c->stream>>>(A); c->launches++;
-}
 
 void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta) {
     Cells &C = c->cells;
@@ -833,11 +924,11 @@ void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, do
     Cells &C = c->cells;
     P2MArgs B;
     B.x = P.x; B.y = P.y; B.z = P.z; B.m = P.m; B.hi4 = P.hi4; B.lo4 = P.lo4;
-    B.first = C.first; B.count = C.count;
+    B.first = C.first; B.count = C.count; B.child0 = C.child0; B.nchild = C.nchild; B.parent = C.parent;
+    B.leaves = C.leaves; B.arrive = C.arrive_m;
     B.sx = C.sx; B.sy = C.sy; B.sz = C.sz; B.rho = C.rho; B.gh = C.gh; B.gl = C.gl;
-    B.Mh = C.Mh; B.part = C.part; B.items = C.items; B.item_base = C.item_base; B.item_cap = C.item_cap;
+    B.Mh = C.Mh;
     B.G = G; B.ctl = c->ctl;
-    k_p2m_alloc<<<grid_for(C.cap, 256, 4 * c->num_sms), 256, 0, c->stream>>>(B); c->launches++;
 #define NCORP_P2M_CASE(PP)                     \
     case PP:                                   \
         if (mixed) p2m_t<PP, float>(c, B);     \
@@ -860,7 +951,8 @@ void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, do
 // Collision climb (Eqs. center, rmax, rcrit): s-bar is the mean moonlet
 // position (children weighted by their moonlet counts); r_crit = r_max + max
 // over children of (r_crit - r_max), a moonlet's being R + dt |v| (stored,
-// rounded up to FP32, for the pair prefilter).
+// rounded up to FP32, with the velocity rounded to FP32, for the pair
+// prefilter).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
     if (aborted(A.ctl)) return;
@@ -879,9 +971,11 @@ __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
         double d2 = 0.0, ex = 0.0;
         for (int k = L.f + L.q; k < L.f + L.cnt; k += 4) {
             d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
-            const double e = dadd(A.R[k], dmul(A.dt, dnorm3(A.vx[k], A.vy[k], A.vz[k])));
+            const double vx = A.vx[k], vy = A.vy[k], vz = A.vz[k];
+            const double e = dadd(A.R[k], dmul(A.dt, dnorm3(vx, vy, vz)));
             ex = fmax(ex, e);
-            A.rcf[k] = __double2float_ru(e);
+            A.cv4[k] = make_float4(static_cast<float>(vx), static_cast<float>(vy), static_cast<float>(vz),
+                                   __double2float_ru(e));
         }
         d2 = quad_max(d2);
         ex = quad_max(ex);
@@ -916,15 +1010,18 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs 
     for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
         int c = A.leaves[gw];
         while (true) {
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             const int pc = A.parent[c];
             if (pc < 0) break;
             int last = 0;
-            if (lane == 0) last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+            if (lane == 0) {
+                last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
+                if (last) fence_acq_rel_gpu();   // acquire: the other children's results
+            }
             last = __shfl_sync(0xffffffffu, last, 0);
             if (!last) break;
-            __threadfence();
+            __syncwarp();   // orders lane 0's acquire before every lane's reads
             c = pc;
             const int c0 = A.child0[c], nch = A.nchild[c];
             if (lane < nch) {
@@ -973,7 +1070,7 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.level = C.level; A.arrive = C.arrive; A.cx = C.cx; A.cy = C.cy; A.cz = C.cz;
     A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
     A.gh = C.bh; A.gl = C.bl;
-    A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.rcf = c->rcf;
+    A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.cv4 = c->cv4;
     k_leaf_collision<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
     k_climb_collision<<<4 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
