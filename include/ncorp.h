@@ -86,11 +86,14 @@ typedef struct {
                                  NCORP_EINVAL at ncorp_init. */
     int n_cb_pre, n_cb_post;  /* thresholds N_cb,pre and N_cb,post of the standard tree code
                                  (ncorp_accel_standard, Algorithm StandardTree, Sect. 3.4.4); >= 0 */
+    int c_cb_pre, c_cb_post;  /* the same thresholds for the standard tree code's collision search
+                                 (ncorp_collide_standard); >= 0 */
 } ncorp_config;
 
 /* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
  * NCORP_MIXED, collisions on (reported, not resolved), no star, no bulge (J2 = 0),
- * standard tree thresholds N_cb,pre = 6 and N_cb,post = 16 (Sect. 4.2). */
+ * standard tree thresholds N_cb,pre = 6 and N_cb,post = 16 for gravity and 0 and
+ * 16 for collisions (Sect. 4.2). */
 void ncorp_config_default(ncorp_config *cfg);
 
 /* Creates a context for disks of up to n_max moonlets on CUDA device `device`.
@@ -182,6 +185,22 @@ int ncorp_accel_standard(ncorp_ctx *ctx, const double *positions, const double *
  * Invalidates the resident step state.  Errors as ncorp_step. */
 int ncorp_collide(ncorp_ctx *ctx, const double *positions, const double *velocities,
                   const double *radii, int64_t n, double dt);
+
+/* Collision search alone by the standard tree code (Algorithm StandardTree,
+ * Sect. 3.4.4, its instructions for collisions) on the tree of the given
+ * positions with the collision geometry of Sect. 3.4.2 (Eqs. center, rmax,
+ * rcrit): every moonlet a is walked from the root with r_crit,a = R_a + dt |v_a|;
+ * a cell B with fewer than c_cb_pre moonlets is searched directly; B is
+ * skipped when ((r_crit,a + r_crit,B)(1 + 2^-40))^2 < |x_a - sbar_B|^2; a cell
+ * with fewer than c_cb_post moonlets, or a leaf, is searched directly; any
+ * other is opened.  Searching B directly tests a against the moonlets of B with
+ * a larger caller index with the pairwise test of Sect. 3.1, so the pairs
+ * found are exactly those of ncorp_collide.  Results via ncorp_collisions;
+ * counters: NCORP_STAT_COL_PAIRS = cells searched directly, NCORP_STAT_COL_TESTS
+ * = moonlet pairs tested.  Invalidates the resident step state.  Errors as
+ * ncorp_collide. */
+int ncorp_collide_standard(ncorp_ctx *ctx, const double *positions, const double *velocities,
+                           const double *radii, int64_t n, double dt);
 
 /* Copies the resident state (caller order) into positions/velocities [n][3].
  * NCORP_ESTATE if no step has run since init/reset. */

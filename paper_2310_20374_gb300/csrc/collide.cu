@@ -9,6 +9,8 @@
 // (dv = 0: no collision).  Evaluated in FP64 with exactly rounded operations
 // in a fixed order, (1, 2) being the pair in increasing caller index, so that
 // the set of pairs is reproducible bit for bit.
+#include <algorithm>
+
 #include "ctx.h"
 
 namespace ncorp {
@@ -193,6 +195,166 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     // two blocks per SM beside the main chain (its cooperative kernels must find room on every SM
     // while the search runs); four (the register file's limit) when nothing else runs
     k_collide<<<(wide ? 4 : 2) * c->num_sms, 32 * COL_WARPS, 0, c->stream>>>(A); c->launches++;
+    NCORP_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Collision search by the standard tree code (Algorithm StandardTree, Sect.
+// 3.4.4, the instructions for collisions).  Every moonlet a is walked from the
+// root with its own r_crit,a = R_a + dt |v_a| (a point: r_max = 0): a cell B
+// with fewer than N_cb,pre moonlets is searched directly; B is skipped when
+// ((r_crit,a + r_crit,B)(1 + 2^-40))^2 < |x_a - sbar_B|^2 (the dual walk's
+// pruning rule); a cell with fewer than N_cb,post moonlets, or a leaf, is
+// searched directly; any other is opened, children in order.  Searching B
+// directly tests a against the moonlets of B with a larger caller index, so
+// every pair is tested once, from the walk of its lower index.
+//
+// Work layout as for the standard gravity code: a warp walks 32 consecutive
+// moonlets of the key order together with a (cell, lanes) stack; each lane
+// takes its own moonlet's decisions.  The pruning test is decided in FP32
+// only where it is clear by a 2^-16 relative margin (the double-float
+// separation and the FP32 radii are accurate to ~1e-7), in FP64 in the
+// oracle's order of operations otherwise, so the walk is the oracle's.  The
+// moonlet pairs go through the same two FP32 prefilters and the exact FP64
+// test as the dual walk's pairs.
+// ---------------------------------------------------------------------------
+constexpr int SC_WARPS = 4;
+constexpr int SC_STACK = 8 * (MAX_LEVEL + 3);
+
+struct StdCollideArgs {
+    CollideArgs C;
+    const int *child0, *nchild;
+    const double *bx, *by, *bz, *bcrit;
+    const float4 *bh, *bl;    // collision centre hi (xyz), r_crit in FP32 (w); centre lo
+    int pre, post, n;
+};
+
+__global__ void __launch_bounds__(32 * SC_WARPS) k_standard_collide(StdCollideArgs S) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ int s_cell[SC_WARPS][SC_STACK];
+    __shared__ unsigned s_mask[SC_WARPS][SC_STACK];
+    const CollideArgs &A = S.C;
+    if (aborted(A.ctl)) return;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const float dtf = static_cast<float>(A.dt) * (1.0f + 0x1p-20f);
+    long long n_dir = 0, n_tests = 0;
+    bool overflow = false;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < S.n; base += nwarps * 32) {
+        const int i = base + lane;
+        const bool valid = i < S.n;
+        const int a = valid ? i : base;
+        const double X = A.x[a], Y = A.y[a], Z = A.z[a];
+        const double rca = dadd(A.R[a], dmul(A.dt, dnorm3(A.vx[a], A.vy[a], A.vz[a])));
+        const float4 th = A.hi4[a], tl = A.lo4[a], tv = A.cv[a];
+        const float tR = static_cast<float>(A.R[a]), rcf = static_cast<float>(rca);
+        const int pa = A.perm[a];
+        const unsigned lanes = __ballot_sync(FULL, valid);
+        __syncwarp();
+        if (lane == 0) {
+            s_cell[wl][0] = 0;
+            s_mask[wl][0] = lanes;
+        }
+        __syncwarp();
+        int sp = 1;
+        while (sp > 0) {
+            sp--;
+            const int c = s_cell[wl][sp];
+            const unsigned mask = s_mask[wl][sp];
+            __syncwarp();
+            const bool mine = (mask >> lane) & 1u;
+            const int nb = A.count[c], f = A.first[c];
+            const bool leaf = S.nchild[c] == 0;
+            int d = -1;   // 0: search directly, 1: pruned, 2: open
+            if (mine) {
+                if (nb < S.pre) {
+                    d = 0;
+                } else {
+                    const float4 ch = S.bh[c], cl = S.bl[c];
+                    const float dx = (th.x - ch.x) + (tl.x - cl.x);
+                    const float dy = (th.y - ch.y) + (tl.y - cl.y);
+                    const float dz = (th.z - ch.z) + (tl.z - cl.z);
+                    const float d2f = dx * dx + dy * dy + dz * dz, tf = rcf + ch.w, t2f = tf * tf;
+                    const float fl = (fabsf(th.x) + fabsf(th.y) + fabsf(th.z)) * 0x1p-26f;
+                    bool pruned;
+                    if (d2f > fl * fl && d2f > t2f * (1.0f + 0x1p-16f)) {
+                        pruned = true;
+                    } else if (d2f > fl * fl && d2f < t2f * (1.0f - 0x1p-16f)) {
+                        pruned = false;
+                    } else {
+                        const double ex = dsub(X, S.bx[c]), ey = dsub(Y, S.by[c]), ez = dsub(Z, S.bz[c]);
+                        const double t = dmul(dadd(rca, S.bcrit[c]), 1.0 + 0x1p-40);
+                        pruned = dmul(t, t) < dsq3(ex, ey, ez);
+                    }
+                    d = pruned ? 1 : ((nb < S.post || leaf) ? 0 : 2);
+                }
+            }
+            const unsigned m_dir = __ballot_sync(FULL, d == 0);
+            const unsigned m_open = __ballot_sync(FULL, d == 2);
+            if (m_dir) {   // the cell's moonlets, read once for the warp
+                if (d == 0) n_dir++;
+                for (int k = f; k < f + nb; k++) {
+                    const float4 h = A.hi4[k], l = A.lo4[k], v = A.cv[k];
+                    const int pk = A.perm[k];
+                    const float Rk = static_cast<float>(A.R[k]);
+                    if (d == 0 && pk > pa) {
+                        n_tests++;
+                        float dx, dy, dz;
+                        if (may_touch(h, l, v.w, th, tl, tv.w, dx, dy, dz) &&
+                            may_meet(dx, dy, dz, v, tv, (Rk + tR) * (1.0f + 0x1p-20f), dtf))
+                            test_and_emit(A, a, k);
+                    }
+                }
+            }
+            if (m_open) {
+                const int c0 = S.child0[c], nch = S.nchild[c];
+                if (sp + nch > SC_STACK) {   // cannot happen within MAX_LEVEL levels; never write past the stack
+                    overflow = true;
+                    break;
+                }
+                if (lane < nch) {   // children pushed last first, so the first is taken next
+                    s_cell[wl][sp + nch - 1 - lane] = c0 + lane;
+                    s_mask[wl][sp + nch - 1 - lane] = m_open;
+                }
+                sp += nch;
+                __syncwarp();
+            }
+        }
+    }
+    if (__any_sync(FULL, overflow) && lane == 0) atomicOr(&A.ctl->err, ERR_LEVEL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_dir += __shfl_xor_sync(FULL, n_dir, o);
+        n_tests += __shfl_xor_sync(FULL, n_tests, o);
+    }
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->col_pairs), static_cast<unsigned long long>(n_dir));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_tests), static_cast<unsigned long long>(n_tests));
+    }
+}
+
+void launch_standard_collide(ncorp_ctx *c, const ParticleSet &P, double dt, int n, int pre, int post) {
+    StdCollideArgs S;
+    CollideArgs &A = S.C;
+    A.p2p = nullptr; A.self = nullptr;
+    A.first = c->cells.first; A.count = c->cells.count;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.vx = P.vx; A.vy = P.vy; A.vz = P.vz; A.R = P.R;
+    A.hi4 = P.hi4; A.lo4 = P.lo4; A.cv = c->cv4;
+    A.perm = P.perm;
+    A.dt = dt;
+    A.pairs = c->pairs;
+    A.where = nullptr;
+    A.cap = c->pair_cap;
+    A.self_cap = 0;
+    A.p2p_cap = 0;
+    A.ctl = c->ctl;
+    S.child0 = c->cells.child0; S.nchild = c->cells.nchild;
+    S.bx = c->cells.bx; S.by = c->cells.by; S.bz = c->cells.bz; S.bcrit = c->cells.bcrit;
+    S.bh = c->cells.bh; S.bl = c->cells.bl;
+    S.pre = pre; S.post = post; S.n = n;
+    const int warps = (n + 31) / 32;
+    const int grid = std::max(1, std::min((warps + SC_WARPS - 1) / SC_WARPS, 16 * c->num_sms));
+    k_standard_collide<<<grid, 32 * SC_WARPS, 0, c->stream>>>(S); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 

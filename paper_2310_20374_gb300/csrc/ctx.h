@@ -240,6 +240,9 @@ void launch_resolve(ncorp_ctx *c, const ParticleSet &S, ParticleSet &D, int n, d
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
                     double dt, bool wide);
 void launch_sort_pairs(ncorp_ctx *c, int count);
+// collision search of the moonlets of P (tree order, velocities P.v*) by the standard tree code, on the
+// current tree with its collision geometry
+void launch_standard_collide(ncorp_ctx *c, const ParticleSet &P, double dt, int n, int pre, int post);
 
 // ---- kdk.cu ----
 void launch_aos_to_soa(ncorp_ctx *c, const double *aos, double *x, double *y, double *z, int n);

@@ -343,6 +343,8 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     ctl->n_resolved = 0;
     ctl->n_tests = 0;
     ctl->dec_pairs = 0;
+    ctl->col_pairs = 0;
+    ctl->col_self = 0;
     ctl->n_inter = 0;
     ctl->n_m2p = 0;
     ctl->bar_count = 0;
@@ -526,6 +528,14 @@ void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const doub
     launch_climb_collision(c, S, vx, vy, vz, dt);
     launch_walk(c, false);
     launch_collide(c, S, vx, vy, vz, dt, wide);
+}
+
+// The same search by the standard tree code (Algorithm StandardTree): the collision climb, then one walk
+// per moonlet.  S's velocities are the ones searched.
+void collisions_standard(ncorp_ctx *c, const ParticleSet &S, int n, double dt) {
+    Stage st(c, NCORP_STAGE_COLLIDE);
+    launch_climb_collision(c, S, S.vx, S.vy, S.vz, dt);
+    launch_standard_collide(c, S, dt, n, c->cfg.c_cb_pre, c->cfg.c_cb_post);
 }
 
 constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision walk beside the gravity pipeline
@@ -796,6 +806,8 @@ void ncorp_config_default(ncorp_config *cfg) {
     cfg->collisions = 1;
     cfg->n_cb_pre = 6;
     cfg->n_cb_post = 16;
+    cfg->c_cb_pre = 0;
+    cfg->c_cb_post = 16;
 }
 
 int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream) {
@@ -803,7 +815,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
     if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
     if (!(cfg->G > 0.0) || !(cfg->central_mass >= 0.0) || cfg->leaf_size < 0) return NCORP_EINVAL;
     if (!(cfg->resolve_f == 0.0 || (cfg->resolve_f >= 1.0 && cfg->resolve_f <= 2.0))) return NCORP_EINVAL;
-    if (cfg->n_cb_pre < 0 || cfg->n_cb_post < 0) return NCORP_EINVAL;
+    if (cfg->n_cb_pre < 0 || cfg->n_cb_post < 0 || cfg->c_cb_pre < 0 || cfg->c_cb_post < 0) return NCORP_EINVAL;
     *out = nullptr;
     ncorp_ctx *c = new (std::nothrow) ncorp_ctx();
     if (!c) return NCORP_ENOMEM;
@@ -977,8 +989,9 @@ int ncorp_accel_standard(ncorp_ctx *c, const double *positions, const double *ma
     })
 }
 
-int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocities, const double *radii, int64_t n64,
-                  double dt) {
+// Collision search alone, by falcON's dual walk (standard = false) or by the standard tree code.
+static int collide_call(ncorp_ctx *c, const double *positions, const double *velocities, const double *radii, int64_t n64,
+                 double dt, bool standard) {
     if (!c) return NCORP_EINVAL;
     if (n64 < 1 || n64 > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "n out of range");
     if (!positions || !velocities || !radii) return fail(c, NCORP_EINVAL, "null pointer");
@@ -1001,7 +1014,8 @@ int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocitie
             launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
             build_tree(c, A, A, A, c->Cset, n);
             std::swap(c->A, c->Cset);
-            collisions(c, c->A, c->A.vx, c->A.vy, c->A.vz, dt, true);
+            if (standard) collisions_standard(c, c->A, n, dt);
+            else collisions(c, c->A, c->A.vx, c->A.vy, c->A.vz, dt, true);
             int err = finish(c);
             if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
             if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
@@ -1016,6 +1030,16 @@ int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocitie
         record_stats(c, false);
         return NCORP_OK;
     })
+}
+
+int ncorp_collide(ncorp_ctx *c, const double *positions, const double *velocities, const double *radii, int64_t n64,
+                  double dt) {
+    return collide_call(c, positions, velocities, radii, n64, dt, false);
+}
+
+int ncorp_collide_standard(ncorp_ctx *c, const double *positions, const double *velocities, const double *radii,
+                           int64_t n64, double dt) {
+    return collide_call(c, positions, velocities, radii, n64, dt, true);
 }
 
 int ncorp_step(ncorp_ctx *c, double *positions, double *velocities, const double *masses, const double *radii,

@@ -37,7 +37,7 @@ class ncorp_config(C.Structure):
                 ("precision", C.c_int), ("collisions", C.c_int),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
                 ("t0", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double),
-                ("n_cb_pre", C.c_int), ("n_cb_post", C.c_int)]
+                ("n_cb_pre", C.c_int), ("n_cb_post", C.c_int), ("c_cb_pre", C.c_int), ("c_cb_post", C.c_int)]
 
 
 _lib = None
@@ -68,6 +68,7 @@ def load(path: str | None = None):
     L.ncorp_accel.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
     L.ncorp_accel_standard.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
     L.ncorp_collide.argtypes = [vp, vp, vp, vp, i64, dbl]
+    L.ncorp_collide_standard.argtypes = [vp, vp, vp, vp, i64, dbl]
     L.ncorp_get_state.argtypes = [vp, vp, vp]
     L.ncorp_stats.argtypes = [vp, C.POINTER(i64), ip]
     L.ncorp_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
@@ -92,7 +93,7 @@ def load(path: str | None = None):
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
     for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
-                 "ncorp_accel_standard", "ncorp_collide", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
+                 "ncorp_accel_standard", "ncorp_collide", "ncorp_collide_standard", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
                  "ncorp_hilbert_sort_static", "ncorp_fma_peak", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
                  "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
         getattr(L, name).restype = C.c_int
@@ -219,6 +220,13 @@ def ncorp_collide(ctx, positions, velocities, radii, n, dt):
     return _check(ctx, load().ncorp_collide(ctx, _arr(positions, "f8", 3 * n, "positions"),
                                             _arr(velocities, "f8", 3 * n, "velocities"),
                                             _arr(radii, "f8", n, "radii"), n, float(dt)))
+
+
+def ncorp_collide_standard(ctx, positions, velocities, radii, n, dt):
+    n = int(n)
+    return _check(ctx, load().ncorp_collide_standard(ctx, _arr(positions, "f8", 3 * n, "positions"),
+                                                     _arr(velocities, "f8", 3 * n, "velocities"),
+                                                     _arr(radii, "f8", n, "radii"), n, float(dt)))
 
 
 def ncorp_get_state(ctx, positions, velocities):

@@ -111,3 +111,53 @@ def test_standard_and_falcon_agree_to_their_errors():
         ncorp.ncorp_free(ctx)
     e_s, e_f = np.median(rel(mut_s[idx], ref)), np.median(rel(mut_f[idx], ref))
     assert e_s < 1e-2 and e_f < 1e-2, (e_s, e_f)
+
+
+# ---------------------------------------------------------------- collision search (StandardTree)
+def collide_standard(d, dt, s=16, thresholds=(0, 16)):
+    n = len(d["pos"])
+    cfg = ncorp.ncorp_config_default()
+    cfg.leaf_size = s
+    cfg.c_cb_pre, cfg.c_cb_post = thresholds
+    ctx = ncorp.ncorp_init(cfg, n, 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        ncorp.ncorp_collide_standard(ctx, d["pos"], d["vel"], d["radius"], n, dt)
+        pairs = np.zeros((1 << 15, 2), dtype=np.int64)
+        k = ncorp.ncorp_collisions(ctx, pairs, len(pairs))
+        st = ncorp.ncorp_stats(ctx)
+    finally:
+        ncorp.ncorp_free(ctx)
+    return pairs[:k], st
+
+
+@pytest.mark.parametrize("n,seed,dense,thresholds", [(4000, 31, True, (0, 16)), (3000, 32, True, (6, 40)),
+                                                     (20000, 33, False, (0, 16))])
+def test_collision_search_equals_oracle_and_brute_force(n, seed, dense, thresholds):
+    """Algorithm StandardTree's collision search on the GPU: the same pair set as the oracle's tree search
+    and as brute force (bit-exact), the same direct-search decisions and tested pairs as the oracle."""
+    if dense:
+        d = diskgen.make_disk(n, seed, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
+    else:
+        d = diskgen.make_disk(n, seed)
+    dt = 0.05 if dense else 1e-2
+    got, st = collide_standard(d, dt, thresholds=thresholds)
+    P = oracle.params(p=3, theta=0.5, leaf_size=16, standard_collision_thresholds=thresholds)
+    ref, ost = oracle.collide_standard(P, d["pos"], d["vel"], d["radius"], dt)
+    assert len(ref) > 0 and np.array_equal(got, ref)
+    assert np.array_equal(got, oracle.collide_brute(d["pos"], d["vel"], d["radius"], dt))
+    assert (st["col_pairs"], st["col_tests"]) == (ost["col_pairs"], ost["col_tests"])
+
+
+def test_collision_search_matches_dual_walk():
+    d = diskgen.make_disk(6000, 34, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
+    got, _ = collide_standard(d, 0.05)
+    cfg = ncorp.ncorp_config_default()
+    cfg.leaf_size = 16
+    ctx = ncorp.ncorp_init(cfg, len(d["pos"]), 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        ncorp.ncorp_collide(ctx, d["pos"], d["vel"], d["radius"], len(d["pos"]), 0.05)
+        pairs = np.zeros((1 << 15, 2), dtype=np.int64)
+        k = ncorp.ncorp_collisions(ctx, pairs, len(pairs))
+    finally:
+        ncorp.ncorp_free(ctx)
+    assert np.array_equal(got, pairs[:k])
