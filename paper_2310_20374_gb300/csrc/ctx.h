@@ -39,6 +39,8 @@ struct Cells {
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
     void *Ch = nullptr;       // [cap][num_c(p)] local coefficients of the cell's own M2L (float or double)
     void *Cf = nullptr;       // [cap][num_c(p)] complete local expansion after the descent
+    float *Cf_lo = nullptr;   // [cap][3] mixed precision: low parts of the order-1 coefficients of Cf
+                              // (double-float: the field is the sum of the whole far field)
     int *leaves = nullptr;    // leaf cell ids
     int *bounds = nullptr;    // [cap][9] scratch of the build
     int *maker = nullptr;     // [cap] scratch of the build: block that made the cell

@@ -47,6 +47,7 @@ struct EvalArgs {
     const double *sx, *sy, *sz, *rho;
     const float4 *gh, *gl;
     const void *Cf;   // complete local expansions
+    const float *Cf_lo;   // mixed: low parts of their order-1 coefficients
     const int *p2p_off, *p2p_src;
     int p2p_dir_cap;
     const double *x, *y, *z, *m;
@@ -108,6 +109,13 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
 // A translation is done as three one-dimensional shifts, along x, y, z in
 // turn (beta! = bx! by! bz!): D_gamma = sum_k C_{gamma + k e_axis} h_axis^k / k!,
 // with coefficients beyond order p taken as zero.
+//
+// Mixed precision: the order-1 coefficients (the field at the centre) carry
+// the whole far field of the disk and are passed down every level, so they
+// are kept as double-float pairs (hi in Cf, lo in Cf_lo): the translation of
+// the higher orders into them is formed in FP32 with the parent's order-1
+// terms left out, and it and the cell's own M2L sum are added to the parent's
+// pair exactly (two-sum), so that rounding does not build up with depth.
 // ---------------------------------------------------------------------------
 struct DescendArgs {
     const int *parent;
@@ -115,6 +123,7 @@ struct DescendArgs {
     const double *sx, *sy, *sz, *rho;
     const void *Ch;
     void *Cf;
+    float *Cf_lo;              // [cells][3] mixed: low parts of the order-1 coefficients
     unsigned *done;            // [cells]: epoch of the descent that completed the cell
     int *work;                 // claim counter, zeroed by the M2L launch
     Ctrl *ctl;                 // desc_epoch: this descent's epoch (advanced by the M2L launch)
@@ -138,6 +147,17 @@ __device__ __forceinline__ real shift_axis(const real *src, const real (&w)[P + 
     for (int k = 1; k <= P - 1; k++)
         if (k <= P - n) s += src[shifted_index<AXIS>(n, kk, c, k)] * w[k];
     return s;
+}
+
+// (hi, lo) + b with hi + lo renormalised: Knuth's two-sum of hi and b, its
+// error added to lo
+__device__ __forceinline__ void df_add(float &hi, float &lo, float b) {
+    const float s = hi + b;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (b - bv);
+    const float l = lo + e;
+    hi = s + l;
+    lo = l - (hi - s);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32_any(const unsigned *p) {
@@ -186,6 +206,8 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
             const int i = lane + 32 * k;
             acc[k] = i < NC ? Ch[(size_t)c * NC + i] : real(0);
         }
+        // mixed: the order-1 pair of this cell (lanes 0..2); the root's is its own M2L sum
+        float hi1 = f32 ? static_cast<float>(acc[0]) : 0.0f, lo1 = 0.0f, phi = 0.0f, plo = 0.0f;
         const int a = A.parent[c];
         if (a >= 0) {
             int ok = 1;
@@ -202,6 +224,13 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
             if (!__shfl_sync(0xffffffffu, ok, 0)) return;
             __syncwarp();   // orders lane 0's acquire before every lane's reads of the parent
             for (int i = lane; i < NC; i += 32) sa[i] = __ldcg(&Cf[(size_t)a * NC + i]);
+            if constexpr (f32) {   // the parent's order-1 pair is added exactly below, not shifted
+                if (lane < 3) {
+                    phi = sa[lane];
+                    plo = __ldcg(&A.Cf_lo[3 * a + lane]);
+                    sa[lane] = 0.0f;
+                }
+            }
             real hx, hy, hz, ratio;
             if constexpr (f32) {
                 const float4 ch = A.gh[c], cl = A.gl[c], ah = A.gh[a], al = A.gl[a];
@@ -244,7 +273,16 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
                 if (lane + 32 * k >= NC) continue;
                 real s = shift_axis<P, 2>(sa, wz, on[k], okk[k], oc[k]);
                 for (int q = 0; q < on[k]; q++) s *= ratio;   // (rho_c/rho_a)^n, exact powers of two
-                acc[k] += s;
+                if (f32 && k == 0 && lane < 3) {
+                    // order 1: (parent pair) * ratio + higher orders + own sum, in double-float
+                    hi1 = phi * static_cast<float>(ratio);
+                    lo1 = plo * static_cast<float>(ratio);
+                    df_add(hi1, lo1, static_cast<float>(s));
+                    df_add(hi1, lo1, static_cast<float>(acc[0]));
+                    acc[0] = static_cast<real>(hi1);
+                } else {
+                    acc[k] += s;
+                }
             }
             __syncwarp();
         }
@@ -253,6 +291,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
             const int i = lane + 32 * k;
             if (i < NC) Cf[(size_t)c * NC + i] = acc[k];
         }
+        if (f32 && lane < 3) A.Cf_lo[3 * c + lane] = lo1;
         __syncwarp();
         if (lane == 0) {
             fence_acq_rel_gpu();
@@ -583,6 +622,9 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(EvalArgs A) {
             const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
             l2p<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
                          ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
+            lx += __ldg(&A.Cf_lo[3 * leaf]);   // low parts of the order-1 coefficients
+            ly += __ldg(&A.Cf_lo[3 * leaf + 1]);
+            lz += __ldg(&A.Cf_lo[3 * leaf + 2]);
             lx *= irf; ly *= irf; lz *= irf;
         } else {
             const double irho = 1.0 / A.rho[leaf];
@@ -652,7 +694,7 @@ void launch_descend(ncorp_ctx *c, int p, bool mixed) {
     DescendArgs D;
     D.parent = C.parent;
     D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
-    D.Ch = C.Ch; D.Cf = C.Cf; D.done = C.done; D.work = c->work_counter + 1; D.ctl = c->ctl;
+    D.Ch = C.Ch; D.Cf = C.Cf; D.Cf_lo = C.Cf_lo; D.done = C.done; D.work = c->work_counter + 1; D.ctl = c->ctl;
 #define NCORP_DESC_CASE(PP)                      \
     case PP:                                     \
         if (mixed) descend_t<PP, float>(c, D);   \
@@ -679,6 +721,7 @@ static EvalArgs eval_args(ncorp_ctx *c, const ParticleSet &P, double G, ExtForce
     A.sx = C.sx; A.sy = C.sy; A.sz = C.sz; A.rho = C.rho;
     A.gh = C.gh; A.gl = C.gl;
     A.Cf = C.Cf;
+    A.Cf_lo = C.Cf_lo;
     A.p2p_off = c->wl.p2p_off; A.p2p_src = c->wl.p2p_src; A.p2p_dir_cap = c->wl.p2p_dir_cap;
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m;
     A.hi4 = P.hi4; A.lo4 = P.lo4;

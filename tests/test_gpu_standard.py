@@ -134,12 +134,13 @@ def collide_standard(d, dt, s=16, thresholds=(0, 16)):
                                                      (20000, 33, False, (0, 16))])
 def test_collision_search_equals_oracle_and_brute_force(n, seed, dense, thresholds):
     """Algorithm StandardTree's collision search on the GPU: the same pair set as the oracle's tree search
-    and as brute force (bit-exact), the same direct-search decisions and tested pairs as the oracle."""
+    and as brute force (bit-exact), the same direct-search decisions and tested pairs as the oracle.  The
+    wide disk has moonlets ten times larger than the workloads' so that it has pairs to find."""
     if dense:
         d = diskgen.make_disk(n, seed, a_lo=2.0, a_hi=2.5, r_lo=2e-2, r_hi=5e-2, sigma_e=0.1, sigma_i=0.05)
     else:
-        d = diskgen.make_disk(n, seed)
-    dt = 0.05 if dense else 1e-2
+        d = diskgen.make_disk(n, seed, r_lo=1e-2, r_hi=1e-1)
+    dt = 0.05
     got, st = collide_standard(d, dt, thresholds=thresholds)
     P = oracle.params(p=3, theta=0.5, leaf_size=16, standard_collision_thresholds=thresholds)
     ref, ost = oracle.collide_standard(P, d["pos"], d["vel"], d["radius"], dt)
