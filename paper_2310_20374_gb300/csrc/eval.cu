@@ -149,17 +149,6 @@ __device__ __forceinline__ real shift_axis(const real *src, const real (&w)[P + 
     return s;
 }
 
-// (hi, lo) + b with hi + lo renormalised: Knuth's two-sum of hi and b, its
-// error added to lo
-__device__ __forceinline__ void df_add(float &hi, float &lo, float b) {
-    const float s = hi + b;
-    const float bv = s - hi;
-    const float e = (hi - (s - bv)) + (b - bv);
-    const float l = lo + e;
-    hi = s + l;
-    lo = l - (hi - s);
-}
-
 __device__ __forceinline__ unsigned ld_acquire_u32_any(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -448,7 +437,10 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
 // lane takes two targets (the sources are read once for both), below it the
 // lanes form G = 32 / T groups of T = pow2ceil(m) lanes that share the
 // stage's sources (k = g, g + G, ...) and add their partial sums at the end
-// (shuffles in a fixed order).
+// (shuffles in a fixed order).  Every lane sums at most 32 sources in FP32
+// before it adds that partial sum to a double-float total (two-sum), so that
+// the rounding of a long FP32 running sum (dominated by the nearest pull) does
+// not grow with the length of the direct list.
 // ---------------------------------------------------------------------------
 constexpr int NW_WARPS = 4;
 constexpr int NW_STAGE = 128;
@@ -550,6 +542,8 @@ __global__ void __launch_bounds__(32 * NW_WARPS) k_near(EvalArgs A) {
             const int ia = f + t0 + (actA ? tt : 0), ib = f + t0 + (actB ? 32 + lane : 0);
             const float4 thA = A.hi4[ia], tlA = A.lo4[ia], thB = A.hi4[ib], tlB = A.lo4[ib];
             float axA = 0.f, ayA = 0.f, azA = 0.f, axB = 0.f, ayB = 0.f, azB = 0.f;
+            // double-float totals: (hi, lo) per component and target
+            float hA[3] = {0.f, 0.f, 0.f}, lA[3] = {0.f, 0.f, 0.f}, hB[3] = {0.f, 0.f, 0.f}, lB[3] = {0.f, 0.f, 0.f};
             int si = s0, soff = 0;
             __syncwarp();
             fence_proxy_async();   // the ring was read with ordinary loads before
@@ -564,36 +558,50 @@ __global__ void __launch_bounds__(32 * NW_WARPS) k_near(EvalArgs A) {
                 phase ^= 1u << buf;
                 const float4 *H = W.hi[buf], *Lo = W.lo[buf];
                 if (two) {
+                    for (int k0 = 0; k0 < tot; k0 += 32) {
+                        const int k1 = min(tot, k0 + 32);
 #pragma unroll 4
-                    for (int k = 0; k < tot; k++) {
-                        const float4 h = H[k], l = Lo[k];
-                        p2p_f32(h, l, thA, tlA, axA, ayA, azA);
-                        p2p_f32(h, l, thB, tlB, axB, ayB, azB);
+                        for (int k = k0; k < k1; k++) {
+                            const float4 h = H[k], l = Lo[k];
+                            p2p_f32(h, l, thA, tlA, axA, ayA, azA);
+                            p2p_f32(h, l, thB, tlB, axB, ayB, azB);
+                        }
+                        df_add(hA[0], lA[0], axA); df_add(hA[1], lA[1], ayA); df_add(hA[2], lA[2], azA);
+                        df_add(hB[0], lB[0], axB); df_add(hB[1], lB[1], ayB); df_add(hB[2], lB[2], azB);
+                        axA = ayA = azA = axB = ayB = azB = 0.f;
                     }
                 } else {
+                    for (int k0 = g; k0 < tot; k0 += 32 * G) {
+                        const int k1 = min(tot, k0 + 32 * G);
 #pragma unroll 4
-                    for (int k = g; k < tot; k += G) p2p_f32(H[k], Lo[k], thA, tlA, axA, ayA, azA);
+                        for (int k = k0; k < k1; k += G) p2p_f32(H[k], Lo[k], thA, tlA, axA, ayA, azA);
+                        df_add(hA[0], lA[0], axA); df_add(hA[1], lA[1], ayA); df_add(hA[2], lA[2], azA);
+                        axA = ayA = azA = 0.f;
+                    }
                 }
                 __syncwarp();
                 fence_proxy_async();   // this buffer's reads are done before it is refilled
                 buf = nb;
                 tot = tot_next;
             }
-            // partial sums of the groups, added in a fixed order
+            // partial sums of the groups, added in a fixed order (the high parts by two-sums)
             for (int o = T; o < 32; o <<= 1) {
-                axA += __shfl_xor_sync(0xffffffffu, axA, o);
-                ayA += __shfl_xor_sync(0xffffffffu, ayA, o);
-                azA += __shfl_xor_sync(0xffffffffu, azA, o);
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, hA[q], o), ol = __shfl_xor_sync(0xffffffffu, lA[q], o);
+                    df_add(hA[q], lA[q], oh);
+                    lA[q] += ol;
+                }
             }
             if (g == 0 && actA) {
-                A.nx[f + t0 + tt] = static_cast<double>(axA);
-                A.ny[f + t0 + tt] = static_cast<double>(ayA);
-                A.nz[f + t0 + tt] = static_cast<double>(azA);
+                A.nx[f + t0 + tt] = static_cast<double>(hA[0]) + static_cast<double>(lA[0]);
+                A.ny[f + t0 + tt] = static_cast<double>(hA[1]) + static_cast<double>(lA[1]);
+                A.nz[f + t0 + tt] = static_cast<double>(hA[2]) + static_cast<double>(lA[2]);
             }
             if (actB) {
-                A.nx[f + t0 + 32 + lane] = static_cast<double>(axB);
-                A.ny[f + t0 + 32 + lane] = static_cast<double>(ayB);
-                A.nz[f + t0 + 32 + lane] = static_cast<double>(azB);
+                A.nx[f + t0 + 32 + lane] = static_cast<double>(hB[0]) + static_cast<double>(lB[0]);
+                A.ny[f + t0 + 32 + lane] = static_cast<double>(hB[1]) + static_cast<double>(lB[1]);
+                A.nz[f + t0 + 32 + lane] = static_cast<double>(hB[2]) + static_cast<double>(lB[2]);
             }
         }
     }
@@ -633,9 +641,10 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(EvalArgs A) {
         }
         double ex, ey, ez;
         external_force(A.ext, X, Y, Z, ex, ey, ez);
-        const double mx = static_cast<double>(lx + static_cast<real>(A.nx[i]));
-        const double my = static_cast<double>(ly + static_cast<real>(A.ny[i]));
-        const double mz = static_cast<double>(lz + static_cast<real>(A.nz[i]));
+        // far part + near sums, added in FP64 (the near sums arrive as double-float totals)
+        const double mx = static_cast<double>(lx) + A.nx[i];
+        const double my = static_cast<double>(ly) + A.ny[i];
+        const double mz = static_cast<double>(lz) + A.nz[i];
         const double gx = mx + ex, gy = my + ey, gz = mz + ez;
         A.ax[i] = gx;
         A.ay[i] = gy;

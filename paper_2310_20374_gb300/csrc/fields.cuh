@@ -78,17 +78,35 @@ __device__ __forceinline__ void external_force(const ExtForce &E, double X, doub
 
 // One near-field pair, FP32: the separation from the (hi, lo) pairs, then
 // mu_j d / |d|^3; a coincident pair (r^2 = 0, the moonlet itself) adds 0.
+// The hardware reciprocal square root y carries a relative error d of a few
+// 1e-8 that y^3 triples; with the residual e = 1 - r^2 y^2 = -2d (one FMA),
+// y^3 (1 + 3e/2) = r^-3 (1 + O(d^2)) removes it, so that a term is accurate
+// to the rounding of its few products (a moonlet whose neighbours' pulls
+// nearly cancel sees every term's error against a small total).
 __device__ __forceinline__ void p2p_f32(const float4 &h, const float4 &l, const float4 &th, const float4 &tl, float &ax,
                                         float &ay, float &az) {
     const float dx = (h.x - th.x) + (l.x - tl.x);
     const float dy = (h.y - th.y) + (l.y - tl.y);
     const float dz = (h.z - th.z) + (l.z - tl.z);
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float inv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-    const float f3 = h.w * inv * inv * inv;
+    const float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float y2 = y * y;
+    const float e = fmaf(-r2, y2, 1.0f);
+    const float f = h.w * (y2 * y);
+    const float f3 = fmaf(f, 1.5f * e, f);
     ax += dx * f3;
     ay += dy * f3;
     az += dz * f3;
+}
+
+// (hi, lo) + b, renormalised (Knuth's two-sum of hi and b, its error added to lo)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float b) {
+    const float s = hi + b;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (b - bv);
+    const float l = lo + e;
+    hi = s + l;
+    lo = l - (hi - s);
 }
 
 __device__ __forceinline__ void p2p_f64(double jx, double jy, double jz, double mu, double X, double Y, double Z,

@@ -666,28 +666,40 @@ constexpr int P2M_WARPS = 4;
 
 template <int P, typename real>
 struct M2MShared {
-    real m[P2M_WARPS][num_m(P) < 1 ? 1 : num_m(P)];
-    real w[P2M_WARPS][3][P];   // delta_axis^k / k!
-    real r[P2M_WARPS][P];      // r^n
+    real a[P2M_WARPS][off(P) < 1 ? 1 : off(P)];   // full storage, orders 0..P-1 (dipole slots included)
+    real b[P2M_WARPS][off(P) < 1 ? 1 : off(P)];
+    real w[P2M_WARPS][3][P];                       // delta_axis^k / k!
 };
 
-// the multi-index (a, b, c) of multipole slot j (orders 0, 2..P-1)
+// (n, b + c, c) of slot j of the full storage (orders 0..P-1)
 template <int P>
-__device__ __forceinline__ void m_exps(int j, int &a, int &b, int &c) {
-    a = b = c = 0;
+__device__ __forceinline__ void full_exps(int j, int &n, int &kk, int &c) {
+    n = kk = c = 0;
 #pragma unroll
-    for (int n = 0; n < P; n++) {
-        if (n == 1) continue;
+    for (int nn = 0; nn < P; nn++)
 #pragma unroll
-        for (int k = 0; k <= n; k++)
+        for (int k = 0; k <= nn; k++)
 #pragma unroll
             for (int cc = 0; cc <= k; cc++)
-                if (midx(n - k, k - cc, cc) == j) {
-                    a = n - k;
-                    b = k - cc;
+                if (sidx(nn - k, k - cc, cc) == j) {
+                    n = nn;
+                    kk = k;
                     c = cc;
                 }
+}
+
+// One-dimensional shift of full-storage moments along AXIS: out(a,b,c) = sum_{k <= exponent} in(... - k e_axis) w_k
+template <int P, int AXIS, typename real>
+__device__ __forceinline__ real m_shift(const real *in, const real (&w)[P], int n, int kk, int c) {
+    const int ax = AXIS == 0 ? n - kk : (AXIS == 1 ? kk - c : c);   // the exponent along the axis
+    real s = real(0);
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        if (k > ax) break;
+        const int m = n - k, t = AXIS == 0 ? kk : kk - k, cc = AXIS == 2 ? c - k : c;
+        s += in[m * (m + 1) * (m + 2) / 6 + t * (t + 1) / 2 + cc] * w[k];
     }
+    return s;
 }
 
 template <int P, typename real>
@@ -722,73 +734,86 @@ __device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, int lane, 
     store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
 }
 
+// M2M of a parent from its children, as three one-dimensional shifts per
+// child (the expansion of (d_c + delta)^beta / beta! factorises over the
+// axes): the child's moments scaled by r^|gamma| go into full storage with
+// zero dipole slots, are shifted along x, y and z by delta, and the slots of
+// orders 0 and 2..P-1 are added to the parent's sums (its dipole about its own
+// centre of mass vanishes).
 template <int P, typename real>
 __device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, real> &S, int wl, int pc, int lane,
                                                real *Mh) {
-    constexpr int NM = num_m(P);
-    constexpr int PER = (NM + 31) / 32;
-    int ea[PER], eb[PER], ec[PER];
+    constexpr int NM = num_m(P), NF = off(P);
+    constexpr int PER = (NF + 31) / 32;
+    int en[PER], ek[PER], ec[PER];
 #pragma unroll
-    for (int q = 0; q < PER; q++) m_exps<P>(lane + 32 * q, ea[q], eb[q], ec[q]);
+    for (int q = 0; q < PER; q++) full_exps<P>(lane + 32 * q, en[q], ek[q], ec[q]);
     real acc[PER];
 #pragma unroll
     for (int q = 0; q < PER; q++) acc[q] = real(0);
     const int c0 = A.child0[pc], nch = A.nchild[pc];
     real ipr;
-    if constexpr (sizeof(real) == 4) ipr = 1.0f / A.gl[pc].w;
+    if constexpr (sizeof(real) == 4) ipr = 1.0f / A.gl[pc].w;   // exact: rho is a power of two
     else ipr = 1.0 / A.rho[pc];
+    real *sa = S.a[wl], *sb = S.b[wl];
     for (int ch = 0; ch < nch; ch++) {
         const int c = c0 + ch;
-        __syncwarp();
-        for (int j = lane; j < NM; j += 32) S.m[wl][j] = __ldcg(&Mh[(size_t)c * NM + j]);
-        if (lane < 3) {   // delta^k / k! along axis `lane`
-            real d;
-            if constexpr (sizeof(real) == 4) {
-                const float4 ch_h = A.gh[c], ch_l = A.gl[c], p_h = A.gh[pc], p_l = A.gl[pc];
-                d = lane == 0 ? (ch_h.x - p_h.x) + (ch_l.x - p_l.x)
-                              : (lane == 1 ? (ch_h.y - p_h.y) + (ch_l.y - p_l.y) : (ch_h.z - p_h.z) + (ch_l.z - p_l.z));
-            } else {
-                d = lane == 0 ? A.sx[c] - A.sx[pc] : (lane == 1 ? A.sy[c] - A.sy[pc] : A.sz[c] - A.sz[pc]);
-            }
-            d *= ipr;
-            real w = real(1);
-            S.w[wl][lane][0] = w;
+        real dx, dy, dz, rr;
+        if constexpr (sizeof(real) == 4) {
+            const float4 ch_h = A.gh[c], ch_l = A.gl[c], p_h = A.gh[pc], p_l = A.gl[pc];
+            dx = ((ch_h.x - p_h.x) + (ch_l.x - p_l.x)) * ipr;
+            dy = ((ch_h.y - p_h.y) + (ch_l.y - p_l.y)) * ipr;
+            dz = ((ch_h.z - p_h.z) + (ch_l.z - p_l.z)) * ipr;
+            rr = ch_l.w * ipr;
+        } else {
+            dx = (A.sx[c] - A.sx[pc]) * ipr;
+            dy = (A.sy[c] - A.sy[pc]) * ipr;
+            dz = (A.sz[c] - A.sz[pc]) * ipr;
+            rr = A.rho[c] * ipr;
+        }
+        real wx[P], wy[P], wz[P];
+        wx[0] = wy[0] = wz[0] = real(1);
 #pragma unroll
-            for (int k = 1; k < P; k++) {
-                w *= d;
-                S.w[wl][lane][k] = w * static_cast<real>(ifact(k));
-            }
-        } else if (lane == 3) {
-            real rr;
-            if constexpr (sizeof(real) == 4) rr = A.gl[c].w * ipr;   // exact: powers of two
-            else rr = A.rho[c] * ipr;
-            real v = real(1);
+        for (int k = 1; k < P; k++) {
+            wx[k] = wx[k - 1] * dx;
+            wy[k] = wy[k - 1] * dy;
+            wz[k] = wz[k - 1] * dz;
+        }
 #pragma unroll
-            for (int n = 0; n < P; n++) {
-                S.r[wl][n] = v;
-                v *= rr;
-            }
+        for (int k = 2; k < P; k++) {
+            const real f = static_cast<real>(ifact(k));
+            wx[k] *= f; wy[k] *= f; wz[k] *= f;
         }
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (lane + 32 * q >= NM) continue;
-            const int a = ea[q], b = eb[q], cz = ec[q];
-            real s = real(0);
-            for (int a2 = 0; a2 <= a; a2++)
-                for (int b2 = 0; b2 <= b; b2++)
-                    for (int c2 = 0; c2 <= cz; c2++) {
-                        const int n2 = a2 + b2 + c2;
-                        if (n2 == 1) continue;
-                        s += S.m[wl][midx(a2, b2, c2)] * S.r[wl][n2] * S.w[wl][0][a - a2] * S.w[wl][1][b - b2] *
-                             S.w[wl][2][cz - c2];
-                    }
-            acc[q] += s;
+        for (int q = 0; q < PER; q++) {   // child's moments, scaled by r^n, dipole slots zero
+            const int j = lane + 32 * q;
+            if (j >= NF) continue;
+            real v = real(0);
+            if (en[q] != 1) {
+                v = __ldcg(&Mh[(size_t)c * NM + (en[q] == 0 ? 0 : j - 3)]);
+                for (int t = 0; t < en[q]; t++) v *= rr;
+            }
+            sa[j] = v;
         }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PER; q++)
+            if (lane + 32 * q < NF) sb[lane + 32 * q] = m_shift<P, 0>(sa, wx, en[q], ek[q], ec[q]);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PER; q++)
+            if (lane + 32 * q < NF) sa[lane + 32 * q] = m_shift<P, 1>(sb, wy, en[q], ek[q], ec[q]);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PER; q++)
+            if (lane + 32 * q < NF) acc[q] += m_shift<P, 2>(sa, wz, en[q], ek[q], ec[q]);
     }
 #pragma unroll
-    for (int q = 0; q < PER; q++)
-        if (lane + 32 * q < NM) Mh[(size_t)pc * NM + lane + 32 * q] = acc[q];
+    for (int q = 0; q < PER; q++) {
+        const int j = lane + 32 * q;
+        if (j < NF && en[q] != 1) Mh[(size_t)pc * NM + (en[q] == 0 ? 0 : j - 3)] = acc[q];
+    }
 }
 
 template <int P, typename real>
