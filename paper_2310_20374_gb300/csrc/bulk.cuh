@@ -34,6 +34,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
         ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
+// one arrival (no bytes) on the barrier
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}"
+        ::"r"(smem_addr(bar)) : "memory");
+}
+
 // true when the barrier's phase with the given parity has completed
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     unsigned done;

@@ -38,6 +38,7 @@ struct Cells {
     float4 *bl = nullptr;     // collision centre lo (xyz)
     void *Mh = nullptr;       // [cap][num_m(p)] multipoles (float or double)
     void *Ch = nullptr;       // [cap][num_c(p)] local coefficients of the cell's own M2L (float or double)
+    float *Ch_lo = nullptr;   // [cap][3] mixed precision: low parts of the order-1 coefficients of Ch
     void *Cf = nullptr;       // [cap][num_c(p)] complete local expansion after the descent
     float *Cf_lo = nullptr;   // [cap][3] mixed precision: low parts of the order-1 coefficients of Cf
                               // (double-float: the field is the sum of the whole far field)

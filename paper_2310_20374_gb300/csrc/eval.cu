@@ -87,6 +87,31 @@ __device__ __forceinline__ void l2p(const real *C, real hx, real hy, real hz, re
             }
 }
 
+// l2p without the terms of the order-1 coefficients (the field at the centre)
+template <int P, typename real>
+__device__ __forceinline__ void l2p_high(const real *C, real hx, real hy, real hz, real &ax, real &ay, real &az) {
+    real wx[P], wy[P], wz[P];
+    wx[0] = wy[0] = wz[0] = real(1);
+#pragma unroll
+    for (int k = 1; k < P; k++) {
+        wx[k] = wx[k - 1] * hx;
+        wy[k] = wy[k - 1] * hy;
+        wz[k] = wz[k - 1] * hz;
+    }
+#pragma unroll
+    for (int nb = 1; nb < P; nb++)
+#pragma unroll
+        for (int kb = 0; kb <= nb; kb++)
+#pragma unroll
+            for (int cb = 0; cb <= kb; cb++) {
+                const int ab = nb - kb, bb = kb - cb;
+                const real w = wx[ab] * wy[bb] * wz[cb] * static_cast<real>(inv_mfact(ab, bb, cb));
+                ax += C[cidx(ab + 1, bb, cb)] * w;
+                ay += C[cidx(ab, bb + 1, cb)] * w;
+                az += C[cidx(ab, bb, cb + 1)] * w;
+            }
+}
+
 // ---------------------------------------------------------------------------
 // Tree descent (Sect. 3.4.3, Eq. shifting): every cell's complete local
 // expansion is its own M2L sum plus its parent's complete expansion
@@ -122,6 +147,7 @@ struct DescendArgs {
     const float4 *gh, *gl;
     const double *sx, *sy, *sz, *rho;
     const void *Ch;
+    const float *Ch_lo;        // [cells][3] mixed: low parts of the own order-1 sums
     void *Cf;
     float *Cf_lo;              // [cells][3] mixed: low parts of the order-1 coefficients
     unsigned *done;            // [cells]: epoch of the descent that completed the cell
@@ -197,6 +223,8 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
         }
         // mixed: the order-1 pair of this cell (lanes 0..2); the root's is its own M2L sum
         float hi1 = f32 ? static_cast<float>(acc[0]) : 0.0f, lo1 = 0.0f, phi = 0.0f, plo = 0.0f;
+        const float own_lo = (f32 && lane < 3) ? __ldg(&A.Ch_lo[3 * c + lane]) : 0.0f;
+        lo1 = own_lo;
         const int a = A.parent[c];
         if (a >= 0) {
             int ok = 1;
@@ -268,6 +296,7 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
                     lo1 = plo * static_cast<float>(ratio);
                     df_add(hi1, lo1, static_cast<float>(s));
                     df_add(hi1, lo1, static_cast<float>(acc[0]));
+                    lo1 += own_lo;
                     acc[0] = static_cast<real>(hi1);
                 } else {
                     acc[k] += s;
@@ -424,47 +453,55 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Near field in mixed precision, one warp per target leaf (claimed
-// dynamically), sources streamed through shared memory by the copy engine.
+// Near field in mixed precision: one block of NB_THREADS threads per target
+// leaf (claimed dynamically), the leaf's direct-list sources streamed through
+// a two-stage ring in shared memory by the copy engine.
 //
-// The leaf's direct list is a sequence of source leaves, each a contiguous
-// run of the tree-ordered (hi, lo) arrays (16-byte float4 elements), so a
-// stage of up to NW_STAGE sources is a few bulk copies (cp.async.bulk, one
-// per source-leaf piece and array) completed on the stage's mbarrier.  Each
-// warp owns a ring of two stages: while it sums the sources of one stage the
-// copies of the next are in flight, and no barrier wider than the warp is
-// ever taken.  Targets: a leaf of m <= 64 moonlets at a time; above 32 every
-// lane takes two targets (the sources are read once for both), below it the
-// lanes form G = 32 / T groups of T = pow2ceil(m) lanes that share the
-// stage's sources (k = g, g + G, ...) and add their partial sums at the end
-// (shuffles in a fixed order).  Every lane sums at most 32 sources in FP32
-// before it adds that partial sum to a double-float total (two-sum), so that
-// the rounding of a long FP32 running sum (dominated by the nearest pull) does
-// not grow with the length of the direct list.
+// The direct list is a sequence of source leaves, each a contiguous run of the
+// tree-ordered (hi, lo) arrays (16-byte float4 elements), so a stage of up to
+// NB_STAGE sources is a few bulk copies (cp.async.bulk, one per source-leaf
+// piece and array) completed on the stage's "full" mbarrier.  Warp 0 plans
+// the stages and issues the copies of the next stage while every warp sums
+// the current one; a warp done with a stage arrives on its "empty" mbarrier,
+// which warp 0 waits for before refilling that buffer.  No block-wide barrier
+// is taken per stage.  A stage with no sources ends the leaf's list.
+//
+// Targets: the leaf's m moonlets (NB_THREADS at a time) are taken by
+// G = floor(NB_THREADS / m) groups of m threads; thread (g, t) sums the
+// stage's sources k = g, g + G, ... for target t, so a leaf of a few moonlets
+// keeps the threads busy.  Every thread sums at most 32 sources in FP32 before
+// it adds that partial sum to a double-float total (two-sum), so that the
+// rounding of a long FP32 running sum (dominated by the nearest pull) does
+// not grow with the list; the groups' totals are added in group order.
 // ---------------------------------------------------------------------------
-constexpr int NW_WARPS = 4;
-constexpr int NW_STAGE = 128;
+constexpr int NB_THREADS = 128;
+constexpr int NB_WARPS = NB_THREADS / 32;
+constexpr int NB_STAGE = 128;
 
-struct NearWarpSmem {
-    float4 hi[2][NW_STAGE];
-    float4 lo[2][NW_STAGE];
-    uint64_t bar[2];
+struct NearBlockSmem {
+    float4 hi[2][NB_STAGE];
+    float4 lo[2][NB_STAGE];
+    uint64_t full[2], empty[2];
+    int tot[2];
+    float red[6][NB_THREADS];
+    int leaf;
 };
 
 // Plans the next stage of the direct list [si, s1) (si advanced past the source leaves taken whole,
-// soff = moonlets of the source leaf at si already taken), arms buffer b's barrier and issues the
-// copies.  Returns the stage's source count (0: the list is exhausted, nothing issued).  All lanes.
-__device__ __forceinline__ int near_issue(const EvalArgs &A, NearWarpSmem &W, int b, int &si, int &soff, int s1,
+// soff = moonlets of the source leaf at si already taken), writes its size to S.tot[b], arms the full
+// barrier of buffer b and issues the copies.  Warp 0 only (all its lanes); returns the stage's size
+// (0: the list is exhausted and the stage is the end marker).
+__device__ __forceinline__ int near_issue(const EvalArgs &A, NearBlockSmem &S, int b, int &si, int &soff, int s1,
                                           int lane) {
-    if (si >= s1) return 0;
+    const bool more = si < s1;
     const int idx = si + lane;
     int fst = 0, c = 0;
-    if (idx < s1) {
+    if (more && idx < s1) {
         const int src = A.p2p_src[idx];
         fst = A.first[src];
         c = A.count[src];
     }
-    if (lane == 0) {
+    if (more && lane == 0) {
         fst += soff;
         c -= soff;
     }
@@ -475,134 +512,122 @@ __device__ __forceinline__ int near_issue(const EvalArgs &A, NearWarpSmem &W, in
         if (lane >= o) inc += v;
     }
     const int exc = inc - c;
-    const int tot = min(NW_STAGE, __shfl_sync(0xffffffffu, inc, 31));
-    if (lane == 0) mbar_arrive_expect_tx(&W.bar[b], static_cast<unsigned>(tot) * 32u);
+    const int tot = min(NB_STAGE, __shfl_sync(0xffffffffu, inc, 31));
+    if (lane == 0) {
+        S.tot[b] = tot;
+        mbar_arrive_expect_tx(&S.full[b], static_cast<unsigned>(tot) * 32u);   // 0 bytes: the end marker
+    }
     __syncwarp();
     const int take = min(inc, tot) - exc;
-    if (idx < s1 && take > 0) {
-        bulk_g2s(&W.hi[b][exc], &A.hi4[fst], static_cast<unsigned>(take) * 16u, &W.bar[b]);
-        bulk_g2s(&W.lo[b][exc], &A.lo4[fst], static_cast<unsigned>(take) * 16u, &W.bar[b]);
+    if (more && idx < s1 && take > 0) {
+        bulk_g2s(&S.hi[b][exc], &A.hi4[fst], static_cast<unsigned>(take) * 16u, &S.full[b]);
+        bulk_g2s(&S.lo[b][exc], &A.lo4[fst], static_cast<unsigned>(take) * 16u, &S.full[b]);
     }
-    // source leaves taken whole; the next one may be cut where the stage ends
-    const unsigned whole = __ballot_sync(0xffffffffu, idx < s1 && inc <= tot);
-    const int L = __popc(whole);
-    const int excL = __shfl_sync(0xffffffffu, exc, L & 31);
-    soff = (L < 32 && si + L < s1) ? (L == 0 ? soff : 0) + (tot - excL) : 0;
-    si += L;
+    if (more) {   // source leaves taken whole; the next one may be cut where the stage ends
+        const unsigned whole = __ballot_sync(0xffffffffu, idx < s1 && inc <= tot);
+        const int L = __popc(whole);
+        const int excL = __shfl_sync(0xffffffffu, exc, L & 31);
+        soff = (L < 32 && si + L < s1) ? (L == 0 ? soff : 0) + (tot - excL) : 0;
+        si += L;
+    }
     return tot;
 }
 
-// Waits (bounded) for buffer b's copies; false after a time-out (ERR_TIMEOUT set).
-__device__ __forceinline__ bool near_wait(const EvalArgs &A, NearWarpSmem &W, int b, unsigned parity,
-                                          unsigned long long limit, int lane) {
-    int ok = 1;
-    if (lane == 0) {
-        const unsigned long long t0 = global_ns();
-        while (!mbar_try_wait(&W.bar[b], parity)) {
-            if (global_ns() - t0 > limit) {
-                atomicOr(const_cast<int *>(&A.ctl->err), ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
+// Bounded wait for a barrier phase by one thread; false (ERR_TIMEOUT set) if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned long long limit, Ctrl *ctl) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit) {
+            atomicOr(&ctl->err, ERR_TIMEOUT);
+            return false;
         }
     }
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    return true;
 }
 
-__global__ void __launch_bounds__(32 * NW_WARPS) k_near(EvalArgs A) {
-    __shared__ __align__(128) NearWarpSmem S[NW_WARPS];
+__global__ void __launch_bounds__(NB_THREADS) k_near(EvalArgs A) {
+    __shared__ __align__(128) NearBlockSmem S;
     if (aborted(A.ctl)) return;
-    const int lane = threadIdx.x & 31;
-    NearWarpSmem &W = S[threadIdx.x >> 5];
-    if (lane == 0) {
-        mbar_init(&W.bar[0], 1);
-        mbar_init(&W.bar[1], 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Ctrl *ctl = const_cast<Ctrl *>(A.ctl);
+    if (tid == 0) {
+        mbar_init(&S.full[0], 1);
+        mbar_init(&S.full[1], 1);
+        mbar_init(&S.empty[0], NB_WARPS);
+        mbar_init(&S.empty[1], NB_WARPS);
         mbar_init_fence();
     }
-    __syncwarp();
+    __syncthreads();
     const unsigned long long limit = A.ctl->wait_ns ? A.ctl->wait_ns : 1000000000ull;
     const int nl = A.ctl->n_leaves;
-    unsigned phase = 0;   // bit b: parity of the next completion of buffer b
-    int buf = 0;          // the buffer the next stage goes to
+    unsigned fph = 0, eph = 0, filled = 0;   // per buffer: full / empty parities, ever filled (warp 0)
+    int buf = 0;                             // the buffer of the next stage
     while (true) {
-        int li = 0;
-        if (lane == 0) li = atomicAdd(A.work, 1);
-        li = __shfl_sync(0xffffffffu, li, 0);
+        if (tid == 0) S.leaf = aborted(A.ctl) ? nl : atomicAdd(A.work, 1);
+        __syncthreads();
+        const int li = S.leaf;
         if (li >= nl) break;
         const int leaf = A.leaves[li];
         const int f = A.first[leaf], cnt = A.count[leaf];
         const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
-        for (int t0 = 0; t0 < cnt; t0 += 64) {
-            const int m = min(64, cnt - t0);
-            const bool two = m > 32;
-            int lg = 0;
-            while ((1 << lg) < m && lg < 5) lg++;
-            const int T = two ? 32 : (1 << lg), G = 32 / T, tt = lane & (T - 1), g = lane / T;
-            const bool actA = tt < m, actB = two && 32 + lane < m;
-            const int ia = f + t0 + (actA ? tt : 0), ib = f + t0 + (actB ? 32 + lane : 0);
-            const float4 thA = A.hi4[ia], tlA = A.lo4[ia], thB = A.hi4[ib], tlB = A.lo4[ib];
-            float axA = 0.f, ayA = 0.f, azA = 0.f, axB = 0.f, ayB = 0.f, azB = 0.f;
-            // double-float totals: (hi, lo) per component and target
-            float hA[3] = {0.f, 0.f, 0.f}, lA[3] = {0.f, 0.f, 0.f}, hB[3] = {0.f, 0.f, 0.f}, lB[3] = {0.f, 0.f, 0.f};
-            int si = s0, soff = 0;
-            __syncwarp();
-            fence_proxy_async();   // the ring was read with ordinary loads before
-            int tot = near_issue(A, W, buf, si, soff, s1, lane);
-            while (tot > 0) {
-                const int nb = buf ^ 1;
-                const int tot_next = near_issue(A, W, nb, si, soff, s1, lane);
-                if (!near_wait(A, W, buf, (phase >> buf) & 1u, limit, lane)) {
-                    if (tot_next > 0) near_wait(A, W, nb, (phase >> nb) & 1u, limit, lane);   // copies in flight
-                    return;
+        for (int t0 = 0; t0 < cnt; t0 += NB_THREADS) {
+            const int m = min(NB_THREADS, cnt - t0);
+            const int G = NB_THREADS / m, g = tid / m, tt = tid - g * m;
+            const bool act = g < G;   // the last NB_THREADS - G m threads only help with the ring
+            const int i = f + t0 + (act ? tt : 0);
+            const float4 th = A.hi4[i], tl = A.lo4[i];
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+            int si = s0, soff = 0, last = 1;
+            auto produce = [&](int b) {   // warp 0: refill buffer b once every warp has released it
+                if (filled & (1u << b)) {   // every lane observes the phase
+                    mbar_wait_bounded(&S.empty[b], (eph >> b) & 1u, limit, ctl);
+                    __syncwarp();
+                    eph ^= 1u << b;
                 }
-                phase ^= 1u << buf;
-                const float4 *H = W.hi[buf], *Lo = W.lo[buf];
-                if (two) {
-                    for (int k0 = 0; k0 < tot; k0 += 32) {
-                        const int k1 = min(tot, k0 + 32);
-#pragma unroll 4
-                        for (int k = k0; k < k1; k++) {
-                            const float4 h = H[k], l = Lo[k];
-                            p2p_f32(h, l, thA, tlA, axA, ayA, azA);
-                            p2p_f32(h, l, thB, tlB, axB, ayB, azB);
-                        }
-                        df_add(hA[0], lA[0], axA); df_add(hA[1], lA[1], ayA); df_add(hA[2], lA[2], azA);
-                        df_add(hB[0], lB[0], axB); df_add(hB[1], lB[1], ayB); df_add(hB[2], lB[2], azB);
-                        axA = ayA = azA = axB = ayB = azB = 0.f;
-                    }
-                } else {
+                fence_proxy_async();   // the buffer's ordinary reads are done before the copies
+                filled |= 1u << b;
+                last = near_issue(A, S, b, si, soff, s1, lane);
+            };
+            if (warp == 0) produce(buf);
+            while (true) {
+                if (warp == 0 && last > 0) produce(buf ^ 1);   // the next stage (or the end marker)
+                // every thread observes the phase (the copies' data and S.tot are then visible to it)
+                const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&S.full[buf], (fph >> buf) & 1u, limit, ctl));
+                fph ^= 1u << buf;
+                const int tot = ok ? S.tot[buf] : 0;
+                if (act && tot > 0) {
+                    const float4 *H = S.hi[buf], *Lo = S.lo[buf];
                     for (int k0 = g; k0 < tot; k0 += 32 * G) {
                         const int k1 = min(tot, k0 + 32 * G);
 #pragma unroll 4
-                        for (int k = k0; k < k1; k += G) p2p_f32(H[k], Lo[k], thA, tlA, axA, ayA, azA);
-                        df_add(hA[0], lA[0], axA); df_add(hA[1], lA[1], ayA); df_add(hA[2], lA[2], azA);
-                        axA = ayA = azA = 0.f;
+                        for (int k = k0; k < k1; k += G) p2p_f32(H[k], Lo[k], th, tl, ax, ay, az);
+                        df_add(h[0], l[0], ax); df_add(h[1], l[1], ay); df_add(h[2], l[2], az);
+                        ax = ay = az = 0.f;
                     }
                 }
                 __syncwarp();
-                fence_proxy_async();   // this buffer's reads are done before it is refilled
-                buf = nb;
-                tot = tot_next;
+                if (lane == 0) mbar_arrive(&S.empty[buf]);
+                buf ^= 1;
+                if (tot == 0) break;
             }
-            // partial sums of the groups, added in a fixed order (the high parts by two-sums)
-            for (int o = T; o < 32; o <<= 1) {
+            // totals of the groups, added in group order
+            S.red[0][tid] = h[0]; S.red[1][tid] = h[1]; S.red[2][tid] = h[2];
+            S.red[3][tid] = l[0]; S.red[4][tid] = l[1]; S.red[5][tid] = l[2];
+            __syncthreads();
+            if (g == 0 && act) {
+                float th3[3] = {0.f, 0.f, 0.f}, tl3[3] = {0.f, 0.f, 0.f};
+                for (int q = 0; q < G; q++)
 #pragma unroll
-                for (int q = 0; q < 3; q++) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, hA[q], o), ol = __shfl_xor_sync(0xffffffffu, lA[q], o);
-                    df_add(hA[q], lA[q], oh);
-                    lA[q] += ol;
-                }
+                    for (int d = 0; d < 3; d++) {
+                        df_add(th3[d], tl3[d], S.red[d][q * m + tt]);
+                        tl3[d] += S.red[3 + d][q * m + tt];
+                    }
+                A.nx[i] = static_cast<double>(th3[0]) + static_cast<double>(tl3[0]);
+                A.ny[i] = static_cast<double>(th3[1]) + static_cast<double>(tl3[1]);
+                A.nz[i] = static_cast<double>(th3[2]) + static_cast<double>(tl3[2]);
             }
-            if (g == 0 && actA) {
-                A.nx[f + t0 + tt] = static_cast<double>(hA[0]) + static_cast<double>(lA[0]);
-                A.ny[f + t0 + tt] = static_cast<double>(hA[1]) + static_cast<double>(lA[1]);
-                A.nz[f + t0 + tt] = static_cast<double>(hA[2]) + static_cast<double>(lA[2]);
-            }
-            if (actB) {
-                A.nx[f + t0 + 32 + lane] = static_cast<double>(hB[0]) + static_cast<double>(lB[0]);
-                A.ny[f + t0 + 32 + lane] = static_cast<double>(hB[1]) + static_cast<double>(lB[1]);
-                A.nz[f + t0 + 32 + lane] = static_cast<double>(hB[2]) + static_cast<double>(lB[2]);
-            }
+            __syncthreads();
         }
     }
 }
@@ -623,28 +648,31 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(EvalArgs A) {
         const int leaf = __ldg(&A.leaf_of[i]);
         const real *C = Cf + (size_t)leaf * NC;
         const double X = A.x[i], Y = A.y[i], Z = A.z[i];
-        real lx = real(0), ly = real(0), lz = real(0);
+        double fx, fy, fz;   // the far field at the moonlet
         if constexpr (f32) {
+            // the order-1 pair (hi in Cf, lo in Cf_lo) and the higher orders, added in FP64
             const float4 lgh = __ldg(&A.gh[leaf]), lgl = __ldg(&A.gl[leaf]);
             const float4 th = A.hi4[i], tl = A.lo4[i];
             const float irf = 1.0f / lgl.w;   // exact: rho is a power of two
-            l2p<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
-                         ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
-            lx += __ldg(&A.Cf_lo[3 * leaf]);   // low parts of the order-1 coefficients
-            ly += __ldg(&A.Cf_lo[3 * leaf + 1]);
-            lz += __ldg(&A.Cf_lo[3 * leaf + 2]);
-            lx *= irf; ly *= irf; lz *= irf;
+            float lx = 0.f, ly = 0.f, lz = 0.f;
+            l2p_high<P, real>(C, ((th.x - lgh.x) + (tl.x - lgl.x)) * irf, ((th.y - lgh.y) + (tl.y - lgl.y)) * irf,
+                              ((th.z - lgh.z) + (tl.z - lgl.z)) * irf, lx, ly, lz);
+            const double ir = static_cast<double>(irf);
+            fx = ((static_cast<double>(C[0]) + static_cast<double>(__ldg(&A.Cf_lo[3 * leaf]))) + static_cast<double>(lx)) * ir;
+            fy = ((static_cast<double>(C[1]) + static_cast<double>(__ldg(&A.Cf_lo[3 * leaf + 1]))) + static_cast<double>(ly)) * ir;
+            fz = ((static_cast<double>(C[2]) + static_cast<double>(__ldg(&A.Cf_lo[3 * leaf + 2]))) + static_cast<double>(lz)) * ir;
         } else {
             const double irho = 1.0 / A.rho[leaf];
+            real lx = real(0), ly = real(0), lz = real(0);
             l2p<P, real>(C, (X - A.sx[leaf]) * irho, (Y - A.sy[leaf]) * irho, (Z - A.sz[leaf]) * irho, lx, ly, lz);
-            lx *= irho; ly *= irho; lz *= irho;
+            fx = lx * irho; fy = ly * irho; fz = lz * irho;
         }
         double ex, ey, ez;
         external_force(A.ext, X, Y, Z, ex, ey, ez);
         // far part + near sums, added in FP64 (the near sums arrive as double-float totals)
-        const double mx = static_cast<double>(lx) + A.nx[i];
-        const double my = static_cast<double>(ly) + A.ny[i];
-        const double mz = static_cast<double>(lz) + A.nz[i];
+        const double mx = fx + A.nx[i];
+        const double my = fy + A.ny[i];
+        const double mz = fz + A.nz[i];
         const double gx = mx + ex, gy = my + ey, gz = mz + ez;
         A.ax[i] = gx;
         A.ay[i] = gy;
@@ -671,10 +699,10 @@ static void descend_t(ncorp_ctx *c, DescendArgs D) {
 
 static void near_mixed(ncorp_ctx *c, const EvalArgs &A) {
     int per_sm = 0;
-    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, reinterpret_cast<const void *>(k_near), 32 * NW_WARPS, 0));
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_near),
+                                                                   NB_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
-    k_near<<<per_sm * c->num_sms, 32 * NW_WARPS, 0, c->stream>>>(A);
+    k_near<<<per_sm * c->num_sms, NB_THREADS, 0, c->stream>>>(A);
     c->launches++;
 }
 
@@ -703,7 +731,7 @@ void launch_descend(ncorp_ctx *c, int p, bool mixed) {
     DescendArgs D;
     D.parent = C.parent;
     D.gh = C.gh; D.gl = C.gl; D.sx = C.sx; D.sy = C.sy; D.sz = C.sz; D.rho = C.rho;
-    D.Ch = C.Ch; D.Cf = C.Cf; D.Cf_lo = C.Cf_lo; D.done = C.done; D.work = c->work_counter + 1; D.ctl = c->ctl;
+    D.Ch = C.Ch; D.Ch_lo = C.Ch_lo; D.Cf = C.Cf; D.Cf_lo = C.Cf_lo; D.done = C.done; D.work = c->work_counter + 1; D.ctl = c->ctl;
 #define NCORP_DESC_CASE(PP)                      \
     case PP:                                     \
         if (mixed) descend_t<PP, float>(c, D);   \

@@ -16,6 +16,12 @@
 // so that the per-entry sum needs no alpha-dependent factor and the 1/rho_A is
 // applied once per target.
 //
+// Mixed precision: the order-1 coefficients (the field) of every source's
+// contribution are formed in FP32 and added to double-float totals (two-sum),
+// and the lanes' totals are combined the same way, so that the field of a
+// target cell, summed over many sources whose pulls largely cancel, keeps the
+// accuracy of the single contributions; the low parts go to Ch_lo.
+//
 // Work layout: the directed entries (target, source) are grouped by target.
 // One warp per target cell: the lanes take the target's sources in turn, each
 // accumulating the target's coefficients in registers; a butterfly reduction
@@ -37,6 +43,7 @@ struct M2LArgs {
     const float4 *gh, *gl;
     const void *Mh;
     void *Ch;
+    float *Ch_lo;       // mixed: low parts of the order-1 sums
     Ctrl *ctl;
     int *desc_work;     // the descent's claim counter, zeroed here
 };
@@ -80,8 +87,10 @@ __global__ void __launch_bounds__(32 * M2L_WARPS, 3) k_m2l(M2LArgs A) {
                 tz = A.sz[c];
             }
         }
+        float lo1[3] = {0.f, 0.f, 0.f};   // mixed: low parts of acc[0..2]
         for (int e = e0 + lane; e < e1; e += 32) {
             const int src = A.dir[e].y;
+            real t1[3] = {real(0), real(0), real(0)};   // this source's order-1 contribution
             real ux, uy, uz, q;
             if constexpr (f32) {   // separation from double-float centres, no FP64 work
                 const float4 sh = A.gh[src], sl = A.gl[src];
@@ -118,7 +127,8 @@ __global__ void __launch_bounds__(32 * M2L_WARPS, 3) k_m2l(M2LArgs A) {
 #pragma unroll
                                 for (int ca = 0; ca <= ka; ca++) {
                                     const int aa = na - ka, ba = ka - ca;
-                                    acc[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
+                                    if (na == 1) t1[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
+                                    else acc[cidx(aa, ba, ca)] += D[sidx(aa + ab, ba + bb, ca + cb)] * w;
                                 }
                             }
                         }
@@ -126,12 +136,31 @@ __global__ void __launch_bounds__(32 * M2L_WARPS, 3) k_m2l(M2LArgs A) {
                 }
                 qn *= q;
             }
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if constexpr (f32) df_add(acc[d], lo1[d], t1[d]);
+                else acc[d] += t1[d];
+            }
         }
         // sums over the lanes (the same on every lane), scaled by 1/rho_A; lane l stores l, l + 32, ...
         const real f = f32 ? static_cast<real>(irf) : static_cast<real>(irho);
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             real v = acc[i];
+            if (f32 && i < 3) {   // order 1: double-float butterfly
+                float hv = static_cast<float>(v), lv = lo1[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, hv, o), ol = __shfl_xor_sync(0xffffffffu, lv, o);
+                    df_add(hv, lv, oh);
+                    lv += ol;
+                }
+                if (i == lane) {
+                    Ch[(size_t)c * NC + i] = static_cast<real>(hv) * f;
+                    A.Ch_lo[3 * c + i] = lv * static_cast<float>(f);   // f: a power of two
+                }
+                continue;
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if ((i & 31) == lane) Ch[(size_t)c * NC + i] = v * f;
@@ -154,6 +183,7 @@ void launch_m2l(ncorp_ctx *c, int p, bool mixed) {
     A.gh = C.gh; A.gl = C.gl;
     A.Mh = C.Mh;
     A.Ch = C.Ch;
+    A.Ch_lo = C.Ch_lo;
     A.ctl = c->ctl;
     A.desc_work = c->work_counter + 1;
 #define NCORP_M2L_CASE(PP)                       \

@@ -129,6 +129,7 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.maker, cap);
     dalloc(C.before, cap);
     dalloc(C.Cf_lo, 3 * static_cast<size_t>(cap));
+    dalloc(C.Ch_lo, 3 * static_cast<size_t>(cap));
     dalloc(C.done, cap);   // descent epochs start at 1: zeroed words never match
     NCORP_CUDA_CHECK(cudaMemset(C.done, 0, sizeof(unsigned) * cap));
     WalkLists &W = c->wl;
@@ -1346,7 +1347,7 @@ void ncorp_free(ncorp_ctx *c) {
         dfree(C.level); dfree(C.first); dfree(C.count); dfree(C.child0); dfree(C.nchild); dfree(C.parent);
         dfree(C.arrive); dfree(C.arrive_m); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
         dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
-        dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.Cf_lo);
+        dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.Cf_lo); dfree(C.Ch_lo);
         dfree(C.leaves); dfree(C.leaf_of); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
         WalkLists &W = c->wl;
         dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);

@@ -666,9 +666,8 @@ constexpr int P2M_WARPS = 4;
 
 template <int P, typename real>
 struct M2MShared {
-    real a[P2M_WARPS][off(P) < 1 ? 1 : off(P)];   // full storage, orders 0..P-1 (dipole slots included)
-    real b[P2M_WARPS][off(P) < 1 ? 1 : off(P)];
-    real w[P2M_WARPS][3][P];                       // delta_axis^k / k!
+    real a[P2M_WARPS][8][off(P) < 1 ? 1 : off(P)];   // per child: full storage, orders 0..P-1
+    real b[P2M_WARPS][8][off(P) < 1 ? 1 : off(P)];
 };
 
 // (n, b + c, c) of slot j of the full storage (orders 0..P-1)
@@ -738,56 +737,56 @@ __device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, int lane, 
 // child (the expansion of (d_c + delta)^beta / beta! factorises over the
 // axes): the child's moments scaled by r^|gamma| go into full storage with
 // zero dipole slots, are shifted along x, y and z by delta, and the slots of
-// orders 0 and 2..P-1 are added to the parent's sums (its dipole about its own
-// centre of mass vanishes).
+// orders 0 and 2..P-1 are summed over the children in child order (the
+// parent's dipole about its own centre of mass vanishes).  The children are
+// shifted side by side: four lanes per child (a parent has at most eight),
+// each lane a quarter of the child's slots.
 template <int P, typename real>
 __device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, real> &S, int wl, int pc, int lane,
                                                real *Mh) {
     constexpr int NM = num_m(P), NF = off(P);
-    constexpr int PER = (NF + 31) / 32;
-    int en[PER], ek[PER], ec[PER];
-#pragma unroll
-    for (int q = 0; q < PER; q++) full_exps<P>(lane + 32 * q, en[q], ek[q], ec[q]);
-    real acc[PER];
-#pragma unroll
-    for (int q = 0; q < PER; q++) acc[q] = real(0);
+    constexpr int PER4 = (NF + 3) / 4;   // slots per lane of a child's quad
+    const int ch = lane >> 2, sub = lane & 3;
     const int c0 = A.child0[pc], nch = A.nchild[pc];
-    real ipr;
-    if constexpr (sizeof(real) == 4) ipr = 1.0f / A.gl[pc].w;   // exact: rho is a power of two
-    else ipr = 1.0 / A.rho[pc];
-    real *sa = S.a[wl], *sb = S.b[wl];
-    for (int ch = 0; ch < nch; ch++) {
-        const int c = c0 + ch;
-        real dx, dy, dz, rr;
-        if constexpr (sizeof(real) == 4) {
-            const float4 ch_h = A.gh[c], ch_l = A.gl[c], p_h = A.gh[pc], p_l = A.gl[pc];
-            dx = ((ch_h.x - p_h.x) + (ch_l.x - p_l.x)) * ipr;
-            dy = ((ch_h.y - p_h.y) + (ch_l.y - p_l.y)) * ipr;
-            dz = ((ch_h.z - p_h.z) + (ch_l.z - p_l.z)) * ipr;
-            rr = ch_l.w * ipr;
-        } else {
-            dx = (A.sx[c] - A.sx[pc]) * ipr;
-            dy = (A.sy[c] - A.sy[pc]) * ipr;
-            dz = (A.sz[c] - A.sz[pc]) * ipr;
-            rr = A.rho[c] * ipr;
-        }
-        real wx[P], wy[P], wz[P];
-        wx[0] = wy[0] = wz[0] = real(1);
+    const bool act = ch < nch;
+    const int c = act ? c0 + ch : c0;
+    real ipr, dx, dy, dz, rr;
+    if constexpr (sizeof(real) == 4) {
+        const float4 ch_h = A.gh[c], ch_l = A.gl[c], p_h = A.gh[pc], p_l = A.gl[pc];
+        ipr = 1.0f / p_l.w;   // exact: rho is a power of two
+        dx = ((ch_h.x - p_h.x) + (ch_l.x - p_l.x)) * ipr;
+        dy = ((ch_h.y - p_h.y) + (ch_l.y - p_l.y)) * ipr;
+        dz = ((ch_h.z - p_h.z) + (ch_l.z - p_l.z)) * ipr;
+        rr = ch_l.w * ipr;
+    } else {
+        ipr = 1.0 / A.rho[pc];
+        dx = (A.sx[c] - A.sx[pc]) * ipr;
+        dy = (A.sy[c] - A.sy[pc]) * ipr;
+        dz = (A.sz[c] - A.sz[pc]) * ipr;
+        rr = A.rho[c] * ipr;
+    }
+    real wx[P], wy[P], wz[P];
+    wx[0] = wy[0] = wz[0] = real(1);
 #pragma unroll
-        for (int k = 1; k < P; k++) {
-            wx[k] = wx[k - 1] * dx;
-            wy[k] = wy[k - 1] * dy;
-            wz[k] = wz[k - 1] * dz;
-        }
+    for (int k = 1; k < P; k++) {
+        wx[k] = wx[k - 1] * dx;
+        wy[k] = wy[k - 1] * dy;
+        wz[k] = wz[k - 1] * dz;
+    }
 #pragma unroll
-        for (int k = 2; k < P; k++) {
-            const real f = static_cast<real>(ifact(k));
-            wx[k] *= f; wy[k] *= f; wz[k] *= f;
-        }
-        __syncwarp();
+    for (int k = 2; k < P; k++) {
+        const real f = static_cast<real>(ifact(k));
+        wx[k] *= f; wy[k] *= f; wz[k] *= f;
+    }
+    int en[PER4], ek[PER4], ec[PER4];
 #pragma unroll
-        for (int q = 0; q < PER; q++) {   // child's moments, scaled by r^n, dipole slots zero
-            const int j = lane + 32 * q;
+    for (int q = 0; q < PER4; q++) full_exps<P>(sub + 4 * q, en[q], ek[q], ec[q]);
+    real *sa = S.a[wl][ch], *sb = S.b[wl][ch];
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < PER4; q++) {   // the child's moments, scaled by r^n, dipole slots zero
+            const int j = sub + 4 * q;
             if (j >= NF) continue;
             real v = real(0);
             if (en[q] != 1) {
@@ -796,23 +795,34 @@ __device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, re
             }
             sa[j] = v;
         }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < PER; q++)
-            if (lane + 32 * q < NF) sb[lane + 32 * q] = m_shift<P, 0>(sa, wx, en[q], ek[q], ec[q]);
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < PER; q++)
-            if (lane + 32 * q < NF) sa[lane + 32 * q] = m_shift<P, 1>(sb, wy, en[q], ek[q], ec[q]);
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < PER; q++)
-            if (lane + 32 * q < NF) acc[q] += m_shift<P, 2>(sa, wz, en[q], ek[q], ec[q]);
     }
+    __syncwarp();
+    if (act) {
 #pragma unroll
-    for (int q = 0; q < PER; q++) {
-        const int j = lane + 32 * q;
-        if (j < NF && en[q] != 1) Mh[(size_t)pc * NM + (en[q] == 0 ? 0 : j - 3)] = acc[q];
+        for (int q = 0; q < PER4; q++)
+            if (sub + 4 * q < NF) sb[sub + 4 * q] = m_shift<P, 0>(sa, wx, en[q], ek[q], ec[q]);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < PER4; q++)
+            if (sub + 4 * q < NF) sa[sub + 4 * q] = m_shift<P, 1>(sb, wy, en[q], ek[q], ec[q]);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < PER4; q++)
+            if (sub + 4 * q < NF) sb[sub + 4 * q] = m_shift<P, 2>(sa, wz, en[q], ek[q], ec[q]);
+    }
+    __syncwarp();
+    // sums over the children in child order; lane j takes slots j, j + 32
+    for (int j = lane; j < NF; j += 32) {
+        int n, kk, cc;
+        full_exps<P>(j, n, kk, cc);
+        if (n == 1) continue;
+        real acc = real(0);
+        for (int k = 0; k < nch; k++) acc += S.b[wl][k][j];
+        Mh[(size_t)pc * NM + (n == 0 ? 0 : j - 3)] = acc;
     }
 }
 
