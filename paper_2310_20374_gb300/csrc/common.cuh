@@ -103,6 +103,7 @@ struct Ctrl {
     int n_p2p_dir;
     unsigned bar_count;
     unsigned bar_gen;
+    unsigned bar_count2;   // grid barrier of the multipole kernel (runs beside the walk; zeroed by the build)
     int walk_abort[3];     // walk: overflow seen in generation g, slot g mod 3
     long long dec_pairs;   // walk decisions: direct cell pairs
     long long dec_self;    // walk decisions: direct self cells
@@ -172,17 +173,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ bool grid_sync(Ctrl *ctl, unsigned &passed) {
+// the barrier on any arrival counter (ctl->bar_count or a kernel's own)
+__device__ __forceinline__ bool grid_sync_on(unsigned *counter, Ctrl *ctl, unsigned &passed) {
     __syncthreads();
     __shared__ int s_ok;
     passed += gridDim.x;
     if (threadIdx.x == 0) {
-        red_release_add_u32(&ctl->bar_count, 1u);
+        red_release_add_u32(counter, 1u);
         int ok = 1;
         const unsigned long long t0 = global_ns();
         const unsigned long long limit = ctl->wait_ns ? ctl->wait_ns : 1000000000ull;
         const unsigned target = passed + (ctl->stall ? 1u : 0u);
-        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(&ctl->bar_count) - target) < 0; spins++) {
+        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(counter) - target) < 0; spins++) {
             if ((spins & 255u) == 255u && global_ns() - t0 > limit) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
                 ok = 0;
@@ -194,6 +196,8 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctl, unsigned &passed) {
     __syncthreads();
     return s_ok != 0;
 }
+
+__device__ __forceinline__ bool grid_sync(Ctrl *ctl, unsigned &passed) { return grid_sync_on(&ctl->bar_count, ctl, passed); }
 
 // ---- warp helpers -----------------------------------------------------------
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -62,7 +62,7 @@ struct WalkLists {
     int *cnt = nullptr, *offs = nullptr, *cursor = nullptr;     // per-cell counting sort scratch [cap+1]
     int2 *m2l_dir = nullptr;      // (target, source) grouped by target
     int *p2p_off = nullptr;       // [cap+1] offsets of each target leaf's sources
-    int *p2p_src = nullptr;       // source leaf of each directed entry
+    int2 *p2p_src = nullptr;      // each directed entry's source leaf as (first moonlet, moonlet count)
 };
 
 // One tree with everything a walk over it produces: cells, walk lists and

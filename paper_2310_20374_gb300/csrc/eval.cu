@@ -48,7 +48,8 @@ struct EvalArgs {
     const float4 *gh, *gl;
     const void *Cf;   // complete local expansions
     const float *Cf_lo;   // mixed: low parts of their order-1 coefficients
-    const int *p2p_off, *p2p_src;
+    const int *p2p_off;
+    const int2 *p2p_src;      // per directed entry: the source leaf's (first, count)
     int p2p_dir_cap;
     const double *x, *y, *z, *m;
     const float4 *hi4, *lo4;
@@ -372,9 +373,9 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
                     const int idx = si + lane;
                     int fst = 0, c = 0;
                     if (idx < s1) {
-                        const int src = A.p2p_src[idx];
-                        fst = A.first[src];
-                        c = A.count[src];
+                        const int2 e = A.p2p_src[idx];
+                        fst = e.x;
+                        c = e.y;
                     }
                     if (lane == 0) { fst += soff; c -= soff; }
                     int inc = c;
@@ -468,8 +469,8 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
 //
 // Targets: the leaf's m moonlets (NB_THREADS at a time) are taken by
 // G = floor(NB_THREADS / m) groups of m threads; thread (g, t) sums the
-// stage's sources k = g, g + G, ... for target t, so a leaf of a few moonlets
-// keeps the threads busy.  Every thread sums at most 32 sources in FP32 before
+// g-th of G contiguous slices of the stage's sources for target t, so a leaf
+// of a few moonlets keeps the threads busy.  Every thread sums at most 32 sources in FP32 before
 // it adds that partial sum to a double-float total (two-sum), so that the
 // rounding of a long FP32 running sum (dominated by the nearest pull) does
 // not grow with the list; the groups' totals are added in group order.
@@ -497,9 +498,9 @@ __device__ __forceinline__ int near_issue(const EvalArgs &A, NearBlockSmem &S, i
     const int idx = si + lane;
     int fst = 0, c = 0;
     if (more && idx < s1) {
-        const int src = A.p2p_src[idx];
-        fst = A.first[src];
-        c = A.count[src];
+        const int2 e = A.p2p_src[idx];
+        fst = e.x;
+        c = e.y;
     }
     if (more && lane == 0) {
         fst += soff;
@@ -596,12 +597,13 @@ __global__ void __launch_bounds__(NB_THREADS) k_near(EvalArgs A) {
                 const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&S.full[buf], (fph >> buf) & 1u, limit, ctl));
                 fph ^= 1u << buf;
                 const int tot = ok ? S.tot[buf] : 0;
-                if (act && tot > 0) {
+                if (act && tot > 0) {   // group g: the contiguous slice [tot g / G, tot (g + 1) / G) of the stage
                     const float4 *H = S.hi[buf], *Lo = S.lo[buf];
-                    for (int k0 = g; k0 < tot; k0 += 32 * G) {
-                        const int k1 = min(tot, k0 + 32 * G);
+                    const int ka = (tot * g) / G, kb = (tot * (g + 1)) / G;
+                    for (int k0 = ka; k0 < kb; k0 += 32) {
+                        const int k1 = min(kb, k0 + 32);
 #pragma unroll 4
-                        for (int k = k0; k < k1; k += G) p2p_f32(H[k], Lo[k], th, tl, ax, ay, az);
+                        for (int k = k0; k < k1; k++) p2p_f32(H[k], Lo[k], th, tl, ax, ay, az);
                         df_add(h[0], l[0], ax); df_add(h[1], l[1], ay); df_add(h[2], l[2], az);
                         ax = ay = az = 0.f;
                     }

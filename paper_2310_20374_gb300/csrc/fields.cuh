@@ -77,7 +77,7 @@ __device__ __forceinline__ void external_force(const ExtForce &E, double X, doub
 }
 
 // One near-field pair, FP32: the separation from the (hi, lo) pairs, then
-// mu_j d / |d|^3; a coincident pair (r^2 = 0, the moonlet itself) adds 0.
+// mu_j d / |d|^3; a coincident pair (d = 0, the moonlet itself) adds 0.
 // The hardware reciprocal square root y carries a relative error d of a few
 // 1e-8 that y^3 triples; with the residual e = 1 - r^2 y^2 = -2d (one FMA),
 // y^3 (1 + 3e/2) = r^-3 (1 + O(d^2)) removes it, so that a term is accurate
@@ -88,8 +88,10 @@ __device__ __forceinline__ void p2p_f32(const float4 &h, const float4 &l, const 
     const float dx = (h.x - th.x) + (l.x - tl.x);
     const float dy = (h.y - th.y) + (l.y - tl.y);
     const float dz = (h.z - th.z) + (l.z - tl.z);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float y = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    // r^2 below 1e-20 (coincident pairs, the moonlet itself) is raised to 1e-20: y^3 stays finite and
+    // d = 0 makes the term 0 (pairs closer than 1e-10 do not occur in a disk of moonlets)
+    const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-20f);
+    const float y = rsqrtf(r2);
     const float y2 = y * y;
     const float e = fmaf(-r2, y2, 1.0f);
     const float f = h.w * (y2 * y);

@@ -155,7 +155,7 @@ void alloc_lists(ncorp_ctx *c, int front, int m2l, int p2p, int self) {
     if (p2p != W.p2p_cap || self != W.self_cap) {
         dalloc(W.p2p, p2p);
         dalloc(W.self, self);
-        dalloc(W.p2p_src, 2 * static_cast<size_t>(p2p) + self);
+        dalloc(W.p2p_src, 2 * static_cast<size_t>(p2p) + self);   // int2
         W.p2p_cap = p2p;
         W.self_cap = self;
         W.p2p_dir_cap = 2 * p2p + self;

@@ -89,6 +89,7 @@ __global__ void k_build_init(BuildArgs A) {
     A.ctl->bar_count = 0;
     A.arrive[0] = 0;        // arrival counters of the collision climb and of the multipoles,
     A.arrive_m[0] = 0;      // zeroed as cells are made
+    A.ctl->bar_count2 = 0;  // the multipole kernel's grid barrier
 }
 
 // Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
@@ -646,10 +647,7 @@ __device__ __forceinline__ void parent_gravity_group(const ClimbArgs &A, int c, 
 //   M-hat_P(beta) = sum_children sum_{gamma <= beta, |gamma| != 1}
 //                   M-hat_c(gamma) r^|gamma| delta^(beta - gamma) / (beta - gamma)!
 // (the multinomial expansion of (d_c + delta)^beta / beta!, axis by axis).
-// One launch, no waiting: a warp that has finished a cell adds its arrival to
-// the parent's counter, and the warp that arrives last computes the parent
-// (its children are all done), then goes on up; the children are added in
-// child order, so the result does not depend on who arrives last.
+// The children are added in child order.
 struct P2MArgs {
     const double *x, *y, *z, *m;
     const float4 *hi4, *lo4;
@@ -826,39 +824,39 @@ __device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, re
     }
 }
 
+// Level by level in one cooperative launch: the leaves' moments from their
+// moonlets, then the parents of each level from the deepest up, one grid
+// barrier per level (every parent of a level in parallel).
 template <int P, typename real>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_multipoles(P2MArgs A) {
     __shared__ M2MShared<P, real> S;
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    // warps numbered across the blocks first, so that consecutive work items land on different SMs
+    const int gw0 = wl * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nl = A.ctl->n_leaves;
     real *Mh = static_cast<real *>(A.Mh);
-    for (int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < nl; li += nwarps) {
-        int c = A.leaves[li];
-        leaf_moments<P, real>(A, c, lane, Mh);
-        while (true) {   // up the tree while this warp is the last child to finish
-            const int pc = A.parent[c];
-            if (pc < 0) break;
-            __syncwarp();
-            int last = 0;
-            if (lane == 0) {
-                fence_acq_rel_gpu();   // release: this cell's moments before the arrival
-                last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
-                if (last) fence_acq_rel_gpu();   // acquire: the other children's moments
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (!last) break;
-            __syncwarp();
-            parent_moments<P, real>(A, S, wl, pc, lane, Mh);
-            c = pc;
-        }
+    for (int li = gw0; li < nl; li += nwarps) leaf_moments<P, real>(A, A.leaves[li], lane, Mh);
+    unsigned bar = 0;
+    if (!grid_sync_on(&A.ctl->bar_count2, A.ctl, bar)) return;
+    const int maxl = A.ctl->max_level;
+    for (int lev = maxl - 1; lev >= 0; lev--) {
+        const int ls = A.ctl->level_start[lev], le = A.ctl->level_start[lev + 1];
+        for (int c = ls + gw0; c < le; c += nwarps)
+            if (A.nchild[c] > 0) parent_moments<P, real>(A, S, wl, c, lane, Mh);
+        if (lev > 0 && !grid_sync_on(&A.ctl->bar_count2, A.ctl, bar)) return;
     }
 }
 
 template <int P, typename real>
 static void p2m_t(ncorp_ctx *c, const P2MArgs &B) {
-    k_multipoles<P, real><<<4 * c->num_sms, 32 * P2M_WARPS, 0, c->stream>>>(B); c->launches++;
+    // cooperative (every block resident: the level barriers); up to two blocks per SM beside the walk
+    const int grid = coop_grid(c, reinterpret_cast<const void *>(k_multipoles<P, real>), 32 * P2M_WARPS, 0);
+    P2MArgs args = B;
+    void *kargs[] = {&args};
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_multipoles<P, real>), dim3(grid),
+                                                 dim3(32 * P2M_WARPS), kargs, 0, c->stream));
+    c->launches++;
 }
 
 // theta(M) of Dehnen (2002) Eq. 13: theta^5/(1-theta)^2 = K (M/M_tot)^(-1/3),

@@ -41,7 +41,9 @@ struct WalkArgs {
     int *self;
     int self_cap;
     // per-target lists (gravity): counting sort by target cell
-    int *cnt, *offs, *cursor, *p2p_off, *p2p_src;
+    int *cnt, *offs, *cursor, *p2p_off;
+    int2 *p2p_src;             // per directed near-field entry: the source leaf's (first, count)
+    const int *first;
     int2 *m2l_dir;
     int m2l_dir_cap, p2p_dir_cap;
     int *work;                 // gravity: the near-field kernel's work counter, zeroed by k_walk_init
@@ -221,13 +223,13 @@ __device__ void walk_lists(const WalkArgs &A, int *s_tmp, unsigned &bar) {
             }
         } else if (i < nm + np) {
             if (a < A.p2p_dir_cap && b < A.p2p_dir_cap) {
-                A.p2p_src[a] = e.y;
-                A.p2p_src[b] = e.x;
+                A.p2p_src[a] = make_int2(__ldg(&A.first[e.y]), __ldg(&A.count[e.y]));
+                A.p2p_src[b] = make_int2(__ldg(&A.first[e.x]), __ldg(&A.count[e.x]));
             } else {
                 atomicOr(&A.ctl->err, ERR_DIRECTED);
             }
         } else if (i < total) {
-            if (a < A.p2p_dir_cap) A.p2p_src[a] = e.x;
+            if (a < A.p2p_dir_cap) A.p2p_src[a] = make_int2(__ldg(&A.first[e.x]), __ldg(&A.count[e.x]));
             else atomicOr(&A.ctl->err, ERR_DIRECTED);
         }
     }
@@ -471,7 +473,7 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     A.n_cs = gravity ? c->g_cs : c->c_cs;
     A.pre = gravity ? c->g_pre : c->c_pre;
     A.post = gravity ? c->g_post : c->c_post;
-    A.count = C.count; A.child0 = C.child0; A.nchild = C.nchild;
+    A.count = C.count; A.first = C.first; A.child0 = C.child0; A.nchild = C.nchild;
     A.sx = gravity ? C.sx : C.bx;
     A.sy = gravity ? C.sy : C.by;
     A.sz = gravity ? C.sz : C.bz;
