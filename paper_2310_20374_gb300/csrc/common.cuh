@@ -103,7 +103,6 @@ struct Ctrl {
     int n_p2p_dir;
     unsigned bar_count;
     unsigned bar_gen;
-    unsigned bar_count2;   // grid barrier of the multipole kernel (runs beside the walk; zeroed by the build)
     int walk_abort[3];     // walk: overflow seen in generation g, slot g mod 3
     long long dec_pairs;   // walk decisions: direct cell pairs
     long long dec_self;    // walk decisions: direct self cells

@@ -18,7 +18,6 @@
 // pair.
 #include <type_traits>
 
-#include "bulk.cuh"
 #include "ctx.h"
 #include "fields.cuh"
 
@@ -324,9 +323,12 @@ __global__ void __launch_bounds__(32 * DESC_WARPS) k_descend(DescendArgs A) {
 // out dynamically.  The leaf's m targets (taken EV_THREADS at a time if the
 // leaf is larger) are taken by G = floor(EV_THREADS / m) groups of m threads:
 // thread (g, t) sums the staged sources k = g, g + G, g + 2G, ... for target
-// t, so a leaf of a few moonlets keeps the lanes busy.  The G partial sums of a target are then added in group
-// order.  The direct list is staged
-// EV_BUF moonlets at a time, cutting source leaves where the buffer ends.
+// t, so a leaf of a few moonlets keeps the lanes busy.  The direct list is
+// staged EV_BUF moonlets at a time, cutting source leaves where the buffer
+// ends.  Mixed precision: every thread adds its FP32 partial sum to a
+// double-float total every 32 sources (two-sum), and the groups' totals are
+// added in group order, so that the rounding of a long FP32 running sum
+// (dominated by the nearest pull) does not grow with the direct list.
 // ---------------------------------------------------------------------------
 constexpr int EV_THREADS = 128;
 constexpr int EV_BUF = 512;
@@ -335,7 +337,7 @@ template <int P, typename real>
 struct EvShared {
     __align__(16) unsigned char buf[EV_BUF * 32];   // FP32: float4 hi[EV_BUF] (xyz, mu), lo[EV_BUF]
                                                     // FP64: double x, y, z, mu [EV_BUF]
-    real red[3][EV_THREADS];
+    real red[6][EV_THREADS];
     int lfirst[32], lpre[32];
     int leaf, total, next_si, next_soff;
 };
@@ -366,6 +368,8 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
             const float4 th = A.hi4[i], tl = A.lo4[i];
             const double X = A.x[i], Y = A.y[i], Z = A.z[i];
             real ax = real(0), ay = real(0), az = real(0);
+            // mixed: double-float totals, to which the FP32 partial sums are added every 32 sources
+            float h3[3] = {0.f, 0.f, 0.f}, l3[3] = {0.f, 0.f, 0.f};
             int si = s0, soff = 0;
             while (si < s1) {
                 __syncthreads();
@@ -421,215 +425,66 @@ __global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
                 __syncthreads();
                 if (act) {
                     if constexpr (f32) {
+                        for (int k0 = g; k0 < total; k0 += 32 * G) {
+                            const int k1 = min(total, k0 + 32 * G);
 #pragma unroll 4
-                        for (int k = g; k < total; k += G) p2p_f32(sh[k], sl[k], th, tl, ax, ay, az);
+                            for (int k = k0; k < k1; k += G) p2p_f32(sh[k], sl[k], th, tl, ax, ay, az);
+                            df_add(h3[0], l3[0], ax); df_add(h3[1], l3[1], ay); df_add(h3[2], l3[2], az);
+                            ax = ay = az = 0.f;
+                        }
                     } else {
 #pragma unroll 2
                         for (int k = g; k < total; k += G) p2p_f64(bx[k], by[k], bz[k], bm[k], X, Y, Z, ax, ay, az);
                     }
                 }
             }
-            if (G > 1) {
-                __syncthreads();
-                S.red[0][tid] = ax;
-                S.red[1][tid] = ay;
-                S.red[2][tid] = az;
-                __syncthreads();
-                if (g == 0) {
-                    ax = ay = az = real(0);
-                    for (int q = 0; q < G; q++) {
-                        ax += S.red[0][q * m + tt];
-                        ay += S.red[1][q * m + tt];
-                        az += S.red[2][q * m + tt];
-                    }
-                }
-            }
-            if (g == 0 && act) {
-                A.nx[i] = static_cast<double>(ax);
-                A.ny[i] = static_cast<double>(ay);
-                A.nz[i] = static_cast<double>(az);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Near field in mixed precision: one block of NB_THREADS threads per target
-// leaf (claimed dynamically), the leaf's direct-list sources streamed through
-// a two-stage ring in shared memory by the copy engine.
-//
-// The direct list is a sequence of source leaves, each a contiguous run of the
-// tree-ordered (hi, lo) arrays (16-byte float4 elements), so a stage of up to
-// NB_STAGE sources is a few bulk copies (cp.async.bulk, one per source-leaf
-// piece and array) completed on the stage's "full" mbarrier.  Warp 0 plans
-// the stages and issues the copies of the next stage while every warp sums
-// the current one; a warp done with a stage arrives on its "empty" mbarrier,
-// which warp 0 waits for before refilling that buffer.  No block-wide barrier
-// is taken per stage.  A stage with no sources ends the leaf's list.
-//
-// Targets: the leaf's m moonlets (NB_THREADS at a time) are taken by
-// G = floor(NB_THREADS / m) groups of m threads; thread (g, t) sums the
-// g-th of G contiguous slices of the stage's sources for target t, so a leaf
-// of a few moonlets keeps the threads busy.  Every thread sums at most 32 sources in FP32 before
-// it adds that partial sum to a double-float total (two-sum), so that the
-// rounding of a long FP32 running sum (dominated by the nearest pull) does
-// not grow with the list; the groups' totals are added in group order.
-// ---------------------------------------------------------------------------
-constexpr int NB_THREADS = 128;
-constexpr int NB_WARPS = NB_THREADS / 32;
-constexpr int NB_STAGE = 128;
-
-struct NearBlockSmem {
-    float4 hi[2][NB_STAGE];
-    float4 lo[2][NB_STAGE];
-    uint64_t full[2], empty[2];
-    int tot[2];
-    float red[6][NB_THREADS];
-    int leaf;
-};
-
-// Plans the next stage of the direct list [si, s1) (si advanced past the source leaves taken whole,
-// soff = moonlets of the source leaf at si already taken), writes its size to S.tot[b], arms the full
-// barrier of buffer b and issues the copies.  Warp 0 only (all its lanes); returns the stage's size
-// (0: the list is exhausted and the stage is the end marker).
-__device__ __forceinline__ int near_issue(const EvalArgs &A, NearBlockSmem &S, int b, int &si, int &soff, int s1,
-                                          int lane) {
-    const bool more = si < s1;
-    const int idx = si + lane;
-    int fst = 0, c = 0;
-    if (more && idx < s1) {
-        const int2 e = A.p2p_src[idx];
-        fst = e.x;
-        c = e.y;
-    }
-    if (more && lane == 0) {
-        fst += soff;
-        c -= soff;
-    }
-    int inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
-    }
-    const int exc = inc - c;
-    const int tot = min(NB_STAGE, __shfl_sync(0xffffffffu, inc, 31));
-    if (lane == 0) {
-        S.tot[b] = tot;
-        mbar_arrive_expect_tx(&S.full[b], static_cast<unsigned>(tot) * 32u);   // 0 bytes: the end marker
-    }
-    __syncwarp();
-    const int take = min(inc, tot) - exc;
-    if (more && idx < s1 && take > 0) {
-        bulk_g2s(&S.hi[b][exc], &A.hi4[fst], static_cast<unsigned>(take) * 16u, &S.full[b]);
-        bulk_g2s(&S.lo[b][exc], &A.lo4[fst], static_cast<unsigned>(take) * 16u, &S.full[b]);
-    }
-    if (more) {   // source leaves taken whole; the next one may be cut where the stage ends
-        const unsigned whole = __ballot_sync(0xffffffffu, idx < s1 && inc <= tot);
-        const int L = __popc(whole);
-        const int excL = __shfl_sync(0xffffffffu, exc, L & 31);
-        soff = (L < 32 && si + L < s1) ? (L == 0 ? soff : 0) + (tot - excL) : 0;
-        si += L;
-    }
-    return tot;
-}
-
-// Bounded wait for a barrier phase by one thread; false (ERR_TIMEOUT set) if it did not complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned long long limit, Ctrl *ctl) {
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > limit) {
-            atomicOr(&ctl->err, ERR_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-
-__global__ void __launch_bounds__(NB_THREADS) k_near(EvalArgs A) {
-    __shared__ __align__(128) NearBlockSmem S;
-    if (aborted(A.ctl)) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    Ctrl *ctl = const_cast<Ctrl *>(A.ctl);
-    if (tid == 0) {
-        mbar_init(&S.full[0], 1);
-        mbar_init(&S.full[1], 1);
-        mbar_init(&S.empty[0], NB_WARPS);
-        mbar_init(&S.empty[1], NB_WARPS);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    const unsigned long long limit = A.ctl->wait_ns ? A.ctl->wait_ns : 1000000000ull;
-    const int nl = A.ctl->n_leaves;
-    unsigned fph = 0, eph = 0, filled = 0;   // per buffer: full / empty parities, ever filled (warp 0)
-    int buf = 0;                             // the buffer of the next stage
-    while (true) {
-        if (tid == 0) S.leaf = aborted(A.ctl) ? nl : atomicAdd(A.work, 1);
-        __syncthreads();
-        const int li = S.leaf;
-        if (li >= nl) break;
-        const int leaf = A.leaves[li];
-        const int f = A.first[leaf], cnt = A.count[leaf];
-        const int s0 = min(A.p2p_off[leaf], A.p2p_dir_cap), s1 = min(A.p2p_off[leaf + 1], A.p2p_dir_cap);
-        for (int t0 = 0; t0 < cnt; t0 += NB_THREADS) {
-            const int m = min(NB_THREADS, cnt - t0);
-            const int G = NB_THREADS / m, g = tid / m, tt = tid - g * m;
-            const bool act = g < G;   // the last NB_THREADS - G m threads only help with the ring
-            const int i = f + t0 + (act ? tt : 0);
-            const float4 th = A.hi4[i], tl = A.lo4[i];
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-            int si = s0, soff = 0, last = 1;
-            auto produce = [&](int b) {   // warp 0: refill buffer b once every warp has released it
-                if (filled & (1u << b)) {   // every lane observes the phase
-                    mbar_wait_bounded(&S.empty[b], (eph >> b) & 1u, limit, ctl);
-                    __syncwarp();
-                    eph ^= 1u << b;
-                }
-                fence_proxy_async();   // the buffer's ordinary reads are done before the copies
-                filled |= 1u << b;
-                last = near_issue(A, S, b, si, soff, s1, lane);
-            };
-            if (warp == 0) produce(buf);
-            while (true) {
-                if (warp == 0 && last > 0) produce(buf ^ 1);   // the next stage (or the end marker)
-                // every thread observes the phase (the copies' data and S.tot are then visible to it)
-                const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&S.full[buf], (fph >> buf) & 1u, limit, ctl));
-                fph ^= 1u << buf;
-                const int tot = ok ? S.tot[buf] : 0;
-                if (act && tot > 0) {   // group g: the contiguous slice [tot g / G, tot (g + 1) / G) of the stage
-                    const float4 *H = S.hi[buf], *Lo = S.lo[buf];
-                    const int ka = (tot * g) / G, kb = (tot * (g + 1)) / G;
-                    for (int k0 = ka; k0 < kb; k0 += 32) {
-                        const int k1 = min(kb, k0 + 32);
-#pragma unroll 4
-                        for (int k = k0; k < k1; k++) p2p_f32(H[k], Lo[k], th, tl, ax, ay, az);
-                        df_add(h[0], l[0], ax); df_add(h[1], l[1], ay); df_add(h[2], l[2], az);
-                        ax = ay = az = 0.f;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.empty[buf]);
-                buf ^= 1;
-                if (tot == 0) break;
-            }
-            // totals of the groups, added in group order
-            S.red[0][tid] = h[0]; S.red[1][tid] = h[1]; S.red[2][tid] = h[2];
-            S.red[3][tid] = l[0]; S.red[4][tid] = l[1]; S.red[5][tid] = l[2];
-            __syncthreads();
-            if (g == 0 && act) {
-                float th3[3] = {0.f, 0.f, 0.f}, tl3[3] = {0.f, 0.f, 0.f};
-                for (int q = 0; q < G; q++)
+            if constexpr (f32) {   // the groups' double-float totals, added in group order
+                if (G > 1) {
+                    __syncthreads();
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        df_add(th3[d], tl3[d], S.red[d][q * m + tt]);
-                        tl3[d] += S.red[3 + d][q * m + tt];
+                        S.red[d][tid] = h3[d];
+                        S.red[3 + d][tid] = l3[d];
                     }
-                A.nx[i] = static_cast<double>(th3[0]) + static_cast<double>(tl3[0]);
-                A.ny[i] = static_cast<double>(th3[1]) + static_cast<double>(tl3[1]);
-                A.nz[i] = static_cast<double>(th3[2]) + static_cast<double>(tl3[2]);
+                    __syncthreads();
+                    if (g == 0) {
+#pragma unroll
+                        for (int d = 0; d < 3; d++) {
+                            h3[d] = l3[d] = 0.f;
+                            for (int q = 0; q < G; q++) {
+                                df_add(h3[d], l3[d], S.red[d][q * m + tt]);
+                                l3[d] += S.red[3 + d][q * m + tt];
+                            }
+                        }
+                    }
+                }
+                if (g == 0 && act) {
+                    A.nx[i] = static_cast<double>(h3[0]) + static_cast<double>(l3[0]);
+                    A.ny[i] = static_cast<double>(h3[1]) + static_cast<double>(l3[1]);
+                    A.nz[i] = static_cast<double>(h3[2]) + static_cast<double>(l3[2]);
+                }
+            } else {
+                if (G > 1) {
+                    __syncthreads();
+                    S.red[0][tid] = ax;
+                    S.red[1][tid] = ay;
+                    S.red[2][tid] = az;
+                    __syncthreads();
+                    if (g == 0) {
+                        ax = ay = az = real(0);
+                        for (int q = 0; q < G; q++) {
+                            ax += S.red[0][q * m + tt];
+                            ay += S.red[1][q * m + tt];
+                            az += S.red[2][q * m + tt];
+                        }
+                    }
+                }
+                if (g == 0 && act) {
+                    A.nx[i] = static_cast<double>(ax);
+                    A.ny[i] = static_cast<double>(ay);
+                    A.nz[i] = static_cast<double>(az);
+                }
             }
-            __syncthreads();
         }
     }
 }
@@ -699,21 +554,8 @@ static void descend_t(ncorp_ctx *c, DescendArgs D) {
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
-static void near_mixed(ncorp_ctx *c, const EvalArgs &A) {
-    int per_sm = 0;
-    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_near),
-                                                                   NB_THREADS, 0));
-    if (per_sm < 1) per_sm = 1;
-    k_near<<<per_sm * c->num_sms, NB_THREADS, 0, c->stream>>>(A);
-    c->launches++;
-}
-
 template <int P, typename real>
 static void eval_t(ncorp_ctx *c, const EvalArgs &A) {
-    if constexpr (std::is_same<real, float>::value) {   // the mixed path (any p: the near field has no p)
-        near_mixed(c, A);
-        return;
-    }
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, reinterpret_cast<const void *>(k_eval<P, real>), EV_THREADS, 0));

@@ -89,7 +89,6 @@ __global__ void k_build_init(BuildArgs A) {
     A.ctl->bar_count = 0;
     A.arrive[0] = 0;        // arrival counters of the collision climb and of the multipoles,
     A.arrive_m[0] = 0;      // zeroed as cells are made
-    A.ctl->bar_count2 = 0;  // the multipole kernel's grid barrier
 }
 
 // Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
@@ -668,21 +667,16 @@ struct M2MShared {
     real b[P2M_WARPS][8][off(P) < 1 ? 1 : off(P)];
 };
 
-// (n, b + c, c) of slot j of the full storage (orders 0..P-1)
+// (n, b + c, c) of slot j of the full storage (orders 0..P-1): order n starts
+// at n(n+1)(n+2)/6, and within it k = b + c runs 0..n with c = 0..k
 template <int P>
 __device__ __forceinline__ void full_exps(int j, int &n, int &kk, int &c) {
-    n = kk = c = 0;
-#pragma unroll
-    for (int nn = 0; nn < P; nn++)
-#pragma unroll
-        for (int k = 0; k <= nn; k++)
-#pragma unroll
-            for (int cc = 0; cc <= k; cc++)
-                if (sidx(nn - k, k - cc, cc) == j) {
-                    n = nn;
-                    kk = k;
-                    c = cc;
-                }
+    n = 0;
+    while (n + 1 < P && off(n + 1) <= j) n++;
+    const int rem = j - off(n);
+    kk = 0;
+    while (kk < n && tri(kk + 1) <= rem) kk++;
+    c = rem - tri(kk);
 }
 
 // One-dimensional shift of full-storage moments along AXIS: out(a,b,c) = sum_{k <= exponent} in(... - k e_axis) w_k
@@ -699,25 +693,31 @@ __device__ __forceinline__ real m_shift(const real *in, const real (&w)[P], int 
     return s;
 }
 
+// Eight leaves per warp, four lanes per leaf: each lane sums a quarter of its
+// leaf's moonlets, then the four partial sums are added by two butterfly
+// steps and each lane stores a quarter of the coefficients.  Every lane of
+// the warp calls this (valid: the lane's group has a leaf).
 template <int P, typename real>
-__device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, int lane, real *Mh) {
+__device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, bool valid, int q, real *Mh) {
     constexpr int NM = num_m(P);
     real acc[NM];
 #pragma unroll
     for (int j = 0; j < NM; j++) acc[j] = real(0);
-    const int f = A.first[c], e = f + A.count[c];
-    if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
-        const float4 gh = A.gh[c], gl = A.gl[c];
-        const float ir = 1.0f / gl.w;   // exact: rho is a power of two
-        for (int k = f + lane; k < e; k += 32) {
-            const float4 h = A.hi4[k], l = A.lo4[k];
-            p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
-                             ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
+    if (valid) {
+        const int f = A.first[c], e = f + A.count[c];
+        if constexpr (sizeof(real) == 4) {   // double-float difference, no FP64 work
+            const float4 gh = A.gh[c], gl = A.gl[c];
+            const float ir = 1.0f / gl.w;   // exact: rho is a power of two
+            for (int k = f + q; k < e; k += 4) {
+                const float4 h = A.hi4[k], l = A.lo4[k];
+                p2m_add<P, real>(((h.x - gh.x) + (l.x - gl.x)) * ir, ((h.y - gh.y) + (l.y - gl.y)) * ir,
+                                 ((h.z - gh.z) + (l.z - gl.z)) * ir, h.w, acc);
+            }
+        } else {
+            const double irho = 1.0 / A.rho[c], sx = A.sx[c], sy = A.sy[c], sz = A.sz[c];
+            for (int k = f + q; k < e; k += 4)
+                p2m_add<P, real>((A.x[k] - sx) * irho, (A.y[k] - sy) * irho, (A.z[k] - sz) * irho, A.G * A.m[k], acc);
         }
-    } else {
-        const double irho = 1.0 / A.rho[c], sx = A.sx[c], sy = A.sy[c], sz = A.sz[c];
-        for (int k = f + lane; k < e; k += 32)
-            p2m_add<P, real>((A.x[k] - sx) * irho, (A.y[k] - sy) * irho, (A.z[k] - sz) * irho, A.G * A.m[k], acc);
     }
 #pragma unroll
     for (int n = 0; n < P; n++) {
@@ -725,10 +725,14 @@ __device__ __forceinline__ void leaf_moments(const P2MArgs &A, int c, int lane, 
 #pragma unroll
         for (int k = 0; k <= n; k++)
 #pragma unroll
-            for (int cc = 0; cc <= k; cc++)
-                acc[midx(n - k, k - cc, cc)] *= static_cast<real>(inv_mfact(n - k, k - cc, cc));
+            for (int cc = 0; cc <= k; cc++) {
+                const int j = midx(n - k, k - cc, cc);
+                real v = acc[j] * static_cast<real>(inv_mfact(n - k, k - cc, cc));
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if (valid && (j & 3) == q) Mh[(size_t)c * NM + j] = v;
+            }
     }
-    store_reduced<P, real>(acc, Mh + (size_t)c * NM, lane);
 }
 
 // M2M of a parent from its children, as three one-dimensional shifts per
@@ -824,39 +828,61 @@ __device__ __forceinline__ void parent_moments(const P2MArgs &A, M2MShared<P, re
     }
 }
 
-// Level by level in one cooperative launch: the leaves' moments from their
-// moonlets, then the parents of each level from the deepest up, one grid
-// barrier per level (every parent of a level in parallel).
+// One launch, no waiting: the leaves' moments from their moonlets (eight
+// leaves per warp), then the parents up the tree.  A warp that has finished a
+// cell adds its arrival to the parent's counter (release); the warp that
+// arrives last (acquire) computes the parent, whose children are then all
+// done, and goes on up.  The children are added in child order, so the
+// result does not depend on which warp arrives last.
+template <int P, typename real>
+__device__ __forceinline__ int arrive_last(const P2MArgs &A, int c) {
+    const int pc = A.parent[c];
+    if (pc < 0) return -1;
+    fence_acq_rel_gpu();   // release: the cell's moments before the arrival
+    if (atomicAdd(&A.arrive[pc], 1) != A.nchild[pc] - 1) return -1;
+    fence_acq_rel_gpu();   // acquire: the other children's moments
+    return pc;
+}
+
 template <int P, typename real>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_multipoles(P2MArgs A) {
     __shared__ M2MShared<P, real> S;
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    // warps numbered across the blocks first, so that consecutive work items land on different SMs
-    const int gw0 = wl * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gw0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nl = A.ctl->n_leaves;
     real *Mh = static_cast<real *>(A.Mh);
-    for (int li = gw0; li < nl; li += nwarps) leaf_moments<P, real>(A, A.leaves[li], lane, Mh);
-    unsigned bar = 0;
-    if (!grid_sync_on(&A.ctl->bar_count2, A.ctl, bar)) return;
-    const int maxl = A.ctl->max_level;
-    for (int lev = maxl - 1; lev >= 0; lev--) {
-        const int ls = A.ctl->level_start[lev], le = A.ctl->level_start[lev + 1];
-        for (int c = ls + gw0; c < le; c += nwarps)
-            if (A.nchild[c] > 0) parent_moments<P, real>(A, S, wl, c, lane, Mh);
-        if (lev > 0 && !grid_sync_on(&A.ctl->bar_count2, A.ctl, bar)) return;
+    for (int base = gw0 * 8; base < nl; base += nwarps * 8) {   // eight leaves per warp, four lanes each
+        const int li = base + (lane >> 2);
+        const bool valid = li < nl;
+        const int c = valid ? A.leaves[li] : 0;
+        leaf_moments<P, real>(A, c, valid, lane & 3, Mh);
+        __syncwarp();
+        int up = -1;   // the parent this quad's leaf completed, if any
+        if (valid && (lane & 3) == 0) up = arrive_last<P, real>(A, c);
+        unsigned todo = __ballot_sync(0xffffffffu, up >= 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            int pc = __shfl_sync(0xffffffffu, up, src);
+            __syncwarp();   // orders the quad leader's acquire before every lane's reads
+            while (true) {
+                parent_moments<P, real>(A, S, wl, pc, lane, Mh);
+                __syncwarp();
+                int next = -1;
+                if (lane == 0) next = arrive_last<P, real>(A, pc);
+                next = __shfl_sync(0xffffffffu, next, 0);
+                if (next < 0) break;
+                __syncwarp();
+                pc = next;
+            }
+        }
     }
 }
 
 template <int P, typename real>
 static void p2m_t(ncorp_ctx *c, const P2MArgs &B) {
-    // cooperative (every block resident: the level barriers); up to two blocks per SM beside the walk
-    const int grid = coop_grid(c, reinterpret_cast<const void *>(k_multipoles<P, real>), 32 * P2M_WARPS, 0);
-    P2MArgs args = B;
-    void *kargs[] = {&args};
-    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_multipoles<P, real>), dim3(grid),
-                                                 dim3(32 * P2M_WARPS), kargs, 0, c->stream));
-    c->launches++;
+    k_multipoles<P, real><<<4 * c->num_sms, 32 * P2M_WARPS, 0, c->stream>>>(B); c->launches++;
 }
 
 // theta(M) of Dehnen (2002) Eq. 13: theta^5/(1-theta)^2 = K (M/M_tot)^(-1/3),
