@@ -151,6 +151,31 @@ int ncorp_set_graphs(ncorp_ctx *ctx, int enable);
 /* Forgets the resident state, so the next ncorp_step re-reads its inputs. */
 int ncorp_reset(ncorp_ctx *ctx);
 
+/* Most disks one context can hold side by side (ncorp_set_disks). */
+#define NCORP_MAX_DISKS 256
+
+/* Lays the context's moonlets out as n_disks independent disks (a forest):
+ * disk d is the sizes[d] (>= 1) moonlets that follow the earlier disks' in
+ * every array a later call passes, whose n must then be the sum of sizes.
+ * Every disk is a separate system: it has its own root cell and root cube
+ * (Sect. 3.4.1 applied per disk), its own total mass in theta(M) (Dehnen
+ * 2002, Eq. 13), and neither gravity nor the collision search (Algorithm
+ * TreeWalk) ever pairs cells or moonlets of two disks; the central body,
+ * bulge and star act on every disk alike.  Each stage of ncorp_step,
+ * ncorp_accel and ncorp_collide then runs once over all disks (one launch
+ * per stage, not one per disk), and the results of disk d equal those of the
+ * same disk in a context of its own up to the rounding order of sums
+ * (bit-equal colliding pairs; accelerations within the precision's
+ * tolerance).  ncorp_collisions reports the pairs with indices into the
+ * concatenated arrays (a pair never spans two disks).  The standard-tree
+ * entry points (ncorp_accel_standard, ncorp_collide_standard) take one disk
+ * only.  n_disks = 1 returns to one disk (sizes may then be NULL; if given,
+ * its one entry is checked like the others).  The resident
+ * state is dropped.  sizes: host memory [n_disks].  Synchronous.
+ * Errors: NCORP_EINVAL (n_disks outside 1..NCORP_MAX_DISKS, a size < 1, more
+ * than 2^30 moonlets in all), NCORP_ECUDA, NCORP_ENOMEM. */
+int ncorp_set_disks(ncorp_ctx *ctx, int n_disks, const int64_t *sizes);
+
 /* Colliding pairs found by the last ncorp_step or ncorp_collide: rows (i, j)
  * of caller indices with i < j, sorted lexicographically, no duplicates.
  * pairs: [cap][2] int64 (host or device); *n_pairs receives the total found.
@@ -265,7 +290,8 @@ int ncorp_stage_times(ncorp_ctx *ctx, double *ms, int n);
  * Any output may be NULL; all are host or device arrays:
  *   order [n] int64: caller index of the i-th moonlet in tree order
  *   keys  [n] uint64: 63-bit Hilbert key of the i-th moonlet in tree order
- *   root  [4] double: x_lo, y_lo, z_lo, L of the root cube
+ *   root  [4] double: x_lo, y_lo, z_lo, L of the root cube (a forest of
+ *         n_disks disks: [n_disks][4], every disk's root cube)
  *   cells [cap][7] int64: level, cx, cy, cz, first, count, n_children
  *   ggeo  [cap][6] double: M, s_x, s_y, s_z, r_max, r_crit (gravity climb)
  *   cgeo  [cap][5] double: sbar_x, sbar_y, sbar_z, r_max, r_crit (collision climb)
@@ -298,38 +324,50 @@ void ncorp_free(ncorp_ctx *ctx);
 const char *ncorp_last_error(const ncorp_ctx *ctx);
 
 /* ---- Batches: many independent disks on one GPU ----------------------------
- * A batch owns one resident state per disk and advances all of them together:
- * ncorp_batch_run enqueues the steps of every disk on a pool of CUDA streams
- * and waits once, so the kernels of different disks overlap on the GPU.  Each
- * disk is integrated exactly as by ncorp_step (the same SBAB1 step of
- * Sect. 4.1 with the falcON forces and the collision search of Sect. 3.1).
- * A batch is not thread-safe: call it from one host thread at a time. */
+ * A batch keeps every disk's state on the device and advances all of them
+ * together.  The disks that share (p, theta, dt) form one forest: a context
+ * laid out by ncorp_set_disks, so that each stage of a step is one launch over
+ * all of them however many there are.  ncorp_batch_run advances every forest
+ * by n_steps steps through one CUDA graph per forest (captured on the first
+ * run of that length and buffer rotation, replayed afterwards); forests run
+ * on separate streams and overlap.  Each disk is integrated as by ncorp_step
+ * in a context of its own (the same SBAB1 step of Sect. 4.1 with the falcON
+ * forces and the collision search of Sect. 3.1), up to the rounding order of
+ * sums.  A batch is not thread-safe: call it from one host thread at a time.
+ * Batches take no distant star (its position depends on each disk's time). */
 typedef struct ncorp_batch ncorp_batch;
 
 /* Creates an empty batch on the current CUDA device; every disk uses cfg
- * (copied).  hbm_budget_bytes caps the device memory the batch's disks may
- * take (0: no cap); cuda_stream is the caller's stream: ncorp_batch_run starts
- * after the work queued on it so far, and work queued on it later starts after
- * the run.  NCORP_EINVAL for NULL arguments or an invalid precision. */
+ * (copied).  hbm_budget_bytes caps the device memory the batch may hold (0:
+ * no cap); cuda_stream is the caller's stream: ncorp_batch_run starts after
+ * the work already enqueued on it and the caller's later work waits for the
+ * run.  Errors: NCORP_EINVAL (bad config, star_mass != 0), NCORP_ECUDA,
+ * NCORP_ENOMEM. */
 int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_budget_bytes, void *cuda_stream);
 
 /* Adds a disk of n moonlets: positions/velocities [n][3], masses/radii [n],
  * host or device arrays (copied; the caller keeps ownership); p, theta and
- * dt as for ncorp_step, fixed for the disk.  Computes the disk's tree and
- * acceleration (one synchronous force evaluation).  *disk_id receives the
- * disk's id (unique within the batch).  Errors: NCORP_EINVAL (arguments,
- * non-finite input), NCORP_ENOMEM (allocation failed, or the disk would exceed
- * the batch's device-memory budget), NCORP_ECUDA, NCORP_EOVERFLOW,
- * NCORP_ETIMEOUT; on error no disk is added. */
+ * dt as for ncorp_step, fixed for the disk.  The disk joins the forest of
+ * its (p, theta, dt); that forest's tree and acceleration are computed at
+ * the start of the next ncorp_batch_run (one force evaluation for all the
+ * disks added or removed since the last run).  Admission by device memory:
+ * the disk is refused when the bytes the batch holds plus n times the
+ * largest footprint per moonlet measured so far (4096 bytes before any
+ * measurement) exceed the budget.  *disk_id receives the disk's id (unique
+ * within the batch).  Errors: NCORP_EINVAL (arguments, non-finite positions
+ * or velocities, more than NCORP_MAX_DISKS disks with the same (p, theta,
+ * dt)), NCORP_ENOMEM (allocation failed, or over the budget), NCORP_ECUDA;
+ * on error no disk is added. */
 int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *velocities, const double *masses,
                          const double *radii, int64_t n, int p, double theta, double dt, int32_t *disk_id);
 
-/* Advances every disk by n_steps SBAB1 steps (Sect. 4.1) and waits for them.
- * If an internal buffer of some disk overflowed during the run, that disk is
- * rerun from its state at the start of the run one synchronous step at a
- * time with grown buffers (counted in NCORP_BATCH_FALLBACKS).  The colliding
- * pairs of each disk's last step are kept for ncorp_batch_collisions.
- * Errors: NCORP_EINVAL (n_steps < 0, non-finite state), NCORP_ECUDA,
+/* Advances every disk by n_steps SBAB1 steps (Sect. 4.1) and waits for them
+ * (n_steps = 0 only lays out the forests that changed).  If an internal
+ * buffer of a forest overflowed during the run, that forest is rerun from
+ * its state at the start of the run one synchronous step at a time with
+ * grown buffers (counted in NCORP_BATCH_FALLBACKS).  The colliding pairs of
+ * each disk's last step are kept for ncorp_batch_collisions.  Errors:
+ * NCORP_EINVAL (n_steps < 0, non-finite state), NCORP_ECUDA, NCORP_ENOMEM,
  * NCORP_ETIMEOUT, NCORP_EOVERFLOW. */
 int ncorp_batch_run(ncorp_batch *b, int n_steps);
 
@@ -337,20 +375,23 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps);
  * positions/velocities [n][3] (host or device).  NCORP_EINVAL for an unknown id. */
 int ncorp_batch_get_state(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities);
 
-/* Colliding pairs of a disk's last step, as ncorp_collisions gives them. */
+/* Colliding pairs of a disk's last step, as ncorp_collisions gives them
+ * (indices into the disk's own arrays). */
 int ncorp_batch_collisions(ncorp_batch *b, int32_t disk_id, int64_t *pairs, int64_t cap, int64_t *n_pairs);
 
-/* Removes a disk and releases its device memory; if positions and
- * velocities are given (both or neither), the disk's final state is copied
- * there first, as by ncorp_batch_get_state.  NCORP_EINVAL for an unknown id. */
+/* Removes a disk and releases its share of device memory (a forest whose
+ * last disk leaves is released; one that shrinks below half its capacity is
+ * reallocated at its next layout); if positions and velocities are given
+ * (both or neither), the disk's final state is copied there first, as by
+ * ncorp_batch_get_state.  NCORP_EINVAL for an unknown id. */
 int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities);
 
 /* Batch counters (int64 slots): */
 #define NCORP_BATCH_DISKS      0   /* disks in the batch */
 #define NCORP_BATCH_MOONLETS   1   /* moonlets over all disks */
-#define NCORP_BATCH_BYTES      2   /* device bytes taken by the disks */
-#define NCORP_BATCH_STREAMS    3   /* streams the disks are spread over */
-#define NCORP_BATCH_FALLBACKS  4   /* disk reruns after a buffer overflow, since creation */
+#define NCORP_BATCH_BYTES      2   /* device bytes the batch holds (measured) */
+#define NCORP_BATCH_FORESTS    3   /* forests: groups of disks with the same (p, theta, dt) */
+#define NCORP_BATCH_FALLBACKS  4   /* forest reruns after a buffer overflow, since creation */
 #define NCORP_BATCH_LAUNCHES   5   /* kernels launched by the last run */
 #define NCORP_BATCH_NINFO      6
 

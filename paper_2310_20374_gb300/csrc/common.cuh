@@ -114,6 +114,14 @@ struct Ctrl {
     int col_iters;         // collision walk: generations
     unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
     double root[4];        // x_lo, y_lo, z_lo, L
+    // Several independent disks in one tree set (a forest): nd roots, cells 0..nd-1; disk d holds the
+    // moonlets [doff[d], doff[d + 1]) in every order (the key sort orders by (disk, key)).  One disk:
+    // nd = 1, disk_of = doff = null, dbox / droot point at bbox / root above.  Set once per context.
+    int nd;
+    const unsigned short *disk_of;   // [n] disk of each moonlet (null: one disk)
+    const int *doff;                 // [nd + 1]
+    unsigned long long *dbox;        // [nd][6] order-preserving encodings of each disk's box
+    double *droot;                   // [nd][4] each disk's root cube: x_lo, y_lo, z_lo, L
     unsigned long long wait_ns;   // limit of a grid barrier's wait (0: one second); set once per context
     unsigned desc_epoch;   // epoch of the current descent (advanced by every M2L launch; never reset)
     int stall;             // nonzero: the grid barriers of this tree set wait for one arrival that never
@@ -128,6 +136,41 @@ __device__ __forceinline__ unsigned long long ord_encode(double v) {
 __device__ __forceinline__ double ord_decode(unsigned long long u) {
     unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
     return __longlong_as_double(static_cast<long long>(b));
+}
+
+// disk of moonlet i (tree or caller order: the disks' ranges are the same) and its root cube
+__device__ __forceinline__ int disk_of(const Ctrl *ctl, int i) { return ctl->disk_of ? ctl->disk_of[i] : 0; }
+__device__ __forceinline__ const double *disk_root(const Ctrl *ctl, int d) { return ctl->droot + 4 * d; }
+
+// Folds a lane's coordinates into the box of its disk d (forests: every lane of the warp calls this;
+// a warp within one disk reduces first and adds one atomic per bound).
+__device__ __forceinline__ void fold_disk_box(Ctrl *ctl, int d, bool valid, const unsigned long long lo[3],
+                                              const unsigned long long hi[3]) {
+    const unsigned same = __match_any_sync(0xffffffffu, valid ? d : -1);
+    if (same == 0xffffffffu && valid) {
+        unsigned long long l[3] = {lo[0], lo[1], lo[2]}, h[3] = {hi[0], hi[1], hi[2]};
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, l[k], o);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, h[k], o);
+                l[k] = a < l[k] ? a : l[k];
+                h[k] = b > h[k] ? b : h[k];
+            }
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                atomicMin(&ctl->dbox[6 * d + k], l[k]);
+                atomicMax(&ctl->dbox[6 * d + 3 + k], h[k]);
+            }
+    } else if (valid) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            atomicMin(&ctl->dbox[6 * d + k], lo[k]);
+            atomicMax(&ctl->dbox[6 * d + 3 + k], hi[k]);
+        }
+    }
 }
 
 // true when an earlier stage overflowed a buffer or timed out: later kernels

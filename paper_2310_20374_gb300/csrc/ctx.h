@@ -115,6 +115,13 @@ struct ncorp_ctx {
 
     int64_t n_cap = 0;
     int n = 0;
+    // a forest (nd > 1): independent disks in the same arrays, disk d = moonlets [doff[d], doff[d + 1])
+    int nd = 1;
+    int forest_n = 0;                    // moonlets of all disks (nd > 1)
+    unsigned short *disk_of = nullptr;   // device [forest_n]
+    int *doff = nullptr;                 // device [nd + 1]
+    unsigned long long *fbox[2] = {nullptr, nullptr};   // device [nd][6] per tree set
+    double *froot[2] = {nullptr, nullptr};              // device [nd][4] per tree set
     int cur_n = 0;                  // moonlets of the tree being built or walked
     int p = 0;
     double theta = 0.5;
@@ -200,8 +207,9 @@ namespace ncorp {
 // (a step's tree is rebuilt only when its collision resolution moved a moonlet)
 void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, uint64_t *key,
                       uint32_t *qx, uint32_t *qy, uint32_t *qz, bool bbox_done = false, const int *gate = nullptr);
+// by_disk: the keys are a forest's moonlet keys (every disk's own root cube); they are sorted by (disk, key)
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits, bool bar_zeroed = false, const int *gate = nullptr);
+                    int bits, bool bar_zeroed = false, const int *gate = nullptr, bool by_disk = false);
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
                    const uint32_t *idx, double G, const int *gate = nullptr);
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);

@@ -44,6 +44,36 @@ __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
     __shared__ int s_bad;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
+    if (A.ctl->disk_of) {   // a forest: the same step, every disk's own box
+        const int lane = threadIdx.x & 31;
+        for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < A.n; base += gridDim.x * blockDim.x) {
+            const int i = base + lane;
+            const bool valid = i < A.n;
+            unsigned long long l[3] = {~0ull, ~0ull, ~0ull}, h[3] = {0ull, 0ull, 0ull};
+            if (valid) {
+                const double vx = dadd(A.vx[i], dmul(A.h, A.ax[i]));
+                const double vy = dadd(A.vy[i], dmul(A.h, A.ay[i]));
+                const double vz = dadd(A.vz[i], dmul(A.h, A.az[i]));
+                A.ovx[i] = vx;
+                A.ovy[i] = vy;
+                A.ovz[i] = vz;
+                const double v[3] = {dadd(A.x[i], dmul(A.dt, vx)), dadd(A.y[i], dmul(A.dt, vy)),
+                                     dadd(A.z[i], dmul(A.dt, vz))};
+                A.ox[i] = v[0];
+                A.oy[i] = v[1];
+                A.oz[i] = v[2];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v[k]));
+                    bad |= (u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+                    l[k] = h[k] = ord_encode(v[k]);
+                }
+            }
+            fold_disk_box(A.ctl, valid ? A.ctl->disk_of[i] : 0, valid, l, h);
+        }
+        if (bad) atomicOr(&A.ctl->err, ERR_NONFINITE);
+        return;
+    }
     if (threadIdx.x == 0) s_bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
         const double vx = dadd(A.vx[i], dmul(A.h, A.ax[i]));

@@ -352,10 +352,11 @@ __device__ void reset_one(Ctrl *ctl, int *fold) {
     ctl->bar_count = 0;
     ctl->resort_ok = 0;
     if (!fold) ctl->stall = 0;   // a set recycled within a call (fold) keeps the call's armed stall
-    for (int k = 0; k < 3; k++) {
-        ctl->bbox[k] = ~0ull;
-        ctl->bbox[3 + k] = 0ull;
-    }
+    for (int d = 0; d < ctl->nd; d++)   // every disk's box (one disk: dbox is bbox)
+        for (int k = 0; k < 3; k++) {
+            ctl->dbox[6 * d + k] = ~0ull;
+            ctl->dbox[6 * d + 3 + k] = 0ull;
+        }
 }
 
 __global__ void k_arm_stall(Ctrl *ctl, Ctrl *ctl2) {
@@ -367,6 +368,71 @@ __global__ void k_reset_ctl(Ctrl *ctl, Ctrl *ctl2, int *fold, int *clear) {
     reset_one(ctl, fold);
     if (ctl2) reset_one(ctl2, nullptr);
     if (clear) *clear = 0;
+}
+
+// The disk layout of a tree set (one disk: null arrays, the control block's own box and root cube).
+__global__ void k_set_disks(Ctrl *ctl, int nd, const unsigned short *disk_of, const int *doff,
+                            unsigned long long *dbox, double *droot) {
+    ctl->nd = nd;
+    ctl->disk_of = disk_of;
+    ctl->doff = doff;
+    ctl->dbox = dbox ? dbox : ctl->bbox;
+    ctl->droot = droot ? droot : ctl->root;
+}
+
+// disk_of[i] = the d with doff[d] <= i < doff[d + 1]
+__global__ void k_fill_disk_of(const int *__restrict__ doff, int nd, unsigned short *disk_of, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = nd - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (doff[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        disk_of[i] = static_cast<unsigned short>(lo);
+    }
+}
+
+// Lays the context's moonlets out as nd independent disks of sizes[d]
+// moonlets each, disk d taking [sum of the earlier sizes, + sizes[d]) in the
+// caller's arrays and in every internal order; nd = 1 returns to one disk.
+// The resident state and tree are dropped (the next call reads the caller's
+// arrays).  Synchronous.
+void drop_graph(StepGraph &g);
+
+void configure_disks(ncorp_ctx *c, int nd, const int64_t *sizes) {
+    std::vector<int> off(nd + 1, 0);
+    for (int d = 0; d < nd && sizes; d++) off[d + 1] = off[d] + static_cast<int>(sizes[d]);
+    const int n = off[nd];
+    NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    for (StepGraph &g : c->graphs) drop_graph(g);
+    if (nd == 1) {
+        dfree(c->disk_of);
+        dfree(c->doff);
+        for (int s = 0; s < 2; s++) {
+            dfree(c->fbox[s]);
+            dfree(c->froot[s]);
+        }
+        k_set_disks<<<1, 1, 0, c->stream>>>(c->ctl, 1, nullptr, nullptr, nullptr, nullptr);
+        k_set_disks<<<1, 1, 0, c->stream>>>(c->alt.ctl, 1, nullptr, nullptr, nullptr, nullptr);
+    } else {
+        dalloc(c->disk_of, n);
+        dalloc(c->doff, nd + 1);
+        for (int s = 0; s < 2; s++) {
+            dalloc(c->fbox[s], 6 * static_cast<size_t>(nd));
+            dalloc(c->froot[s], 4 * static_cast<size_t>(nd));
+        }
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(c->doff, off.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice, c->stream));
+        k_fill_disk_of<<<grid_for(n, 256, 4 * c->num_sms), 256, 0, c->stream>>>(c->doff, nd, c->disk_of, n);
+        k_set_disks<<<1, 1, 0, c->stream>>>(c->ctl, nd, c->disk_of, c->doff, c->fbox[0], c->froot[0]);
+        k_set_disks<<<1, 1, 0, c->stream>>>(c->alt.ctl, nd, c->disk_of, c->doff, c->fbox[1], c->froot[1]);
+    }
+    NCORP_CUDA_CHECK(cudaGetLastError());
+    NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    c->nd = nd;
+    c->forest_n = nd > 1 ? n : 0;
+    c->have_state = false;
+    c->tree_valid = false;
 }
 
 void reset_ctl(ncorp_ctx *c, bool fold = false) {
@@ -448,8 +514,9 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
     {
         Stage st(c, NCORP_STAGE_SORT);
         launch_bbox_keys(c, sx.x, sx.y, sx.z, n, dst.key, c->B.qx, c->B.qy, c->B.qz, bbox_done, gate);
-        if (near_sorted) sort_near_sorted(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
-        else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true, gate);
+        // (a forest's keys restart in every disk: they are sorted by (disk, key) with the full radix sort)
+        if (near_sorted && c->nd == 1) sort_near_sorted(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS);
+        else radix_sort_u64(c, dst.key, c->idx, c->key_alt, c->idx_alt, n, 3 * KEY_BITS, true, gate, true);
         ParticleSet view = sr;
         view.x = sx.x; view.y = sx.y; view.z = sx.z;
         view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
@@ -660,6 +727,8 @@ int check_common(ncorp_ctx *c, int64_t n, int p, double theta) {
     if (n < 1 || n > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "n = %lld out of range", (long long)n);
     if (p < 1 || p > MAXP) return fail(c, NCORP_EINVAL, "p = %d outside 1..6", p);
     if (!(theta > 0.0 && theta < 1.0)) return fail(c, NCORP_EINVAL, "theta = %g outside (0, 1)", theta);
+    if (c->nd > 1 && n != c->forest_n)
+        return fail(c, NCORP_EINVAL, "n = %lld is not the %d disks' total of %d", (long long)n, c->nd, c->forest_n);
     return NCORP_OK;
 }
 
@@ -846,6 +915,9 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
             NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->ctl_h), sizeof(Ctrl)));
             std::memset(c->ctl_h, 0, sizeof(Ctrl));
             c->ctl_h->wait_ns = wait_ns;
+            c->ctl_h->nd = 1;   // one disk: its box and root cube are the control block's own
+            c->ctl_h->dbox = c->ctl->bbox;
+            c->ctl_h->droot = c->ctl->root;
             NCORP_CUDA_CHECK(cudaMemcpy(c->ctl, c->ctl_h, sizeof(Ctrl), cudaMemcpyHostToDevice));
             swap_sets(c);
         }
@@ -901,6 +973,23 @@ int ncorp_reset(ncorp_ctx *c) {
     return NCORP_OK;
 }
 
+int ncorp_set_disks(ncorp_ctx *c, int n_disks, const int64_t *sizes) {
+    if (!c) return NCORP_EINVAL;
+    if (n_disks < 1 || n_disks > NCORP_MAX_DISKS)
+        return fail(c, NCORP_EINVAL, "n_disks = %d outside 1..%d", n_disks, NCORP_MAX_DISKS);
+    if (n_disks > 1 && !sizes) return fail(c, NCORP_EINVAL, "null pointer");
+    int64_t total = 0;
+    for (int d = 0; sizes && d < n_disks; d++) {
+        if (sizes[d] < 1) return fail(c, NCORP_EINVAL, "disk %d has %lld moonlets", d, (long long)sizes[d]);
+        total += sizes[d];
+    }
+    if (total > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "%lld moonlets in all", (long long)total);
+    NCORP_API_BODY(c, {
+        configure_disks(c, n_disks, n_disks > 1 ? sizes : nullptr);
+        return NCORP_OK;
+    })
+}
+
 int ncorp_accel(ncorp_ctx *c, const double *positions, const double *masses, int64_t n64, int p, double theta,
                 double *acc, double *acc_mutual) {
     int st = check_common(c, n64, p, theta);
@@ -947,6 +1036,7 @@ int ncorp_accel_standard(ncorp_ctx *c, const double *positions, const double *ma
                          double theta, double *acc, double *acc_mutual) {
     int st = check_common(c, n64, p, theta);
     if (st) return st;
+    if (c->nd > 1) return fail(c, NCORP_EINVAL, "the standard tree code walks one disk: ncorp_set_disks(ctx, 1, ...)");
     if (!positions || !masses || !acc) return fail(c, NCORP_EINVAL, "null pointer");
     NCORP_API_BODY(c, {
         begin_call(c);
@@ -998,6 +1088,10 @@ static int collide_call(ncorp_ctx *c, const double *positions, const double *vel
     if (n64 < 1 || n64 > (int64_t(1) << 30)) return fail(c, NCORP_EINVAL, "n out of range");
     if (!positions || !velocities || !radii) return fail(c, NCORP_EINVAL, "null pointer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NCORP_EINVAL, "dt must be > 0");
+    if (c->nd > 1 && n64 != c->forest_n)
+        return fail(c, NCORP_EINVAL, "n = %lld is not the %d disks' total of %d", (long long)n64, c->nd, c->forest_n);
+    if (standard && c->nd > 1)
+        return fail(c, NCORP_EINVAL, "the standard tree code walks one disk: ncorp_set_disks(ctx, 1, ...)");
     NCORP_API_BODY(c, {
         begin_call(c);
         const int n = static_cast<int>(n64);
@@ -1208,7 +1302,10 @@ int ncorp_tree_export(ncorp_ctx *c, int64_t *order, uint64_t *keys, double *root
             NCORP_CUDA_CHECK(cudaMemcpy(order, o.data(), sizeof(int64_t) * n, cudaMemcpyDefault));
         }
         if (keys) NCORP_CUDA_CHECK(cudaMemcpy(keys, c->A.key, sizeof(uint64_t) * n, cudaMemcpyDefault));
-        if (root) NCORP_CUDA_CHECK(cudaMemcpy(root, c->ctl_h->root, sizeof(double) * 4, cudaMemcpyDefault));
+        if (root) {   // one root cube per disk (a forest's are in the current tree set's own array)
+            const double *src = c->nd > 1 ? c->ctl_h->droot : c->ctl->root;
+            NCORP_CUDA_CHECK(cudaMemcpy(root, src, sizeof(double) * 4 * c->nd, cudaMemcpyDefault));
+        }
         const int k = static_cast<int>(std::min<int64_t>(cap, nc));
         if (k > 0 && cells) {
             std::vector<int> lv(k), f(k), cnt(k), nch(k);
@@ -1360,6 +1457,11 @@ void ncorp_free(ncorp_ctx *c) {
     dfree(c->pairs); dfree(c->pairs_alt); dfree(c->pair_idx); dfree(c->pair_idx_alt); dfree(c->pairs_out);
     dfree(c->pair_where); dfree(c->res_tc); dfree(c->res_state);
     dfree(c->node_tc); dfree(c->node_ij); dfree(c->node_owner);
+    dfree(c->disk_of); dfree(c->doff);
+    for (int s = 0; s < 2; s++) {
+        dfree(c->fbox[s]);
+        dfree(c->froot[s]);
+    }
     dfree(c->err_acc);
     if (c->err_acc_h) cudaFreeHost(c->err_acc_h);
     if (c->side) {
@@ -1392,25 +1494,67 @@ const char *ncorp_last_error(const ncorp_ctx *c) {
 }  // extern "C"
 
 // ===========================================================================
-// Batches of independent disks.  Every disk keeps its own context (state,
-// tree, lists); the batch drives the contexts on a pool of streams, enqueuing
-// the steps of all disks before it waits once, so that the disks' kernels
-// overlap on the GPU.  The cooperative grids of every context are capped so
-// that those of all streams fit on the device at the same time.
+// Batches of independent disks.  The disks that share (p, theta, dt) form a
+// forest: one context whose arrays hold the disks side by side
+// (configure_disks), so that every stage of a step is one launch over all of
+// them, whatever their number.  ncorp_batch_run advances each forest by k
+// steps through one CUDA graph (a snapshot of the state for a rerun, then
+// the k steps), cached per (k, buffer rotation); forests run on separate
+// streams and overlap.  A forest whose membership changed is laid out anew
+// and its tree and acceleration recomputed at the start of the next run.
 // ===========================================================================
 namespace {
 
-constexpr int BATCH_STREAMS = 8;
+constexpr int BATCH_STREAMS = 4;                    // forests f use stream f mod BATCH_STREAMS
+constexpr double BATCH_DEFAULT_BYTES_PER_MOONLET = 4096.0;   // admission estimate before any measurement
+constexpr int64_t BATCH_MEASURE_MIN = 1 << 16;               // forests measured for the estimate: n at least this
+
+// Device arrays owned by the batch: plain allocations that leave the
+// context allocation counter alone (the cached graphs of other forests stay
+// valid; a forest's own graphs name its arrays).
+void balloc(double *&p, size_t count) {
+    p = nullptr;
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(double) * std::max<size_t>(count, 1));
+    if (e != cudaSuccess) {
+        p = nullptr;
+        throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+}
+
+void bfree(double *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
 
 struct BatchDisk {
     int32_t id = 0;
-    ncorp_ctx *c = nullptr;
     int64_t n = 0;
+    int64_t off = 0;   // first moonlet in the forest's arrays
+};
+
+struct RunGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *key[4] = {};
+    long long nums[4] = {};
+    int launches = 0;
+};
+
+struct Forest {
     int p = 0;
     double theta = 0.5, dt = 0.0;
     int stream = 0;
-    double *pos = nullptr, *vel = nullptr, *m = nullptr, *R = nullptr;   // owned, caller order
-    size_t bytes = 0;
+    ncorp_ctx *c = nullptr;
+    std::vector<BatchDisk> disks;   // in array order
+    int64_t n = 0, cap = 0;         // moonlets of all disks; room in the arrays below
+    double *pos = nullptr, *vel = nullptr, *m = nullptr, *R = nullptr;   // [cap] side by side, caller order
+    bool synced = true;    // pos / vel hold the current state (else it is resident in the context only)
+    bool primed = false;   // the context holds the tree and acceleration of the current layout
+    size_t ctx_bytes = 0;  // device bytes the context took when created or grown (measured)
+    RunGraph graphs[2];
+    int graph_next = 0;
+    std::vector<int64_t> pairs;   // the last step's pairs of all disks, host copy
+    bool pairs_valid = false;
+    int64_t n_found = 0;
 };
 
 }  // namespace
@@ -1420,11 +1564,14 @@ struct ncorp_batch {
     int device = 0;
     int num_sms = 0;
     cudaStream_t user = nullptr;
-    size_t budget = 0, used = 0;
+    size_t budget = 0;
+    double bytes_per_moonlet = BATCH_DEFAULT_BYTES_PER_MOONLET;   // the largest measured so far
+    bool measured = false;
+    int *flag = nullptr;   // device word of the input check
     cudaStream_t pool[BATCH_STREAMS] = {};
-    int64_t load[BATCH_STREAMS] = {};
     cudaEvent_t ev_start = nullptr, ev_done[BATCH_STREAMS] = {};
-    std::vector<BatchDisk> disks;
+    std::vector<Forest *> forests;
+    std::vector<std::pair<int32_t, Forest *>> where;   // disk id -> forest
     int32_t next_id = 0;
     int64_t fallbacks = 0;
     int64_t launches = 0;
@@ -1441,57 +1588,266 @@ int batch_fail(ncorp_batch *b, int code, const char *fmt, ...) {
     return code;
 }
 
-BatchDisk *find_disk(ncorp_batch *b, int32_t id) {
-    for (auto &d : b->disks)
-        if (d.id == id) return &d;
+size_t free_bytes() {
+    size_t f = 0, t = 0;
+    cudaMemGetInfo(&f, &t);
+    return f;
+}
+
+size_t array_bytes(const Forest &f) { return static_cast<size_t>(f.cap) * 8 * sizeof(double); }
+
+size_t batch_used(const ncorp_batch *b) {
+    size_t u = 0;
+    for (const Forest *f : b->forests) u += f->ctx_bytes + array_bytes(*f);
+    return u;
+}
+
+Forest *forest_of(ncorp_batch *b, int32_t id, BatchDisk **disk) {
+    for (auto &w : b->where)
+        if (w.first == id) {
+            for (BatchDisk &d : w.second->disks)
+                if (d.id == id) {
+                    *disk = &d;
+                    return w.second;
+                }
+        }
     return nullptr;
 }
 
-void release_disk(BatchDisk &d) {
-    if (d.c) ncorp_free(d.c);
-    d.c = nullptr;
-    dfree(d.pos); dfree(d.vel); dfree(d.m); dfree(d.R);
+void drop_run_graphs(Forest &f) {
+    for (RunGraph &g : f.graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = RunGraph{};
+    }
 }
 
-// Tree and acceleration of the disk's initial state (what the first
-// ncorp_step of a context computes before stepping), with the usual growth
-// and retry; leaves the context resident.
-int prime_disk(ncorp_ctx *c, BatchDisk &d) {
-    const int n = static_cast<int>(d.n);
-    ensure_particles(c, n);
-    choose_parameters(c, d.p);
-    for (int attempt = 0;; attempt++) {
-        begin_call(c);
-        ensure_both_capacities(c, n);
-        reset_ctl(c);
-        ParticleSet &A = c->A;
-        upload_vec(c, d.pos, A.x, A.y, A.z, n);
-        upload_vec(c, d.vel, A.vx, A.vy, A.vz, n);
-        upload_scalar(c, d.m, A.m, n);
-        upload_scalar(c, d.R, A.R, n);
-        launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
-        build_tree(c, c->A, c->A, c->A, c->Cset, n);
-        std::swap(c->A, c->Cset);
-        gravity(c, c->A, d.p, d.theta, c->time, false);
-        const int err = finish(c);
-        if (!finite_ok(c)) return fail(c, NCORP_EINVAL, "non-finite position");
-        if (err & ERR_TIMEOUT) return fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
-        if (err == 0) break;
-        if (attempt >= MAX_RETRIES || !grow_after(c, err))
-            return fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+void free_forest(Forest *f) {
+    drop_run_graphs(*f);
+    if (f->c) ncorp_free(f->c);
+    f->c = nullptr;
+    bfree(f->pos); bfree(f->vel); bfree(f->m); bfree(f->R);
+    delete f;
+}
+
+// Arrays of room for `cap` moonlets holding the first `keep` of the old ones.
+void regrow_arrays(Forest &f, int64_t cap, int64_t keep, cudaStream_t s) {
+    double *np = nullptr, *nv = nullptr, *nm = nullptr, *nr = nullptr;
+    try {
+        balloc(np, 3 * cap); balloc(nv, 3 * cap); balloc(nm, cap); balloc(nr, cap);
+        if (keep > 0) {
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(np, f.pos, sizeof(double) * 3 * keep, cudaMemcpyDeviceToDevice, s));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(nv, f.vel, sizeof(double) * 3 * keep, cudaMemcpyDeviceToDevice, s));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(nm, f.m, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(nr, f.R, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s));
+        }
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
+    } catch (...) {
+        bfree(np); bfree(nv); bfree(nm); bfree(nr);
+        throw;
+    }
+    bfree(f.pos); bfree(f.vel); bfree(f.m); bfree(f.R);
+    f.pos = np; f.vel = nv; f.m = nm; f.R = nr;
+    f.cap = cap;
+}
+
+// The forest's current state into its arrays (caller order), if it is resident only.
+void sync_state(Forest &f) {
+    if (f.synced) return;
+    ncorp_ctx *c = f.c;
+    const int n = static_cast<int>(f.n);
+    launch_scatter_aos(c, c->A.x, c->A.y, c->A.z, c->A.perm, f.pos, n, nullptr, nullptr);
+    launch_scatter_aos(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, f.vel, n, nullptr, nullptr);
+    NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    f.synced = true;
+}
+
+// Cooperative grids of concurrent forests are capped so that the grids of all
+// streams fit on the device together; a lone forest runs uncapped, with its
+// collision search beside the gravity pipeline as in ncorp_step.
+int coop_cap(const ncorp_batch *b) {
+    const int nf = static_cast<int>(b->forests.size());
+    return nf > 1 ? std::max(16, b->num_sms / std::min(nf, BATCH_STREAMS)) : 0;
+}
+
+// Lays the forest out for its current disks and computes their tree and
+// acceleration from the arrays (which must hold the state); creates the
+// context, or creates it anew when its buffers are more than twice the size
+// the forest needs.  Synchronous.
+int prime_forest(ncorp_batch *b, Forest &f) {
+    const int n = static_cast<int>(f.n);
+    const size_t free0 = free_bytes();
+    if (f.c && f.c->n_cap > 2 * f.n && f.c->n_cap > (1 << 16)) {
+        drop_run_graphs(f);
+        ncorp_free(f.c);
+        f.c = nullptr;
+        f.ctx_bytes = 0;
+    }
+    if (!f.c) {
+        const int st = ncorp_init(&f.c, &b->cfg, f.n, b->device, b->pool[f.stream]);
+        if (st != NCORP_OK) {
+            f.c = nullptr;
+            return batch_fail(b, st, "context for %lld moonlets: allocation failed", (long long)f.n);
+        }
+    }
+    ncorp_ctx *c = f.c;
+    c->stream = b->pool[f.stream];
+    c->coop_max = coop_cap(b);
+    drop_run_graphs(f);
+    int status = NCORP_OK;
+    try {
+        std::vector<int64_t> sizes;
+        for (const BatchDisk &d : f.disks) sizes.push_back(d.n);
+        configure_disks(c, static_cast<int>(sizes.size()), sizes.data());
+        ensure_particles(c, n);
+        choose_parameters(c, f.p);
+        for (int attempt = 0;; attempt++) {
+            begin_call(c);
+            ensure_both_capacities(c, n);
+            reset_ctl(c);
+            ParticleSet &A = c->A;
+            launch_aos_to_soa(c, f.pos, A.x, A.y, A.z, n);
+            launch_aos_to_soa(c, f.vel, A.vx, A.vy, A.vz, n);
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(A.m, f.m, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+            NCORP_CUDA_CHECK(cudaMemcpyAsync(A.R, f.R, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+            launch_iota(c, reinterpret_cast<uint32_t *>(A.perm), n);
+            build_tree(c, c->A, c->A, c->A, c->Cset, n);
+            std::swap(c->A, c->Cset);
+            gravity(c, c->A, f.p, f.theta, c->time, false);
+            const int err = finish(c);
+            if (!finite_ok(c)) {
+                status = fail(c, NCORP_EINVAL, "non-finite position");
+                break;
+            }
+            if (err & ERR_TIMEOUT) {
+                status = fail(c, NCORP_ETIMEOUT, "device-side barrier timed out");
+                break;
+            }
+            if (err == 0) break;
+            if (attempt >= MAX_RETRIES || !grow_after(c, err)) {
+                status = fail(c, NCORP_EOVERFLOW, "internal list overflow (flags 0x%x)", err);
+                break;
+            }
+        }
+    } catch (const CudaError &e) {
+        status = fail(c, e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA, "%s: %s (%s:%d)", e.expr,
+                      cudaGetErrorString(e.code), e.file, e.line);
+    }
+    const size_t free1 = free_bytes();
+    if (free0 > free1) f.ctx_bytes += free0 - free1;
+    if (f.n >= BATCH_MEASURE_MIN) {   // large enough that the fixed minimum capacities do not dominate
+        const double per = static_cast<double>(f.ctx_bytes + array_bytes(f)) / static_cast<double>(f.n);
+        b->bytes_per_moonlet = b->measured ? std::max(b->bytes_per_moonlet, per) : per;
+        b->measured = true;
+    }
+    if (status != NCORP_OK) {
+        c->have_state = false;
+        c->tree_valid = false;
+        return batch_fail(b, status, "%s", ncorp_last_error(c));
     }
     c->n = n;
     c->have_state = true;
     c->tree_valid = true;
     c->tree_kind = 1;
-    c->last_pos = d.pos;
-    c->last_vel = d.vel;
-    c->last_m = d.m;
-    c->last_R = d.R;
-    c->last_p = d.p;
-    c->last_theta = d.theta;
+    c->last_pos = f.pos;
+    c->last_vel = f.vel;
+    c->last_m = f.m;
+    c->last_R = f.R;
+    c->last_p = f.p;
+    c->last_theta = f.theta;
     c->n_found = 0;
+    f.primed = true;
+    f.pairs_valid = false;
+    f.n_found = 0;
     return NCORP_OK;
+}
+
+// The device work of one run: snapshot of the state at its start (into the
+// forest's arrays, for a rerun), cleared control blocks, k steps.
+void run_body(Forest &f, int k) {
+    ncorp_ctx *c = f.c;
+    const int n = static_cast<int>(f.n);
+    const bool overlap = c->coop_max == 0;
+    launch_scatter_aos(c, c->A.x, c->A.y, c->A.z, c->A.perm, f.pos, n, nullptr, nullptr);
+    launch_scatter_aos(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, f.vel, n, nullptr, nullptr);
+    reset_ctls(c);
+    for (int s = 0; s < k; s++) {
+        enqueue_kdk(c, n, f.p, f.theta, f.dt, overlap);
+        std::swap(c->A, c->Cset);
+    }
+}
+
+void run_key(Forest &f, int k, RunGraph &g) {
+    ncorp_ctx *c = f.c;
+    const void *ptrs[4] = {c->A.x, c->ctl, f.pos, c->stream};
+    const long long nums[4] = {k, static_cast<long long>(alloc_generation()), c->coop_max, f.n};
+    std::memcpy(g.key, ptrs, sizeof ptrs);
+    std::memcpy(g.nums, nums, sizeof nums);
+}
+
+// Enqueues a run of k steps on the forest's stream through a cached graph,
+// capturing it first when none fits; a run that cannot be captured is
+// launched directly.  On return the host state describes the state after
+// the run (tree sets and particle sets traded k times).
+void enqueue_run(Forest &f, int k) {
+    ncorp_ctx *c = f.c;
+    RunGraph want;
+    run_key(f, k, want);
+    for (RunGraph &g : f.graphs)
+        if (g.exec && std::memcmp(g.key, want.key, sizeof g.key) == 0 &&
+            std::memcmp(g.nums, want.nums, sizeof g.nums) == 0) {
+            NCORP_CUDA_CHECK(cudaGraphLaunch(g.exec, c->stream));
+            for (int s = 0; s < k; s++) {
+                swap_sets(c);
+                std::swap(c->A, c->Cset);
+            }
+            c->cur_n = static_cast<int>(f.n);
+            c->grav_p = f.p;
+            c->grav_mixed = c->cfg.precision == NCORP_MIXED;
+            c->grav_local = true;
+            c->launches += g.launches;
+            return;
+        }
+    const Ctrl *ctl0 = c->ctl;
+    const double *ax0 = c->A.x;
+    const int launches0 = c->launches;
+    cudaGraph_t graph = nullptr;
+    NCORP_CUDA_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    bool ok = true;
+    try {
+        run_body(f, k);
+    } catch (const CudaError &) {
+        ok = false;
+    }
+    const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (ok && end == cudaSuccess && graph)
+        ok = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
+    else ok = false;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {   // back to the state before the capture, then the same work launched directly
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (c->ctl != ctl0) swap_sets(c);
+        if (c->A.x != ax0) std::swap(c->A, c->Cset);
+        c->launches = launches0;
+        run_body(f, k);
+        return;
+    }
+    NCORP_CUDA_CHECK(cudaGraphLaunch(exec, c->stream));
+    RunGraph &slot = f.graphs[f.graph_next];
+    f.graph_next ^= 1;
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    slot = want;
+    slot.exec = exec;
+    slot.launches = c->launches - launches0;
+}
+
+__global__ void k_count_nonfinite(const double *__restrict__ a, int64_t n, int *bad) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a[i]));
+        if ((u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(bad, 1);
+    }
 }
 
 }  // namespace
@@ -1503,16 +1859,21 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
     *out = nullptr;
     if (cfg->precision != NCORP_FP64 && cfg->precision != NCORP_MIXED) return NCORP_EINVAL;
     if (!(cfg->resolve_f == 0.0 || (cfg->resolve_f >= 1.0 && cfg->resolve_f <= 2.0))) return NCORP_EINVAL;
+    if (cfg->star_mass != 0.0) return NCORP_EINVAL;   // the star's tide needs each disk's own time
     ncorp_batch *b = new (std::nothrow) ncorp_batch();
     if (!b) return NCORP_ENOMEM;
     b->cfg = *cfg;
     b->budget = hbm_budget_bytes;
     b->user = static_cast<cudaStream_t>(cuda_stream);
+    int least = 0, greatest = 0;
     bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) == cudaSuccess;
+              cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void **>(&b->flag), sizeof(int)) == cudaSuccess;
+    // the forests' main chains at the highest priority (their side streams are at the lowest)
     for (int s = 0; ok && s < BATCH_STREAMS; s++)
-        ok = cudaStreamCreateWithFlags(&b->pool[s], cudaStreamNonBlocking) == cudaSuccess &&
+        ok = cudaStreamCreateWithPriority(&b->pool[s], cudaStreamNonBlocking, greatest) == cudaSuccess &&
              cudaEventCreateWithFlags(&b->ev_done[s], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         ncorp_batch_free(b);
@@ -1532,57 +1893,78 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
     if (!(theta > 0.0 && theta < 1.0)) return batch_fail(b, NCORP_EINVAL, "theta = %g outside (0, 1)", theta);
     if (!(dt > 0.0) || !std::isfinite(dt)) return batch_fail(b, NCORP_EINVAL, "dt must be > 0");
     if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, NCORP_ECUDA, "cudaSetDevice failed");
-    int s = 0;
-    for (int k = 1; k < BATCH_STREAMS; k++)
-        if (b->load[k] < b->load[s]) s = k;
-    BatchDisk d;
-    d.id = b->next_id;
-    d.n = n;
-    d.p = p;
-    d.theta = theta;
-    d.dt = dt;
-    d.stream = s;
-    size_t free0 = 0, free1 = 0, total = 0;
-    cudaMemGetInfo(&free0, &total);
-    int st = ncorp_init(&d.c, &b->cfg, n, b->device, b->pool[s]);
-    if (st != NCORP_OK) return batch_fail(b, st, "context for disk of %lld moonlets: allocation failed", (long long)n);
-    d.c->coop_max = std::max(8, 2 * b->num_sms / BATCH_STREAMS);
+    Forest *f = nullptr;
+    for (Forest *g : b->forests)
+        if (g->p == p && g->theta == theta && g->dt == dt) f = g;
+    const int64_t total = f ? f->n + n : n;
+    if (total > (int64_t(1) << 30)) return batch_fail(b, NCORP_EINVAL, "more than 2^30 moonlets with (p, theta, dt)");
+    if (f && static_cast<int>(f->disks.size()) >= NCORP_MAX_DISKS)
+        return batch_fail(b, NCORP_EINVAL, "%d disks already share (p, theta, dt)", NCORP_MAX_DISKS);
+    // admission by device memory: what the batch holds plus the new disk's share at the largest
+    // footprint per moonlet measured so far
+    const size_t used = batch_used(b);
+    const size_t need = static_cast<size_t>(b->bytes_per_moonlet * static_cast<double>(n));
+    if (b->budget && used + need > b->budget)
+        return batch_fail(b, NCORP_ENOMEM, "device-memory budget exceeded: %zu + %zu > %zu bytes", used, need,
+                          b->budget);
+    const bool fresh = f == nullptr;
+    if (fresh) {
+        f = new (std::nothrow) Forest();
+        if (!f) return batch_fail(b, NCORP_ENOMEM, "host allocation failed");
+        f->p = p;
+        f->theta = theta;
+        f->dt = dt;
+        f->stream = static_cast<int>(b->forests.size()) % BATCH_STREAMS;
+    }
+    cudaStream_t s = b->pool[f->stream];
+    int *bad = b->flag;
     try {
-        dalloc(d.pos, 3 * n);
-        dalloc(d.vel, 3 * n);
-        dalloc(d.m, n);
-        dalloc(d.R, n);
-        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, cudaMemcpyDefault, b->pool[s]));
-        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.vel, velocities, sizeof(double) * 3 * n, cudaMemcpyDefault, b->pool[s]));
-        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.m, masses, sizeof(double) * n, cudaMemcpyDefault, b->pool[s]));
-        NCORP_CUDA_CHECK(cudaMemcpyAsync(d.R, radii, sizeof(double) * n, cudaMemcpyDefault, b->pool[s]));
-        NCORP_CUDA_CHECK(cudaStreamSynchronize(b->pool[s]));
+        if (fresh) {   // the context now, so that it reads the environment at the time of the first add
+            const size_t free0 = free_bytes();
+            const int st = ncorp_init(&f->c, &b->cfg, n, b->device, s);
+            if (st != NCORP_OK) {
+                f->c = nullptr;
+                free_forest(f);
+                return batch_fail(b, st, "context for %lld moonlets: allocation failed", (long long)n);
+            }
+            const size_t free1 = free_bytes();
+            f->ctx_bytes = free0 > free1 ? free0 - free1 : 0;
+        } else {
+            sync_state(*f);
+        }
+        if (f->n + n > f->cap) regrow_arrays(*f, std::max(f->n + n, f->cap * 3 / 2), f->n, s);
+        const int64_t o = f->n;
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(f->pos + 3 * o, positions, sizeof(double) * 3 * n, cudaMemcpyDefault, s));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(f->vel + 3 * o, velocities, sizeof(double) * 3 * n, cudaMemcpyDefault, s));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(f->m + o, masses, sizeof(double) * n, cudaMemcpyDefault, s));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(f->R + o, radii, sizeof(double) * n, cudaMemcpyDefault, s));
+        NCORP_CUDA_CHECK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        const int g = std::max(1, std::min(static_cast<int>((3 * n + 255) / 256), 4 * b->num_sms));
+        k_count_nonfinite<<<g, 256, 0, s>>>(f->pos + 3 * o, 3 * n, bad);
+        k_count_nonfinite<<<g, 256, 0, s>>>(f->vel + 3 * o, 3 * n, bad);
+        NCORP_CUDA_CHECK(cudaGetLastError());
+        int hbad = 0;
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
+        if (hbad) {   // the disk is not added (its rows past f->n are ignored)
+            if (fresh) free_forest(f);
+            return batch_fail(b, NCORP_EINVAL, "non-finite position or velocity");
+        }
     } catch (const CudaError &e) {
-        release_disk(d);
+        if (fresh) free_forest(f);
         return batch_fail(b, e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA, "%s: %s", e.expr,
                           cudaGetErrorString(e.code));
     }
-    cudaMemGetInfo(&free1, &total);
-    d.bytes = free0 > free1 ? free0 - free1 : 0;
-    if (b->budget && b->used + d.bytes > b->budget) {
-        release_disk(d);
-        return batch_fail(b, NCORP_ENOMEM, "device-memory budget exceeded: %zu + %zu > %zu bytes", b->used, d.bytes,
-                          b->budget);
-    }
-    try {
-        st = prime_disk(d.c, d);
-    } catch (const CudaError &e) {
-        st = fail(d.c, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
-    }
-    if (st != NCORP_OK) {
-        batch_fail(b, st, "disk of %lld moonlets: %s", (long long)n, ncorp_last_error(d.c));
-        release_disk(d);
-        return st;
-    }
-    b->used += d.bytes;
-    b->load[s] += n;
-    b->disks.push_back(d);
-    b->next_id++;
+    BatchDisk d;
+    d.id = b->next_id++;
+    d.n = n;
+    d.off = f->n;
+    f->disks.push_back(d);
+    f->n += n;
+    f->primed = false;
+    f->pairs_valid = false;
+    if (fresh) b->forests.push_back(f);
+    b->where.emplace_back(d.id, f);
     *disk_id = d.id;
     return NCORP_OK;
 }
@@ -1590,34 +1972,31 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
 int ncorp_batch_run(ncorp_batch *b, int n_steps) {
     if (!b) return NCORP_EINVAL;
     if (n_steps < 0) return batch_fail(b, NCORP_EINVAL, "n_steps < 0");
-    if (n_steps == 0 || b->disks.empty()) return NCORP_OK;
-    std::vector<double> t0(b->disks.size());
     b->launches = 0;
+    if (b->forests.empty()) return NCORP_OK;
     try {
         NCORP_CUDA_CHECK(cudaSetDevice(b->device));
+        // forests whose disks changed: new layout, tree and acceleration
+        for (Forest *f : b->forests)
+            if (!f->primed) {
+                const int st = prime_forest(b, *f);
+                if (st != NCORP_OK) return st;
+                b->launches += f->c->launches;
+            }
+        if (n_steps == 0) return NCORP_OK;
         NCORP_CUDA_CHECK(cudaEventRecord(b->ev_start, b->user));
         for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamWaitEvent(b->pool[s], b->ev_start, 0));
-        for (size_t i = 0; i < b->disks.size(); i++) {
-            BatchDisk &d = b->disks[i];
-            ncorp_ctx *c = d.c;
-            c->stream = b->pool[d.stream];
-            t0[i] = c->time;
-            begin_call(c);
-            choose_parameters(c, d.p);
-            // state at the start of the run, kept in the disk's own arrays for a rerun
-            download_vec(c, c->A.x, c->A.y, c->A.z, c->A.perm, d.pos, static_cast<int>(d.n), c->stage);
-            download_vec(c, c->A.vx, c->A.vy, c->A.vz, c->A.perm, d.vel, static_cast<int>(d.n), c->stage2);
-            reset_ctls(c);
-        }
-        for (int k = 0; k < n_steps; k++)
-            for (auto &d : b->disks) {
-                ncorp_ctx *c = d.c;
-                enqueue_kdk(c, static_cast<int>(d.n), d.p, d.theta, d.dt, false);
-                std::swap(c->A, c->Cset);
-                c->time += d.dt;
+        const int cap = coop_cap(b);
+        for (Forest *f : b->forests) {
+            ncorp_ctx *c = f->c;
+            c->stream = b->pool[f->stream];
+            if (c->coop_max != cap) {
+                c->coop_max = cap;
+                drop_run_graphs(*f);
             }
-        for (auto &d : b->disks) {
-            ncorp_ctx *c = d.c;
+            begin_call(c);
+            choose_parameters(c, f->p);
+            enqueue_run(*f, n_steps);
             NCORP_CUDA_CHECK(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
             NCORP_CUDA_CHECK(cudaMemcpyAsync(c->alt.ctl_h, c->alt.ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
             NCORP_CUDA_CHECK(cudaMemcpyAsync(c->err_acc_h, c->err_acc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1628,82 +2007,197 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
         }
         for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamSynchronize(b->pool[s]));
     } catch (const CudaError &e) {
-        for (auto &d : b->disks) {
-            d.c->have_state = false;
-            d.c->tree_valid = false;
+        for (Forest *f : b->forests) {
+            f->primed = false;   // the arrays hold the state at the start of the run at the latest
+            f->synced = true;
+            if (f->c) {
+                f->c->have_state = false;
+                f->c->tree_valid = false;
+            }
         }
         return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
     }
-    for (size_t i = 0; i < b->disks.size(); i++) {
-        BatchDisk &d = b->disks[i];
-        ncorp_ctx *c = d.c;
+    for (Forest *f : b->forests) {
+        ncorp_ctx *c = f->c;
         b->launches += c->launches;
+        f->synced = false;
+        f->pairs_valid = false;
         const int err = c->ctl_h->err | c->alt.ctl_h->err | *c->err_acc_h;
         if (err & ERR_TIMEOUT) c->radix_dirty = true;
         if (err == 0) {
             c->n_found = c->cfg.collisions ? c->alt.ctl_h->n_found : 0;
             c->pairs_sorted = false;
+            c->time += n_steps * f->dt;
             record_stats(c, true, c->alt.ctl_h);
             c->stats[NCORP_STAT_COL_FOUND] = c->n_found;
+            f->n_found = c->n_found;
             continue;
         }
-        // A list overflowed or a barrier gave up in some step: rerun this disk's
-        // steps from the saved state, one synchronous step at a time (buffers
-        // grow as needed).
+        // A list overflowed or a barrier gave up in some step: rerun the forest from the state at the
+        // start of the run (in its arrays), one synchronous step at a time, buffers growing as needed.
         b->fallbacks++;
-        c->time = t0[i];
+        f->synced = true;
         c->have_state = false;
         c->tree_valid = false;
+        drop_run_graphs(*f);
+        const size_t free0 = free_bytes();
         for (int k = 0; k < n_steps; k++) {
-            const int st = ncorp_step(c, d.pos, d.vel, d.m, d.R, d.n, d.p, d.theta, d.dt);
-            if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", d.id, ncorp_last_error(c));
+            const int st = ncorp_step(c, f->pos, f->vel, f->m, f->R, f->n, f->p, f->theta, f->dt);
+            if (st != NCORP_OK) {
+                f->primed = false;
+                return batch_fail(b, st, "forest of %zu disks (p = %d): %s", f->disks.size(), f->p,
+                                  ncorp_last_error(c));
+            }
+            b->launches += c->launches;
         }
+        const size_t free1 = free_bytes();
+        if (free0 > free1) f->ctx_bytes += free0 - free1;
+        f->primed = true;
+        f->synced = true;
+        f->n_found = c->n_found;
     }
     return NCORP_OK;
 }
 
 int ncorp_batch_get_state(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities) {
     if (!b) return NCORP_EINVAL;
-    BatchDisk *d = find_disk(b, disk_id);
-    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
-    const int st = ncorp_get_state(d->c, positions, velocities);
-    if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
+    BatchDisk *d = nullptr;
+    Forest *f = forest_of(b, disk_id, &d);
+    if (!f) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    if (!positions || !velocities) return batch_fail(b, NCORP_EINVAL, "null pointer");
+    try {
+        NCORP_CUDA_CHECK(cudaSetDevice(b->device));
+        sync_state(*f);
+        cudaStream_t s = b->pool[f->stream];
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(positions, f->pos + 3 * d->off, sizeof(double) * 3 * d->n, cudaMemcpyDefault, s));
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(velocities, f->vel + 3 * d->off, sizeof(double) * 3 * d->n, cudaMemcpyDefault,
+                                         s));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
+    } catch (const CudaError &e) {
+        return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
+    }
     return NCORP_OK;
 }
 
 int ncorp_batch_collisions(ncorp_batch *b, int32_t disk_id, int64_t *pairs, int64_t cap, int64_t *n_pairs) {
     if (!b) return NCORP_EINVAL;
-    BatchDisk *d = find_disk(b, disk_id);
-    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
-    const int st = ncorp_collisions(d->c, pairs, cap, n_pairs);
-    if (st != NCORP_OK && st != NCORP_EOVERFLOW) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
-    return st;
+    BatchDisk *d = nullptr;
+    Forest *f = forest_of(b, disk_id, &d);
+    if (!f) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    if (cap < 0 || (cap > 0 && !pairs)) return batch_fail(b, NCORP_EINVAL, "bad pair buffer");
+    if (!f->pairs_valid) {   // the forest's pairs of its last step, once per run (indices of its arrays)
+        f->pairs.assign(2 * static_cast<size_t>(f->n_found), 0);
+        if (f->n_found > 0 && f->primed) {
+            int64_t got = 0;
+            const int st = ncorp_collisions(f->c, f->pairs.data(), f->n_found, &got);
+            if (st != NCORP_OK) return batch_fail(b, st, "%s", ncorp_last_error(f->c));
+        } else {
+            f->pairs.clear();
+        }
+        f->pairs_valid = true;
+    }
+    // rows are sorted by their first index and a pair never spans two disks: the disk's rows are one range
+    const int64_t rows = static_cast<int64_t>(f->pairs.size() / 2);
+    int64_t lo = 0, hi = rows;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (f->pairs[2 * mid] < d->off) lo = mid + 1;
+        else hi = mid;
+    }
+    int64_t e = lo;
+    while (e < rows && f->pairs[2 * e] < d->off + d->n) e++;
+    const int64_t k = e - lo;
+    if (n_pairs) *n_pairs = k;
+    const int64_t w = std::min(k, cap);
+    if (w > 0) {
+        std::vector<int64_t> out(2 * w);
+        for (int64_t r = 0; r < w; r++) {
+            out[2 * r] = f->pairs[2 * (lo + r)] - d->off;
+            out[2 * r + 1] = f->pairs[2 * (lo + r) + 1] - d->off;
+        }
+        if (cudaMemcpy(pairs, out.data(), sizeof(int64_t) * 2 * w, cudaMemcpyDefault) != cudaSuccess)
+            return batch_fail(b, NCORP_ECUDA, "copy of the pairs failed");
+    }
+    if (k > cap) return batch_fail(b, NCORP_EOVERFLOW, "%lld pairs found, room for %lld", (long long)k, (long long)cap);
+    return NCORP_OK;
 }
 
 int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, double *velocities) {
     if (!b) return NCORP_EINVAL;
-    BatchDisk *d = find_disk(b, disk_id);
-    if (!d) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
+    BatchDisk *dp = nullptr;
+    Forest *f = forest_of(b, disk_id, &dp);
+    if (!f) return batch_fail(b, NCORP_EINVAL, "no disk %d", disk_id);
     if ((positions == nullptr) != (velocities == nullptr))
         return batch_fail(b, NCORP_EINVAL, "give both output arrays or neither");
     if (positions) {
-        const int st = ncorp_get_state(d->c, positions, velocities);
-        if (st != NCORP_OK) return batch_fail(b, st, "disk %d: %s", disk_id, ncorp_last_error(d->c));
+        const int st = ncorp_batch_get_state(b, disk_id, positions, velocities);
+        if (st != NCORP_OK) return st;
     }
-    cudaSetDevice(b->device);
-    b->used -= std::min(b->used, d->bytes);
-    b->load[d->stream] -= d->n;
-    release_disk(*d);
-    b->disks.erase(b->disks.begin() + (d - b->disks.data()));
+    const BatchDisk d = *dp;
+    try {
+        NCORP_CUDA_CHECK(cudaSetDevice(b->device));
+        for (size_t i = 0; i < b->where.size(); i++)
+            if (b->where[i].first == disk_id) {
+                b->where.erase(b->where.begin() + i);
+                break;
+            }
+        if (f->disks.size() == 1) {   // the forest's last disk: release all of it
+            for (size_t i = 0; i < b->forests.size(); i++)
+                if (b->forests[i] == f) {
+                    b->forests.erase(b->forests.begin() + i);
+                    break;
+                }
+            free_forest(f);
+            return NCORP_OK;
+        }
+        sync_state(*f);
+        // the disks after it move down by d.n moonlets (through a copy: the ranges may overlap)
+        const int64_t tail = f->n - (d.off + d.n);
+        if (tail > 0) {
+            cudaStream_t s = b->pool[f->stream];
+            double *tmp = nullptr;
+            balloc(tmp, 3 * tail);
+            double *src[4] = {f->pos + 3 * (d.off + d.n), f->vel + 3 * (d.off + d.n), f->m + d.off + d.n,
+                              f->R + d.off + d.n};
+            double *dst[4] = {f->pos + 3 * d.off, f->vel + 3 * d.off, f->m + d.off, f->R + d.off};
+            const int64_t len[4] = {3 * tail, 3 * tail, tail, tail};
+            try {
+                for (int a = 0; a < 4; a++) {
+                    NCORP_CUDA_CHECK(cudaMemcpyAsync(tmp, src[a], sizeof(double) * len[a], cudaMemcpyDeviceToDevice, s));
+                    NCORP_CUDA_CHECK(cudaMemcpyAsync(dst[a], tmp, sizeof(double) * len[a], cudaMemcpyDeviceToDevice, s));
+                }
+                NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
+            } catch (...) {
+                bfree(tmp);
+                throw;
+            }
+            bfree(tmp);
+        }
+    } catch (const CudaError &e) {
+        return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
+    }
+    for (size_t i = 0; i < f->disks.size(); i++)
+        if (f->disks[i].id == disk_id) {
+            f->disks.erase(f->disks.begin() + i);
+            break;
+        }
+    for (BatchDisk &o : f->disks)
+        if (o.off > d.off) o.off -= d.n;
+    f->n -= d.n;
+    f->primed = false;
+    f->pairs_valid = false;
     return NCORP_OK;
 }
 
 int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info) {
     if (!b || !info || n_info < 0) return NCORP_EINVAL;
-    int64_t moonlets = 0;
-    for (const auto &d : b->disks) moonlets += d.n;
-    const int64_t v[NCORP_BATCH_NINFO] = {static_cast<int64_t>(b->disks.size()), moonlets,
-                                          static_cast<int64_t>(b->used), BATCH_STREAMS, b->fallbacks, b->launches};
+    int64_t moonlets = 0, disks = 0;
+    for (const Forest *f : b->forests) {
+        moonlets += f->n;
+        disks += static_cast<int64_t>(f->disks.size());
+    }
+    const int64_t v[NCORP_BATCH_NINFO] = {disks, moonlets, static_cast<int64_t>(batch_used(b)),
+                                          static_cast<int64_t>(b->forests.size()), b->fallbacks, b->launches};
     for (int i = 0; i < n_info && i < NCORP_BATCH_NINFO; i++) info[i] = v[i];
     return NCORP_OK;
 }
@@ -1711,16 +2205,16 @@ int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info) {
 void ncorp_batch_free(ncorp_batch *b) {
     if (!b) return;
     cudaSetDevice(b->device);
-    for (auto &d : b->disks) release_disk(d);
-    b->disks.clear();
+    for (int s = 0; s < BATCH_STREAMS; s++)
+        if (b->pool[s]) cudaStreamSynchronize(b->pool[s]);
+    for (Forest *f : b->forests) free_forest(f);
+    b->forests.clear();
     for (int s = 0; s < BATCH_STREAMS; s++) {
-        if (b->pool[s]) {
-            cudaStreamSynchronize(b->pool[s]);
-            cudaStreamDestroy(b->pool[s]);
-        }
+        if (b->pool[s]) cudaStreamDestroy(b->pool[s]);
         if (b->ev_done[s]) cudaEventDestroy(b->ev_done[s]);
     }
     if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->flag) cudaFree(b->flag);
     delete b;
 }
 

@@ -34,6 +34,26 @@ __global__ void __launch_bounds__(256) k_bbox(const double *__restrict__ x, cons
     if (gate && *gate == 0) return;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
+    if (ctl->disk_of) {   // a forest: every disk's own box
+        const int lane = threadIdx.x & 31;
+        for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += gridDim.x * blockDim.x) {
+            const int i = base + lane;
+            const bool valid = i < n;
+            unsigned long long l[3] = {~0ull, ~0ull, ~0ull}, h[3] = {0ull, 0ull, 0ull};
+            if (valid) {
+                const double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v[k]));
+                    bad |= (u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+                    l[k] = h[k] = ord_encode(v[k]);
+                }
+            }
+            fold_disk_box(ctl, valid ? ctl->disk_of[i] : 0, valid, l, h);
+        }
+        if (bad) atomicOr(&ctl->err, ERR_NONFINITE);
+        return;
+    }
     if (threadIdx.x == 0) s_bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double v[3] = {x[i], y[i], z[i]};
@@ -129,11 +149,11 @@ __device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32
 
 // Root cube: centre = midpoint of the bounding box, side L = smallest power of
 // two >= (max extent)(1 + 2^-20); q = floor((x - x_lo) 2^21 / L), clamped.
-__device__ void root_cube(const Ctrl *ctl, double out[4]) {
+__device__ void root_cube(const unsigned long long *box, double out[4]) {
     double lo[3], hi[3], ext = 0.0;
     for (int k = 0; k < 3; k++) {
-        lo[k] = ord_decode(ctl->bbox[k]);
-        hi[k] = ord_decode(ctl->bbox[3 + k]);
+        lo[k] = ord_decode(box[k]);
+        hi[k] = ord_decode(box[3 + k]);
         double e = dsub(hi[k], lo[k]);
         if (e > ext) ext = e;
     }
@@ -169,8 +189,24 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     __shared__ double s_root[4];
     __shared__ int s_shift;
     if (gate && *gate == 0) return;
+    if (ctl->disk_of) {   // a forest: each moonlet in its disk's root cube (k_disk_roots made them)
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bar_count = 0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double *r = ctl->droot + 4 * ctl->disk_of[i];
+            const int sh = KEY_BITS - (static_cast<int>((__double_as_longlong(r[3]) >> 52) & 0x7ff) - 1023);
+            const uint32_t a = quantise(x[i], r[0], sh);
+            const uint32_t b = quantise(y[i], r[1], sh);
+            const uint32_t c = quantise(z[i], r[2], sh);
+            qx[i] = a;
+            qy[i] = b;
+            qz[i] = c;
+            key[i] = hilbert_key(a, b, c);
+            idx[i] = static_cast<uint32_t>(i);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
-        root_cube(ctl, s_root);
+        root_cube(ctl->bbox, s_root);
         if (blockIdx.x == 0) {
             for (int k = 0; k < 4; k++) ctl->root[k] = s_root[k];
             ctl->bar_count = 0;
@@ -193,6 +229,13 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     }
 }
 
+// A forest's root cubes, one thread per disk, from the disks' boxes.
+__global__ void k_disk_roots(Ctrl *ctl, const int *gate) {
+    if (gate && *gate == 0) return;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ctl->nd; d += gridDim.x * blockDim.x)
+        root_cube(ctl->dbox + 6 * d, ctl->droot + 4 * d);
+}
+
 // The bounding box in ctl must be empty on entry (k_reset_ctl leaves it so),
 // or already hold the positions' box (bbox_done: the step's kick-drift kernel
 // folds it); k_keys also zeroes the grid-barrier counter for the sort that
@@ -203,6 +246,9 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
         k_bbox<<<grid_for(n, 256, c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, gate); c->launches++;
         NCORP_CUDA_CHECK(cudaGetLastError());
     }
+    if (c->nd > 1) {
+        k_disk_roots<<<grid_for(c->nd, 128), 128, 0, c->stream>>>(c->ctl, gate); c->launches++;
+    }
     k_keys<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(x, y, z, n, c->ctl, key, c->idx, qx, qy, qz,
                                                                        gate);
     c->launches++;
@@ -211,10 +257,11 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
 
 __global__ void k_bbox_reset(Ctrl *ctl, const int *gate) {
     if (*gate == 0) return;
-    for (int d = 0; d < 3; d++) {
-        ctl->bbox[d] = ~0ull;
-        ctl->bbox[3 + d] = 0ull;
-    }
+    for (int d = 0; d < ctl->nd; d++)   // (one disk: dbox is bbox)
+        for (int k = 0; k < 3; k++) {
+            ctl->dbox[6 * d + k] = ~0ull;
+            ctl->dbox[6 * d + 3 + k] = 0ull;
+        }
 }
 
 void launch_bbox_gated(ncorp_ctx *c, const double *x, const double *y, const double *z, int n, Ctrl *ctl,
@@ -270,7 +317,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
 // barrier ends each pass.
 // ---------------------------------------------------------------------------
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_SLICE = RS_TILE / RS_W;
-constexpr int RS_MAX_PASSES = 8;
+constexpr int RS_MAX_PASSES = 10;   // 8 key passes, and for a forest the disk pass and a copy pass
 constexpr unsigned long long RS_AGG = 0ull, RS_INC = 1ull << 31;   // kind bit of a status word
 
 struct RadixArgs {
@@ -312,10 +359,12 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
         int *const nxt = A.ghist + ((epoch + 1u) & 1u) * (RS_MAX_PASSES * 256);
         for (int i = blockIdx.x * RS_T + threadIdx.x; i < RS_MAX_PASSES * 256; i += gridDim.x * RS_T) nxt[i] = 0;
     }
-    // ---- 0. digit counts of every pass (s_cnt reused as [8][256])
+    // ---- 0. digit counts of every key pass (s_cnt reused as [8][256]); a forest's disk pass counts
+    // are the disks' sizes and its copy pass has the one digit 0, written by block 0
+    const int kpasses = min(A.passes, 8);
     {
         int *s_h = &s_cnt[0][0];
-        for (int i = threadIdx.x; i < RS_MAX_PASSES * 256; i += RS_T) s_h[i] = 0;
+        for (int i = threadIdx.x; i < 8 * 256; i += RS_T) s_h[i] = 0;
         __syncthreads();
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const long long base = static_cast<long long>(tile) * RS_TILE;
@@ -323,13 +372,18 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
                 const long long i = base + static_cast<long long>(k) * RS_T + threadIdx.x;
                 if (i < n) {
                     const uint64_t key = A.k0[i];
-                    for (int p = 0; p < A.passes; p++) atomicAdd(&s_h[p * 256 + ((key >> (8 * p)) & 0xffu)], 1);
+                    for (int p = 0; p < kpasses; p++) atomicAdd(&s_h[p * 256 + ((key >> (8 * p)) & 0xffu)], 1);
                 }
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < A.passes * 256; i += RS_T)
+        for (int i = threadIdx.x; i < kpasses * 256; i += RS_T)
             if (s_h[i]) atomicAdd(&ghist[i], s_h[i]);
+        if (A.passes > 8 && blockIdx.x == 0) {
+            const int t = threadIdx.x;   // RS_T = 256 threads: one digit each
+            ghist[8 * 256 + t] = t < A.ctl->nd ? A.ctl->doff[t + 1] - A.ctl->doff[t] : 0;
+            ghist[9 * 256 + t] = t == 0 ? n : 0;
+        }
     }
     if (!grid_sync(A.ctl, bar)) return;
     const bool wrap = epoch + 1 >= A.epoch_limit;
@@ -359,7 +413,8 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
             for (int r = 0; r < RS_I; r++) {
                 const long long i = base + r * 32 + lane;
                 const bool ok = i < n;
-                const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
+                const int d = ps < 8 ? static_cast<int>((kk[r] >> shift) & 0xffu)
+                                     : (ps == 8 && ok ? A.ctl->disk_of[vv[r]] : 0);   // disk pass, copy pass
                 // lanes holding the same digit: one ballot per digit bit, every lane of the warp taking part
                 // in every ballot (lanes past n start from the mask of valid lanes and keep only themselves)
                 unsigned peers = __ballot_sync(0xffffffffu, ok);
@@ -427,7 +482,8 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
             for (int r = 0; r < RS_I; r++) {
                 const long long i = base + r * 32 + lane;
                 if (i < n) {
-                    const int d = static_cast<int>((kk[r] >> shift) & 0xffu);
+                    const int d = ps < 8 ? static_cast<int>((kk[r] >> shift) & 0xffu)
+                                         : (ps == 8 ? A.ctl->disk_of[vv[r]] : 0);
                     const int pos = s_start[d] + s_excl[d] + s_cnt[w][d] + rank[r];
                     // always in range for a consistent prefix; a look-back that gave up (ERR_TIMEOUT, the
                     // call fails) must not write outside the arrays
@@ -474,7 +530,7 @@ unsigned radix_epoch_limit() {
 }
 
 // Layout of the context's radix scratch (ints): two sets of digit histograms
-// of every pass at [0, 4096), the epoch counter at RS_EPOCH_AT, the tile
+// of every pass at [0, 2 RS_MAX_PASSES 256), the epoch counter at RS_EPOCH_AT, the tile
 // status words from RS_STATUS_AT on.  The status words never share memory with anything
 // else, so a word left by an earlier sort (of any size) carries an older tag.
 constexpr int RS_EPOCH_AT = 2 * RS_MAX_PASSES * 256;
@@ -494,7 +550,7 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
 }
 
 static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                            int n, int bits) {
+                            int n, int bits, bool by_disk = false) {
     ensure_radix_scratch(c, n);
     if (c->radix_dirty) {
         // A sort of an earlier call may have stopped at a timed-out barrier before advancing the epoch,
@@ -505,6 +561,7 @@ static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64
     }
     int passes = (bits + 7) / 8;
     if (passes & 1) passes++;
+    if (by_disk) passes = RS_MAX_PASSES;   // the key passes, the disk pass and the copy pass
     RadixArgs A;
     A.k0 = keys; A.k1 = keys_alt; A.v0 = vals; A.v1 = vals_alt;
     A.n = n; A.ntiles = (n + RS_TILE - 1) / RS_TILE; A.passes = passes;
@@ -519,9 +576,9 @@ static RadixArgs radix_args(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64
 }
 
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
-                    int bits, bool bar_zeroed, const int *gate) {
+                    int bits, bool bar_zeroed, const int *gate, bool by_disk) {
     if (n <= 1) return;
-    RadixArgs A = radix_args(c, keys, vals, keys_alt, vals_alt, n, bits);
+    RadixArgs A = radix_args(c, keys, vals, keys_alt, vals_alt, n, bits, by_disk && c->nd > 1);
     A.gate = gate;
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_radix),
@@ -768,6 +825,7 @@ struct GatherArgs {
     float4 *hi4, *lo4;
     const uint32_t *idx;
     const uint64_t *key;   // sorted keys
+    const unsigned short *disk_of;   // a forest: disk of each position (equal keys of two disks are no run)
     double G;
     int n;
     const int *gate;       // nothing to do while *gate is 0 (null: always)
@@ -779,10 +837,12 @@ __global__ void k_gather(GatherArgs g) {
         const int j = static_cast<int>(g.idx[i]);
         int d = i;
         const uint64_t k = g.key[i];
-        if ((i > 0 && g.key[i - 1] == k) || (i + 1 < g.n && g.key[i + 1] == k)) {
+        const int dk = g.disk_of ? g.disk_of[i] : 0;
+        auto same = [&](int u) { return g.key[u] == k && (!g.disk_of || g.disk_of[u] == dk); };
+        if ((i > 0 && same(i - 1)) || (i + 1 < g.n && same(i + 1))) {
             int s = i, e = i + 1;
-            while (s > 0 && g.key[s - 1] == k) s--;
-            while (e < g.n && g.key[e] == k) e++;
+            while (s > 0 && same(s - 1)) s--;
+            while (e < g.n && same(e)) e++;
             const int pj = g.perm[j];
             int r = 0;
             for (int u = s; u < e; u++) r += g.perm[g.idx[u]] < pj;
@@ -824,6 +884,7 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     g.hi4 = dst.hi4; g.lo4 = dst.lo4;
     g.idx = idx;
     g.key = dst.key;
+    g.disk_of = c->nd > 1 ? c->disk_of : nullptr;
     g.G = G;
     g.n = n;
     k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g); c->launches++;
@@ -856,6 +917,11 @@ __global__ void k_static_reset(StaticScratch *S) {
     Ctrl &c = S->ctl;
     c.err = 0;
     c.bar_count = 0;
+    c.nd = 1;   // one disk: the box and root cube of the control block itself
+    c.disk_of = nullptr;
+    c.doff = nullptr;
+    c.dbox = c.bbox;
+    c.droot = c.root;
     for (int k = 0; k < 3; k++) {
         c.bbox[k] = ~0ull;
         c.bbox[3 + k] = 0ull;

@@ -70,25 +70,29 @@ struct BuildArgs {
     const int *gate;        // nothing to do while *gate is 0 (null: always build)
 };
 
+// The roots: one per disk (cell d holds disk d's moonlets; one disk: cell 0 holds all).
 __global__ void k_build_init(BuildArgs A) {
     if (A.gate && *A.gate == 0) return;
-    A.level[0] = 0;
-    A.first[0] = 0;
-    A.count[0] = A.n;
-    A.child0[0] = -1;
-    A.nchild[0] = 0;
-    A.parent[0] = -1;
-    A.cx[0] = A.cy[0] = A.cz[0] = 0;
-    A.maker[0] = 0;
-    A.before[0] = 0;
+    const int nd = A.ctl->nd;
+    for (int d = 0; d < nd; d++) {
+        A.level[d] = 0;
+        A.first[d] = A.ctl->doff ? A.ctl->doff[d] : 0;
+        A.count[d] = A.ctl->doff ? A.ctl->doff[d + 1] - A.ctl->doff[d] : A.n;
+        A.child0[d] = -1;
+        A.nchild[d] = 0;
+        A.parent[d] = -1;
+        A.cx[d] = A.cy[d] = A.cz[d] = 0;
+        A.maker[d] = 0;
+        A.before[d] = 0;
+        A.arrive[d] = 0;     // arrival counters of the collision climb and of the multipoles,
+        A.arrive_m[d] = 0;   // zeroed as cells are made
+    }
     A.ctl->level_start[0] = 0;
-    A.ctl->level_start[1] = 1;
-    A.ctl->n_cells = 1;
+    A.ctl->level_start[1] = nd;
+    A.ctl->n_cells = nd;
     A.ctl->max_level = 0;
     A.ctl->n_leaves = 0;
     A.ctl->bar_count = 0;
-    A.arrive[0] = 0;        // arrival counters of the collision climb and of the multipoles,
-    A.arrive_m[0] = 0;      // zeroed as cells are made
 }
 
 // Octant boundaries of cell c (level lev, moonlets [f, f + cnt)), written to
@@ -178,8 +182,8 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     const int G = gridDim.x;
     unsigned bar = 0;
     if (A.gate && *A.gate == 0) return;   // every block returns before the first barrier
-    {
-        const int t = made_cells(A, 0, blockIdx.x == 0 ? 1 : 0, 0, s_red);
+    {   // block 0 makes the roots' children counts
+        const int t = made_cells(A, 0, blockIdx.x == 0 ? vc->level_start[1] : 0, 0, s_red);
         if (threadIdx.x == 0) A.blocksum[blockIdx.x] = t;
     }
     if (!grid_sync(A.ctl, bar)) return;
@@ -345,27 +349,33 @@ void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *g
 // Corner cap (Sect. 3.4.2): distance from s to the farthest corner of the
 // cell's cube, the cube widened by L 2^-48 on each side.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cell_side(const Ctrl *ctl, int lev) { return ldexp(ctl->root[3], -lev); }
+// root: the cube of the cell's disk (x_lo, y_lo, z_lo, L)
+__device__ __forceinline__ double cell_side(const double *root, int lev) { return ldexp(root[3], -lev); }
 
-__device__ __forceinline__ double corner_axis(const Ctrl *ctl, int k, double h, uint32_t c, double s) {
-    const double eps = dmul(ctl->root[3], 0x1p-48);
-    const double lo = dadd(ctl->root[k], dmul(static_cast<double>(c), h));
+// the root cube of cell c's disk
+__device__ __forceinline__ const double *cell_root(const Ctrl *ctl, const int *first, int c) {
+    return disk_root(ctl, disk_of(ctl, first[c]));
+}
+
+__device__ __forceinline__ double corner_axis(const double *root, int k, double h, uint32_t c, double s) {
+    const double eps = dmul(root[3], 0x1p-48);
+    const double lo = dadd(root[k], dmul(static_cast<double>(c), h));
     const double a = dsub(s, dsub(lo, eps));
     const double b = dsub(dadd(dadd(lo, h), eps), s);
     return a > b ? a : b;
 }
 
-__device__ __forceinline__ double corner_distance(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz,
+__device__ __forceinline__ double corner_distance(const double *root, int lev, uint32_t cx, uint32_t cy, uint32_t cz,
                                                   double sx, double sy, double sz) {
-    const double h = cell_side(ctl, lev);
-    return dnorm3(corner_axis(ctl, 0, h, cx, sx), corner_axis(ctl, 1, h, cy, sy), corner_axis(ctl, 2, h, cz, sz));
+    const double h = cell_side(root, lev);
+    return dnorm3(corner_axis(root, 0, h, cx, sx), corner_axis(root, 1, h, cy, sy), corner_axis(root, 2, h, cz, sz));
 }
 
 // Power-of-two scale of a cell's expansions: >= r_max (so |x - s|/rho <= 1)
 // and >= side/256, so that the scale ratios met in M2M, M2L and L2L stay
 // below 2^(level difference + 8) even for one-moonlet cells (r_max ~ 0).
-__device__ __forceinline__ double cell_scale(const Ctrl *ctl, int lev, double rmax) {
-    return pow2_ceil(fmax(rmax, cell_side(ctl, lev) * 0x1p-8));
+__device__ __forceinline__ double cell_scale(const double *root, int lev, double rmax) {
+    return pow2_ceil(fmax(rmax, cell_side(root, lev) * 0x1p-8));
 }
 
 // FP32 double-float copy of a centre: hi = fl32(s), lo = fl32(s - hi)
@@ -457,8 +467,9 @@ __device__ __forceinline__ double quad_corner(const ClimbArgs &A, const LeafSlot
     double d = 0.0;
     if (L.valid && L.q < 3) {
         const int lev = A.level[L.c];
-        const double h = cell_side(A.ctl, lev);
-        d = corner_axis(A.ctl, L.q, h, L.q == 0 ? A.cx[L.c] : (L.q == 1 ? A.cy[L.c] : A.cz[L.c]),
+        const double *rt = disk_root(A.ctl, disk_of(A.ctl, L.f));
+        const double h = cell_side(rt, lev);
+        d = corner_axis(rt, L.q, h, L.q == 0 ? A.cx[L.c] : (L.q == 1 ? A.cy[L.c] : A.cz[L.c]),
                         L.q == 0 ? sx : (L.q == 1 ? sy : sz));
     }
     const double d0 = __shfl_sync(0xffffffffu, d, L.base), d1 = __shfl_sync(0xffffffffu, d, L.base + 1),
@@ -489,7 +500,7 @@ __device__ __forceinline__ void leaf_gravity_group(const ClimbArgs &A, int gw, i
     if (cap < rmax) rmax = cap;
     if (L.valid && L.q == 0) {
         const int c = L.c;
-        const double rho = cell_scale(A.ctl, A.level[c], rmax);
+        const double rho = cell_scale(cell_root(A.ctl, A.first, c), A.level[c], rmax);
         A.M[c] = M;
         A.sx[c] = sx;
         A.sy[c] = sy;
@@ -559,11 +570,11 @@ __device__ __forceinline__ void parent_centre(const ClimbShared &S, int nch, int
     pz = __shfl_sync(0xffffffffu, q, 3);
 }
 
-__device__ __forceinline__ double corner_warp(const Ctrl *ctl, int lev, uint32_t cx, uint32_t cy, uint32_t cz, double sx,
+__device__ __forceinline__ double corner_warp(const double *root, int lev, uint32_t cx, uint32_t cy, uint32_t cz, double sx,
                                               double sy, double sz, int lane) {
-    const double h = cell_side(ctl, lev);
+    const double h = cell_side(root, lev);
     double d = 0;
-    if (lane < 3) d = corner_axis(ctl, lane, h, lane == 0 ? cx : (lane == 1 ? cy : cz), lane == 0 ? sx : (lane == 1 ? sy : sz));
+    if (lane < 3) d = corner_axis(root, lane, h, lane == 0 ? cx : (lane == 1 ? cy : cz), lane == 0 ? sx : (lane == 1 ? sy : sz));
     const double d0 = __shfl_sync(0xffffffffu, d, 0), d1 = __shfl_sync(0xffffffffu, d, 1),
                  d2 = __shfl_sync(0xffffffffu, d, 2);
     return dnorm3(d0, d1, d2);
@@ -613,15 +624,16 @@ __device__ __forceinline__ void parent_gravity_group(const ClimbArgs &A, int c, 
     const int plev = valid ? A.level[c] : 0;
     double d = 0.0;
     if (valid && j < 3) {
-        const double h = cell_side(A.ctl, plev);
-        d = corner_axis(A.ctl, j, h, j == 0 ? A.cx[c] : (j == 1 ? A.cy[c] : A.cz[c]), j == 0 ? px : (j == 1 ? py : pz));
+        const double *rt = cell_root(A.ctl, A.first, c);
+        const double h = cell_side(rt, plev);
+        d = corner_axis(rt, j, h, j == 0 ? A.cx[c] : (j == 1 ? A.cy[c] : A.cz[c]), j == 0 ? px : (j == 1 ? py : pz));
     }
     const double d0 = __shfl_sync(0xffffffffu, d, base), d1 = __shfl_sync(0xffffffffu, d, base + 1),
                  d2 = __shfl_sync(0xffffffffu, d, base + 2);
     const double pcap = dnorm3(d0, d1, d2);
     if (pcap < rm) rm = pcap;
     if (valid && j == 0) {
-        const double prho = cell_scale(A.ctl, plev, rm);
+        const double prho = cell_scale(cell_root(A.ctl, A.first, c), plev, rm);
         A.M[c] = M;
         A.sx[c] = px;
         A.sy[c] = py;
@@ -947,11 +959,12 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_geometry(ClimbArgs A)
         if (!grid_sync(A.ctl, bar)) return;
     }
     const int nc = min(A.ctl->n_cells, A.cap);
-    const double Mtot = __ldcg(&A.M[0]);
     // theta(M): every lane one cell; the dependent FP64 chain of a warp bounds this phase, so fewer,
-    // fuller warps (at most one per sub-partition) finish first
+    // fuller warps (at most one per sub-partition) finish first.  M_tot is the mass of the cell's disk
+    // (its root: cell d of disk d).
     {
         for (int i = gw0 * 32 + lane; i < nc; i += nwarps * 32) {
+            const double Mtot = __ldcg(&A.M[disk_of(A.ctl, A.first[i])]);
             const double rc = ddiv(__ldcg(&A.rmax[i]), theta_of(__ldcg(&A.M[i]), Mtot, A.theta));
             A.rcrit[i] = rc;
             A.gh[i].w = static_cast<float>(rc);
@@ -1100,7 +1113,8 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs 
             }
             rm = warp_max(rm);
             e2 = warp_max(e2);
-            const double pcap = corner_warp(A.ctl, A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py, pz, lane);
+            const double pcap = corner_warp(cell_root(A.ctl, A.first, c), A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py,
+                                            pz, lane);
             if (pcap < rm) rm = pcap;
             if (lane == 0) {
                 const double rc = dadd(rm, e2);

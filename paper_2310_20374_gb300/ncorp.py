@@ -13,10 +13,13 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
+
 from . import build as _build
 
 NCORP_OK, NCORP_EINVAL, NCORP_ENOMEM, NCORP_ECUDA, NCORP_EOVERFLOW, NCORP_ETIMEOUT, NCORP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 NCORP_FP64, NCORP_MIXED = 0, 1
+NCORP_MAX_DISKS = 256
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
               "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters",
               "graph", "sort_path", "resolved"]
@@ -63,6 +66,7 @@ def load(path: str | None = None):
     L.ncorp_set_stream.argtypes = [vp, vp]
     L.ncorp_step.argtypes = [vp, vp, vp, vp, vp, i64, ip, dbl, dbl]
     L.ncorp_reset.argtypes = [vp]
+    L.ncorp_set_disks.argtypes = [vp, ip, vp]
     L.ncorp_set_graphs.argtypes = [vp, ip]
     L.ncorp_collisions.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.ncorp_accel.argtypes = [vp, vp, vp, i64, ip, dbl, vp, vp]
@@ -92,7 +96,7 @@ def load(path: str | None = None):
     L.ncorp_free.restype = None
     L.ncorp_last_error.argtypes = [vp]
     L.ncorp_last_error.restype = C.c_char_p
-    for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
+    for name in ("ncorp_init", "ncorp_set_stream", "ncorp_step", "ncorp_reset", "ncorp_set_disks", "ncorp_set_graphs", "ncorp_collisions", "ncorp_accel",
                  "ncorp_accel_standard", "ncorp_collide", "ncorp_collide_standard", "ncorp_get_state", "ncorp_stats", "ncorp_tree_export", "ncorp_expansions", "ncorp_profile", "ncorp_stage_times",
                  "ncorp_hilbert_sort_static", "ncorp_fma_peak", "ncorp_batch_create", "ncorp_batch_add_disk", "ncorp_batch_run",
                  "ncorp_batch_get_state", "ncorp_batch_collisions", "ncorp_batch_remove_disk", "ncorp_batch_info"):
@@ -187,6 +191,13 @@ def ncorp_reset(ctx):
     return _check(ctx, load().ncorp_reset(ctx))
 
 
+def ncorp_set_disks(ctx, sizes):
+    """Lays the context's moonlets out as len(sizes) independent disks (sizes: moonlets per disk, in the
+    order the disks follow one another in the arrays of later calls); [n] returns to one disk."""
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64).reshape(-1))
+    return _check(ctx, load().ncorp_set_disks(ctx, int(sz.size), sz.ctypes.data if sz.size else None))
+
+
 def ncorp_set_graphs(ctx, enable):
     return _check(ctx, load().ncorp_set_graphs(ctx, 1 if enable else 0))
 
@@ -277,7 +288,7 @@ def ncorp_stage_times(ctx) -> dict:
 
 
 NCORP_STATIC_MAX_N = 65536
-BATCH_INFO_NAMES = ["disks", "moonlets", "bytes", "streams", "fallbacks", "launches"]
+BATCH_INFO_NAMES = ["disks", "moonlets", "bytes", "forests", "fallbacks", "launches"]
 
 
 def _bcheck(b, st, ok=(NCORP_OK,)):

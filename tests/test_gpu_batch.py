@@ -1,9 +1,11 @@
 """Batches of independent disks (ncorp_batch_*), needs a GB300.
 
 Every disk of a batch must evolve as the same disk stepped alone with
-ncorp_step: the batch only changes how the work is scheduled (streams,
-cooperative grid sizes), so FP64 states agree to rounding of the M2L sums
-(whose atomics add in a different order) and the colliding pairs are the same.
+ncorp_step: the batch only changes how the work is scheduled (disks of the
+same (p, theta, dt) side by side in one forest, one launch per stage over
+them, runs replayed from CUDA graphs, forests on separate streams), so FP64
+states agree to the rounding of sums taken in another order and the
+colliding pairs are the same.
 """
 import numpy as np
 import pytest
@@ -77,7 +79,7 @@ def test_batch_disks_evolve_as_single_disks():
         ncorp.ncorp_batch_run(b, 2)
         info = ncorp.ncorp_batch_info(b)
         assert info["disks"] == len(DISKS) and info["moonlets"] == sum(x[0] for x in DISKS)
-        assert info["launches"] > 0
+        assert info["launches"] > 0 and info["forests"] == len(DISKS)
         for (n, p, theta, dt, _, dense), d, did in zip(DISKS, disks, ids):
             pos = np.zeros((n, 3))
             vel = np.zeros((n, 3))
@@ -98,6 +100,64 @@ def test_batch_disks_evolve_as_single_disks():
         np.testing.assert_allclose(out_p.cpu().numpy(), xs, rtol=0, atol=1e-12 * np.abs(xs).max())
         ncorp.ncorp_batch_run(b, 1)
         assert ncorp.ncorp_batch_info(b)["disks"] == len(DISKS) - 1
+    finally:
+        ncorp.ncorp_batch_free(b)
+
+
+def batch_of(disks, p, theta, dt):
+    b = ncorp.ncorp_batch_create(config(), 0, torch.cuda.current_stream().cuda_stream)
+    ids = [ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], len(d["pos"]), p, theta, dt)
+           for d in disks]
+    return b, ids
+
+
+def check_disk(b, did, d, p, theta, dt, steps):
+    n = len(d["pos"])
+    pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+    ncorp.ncorp_batch_get_state(b, did, pos, vel)
+    pairs = np.zeros((1 << 14, 2), dtype=np.int64)
+    k = ncorp.ncorp_batch_collisions(b, did, pairs, len(pairs))
+    xs, vs, ps = single_disk_run(d, p, theta, dt, steps)
+    np.testing.assert_allclose(pos, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+    np.testing.assert_allclose(vel, vs, rtol=0, atol=1e-11 * np.abs(vs).max())
+    assert np.array_equal(pairs[:k], ps)
+    return k
+
+
+def test_forest_of_many_disks_evolves_as_single_disks():
+    """Twelve disks of mixed size with one (p, theta, dt): one forest, launches per run independent of the
+    number of disks; a disk removed or added in the middle leaves the others' evolution unchanged."""
+    p, theta, dt = 4, 0.5, 2e-2
+    sizes = np.exp(np.random.default_rng(5).uniform(np.log(500), np.log(8000), 12)).astype(int)
+    disks = [make_disk(int(n), 400 + k, k % 4 == 0) for k, n in enumerate(sizes)]
+    b, ids = batch_of(disks, p, theta, dt)
+    try:
+        ncorp.ncorp_batch_run(b, 3)
+        ncorp.ncorp_batch_run(b, 2)   # a second graph (another length), then the first one replayed
+        ncorp.ncorp_batch_run(b, 3)
+        info = ncorp.ncorp_batch_info(b)
+        assert info["forests"] == 1 and info["disks"] == 12 and info["fallbacks"] == 0
+        launches12 = info["launches"]
+        found = sum(check_disk(b, did, d, p, theta, dt, 8) for did, d in zip(ids, disks))
+        assert found > 0
+        # remove one in the middle, add a new one: both take effect at the next run
+        ncorp.ncorp_batch_remove_disk(b, ids[5])
+        extra = make_disk(3000, 450, True)
+        new_id = ncorp.ncorp_batch_add_disk(b, extra["pos"], extra["vel"], extra["mass"], extra["radius"], 3000, p,
+                                            theta, dt)
+        ncorp.ncorp_batch_run(b, 2)
+        assert ncorp.ncorp_batch_info(b)["disks"] == 12
+        for k in (0, 4, 6, 11):
+            check_disk(b, ids[k], disks[k], p, theta, dt, 10)
+        check_disk(b, new_id, extra, p, theta, dt, 2)
+    finally:
+        ncorp.ncorp_batch_free(b)
+    # the same runs with a quarter of the disks: the same launches (one per stage, not per disk)
+    b, _ = batch_of(disks[:3], p, theta, dt)
+    try:
+        for k in (3, 2, 3):
+            ncorp.ncorp_batch_run(b, k)
+        assert ncorp.ncorp_batch_info(b)["launches"] == launches12
     finally:
         ncorp.ncorp_batch_free(b)
 
