@@ -64,6 +64,8 @@ def parse():
                          "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="serving: length of the arrival window")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
+    ap.add_argument("--tick-steps", type=int, default=10, help="serving: most steps per ncorp_batch_run")
+    ap.add_argument("--steps4", type=int, default=50, help="default run: steps of the 64-disk ensemble")
     return ap.parse_args()
 
 
@@ -390,6 +392,8 @@ def run_gpu(a):
         extra["config3"] = {"config": workload_config(a, n=n3, seed=3, p=4, theta=0.6, precision="mixed"),
                             **summarize(a, t3, n3, a.steps3, world, dist, hbm, peaks["fp32_tflops"], 4),
                             "roofline": near_roofline(t3, peaks["fp32_tflops"], "mixed", None)}
+        # ---- workload 4: 64 disks of mixed size in one batch, 50 steps replayed from one graph
+        extra["config4"] = time_ensemble(a, ncorp, torch, dist, world, rank, stream, a.steps4, 3)
     clocks = sampler.stop()
 
     # ---- end to end through the C ABI with pinned host buffers: every step
@@ -565,64 +569,76 @@ def batch_common(a):
     return torch, dist, ncorp, cfg, rank, world, local
 
 
-def run_ensemble(a):
-    """64 disks per GPU, N log-uniform in [1e3, 2e5], seeds 100..163 (+ 64 rank), p = 6, theta_min = 0.5,
-    advanced together by ncorp_batch_run; value = moonlet-steps of all disks / time."""
-    torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
+def time_ensemble(a, ncorp, torch, dist, world, rank, stream, steps, warmup):
+    """Workload 4: 64 disks per GPU, N log-uniform in [1e3, 2e5] (sizes seeded 100 + rank, disk k seeded
+    100 + 64 rank + k), p = 6, theta_min = 0.5, mixed, dt = 1e-3, advanced together by ncorp_batch_run: every
+    disk in one forest, one launch per stage, the run of `steps` steps replayed from one CUDA graph."""
     from paper_2310_20374_gb300 import diskgen
-    stream = torch.cuda.current_stream()
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED
+    p, theta, dt = 6, 0.5, 1e-3
     sizes = ensemble_sizes(64, 1e3, 2e5, 100 + rank)
     b = ncorp.ncorp_batch_create(cfg, 0, stream.cuda_stream)
-    for k, n in enumerate(sizes):
-        d = diskgen.make_disk(int(n), 100 + 64 * rank + k)
-        args = [torch.tensor(d[f], device="cuda") for f in ("pos", "vel", "mass", "radius")]
-        ncorp.ncorp_batch_add_disk(b, *args, int(n), a.p, a.theta, a.dt)
-    total = int(sizes.sum())
-    ncorp.ncorp_batch_run(b, max(a.warmup, 3))
-
-    def barrier():
+    try:
+        for k, n in enumerate(sizes):
+            d = diskgen.make_disk(int(n), 100 + 64 * rank + k)
+            args = [torch.tensor(d[f], device="cuda") for f in ("pos", "vel", "mass", "radius")]
+            ncorp.ncorp_batch_add_disk(b, *args, int(n), p, theta, dt)
+        total = int(sizes.sum())
+        ncorp.ncorp_batch_run(b, warmup)
+        ncorp.ncorp_batch_run(b, steps)   # captures the graph of this run length
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ncorp.ncorp_batch_run(b, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = ncorp.ncorp_batch_info(b)
+        t_max = slowest_rank(dist, ms, world)
+        # end to end: another run, then every disk's state read back to pinned host memory
+        hp = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
+        hv = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
+        t0 = time.perf_counter()
+        ncorp.ncorp_batch_run(b, steps)
+        for k in range(len(sizes)):
+            ncorp.ncorp_batch_get_state(b, k, hp[k], hv[k])
+        e2e_s = slowest_rank(dist, time.perf_counter() - t0, world)
+    finally:
+        ncorp.ncorp_batch_free(b)
+    value = replica_throughput(total, steps, world, t_max * 1e-3)
+    return {"value": round(value, 1), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": round(t_max / steps, 4),
+            "config": {"workload": f"64 disks per GPU, N log-uniform in [1e3, 2e5] (total {total} moonlets), "
+                                   f"falcON p={p} theta_min={theta}, {steps} SBAB1 steps dt={dt} with collision "
+                                   f"search, mixed precision, one ncorp_batch_run (one forest: one launch per "
+                                   f"stage over all disks, the run replayed from one CUDA graph)",
+                       "moonlets_per_gpu": total, "disks_per_gpu": 64, "leaf_size": leaf_size_for(p),
+                       "gravity_thresholds": list(thresholds_for(p)),
+                       "l2": "inputs larger than L2 (about 1 kB of state and tree per moonlet)",
+                       "parallelism": "replicas (one batch of 64 disks per GPU)"},
+            "gpu_launches": info["launches"], "forests": info["forests"],
+            "e2e": {"value": round(replica_throughput(total, steps, world, e2e_s), 1), "unit": UNIT,
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(48 * total / steps),
+                    "note": "host wall time of ncorp_batch_run plus reading every disk's state back to pinned "
+                            "host memory once per run (per-step bytes averaged)"}}
 
+
+def run_ensemble(a):
+    """Workload 4 alone (see time_ensemble); value = moonlet-steps of all disks / time."""
+    torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
+    stream = torch.cuda.current_stream()
     sampler = ClockSampler(physical_gpu_index(local))
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ncorp.ncorp_batch_run(b, a.steps)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    barrier()
+    r = time_ensemble(a, ncorp, torch, dist, world, rank, stream, a.steps, max(a.warmup, 3))
     clocks = sampler.stop()
-    info = ncorp.ncorp_batch_info(b)
-    t_max = slowest_rank(dist, ms, world)
-    # end to end: states read back to host memory after the run (state stays resident between runs)
-    hp = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
-    hv = [torch.empty((int(n), 3), dtype=torch.float64).pin_memory() for n in sizes]
-    t0 = time.perf_counter()
-    ncorp.ncorp_batch_run(b, a.steps)
-    for k in range(len(sizes)):
-        ncorp.ncorp_batch_get_state(b, k, hp[k], hv[k])
-    e2e_s = slowest_rank(dist, time.perf_counter() - t0, world)
-    ncorp.ncorp_batch_free(b)
-    value = replica_throughput(total, a.steps, world, t_max * 1e-3)
-    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
-           "warmup": max(a.warmup, 3), "ms_per_step": round(t_max / a.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
-           "data": "synthetic (seeded moonlet disks shaped like the paper's)",
-           "config": {"workload": f"64 disks per GPU, N log-uniform in [1e3, 2e5] (total {total} moonlets), "
-                                  f"falcON p={a.p} theta_min={a.theta}, {a.steps} SBAB1 steps dt={a.dt} with collision "
-                                  f"search, {a.precision} precision, one ncorp_batch_run",
-                      "moonlets_per_gpu": total, "disks_per_gpu": 64,
-                      "l2": "inputs larger than L2 (about 1 kB of state and tree per moonlet)",
-                      "parallelism": "replicas (one batch of 64 disks per GPU)"},
-           "gpu_launches": info["launches"], "clocks": clocks,
-           "e2e": {"value": round(replica_throughput(total, a.steps, world, e2e_s), 1), "unit": UNIT, "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": int(48 * total / a.steps),
-                   "note": "host wall time of ncorp_batch_run plus reading every disk's state back to pinned host "
-                           "memory once per run (per-step bytes averaged)"}}
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": max(a.warmup, 3), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+           "data": "synthetic (seeded moonlet disks shaped like the paper's)", "config": r["config"],
+           "gpu_launches": r["gpu_launches"], "clocks": clocks, "e2e": r["e2e"]}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -630,70 +646,54 @@ def run_ensemble(a):
 
 
 def run_serving(a):
-    """Disks arrive as a Poisson stream (rate r per s over the window), N log-uniform in [1e3, 1e6], p uniform in
-    {3, 4, 6}, theta_min = 0.5, each integrated for 100 steps; every tick advances all active disks one step.
-    Reports the p50/p99 of the step latency seen by the disks and the aggregate moonlet-steps/s."""
+    """Serving (continuous batching): disks arrive as a Poisson stream (rate r per s over the window), N
+    log-uniform in [1e3, 1e6], p uniform in {3, 4, 6}, theta_min = 0.5, each integrated for 100 steps; the loop
+    of paper_2310_20374_gb300.serving admits arrived requests in order while the batch's memory budget allows
+    and advances every resident disk by up to --tick-steps steps per ncorp_batch_run."""
     torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
-    from paper_2310_20374_gb300 import diskgen
-    rng = np.random.default_rng(500 + rank)
-    arrivals = []
-    t = rng.exponential(1.0 / a.serve_rate)
-    while t < a.serve_seconds:
-        arrivals.append(t)
-        t += rng.exponential(1.0 / a.serve_rate)
-    sizes = ensemble_sizes(len(arrivals), 1e3, 1e6, 600 + rank)
-    ps = rng.choice([3, 4, 6], size=len(arrivals))
+    from paper_2310_20374_gb300 import diskgen, serving
+    reqs = serving.poisson_requests(a.serve_rate, a.serve_seconds, 1e3, 1e6, (3, 4, 6), 100, seed=500 + rank)
     # inputs are generated before the clock starts (they stand in for requests already in host memory)
-    disks = [diskgen.make_disk(int(n), 700 + k) for k, n in enumerate(sizes)]
+    for k, r in enumerate(reqs):
+        r.disk = diskgen.make_disk(r.n, 700 + 1000 * rank + k)
     stream = torch.cuda.current_stream()
     free_b, _ = torch.cuda.mem_get_info()
     b = ncorp.ncorp_batch_create(cfg, int(0.8 * free_b), stream.cuda_stream)   # admission: 80% of free HBM
-    active = {}           # disk id -> [request index, steps left]
-    lat, wait, work, nxt = [], [], 0, 0
-    start = time.perf_counter()
-    while nxt < len(arrivals) or active:
-        now = time.perf_counter() - start
-        while nxt < len(arrivals) and arrivals[nxt] <= now:
-            d = disks[nxt]
-            try:
-                did = ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], int(sizes[nxt]),
-                                                 int(ps[nxt]), a.theta, a.dt)
-            except ncorp.NcorpError as e:
-                if e.code != ncorp.NCORP_ENOMEM or not active:
-                    raise
-                break     # memory budget full: the request waits for a disk to leave
-            wait.append(time.perf_counter() - start - arrivals[nxt])
-            active[did] = [nxt, 100]
-            nxt += 1
-        if not active:
-            time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
-            continue
-        t0 = time.perf_counter()
-        ncorp.ncorp_batch_run(b, 1)
-        dt_tick = time.perf_counter() - t0
-        for did, v in list(active.items()):
-            lat.append(dt_tick)
-            work += int(sizes[v[0]])
-            v[1] -= 1
-            if v[1] == 0:
-                ncorp.ncorp_batch_remove_disk(b, did)
-                del active[did]
-    wall = time.perf_counter() - start
-    ncorp.ncorp_batch_free(b)
-    lat_ms = np.array(lat) * 1e3
-    out = {"metric": METRIC, "value": round(work / wall, 1), "unit": UNIT, "n_gpus": world,
+    sampler = ClockSampler(physical_gpu_index(local))
+    try:
+        # each finished disk's state goes back to host memory (what a client receives)
+        st = serving.serve(serving.BatchBackend(ncorp, b, a.theta, a.dt), reqs, tick_steps=a.tick_steps,
+                           on_done=lambda r: (np.empty((r.n, 3)), np.empty((r.n, 3))))
+    finally:
+        clocks = sampler.stop()
+        ncorp.ncorp_batch_free(b)
+    offered = sum(r.n for r in reqs) * 100 / a.serve_seconds
+    value = slowest_rank(dist, st["throughput"], world) if world > 1 else st["throughput"]
+    out = {"metric": METRIC, "value": round(value * (world if world > 1 else 1), 1), "unit": UNIT, "n_gpus": world,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
            "data": "synthetic (seeded moonlet disks shaped like the paper's)",
            "config": {"workload": f"serving: Poisson arrivals at {a.serve_rate}/s for {a.serve_seconds} s "
-                                  f"({len(arrivals)} disks), N log-uniform in [1e3, 1e6], p in {{3,4,6}}, "
-                                  f"theta_min={a.theta}, 100 SBAB1 steps each, dt={a.dt}, {a.precision} precision",
-                      "requests": len(arrivals), "moonlet_steps": work},
-           "p50_step_ms": round(float(np.percentile(lat_ms, 50)), 3),
-           "p99_step_ms": round(float(np.percentile(lat_ms, 99)), 3),
-           "admission_wait_ms_p50": round(float(np.percentile(np.array(wait) * 1e3, 50)), 3),
-           "admission_wait_ms_p99": round(float(np.percentile(np.array(wait) * 1e3, 99)), 3),
-           "wall_s": round(wall, 2), "offered_moonlet_steps_per_s": round(float(sizes.sum()) * 100 / a.serve_seconds, 1)}
+                                  f"({len(reqs)} disks), N log-uniform in [1e3, 1e6], p in {{3,4,6}}, "
+                                  f"theta_min={a.theta}, 100 SBAB1 steps each, dt={a.dt}, {a.precision} precision, "
+                                  f"up to {a.tick_steps} steps per tick",
+                      "requests": st["requests"], "served": st["served"], "moonlet_steps": st["moonlet_steps"],
+                      "parallelism": "replicas (one serving loop per GPU)"},
+           "latency": {
+               "step_ms_p50": st["step_ms_p50"], "step_ms_p99": st["step_ms_p99"],
+               "tick_ms_p50": st["tick_ms_p50"], "tick_ms_p99": st["tick_ms_p99"],
+               "request_s_p50": st["request_s_p50"], "request_s_p99": st["request_s_p99"],
+               "admission_wait_s_p50": st["admission_wait_s_p50"], "admission_wait_s_p99": st["admission_wait_s_p99"],
+               "note": "host wall times: step = one tick (one ncorp_batch_run of k steps over every resident disk) "
+                       "/ k, one sample per disk and step; request = arrival to last step, admission wait included"},
+           "concurrent_disks_mean": round(st["concurrent_disks_mean"], 2),
+           "concurrent_disks_max": st["concurrent_disks_max"],
+           "busy_throughput": round(st["busy_throughput"], 1),
+           "wall_s": round(st["wall_s"], 2), "offered_moonlet_steps_per_s": round(offered, 1),
+           "clocks": clocks,
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                   "note": "the serving throughput is end to end: host arrays in, each disk's state back to host "
+                           "memory when it finishes"}}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
