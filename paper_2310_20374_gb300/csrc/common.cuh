@@ -82,7 +82,8 @@ enum : int {
     ERR_NONFINITE = 256,  // a position was NaN or infinite
 };
 
-constexpr int ERR_ABORT_MASK = ERR_CELLS | ERR_FRONTIER | ERR_M2L | ERR_P2P | ERR_TIMEOUT | ERR_DIRECTED | ERR_LEVEL;
+constexpr int ERR_ABORT_MASK =
+    ERR_CELLS | ERR_FRONTIER | ERR_M2L | ERR_P2P | ERR_TIMEOUT | ERR_DIRECTED | ERR_LEVEL | ERR_NONFINITE;
 
 // Device control block: counters written by kernels, read back by the host.
 struct Ctrl {

@@ -193,6 +193,9 @@ struct ncorp_ctx {
     // list/pair capacities capped until they first overflow, and the ncorp_step call (1-based) whose
     // grid barriers wait for an arrival that never comes (each gives up after the wait limit)
     int test_list_cap = 0, test_pair_cap = 0;
+    // capacities an overflow has shown to be needed, applied to both tree sets (so that a tree set grown
+    // after an overflow does not leave the other one to overflow on the next step)
+    int floor_cells = 0, floor_front = 0, floor_m2l = 0, floor_p2p = 0, floor_self = 0;
     long long stall_call = 0, step_calls = 0;
     cudaEvent_t ev[NCORP_NSTAGES][8][2] = {};   // up to 8 intervals per stage per call
     int ev_used[NCORP_NSTAGES] = {0};

@@ -42,6 +42,7 @@ __global__ void k_scatter_aos(const double *__restrict__ x, const double *__rest
 __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
     __shared__ unsigned long long s_b[6][8];
     __shared__ int s_bad;
+    if (aborted(A.ctl)) return;   // the run aborted in an earlier step: nothing is computed from it
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
     if (A.ctl->disk_of) {   // a forest: the same step, every disk's own box

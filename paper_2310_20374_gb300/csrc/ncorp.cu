@@ -195,21 +195,23 @@ void choose_parameters(ncorp_ctx *c, int p) {
 }
 
 void ensure_tree_capacity(ncorp_ctx *c, int n) {
-    int want = std::max(4096, 4 * (n / std::max(1, c->s)) + 1024);
+    int want = std::max({4096, 4 * (n / std::max(1, c->s)) + 1024, c->floor_cells});
     if (c->cells.cap < want) alloc_cells(c, want);
     if (c->cells.leaf_of_cap < n) {
         dalloc(c->cells.leaf_of, static_cast<size_t>(n));
         c->cells.leaf_of_cap = n;
     }
     const int cc = c->cells.cap;
-    int front = std::max(1 << 16, 48 * cc), m2l = std::max(1 << 16, 64 * cc), p2p = std::max(1 << 16, 48 * cc);
+    int front = std::max({1 << 16, 48 * cc, c->floor_front}), m2l = std::max({1 << 16, 64 * cc, c->floor_m2l}),
+        p2p = std::max({1 << 16, 48 * cc, c->floor_p2p});
     if (c->test_list_cap > 0) {   // failure-path tests: lists too small until they first overflow
         m2l = std::min(m2l, c->test_list_cap);
         p2p = std::min(p2p, c->test_list_cap);
     }
-    if (c->wl.front_cap < front || c->wl.m2l_cap < m2l || c->wl.p2p_cap < p2p || c->wl.self_cap < cc)
+    const int self = std::max(cc, c->floor_self);
+    if (c->wl.front_cap < front || c->wl.m2l_cap < m2l || c->wl.p2p_cap < p2p || c->wl.self_cap < self)
         alloc_lists(c, std::max(front, c->wl.front_cap), std::max(m2l, c->wl.m2l_cap), std::max(p2p, c->wl.p2p_cap),
-                    std::max(cc, c->wl.self_cap));
+                    std::max(self, c->wl.self_cap));
     int pc = std::max(1 << 16, 4 * n);
     if (c->test_pair_cap > 0) pc = std::min(pc, c->test_pair_cap);
     if (c->pair_cap < pc) alloc_pairs(c, pc);
@@ -251,6 +253,7 @@ bool grow_after(ncorp_ctx *c, int err) {
     bool grew = false;
     if (err & ERR_CELLS) {
         alloc_cells(c, std::max(2 * c->cells.cap, c->ctl_h->n_cells + 1024));
+        c->floor_cells = std::max(c->floor_cells, c->cells.cap);
         grew = true;
     }
     WalkLists &W = c->wl;
@@ -265,6 +268,10 @@ bool grow_after(ncorp_ctx *c, int err) {
     if (grew) {
         alloc_lists(c, front, m2l, p2p, self);
         c->test_list_cap = 0;
+        c->floor_front = std::max(c->floor_front, front);
+        c->floor_m2l = std::max(c->floor_m2l, m2l);
+        c->floor_p2p = std::max(c->floor_p2p, p2p);
+        c->floor_self = std::max(c->floor_self, self);
     }
     if (err & ERR_PAIRS) {
         c->test_pair_cap = 0;
@@ -339,7 +346,15 @@ ExtForce external(ncorp_ctx *c, double t) {
 // and clear (optional) is zeroed: one launch resets both tree sets and the
 // accumulator at the start of a step.
 __device__ void reset_one(Ctrl *ctl, int *fold) {
-    if (fold) *fold |= ctl->err;
+    if (fold) {
+        *fold |= ctl->err;
+        // a run of steps that aborted stays aborted: the set is not reused, so that no later step of the
+        // run computes from the results the aborted step never wrote (the run is redone by the host)
+        if (*fold & ERR_ABORT_MASK) {
+            ctl->err = *fold & ERR_ABORT_MASK;
+            return;
+        }
+    }
     ctl->err = 0;
     ctl->n_found = 0;
     ctl->n_resolved = 0;
@@ -1568,6 +1583,7 @@ struct ncorp_batch {
     double bytes_per_moonlet = BATCH_DEFAULT_BYTES_PER_MOONLET;   // the largest measured so far
     bool measured = false;
     int *flag = nullptr;   // device word of the input check
+    bool validate = false; // NCORP_VALIDATE set: check the resident state around every forest step
     cudaStream_t pool[BATCH_STREAMS] = {};
     cudaEvent_t ev_start = nullptr, ev_done[BATCH_STREAMS] = {};
     std::vector<Forest *> forests;
@@ -1842,6 +1858,118 @@ void enqueue_run(Forest &f, int k) {
     slot.launches = c->launches - launches0;
 }
 
+// ---- validation mode: invariants of a forest's resident state, checked by
+// kernels that only read inside the bounds they check (a violated invariant
+// is recorded, never followed).  bad[0] = first violated invariant, bad[1] =
+// its index, bad[2] = the offending value, bad[3] = violations.
+struct ValidateArgs {
+    const int *perm;
+    int n;
+    const unsigned short *disk_of;
+    const int *doff;
+    int nd;
+    const int *first, *count, *nchild, *child0, *parent, *leaves, *leaf_of;
+    int cap;
+    const Ctrl *ctl;
+    int *hist;   // [n], zero on entry
+    int *bad;    // [4], zero on entry
+};
+
+__device__ void report(int *bad, int code, int idx, int val) {
+    if (atomicCAS(&bad[0], 0, code) == 0) {
+        bad[1] = idx;
+        bad[2] = val;
+    }
+    atomicAdd(&bad[3], 1);
+}
+
+__global__ void k_validate(ValidateArgs V) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int nc = V.ctl->n_cells, nl = V.ctl->n_leaves, roots = V.ctl->nd;
+    if (tid == 0) {
+        if (nc < 1 || nc > V.cap) report(V.bad, 3, nc, V.cap);
+        if (nl < 1 || nl > nc) report(V.bad, 7, nl, nc);
+        if (roots != V.nd) report(V.bad, 11, roots, V.nd);
+    }
+    for (int i = tid; i < V.n; i += nt) {
+        const int u = V.perm[i];
+        if (u < 0 || u >= V.n) report(V.bad, 1, i, u);
+        else atomicAdd(&V.hist[u], 1);
+        if (V.disk_of) {
+            const int d = V.disk_of[i];
+            if (d >= V.nd || V.doff[d] > i || V.doff[d + 1] <= i) report(V.bad, 2, i, d);
+        }
+    }
+    const int ncv = min(max(nc, 0), V.cap);
+    for (int c = tid; c < ncv; c += nt) {
+        const int f = V.first[c], k = V.count[c];
+        if (f < 0 || k < 1 || f > V.n - k) report(V.bad, 4, c, f);
+        const int ch = V.nchild[c];
+        if (ch < 0 || ch > 8) report(V.bad, 12, c, ch);
+        else if (ch > 0) {
+            const int c0 = V.child0[c];
+            if (c0 <= c || c0 > ncv - ch) report(V.bad, 5, c, c0);
+        }
+        const int pa = V.parent[c];
+        if (c < V.nd ? pa != -1 : (pa < 0 || pa >= c)) report(V.bad, 6, c, pa);
+    }
+    const int nlv = min(max(nl, 0), ncv);
+    for (int t = tid; t < nlv; t += nt) {
+        const int l = V.leaves[t];
+        if (l < 0 || l >= ncv || V.nchild[l] != 0) report(V.bad, 8, t, l);
+    }
+    for (int i = tid; i < V.n; i += nt) {
+        const int l = V.leaf_of[i];
+        if (l < 0 || l >= ncv || V.first[l] > i || i - V.first[l] >= V.count[l]) report(V.bad, 9, i, l);
+    }
+}
+
+__global__ void k_validate_perm(ValidateArgs V) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < V.n; u += gridDim.x * blockDim.x)
+        if (V.hist[u] != 1) report(V.bad, 10, u, V.hist[u]);
+}
+
+// NCORP_OK, or NCORP_ESTATE with the first violated invariant in the batch's message.
+int validate_forest(ncorp_batch *b, Forest &f, const char *when) {
+    ncorp_ctx *c = f.c;
+    const int n = static_cast<int>(f.n);
+    if (c->n != n || c->n_cap < n || c->nd != static_cast<int>(f.disks.size()))
+        return batch_fail(b, NCORP_ESTATE, "validation %s: host state n %d / %lld, cap %lld, disks %d / %zu", when,
+                          c->n, (long long)f.n, (long long)c->n_cap, c->nd, f.disks.size());
+    int *scratch = nullptr;
+    int hbad[4] = {0, 0, 0, 0};
+    NCORP_CUDA_CHECK(cudaMalloc(reinterpret_cast<void **>(&scratch), sizeof(int) * (n + 4)));
+    try {
+        NCORP_CUDA_CHECK(cudaMemsetAsync(scratch, 0, sizeof(int) * (n + 4), c->stream));
+        ValidateArgs V;
+        V.perm = c->A.perm;
+        V.n = n;
+        V.disk_of = c->nd > 1 ? c->disk_of : nullptr;
+        V.doff = c->doff;
+        V.nd = c->nd;
+        const Cells &C = c->cells;
+        V.first = C.first; V.count = C.count; V.nchild = C.nchild; V.child0 = C.child0; V.parent = C.parent;
+        V.leaves = C.leaves; V.leaf_of = C.leaf_of; V.cap = C.cap;
+        V.ctl = c->ctl;
+        V.hist = scratch;
+        V.bad = scratch + n;
+        k_validate<<<4 * b->num_sms, 256, 0, c->stream>>>(V);
+        k_validate_perm<<<4 * b->num_sms, 256, 0, c->stream>>>(V);
+        NCORP_CUDA_CHECK(cudaGetLastError());
+        NCORP_CUDA_CHECK(cudaMemcpyAsync(hbad, scratch + n, sizeof(hbad), cudaMemcpyDeviceToHost, c->stream));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+        cudaFree(scratch);
+        throw;
+    }
+    cudaFree(scratch);
+    if (hbad[0])
+        return batch_fail(b, NCORP_ESTATE, "validation %s (forest p = %d, %zu disks, n = %d): invariant %d at %d "
+                          "(value %d), %d violations", when, f.p, f.disks.size(), n, hbad[0], hbad[1], hbad[2],
+                          hbad[3]);
+    return NCORP_OK;
+}
+
 __global__ void k_count_nonfinite(const double *__restrict__ a, int64_t n, int *bad) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -1865,6 +1993,7 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
     b->cfg = *cfg;
     b->budget = hbm_budget_bytes;
     b->user = static_cast<cudaStream_t>(cuda_stream);
+    b->validate = env_int("NCORP_VALIDATE", 0, 0, 1) != 0;
     int least = 0, greatest = 0;
     bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
@@ -1979,11 +2108,46 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
         // forests whose disks changed: new layout, tree and acceleration
         for (Forest *f : b->forests)
             if (!f->primed) {
-                const int st = prime_forest(b, *f);
+                int st = prime_forest(b, *f);
                 if (st != NCORP_OK) return st;
                 b->launches += f->c->launches;
+                if (b->validate && (st = validate_forest(b, *f, "after the layout")) != NCORP_OK) return st;
             }
         if (n_steps == 0) return NCORP_OK;
+        if (b->validate) {   // one forest and one step at a time, the resident state checked around each
+            for (int k = 0; k < n_steps; k++)
+                for (Forest *f : b->forests) {
+                    ncorp_ctx *c = f->c;
+                    c->stream = b->pool[f->stream];
+                    c->coop_max = coop_cap(b);
+                    int st = validate_forest(b, *f, "before a step");
+                    if (st != NCORP_OK) return st;
+                    begin_call(c);
+                    choose_parameters(c, f->p);
+                    run_body(*f, 1);
+                    const int err = finish(c, true);
+                    f->synced = false;
+                    f->pairs_valid = false;
+                    b->launches += c->launches;
+                    if (err != 0) {   // the step again from its snapshot, buffers growing, as after a run
+                        b->fallbacks++;
+                        c->have_state = false;
+                        c->tree_valid = false;
+                        st = ncorp_step(c, f->pos, f->vel, f->m, f->R, f->n, f->p, f->theta, f->dt);
+                        if (st != NCORP_OK) return batch_fail(b, st, "validation step: %s", ncorp_last_error(c));
+                        f->synced = true;
+                        f->n_found = c->n_found;
+                    } else {
+                        c->n_found = c->cfg.collisions ? c->alt.ctl_h->n_found : 0;
+                        c->pairs_sorted = false;
+                        c->time += f->dt;
+                        f->n_found = c->n_found;
+                    }
+                    st = validate_forest(b, *f, "after a step");
+                    if (st != NCORP_OK) return st;
+                }
+            return NCORP_OK;
+        }
         NCORP_CUDA_CHECK(cudaEventRecord(b->ev_start, b->user));
         for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamWaitEvent(b->pool[s], b->ev_start, 0));
         const int cap = coop_cap(b);

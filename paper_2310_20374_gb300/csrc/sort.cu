@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_bbox(const double *__restrict__ x, cons
                                               const int *gate = nullptr) {
     __shared__ unsigned long long s_b[6][8];
     __shared__ int s_bad;
-    if (gate && *gate == 0) return;
+    if ((gate && *gate == 0) || aborted(ctl)) return;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     bool bad = false;
     if (ctl->disk_of) {   // a forest: every disk's own box
@@ -188,7 +188,7 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
                        const int *gate = nullptr) {
     __shared__ double s_root[4];
     __shared__ int s_shift;
-    if (gate && *gate == 0) return;
+    if ((gate && *gate == 0) || aborted(ctl)) return;
     if (ctl->disk_of) {   // a forest: each moonlet in its disk's root cube (k_disk_roots made them)
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bar_count = 0;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -508,7 +508,8 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
 }
 
 __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
-    if (A.gate && *A.gate == 0) return;   // every block returns before the first barrier
+    // every block returns before the first barrier (an aborted step's keys are never used)
+    if ((A.gate && *A.gate == 0) || aborted(A.ctl)) return;
     unsigned bar = 0;
     radix_body(A, bar);
 }
@@ -644,6 +645,7 @@ __device__ __forceinline__ bool is_mover(const uint64_t *k, int i, int n) {
 __global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
     extern __shared__ unsigned long long rz_smem[];
     __shared__ int s_warp[33];
+    if (aborted(A.ctl)) return;   // every block, before the first barrier
     const int n = A.n, G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
     const int chunk = (n + G - 1) / G, c0 = min(n, b * chunk), c1 = min(n, c0 + chunk);
     unsigned bar = 0;
@@ -826,13 +828,14 @@ struct GatherArgs {
     const uint32_t *idx;
     const uint64_t *key;   // sorted keys
     const unsigned short *disk_of;   // a forest: disk of each position (equal keys of two disks are no run)
+    const Ctrl *ctl;       // the tree set being built (an aborted step gathers nothing)
     double G;
     int n;
     const int *gate;       // nothing to do while *gate is 0 (null: always)
 };
 
 __global__ void k_gather(GatherArgs g) {
-    if (g.gate && *g.gate == 0) return;
+    if ((g.gate && *g.gate == 0) || aborted(g.ctl)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
         const int j = static_cast<int>(g.idx[i]);
         int d = i;
@@ -885,6 +888,7 @@ void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &s
     g.idx = idx;
     g.key = dst.key;
     g.disk_of = c->nd > 1 ? c->disk_of : nullptr;
+    g.ctl = c->ctl;
     g.G = G;
     g.n = n;
     k_gather<<<grid_for(n, 256, 16 * c->num_sms), 256, 0, c->stream>>>(g); c->launches++;

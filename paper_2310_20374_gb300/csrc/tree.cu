@@ -72,7 +72,7 @@ struct BuildArgs {
 
 // The roots: one per disk (cell d holds disk d's moonlets; one disk: cell 0 holds all).
 __global__ void k_build_init(BuildArgs A) {
-    if (A.gate && *A.gate == 0) return;
+    if ((A.gate && *A.gate == 0) || aborted(A.ctl)) return;
     const int nd = A.ctl->nd;
     for (int d = 0; d < nd; d++) {
         A.level[d] = 0;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) k_build(BuildArgs A) {
     volatile Ctrl *vc = A.ctl;
     const int G = gridDim.x;
     unsigned bar = 0;
-    if (A.gate && *A.gate == 0) return;   // every block returns before the first barrier
+    if ((A.gate && *A.gate == 0) || aborted(A.ctl)) return;   // every block, before the first barrier
     {   // block 0 makes the roots' children counts
         const int t = made_cells(A, 0, blockIdx.x == 0 ? vc->level_start[1] : 0, 0, s_red);
         if (threadIdx.x == 0) A.blocksum[blockIdx.x] = t;

@@ -55,6 +55,7 @@ constexpr int FORCED = static_cast<int>(0x80000000u);
 // One thread: the root pairs, zeroed frontier counts and counters, and (for
 // gravity) the work counter of the near-field kernel that reads the lists.
 __global__ void k_walk_init(WalkArgs A) {
+    if (aborted(A.ctl)) return;
     const int nd = A.ctl->nd;   // one root pair per disk (a forest's disks never interact)
     for (int d = 0; d < nd; d++) A.front0[d] = make_int2(d, d);
     for (int i = 1; i <= WALK_MAX_ITERS; i++) A.fcount[i] = 0;
