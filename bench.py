@@ -616,7 +616,9 @@ def time_ensemble(a, ncorp, torch, dist, world, rank, stream, steps, warmup):
                                    f"falcON p={p} theta_min={theta}, {steps} SBAB1 steps dt={dt} with collision "
                                    f"search, mixed precision, one ncorp_batch_run (one forest: one launch per "
                                    f"stage over all disks, the run replayed from one CUDA graph)",
-                       "moonlets_per_gpu": total, "disks_per_gpu": 64, "leaf_size": leaf_size_for(p),
+                       "moonlets_per_gpu": total, "disks_per_gpu": 64, "leaf_size": info["leaf_size"],
+                       "leaf_size_chosen_by": "the batch's autotuner (timed candidates around the default "
+                                              f"{leaf_size_for(p)} for p = {p})" if info["tuned"] else "default",
                        "gravity_thresholds": list(thresholds_for(p)),
                        "l2": "inputs larger than L2 (about 1 kB of state and tree per moonlet)",
                        "parallelism": "replicas (one batch of 64 disks per GPU)"},
@@ -662,7 +664,8 @@ def run_serving(a):
     sampler = ClockSampler(physical_gpu_index(local))
     try:
         # each finished disk's state goes back to host memory (what a client receives)
-        st = serving.serve(serving.BatchBackend(ncorp, b, a.theta, a.dt), reqs, tick_steps=a.tick_steps,
+        backend = serving.BatchBackend(ncorp, b, a.theta, a.dt)
+        st = serving.serve(backend, reqs, tick_steps=a.tick_steps,
                            on_done=lambda r: (np.empty((r.n, 3)), np.empty((r.n, 3))))
     finally:
         clocks = sampler.stop()
@@ -686,6 +689,9 @@ def run_serving(a):
                "admission_wait_s_p50": st["admission_wait_s_p50"], "admission_wait_s_p99": st["admission_wait_s_p99"],
                "note": "host wall times: step = one tick (one ncorp_batch_run of k steps over every resident disk) "
                        "/ k, one sample per disk and step; request = arrival to last step, admission wait included"},
+           "peak_batch_bytes": getattr(backend, "peak_bytes", None),
+           "peak_resident_moonlets": getattr(backend, "peak_moonlets", None),
+           "hbm_budget_bytes": int(0.8 * free_b),
            "concurrent_disks_mean": round(st["concurrent_disks_mean"], 2),
            "concurrent_disks_max": st["concurrent_disks_max"],
            "busy_throughput": round(st["busy_throughput"], 1),

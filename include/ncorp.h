@@ -334,7 +334,17 @@ const char *ncorp_last_error(const ncorp_ctx *ctx);
  * in a context of its own (the same SBAB1 step of Sect. 4.1 with the falcON
  * forces and the collision search of Sect. 3.1), up to the rounding order of
  * sums.  A batch is not thread-safe: call it from one host thread at a time.
- * Batches take no distant star (its position depends on each disk's time). */
+ * Batches take no distant star (its position depends on each disk's time).
+ * With leaf_size = 0 in the configuration, an autotuner chooses each large
+ * forest's leaf size s: at the forest's first run (and when its size has
+ * changed more than fourfold) it lays the forest out with each of a few
+ * candidates around the default for p and times two steps from the same
+ * state, keeping the fastest (NCORP_BATCH_TUNED, NCORP_BATCH_LEAF).
+ * Environment variables read by ncorp_batch_create: NCORP_AUTOTUNE=0 turns
+ * the tuner off; NCORP_VALIDATE=1 runs every forest one step at a time and
+ * checks the invariants of its resident state (permutation, disk map, cell
+ * ranges, leaf map) around each step, failing with NCORP_ESTATE on the first
+ * violation (a diagnostic mode, slow). */
 typedef struct ncorp_batch ncorp_batch;
 
 /* Creates an empty batch on the current CUDA device; every disk uses cfg
@@ -393,7 +403,9 @@ int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, 
 #define NCORP_BATCH_FORESTS    3   /* forests: groups of disks with the same (p, theta, dt) */
 #define NCORP_BATCH_FALLBACKS  4   /* forest reruns after a buffer overflow, since creation */
 #define NCORP_BATCH_LAUNCHES   5   /* kernels launched by the last run */
-#define NCORP_BATCH_NINFO      6
+#define NCORP_BATCH_TUNED      6   /* forests whose leaf size the autotuner chose, since creation */
+#define NCORP_BATCH_LEAF       7   /* leaf size s of the batch's largest forest */
+#define NCORP_BATCH_NINFO      8
 
 /* Writes min(n_info, NCORP_BATCH_NINFO) batch counters to host memory info[]. */
 int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info);

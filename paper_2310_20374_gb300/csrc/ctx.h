@@ -118,6 +118,7 @@ struct ncorp_ctx {
     // a forest (nd > 1): independent disks in the same arrays, disk d = moonlets [doff[d], doff[d + 1])
     int nd = 1;
     int forest_n = 0;                    // moonlets of all disks (nd > 1)
+    int disk_of_cap = 0, nd_cap = 0;     // room in disk_of / doff, fbox, froot (kept across layouts)
     unsigned short *disk_of = nullptr;   // device [forest_n]
     int *doff = nullptr;                 // device [nd + 1]
     unsigned long long *fbox[2] = {nullptr, nullptr};   // device [nd][6] per tree set
@@ -126,6 +127,7 @@ struct ncorp_ctx {
     int p = 0;
     double theta = 0.5;
     int s = 0;
+    int s_tuned = 0;                // leaf size chosen by a batch's autotuner (0: none)
     long long g_cs = 0, g_pre = 0, g_post = 0;
     long long c_cs = 12, c_pre = 0, c_post = 16;
 

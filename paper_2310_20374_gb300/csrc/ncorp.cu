@@ -77,9 +77,15 @@ void free_set(ParticleSet &S) {
     dfree(S.hi4); dfree(S.lo4);
 }
 
+// Every allocator below records a capacity only after all its buffers exist:
+// an allocation that fails leaves the capacity at 0, so the next call
+// allocates again instead of using a buffer that is missing or too small.
 void ensure_particles(ncorp_ctx *c, int64_t n) {
     if (n <= c->n_cap) return;
     int64_t cap = std::max<int64_t>(n, c->n_cap * 3 / 2);
+    c->n_cap = 0;
+    c->have_state = false;
+    c->tree_valid = false;
     alloc_set(c->A, cap);
     alloc_set(c->B, cap);
     alloc_set(c->Cset, cap);
@@ -106,6 +112,8 @@ void ensure_particles(ncorp_ctx *c, int64_t n) {
 
 void alloc_cells(ncorp_ctx *c, int cap) {
     Cells &C = c->cells;
+    C.cap = 0;
+    c->tree_valid = false;
     dalloc(C.level, cap); dalloc(C.first, cap); dalloc(C.count, cap); dalloc(C.child0, cap);
     dalloc(C.nchild, cap); dalloc(C.parent, cap); dalloc(C.arrive, cap); dalloc(C.arrive_m, cap);
     dalloc(C.cx, cap); dalloc(C.cy, cap); dalloc(C.cz, cap);
@@ -141,18 +149,24 @@ void alloc_cells(ncorp_ctx *c, int cap) {
 void alloc_lists(ncorp_ctx *c, int front, int m2l, int p2p, int self) {
     WalkLists &W = c->wl;
     if (front != W.front_cap) {
+        W.front_cap = 0;
         dalloc(W.front[0], front);
         dalloc(W.front[1], front);
         W.front_cap = front;
     }
     if (!W.front_count) dalloc(W.front_count, WALK_MAX_ITERS + 2);
     if (m2l != W.m2l_cap) {
+        W.m2l_cap = 0;
+        W.m2l_dir_cap = 0;
         dalloc(W.m2l, m2l);
         dalloc(W.m2l_dir, 2 * static_cast<size_t>(m2l));
         W.m2l_cap = m2l;
         W.m2l_dir_cap = 2 * m2l;
     }
     if (p2p != W.p2p_cap || self != W.self_cap) {
+        W.p2p_cap = 0;
+        W.self_cap = 0;
+        W.p2p_dir_cap = 0;
         dalloc(W.p2p, p2p);
         dalloc(W.self, self);
         dalloc(W.p2p_src, 2 * static_cast<size_t>(p2p) + self);   // int2
@@ -163,6 +177,7 @@ void alloc_lists(ncorp_ctx *c, int front, int m2l, int p2p, int self) {
 }
 
 void alloc_pairs(ncorp_ctx *c, int cap) {
+    c->pair_cap = 0;
     dalloc(c->pairs, cap);
     dalloc(c->pairs_alt, cap);
     dalloc(c->pair_idx, cap);
@@ -179,7 +194,7 @@ void alloc_pairs(ncorp_ctx *c, int cap) {
 // leaf size and thresholds for expansion order p (config values win when set)
 void choose_parameters(ncorp_ctx *c, int p) {
     const ncorp_config &g = c->cfg;
-    c->s = g.leaf_size > 0 ? g.leaf_size : (p <= 3 ? 32 : (p <= 5 ? 48 : 64));
+    c->s = g.leaf_size > 0 ? g.leaf_size : (c->s_tuned > 0 ? c->s_tuned : (p <= 3 ? 32 : (p <= 5 ? 48 : 64)));
     if (g.n_cs || g.n_cc_pre || g.n_cc_post) {
         c->g_cs = g.n_cs; c->g_pre = g.n_cc_pre; c->g_post = g.n_cc_post;
     } else if (p >= 6) {
@@ -198,6 +213,7 @@ void ensure_tree_capacity(ncorp_ctx *c, int n) {
     int want = std::max({4096, 4 * (n / std::max(1, c->s)) + 1024, c->floor_cells});
     if (c->cells.cap < want) alloc_cells(c, want);
     if (c->cells.leaf_of_cap < n) {
+        c->cells.leaf_of_cap = 0;
         dalloc(c->cells.leaf_of, static_cast<size_t>(n));
         c->cells.leaf_of_cap = n;
     }
@@ -421,21 +437,24 @@ void configure_disks(ncorp_ctx *c, int nd, const int64_t *sizes) {
     const int n = off[nd];
     NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
     for (StepGraph &g : c->graphs) drop_graph(g);
-    if (nd == 1) {
-        dfree(c->disk_of);
-        dfree(c->doff);
-        for (int s = 0; s < 2; s++) {
-            dfree(c->fbox[s]);
-            dfree(c->froot[s]);
-        }
+    if (nd == 1) {   // (the layout buffers are kept for the next forest layout)
         k_set_disks<<<1, 1, 0, c->stream>>>(c->ctl, 1, nullptr, nullptr, nullptr, nullptr);
         k_set_disks<<<1, 1, 0, c->stream>>>(c->alt.ctl, 1, nullptr, nullptr, nullptr, nullptr);
     } else {
-        dalloc(c->disk_of, n);
-        dalloc(c->doff, nd + 1);
-        for (int s = 0; s < 2; s++) {
-            dalloc(c->fbox[s], 6 * static_cast<size_t>(nd));
-            dalloc(c->froot[s], 4 * static_cast<size_t>(nd));
+        // grown, never shrunk: a re-layout of a batch's forest allocates nothing in the common case
+        if (c->disk_of_cap < n) {
+            c->disk_of_cap = 0;
+            dalloc(c->disk_of, n);
+            c->disk_of_cap = n;
+        }
+        if (c->nd_cap < nd) {
+            c->nd_cap = 0;
+            dalloc(c->doff, NCORP_MAX_DISKS + 1);
+            for (int s = 0; s < 2; s++) {
+                dalloc(c->fbox[s], 6 * static_cast<size_t>(NCORP_MAX_DISKS));
+                dalloc(c->froot[s], 4 * static_cast<size_t>(NCORP_MAX_DISKS));
+            }
+            c->nd_cap = NCORP_MAX_DISKS;
         }
         NCORP_CUDA_CHECK(cudaMemcpyAsync(c->doff, off.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice, c->stream));
         k_fill_disk_of<<<grid_for(n, 256, 4 * c->num_sms), 256, 0, c->stream>>>(c->doff, nd, c->disk_of, n);
@@ -1570,6 +1589,7 @@ struct Forest {
     std::vector<int64_t> pairs;   // the last step's pairs of all disks, host copy
     bool pairs_valid = false;
     int64_t n_found = 0;
+    int64_t tuned_n = 0;          // moonlets the leaf size was tuned for (0: not tuned)
 };
 
 }  // namespace
@@ -1584,6 +1604,7 @@ struct ncorp_batch {
     bool measured = false;
     int *flag = nullptr;   // device word of the input check
     bool validate = false; // NCORP_VALIDATE set: check the resident state around every forest step
+    bool autotune = true;  // NCORP_AUTOTUNE=0 turns the leaf-size tuner off
     cudaStream_t pool[BATCH_STREAMS] = {};
     cudaEvent_t ev_start = nullptr, ev_done[BATCH_STREAMS] = {};
     std::vector<Forest *> forests;
@@ -1591,6 +1612,7 @@ struct ncorp_batch {
     int32_t next_id = 0;
     int64_t fallbacks = 0;
     int64_t launches = 0;
+    int64_t tuned = 0;
     char err[512] = {0};
 };
 
@@ -1687,12 +1709,14 @@ int coop_cap(const ncorp_batch *b) {
 
 // Lays the forest out for its current disks and computes their tree and
 // acceleration from the arrays (which must hold the state); creates the
-// context, or creates it anew when its buffers are more than twice the size
-// the forest needs.  Synchronous.
+// context, or creates it anew (returning the memory) when its buffers hold
+// more than four times the moonlets the forest has left, and over a million.
+// Synchronous.
 int prime_forest(ncorp_batch *b, Forest &f) {
     const int n = static_cast<int>(f.n);
     const size_t free0 = free_bytes();
-    if (f.c && f.c->n_cap > 2 * f.n && f.c->n_cap > (1 << 16)) {
+    const int s_tuned = f.c ? f.c->s_tuned : 0;   // (kept by a context created anew)
+    if (f.c && f.c->n_cap > 4 * f.n && f.c->n_cap > (1 << 20)) {
         drop_run_graphs(f);
         ncorp_free(f.c);
         f.c = nullptr;
@@ -1704,6 +1728,7 @@ int prime_forest(ncorp_batch *b, Forest &f) {
             f.c = nullptr;
             return batch_fail(b, st, "context for %lld moonlets: allocation failed", (long long)f.n);
         }
+        f.c->s_tuned = s_tuned;
     }
     ncorp_ctx *c = f.c;
     c->stream = b->pool[f.stream];
@@ -1756,9 +1781,16 @@ int prime_forest(ncorp_batch *b, Forest &f) {
         b->measured = true;
     }
     if (status != NCORP_OK) {
+        batch_fail(b, status, "%s", ncorp_last_error(c));
         c->have_state = false;
         c->tree_valid = false;
-        return batch_fail(b, status, "%s", ncorp_last_error(c));
+        if (status == NCORP_ENOMEM) {   // release what the context holds; the next layout starts afresh
+            drop_run_graphs(f);
+            ncorp_free(c);
+            f.c = nullptr;
+            f.ctx_bytes = 0;
+        }
+        return status;
     }
     c->n = n;
     c->have_state = true;
@@ -1856,6 +1888,61 @@ void enqueue_run(Forest &f, int k) {
     slot = want;
     slot.exec = exec;
     slot.launches = c->launches - launches0;
+}
+
+// ---- autotuner of the leaf size s (Sect. 3.4.1: cells with more than s
+// moonlets are split).  The best s depends on p, on the disks' sizes and on
+// how the work spreads over the SMs, so for a forest of TUNE_MIN_MOONLETS to
+// TUNE_MAX_MOONLETS moonlets (and again when its size has changed more than
+// fourfold) each candidate lays the forest out and times two steps from the
+// same state; the fastest is kept.  The candidates are around the default
+// for p (32, 48, 64 for p <= 3, <= 5, 6).  A configured leaf size disables
+// the tuner, as does NCORP_AUTOTUNE=0.
+constexpr int64_t TUNE_MIN_MOONLETS = 1 << 15, TUNE_MAX_MOONLETS = 1 << 22;
+
+bool needs_tuning(const ncorp_batch *b, const Forest &f) {
+    // (above TUNE_MAX_MOONLETS the trials' larger trees are not worth their memory)
+    if (!b->autotune || b->cfg.leaf_size > 0 || f.n < TUNE_MIN_MOONLETS || f.n > TUNE_MAX_MOONLETS) return false;
+    return f.tuned_n == 0 || f.n > 4 * f.tuned_n || 4 * f.n < f.tuned_n;
+}
+
+int tune_forest(ncorp_batch *b, Forest &f) {
+    const int base = f.p <= 3 ? 32 : (f.p <= 5 ? 48 : 64);
+    const int cand[4] = {base / 2, (3 * base) / 4, base, (3 * base) / 2};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NCORP_CUDA_CHECK(cudaEventCreate(&e0));
+    NCORP_CUDA_CHECK(cudaEventCreate(&e1));
+    float best_ms = 0.0f;
+    int best = base, st = NCORP_OK;
+    for (int s : cand) {
+        if (f.c) f.c->s_tuned = s;
+        f.primed = false;
+        if ((st = prime_forest(b, f)) != NCORP_OK) break;   // lays out from the arrays (the state to keep)
+        ncorp_ctx *c = f.c;
+        begin_call(c);
+        choose_parameters(c, f.p);
+        NCORP_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+        run_body(f, 2);   // its snapshot rewrites the arrays with the same state
+        NCORP_CUDA_CHECK(cudaEventRecord(e1, c->stream));
+        const int err = finish(c, true);
+        float ms = 0.0f;
+        NCORP_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (err == 0 && (best_ms == 0.0f || ms < best_ms)) {
+            best_ms = ms;
+            best = s;
+        }
+        f.synced = true;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NCORP_OK) return st;
+    f.c->s_tuned = best;
+    f.tuned_n = f.n;
+    b->tuned++;
+    // the capacities the trials needed are not the chosen leaf size's
+    f.c->floor_cells = f.c->floor_front = f.c->floor_m2l = f.c->floor_p2p = f.c->floor_self = 0;
+    f.primed = false;
+    return prime_forest(b, f);
 }
 
 // ---- validation mode: invariants of a forest's resident state, checked by
@@ -1994,6 +2081,7 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
     b->budget = hbm_budget_bytes;
     b->user = static_cast<cudaStream_t>(cuda_stream);
     b->validate = env_int("NCORP_VALIDATE", 0, 0, 1) != 0;
+    b->autotune = env_int("NCORP_AUTOTUNE", 1, 0, 1) != 0;
     int least = 0, greatest = 0;
     bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
@@ -2031,11 +2119,14 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
         return batch_fail(b, NCORP_EINVAL, "%d disks already share (p, theta, dt)", NCORP_MAX_DISKS);
     // admission by device memory: what the batch holds plus the new disk's share at the largest
     // footprint per moonlet measured so far
+    // (with a margin of one half: a forest's buffers grow in steps, and an overflow doubles a list)
     const size_t used = batch_used(b);
-    const size_t need = static_cast<size_t>(b->bytes_per_moonlet * static_cast<double>(n));
+    const size_t need = static_cast<size_t>(1.5 * b->bytes_per_moonlet * static_cast<double>(n));
     if (b->budget && used + need > b->budget)
         return batch_fail(b, NCORP_ENOMEM, "device-memory budget exceeded: %zu + %zu > %zu bytes", used, need,
                           b->budget);
+    if (b->budget && free_bytes() < need)
+        return batch_fail(b, NCORP_ENOMEM, "device-memory budget: %zu bytes free, %zu needed", free_bytes(), need);
     const bool fresh = f == nullptr;
     if (fresh) {
         f = new (std::nothrow) Forest();
@@ -2112,6 +2203,11 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
                 if (st != NCORP_OK) return st;
                 b->launches += f->c->launches;
                 if (b->validate && (st = validate_forest(b, *f, "after the layout")) != NCORP_OK) return st;
+            }
+        for (Forest *f : b->forests)
+            if (needs_tuning(b, *f)) {
+                const int st = tune_forest(b, *f);
+                if (st != NCORP_OK) return st;
             }
         if (n_steps == 0) return NCORP_OK;
         if (b->validate) {   // one forest and one step at a time, the resident state checked around each
@@ -2320,7 +2416,9 @@ int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, 
         if (tail > 0) {
             cudaStream_t s = b->pool[f->stream];
             double *tmp = nullptr;
-            balloc(tmp, 3 * tail);
+            const bool own = !f->c || f->c->n_cap < tail;   // the context's staging buffer: 3 n_cap doubles
+            if (own) balloc(tmp, 3 * tail);
+            else tmp = f->c->stage;
             double *src[4] = {f->pos + 3 * (d.off + d.n), f->vel + 3 * (d.off + d.n), f->m + d.off + d.n,
                               f->R + d.off + d.n};
             double *dst[4] = {f->pos + 3 * d.off, f->vel + 3 * d.off, f->m + d.off, f->R + d.off};
@@ -2332,10 +2430,10 @@ int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, 
                 }
                 NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
             } catch (...) {
-                bfree(tmp);
+                if (own) bfree(tmp);
                 throw;
             }
-            bfree(tmp);
+            if (own) bfree(tmp);
         }
     } catch (const CudaError &e) {
         return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
@@ -2355,13 +2453,18 @@ int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, 
 
 int ncorp_batch_info(const ncorp_batch *b, int64_t *info, int n_info) {
     if (!b || !info || n_info < 0) return NCORP_EINVAL;
-    int64_t moonlets = 0, disks = 0;
+    int64_t moonlets = 0, disks = 0, leaf = 0, largest = -1;
     for (const Forest *f : b->forests) {
         moonlets += f->n;
         disks += static_cast<int64_t>(f->disks.size());
+        if (f->n > largest && f->c) {
+            largest = f->n;
+            leaf = f->c->s;
+        }
     }
     const int64_t v[NCORP_BATCH_NINFO] = {disks, moonlets, static_cast<int64_t>(batch_used(b)),
-                                          static_cast<int64_t>(b->forests.size()), b->fallbacks, b->launches};
+                                          static_cast<int64_t>(b->forests.size()), b->fallbacks, b->launches,
+                                          b->tuned, leaf};
     for (int i = 0; i < n_info && i < NCORP_BATCH_NINFO; i++) info[i] = v[i];
     return NCORP_OK;
 }

@@ -541,12 +541,17 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
     const int ntiles = std::max(1, (n + RS_TILE - 1) / RS_TILE);
     const int need = RS_STATUS_AT + 2 * 256 * ntiles;   // status words take two ints each
     if (c->tile_hist_cap < need) {
+        // the capacity is recorded only once the buffer exists, so a failed allocation leaves none
         if (c->tile_hist) cudaFree(c->tile_hist);
         c->tile_hist = nullptr;
-        c->tile_hist_cap = need + 4096;
-        NCORP_CUDA_CHECK(cudaMalloc(&c->tile_hist, sizeof(int) * c->tile_hist_cap));
-        NCORP_CUDA_CHECK(cudaMemset(c->tile_hist, 0, sizeof(int) * c->tile_hist_cap));
+        c->tile_hist_cap = 0;
         bump_alloc_generation();
+        int *p = nullptr;
+        const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(int) * (need + 4096));
+        if (e != cudaSuccess) throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
+        c->tile_hist = p;
+        NCORP_CUDA_CHECK(cudaMemset(c->tile_hist, 0, sizeof(int) * (need + 4096)));
+        c->tile_hist_cap = need + 4096;
     }
 }
 

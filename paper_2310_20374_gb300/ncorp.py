@@ -288,7 +288,7 @@ def ncorp_stage_times(ctx) -> dict:
 
 
 NCORP_STATIC_MAX_N = 65536
-BATCH_INFO_NAMES = ["disks", "moonlets", "bytes", "forests", "fallbacks", "launches"]
+BATCH_INFO_NAMES = ["disks", "moonlets", "bytes", "forests", "fallbacks", "launches", "tuned", "leaf_size"]
 
 
 def _bcheck(b, st, ok=(NCORP_OK,)):

@@ -72,6 +72,9 @@ class BatchBackend:
 
     def run(self, k: int) -> None:
         self.ncorp.ncorp_batch_run(self.b, k)
+        info = self.ncorp.ncorp_batch_info(self.b)
+        self.peak_bytes = max(getattr(self, "peak_bytes", 0), info["bytes"])
+        self.peak_moonlets = max(getattr(self, "peak_moonlets", 0), info["moonlets"])
 
     def finish(self, req: Request, out=None) -> None:
         """Removes the disk; with out = (positions, velocities) its final state is copied there first."""

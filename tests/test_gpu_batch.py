@@ -45,9 +45,11 @@ def config(precision=ncorp.NCORP_FP64):
     return cfg
 
 
-def single_disk_run(d, p, theta, dt, steps):
+def single_disk_run(d, p, theta, dt, steps, leaf_size=24):
     n = len(d["pos"])
-    ctx = ncorp.ncorp_init(config(), n, 0, torch.cuda.current_stream().cuda_stream)
+    cfg = config()
+    cfg.leaf_size = leaf_size
+    ctx = ncorp.ncorp_init(cfg, n, 0, torch.cuda.current_stream().cuda_stream)
     pos = torch.tensor(d["pos"], device="cuda")
     vel = torch.tensor(d["vel"], device="cuda")
     m = torch.tensor(d["mass"], device="cuda")
@@ -158,6 +160,33 @@ def test_forest_of_many_disks_evolves_as_single_disks():
         for k in (3, 2, 3):
             ncorp.ncorp_batch_run(b, k)
         assert ncorp.ncorp_batch_info(b)["launches"] == launches12
+    finally:
+        ncorp.ncorp_batch_free(b)
+
+
+def test_autotuned_forest_equals_single_disks_at_the_chosen_leaf_size():
+    """leaf_size = 0: the tuner times candidate leaf sizes on the forest's own state and keeps one; the
+    disks then evolve as single disks with that leaf size (the trials leave the state as it was)."""
+    p, theta, dt, steps = 3, 0.5, 2e-2, 3
+    sizes = [20000, 15000, 8000]
+    disks = [make_disk(n, 470 + k, k == 0) for k, n in enumerate(sizes)]
+    cfg = config()
+    cfg.leaf_size = 0
+    b = ncorp.ncorp_batch_create(cfg, 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        ids = [ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], len(d["pos"]), p, theta, dt)
+               for d in disks]
+        ncorp.ncorp_batch_run(b, steps)
+        info = ncorp.ncorp_batch_info(b)
+        assert info["tuned"] == 1 and info["leaf_size"] in (16, 24, 32, 48)
+        s = info["leaf_size"]
+        for did, d in zip(ids, disks):
+            n = len(d["pos"])
+            pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+            ncorp.ncorp_batch_get_state(b, did, pos, vel)
+            xs, vs, _ = single_disk_run(d, p, theta, dt, steps, leaf_size=s)
+            np.testing.assert_allclose(pos, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+            np.testing.assert_allclose(vel, vs, rtol=0, atol=1e-11 * np.abs(vs).max())
     finally:
         ncorp.ncorp_batch_free(b)
 
