@@ -329,8 +329,8 @@ const char *ncorp_last_error(const ncorp_ctx *ctx);
  * laid out by ncorp_set_disks, so that each stage of a step is one launch over
  * all of them however many there are.  ncorp_batch_run advances every forest
  * by n_steps steps through one CUDA graph per forest (captured on the first
- * run of that length and buffer rotation, replayed afterwards); forests run
- * on separate streams and overlap.  Each disk is integrated as by ncorp_step
+ * run of that length and buffer rotation, replayed afterwards); the forests
+ * run one after another, each filling the GPU.  Each disk is integrated as by ncorp_step
  * in a context of its own (the same SBAB1 step of Sect. 4.1 with the falcON
  * forces and the collision search of Sect. 3.1), up to the rounding order of
  * sums.  A batch is not thread-safe: call it from one host thread at a time.
@@ -357,17 +357,17 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
 
 /* Adds a disk of n moonlets: positions/velocities [n][3], masses/radii [n],
  * host or device arrays (copied; the caller keeps ownership); p, theta and
- * dt as for ncorp_step, fixed for the disk.  The disk joins the forest of
- * its (p, theta, dt); that forest's tree and acceleration are computed at
- * the start of the next ncorp_batch_run (one force evaluation for all the
- * disks added or removed since the last run).  Admission by device memory:
- * the disk is refused when the bytes the batch holds plus n times the
- * largest footprint per moonlet measured so far (4096 bytes before any
- * measurement) exceed the budget.  *disk_id receives the disk's id (unique
- * within the batch).  Errors: NCORP_EINVAL (arguments, non-finite positions
- * or velocities, more than NCORP_MAX_DISKS disks with the same (p, theta,
- * dt)), NCORP_ENOMEM (allocation failed, or over the budget), NCORP_ECUDA;
- * on error no disk is added. */
+ * dt as for ncorp_step, fixed for the disk.  The disk joins a forest of its
+ * (p, theta, dt) (another one is started when those have NCORP_MAX_DISKS
+ * disks); that forest's tree and acceleration are computed at the start of
+ * the next ncorp_batch_run (one force evaluation for all the disks added or
+ * removed since the last run).  Admission by device memory: the disk is
+ * refused when the bytes the batch holds plus 1.5 n times the largest
+ * footprint per moonlet measured so far (4096 bytes before any measurement)
+ * exceed the budget, or exceed the device memory still free.  *disk_id
+ * receives the disk's id (unique within the batch).  Errors: NCORP_EINVAL
+ * (arguments, non-finite positions or velocities), NCORP_ENOMEM (allocation
+ * failed, or over the budget), NCORP_ECUDA; on error no disk is added. */
 int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *velocities, const double *masses,
                          const double *radii, int64_t n, int p, double theta, double dt, int32_t *disk_id);
 

@@ -190,10 +190,13 @@ __device__ __forceinline__ bool aborted(const Ctrl *ctl) {
 // block before the barrier (ordered by __syncthreads) are visible to every
 // block after it.  A wait longer than ctl->wait_ns (one second when 0) sets
 // ERR_TIMEOUT and returns false; the kernels then leave, so no launch can
-// hang.  `passed` counts the grid-size steps of the barriers this block has
-// passed.  With ctl->stall set the barrier also waits for one arrival that
-// no block makes, so every block gives up after the limit (the host-armed
-// failure of the failure-path tests).
+// hang.  A block that gives up also sets BAR_FAILED in the counter, so that
+// a block arriving later fails at once instead of passing with the arrivals
+// already counted and running on alone.  `passed` counts the grid-size steps
+// of the barriers this block has passed.  With ctl->stall set the barrier
+// also waits for one arrival that no block makes, so every block gives up
+// after the limit (the host-armed failure of the failure-path tests).
+constexpr unsigned BAR_FAILED = 1u << 30;   // (a launch's arrivals stay far below)
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -227,9 +230,16 @@ __device__ __forceinline__ bool grid_sync_on(unsigned *counter, Ctrl *ctl, unsig
         const unsigned long long t0 = global_ns();
         const unsigned long long limit = ctl->wait_ns ? ctl->wait_ns : 1000000000ull;
         const unsigned target = passed + (ctl->stall ? 1u : 0u);
-        for (unsigned spins = 0; static_cast<int>(ld_acquire_u32(counter) - target) < 0; spins++) {
+        for (unsigned spins = 0;; spins++) {
+            const unsigned v = ld_acquire_u32(counter);
+            if (v & BAR_FAILED) {   // another block gave up
+                ok = 0;
+                break;
+            }
+            if (static_cast<int>(v - target) >= 0) break;
             if ((spins & 255u) == 255u && global_ns() - t0 > limit) {
                 atomicOr(&ctl->err, ERR_TIMEOUT);
+                atomicOr(counter, BAR_FAILED);
                 ok = 0;
                 break;
             }

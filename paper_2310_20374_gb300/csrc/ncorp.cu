@@ -1533,13 +1533,17 @@ const char *ncorp_last_error(const ncorp_ctx *c) {
 // (configure_disks), so that every stage of a step is one launch over all of
 // them, whatever their number.  ncorp_batch_run advances each forest by k
 // steps through one CUDA graph (a snapshot of the state for a rerun, then
-// the k steps), cached per (k, buffer rotation); forests run on separate
-// streams and overlap.  A forest whose membership changed is laid out anew
+// the k steps), cached per (k, buffer rotation); forests run one after
+// another on the batch's stream.  A forest whose membership changed is laid out anew
 // and its tree and acceleration recomputed at the start of the next run.
 // ===========================================================================
 namespace {
 
-constexpr int BATCH_STREAMS = 4;                    // forests f use stream f mod BATCH_STREAMS
+// Forests run one after another on one stream: each forest's launches cover
+// all its disks and fill the GPU, and no forest's cooperative grids then
+// share the SMs with another forest's kernels (a grid whose blocks could not
+// all be resident together would give up at its first barrier).
+constexpr int BATCH_STREAMS = 1;
 constexpr double BATCH_DEFAULT_BYTES_PER_MOONLET = 4096.0;   // admission estimate before any measurement
 constexpr int64_t BATCH_MEASURE_MIN = 1 << 16;               // forests measured for the estimate: n at least this
 
@@ -1699,12 +1703,13 @@ void sync_state(Forest &f) {
     f.synced = true;
 }
 
-// Cooperative grids of concurrent forests are capped so that the grids of all
-// streams fit on the device together; a lone forest runs uncapped, with its
-// collision search beside the gravity pipeline as in ncorp_step.
+// Cooperative grids of forests that share the GPU at the same time would be
+// capped so that all of them fit on the device together; with the forests
+// one after another every forest runs uncapped, with its collision search
+// beside the gravity pipeline as in ncorp_step.
 int coop_cap(const ncorp_batch *b) {
-    const int nf = static_cast<int>(b->forests.size());
-    return nf > 1 ? std::max(16, b->num_sms / std::min(nf, BATCH_STREAMS)) : 0;
+    const int nf = std::min(static_cast<int>(b->forests.size()), BATCH_STREAMS);
+    return nf > 1 ? std::max(16, b->num_sms / nf) : 0;
 }
 
 // Lays the forest out for its current disks and computes their tree and
@@ -2111,12 +2116,11 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
     if (!(dt > 0.0) || !std::isfinite(dt)) return batch_fail(b, NCORP_EINVAL, "dt must be > 0");
     if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, NCORP_ECUDA, "cudaSetDevice failed");
     Forest *f = nullptr;
+    // the forest of (p, theta, dt) with room for one more disk (a full one: the disk starts another)
     for (Forest *g : b->forests)
-        if (g->p == p && g->theta == theta && g->dt == dt) f = g;
-    const int64_t total = f ? f->n + n : n;
-    if (total > (int64_t(1) << 30)) return batch_fail(b, NCORP_EINVAL, "more than 2^30 moonlets with (p, theta, dt)");
-    if (f && static_cast<int>(f->disks.size()) >= NCORP_MAX_DISKS)
-        return batch_fail(b, NCORP_EINVAL, "%d disks already share (p, theta, dt)", NCORP_MAX_DISKS);
+        if (g->p == p && g->theta == theta && g->dt == dt && static_cast<int>(g->disks.size()) < NCORP_MAX_DISKS &&
+            g->n + n <= (int64_t(1) << 30))
+            f = g;
     // admission by device memory: what the batch holds plus the new disk's share at the largest
     // footprint per moonlet measured so far
     // (with a margin of one half: a forest's buffers grow in steps, and an overflow doubles a list)

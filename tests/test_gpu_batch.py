@@ -191,6 +191,22 @@ def test_autotuned_forest_equals_single_disks_at_the_chosen_leaf_size():
         ncorp.ncorp_batch_free(b)
 
 
+def test_a_full_forest_starts_another():
+    """More than NCORP_MAX_DISKS disks of one (p, theta, dt): the batch starts a second forest, and a disk
+    in it evolves as the same disk alone."""
+    p, theta, dt = 3, 0.5, 2e-2
+    disks = [diskgen.make_disk(300, 1000 + k) for k in range(ncorp.NCORP_MAX_DISKS + 3)]
+    b, ids = batch_of(disks, p, theta, dt)
+    try:
+        ncorp.ncorp_batch_run(b, 2)
+        info = ncorp.ncorp_batch_info(b)
+        assert info["forests"] == 2 and info["disks"] == len(disks)
+        for k in (0, ncorp.NCORP_MAX_DISKS, len(disks) - 1):
+            check_disk(b, ids[k], disks[k], p, theta, dt, 2)
+    finally:
+        ncorp.ncorp_batch_free(b)
+
+
 def test_batch_mixed_precision_runs_and_matches_single_disk():
     n, p, theta, dt = 20000, 6, 0.5, 1e-3
     d = diskgen.make_disk(n, 65)
