@@ -116,7 +116,9 @@ void ncorp_config_default(ncorp_config *cfg);
  * NCORP_ENOMEM. */
 int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int device, void *cuda_stream);
 
-/* Changes the stream later calls enqueue their work on. */
+/* Changes the stream later calls enqueue their work on.  Waits first for the
+ * work already enqueued on the old stream.  Errors: NCORP_EINVAL (null ctx),
+ * NCORP_ECUDA (the old stream reported an error). */
 int ncorp_set_stream(ncorp_ctx *ctx, void *cuda_stream);
 
 /* One SBAB1 step (Sect. 4.1): v += dt/2 a(x); collision search on (x, v)

@@ -139,7 +139,9 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.Cf_lo, 3 * static_cast<size_t>(cap));
     dalloc(C.Ch_lo, 3 * static_cast<size_t>(cap));
     dalloc(C.done, cap);   // descent epochs start at 1: zeroed words never match
-    NCORP_CUDA_CHECK(cudaMemset(C.done, 0, sizeof(unsigned) * cap));
+    // (on the context's stream, ahead of every kernel that reads them: a plain memset would run on the
+    // legacy stream, which is not ordered with the non-blocking streams the library is driven on)
+    NCORP_CUDA_CHECK(cudaMemsetAsync(C.done, 0, sizeof(unsigned) * cap, c->stream));
     WalkLists &W = c->wl;
     dalloc(W.cnt, cap + 1); dalloc(W.offs, cap + 1); dalloc(W.cursor, cap + 1); dalloc(W.p2p_off, cap + 1);
     C.cap = cap;
@@ -395,7 +397,11 @@ __global__ void k_arm_stall(Ctrl *ctl, Ctrl *ctl2) {
     ctl2->stall = 1;
 }
 
-__global__ void k_reset_ctl(Ctrl *ctl, Ctrl *ctl2, int *fold, int *clear) {
+// inherit (nullable, with fold): the control block of the tree whose results the cleared set's work
+// starts from (the opening kick reads that tree's accelerations); its abort bits are folded first, so
+// that nothing is computed from an evaluation that never ran.
+__global__ void k_reset_ctl(Ctrl *ctl, Ctrl *ctl2, int *fold, int *clear, const Ctrl *inherit) {
+    if (fold && inherit) *fold |= inherit->err & ERR_ABORT_MASK;
     reset_one(ctl, fold);
     if (ctl2) reset_one(ctl2, nullptr);
     if (clear) *clear = 0;
@@ -469,15 +475,18 @@ void configure_disks(ncorp_ctx *c, int nd, const int64_t *sizes) {
     c->tree_valid = false;
 }
 
+// fold: the set is recycled within a call (called with the other tree set as c->alt, the one the
+// recycled set's next work starts from)
 void reset_ctl(ncorp_ctx *c, bool fold = false) {
-    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, nullptr, fold ? c->err_acc : nullptr, nullptr);
+    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, nullptr, fold ? c->err_acc : nullptr, nullptr,
+                                        fold ? c->alt.ctl : nullptr);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
 
 // Both tree sets and the error accumulator, before a step.
 void reset_ctls(ncorp_ctx *c) {
-    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, c->alt.ctl, nullptr, c->err_acc);
+    k_reset_ctl<<<1, 1, 0, c->stream>>>(c->ctl, c->alt.ctl, nullptr, c->err_acc, nullptr);
     c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
 }
@@ -664,7 +673,9 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
     const double h = 0.5 * dt;
     ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
     // the other tree set becomes the new tree's: cleared (its errors kept) before the kick-drift
-    // kernel folds the drifted positions' bounding box into its control block
+    // kernel folds the drifted positions' bounding box into its control block.  It also takes over
+    // the abort bits of A's tree: if A's acceleration was never computed (an overflow in the same
+    // call), the kick-drift and everything built from it do nothing.
     on_alt(c, [&] { reset_ctl(c, true); });
     {
         Stage st(c, NCORP_STAGE_KDK);
@@ -957,7 +968,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         }
         dalloc(c->work_counter, 4);
         dalloc(c->err_acc, 1);
-        NCORP_CUDA_CHECK(cudaMemset(c->err_acc, 0, sizeof(int)));
+        NCORP_CUDA_CHECK(cudaMemsetAsync(c->err_acc, 0, sizeof(int), c->stream));
         NCORP_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void **>(&c->err_acc_h), sizeof(int)));
         *c->err_acc_h = 0;
         // side streams at the lowest priority: when blocks of both wait for room on the SMs, the main
@@ -973,6 +984,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         ensure_particles(c, n_max);
         choose_parameters(c, 6);
         ensure_both_capacities(c, static_cast<int>(n_max));
+        NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));   // the clears above, before any other stream's use
     } catch (const CudaError &e) {
         int code = (e.code == cudaErrorMemoryAllocation) ? NCORP_ENOMEM : NCORP_ECUDA;
         ncorp_free(c);
@@ -984,6 +996,8 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
 
 int ncorp_set_stream(ncorp_ctx *c, void *cuda_stream) {
     if (!c) return NCORP_EINVAL;
+    // work already enqueued on the old stream (buffer clears included) ends before the new one's
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, NCORP_ECUDA, "%s", "stream synchronize failed");
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     return NCORP_OK;
 }

@@ -550,7 +550,9 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
         const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(int) * (need + 4096));
         if (e != cudaSuccess) throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
         c->tile_hist = p;
-        NCORP_CUDA_CHECK(cudaMemset(c->tile_hist, 0, sizeof(int) * (need + 4096)));
+        // on the context's stream, ordered before the sorts that use it (the legacy stream is not
+        // ordered with the non-blocking streams the library is driven on)
+        NCORP_CUDA_CHECK(cudaMemsetAsync(c->tile_hist, 0, sizeof(int) * (need + 4096), c->stream));
         c->tile_hist_cap = need + 4096;
     }
 }
