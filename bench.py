@@ -361,7 +361,7 @@ def run_gpu(a):
     sampler = ClockSampler(physical_gpu_index(local))
     peaks = {"fp32_tflops": ncorp.ncorp_fma_peak(local, ncorp.NCORP_MIXED, stream.cuda_stream) / 1e12,
              "fp64_tflops": ncorp.ncorp_fma_peak(local, ncorp.NCORP_FP64, stream.cuda_stream) / 1e12,
-             "hbm_gbs": hbm, "how": "FMA: ncorp_fma_peak (in-bounds FMA chains on every SM, best of 5 ~5 ms "
+             "hbm_gbs": hbm, "how": "FMA: ncorp_fma_peak (in-bounds FMA chains on every SM, best of 5 ~4 ms "
                                     "launches, 2 FLOP per FMA); HBM: MEASURED_PEAKS.json copy bandwidth"}
     peak = peaks["fp32_tflops"] if a.precision == "mixed" else peaks["fp64_tflops"]
     ctx_args = {"barrier": barrier}
@@ -671,6 +671,7 @@ def run_serving(a):
         clocks = sampler.stop()
         ncorp.ncorp_batch_free(b)
     offered = sum(r.n for r in reqs) * 100 / a.serve_seconds
+    served_n = sum(r.n for r in reqs if r.done is not None)
     value = slowest_rank(dist, st["throughput"], world) if world > 1 else st["throughput"]
     out = {"metric": METRIC, "value": round(value * (world if world > 1 else 1), 1), "unit": UNIT, "n_gpus": world,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -697,9 +698,14 @@ def run_serving(a):
            "busy_throughput": round(st["busy_throughput"], 1),
            "wall_s": round(st["wall_s"], 2), "offered_moonlet_steps_per_s": round(offered, 1),
            "clocks": clocks,
-           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+           "e2e": {"value": round(value, 1), "unit": UNIT,
+                   # every served disk's state in (x, v, m, R: 64 B per moonlet) and out (x, v: 48 B per moonlet),
+                   # over the batch steps of the run
+                   "h2d_bytes_per_step": round(64 * served_n / max(st["batch_steps"], 1)),
+                   "d2h_bytes_per_step": round(48 * served_n / max(st["batch_steps"], 1)),
                    "note": "the serving throughput is end to end: host arrays in, each disk's state back to host "
-                           "memory when it finishes"}}
+                           "memory when it finishes; bytes per step = all requests' bytes / batch steps "
+                           "(ncorp_batch_run steps over every resident disk)"}}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -47,6 +47,7 @@ struct CollideArgs {
     const double *x, *y, *z, *vx, *vy, *vz, *R;
     const float4 *hi4, *lo4;
     const float4 *cv;          // velocity rounded to FP32 (xyz), R + dt |v| rounded up to FP32 (w)
+    const float4 *bh, *bl;     // per cell: collision centre hi (xyz) and r_crit in FP32 (w); centre lo
     const int *perm;
     double dt;
     uint64_t *pairs;
@@ -108,19 +109,40 @@ __device__ __forceinline__ bool may_meet(float dx, float dy, float dz, const flo
 
 constexpr int COL_WARPS = 8;
 
+// 3. Before the pairs of two different leaves A and B are formed, each
+//    moonlet is tested against the other leaf's sphere: a pair (a, b) can
+//    only collide if |x_a - x_b| <= rc_a + rc_b, and every moonlet b of B has
+//    |x_b - sbar_B| <= r_max,B <= r_crit,B - rc_b, so |x_a - sbar_B| <= rc_a +
+//    r_crit,B (and the same with A and B exchanged).  In FP32 with the
+//    margins of test 1; the moonlets of A and B that fail take no part in the
+//    item's pairs.  Tests are still counted per item (n_A n_B pairs), as the
+//    walk defines them.
+__device__ __forceinline__ bool near_sphere(const float4 &h, const float4 &l, float r, const float4 &ch,
+                                            const float4 &cl) {
+    const float dx = (h.x - ch.x) + (l.x - cl.x);
+    const float dy = (h.y - ch.y) + (l.y - cl.y);
+    const float dz = (h.z - ch.z) + (l.z - cl.z);
+    const float s = r + ch.w;
+    return dx * dx + dy * dy + dz * dz <= s * s * (1.0f + 0x1p-10f);
+}
+
 // Warp per direct item (a leaf with itself, or a pair of leaves).  The
-// source leaf is staged COL_STAGE moonlets at a time; the item's targets are
-// taken 32 at a time, m of them occupying T = pow2ceil(m) lanes, and the
-// warp's lanes form G = 32 / T groups: lane (g, t) tests target t against the
-// staged sources k = g, g + G, ...  so small leaves keep the lanes busy.
+// item's targets are taken 32 at a time and, for a pair of leaves, only those
+// near the source leaf's sphere are kept; the m kept targets occupy T =
+// pow2ceil(m) lanes and the warp's lanes form G = 32 / T groups.  The source
+// leaf is staged COL_STAGE moonlets at a time, compacted to those near the
+// target leaf's sphere; lane (g, t) tests target t against the staged sources
+// k = g, g + G, ...  so small leaves keep the lanes busy.
 constexpr int COL_STAGE = 64;
 
-__global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
+__global__ void __launch_bounds__(32 * COL_WARPS, 4) k_collide(CollideArgs A) {
     __shared__ float4 s_h[COL_WARPS][COL_STAGE], s_l[COL_WARPS][COL_STAGE], s_v[COL_WARPS][COL_STAGE];
     __shared__ float s_R[COL_WARPS][COL_STAGE];
+    __shared__ int s_j[COL_WARPS][COL_STAGE];
     const float dtf = static_cast<float>(A.dt) * (1.0f + 0x1p-20f);
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     long long tests = 0;
@@ -136,13 +158,25 @@ __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
         const bool self = ct == cs;
         const int ft = A.first[ct], nt = A.count[ct], fs = A.first[cs], nsrc = A.count[cs];
         if (lane == 0) tests += self ? static_cast<long long>(nt) * (nt - 1) / 2 : static_cast<long long>(nt) * nsrc;
+        float4 tch = make_float4(0.f, 0.f, 0.f, 0.f), tcl = tch, sch = tch, scl = tch;   // leaves' spheres
+        if (!self) {
+            tch = A.bh[ct];
+            tcl = A.bl[ct];
+            sch = A.bh[cs];
+            scl = A.bl[cs];
+        }
         for (int t0 = 0; t0 < nt; t0 += 32) {
-            const int m = min(32, nt - t0);
+            bool keep = t0 + lane < nt;
+            if (keep && !self)
+                keep = near_sphere(A.hi4[ft + t0 + lane], A.lo4[ft + t0 + lane], A.cv[ft + t0 + lane].w, sch, scl);
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            const int m = __popc(kept);
+            if (m == 0) continue;
             int lg = 0;
             while ((1 << lg) < m) lg++;
             const int T = 1 << lg, G = 32 >> lg, tt = lane & (T - 1), g = lane >> lg;
-            const int u = t0 + tt;
             const bool act = tt < m;
+            const int u = act ? t0 + static_cast<int>(__fns(kept, 0, tt + 1)) : 0;
             float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th, tv = th;
             float tR = 0.f;
             if (act) {
@@ -154,16 +188,33 @@ __global__ void __launch_bounds__(32 * COL_WARPS) k_collide(CollideArgs A) {
             for (int j0 = 0; j0 < nsrc; j0 += COL_STAGE) {
                 const int lim = min(COL_STAGE, nsrc - j0);
                 __syncwarp();
-                for (int k = lane; k < lim; k += 32) {
-                    s_h[wl][k] = A.hi4[fs + j0 + k];
-                    s_l[wl][k] = A.lo4[fs + j0 + k];
-                    s_v[wl][k] = A.cv[fs + j0 + k];
-                    s_R[wl][k] = static_cast<float>(A.R[fs + j0 + k]);
+                int cnt = 0;
+#pragma unroll
+                for (int r = 0; r < COL_STAGE / 32; r++) {
+                    const int k = r * 32 + lane;
+                    bool in = k < lim;
+                    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h, v = h;
+                    if (in) {
+                        h = A.hi4[fs + j0 + k];
+                        l = A.lo4[fs + j0 + k];
+                        v = A.cv[fs + j0 + k];
+                        if (!self) in = near_sphere(h, l, v.w, tch, tcl);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        const int slot = cnt + __popc(bal & below);
+                        s_h[wl][slot] = h;
+                        s_l[wl][slot] = l;
+                        s_v[wl][slot] = v;
+                        s_R[wl][slot] = static_cast<float>(A.R[fs + j0 + k]);
+                        s_j[wl][slot] = j0 + k;
+                    }
+                    cnt += __popc(bal);
                 }
                 __syncwarp();
                 if (act) {
-                    for (int k = g; k < lim; k += G) {
-                        const int v = j0 + k;
+                    for (int k = g; k < cnt; k += G) {
+                        const int v = s_j[wl][k];
                         float dx, dy, dz;
                         if ((!self || v > u) && may_touch(s_h[wl][k], s_l[wl][k], s_v[wl][k].w, th, tl, tv.w, dx, dy, dz) &&
                             may_meet(dx, dy, dz, s_v[wl][k], tv, (s_R[wl][k] + tR) * (1.0f + 0x1p-20f), dtf))
@@ -184,6 +235,7 @@ void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const 
     A.first = c->cells.first; A.count = c->cells.count;
     A.x = P.x; A.y = P.y; A.z = P.z; A.vx = vx; A.vy = vy; A.vz = vz; A.R = P.R;
     A.hi4 = P.hi4; A.lo4 = P.lo4; A.cv = c->cv4;
+    A.bh = c->cells.bh; A.bl = c->cells.bl;
     A.perm = P.perm;
     A.dt = dt;
     A.pairs = c->pairs;
@@ -340,6 +392,7 @@ void launch_standard_collide(ncorp_ctx *c, const ParticleSet &P, double dt, int 
     A.first = c->cells.first; A.count = c->cells.count;
     A.x = P.x; A.y = P.y; A.z = P.z; A.vx = P.vx; A.vy = P.vy; A.vz = P.vz; A.R = P.R;
     A.hi4 = P.hi4; A.lo4 = P.lo4; A.cv = c->cv4;
+    A.bh = c->cells.bh; A.bl = c->cells.bl;
     A.perm = P.perm;
     A.dt = dt;
     A.pairs = c->pairs;

@@ -164,6 +164,7 @@ def summarize(reqs, ticks, step_ms, concurrent, wall):
         "throughput": work / wall if wall > 0 else 0.0,
         "busy_throughput": work / busy if busy > 0 else 0.0,
         "ticks": len(ticks),
+        "batch_steps": sum(k for _, _, k, _, _ in ticks),
         "tick_ms_p50": _pct(tick_ms, 50), "tick_ms_p99": _pct(tick_ms, 99),
         "step_ms_p50": _pct(sv, 50, sw), "step_ms_p99": _pct(sv, 99, sw),
         "request_s_p50": _pct([r.done - r.arrival for r in served], 50),

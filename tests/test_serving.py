@@ -100,7 +100,7 @@ def test_latencies_of_a_worked_example():
     # tick 2: [1.0, 2.0] A and B, 10 steps: both finish at 2.0.
     reqs = [serving.Request(arrival=0.0, n=1000, p=3, steps=20), serving.Request(arrival=0.5, n=1000, p=3, steps=10)]
     st, _ = run(reqs, tick_steps=10, step_s=lambda moonlets: 0.1)
-    assert st["ticks"] == 2
+    assert st["ticks"] == 2 and st["batch_steps"] == 20
     assert st["tick_ms_p50"] == pytest.approx(1000.0) and st["tick_ms_p99"] == pytest.approx(1000.0)
     assert st["step_ms_p50"] == pytest.approx(100.0) and st["step_ms_p99"] == pytest.approx(100.0)
     assert reqs[0].done == pytest.approx(2.0) and reqs[1].done == pytest.approx(2.0)
@@ -116,6 +116,7 @@ def test_ticks_are_shortened_so_no_disk_overshoots():
     st, _ = run(reqs, tick_steps=10)
     assert st["served"] == 2          # finish() asserts the exact step counts
     assert st["ticks"] == 3           # 7 (both), then 10 and 6 (the second alone): 7 + 10 + 6 = 23
+    assert st["batch_steps"] == 23
 
 
 def test_admission_stops_at_the_end_of_the_window():
