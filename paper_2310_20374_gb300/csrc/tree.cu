@@ -412,18 +412,7 @@ struct ClimbArgs {
     int cap;
 };
 
-constexpr int CLIMB_WARPS = 4;
 constexpr int CLIMB_WARPS_COOP = 8;
-
-struct ClimbShared {
-    double a[32], b[32], c[32], d[32], e[32];
-};
-
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 template <typename real>
 __device__ __forceinline__ real warp_sum_r(real v) {
@@ -544,40 +533,6 @@ __device__ __forceinline__ void store_reduced(real *acc, real *dst, int lane) {
         const real v = warp_sum_r(acc[j]);
         if (lane == (j & 31)) dst[j] = v;
     }
-}
-
-// Parent geometry with the warp: lane 0 sums the masses and lanes 1..3 the
-// mass-weighted coordinates, each in child order (as a sequential sum would);
-// lanes 1..3 divide; one lane per child forms r_max,c + |s_c - s|; one lane
-// per axis the corner distance.  Children are staged in S (a = M or count,
-// b, c, d = centre, e = r_max).  weights_are_mass: gravity (M) or collisions
-// (moonlet counts, divisor = the cell's count).
-__device__ __forceinline__ void parent_centre(const ClimbShared &S, int nch, int lane, bool weights_are_mass,
-                                              double cnt_parent, double &M, double &px, double &py, double &pz) {
-    double acc = 0;
-    if (lane < 4) {
-        const double *coord = lane == 1 ? S.b : (lane == 2 ? S.c : S.d);
-        for (int ch = 0; ch < nch; ch++) {
-            const double w = S.a[ch];
-            acc = lane == 0 ? dadd(acc, w) : dadd(acc, dmul(w, coord[ch]));
-        }
-    }
-    M = __shfl_sync(0xffffffffu, acc, 0);
-    const double div = weights_are_mass ? M : cnt_parent;
-    double q = (lane >= 1 && lane < 4) ? ddiv(acc, div) : 0.0;
-    px = __shfl_sync(0xffffffffu, q, 1);
-    py = __shfl_sync(0xffffffffu, q, 2);
-    pz = __shfl_sync(0xffffffffu, q, 3);
-}
-
-__device__ __forceinline__ double corner_warp(const double *root, int lev, uint32_t cx, uint32_t cy, uint32_t cz, double sx,
-                                              double sy, double sz, int lane) {
-    const double h = cell_side(root, lev);
-    double d = 0;
-    if (lane < 3) d = corner_axis(root, lane, h, lane == 0 ? cx : (lane == 1 ? cy : cz), lane == 0 ? sx : (lane == 1 ? sy : sz));
-    const double d0 = __shfl_sync(0xffffffffu, d, 0), d1 = __shfl_sync(0xffffffffu, d, 1),
-                 d2 = __shfl_sync(0xffffffffu, d, 2);
-    return dnorm3(d0, d1, d2);
 }
 
 // ---- gravity geometry of parents from their children (Eqs. expansion_center,
@@ -1027,6 +982,9 @@ void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, do
 // prefilter).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
+    // the grid barrier counter of the parents' cooperative climb that follows on this stream (nothing
+    // else uses this tree set's counter meanwhile)
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->bar_count = 0;
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
@@ -1072,65 +1030,91 @@ __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
     }
 }
 
-__global__ void __launch_bounds__(32 * CLIMB_WARPS) k_climb_collision(ClimbArgs A) {
-    __shared__ ClimbShared sh_all[CLIMB_WARPS];
+// ---- collision geometry of parents from their children (Eqs. center, rmax,
+// rcrit, corner cap), four parents per warp, eight lanes each, as for gravity
+// (parent_gravity_group) with the children's moonlet counts as weights and
+// the parent's count as divisor; r_crit = r_max + the largest (r_crit - r_max)
+// of the children.  c is the group's parent, -1 for none; every lane of the
+// warp calls this.
+__device__ __forceinline__ void parent_collision_group(const ClimbArgs &A, int c, int lane) {
+    const int j = lane & 7, base = lane & ~7;
+    const bool valid = c >= 0;
+    const int c0 = valid ? A.child0[c] : 0, nch = valid ? A.nchild[c] : 0;
+    double cw = 0.0, csx = 0.0, csy = 0.0, csz = 0.0, crm = 0.0, cex = 0.0;
+    if (j < nch) {
+        cw = static_cast<double>(A.count[c0 + j]);
+        csx = __ldcg(&A.sx[c0 + j]);
+        csy = __ldcg(&A.sy[c0 + j]);
+        csz = __ldcg(&A.sz[c0 + j]);
+        crm = __ldcg(&A.rmax[c0 + j]);
+        cex = dsub(__ldcg(&A.rcrit[c0 + j]), crm);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ch++) {
+        const double w = __shfl_sync(0xffffffffu, cw, base + ch);
+        const double bx = __shfl_sync(0xffffffffu, csx, base + ch);
+        const double by = __shfl_sync(0xffffffffu, csy, base + ch);
+        const double bz = __shfl_sync(0xffffffffu, csz, base + ch);
+        const double coord = j == 1 ? bx : (j == 2 ? by : (j == 3 ? bz : 1.0));
+        const double t = dmul(w, coord);
+        if (ch < nch) acc = dadd(acc, t);
+    }
+    const double q = ddiv(acc, valid ? static_cast<double>(A.count[c]) : 1.0);
+    const double px = __shfl_sync(0xffffffffu, q, base + 1), py = __shfl_sync(0xffffffffu, q, base + 2),
+                 pz = __shfl_sync(0xffffffffu, q, base + 3);
+    double rm = 0.0;
+    if (j < nch) rm = dadd(crm, dnorm3(dsub(csx, px), dsub(csy, py), dsub(csz, pz)));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        cex = fmax(cex, __shfl_xor_sync(0xffffffffu, cex, o));
+    }
+    double d = 0.0;
+    if (valid && j < 3) {
+        const double *rt = cell_root(A.ctl, A.first, c);
+        const double h = cell_side(rt, A.level[c]);
+        d = corner_axis(rt, j, h, j == 0 ? A.cx[c] : (j == 1 ? A.cy[c] : A.cz[c]), j == 0 ? px : (j == 1 ? py : pz));
+    }
+    const double d0 = __shfl_sync(0xffffffffu, d, base), d1 = __shfl_sync(0xffffffffu, d, base + 1),
+                 d2 = __shfl_sync(0xffffffffu, d, base + 2);
+    const double pcap = dnorm3(d0, d1, d2);
+    if (pcap < rm) rm = pcap;
+    if (valid && j == 0) {
+        const double rc = dadd(rm, cex);
+        A.sx[c] = px;
+        A.sy[c] = py;
+        A.sz[c] = pz;
+        A.rmax[c] = rm;
+        A.rcrit[c] = rc;
+        float4 hi, lo;
+        split3(px, py, pz, hi, lo);
+        hi.w = static_cast<float>(rc);
+        lo.w = 0.f;
+        A.gh[c] = hi;
+        A.gl[c] = lo;
+    }
+}
+
+// The parents, level by level from the deepest, in one cooperative launch
+// (the leaves were done by k_leaf_collision, which also zeroed the barrier
+// counter).  Four parents per warp, so that one FP64 warp instruction
+// advances four parents.
+__global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_climb_collision(ClimbArgs A) {
     if (aborted(A.ctl)) return;
-    ClimbShared &S = sh_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int n_leaves = A.ctl->n_leaves;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < n_leaves; gw += nwarps) {
-        int c = A.leaves[gw];
-        while (true) {
-            fence_acq_rel_gpu();
-            __syncwarp();
-            const int pc = A.parent[c];
-            if (pc < 0) break;
-            int last = 0;
-            if (lane == 0) {
-                last = atomicAdd(&A.arrive[pc], 1) == A.nchild[pc] - 1;
-                if (last) fence_acq_rel_gpu();   // acquire: the other children's results
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (!last) break;
-            __syncwarp();   // orders lane 0's acquire before every lane's reads
-            c = pc;
-            const int c0 = A.child0[c], nch = A.nchild[c];
-            if (lane < nch) {
-                S.a[lane] = static_cast<double>(A.count[c0 + lane]);
-                S.b[lane] = __ldcg(&A.sx[c0 + lane]);
-                S.c[lane] = __ldcg(&A.sy[c0 + lane]);
-                S.d[lane] = __ldcg(&A.sz[c0 + lane]);
-                S.e[lane] = __ldcg(&A.rmax[c0 + lane]);
-            }
-            __syncwarp();
-            double Mdummy, px, py, pz;
-            parent_centre(S, nch, lane, false, static_cast<double>(A.count[c]), Mdummy, px, py, pz);
-            double rm = 0, e2 = 0;
-            if (lane < nch) {
-                rm = dadd(S.e[lane], dnorm3(dsub(S.b[lane], px), dsub(S.c[lane], py), dsub(S.d[lane], pz)));
-                e2 = dsub(__ldcg(&A.rcrit[c0 + lane]), S.e[lane]);
-            }
-            rm = warp_max(rm);
-            e2 = warp_max(e2);
-            const double pcap = corner_warp(cell_root(A.ctl, A.first, c), A.level[c], A.cx[c], A.cy[c], A.cz[c], px, py,
-                                            pz, lane);
-            if (pcap < rm) rm = pcap;
-            if (lane == 0) {
-                const double rc = dadd(rm, e2);
-                A.sx[c] = px;
-                A.sy[c] = py;
-                A.sz[c] = pz;
-                A.rmax[c] = rm;
-                A.rcrit[c] = rc;
-                float4 hi, lo;
-                split3(px, py, pz, hi, lo);
-                hi.w = static_cast<float>(rc);
-                lo.w = 0.f;
-                A.gh[c] = hi;
-                A.gl[c] = lo;
-            }
+    // warps numbered across the blocks first, so that consecutive work items land on different SMs
+    const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned bar = 0;
+    const int maxl = A.ctl->max_level;
+    for (int lev = maxl - 1; lev >= 0; lev--) {
+        const int ls = A.ctl->level_start[lev], le = A.ctl->level_start[lev + 1];
+        for (int g = gw0; ls + g * PARENT_GROUP < le; g += nwarps) {
+            const int cc = ls + g * PARENT_GROUP + (lane >> 3);
+            const int c = (cc < le && A.nchild[cc] > 0) ? cc : -1;
+            if (__any_sync(0xffffffffu, c >= 0)) parent_collision_group(A, c, lane);
         }
+        if (lev > 0 && !grid_sync(A.ctl, bar)) return;
     }
 }
 
@@ -1145,8 +1129,13 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.cv4 = c->cv4;
     k_leaf_collision<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
-    k_climb_collision<<<4 * c->num_sms, 32 * CLIMB_WARPS, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
+    const int block = 32 * CLIMB_WARPS_COOP;
+    const int grid = coop_grid(c, reinterpret_cast<const void *>(k_climb_collision), block, 0);
+    void *args[] = {&A};   // ctl->bar_count was zeroed by k_leaf_collision
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_climb_collision), dim3(grid),
+                                                 dim3(block), args, 0, c->stream));
+    c->launches++;
 }
 
 }  // namespace ncorp
