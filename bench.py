@@ -323,7 +323,7 @@ def summarize(a, t, n, steps, world, dist, hbm, peak_tflops, p):
     t_max = slowest_rank(dist, total, world)
     last = {k: t["last"][k] for k in ("cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions",
                                       "walk_iters", "col_pairs", "col_self", "col_tests", "col_iters",
-                                      "m2l_directed", "p2p_directed")}
+                                      "m2l_directed", "p2p_directed", "sort_path")}
     return {"value": round(replica_throughput(n, steps, world, t_max * 1e-3), 1), "unit": UNIT,
             "ms_per_step": round(t_max / steps, 4),
             "p50_step_ms": round(float(np.percentile(t["step_ms"], 50)), 4),

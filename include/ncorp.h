@@ -254,8 +254,10 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
 #define NCORP_STAT_LAUNCHES    14   /* CUDA kernels the last call launched */
 #define NCORP_STAT_COL_ITERS   15   /* frontier iterations of the collision walk */
 #define NCORP_STAT_GRAPH       16   /* 1 if the last ncorp_step ran as a replayed (or just captured) CUDA graph */
-#define NCORP_STAT_SORT_PATH   17   /* key sort of the last tree: 1 nearly-sorted merge (steps), 0 radix sort,
-                                       -1 radix sort after the merge found the kept keys out of order */
+#define NCORP_STAT_SORT_PATH   17   /* key sort of the last tree: 1 nearly-sorted merge (steps) with the
+                                       out-of-place keys ranked (at most 4096 of them), 2 the same with
+                                       them radix-sorted (at most 65536), 0 radix sort of all keys, -1 radix
+                                       sort after the merge found the kept keys out of order */
 #define NCORP_STAT_RESOLVED    18   /* impacts resolved by the last ncorp_step (resolve_f > 0) */
 #define NCORP_NSTATS           19
 

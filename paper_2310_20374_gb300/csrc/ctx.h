@@ -91,7 +91,7 @@ void ensure_radix_scratch(ncorp_ctx *c, int n);
 unsigned radix_epoch_limit();
 void sort_near_sorted(ncorp_ctx *c, uint64_t *keys, uint32_t *idx, uint64_t *keys_alt, uint32_t *idx_alt, int n,
                       int bits);
-constexpr int RESORT_MOVERS_CAP = 4096;   // movers of the nearly-sorted key sort (RS_MOVERS_MAX)
+constexpr int RESORT_MOVERS_CAP = 65536;  // movers of the nearly-sorted key sort (RS_MOVERS_MAX)
 constexpr int RESORT_BLOCKS_CAP = 4096;
 
 }  // namespace ncorp

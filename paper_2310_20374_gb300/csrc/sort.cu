@@ -344,7 +344,8 @@ __device__ __forceinline__ unsigned long long ld_status(const unsigned long long
 
 // The whole sort, run by every block of a cooperative grid of any size (256
 // threads per block); bar counts the grid barriers the blocks have passed.
-__device__ void radix_body(const RadixArgs &A, unsigned &bar) {
+// Returns false if a grid barrier gave up (the call has failed).
+__device__ bool radix_body(const RadixArgs &A, unsigned &bar) {
     __shared__ int s_cnt[RS_W][256];
     __shared__ int s_start[256];
     __shared__ int s_excl[256];
@@ -385,7 +386,7 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
             ghist[9 * 256 + t] = t == 0 ? n : 0;
         }
     }
-    if (!grid_sync(A.ctl, bar)) return;
+    if (!grid_sync(A.ctl, bar)) return false;
     const bool wrap = epoch + 1 >= A.epoch_limit;
     if (blockIdx.x == 0 && threadIdx.x == 0) *A.epoch = wrap ? 0u : epoch + 1;
     for (int ps = 0; ps < A.passes; ps++) {
@@ -495,16 +496,17 @@ __device__ void radix_body(const RadixArgs &A, unsigned &bar) {
             }
             __syncthreads();
         }
-        if (ps + 1 < A.passes && !grid_sync(A.ctl, bar)) return;
+        if (ps + 1 < A.passes && !grid_sync(A.ctl, bar)) return false;
     }
     if (wrap) {   // every look-back of the call is over after this barrier: no status word is read again
-        if (!grid_sync(A.ctl, bar)) return;
+        if (!grid_sync(A.ctl, bar)) return false;
         for (long long i = static_cast<long long>(blockIdx.x) * RS_T + threadIdx.x; i < A.status_words;
              i += static_cast<long long>(gridDim.x) * RS_T)
             A.status[i] = 0ull;
         for (int i = blockIdx.x * RS_T + threadIdx.x; i < RS_MAX_PASSES * 256; i += gridDim.x * RS_T)
             ghist[i] = 0;   // the next call (epoch 0) takes the first half
     }
+    return true;
 }
 
 __global__ void __launch_bounds__(RS_T) k_radix(RadixArgs A) {
@@ -607,51 +609,88 @@ void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys
 // by a small fraction of their spacing, so only a few keys are out of place
 // (at dt = 1e-3 on the 1e5 disk: 627 of 1e5, i.e. n minus the longest
 // sorted subsequence).  One cooperative launch:
-//   1. every key adjacent to a descent (k[i] > k[i+1]) is a "mover", the rest
-//      are "stayers"; per-block counts;
+//   1. every key adjacent to a descent (k[i] > k[i+1]) is a "mover", and so
+//      is a key out of order with the nearest non-adjacent keys on either
+//      side (a second round: a few keys that moved together leave the inner
+//      ones of their run behind; on the 1e6 disk at dt = 1e-3 the first
+//      round leaves 46 of them out of order, the second none); the rest are
+//      "stayers"; per-block counts;
 //   2. stayers and movers are compacted in input order (stayer keys and
 //      indices into the radix sort's scratch arrays, movers into a small
 //      buffer);
-//   3. the stayers are checked to be sorted, and the movers are placed by
-//      rank (the count of movers with a smaller key, one warp per mover);
+//   3. the stayers are checked to be sorted, and the movers are sorted: by
+//      rank in shared memory when they are few (the count of movers with a
+//      smaller key, one warp per mover), else by the radix sort of the movers
+//      alone;
 //   4. the two sorted sequences are merged: a stayer goes to its rank among
-//      the stayers plus the number of movers with a smaller key, a mover to
-//      its rank among the movers plus the number of stayers with a key not
-//      larger than its own.
+//      the stayers plus the number of movers with a smaller key (each block
+//      takes a contiguous run of stayers and the movers whose keys fall in
+//      its key range), a mover to its rank among the movers plus the number
+//      of stayers with a key not larger than its own.
 // The result is sorted by key (equal keys in any order: the gather ranks
 // them by caller index).  If there are more than RS_MOVERS_MAX movers or
 // the stayers are not sorted, nothing has been written to the keys or the
 // index (the index must be the identity on entry) and the same launch sorts
 // them with the full radix sort; ctl->resort_ok tells which path ran (1
-// fast, 0 or -1 radix).
+// fast with the movers ranked, 2 fast with the movers' radix sort, 0 or -1
+// the full radix sort).
 // ---------------------------------------------------------------------------
 constexpr int RS_MOVERS_MAX = RESORT_MOVERS_CAP;
-constexpr int RS_SAMPLES = 2048;     // stayer keys sampled into shared memory for the movers' searches
+constexpr int RS_MOVERS_SMEM = 4096;  // movers ranked in shared memory; larger counts take the movers' radix sort
+constexpr int RS_MSLICE = 4096;       // movers of a block's key range searched in shared memory
+constexpr int RS_SAMPLES = 2048;      // stayer keys sampled into shared memory for the movers' searches
 constexpr int RZ_T = 256;
 
 struct ResortArgs {
     RadixArgs radix;      // the full sort of the same arrays (its alt buffers are the stayer scratch)
+    RadixArgs movers;     // the radix sort of the movers (m_key, m_idx; alt m_key2, m_idx2), n set on the device
     uint64_t *key;        // [n] in: keys in input order; out: sorted
     uint32_t *idx;        // [n] in: identity; out: input index of every sorted key
     uint64_t *s_key;      // [n] scratch: stayer keys
     uint32_t *s_idx;      // [n] scratch: stayer input indices
     uint64_t *m_key;      // [RS_MOVERS_MAX] movers in input order
     uint32_t *m_idx;
-    uint64_t *m_key2;     // [RS_MOVERS_MAX] movers sorted by key
+    uint64_t *m_key2;     // [RS_MOVERS_MAX] movers sorted by key (rank path) / scratch (radix path)
     uint32_t *m_idx2;
     int *bcount;          // [gridDim.x] movers per block
     int n;
     Ctrl *ctl;
 };
 
-__device__ __forceinline__ bool is_mover(const uint64_t *k, int i, int n) {
+__device__ __forceinline__ bool next_to_descent(const uint64_t *k, int i, int n) {
     const uint64_t v = k[i];
     return (i > 0 && k[i - 1] > v) || (i + 1 < n && v > k[i + 1]);
+}
+
+constexpr int RZ_REACH = 16;   // a key with this many keys next to descents beside it is a mover
+
+__device__ __forceinline__ bool is_mover(const uint64_t *k, int i, int n) {
+    if (next_to_descent(k, i, n)) return true;
+    const uint64_t v = k[i];
+    int j = i - 1;   // the nearest key before i that is not next to a descent
+    for (int steps = 0; j >= 0 && next_to_descent(k, j, n); j--)
+        if (++steps == RZ_REACH) return true;
+    if (j >= 0 && k[j] > v) return true;
+    j = i + 1;       // and after i
+    for (int steps = 0; j < n && next_to_descent(k, j, n); j++)
+        if (++steps == RZ_REACH) return true;
+    return j < n && v > k[j];
+}
+
+// number of a[lo, hi) (sorted) smaller than v, plus lo
+__device__ __forceinline__ int count_below(const unsigned long long *a, int lo, int hi, unsigned long long v) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldcg(&a[mid]) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 __global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
     extern __shared__ unsigned long long rz_smem[];
     __shared__ int s_warp[33];
+    __shared__ int s_range[2];
     if (aborted(A.ctl)) return;   // every block, before the first barrier
     const int n = A.n, G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
     const int chunk = (n + G - 1) / G, c0 = min(n, b * chunk), c1 = min(n, c0 + chunk);
@@ -700,14 +739,16 @@ __global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
         }
     }
     if (!grid_sync(A.ctl, bar)) return;
-    // ---- 3. stayers sorted?  movers sorted by rank: a mover's place is the number of movers with a
-    // smaller key, or an equal key and a smaller slot; one warp per mover, the keys in shared memory
+    // ---- 3. stayers sorted?  movers sorted (stable: equal keys keep their input order)
     {
         bool bad = false;
         for (int p = b * RZ_T + t; p + 1 < ns; p += G * RZ_T) bad |= __ldcg(&A.s_key[p]) > __ldcg(&A.s_key[p + 1]);
         if (__syncthreads_or(bad) && t == 0) A.ctl->resort_ok = -1;
     }
-    {
+    const bool by_rank = nm <= RS_MOVERS_SMEM;   // uniform
+    if (by_rank) {
+        // a mover's place is the number of movers with a smaller key, or an equal key and a smaller
+        // slot; one warp per mover, the keys in shared memory
         unsigned long long *mk = rz_smem;
         for (int q = t; q < nm; q += RZ_T) mk[q] = __ldcg(&A.m_key[q]);
         __syncthreads();
@@ -725,36 +766,60 @@ __global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
                 A.m_idx2[r] = __ldcg(&A.m_idx[q]);
             }
         }
+    } else {
+        RadixArgs R = A.movers;   // sorts m_key / m_idx in place
+        R.n = nm;
+        R.ntiles = (nm + RS_TILE - 1) / RS_TILE;
+        if (!radix_body(R, bar)) return;
     }
     if (!grid_sync(A.ctl, bar)) return;
     if (*reinterpret_cast<volatile int *>(&A.ctl->resort_ok) != 0) {   // stayers out of order (uniform)
         radix_body(A.radix, bar);
         return;
     }
+    // the sorted movers
+    const unsigned long long *mks = reinterpret_cast<const unsigned long long *>(by_rank ? A.m_key2 : A.m_key);
+    const uint32_t *mis = by_rank ? A.m_idx2 : A.m_idx;
     // ---- 4. merge
-    unsigned long long *mk = rz_smem;                   // movers' keys
-    unsigned long long *smp = rz_smem + RS_MOVERS_MAX;  // every step-th stayer key
+    unsigned long long *sl = rz_smem;                   // the movers of this block's key range
+    unsigned long long *smp = rz_smem + RS_MSLICE;      // every step-th stayer key
     const int step = max(1, (ns + RS_SAMPLES - 1) / RS_SAMPLES), nsmp = (ns + step - 1) / step;
     __syncthreads();   // the rank phase's reads of rz_smem are over in this block
-    for (int q = t; q < nm; q += RZ_T) mk[q] = __ldcg(&A.m_key2[q]);
+    const int sc = (ns + G - 1) / G, p0 = min(ns, b * sc), p1 = min(ns, p0 + sc);
+    if (t == 0) {
+        // movers below this block's first stayer, and below its last one
+        s_range[0] = p0 < p1 ? count_below(mks, 0, nm, __ldcg(&A.s_key[p0])) : 0;
+        s_range[1] = p0 < p1 ? count_below(mks, s_range[0], nm, __ldcg(&A.s_key[p1 - 1])) : 0;
+    }
     for (int q = t; q < nsmp; q += RZ_T) smp[q] = __ldcg(&A.s_key[q * step]);
     __syncthreads();
-    for (int p = b * RZ_T + t; p < ns; p += G * RZ_T) {
+    const int mlo = s_range[0], mhi = s_range[1];
+    const bool in_smem = mhi - mlo <= RS_MSLICE;  // uniform in the block
+    if (in_smem)
+        for (int q = mlo + t; q < mhi; q += RZ_T) sl[q - mlo] = __ldcg(&mks[q]);
+    __syncthreads();
+    for (int p = p0 + t; p < p1; p += RZ_T) {
         const unsigned long long v = __ldcg(&A.s_key[p]);
-        int lo = 0, hi = nm;                        // movers with a key < v
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (mk[mid] < v) lo = mid + 1;
-            else hi = mid;
+        int below;                                  // movers with a key < v: in [mlo, mhi]
+        if (in_smem) {
+            int lo = 0, hi = mhi - mlo;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sl[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            below = mlo + lo;
+        } else {
+            below = count_below(mks, mlo, mhi, v);
         }
-        A.key[p + lo] = v;
-        A.idx[p + lo] = __ldcg(&A.s_idx[p]);
+        A.key[p + below] = v;
+        A.idx[p + below] = __ldcg(&A.s_idx[p]);
     }
-    // movers: one warp each; the sample search brackets the stayers with a key <= v, the warp counts
-    // them inside the bracket
-    const int lane = t & 31, gw = (b * RZ_T + t) >> 5, nwarps = (G * RZ_T) >> 5;
-    for (int q = gw; q < nm; q += nwarps) {
-        const unsigned long long v = mk[q];
+    // movers: one thread each; the sample search in shared memory brackets the stayers with a key <= v,
+    // a binary search inside the bracket counts them
+    const unsigned long long *skey = reinterpret_cast<const unsigned long long *>(A.s_key);
+    for (int q = b * RZ_T + t; q < nm; q += G * RZ_T) {
+        const unsigned long long v = __ldcg(&mks[q]);
         int lo = 0, hi = nsmp;                      // samples with a key <= v
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -762,19 +827,16 @@ __global__ void __launch_bounds__(RZ_T) k_resort(ResortArgs A) {
             else hi = mid;
         }
         // stayers [0, (lo - 1) step] have keys <= v; the count ends in [(lo - 1) step + 1, lo step]
-        int r = lo == 0 ? 0 : (lo - 1) * step + 1;
-        const int e = min(ns, lo * step);
-        for (int base = r; base < e; base += 32) {
-            const int p = base + lane;
-            const bool le = p < e && __ldcg(&A.s_key[p]) <= v;
-            r += __popc(__ballot_sync(0xffffffffu, le));
+        int r = lo == 0 ? 0 : (lo - 1) * step + 1, e = min(ns, lo * step);
+        while (r < e) {                             // first stayer in [r, e) with a key > v
+            const int mid = (r + e) >> 1;
+            if (__ldcg(&skey[mid]) <= v) r = mid + 1;
+            else e = mid;
         }
-        if (lane == 0) {
-            A.key[q + r] = v;
-            A.idx[q + r] = __ldcg(&A.m_idx2[q]);
-        }
+        A.key[q + r] = v;
+        A.idx[q + r] = __ldcg(&mis[q]);
     }
-    if (b == 0 && t == 0) A.ctl->resort_ok = 1;
+    if (b == 0 && t == 0) A.ctl->resort_ok = by_rank ? 1 : 2;
 }
 
 // Sorts keys (with idx = identity on entry) like radix_sort_u64 with the
@@ -789,9 +851,10 @@ void sort_near_sorted(ncorp_ctx *c, uint64_t *keys, uint32_t *idx, uint64_t *key
     A.s_key = keys_alt; A.s_idx = idx_alt;
     A.m_key = c->resort_mkey; A.m_idx = c->resort_midx; A.bcount = c->resort_bcount;
     A.m_key2 = c->resort_mkey + RESORT_MOVERS_CAP; A.m_idx2 = c->resort_midx + RESORT_MOVERS_CAP;
+    A.movers = radix_args(c, A.m_key, A.m_idx, A.m_key2, A.m_idx2, std::min(n, RESORT_MOVERS_CAP), bits);
     A.n = n;
     A.ctl = c->ctl;
-    const size_t smem = sizeof(unsigned long long) * (RS_MOVERS_MAX + RS_SAMPLES);
+    const size_t smem = sizeof(unsigned long long) * (RS_MSLICE + RS_SAMPLES);
     NCORP_CUDA_CHECK(cudaFuncSetAttribute(reinterpret_cast<const void *>(k_resort),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     // about 512 keys per block (short compaction loops), at most one block per SM: the collision

@@ -237,16 +237,29 @@ __device__ void walk_lists(const WalkArgs &A, int *s_tmp, unsigned &bar) {
     }
 }
 
+constexpr int WALK_THREADS = 256, WALK_WARPS = WALK_THREADS / 32;
+
+// Per block: the slots one iteration's warps want in the four append lists
+// (M2L, direct pairs, self leaves, next frontier), reserved with one atomic
+// per list for the whole block (a global counter that every warp hit in turn
+// was the walk's bottleneck at N = 1e6).
+struct WalkSlots {
+    int want[WALK_WARPS][4];
+    int base[WALK_WARPS][4];
+};
+
 // One generation of the walk: the pairs cur[0, nf) of generation it, taken
-// a warp of 32 at a time from warp offset first in steps of stride threads;
+// a block of WALK_THREADS at a time (warp w of the block takes the w-th 32);
 // outcomes appended to the lists and children pairs to the next frontier.
-__device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int nf, int first, int stride) {
-    const int lane = threadIdx.x & 31;
+// The decision statistics are added to the thread's totals st[3].
+__device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int nf, long long *st, WalkSlots &S) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int2 *cur = (it & 1) ? A.front1 : A.front0;
     int2 *nxt = (it & 1) ? A.front0 : A.front1;
     int *ncount = A.fcount + it + 1;
-    for (int base = first; base < nf; base += stride) {
-        const int i = base + lane;
+    // the loop bounds are the same for every thread of the block (block barriers inside)
+    for (int bbase = blockIdx.x * WALK_THREADS; bbase < nf; bbase += gridDim.x * WALK_THREADS) {
+        const int i = bbase + w * 32 + lane;
         const bool valid = i < nf;
         int cA = 0, cB = 0;
         bool forced = false;
@@ -349,19 +362,11 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
                 }
             }
         }
-        // statistics
-        dpair = warp_sum_ll(dpair);
-        dself = warp_sum_ll(dself);
-        inter = warp_sum_ll(inter);
-        if (lane == 0) {
-            if (dpair) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_pairs),
-                                 static_cast<unsigned long long>(dpair));
-            if (dself) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->dec_self),
-                                 static_cast<unsigned long long>(dself));
-            if (inter) atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctl->n_inter),
-                                 static_cast<unsigned long long>(inter));
-        }
-        // outputs: one atomic per list per warp, the four issued together
+        // statistics (added to the lists' counters once per block at the end of the walk)
+        st[0] += dpair;
+        st[1] += dself;
+        st[2] += inter;
+        // outputs: the block's warps reserve their slots together, one atomic per list
         int c0 = 0, nch = 0, k = 0;
         if (split_kind == 1) {
             c0 = c0A;
@@ -385,17 +390,28 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
             if (lane >= o) kin += v;
         }
         const int ktot = __shfl_sync(0xffffffffu, kin, 31);
-        int base_m = 0, base_p = 0, base_s = 0, base_f = 0;
         if (lane == 0) {
-            if (bm) base_m = atomicAdd(&A.ctl->n_m2l, __popc(bm));
-            if (bp) base_p = atomicAdd(&A.ctl->n_p2p, __popc(bp));
-            if (bs) base_s = atomicAdd(&A.ctl->n_self, __popc(bs));
-            if (ktot) base_f = atomicAdd(ncount, ktot);
+            S.want[w][0] = __popc(bm);
+            S.want[w][1] = __popc(bp);
+            S.want[w][2] = __popc(bs);
+            S.want[w][3] = ktot;
         }
-        base_m = __shfl_sync(0xffffffffu, base_m, 0);
-        base_p = __shfl_sync(0xffffffffu, base_p, 0);
-        base_s = __shfl_sync(0xffffffffu, base_s, 0);
-        base_f = __shfl_sync(0xffffffffu, base_f, 0);
+        __syncthreads();
+        if (threadIdx.x < 4) {   // one thread per list: the warps' offsets, one atomic for the block
+            const int q = threadIdx.x;
+            int tot = 0;
+#pragma unroll
+            for (int ww = 0; ww < WALK_WARPS; ww++) {
+                S.base[ww][q] = tot;
+                tot += S.want[ww][q];
+            }
+            int *ctr = q == 0 ? &A.ctl->n_m2l : (q == 1 ? &A.ctl->n_p2p : (q == 2 ? &A.ctl->n_self : ncount));
+            const int b0 = tot ? atomicAdd(ctr, tot) : 0;
+#pragma unroll
+            for (int ww = 0; ww < WALK_WARPS; ww++) S.base[ww][q] += b0;
+        }
+        __syncthreads();
+        const int base_m = S.base[w][0], base_p = S.base[w][1], base_s = S.base[w][2], base_f = S.base[w][3];
         const unsigned lt = (1u << lane) - 1u;
         if (emit_m2l) {
             const int slot = base_m + __popc(bm & lt);
@@ -432,8 +448,10 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
     }
 }
 
-__global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs A) {
     __shared__ int s_tmp[33];
+    __shared__ WalkSlots S;
+    __shared__ long long s_stat[WALK_WARPS][3];
     if (aborted(A.ctl)) return;
     if (A.gravity) {   // list counters, zeroed before the first barrier of the walk
         const int nc = A.ctl->n_cells + 1;
@@ -445,14 +463,33 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs A) {
     volatile int *vcount = A.fcount;
     unsigned bar = 0;
     int it = 0;
+    long long st[3] = {0, 0, 0};   // decision statistics of this thread's pairs
     for (; it < WALK_MAX_ITERS; it++) {
         const int nf = min(vcount[it], A.front_cap);
         if (nf == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->walk_abort[(it + 1) % 3] = 0;   // slot of the next generation
-        walk_generation(A, it, nf, blockIdx.x * blockDim.x + (threadIdx.x & ~31), gridDim.x * blockDim.x);
+        walk_generation(A, it, nf, st, S);
         if (!grid_sync(A.ctl, bar)) return;
         // overflow in this generation (slot it mod 3: identical for every block after the barrier)
         if (((volatile int *)A.ctl->walk_abort)[it % 3]) { it++; break; }
+    }
+    {   // the statistics: one atomic per block and counter
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const long long v = warp_sum_ll(st[k]);
+            if (lane == 0) s_stat[w][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            long long v = 0;
+#pragma unroll
+            for (int ww = 0; ww < WALK_WARPS; ww++) v += s_stat[ww][threadIdx.x];
+            long long *dst = threadIdx.x == 0 ? &A.ctl->dec_pairs : (threadIdx.x == 1 ? &A.ctl->dec_self : &A.ctl->n_inter);
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(dst), static_cast<unsigned long long>(v));
+        }
+        // the collision walk's copies below read every block's totals
+        if (!A.gravity && !grid_sync(A.ctl, bar)) return;
     }
     // the generation count and the barrier snapshot are the same in every block
     if (A.gravity && it < WALK_MAX_ITERS && !((volatile int *)A.ctl->walk_abort)[(it + 2) % 3]) walk_lists(A, s_tmp, bar);
@@ -494,14 +531,14 @@ void launch_walk(ncorp_ctx *c, bool gravity) {
     NCORP_CUDA_CHECK(cudaGetLastError());
     int per_sm = 0;
     NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_walk),
-                                                                   256, 0));
+                                                                   WALK_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
     // about one block per 640 moonlets (frontiers peak near a third of n pairs), 32 to the cooperative limit
     const int grid = std::min(coop_blocks(c, per_sm), std::max(32, c->cur_n / 640));
     void *args[] = {&A};
-    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(256), args,
-                                                 0, c->stream));
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(WALK_THREADS),
+                                                 args, 0, c->stream));
     c->launches++;
 }
 
