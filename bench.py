@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--leaf-size", type=int, default=0, help="disk: leaf size s (0: the default for p)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--resolve-f", type=float, default=0.0,
                     help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
@@ -144,7 +145,7 @@ def measured_hbm_gbs(default=6800.0):
 
 
 def leaf_size_for(p):
-    return 64 if p >= 6 else (48 if p >= 4 else 32)
+    return 64 if p >= 4 else 32
 
 
 def thresholds_for(p):
@@ -160,7 +161,8 @@ def workload_config(a, n=None, seed=None, p=None, theta=None, precision=None):
     res = f", collisions resolved with f={a.resolve_f}" if a.resolve_f else ""
     return {"workload": f"1 disk x {n} moonlets per GPU (seed {seed}+rank), falcON p={p} theta_min={theta}, "
                         f"SBAB1 step dt={a.dt} with tree collision search{res}, {precision} precision",
-            "n_per_gpu": n, "p": p, "theta_min": theta, "dt": a.dt, "leaf_size": leaf_size_for(p),
+            "n_per_gpu": n, "p": p, "theta_min": theta, "dt": a.dt,
+            "leaf_size": a.leaf_size if a.leaf_size > 0 and n == a.n else leaf_size_for(p),
             "gravity_thresholds": thresholds_for(p), "collision_thresholds": [12, 0, 16],
             "precision": precision, "l2": "flushed by a 256 MiB device write before every timed step",
             "parallelism": "replicas (one independent disk per GPU)",
@@ -246,7 +248,7 @@ def time_disk(a, ncorp, torch, ctx_args, d, n, p, theta, precision, steps, warmu
     per-step times, counters of the last step, summed launches and the stage times per step."""
     cfg = ncorp.ncorp_config_default()
     cfg.precision = ncorp.NCORP_MIXED if precision == "mixed" else ncorp.NCORP_FP64
-    cfg.leaf_size = leaf_size_for(p)
+    cfg.leaf_size = a.leaf_size if a.leaf_size > 0 and n == a.n else leaf_size_for(p)
     cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = thresholds_for(p)
     cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = 12, 0, 16
     cfg.resolve_f = a.resolve_f

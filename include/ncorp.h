@@ -102,6 +102,9 @@ void ncorp_config_default(ncorp_config *cfg);
  * Environment variables read here (all optional):
  *   NCORP_RADIX_EPOCH_LIMIT (>= 1) lowers the number of radix sorts after
  *     which the context's sort scratch is cleared (default 2^28);
+ *   NCORP_SIDE_BLOCKS (8..1024, default 64) caps the cooperative grids of
+ *     a step's collision search, which runs beside the new tree's build and
+ *     walk (their blocks must find room on the SMs together);
  *   NCORP_WAIT_LIMIT_MS (1..60000, default 1000) bounds every device-side
  *     grid-barrier wait of the context: a wait that runs longer makes the
  *     call fail with NCORP_ETIMEOUT instead of hanging;

@@ -111,6 +111,7 @@ struct ncorp_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int coop_max = 0;               // cap on cooperative grid sizes (0: none); set when contexts run concurrently
+    int side_blocks = 64;           // cap on the cooperative grids of a step's collision search (side stream)
     char err[512] = {0};
 
     int64_t n_cap = 0;

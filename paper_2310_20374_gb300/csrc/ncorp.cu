@@ -196,7 +196,7 @@ void alloc_pairs(ncorp_ctx *c, int cap) {
 // leaf size and thresholds for expansion order p (config values win when set)
 void choose_parameters(ncorp_ctx *c, int p) {
     const ncorp_config &g = c->cfg;
-    c->s = g.leaf_size > 0 ? g.leaf_size : (c->s_tuned > 0 ? c->s_tuned : (p <= 3 ? 32 : (p <= 5 ? 48 : 64)));
+    c->s = g.leaf_size > 0 ? g.leaf_size : (c->s_tuned > 0 ? c->s_tuned : (p <= 3 ? 32 : 64));
     if (g.n_cs || g.n_cc_pre || g.n_cc_post) {
         c->g_cs = g.n_cs; c->g_pre = g.n_cc_pre; c->g_post = g.n_cc_post;
     } else if (p >= 6) {
@@ -650,7 +650,6 @@ void collisions_standard(ncorp_ctx *c, const ParticleSet &S, int n, double dt) {
     launch_standard_collide(c, S, dt, n, c->cfg.c_cb_pre, c->cfg.c_cb_post);
 }
 
-constexpr int COLLISION_SIDE_BLOCKS = 64;   // cooperative grid of the collision walk beside the gravity pipeline
 
 // One SBAB1 step of the resident state A (its tree, in the current tree set,
 // and its acceleration valid): half kick, collision search on A's tree, drift,
@@ -697,7 +696,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             NCORP_CUDA_CHECK(cudaEventRecord(c->ev_fork, main));
             NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
             c->stream = c->side;
-            c->coop_max = cap > 0 ? std::min(cap, COLLISION_SIDE_BLOCKS) : COLLISION_SIDE_BLOCKS;
+            c->coop_max = cap > 0 ? std::min(cap, c->side_blocks) : c->side_blocks;
             try {
                 collisions(c, A, B.vx, B.vy, B.vz, dt, false);
                 if (resolve) launch_resolve(c, A, B, n, dt);   // may rewrite the drift the main stream reads
@@ -953,6 +952,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         const unsigned long long wait_ns = static_cast<unsigned long long>(env_int("NCORP_WAIT_LIMIT_MS", 1000, 1,
                                                                                     60000)) * 1000000ull;
         c->stall_call = env_int("NCORP_TEST_STALL_STEP", 0, 0, 1 << 30);
+        c->side_blocks = static_cast<int>(env_int("NCORP_SIDE_BLOCKS", 64, 8, 1024));
         c->test_list_cap = static_cast<int>(env_int("NCORP_TEST_LIST_CAP", 0, 0, 1 << 30));
         c->test_pair_cap = static_cast<int>(env_int("NCORP_TEST_PAIR_CAP", 0, 0, 1 << 30));
         for (int set = 0; set < 2; set++) {
@@ -1915,7 +1915,7 @@ void enqueue_run(Forest &f, int k) {
 // TUNE_MAX_MOONLETS moonlets (and again when its size has changed more than
 // fourfold) each candidate lays the forest out and times two steps from the
 // same state; the fastest is kept.  The candidates are around the default
-// for p (32, 48, 64 for p <= 3, <= 5, 6).  A configured leaf size disables
+// for p (32 for p <= 3, else 64).  A configured leaf size disables
 // the tuner, as does NCORP_AUTOTUNE=0.
 constexpr int64_t TUNE_MIN_MOONLETS = 1 << 15, TUNE_MAX_MOONLETS = 1 << 22;
 
@@ -1926,7 +1926,7 @@ bool needs_tuning(const ncorp_batch *b, const Forest &f) {
 }
 
 int tune_forest(ncorp_batch *b, Forest &f) {
-    const int base = f.p <= 3 ? 32 : (f.p <= 5 ? 48 : 64);
+    const int base = f.p <= 3 ? 32 : 64;
     const int cand[4] = {base / 2, (3 * base) / 4, base, (3 * base) / 2};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     NCORP_CUDA_CHECK(cudaEventCreate(&e0));
