@@ -65,6 +65,8 @@ def parse():
                          "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="serving: length of the arrival window")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
+    ap.add_argument("--serve-pool", type=int, default=600,
+                    help="serving: distinct initial disks (later requests reuse them; 0: one per request)")
     ap.add_argument("--tick-steps", type=int, default=10, help="serving: most steps per ncorp_batch_run")
     ap.add_argument("--steps4", type=int, default=50, help="default run: steps of the 64-disk ensemble")
     return ap.parse_args()
@@ -657,9 +659,14 @@ def run_serving(a):
     torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
     from paper_2310_20374_gb300 import diskgen, serving
     reqs = serving.poisson_requests(a.serve_rate, a.serve_seconds, 1e3, 1e6, (3, 4, 6), 100, seed=500 + rank)
-    # inputs are generated before the clock starts (they stand in for requests already in host memory)
+    # inputs are generated before the clock starts (they stand in for requests already in host memory); a
+    # long window reuses the disks of its first --serve-pool requests (request k starts from disk k mod pool,
+    # with that disk's N), so the host holds a bounded number of initial states
+    pool = len(reqs) if a.serve_pool <= 0 else min(len(reqs), a.serve_pool)
+    disks = [diskgen.make_disk(r.n, 700 + 1000 * rank + k) for k, r in enumerate(reqs[:pool])]
     for k, r in enumerate(reqs):
-        r.disk = diskgen.make_disk(r.n, 700 + 1000 * rank + k)
+        r.disk = disks[k % pool]
+        r.n = len(r.disk["pos"])
     stream = torch.cuda.current_stream()
     free_b, _ = torch.cuda.mem_get_info()
     b = ncorp.ncorp_batch_create(cfg, int(0.8 * free_b), stream.cuda_stream)   # admission: 80% of free HBM
@@ -680,7 +687,8 @@ def run_serving(a):
            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
            "data": "synthetic (seeded moonlet disks shaped like the paper's)",
            "config": {"workload": f"serving: Poisson arrivals at {a.serve_rate}/s for {a.serve_seconds} s "
-                                  f"({len(reqs)} disks), N log-uniform in [1e3, 1e6], p in {{3,4,6}}, "
+                                  f"({len(reqs)} disks, {pool} distinct initial states), N log-uniform in "
+                                  f"[1e3, 1e6], p in {{3,4,6}}, "
                                   f"theta_min={a.theta}, 100 SBAB1 steps each, dt={a.dt}, {a.precision} precision, "
                                   f"up to {a.tick_steps} steps per tick",
                       "requests": st["requests"], "served": st["served"], "moonlet_steps": st["moonlet_steps"],
