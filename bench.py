@@ -529,7 +529,7 @@ def run_reference(a):
     # bounded sample: a disk small enough that warmup + steps end within ~2 minutes
     per_particle_s = 6e-5
     n = int(min(a.n, max(2000, 120.0 / (per_particle_s * (a.steps + max(a.warmup, 3) + 1)))))
-    cfgd = workload_config(a, n=n)
+    cfgd = workload_config(a, n=n, precision="fp64 (the plain-C oracle)")
     d = diskgen.make_disk(n, a.seed)
     import copy
     b = copy.copy(a)

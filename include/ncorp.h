@@ -384,8 +384,11 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
  * its state at the start of the run one synchronous step at a time with
  * grown buffers (counted in NCORP_BATCH_FALLBACKS).  The colliding pairs of
  * each disk's last step are kept for ncorp_batch_collisions.  Errors:
- * NCORP_EINVAL (n_steps < 0, non-finite state), NCORP_ECUDA, NCORP_ENOMEM,
- * NCORP_ETIMEOUT, NCORP_EOVERFLOW. */
+ * NCORP_EINVAL (n_steps < 0, non-finite state), NCORP_ECUDA, NCORP_ENOMEM
+ * (a forest could not be laid out in device memory: no disk was stepped, and
+ * the run can be retried after removing disks), NCORP_ETIMEOUT,
+ * NCORP_EOVERFLOW (also when the rerun of an overflowed forest could not
+ * grow its buffers; the other forests have then taken their steps). */
 int ncorp_batch_run(ncorp_batch *b, int n_steps);
 
 /* Copies a disk's current state, in the order it was given, into

@@ -2248,7 +2248,9 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
                         c->have_state = false;
                         c->tree_valid = false;
                         st = ncorp_step(c, f->pos, f->vel, f->m, f->R, f->n, f->p, f->theta, f->dt);
-                        if (st != NCORP_OK) return batch_fail(b, st, "validation step: %s", ncorp_last_error(c));
+                        if (st != NCORP_OK)
+                            return batch_fail(b, st == NCORP_ENOMEM ? NCORP_EOVERFLOW : st, "validation step: %s",
+                                              ncorp_last_error(c));
                         f->synced = true;
                         f->n_found = c->n_found;
                     } else {
@@ -2323,8 +2325,9 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
             const int st = ncorp_step(c, f->pos, f->vel, f->m, f->R, f->n, f->p, f->theta, f->dt);
             if (st != NCORP_OK) {
                 f->primed = false;
-                return batch_fail(b, st, "forest of %zu disks (p = %d): %s", f->disks.size(), f->p,
-                                  ncorp_last_error(c));
+                // (NCORP_ENOMEM is kept for runs that stepped nothing: here other forests have run)
+                return batch_fail(b, st == NCORP_ENOMEM ? NCORP_EOVERFLOW : st, "forest of %zu disks (p = %d): %s",
+                                  f->disks.size(), f->p, ncorp_last_error(c));
             }
             b->launches += c->launches;
         }

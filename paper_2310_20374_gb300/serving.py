@@ -10,7 +10,11 @@ forest, one launch per stage), and repeats ticks:
      NCORP_ENOMEM when it does not fit; the request then waits, and so do
      the ones behind it, until a disk leaves);
   2. advance all resident disks by k steps in one ncorp_batch_run, k = the
-     tick length, shortened so that no disk runs past its request;
+     tick length, shortened so that no disk runs past its request; if the
+     run cannot lay out its disks in device memory (it then steps none of
+     them), the requests admitted at this tick leave the batch again, newest
+     first, until it fits, go back to the head of the queue, and admission
+     pauses until a disk finishes;
   3. hand every finished disk's final state to the caller and remove it.
 
 Requests that arrive while others are on the GPU join at the next tick, so
@@ -71,10 +75,19 @@ class BatchBackend:
             raise
 
     def run(self, k: int) -> None:
-        self.ncorp.ncorp_batch_run(self.b, k)
+        try:
+            self.ncorp.ncorp_batch_run(self.b, k)
+        except self.ncorp.NcorpError as e:
+            if e.code == self.ncorp.NCORP_ENOMEM:   # no disk was stepped
+                raise BudgetFull(str(e)) from None
+            raise
         info = self.ncorp.ncorp_batch_info(self.b)
         self.peak_bytes = max(getattr(self, "peak_bytes", 0), info["bytes"])
         self.peak_moonlets = max(getattr(self, "peak_moonlets", 0), info["moonlets"])
+
+    def evict(self, req: Request) -> None:
+        """Removes a disk that has not been stepped (it goes back to the queue)."""
+        self.ncorp.ncorp_batch_remove_disk(self.b, req.disk_id)
 
     def finish(self, req: Request, out=None) -> None:
         """Removes the disk; with out = (positions, velocities) its final state is copied there first."""
@@ -97,10 +110,14 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
     step_ms = []          # (value, weight): per disk-step
     concurrent = []
     start = clock()
+    hold = False          # admission paused after a run did not fit, until a disk finishes
+    solo = False          # a run did not fit with only fresh disks: admit one at a time
     while waiting or active:
         now = clock() - start
         # 1. admission, in arrival order
-        while waiting and waiting[0].arrival <= now and (max_wall is None or now <= max_wall):
+        while not hold and waiting and waiting[0].arrival <= now and (max_wall is None or now <= max_wall):
+            if solo and active:
+                break
             r = waiting[0]
             try:
                 r.disk_id = backend.add(r)
@@ -121,7 +138,29 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
         # 2. one tick
         k = min(tick_steps, min(r.steps_left for r in active.values()))
         t0 = clock()
-        backend.run(k)
+        while True:
+            try:
+                backend.run(k)
+                break
+            except BudgetFull:
+                fresh = [r for r in active.values() if r.steps_left == r.steps]   # admitted at this tick
+                if not fresh:
+                    raise
+                if solo and len(active) == 1:
+                    raise RuntimeError(f"a disk of {fresh[0].n} moonlets does not fit the device on its own")
+                r = max(fresh, key=lambda q: (q.admitted, q.arrival))
+                backend.evict(r)
+                del active[r.disk_id]
+                r.disk_id, r.admitted = None, None
+                # back to the head of the queue, ahead of the later arrivals
+                waiting.appendleft(r)
+                hold = True
+                if not active:   # nothing left to run: admit the evicted ones again, one at a time
+                    hold, solo = False, True
+                    break
+        if not active:
+            continue
+        solo = False
         t1 = clock()
         moonlets = sum(r.n for r in active.values())
         ticks.append((t0 - start, t1 - start, k, moonlets, len(active)))
@@ -135,6 +174,7 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
                 out = on_done(r) if on_done else None
                 backend.finish(r, out)
                 del active[did]
+                hold = False
     wall = clock() - start
     return summarize(reqs, ticks, step_ms, concurrent, wall)
 

@@ -53,6 +53,11 @@ class FakeBatch:
             v[1] += k
         self.max_disks = max(self.max_disks, len(self.disks))
 
+    def evict(self, req):
+        r, done = self.disks.pop(req.disk_id)
+        assert r is req and done == 0        # only disks that were never stepped go back to the queue
+        self.used -= self.bpm * req.n
+
     def finish(self, req, out=None):
         r, done = self.disks.pop(req.disk_id)
         assert r is req and done == req.steps   # exactly the steps asked for, never more
@@ -124,3 +129,35 @@ def test_admission_stops_at_the_end_of_the_window():
     st, _ = run(reqs, tick_steps=10, max_wall=3.0)
     assert 0 < st["served"] < len(reqs)
     assert all(r.admitted is None or r.admitted <= 3.0 + 1e-9 for r in reqs)
+
+
+class TightBatch(FakeBatch):
+    """A fake batch whose runs fail (stepping nothing) while its disks hold more than `run_limit`, as a
+    real batch does when it cannot lay out its forests in device memory."""
+
+    def __init__(self, clock, run_limit, **kw):
+        super().__init__(clock, **kw)
+        self.run_limit, self.failed_runs = run_limit, 0
+
+    def run(self, k):
+        if self.used > self.run_limit:
+            self.failed_runs += 1
+            raise serving.BudgetFull("run")
+        super().run(k)
+
+
+def test_a_run_that_does_not_fit_sends_the_newest_admissions_back():
+    clock = Clock()
+    reqs = [serving.Request(arrival=0.0, n=1000, p=3, steps=20) for i in range(8)]
+    fb = TightBatch(clock, run_limit=1000 * 1000 * 3)   # three disks fit a run, more are admitted
+    st = serving.serve(fb, reqs, tick_steps=5, clock=clock, sleep=clock.sleep)
+    assert st["served"] == len(reqs) and fb.failed_runs > 0   # finish() checked the exact step counts
+    assert fb.max_disks <= 3
+    assert all(r.done > r.admitted >= r.arrival for r in reqs)
+
+
+def test_a_disk_that_no_run_fits_is_an_error():
+    clock = Clock()
+    fb = TightBatch(clock, run_limit=10)
+    with pytest.raises(RuntimeError, match="on its own"):
+        serving.serve(fb, [serving.Request(arrival=0.0, n=1000, p=3, steps=5)], clock=clock, sleep=clock.sleep)
