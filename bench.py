@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--leaf-size", type=int, default=0, help="disk: leaf size s (0: the default for p)")
+    ap.add_argument("--thresholds", default="", help="disk: N_cs,N_cc_pre,N_cc_post of the gravity walk at --p")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--resolve-f", type=float, default=0.0,
                     help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
@@ -150,8 +151,45 @@ def leaf_size_for(p):
     return 64 if p >= 4 else 32
 
 
+THRESHOLDS_OVERRIDE = {}   # p -> [N_cs, N_cc,pre, N_cc,post] given with --thresholds
+
+
 def thresholds_for(p):
+    if p in THRESHOLDS_OVERRIDE:
+        return list(THRESHOLDS_OVERRIDE[p])
     return [256, 256, 512] if p >= 6 else [64, 8, 64]
+
+
+def direct_sample_errors(pos, mass, acc_mutual, k=1000, seed=0):
+    """Median and 99th percentile over a seeded sample of k moonlets of |a - a_direct| / |a_direct|, the
+    mutual accelerations against FP64 direct summation (G = 1; coincident pairs contribute nothing)."""
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(pos), size=min(k, len(pos)), replace=False)
+    ref = np.zeros((len(idx), 3))
+    for j0 in range(0, len(pos), 20000):
+        src, m = pos[j0:j0 + 20000], mass[j0:j0 + 20000]
+        d = src[None, :, :] - pos[idx][:, None, :]
+        r2 = np.einsum("ijk,ijk->ij", d, d)
+        with np.errstate(divide="ignore"):
+            w = np.where(r2 > 0.0, m[None, :] / (r2 * np.sqrt(r2)), 0.0)
+        ref += np.einsum("ij,ijk->ik", w, d)
+    err = np.linalg.norm(acc_mutual[idx] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return {"median": float(np.median(err)), "p99": float(np.percentile(err, 99)), "sample": int(len(idx)),
+            "note": "mutual accelerations (ncorp_accel) against FP64 direct summation on a seeded sample"}
+
+
+def measure_accuracy(ncorp, d, n, p, theta, precision, local, stream):
+    cfg = ncorp.ncorp_config_default()
+    cfg.precision = ncorp.NCORP_MIXED if precision == "mixed" else ncorp.NCORP_FP64
+    cfg.leaf_size = leaf_size_for(p)
+    cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = thresholds_for(p)
+    ctx = ncorp.ncorp_init(cfg, n, local, stream.cuda_stream)
+    try:
+        acc, mut = np.zeros((n, 3)), np.zeros((n, 3))
+        ncorp.ncorp_accel(ctx, d["pos"], d["mass"], n, p, theta, acc, mut)
+    finally:
+        ncorp.ncorp_free(ctx)
+    return direct_sample_errors(d["pos"], d["mass"], mut)
 
 
 def workload_config(a, n=None, seed=None, p=None, theta=None, precision=None):
@@ -399,6 +437,13 @@ def run_gpu(a):
         # ---- workload 4: 64 disks of mixed size in one batch, 50 steps replayed from one graph
         extra["config4"] = time_ensemble(a, ncorp, torch, dist, world, rank, stream, a.steps4, 3)
     clocks = sampler.stop()
+    # ---- accuracy of the headline disk's mutual accelerations against direct summation (rank 0)
+    accuracy = {}
+    if rank == 0:
+        accuracy[a.precision] = measure_accuracy(ncorp, d, a.n, a.p, a.theta, a.precision, local, stream)
+        if not a.headline_only:
+            other = "fp64" if a.precision == "mixed" else "mixed"
+            accuracy[other] = measure_accuracy(ncorp, d, a.n, a.p, a.theta, other, local, stream)
 
     # ---- end to end through the C ABI with pinned host buffers: every step
     # copies the state in (positions, velocities, masses, radii), runs the step
@@ -443,7 +488,7 @@ def run_gpu(a):
            "tree_stats_last_step": head["tree_stats_last_step"],
            "stage_ms_per_step": head["stage_ms_per_step"], "stage_note": head["stage_note"],
            "clocks": clocks, "e2e": e2e, "roofline": roofline, "peaks": peaks,
-           "stage_roofline": head["stage_roofline"],
+           "stage_roofline": head["stage_roofline"], "accuracy": accuracy,
            "stage_roofline_note": "per stage of one step against the measured HBM copy bandwidth or the measured "
                                   "FMA peak of the stage's precision; at N = 1e5 the working set (~20 MB) stays "
                                   "in L2, and walk/descend are latency-bound chains",
@@ -782,6 +827,8 @@ def run_standard(a):
 
 def main():
     a = parse()
+    if a.thresholds:
+        THRESHOLDS_OVERRIDE[a.p] = [int(v) for v in a.thresholds.split(",")]
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "ensemble":
