@@ -714,7 +714,7 @@ def run_serving(a):
         r.n = len(r.disk["pos"])
     stream = torch.cuda.current_stream()
     free_b, _ = torch.cuda.mem_get_info()
-    b = ncorp.ncorp_batch_create(cfg, int(0.8 * free_b), stream.cuda_stream)   # admission: 80% of free HBM
+    b = ncorp.ncorp_batch_create(cfg, int(0.7 * free_b), stream.cuda_stream)   # admission: 70% of free HBM
     sampler = ClockSampler(physical_gpu_index(local))
     try:
         # each finished disk's state goes back to host memory (what a client receives)
@@ -747,7 +747,7 @@ def run_serving(a):
                        "/ k, one sample per disk and step; request = arrival to last step, admission wait included"},
            "peak_batch_bytes": getattr(backend, "peak_bytes", None),
            "peak_resident_moonlets": getattr(backend, "peak_moonlets", None),
-           "hbm_budget_bytes": int(0.8 * free_b),
+           "hbm_budget_bytes": int(0.7 * free_b),
            "concurrent_disks_mean": round(st["concurrent_disks_mean"], 2),
            "concurrent_disks_max": st["concurrent_disks_max"],
            "busy_throughput": round(st["busy_throughput"], 1),

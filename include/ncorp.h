@@ -370,7 +370,8 @@ int ncorp_batch_create(ncorp_batch **out, const ncorp_config *cfg, size_t hbm_bu
  * the next ncorp_batch_run (one force evaluation for all the disks added or
  * removed since the last run).  Admission by device memory: the disk is
  * refused when the bytes the batch holds plus 1.5 n times the largest
- * footprint per moonlet measured so far (4096 bytes before any measurement)
+ * footprint per moonlet measured so far (4096 bytes before any measurement;
+ * measured on forests of at least 65536 moonlets whose layout succeeded)
  * exceed the budget, or exceed the device memory still free.  *disk_id
  * receives the disk's id (unique within the batch).  Errors: NCORP_EINVAL
  * (arguments, non-finite positions or velocities), NCORP_ENOMEM (allocation

@@ -1794,7 +1794,9 @@ int prime_forest(ncorp_batch *b, Forest &f) {
     }
     const size_t free1 = free_bytes();
     if (free0 > free1) f.ctx_bytes += free0 - free1;
-    if (f.n >= BATCH_MEASURE_MIN) {   // large enough that the fixed minimum capacities do not dominate
+    // footprint per moonlet, from layouts that succeeded (a failed one held whatever it had grabbed) and
+    // forests large enough that the fixed minimum capacities do not dominate
+    if (status == NCORP_OK && f.n >= BATCH_MEASURE_MIN) {
         const double per = static_cast<double>(f.ctx_bytes + array_bytes(f)) / static_cast<double>(f.n);
         b->bytes_per_moonlet = b->measured ? std::max(b->bytes_per_moonlet, per) : per;
         b->measured = true;

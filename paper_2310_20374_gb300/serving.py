@@ -121,9 +121,9 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
             r = waiting[0]
             try:
                 r.disk_id = backend.add(r)
-            except BudgetFull:
+            except BudgetFull as e:
                 if not active:
-                    raise RuntimeError(f"a disk of {r.n} moonlets does not fit the batch's budget on its own")
+                    raise RuntimeError(f"a disk of {r.n} moonlets does not fit the batch's budget on its own: {e}")
                 break
             waiting.popleft()
             r.admitted = clock() - start
