@@ -88,6 +88,16 @@ typedef struct {
                                  (ncorp_accel_standard, Algorithm StandardTree, Sect. 3.4.4); >= 0 */
     int c_cb_pre, c_cb_post;  /* the same thresholds for the standard tree code's collision search
                                  (ncorp_collide_standard); >= 0 */
+    int fused_walk;           /* 1: one tree walk per ncorp_step for gravity and collisions (Algorithm
+                                 TreeWalk with both criteria; Sect. 3.4.1: one tree per step).  The walk
+                                 of the new tree x_{n+1} also collects the leaf pairs that the next
+                                 step's collision search (at x_{n+1}, v_{n+3/2}) tests, with the collision
+                                 geometry of a bound on each moonlet's R + dt |v_{n+3/2}| made from
+                                 v_{n+1/2} + dt a_n and a margin of dt^2 |a_n| / 2.  The next step checks
+                                 every bound against the true velocity; if one is exceeded it searches
+                                 with its own collision walk as usual.  The pair set is the same either
+                                 way (the brute-force one).  Applies to ncorp_step without collision
+                                 resolution; 0 = separate walks (default). */
 } ncorp_config;
 
 /* Fills *cfg with G = 1, M_c = 1, R_c = 1, automatic leaf size and thresholds,
@@ -262,7 +272,9 @@ int ncorp_get_state(ncorp_ctx *ctx, double *positions, double *velocities);
                                        them radix-sorted (at most 65536), 0 radix sort of all keys, -1 radix
                                        sort after the merge found the kept keys out of order */
 #define NCORP_STAT_RESOLVED    18   /* impacts resolved by the last ncorp_step (resolve_f > 0) */
-#define NCORP_NSTATS           19
+#define NCORP_STAT_FUSED       19   /* 1 if the last ncorp_step's collision search tested the pairs listed by
+                                       the previous step's fused walk (fused_walk = 1, no bound exceeded) */
+#define NCORP_NSTATS           20
 
 /* Writes min(n_stats, NCORP_NSTATS) counters of the last call (slots above)
  * to host memory stats[].  NCORP_EINVAL if ctx or stats is NULL. */

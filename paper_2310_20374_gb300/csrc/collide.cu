@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(32 * COL_WARPS, 4) k_collide(CollideArgs A) {
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int ns = min(A.ctl->n_self, A.self_cap), np = min(A.ctl->n_p2p, A.p2p_cap);
+    const int ns = min(A.ctl->n_cself, A.self_cap), np = min(A.ctl->n_cp2p, A.p2p_cap);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     long long tests = 0;
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ns + np; w += nwarps) {
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(32 * COL_WARPS, 4) k_collide(CollideArgs A) {
 void launch_collide(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy, const double *vz,
                     double dt, bool wide) {
     CollideArgs A;
-    A.p2p = c->wl.p2p; A.self = c->wl.self;
+    A.p2p = c->wl.cp2p; A.self = c->wl.cself;   // the collision walk's lists
     A.first = c->cells.first; A.count = c->cells.count;
     A.x = P.x; A.y = P.y; A.z = P.z; A.vx = vx; A.vy = vy; A.vz = vz; A.R = P.R;
     A.hi4 = P.hi4; A.lo4 = P.lo4; A.cv = c->cv4;

@@ -103,6 +103,8 @@ struct Ctrl {
     int n_m2l_dir;
     int n_p2p_dir;
     unsigned bar_count;
+    unsigned bar_count2;   // grid barriers of the collision climb (it may run beside another cooperative kernel
+                           // of the same tree set)
     unsigned bar_gen;
     int walk_abort[3];     // walk: overflow seen in generation g, slot g mod 3
     long long dec_pairs;   // walk decisions: direct cell pairs
@@ -113,6 +115,12 @@ struct Ctrl {
     long long col_self;    // collision walk: direct self cells
     long long n_m2p;       // standard tree code: moonlet-cell expansions
     int col_iters;         // collision walk: generations
+    int n_cp2p;            // collision walk: leaf pairs to test
+    int n_cself;           // collision walk: leaves to test within
+    long long dec_pairs_c; // collision walk decisions: direct cell pairs
+    long long dec_self_c;  // collision walk decisions: direct self cells
+    int col_stale;         // fused walk: a moonlet's R + dt |v| exceeded the bound its tree's collision
+                           // geometry used, so the collision walk is redone
     unsigned long long bbox[6];   // order-preserving encodings of min x,y,z and max x,y,z
     double root[4];        // x_lo, y_lo, z_lo, L
     // Several independent disks in one tree set (a forest): nd roots, cells 0..nd-1; disk d holds the

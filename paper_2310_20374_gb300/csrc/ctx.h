@@ -49,6 +49,8 @@ struct Cells {
     int *blocksum = nullptr;  // per-block scratch of cooperative kernels
     unsigned *done = nullptr; // [cap] descent: epoch in which the cell's complete expansion was written
     int *leaf_of = nullptr;   // [leaf_of_cap] leaf of each moonlet of the tree (tree order)
+    double *rc_spec = nullptr;// [leaf_of_cap] fused walk: each moonlet's R + dt |v| bound the tree's collision
+                              // geometry was computed with (tree order)
     int leaf_of_cap = 0;
 };
 
@@ -63,6 +65,8 @@ struct WalkLists {
     int2 *m2l_dir = nullptr;      // (target, source) grouped by target
     int *p2p_off = nullptr;       // [cap+1] offsets of each target leaf's sources
     int2 *p2p_src = nullptr;      // each directed entry's source leaf as (first moonlet, moonlet count)
+    int2 *cp2p = nullptr;         // collision walk: leaf pairs to test [p2p_cap]
+    int *cself = nullptr;         // collision walk: leaves to test within [self_cap]
 };
 
 // One tree with everything a walk over it produces: cells, walk lists and
@@ -169,6 +173,7 @@ struct ncorp_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t side2 = nullptr;    // stream of the multipoles and the near field inside a gravity evaluation
     cudaEvent_t ev_geo = nullptr, ev_p2m = nullptr, ev_lists = nullptr, ev_near = nullptr;
+    cudaEvent_t ev_spec0 = nullptr, ev_spec = nullptr;   // fused walk: the bounded collision climb beside the geometry
     int *err_acc = nullptr;          // device: error words of tree sets recycled during a call
     int *err_acc_h = nullptr;        // pinned host mirror
 
@@ -216,19 +221,26 @@ void launch_bbox_keys(ncorp_ctx *c, const double *x, const double *y, const doub
 // by_disk: the keys are a forest's moonlet keys (every disk's own root cube); they are sorted by (disk, key)
 void radix_sort_u64(ncorp_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int n,
                     int bits, bool bar_zeroed = false, const int *gate = nullptr, bool by_disk = false);
+// spec_dt > 0 (fused walk): also the bounds on next step's R + dt |v| of the current tree set's moonlets,
+// from src_xv's velocities and src_rest's accelerations
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx, double G, const int *gate = nullptr);
+                   const uint32_t *idx, double G, const int *gate = nullptr, double spec_dt = 0.0);
 void launch_iota(ncorp_ctx *c, uint32_t *idx, int n);
 
 // ---- tree.cu ----
 void launch_build(ncorp_ctx *c, const ParticleSet &P, int n, int s, const int *gate = nullptr);
 void launch_climb_geometry(ncorp_ctx *c, const ParticleSet &P, double G, double theta);
 void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, double G);
+// rc_given (nullable): each moonlet's R + dt |v| given (the velocities are then not read and the pair
+// test's per-moonlet values are not written); gate (nullable): nothing is done while *gate is 0
 void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
-                            const double *vz, double dt);
+                            const double *vz, double dt, const double *rc_given = nullptr,
+                            const int *gate = nullptr);
 
 // ---- walk.cu ----
-void launch_walk(ncorp_ctx *c, bool gravity);
+// gravity / collisions: the criteria walked (both: one traversal for both; the collision pairs go to
+// the cp2p / cself lists); gate (nullable): the walk does nothing while *gate is 0
+void launch_walk(ncorp_ctx *c, bool gravity, bool collisions, const int *gate = nullptr);
 
 // ---- m2l.cu / eval.cu ----
 void launch_m2l(ncorp_ctx *c, int p, bool mixed);
@@ -275,6 +287,11 @@ struct KickDriftArgs {
     double *ox, *oy, *oz, *ovx, *ovy, *ovz;
     int n;
     Ctrl *ctl;
+    // fused walk (nullable rc_spec): every moonlet's R + dt |v'| is checked against rc_spec (set *stale
+    // if one exceeds it) and written, with v' in FP32, into cv4 for the pair test
+    const double *R, *rc_spec;
+    int *stale;
+    float4 *cv4;
 };
 void launch_kick_drift(ncorp_ctx *c, const KickDriftArgs &A);
 void launch_scatter_state(ncorp_ctx *c, const ParticleSet &S, double *pos, double *vel, int n,

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
         return;
     }
     if (threadIdx.x == 0) s_bad = 0;
+    bool over = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
         const double vx = dadd(A.vx[i], dmul(A.h, A.ax[i]));
         const double vy = dadd(A.vy[i], dmul(A.h, A.ay[i]));
@@ -83,6 +84,12 @@ __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
         A.ovx[i] = vx;
         A.ovy[i] = vy;
         A.ovz[i] = vz;
+        if (A.rc_spec) {   // fused walk: this step's R + dt |v| against the bound the tree was walked with
+            const double e = dadd(A.R[i], dmul(A.dt, dnorm3(vx, vy, vz)));
+            over |= !(e <= A.rc_spec[i]);
+            A.cv4[i] = make_float4(static_cast<float>(vx), static_cast<float>(vy), static_cast<float>(vz),
+                                   __double2float_ru(e));
+        }
         const double v[3] = {dadd(A.x[i], dmul(A.dt, vx)), dadd(A.y[i], dmul(A.dt, vy)), dadd(A.z[i], dmul(A.dt, vz))};
         A.ox[i] = v[0];
         A.oy[i] = v[1];
@@ -96,6 +103,7 @@ __global__ void __launch_bounds__(256) k_kick_drift(KickDriftArgs A) {
             hi[k] = e > hi[k] ? e : hi[k];
         }
     }
+    if (over) atomicOr(A.stale, 1);
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll

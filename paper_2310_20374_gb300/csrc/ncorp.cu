@@ -172,6 +172,8 @@ void alloc_lists(ncorp_ctx *c, int front, int m2l, int p2p, int self) {
         dalloc(W.p2p, p2p);
         dalloc(W.self, self);
         dalloc(W.p2p_src, 2 * static_cast<size_t>(p2p) + self);   // int2
+        dalloc(W.cp2p, p2p);
+        dalloc(W.cself, self);
         W.p2p_cap = p2p;
         W.self_cap = self;
         W.p2p_dir_cap = 2 * p2p + self;
@@ -217,6 +219,7 @@ void ensure_tree_capacity(ncorp_ctx *c, int n) {
     if (c->cells.leaf_of_cap < n) {
         c->cells.leaf_of_cap = 0;
         dalloc(c->cells.leaf_of, static_cast<size_t>(n));
+        dalloc(c->cells.rc_spec, static_cast<size_t>(n));
         c->cells.leaf_of_cap = n;
     }
     const int cc = c->cells.cap;
@@ -551,8 +554,11 @@ int finish(ncorp_ctx *c, bool both = false) {
 // near_sorted: the positions are in the previous tree order of nearby
 // positions (a drift), so the keys are nearly sorted.
 // gate (nullable, radix sort only): every kernel does nothing while *gate is 0.
+// spec_dt > 0 (fused walk): the gather also bounds every moonlet's next R + dt |v| (velocities of sv,
+// accelerations of sr)
 void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, const ParticleSet &sr, ParticleSet &dst,
-                int n, bool near_sorted = false, bool bbox_done = false, const int *gate = nullptr) {
+                int n, bool near_sorted = false, bool bbox_done = false, const int *gate = nullptr,
+                double spec_dt = 0.0) {
     c->cur_n = n;
     {
         Stage st(c, NCORP_STAGE_SORT);
@@ -564,7 +570,7 @@ void build_tree(ncorp_ctx *c, const ParticleSet &sx, const ParticleSet &sv, cons
         view.x = sx.x; view.y = sx.y; view.z = sx.z;
         view.vx = sv.vx; view.vy = sv.vy; view.vz = sv.vz;
         view.qx = c->B.qx; view.qy = c->B.qy; view.qz = c->B.qz;
-        launch_gather(c, view, view, dst, n, c->idx, c->cfg.G, gate);
+        launch_gather(c, view, view, dst, n, c->idx, c->cfg.G, gate, spec_dt);
     }
     Stage st(c, NCORP_STAGE_BUILD);
     launch_build(c, dst, n, c->s, gate);
@@ -590,12 +596,34 @@ void on_stream(ncorp_ctx *c, cudaStream_t s, F body) {
 // walk, then the near field (which needs only the lists) beside M2L and the
 // descent.
 // kick_h != 0: the evaluation also applies the closing half kick v += kick_h a.
-void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual, double kick_h = 0.0) {
+// fused_dt > 0 (fused walk): the walk also collects the collision pairs of the next step, with the
+// collision geometry of the bounds the gather wrote (its climb runs on the second stream beside the
+// gravity geometry).
+void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool want_mutual, double kick_h = 0.0,
+             double fused_dt = 0.0) {
     const bool mixed = c->cfg.precision == NCORP_MIXED;
     const double G = c->cfg.G;
+    const bool fused = fused_dt > 0.0;
     c->grav_p = p;
     c->grav_mixed = mixed;
     c->grav_local = true;
+    if (fused) {
+        NCORP_CUDA_CHECK(cudaEventRecord(c->ev_spec0, c->stream));
+        NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_spec0, 0));
+        const int cap = c->coop_max;
+        c->coop_max = cap > 0 ? std::min(cap, c->side_blocks) : c->side_blocks;   // beside the geometry
+        try {
+            on_stream(c, c->side2, [&] {
+                Stage st(c, NCORP_STAGE_COLLIDE);
+                launch_climb_collision(c, S, S.vx, S.vy, S.vz, fused_dt, c->cells.rc_spec);
+                NCORP_CUDA_CHECK(cudaEventRecord(c->ev_spec, c->stream));
+            });
+        } catch (...) {
+            c->coop_max = cap;
+            throw;
+        }
+        c->coop_max = cap;
+    }
     { Stage st(c, NCORP_STAGE_CLIMB); launch_climb_geometry(c, S, G, theta); }
     NCORP_CUDA_CHECK(cudaEventRecord(c->ev_geo, c->stream));
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_geo, 0));
@@ -604,7 +632,8 @@ void gravity(ncorp_ctx *c, ParticleSet &S, int p, double theta, double t, bool w
         launch_multipoles(c, S, p, mixed, G);
         NCORP_CUDA_CHECK(cudaEventRecord(c->ev_p2m, c->stream));
     });
-    { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true); }
+    if (fused) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_spec, 0));
+    { Stage st(c, NCORP_STAGE_WALK); launch_walk(c, true, fused); }
     NCORP_CUDA_CHECK(cudaEventRecord(c->ev_lists, c->stream));
     NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->side2, c->ev_lists, 0));
     on_stream(c, c->side2, [&] {
@@ -634,11 +663,13 @@ void gravity_standard(ncorp_ctx *c, ParticleSet &S, int n, int p, double theta, 
 }
 
 // wide: nothing else runs on the device meanwhile (the pair test takes every SM)
+// gate (nullable): the climb and the walk run only while *gate is set (fused walk: the pairs to test
+// are already listed unless a bound was exceeded); the pair test always runs
 void collisions(ncorp_ctx *c, const ParticleSet &S, const double *vx, const double *vy, const double *vz, double dt,
-                bool wide) {
+                bool wide, const int *gate = nullptr) {
     Stage st(c, NCORP_STAGE_COLLIDE);
-    launch_climb_collision(c, S, vx, vy, vz, dt);
-    launch_walk(c, false);
+    launch_climb_collision(c, S, vx, vy, vz, dt, nullptr, gate);
+    launch_walk(c, false, true, gate);
     launch_collide(c, S, vx, vy, vz, dt, wide);
 }
 
@@ -671,6 +702,11 @@ void collisions_standard(ncorp_ctx *c, const ParticleSet &S, int n, double dt) {
 void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overlap) {
     const double h = 0.5 * dt;
     ParticleSet &A = c->A, &B = c->B, &Cn = c->Cset;
+    const bool resolve = c->cfg.collisions && c->cfg.resolve_f > 0.0;
+    const bool side = overlap && c->cfg.collisions;
+    // fused walk: A's tree set lists the pairs to test unless its bounds were exceeded (or never made:
+    // a tree set whose last walk was not a fused one is marked stale)
+    const bool fused = c->cfg.fused_walk && side && !resolve && c->nd == 1;
     // the other tree set becomes the new tree's: cleared (its errors kept) before the kick-drift
     // kernel folds the drifted positions' bounding box into its control block.  It also takes over
     // the abort bits of A's tree: if A's acceleration was never computed (an overflow in the same
@@ -685,10 +721,12 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         K.ox = B.x; K.oy = B.y; K.oz = B.z; K.ovx = B.vx; K.ovy = B.vy; K.ovz = B.vz;
         K.n = n;
         K.ctl = c->alt.ctl;
+        K.R = A.R;
+        K.rc_spec = fused ? c->cells.rc_spec : nullptr;
+        K.stale = &c->ctl->col_stale;
+        K.cv4 = c->cv4;
         launch_kick_drift(c, K);
     }
-    const bool resolve = c->cfg.collisions && c->cfg.resolve_f > 0.0;
-    const bool side = overlap && c->cfg.collisions;
     if (c->cfg.collisions) {
         if (side) {
             cudaStream_t main = c->stream;
@@ -698,7 +736,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
             c->stream = c->side;
             c->coop_max = cap > 0 ? std::min(cap, c->side_blocks) : c->side_blocks;
             try {
-                collisions(c, A, B.vx, B.vy, B.vz, dt, false);
+                collisions(c, A, B.vx, B.vy, B.vz, dt, false, fused ? &c->ctl->col_stale : nullptr);
                 if (resolve) launch_resolve(c, A, B, n, dt);   // may rewrite the drift the main stream reads
                 NCORP_CUDA_CHECK(cudaEventRecord(c->ev_join, c->side));
             } catch (...) {
@@ -719,7 +757,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         }
     }
     swap_sets(c);
-    build_tree(c, B, B, A, Cn, n, true, true);
+    build_tree(c, B, B, A, Cn, n, true, true, nullptr, fused ? dt : 0.0);
     if (side && resolve) {
         // The tree above was built beside the search from the unresolved drift.  A step that resolved an
         // impact builds it again from the resolved one; otherwise these launches return at once.
@@ -731,7 +769,7 @@ void enqueue_kdk(ncorp_ctx *c, int n, int p, double theta, double dt, bool overl
         }
         build_tree(c, B, B, A, Cn, n, false, true, moved);
     }
-    gravity(c, Cn, p, theta, c->time + dt, false, h);   // with the closing half kick
+    gravity(c, Cn, p, theta, c->time + dt, false, h, fused ? dt : 0.0);   // with the closing half kick
     if (side && !resolve) NCORP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
 }
 
@@ -755,6 +793,7 @@ void record_stats(ncorp_ctx *c, bool grav, const Ctrl *col = nullptr) {
         c->stats[NCORP_STAT_M2L_DIRECTED] = h.n_m2l_dir;
         c->stats[NCORP_STAT_P2P_DIRECTED] = h.n_p2p_dir;
     }
+    c->stats[NCORP_STAT_FUSED] = (c->cfg.fused_walk && c->cfg.collisions && col && !hc.col_stale) ? 1 : 0;
     if (!grav || c->cfg.collisions) {
         c->stats[NCORP_STAT_COL_PAIRS] = hc.col_pairs;
         c->stats[NCORP_STAT_COL_SELF] = hc.col_self;
@@ -961,6 +1000,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
             std::memset(c->ctl_h, 0, sizeof(Ctrl));
             c->ctl_h->wait_ns = wait_ns;
             c->ctl_h->nd = 1;   // one disk: its box and root cube are the control block's own
+            c->ctl_h->col_stale = 1;   // no fused walk has listed this tree set's collision pairs
             c->ctl_h->dbox = c->ctl->bbox;
             c->ctl_h->droot = c->ctl->root;
             NCORP_CUDA_CHECK(cudaMemcpy(c->ctl, c->ctl_h, sizeof(Ctrl), cudaMemcpyHostToDevice));
@@ -979,7 +1019,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         NCORP_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         NCORP_CUDA_CHECK(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, least));
-        for (cudaEvent_t *e : {&c->ev_geo, &c->ev_p2m, &c->ev_lists, &c->ev_near})
+        for (cudaEvent_t *e : {&c->ev_geo, &c->ev_p2m, &c->ev_lists, &c->ev_near, &c->ev_spec0, &c->ev_spec})
             NCORP_CUDA_CHECK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         ensure_particles(c, n_max);
         choose_parameters(c, 6);
@@ -1493,10 +1533,11 @@ void ncorp_free(ncorp_ctx *c) {
         dfree(C.arrive); dfree(C.arrive_m); dfree(C.cx); dfree(C.cy); dfree(C.cz); dfree(C.M); dfree(C.sx); dfree(C.sy); dfree(C.sz);
         dfree(C.rmax); dfree(C.rcrit); dfree(C.rho); dfree(C.bx); dfree(C.by); dfree(C.bz); dfree(C.bmax);
         dfree(C.bcrit); dfree(C.gh); dfree(C.gl); dfree(C.bh); dfree(C.bl); dfree(C.Mh); dfree(C.Ch); dfree(C.Cf); dfree(C.Cf_lo); dfree(C.Ch_lo);
-        dfree(C.leaves); dfree(C.leaf_of); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
+        dfree(C.leaves); dfree(C.leaf_of); dfree(C.rc_spec); dfree(C.bounds); dfree(C.blocksum); dfree(C.maker); dfree(C.before); dfree(C.done);
         WalkLists &W = c->wl;
         dfree(W.front[0]); dfree(W.front[1]); dfree(W.front_count); dfree(W.m2l); dfree(W.p2p); dfree(W.self);
         dfree(W.cnt); dfree(W.offs); dfree(W.cursor); dfree(W.m2l_dir); dfree(W.p2p_off); dfree(W.p2p_src);
+        dfree(W.cp2p); dfree(W.cself);
         dfree(c->ctl);
         if (c->ctl_h) cudaFreeHost(c->ctl_h);
         c->ctl_h = nullptr;
@@ -1522,7 +1563,7 @@ void ncorp_free(ncorp_ctx *c) {
         cudaStreamSynchronize(c->side2);
         cudaStreamDestroy(c->side2);
     }
-    for (cudaEvent_t e : {c->ev_geo, c->ev_p2m, c->ev_lists, c->ev_near})
+    for (cudaEvent_t e : {c->ev_geo, c->ev_p2m, c->ev_lists, c->ev_near, c->ev_spec0, c->ev_spec})
         if (e) cudaEventDestroy(e);
     for (StepGraph &g : c->graphs) drop_graph(g);
     if (c->gstream) cudaStreamDestroy(c->gstream);

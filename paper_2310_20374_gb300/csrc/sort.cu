@@ -902,6 +902,11 @@ struct GatherArgs {
     double G;
     int n;
     const int *gate;       // nothing to do while *gate is 0 (null: always)
+    // fused walk (nullable rc_spec): each moonlet's bound R + dt (|v + dt a| + dt |a| / 2) on its R + dt |v|
+    // at the next step, from the source's velocity v and acceleration a, into rc_spec (tree order)
+    const double *ax, *ay, *az;
+    double *rc_spec;
+    double dt;
 };
 
 __global__ void k_gather(GatherArgs g) {
@@ -939,13 +944,22 @@ __global__ void k_gather(GatherArgs g) {
         g.hi4[d] = make_float4(hx, hy, hz, static_cast<float>(g.G * g.m[j]));
         g.lo4[d] = make_float4(static_cast<float>(X - static_cast<double>(hx)), static_cast<float>(Y - static_cast<double>(hy)),
                                static_cast<float>(Z - static_cast<double>(hz)), 0.0f);
+        if (g.rc_spec) {
+            const double ax = g.ax[j], ay = g.ay[j], az = g.az[j];
+            const double sp = dnorm3(dadd(g.vx[j], dmul(g.dt, ax)), dadd(g.vy[j], dmul(g.dt, ay)),
+                                     dadd(g.vz[j], dmul(g.dt, az)));
+            g.rc_spec[d] = dadd(g.R[j], dmul(g.dt, dadd(sp, dmul(0.5 * g.dt, dnorm3(ax, ay, az)))));
+        }
     }
 }
 
 void launch_gather(ncorp_ctx *c, const ParticleSet &src_xv, const ParticleSet &src_rest, ParticleSet &dst, int n,
-                   const uint32_t *idx, double G, const int *gate) {
+                   const uint32_t *idx, double G, const int *gate, double spec_dt) {
     GatherArgs g;
     g.gate = gate;
+    g.rc_spec = spec_dt > 0.0 ? c->cells.rc_spec : nullptr;
+    g.ax = src_rest.ax; g.ay = src_rest.ay; g.az = src_rest.az;
+    g.dt = spec_dt;
     g.x = src_xv.x; g.y = src_xv.y; g.z = src_xv.z;
     g.vx = src_xv.vx; g.vy = src_xv.vy; g.vz = src_xv.vz;
     g.m = src_rest.m; g.R = src_rest.R; g.perm = src_rest.perm;

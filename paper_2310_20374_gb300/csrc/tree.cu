@@ -87,6 +87,7 @@ __global__ void k_build_init(BuildArgs A) {
         A.arrive[d] = 0;     // arrival counters of the collision climb and of the multipoles,
         A.arrive_m[d] = 0;   // zeroed as cells are made
     }
+    A.ctl->col_stale = 1;   // a new tree: no collision pairs listed for it yet
     A.ctl->level_start[0] = 0;
     A.ctl->level_start[1] = nd;
     A.ctl->n_cells = nd;
@@ -410,6 +411,8 @@ struct ClimbArgs {
     Ctrl *ctl;
     double G, dt, theta;
     int cap;
+    const double *rc_given;   // collision climb (nullable): each moonlet's R + dt |v| given (tree order)
+    const int *gate;          // collision climb (nullable): nothing to do while *gate is 0
 };
 
 constexpr int CLIMB_WARPS_COOP = 8;
@@ -982,9 +985,9 @@ void launch_multipoles(ncorp_ctx *c, const ParticleSet &P, int p, bool mixed, do
 // prefilter).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
-    // the grid barrier counter of the parents' cooperative climb that follows on this stream (nothing
-    // else uses this tree set's counter meanwhile)
-    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->bar_count = 0;
+    if (A.gate && *A.gate == 0) return;
+    // the grid barrier counter of the parents' cooperative climb that follows on this stream
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->bar_count2 = 0;
     if (aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31;
     const int n_leaves = A.ctl->n_leaves;
@@ -1001,6 +1004,10 @@ __global__ void __launch_bounds__(64) k_leaf_collision(ClimbArgs A) {
         double d2 = 0.0, ex = 0.0;
         for (int k = L.f + L.q; k < L.f + L.cnt; k += 4) {
             d2 = fmax(d2, dsq3(dsub(A.x[k], sx), dsub(A.y[k], sy), dsub(A.z[k], sz)));
+            if (A.rc_given) {   // bounds given: the pair test's per-moonlet values come later
+                ex = fmax(ex, A.rc_given[k]);
+                continue;
+            }
             const double vx = A.vx[k], vy = A.vy[k], vz = A.vz[k];
             const double e = dadd(A.R[k], dmul(A.dt, dnorm3(vx, vy, vz)));
             ex = fmax(ex, e);
@@ -1101,7 +1108,7 @@ __device__ __forceinline__ void parent_collision_group(const ClimbArgs &A, int c
 // counter).  Four parents per warp, so that one FP64 warp instruction
 // advances four parents.
 __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_climb_collision(ClimbArgs A) {
-    if (aborted(A.ctl)) return;
+    if ((A.gate && *A.gate == 0) || aborted(A.ctl)) return;
     const int lane = threadIdx.x & 31;
     // warps numbered across the blocks first, so that consecutive work items land on different SMs
     const int gw0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1114,12 +1121,12 @@ __global__ void __launch_bounds__(32 * CLIMB_WARPS_COOP) k_climb_collision(Climb
             const int c = (cc < le && A.nchild[cc] > 0) ? cc : -1;
             if (__any_sync(0xffffffffu, c >= 0)) parent_collision_group(A, c, lane);
         }
-        if (lev > 0 && !grid_sync(A.ctl, bar)) return;
+        if (lev > 0 && !grid_sync_on(&A.ctl->bar_count2, A.ctl, bar)) return;
     }
 }
 
 void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx, const double *vy,
-                            const double *vz, double dt) {
+                            const double *vz, double dt, const double *rc_given, const int *gate) {
     Cells &C = c->cells;
     ClimbArgs A{};
     A.x = P.x; A.y = P.y; A.z = P.z; A.R = P.R; A.vx = vx; A.vy = vy; A.vz = vz;
@@ -1128,11 +1135,13 @@ void launch_climb_collision(ncorp_ctx *c, const ParticleSet &P, const double *vx
     A.sx = C.bx; A.sy = C.by; A.sz = C.bz; A.rmax = C.bmax; A.rcrit = C.bcrit;
     A.gh = C.bh; A.gl = C.bl;
     A.leaves = C.leaves; A.ctl = c->ctl; A.dt = dt; A.cv4 = c->cv4;
+    A.rc_given = rc_given;
+    A.gate = gate;
     k_leaf_collision<<<8 * c->num_sms, 64, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
     const int block = 32 * CLIMB_WARPS_COOP;
     const int grid = coop_grid(c, reinterpret_cast<const void *>(k_climb_collision), block, 0);
-    void *args[] = {&A};   // ctl->bar_count was zeroed by k_leaf_collision
+    void *args[] = {&A};   // ctl->bar_count2 was zeroed by k_leaf_collision
     NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_climb_collision), dim3(grid),
                                                  dim3(block), args, 0, c->stream));
     c->launches++;

@@ -22,7 +22,7 @@ NCORP_FP64, NCORP_MIXED = 0, 1
 NCORP_MAX_DISKS = 256
 STAT_NAMES = ["cells", "leaves", "depth", "m2l", "p2p_pairs", "p2p_self", "p2p_interactions", "col_pairs",
               "col_self", "col_tests", "col_found", "walk_iters", "m2l_directed", "p2p_directed", "launches", "col_iters",
-              "graph", "sort_path", "resolved"]
+              "graph", "sort_path", "resolved", "fused"]
 STAGE_NAMES = ["sort", "build", "climb", "walk", "m2l", "descend", "eval", "collide", "kdk", "near"]
 HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "ncorp.h")
 
@@ -40,7 +40,8 @@ class ncorp_config(C.Structure):
                 ("precision", C.c_int), ("collisions", C.c_int),
                 ("star_mass", C.c_double), ("star_a", C.c_double), ("star_obliquity", C.c_double),
                 ("t0", C.c_double), ("central_J2", C.c_double), ("resolve_f", C.c_double),
-                ("n_cb_pre", C.c_int), ("n_cb_post", C.c_int), ("c_cb_pre", C.c_int), ("c_cb_post", C.c_int)]
+                ("n_cb_pre", C.c_int), ("n_cb_post", C.c_int), ("c_cb_pre", C.c_int), ("c_cb_post", C.c_int),
+                ("fused_walk", C.c_int)]
 
 
 _lib = None
