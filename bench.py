@@ -66,6 +66,8 @@ def parse():
                          "serving: disks arriving as a Poisson stream, each integrated for 100 steps")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="serving: length of the arrival window")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
+    ap.add_argument("--serve-budget", type=float, default=0.5,
+                    help="serving: the batch's device-memory budget as a fraction of the free memory at the start")
     ap.add_argument("--serve-pool", type=int, default=600,
                     help="serving: distinct initial disks (later requests reuse them; 0: one per request)")
     ap.add_argument("--tick-steps", type=int, default=10, help="serving: most steps per ncorp_batch_run")
@@ -714,7 +716,8 @@ def run_serving(a):
         r.n = len(r.disk["pos"])
     stream = torch.cuda.current_stream()
     free_b, _ = torch.cuda.mem_get_info()
-    b = ncorp.ncorp_batch_create(cfg, int(0.7 * free_b), stream.cuda_stream)   # admission: 70% of free HBM
+    budget = int(a.serve_budget * free_b)
+    b = ncorp.ncorp_batch_create(cfg, budget, stream.cuda_stream)   # admission: a fraction of free HBM
     sampler = ClockSampler(physical_gpu_index(local))
     try:
         # each finished disk's state goes back to host memory (what a client receives)
@@ -747,7 +750,7 @@ def run_serving(a):
                        "/ k, one sample per disk and step; request = arrival to last step, admission wait included"},
            "peak_batch_bytes": getattr(backend, "peak_bytes", None),
            "peak_resident_moonlets": getattr(backend, "peak_moonlets", None),
-           "hbm_budget_bytes": int(0.7 * free_b),
+           "hbm_budget_bytes": budget,
            "concurrent_disks_mean": round(st["concurrent_disks_mean"], 2),
            "concurrent_disks_max": st["concurrent_disks_max"],
            "busy_throughput": round(st["busy_throughput"], 1),

@@ -1837,8 +1837,11 @@ int prime_forest(ncorp_batch *b, Forest &f) {
     if (free0 > free1) f.ctx_bytes += free0 - free1;
     // footprint per moonlet, from layouts that succeeded (a failed one held whatever it had grabbed) and
     // forests large enough that the fixed minimum capacities do not dominate
+    // per moonlet of the context's capacity (a forest that shrank keeps its context's capacity) plus the
+    // forest's arrays per moonlet
     if (status == NCORP_OK && f.n >= BATCH_MEASURE_MIN) {
-        const double per = static_cast<double>(f.ctx_bytes + array_bytes(f)) / static_cast<double>(f.n);
+        const double per = static_cast<double>(f.ctx_bytes) / static_cast<double>(std::max<int64_t>(f.n, c->n_cap)) +
+                           static_cast<double>(array_bytes(f)) / static_cast<double>(std::max<int64_t>(f.n, f.cap));
         b->bytes_per_moonlet = b->measured ? std::max(b->bytes_per_moonlet, per) : per;
         b->measured = true;
     }

@@ -71,7 +71,7 @@ class BatchBackend:
                                                    self.theta, self.dt)
         except self.ncorp.NcorpError as e:
             if e.code == self.ncorp.NCORP_ENOMEM:
-                raise BudgetFull(str(e)) from None
+                raise BudgetFull(f"{e} (batch: {self.ncorp.ncorp_batch_info(self.b)})") from None
             raise
 
     def run(self, k: int) -> None:
