@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--leaf-size", type=int, default=0, help="disk: leaf size s (0: the default for p)")
     ap.add_argument("--thresholds", default="", help="disk: N_cs,N_cc_pre,N_cc_post of the gravity walk at --p")
+    ap.add_argument("--fused-walk", type=int, default=0, choices=[0, 1],
+                    help="disk: one walk per step for gravity and the next step's collision pairs")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--resolve-f", type=float, default=0.0,
                     help="disk: 0 = colliding pairs reported (default); 1..2 = resolved with this f (Sect. 5)")
@@ -208,7 +210,8 @@ def workload_config(a, n=None, seed=None, p=None, theta=None, precision=None):
             "gravity_thresholds": thresholds_for(p), "collision_thresholds": [12, 0, 16],
             "precision": precision, "l2": "flushed by a 256 MiB device write before every timed step",
             "parallelism": "replicas (one independent disk per GPU)",
-            **({"resolve_f": a.resolve_f} if a.resolve_f else {})}
+            **({"resolve_f": a.resolve_f} if a.resolve_f else {}),
+            **({"fused_walk": 1} if a.fused_walk else {})}
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -294,6 +297,7 @@ def time_disk(a, ncorp, torch, ctx_args, d, n, p, theta, precision, steps, warmu
     cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = thresholds_for(p)
     cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = 12, 0, 16
     cfg.resolve_f = a.resolve_f
+    cfg.fused_walk = a.fused_walk
     ctx = ncorp.ncorp_init(cfg, n, local, stream.cuda_stream)
     pos = torch.tensor(d["pos"], device="cuda")
     vel = torch.tensor(d["vel"], device="cuda")
