@@ -121,15 +121,18 @@ void alloc_cells(ncorp_ctx *c, int cap) {
     dalloc(C.rmax, cap); dalloc(C.rcrit, cap); dalloc(C.rho, cap);
     dalloc(C.bx, cap); dalloc(C.by, cap); dalloc(C.bz, cap); dalloc(C.bmax, cap); dalloc(C.bcrit, cap);
     dalloc(C.gh, cap); dalloc(C.gl, cap); dalloc(C.bh, cap); dalloc(C.bl, cap);
+    // each new buffer is stored as soon as it exists, so that an allocation failing part-way leaves
+    // nothing unowned (ncorp_free releases whatever the context holds)
+    for (void **slot : {&C.Mh, &C.Ch, &C.Cf}) {
+        if (*slot) cudaFree(*slot);
+        *slot = nullptr;
+    }
     double *mh = nullptr, *ch = nullptr, *cf = nullptr;
     dalloc(mh, static_cast<size_t>(cap) * num_m(MAXP));
-    dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
-    dalloc(cf, static_cast<size_t>(cap) * num_c(MAXP));
-    if (C.Mh) cudaFree(C.Mh);
-    if (C.Ch) cudaFree(C.Ch);
-    if (C.Cf) cudaFree(C.Cf);
     C.Mh = mh;
+    dalloc(ch, static_cast<size_t>(cap) * num_c(MAXP));
     C.Ch = ch;
+    dalloc(cf, static_cast<size_t>(cap) * num_c(MAXP));
     C.Cf = cf;
     dalloc(C.leaves, cap);
     dalloc(C.bounds, static_cast<size_t>(cap) * 9);

@@ -263,3 +263,31 @@ def test_batch_rejections():
         ncorp.ncorp_batch_run(b, 3)   # empty batch: nothing to do
     finally:
         ncorp.ncorp_batch_free(b)
+
+
+def test_a_layout_that_runs_out_of_memory_leaves_nothing_behind():
+    """A run whose forest cannot be laid out (device memory taken by another allocation) fails with
+    NCORP_ENOMEM, steps nothing, and releases every buffer it had taken: the device's free memory is
+    the same after the batch is freed, and the run succeeds once memory is available again."""
+    d = diskgen.make_disk(200000, 67)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    b = ncorp.ncorp_batch_create(config(), 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        i = ncorp.ncorp_batch_add_disk(b, d["pos"], d["vel"], d["mass"], d["radius"], len(d["pos"]), 3, 0.5, 1e-3)
+        # leave about 60 MB free: not enough for the forest's context
+        hog = torch.empty(max(0, torch.cuda.mem_get_info()[0] - (60 << 20)), dtype=torch.uint8, device="cuda")
+        with pytest.raises(ncorp.NcorpError) as e:
+            ncorp.ncorp_batch_run(b, 2)
+        assert e.value.code == ncorp.NCORP_ENOMEM
+        pos, vel = np.zeros((len(d["pos"]), 3)), np.zeros((len(d["pos"]), 3))
+        ncorp.ncorp_batch_get_state(b, i, pos, vel)
+        assert np.array_equal(pos, d["pos"]) and np.array_equal(vel, d["vel"])   # nothing was stepped
+        del hog
+        torch.cuda.empty_cache()
+        ncorp.ncorp_batch_run(b, 2)
+    finally:
+        ncorp.ncorp_batch_free(b)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (16 << 20)
