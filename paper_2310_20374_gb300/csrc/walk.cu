@@ -364,6 +364,7 @@ __device__ __forceinline__ bool is_split(int k) { return k >= O_SPLIT_SELF; }
 // The decision statistics are added to the thread's totals st[5] (gravity:
 // direct pairs, direct self cells, moonlet pairs; collisions: direct pairs,
 // direct self cells).
+template <bool GRAV, bool COL>
 __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int nf, long long *st, WalkSlots &S) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int2 *cur = (it & 1) ? A.front1 : A.front0;
@@ -379,8 +380,8 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
             const int2 e = __ldcg(&cur[i]);
             cA = e.x & CELL_MASK;
             cB = e.y & 0x7fffffff;
-            g_act = A.gravity && !(e.x & G_DONE);
-            c_act = A.collisions && !(e.x & C_DONE);
+            g_act = GRAV && !(e.x & G_DONE);
+            c_act = COL && !(e.x & C_DONE);
             g_forced = (e.y & FORCED) != 0;
             c_forced = (e.x & C_FORCED) != 0;
         }
@@ -396,7 +397,7 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
             c0A = __ldg(&A.child0[cA]);
             c0B = __ldg(&A.child0[cB]);
         }
-        if (g_act) {
+        if (GRAV && g_act) {
             ha = __ldg(&A.g.H[cA]);
             hb = __ldg(&A.g.H[cB]);
             la = __ldg(&A.g.Lo[cA]);
@@ -404,7 +405,7 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
             rA = __ldg(&A.g.rcrit[cA]);
             rB = __ldg(&A.g.rcrit[cB]);
         }
-        if (c_act) {
+        if (COL && c_act) {
             ka = __ldg(&A.c.H[cA]);
             kb = __ldg(&A.c.H[cB]);
             ma = __ldg(&A.c.Lo[cA]);
@@ -413,8 +414,8 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
             qB = __ldg(&A.c.rcrit[cB]);
         }
         WalkDec gd{O_NONE, false, 0, 0, 0}, cd{O_NONE, false, 0, 0, 0};
-        if (g_act) gd = walk_decide(A.g, true, cA, cB, g_forced, nA, nB, chA, chB, ha, la, hb, lb, rA, rB);
-        if (c_act) cd = walk_decide(A.c, false, cA, cB, c_forced, nA, nB, chA, chB, ka, ma, kb, mb, qA, qB);
+        if (GRAV && g_act) gd = walk_decide(A.g, true, cA, cB, g_forced, nA, nB, chA, chB, ha, la, hb, lb, rA, rB);
+        if (COL && c_act) cd = walk_decide(A.c, false, cA, cB, c_forced, nA, nB, chA, chB, ka, ma, kb, mb, qA, qB);
         st[0] += gd.dpair;
         st[1] += gd.dself;
         st[2] += gd.inter;
@@ -532,6 +533,7 @@ __device__ __forceinline__ void walk_generation(const WalkArgs &A, int it, int n
     }
 }
 
+template <bool GRAV, bool COL>
 __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs A) {
     __shared__ int s_tmp[33];
     __shared__ WalkSlots S;
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs A) {
         const int nf = min(vcount[it], A.front_cap);
         if (nf == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->walk_abort[(it + 1) % 3] = 0;   // slot of the next generation
-        walk_generation(A, it, nf, st, S);
+        walk_generation<GRAV, COL>(A, it, nf, st, S);
         if (!grid_sync(A.ctl, bar)) return;
         // overflow in this generation (slot it mod 3: identical for every block after the barrier)
         if (((volatile int *)A.ctl->walk_abort)[it % 3]) { it++; break; }
@@ -628,16 +630,17 @@ void launch_walk(ncorp_ctx *c, bool gravity, bool collisions, const int *gate) {
     A.ctl = c->ctl;
     k_walk_init<<<1, 1, 0, c->stream>>>(A); c->launches++;
     NCORP_CUDA_CHECK(cudaGetLastError());
+    const void *kern = gravity && collisions ? reinterpret_cast<const void *>(k_walk<true, true>)
+                     : gravity              ? reinterpret_cast<const void *>(k_walk<true, false>)
+                                            : reinterpret_cast<const void *>(k_walk<false, true>);
     int per_sm = 0;
-    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(k_walk),
-                                                                   WALK_THREADS, 0));
+    NCORP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WALK_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
     // about one block per 640 moonlets (frontiers peak near a third of n pairs), 32 to the cooperative limit
     const int grid = std::min(coop_blocks(c, per_sm), std::max(32, c->cur_n / 640));
     void *args[] = {&A};
-    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_walk), dim3(grid), dim3(WALK_THREADS),
-                                                 args, 0, c->stream));
+    NCORP_CUDA_CHECK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(WALK_THREADS), args, 0, c->stream));
     c->launches++;
 }
 
