@@ -49,6 +49,7 @@ void dalloc(T *&p, size_t count) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * count);
     if (e != cudaSuccess) {
         p = nullptr;
+        cudaGetLastError();   // (the failure is reported here; a later check must not see it again)
         throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
     }
 }
@@ -942,9 +943,11 @@ long long env_int(const char *name, long long dflt, long long lo, long long hi) 
         NCORP_CUDA_CHECK(cudaSetDevice((ctxp)->device));                                        \
         __VA_ARGS__                                                                             \
     } catch (const CudaError &e) {                                                              \
+        cudaGetLastError();   /* a non-sticky error is reported once, by this call */           \
         (ctxp)->have_state = false;                                                             \
         (ctxp)->tree_valid = false;                                                             \
-        return fail((ctxp), NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line); \
+        return fail((ctxp), e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA,   \
+                    "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);       \
     } catch (const std::bad_alloc &) {                                                          \
         return fail((ctxp), NCORP_ENOMEM, "host allocation failed");                             \
     }
@@ -1029,6 +1032,7 @@ int ncorp_init(ncorp_ctx **out, const ncorp_config *cfg, int64_t n_max, int devi
         ensure_both_capacities(c, static_cast<int>(n_max));
         NCORP_CUDA_CHECK(cudaStreamSynchronize(c->stream));   // the clears above, before any other stream's use
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         int code = (e.code == cudaErrorMemoryAllocation) ? NCORP_ENOMEM : NCORP_ECUDA;
         ncorp_free(c);
         return code;
@@ -1613,6 +1617,7 @@ void balloc(double *&p, size_t count) {
     const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(double) * std::max<size_t>(count, 1));
     if (e != cudaSuccess) {
         p = nullptr;
+        cudaGetLastError();   // (the failure is reported here; a later check must not see it again)
         throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
     }
 }
@@ -1833,6 +1838,7 @@ int prime_forest(ncorp_batch *b, Forest &f) {
             }
         }
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         status = fail(c, e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA, "%s: %s (%s:%d)", e.expr,
                       cudaGetErrorString(e.code), e.file, e.line);
     }
@@ -2238,6 +2244,7 @@ int ncorp_batch_add_disk(ncorp_batch *b, const double *positions, const double *
             return batch_fail(b, NCORP_EINVAL, "non-finite position or velocity");
         }
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         if (fresh) free_forest(f);
         return batch_fail(b, e.code == cudaErrorMemoryAllocation ? NCORP_ENOMEM : NCORP_ECUDA, "%s: %s", e.expr,
                           cudaGetErrorString(e.code));
@@ -2336,6 +2343,7 @@ int ncorp_batch_run(ncorp_batch *b, int n_steps) {
         }
         for (int s = 0; s < BATCH_STREAMS; s++) NCORP_CUDA_CHECK(cudaStreamSynchronize(b->pool[s]));
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         for (Forest *f : b->forests) {
             f->primed = false;   // the arrays hold the state at the start of the run at the latest
             f->synced = true;
@@ -2404,6 +2412,7 @@ int ncorp_batch_get_state(ncorp_batch *b, int32_t disk_id, double *positions, do
                                          s));
         NCORP_CUDA_CHECK(cudaStreamSynchronize(s));
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
     }
     return NCORP_OK;
@@ -2506,6 +2515,7 @@ int ncorp_batch_remove_disk(ncorp_batch *b, int32_t disk_id, double *positions, 
             if (own) bfree(tmp);
         }
     } catch (const CudaError &e) {
+        cudaGetLastError();   // (a non-sticky error is reported once, here)
         return batch_fail(b, NCORP_ECUDA, "%s: %s (%s:%d)", e.expr, cudaGetErrorString(e.code), e.file, e.line);
     }
     for (size_t i = 0; i < f->disks.size(); i++)

@@ -550,7 +550,10 @@ void ensure_radix_scratch(ncorp_ctx *c, int n) {
         bump_alloc_generation();
         int *p = nullptr;
         const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(int) * (need + 4096));
-        if (e != cudaSuccess) throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
+        if (e != cudaSuccess) {
+            cudaGetLastError();   // (reported here; a later check must not see it again)
+            throw CudaError(e, "cudaMalloc", __FILE__, __LINE__);
+        }
         c->tile_hist = p;
         // on the context's stream, ordered before the sorts that use it (the legacy stream is not
         // ordered with the non-blocking streams the library is driven on)
