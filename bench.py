@@ -35,10 +35,20 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s, falcON p=6 gravity+collisions; p50/p99 step latency mixed-N"
 UNIT = "particle-steps/s"
-# DRAM bytes (read + write) of one k_eval launch on this workload, from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
-# set to None whenever the kernel changes until it is captured again.
-EVAL_DRAM_BYTES_PER_LAUNCH = 4.41e6
+# DRAM bytes (read + write) of one k_eval launch, from ncu captures of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum, mixed precision, leaf size
+# 64), keyed by (N, p, theta_min); entries are removed whenever the kernel changes,
+# until it is captured again.  Other workloads report null.
+EVAL_DRAM_BYTES_PER_LAUNCH = {
+    (100_000, 6, 0.5): 5.54e6,       # one launch, full section set
+    (1_000_000, 4, 0.6): 50.3e6,     # mean of two launches
+}
+
+
+def eval_traffic(n, p, theta, precision, leaf_size):
+    if precision != "mixed" or leaf_size != 64 or THRESHOLDS_OVERRIDE:
+        return None
+    return EVAL_DRAM_BYTES_PER_LAUNCH.get((n, p, theta))
 
 
 def parse():
@@ -73,6 +83,8 @@ def parse():
     ap.add_argument("--serve-pool", type=int, default=600,
                     help="serving: distinct initial disks (later requests reuse them; 0: one per request)")
     ap.add_argument("--tick-steps", type=int, default=10, help="serving: most steps per ncorp_batch_run")
+    ap.add_argument("--serve-log", default="",
+                    help="serving: file to which the loop appends one JSON line per run and tick (flushed each time)")
     ap.add_argument("--steps4", type=int, default=50, help="default run: steps of the 64-disk ensemble")
     return ap.parse_args()
 
@@ -160,6 +172,11 @@ def leaf_size_for(p):
     return 64 if p >= 4 else 32
 
 
+def leaf_size_of(a, n, p):
+    """Leaf size of a run of N = n at order p: --leaf-size for the main workload, else the default for p."""
+    return a.leaf_size if a.leaf_size > 0 and n == a.n else leaf_size_for(p)
+
+
 THRESHOLDS_OVERRIDE = {}   # p -> [N_cs, N_cc,pre, N_cc,post] given with --thresholds
 
 
@@ -220,7 +237,7 @@ def workload_config(a, n=None, seed=None, p=None, theta=None, precision=None):
     return {"workload": f"1 disk x {n} moonlets per GPU (seed {seed}+rank), falcON p={p} theta_min={theta}, "
                         f"SBAB1 step dt={a.dt} with tree collision search{res}, {precision} precision",
             "n_per_gpu": n, "p": p, "theta_min": theta, "dt": a.dt,
-            "leaf_size": a.leaf_size if a.leaf_size > 0 and n == a.n else leaf_size_for(p),
+            "leaf_size": leaf_size_of(a, n, p),
             "gravity_thresholds": thresholds_for(p), "collision_thresholds": [12, 0, 16],
             "precision": precision, "l2": "flushed by a 256 MiB device write before every timed step",
             "parallelism": "replicas (one independent disk per GPU)",
@@ -307,7 +324,7 @@ def time_disk(a, ncorp, torch, ctx_args, d, n, p, theta, precision, steps, warmu
     per-step times, counters of the last step, summed launches and the stage times per step."""
     cfg = ncorp.ncorp_config_default()
     cfg.precision = ncorp.NCORP_MIXED if precision == "mixed" else ncorp.NCORP_FP64
-    cfg.leaf_size = a.leaf_size if a.leaf_size > 0 and n == a.n else leaf_size_for(p)
+    cfg.leaf_size = leaf_size_of(a, n, p)
     cfg.n_cs, cfg.n_cc_pre, cfg.n_cc_post = thresholds_for(p)
     cfg.c_cs, cfg.c_cc_pre, cfg.c_cc_post = 12, 0, 16
     cfg.resolve_f = a.resolve_f
@@ -436,7 +453,7 @@ def run_gpu(a):
     t = time_disk(a, ncorp, torch, ctx_args, d, a.n, a.p, a.theta, a.precision, a.steps, a.warmup,
                   min(a.steps, 10), local, stream, flush)
     head = summarize(a, t, a.n, a.steps, world, dist, hbm, peak, a.p)
-    roofline = near_roofline(t, peak, a.precision, EVAL_DRAM_BYTES_PER_LAUNCH if a.precision == "mixed" else None)
+    roofline = near_roofline(t, peak, a.precision, eval_traffic(a.n, a.p, a.theta, a.precision, leaf_size_of(a, a.n, a.p)))
 
     extra = {}
     if not a.headline_only:
@@ -455,7 +472,8 @@ def run_gpu(a):
         t3 = time_disk(a, ncorp, torch, ctx_args, d3, n3, 4, 0.6, "mixed", a.steps3, 3, 5, local, stream, flush)
         extra["config3"] = {"config": workload_config(a, n=n3, seed=3, p=4, theta=0.6, precision="mixed"),
                             **summarize(a, t3, n3, a.steps3, world, dist, hbm, peaks["fp32_tflops"], 4),
-                            "roofline": near_roofline(t3, peaks["fp32_tflops"], "mixed", None)}
+                            "roofline": near_roofline(t3, peaks["fp32_tflops"], "mixed",
+                                                      eval_traffic(n3, 4, 0.6, "mixed", leaf_size_of(a, n3, 4)))}
         # ---- workload 4: 64 disks of mixed size in one batch, 50 steps replayed from one graph
         extra["config4"] = time_ensemble(a, ncorp, torch, dist, world, rank, stream, a.steps4, 3)
     clocks = sampler.stop()
@@ -738,15 +756,24 @@ def run_serving(a):
     free_b, _ = torch.cuda.mem_get_info()
     budget = int(a.serve_budget * free_b)
     b = ncorp.ncorp_batch_create(cfg, budget, stream.cuda_stream)   # admission: a fraction of free HBM
+    log = open(a.serve_log, "a") if a.serve_log else None
+
+    def progress(state):
+        log.write(json.dumps(state) + "\n")
+        log.flush()
+
     sampler = ClockSampler(physical_gpu_index(local))
     try:
         # each finished disk's state goes back to host memory (what a client receives)
         backend = serving.BatchBackend(ncorp, b, a.theta, a.dt)
         st = serving.serve(backend, reqs, tick_steps=a.tick_steps,
-                           on_done=lambda r: (np.empty((r.n, 3)), np.empty((r.n, 3))))
+                           on_done=lambda r: (np.empty((r.n, 3)), np.empty((r.n, 3))),
+                           progress=progress if log else None)
     finally:
         clocks = sampler.stop()
         ncorp.ncorp_batch_free(b)
+        if log:
+            log.close()
     offered = sum(r.n for r in reqs) * 100 / a.serve_seconds
     served_n = sum(r.n for r in reqs if r.done is not None)
     value = slowest_rank(dist, st["throughput"], world) if world > 1 else st["throughput"]

@@ -98,11 +98,14 @@ class BatchBackend:
 
 
 def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.sleep, on_done=None,
-          max_wall=None):
+          max_wall=None, progress=None):
     """Runs the requests (sorted by arrival) to completion; returns the statistics (see the module doc).
 
     on_done(req) -> None or (positions, velocities) arrays for the finished disk's final state.
-    max_wall (seconds): stop admitting new requests after this time (the admitted ones finish)."""
+    max_wall (seconds): stop admitting new requests after this time (the admitted ones finish).
+    progress(dict) is called before every run and after every tick with the loop's state (elapsed s, event,
+    ticks, steps k, resident disks and moonlets, waiting and served counts), so that a log written from
+    it shows where a run that was cut off from outside stood."""
     reqs = sorted(requests, key=lambda r: r.arrival)
     waiting = collections.deque(reqs)
     active: dict[int, Request] = {}
@@ -139,6 +142,8 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
         k = min(tick_steps, min(r.steps_left for r in active.values()))
         t0 = clock()
         while True:
+            if progress:
+                progress(_state("run", t0 - start, ticks, k, active, waiting, reqs))
             try:
                 backend.run(k)
                 break
@@ -175,8 +180,16 @@ def serve(backend, requests, tick_steps=10, clock=time.perf_counter, sleep=time.
                 backend.finish(r, out)
                 del active[did]
                 hold = False
+        if progress:
+            progress(_state("tick", t1 - start, ticks, k, active, waiting, reqs))
     wall = clock() - start
     return summarize(reqs, ticks, step_ms, concurrent, wall)
+
+
+def _state(event, t, ticks, k, active, waiting, reqs):
+    return {"t": round(t, 3), "event": event, "ticks": len(ticks), "k": k, "disks": len(active),
+            "moonlets": sum(r.n for r in active.values()), "waiting": len(waiting),
+            "served": sum(1 for r in reqs if r.done is not None)}
 
 
 def _pct(values, q, weights=None):

@@ -17,3 +17,13 @@ def test_direct_sample_errors_uses_the_direct_sum():
     bumped = ref + 1e-6 * np.linalg.norm(ref, axis=1)[:, None] * np.array([1.0, 0.0, 0.0])
     e = bench.direct_sample_errors(d["pos"], d["mass"], bumped, k=500)
     assert abs(e["median"] - 1e-6) < 1e-9 and abs(e["p99"] - 1e-6) < 1e-9
+
+
+def test_eval_traffic_only_for_captured_workloads():
+    import bench
+    assert bench.eval_traffic(100_000, 6, 0.5, "mixed", 64) == bench.EVAL_DRAM_BYTES_PER_LAUNCH[(100_000, 6, 0.5)]
+    assert bench.eval_traffic(1_000_000, 4, 0.6, "mixed", 64) is not None
+    # another precision, leaf size or workload has no capture behind it
+    assert bench.eval_traffic(100_000, 6, 0.5, "fp64", 64) is None
+    assert bench.eval_traffic(100_000, 6, 0.5, "mixed", 32) is None
+    assert bench.eval_traffic(200_000, 6, 0.5, "mixed", 64) is None

@@ -161,3 +161,13 @@ def test_a_disk_that_no_run_fits_is_an_error():
     fb = TightBatch(clock, run_limit=10)
     with pytest.raises(RuntimeError, match="on its own"):
         serving.serve(fb, [serving.Request(arrival=0.0, n=1000, p=3, steps=5)], clock=clock, sleep=clock.sleep)
+
+
+def test_progress_reports_every_run_and_tick():
+    reqs = [serving.Request(arrival=0.0, n=1000, p=3, steps=20), serving.Request(arrival=0.5, n=1000, p=3, steps=10)]
+    clock, seen = Clock(), []
+    fb = FakeBatch(clock, step_s=lambda moonlets: 0.1)
+    serving.serve(fb, reqs, tick_steps=10, clock=clock, sleep=clock.sleep, progress=seen.append)
+    assert [s["event"] for s in seen] == ["run", "tick", "run", "tick"]
+    assert [s["disks"] for s in seen] == [1, 1, 2, 0] and seen[-1]["served"] == 2
+    assert seen[1]["t"] == pytest.approx(1.0) and seen[2]["moonlets"] == 2000 and seen[-1]["ticks"] == 2
