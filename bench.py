@@ -38,11 +38,10 @@ UNIT = "particle-steps/s"
 # DRAM bytes (read + write) of one k_eval launch, from ncu captures of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum, mixed precision, leaf size
 # 64), keyed by (N, p, theta_min); entries are removed whenever the kernel changes,
-# until it is captured again.  Other workloads report null.
-EVAL_DRAM_BYTES_PER_LAUNCH = {
-    (100_000, 6, 0.5): 5.54e6,       # one launch, full section set
-    (1_000_000, 4, 0.6): 50.3e6,     # mean of two launches
-}
+# until it is captured again.  Other workloads report null.  Empty: the captures
+# (5.54e6 at N = 1e5, p = 6; 50.3e6 at N = 1e6, p = 4) were taken with the kernel
+# at eight blocks per SM, before its launch bound became six.
+EVAL_DRAM_BYTES_PER_LAUNCH = {}
 
 
 def eval_traffic(n, p, theta, precision, leaf_size):

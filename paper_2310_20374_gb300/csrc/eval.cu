@@ -343,7 +343,7 @@ struct EvShared {
 };
 
 template <int P, typename real>
-__global__ void __launch_bounds__(EV_THREADS, 8) k_eval(EvalArgs A) {
+__global__ void __launch_bounds__(EV_THREADS, 6) k_eval(EvalArgs A) {
     constexpr bool f32 = std::is_same<real, float>::value;
     __shared__ EvShared<P, real> S;
     if (aborted(A.ctl)) return;

@@ -19,10 +19,11 @@ def test_direct_sample_errors_uses_the_direct_sum():
     assert abs(e["median"] - 1e-6) < 1e-9 and abs(e["p99"] - 1e-6) < 1e-9
 
 
-def test_eval_traffic_only_for_captured_workloads():
+def test_eval_traffic_only_for_captured_workloads(monkeypatch):
     import bench
-    assert bench.eval_traffic(100_000, 6, 0.5, "mixed", 64) == bench.EVAL_DRAM_BYTES_PER_LAUNCH[(100_000, 6, 0.5)]
-    assert bench.eval_traffic(1_000_000, 4, 0.6, "mixed", 64) is not None
+    monkeypatch.setattr(bench, "EVAL_DRAM_BYTES_PER_LAUNCH", {(100_000, 6, 0.5): 5.5e6, (1_000_000, 4, 0.6): 5e7})
+    assert bench.eval_traffic(100_000, 6, 0.5, "mixed", 64) == 5.5e6
+    assert bench.eval_traffic(1_000_000, 4, 0.6, "mixed", 64) == 5e7
     # another precision, leaf size or workload has no capture behind it
     assert bench.eval_traffic(100_000, 6, 0.5, "fp64", 64) is None
     assert bench.eval_traffic(100_000, 6, 0.5, "mixed", 32) is None
