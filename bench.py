@@ -739,7 +739,9 @@ def run_serving(a):
     """Serving (continuous batching): disks arrive as a Poisson stream (rate r per s over the window), N
     log-uniform in [1e3, 1e6], p uniform in {3, 4, 6}, theta_min = 0.5, each integrated for 100 steps; the loop
     of paper_2310_20374_gb300.serving admits arrived requests in order while the batch's memory budget allows
-    and advances every resident disk by up to --tick-steps steps per ncorp_batch_run."""
+    and advances every resident disk by up to --tick-steps steps per ncorp_batch_run.  The run lasts the
+    arrival window: admission stops at its end (requests still queued then are reported as not admitted), and
+    the disks already admitted are integrated to the end of their steps."""
     torch, dist, ncorp, cfg, rank, world, local = batch_common(a)
     from paper_2310_20374_gb300 import diskgen, serving
     reqs = serving.poisson_requests(a.serve_rate, a.serve_seconds, 1e3, 1e6, (3, 4, 6), 100, seed=500 + rank)
@@ -767,7 +769,7 @@ def run_serving(a):
         backend = serving.BatchBackend(ncorp, b, a.theta, a.dt)
         st = serving.serve(backend, reqs, tick_steps=a.tick_steps,
                            on_done=lambda r: (np.empty((r.n, 3)), np.empty((r.n, 3))),
-                           progress=progress if log else None)
+                           progress=progress if log else None, max_wall=a.serve_seconds)
     finally:
         clocks = sampler.stop()
         ncorp.ncorp_batch_free(b)
@@ -785,7 +787,8 @@ def run_serving(a):
                                   f"[1e3, 1e6], p in {{3,4,6}}, "
                                   f"theta_min={a.theta}, 100 SBAB1 steps each, dt={a.dt}, {a.precision} precision, "
                                   f"up to {a.tick_steps} steps per tick",
-                      "requests": st["requests"], "served": st["served"], "moonlet_steps": st["moonlet_steps"],
+                      "requests": st["requests"], "served": st["served"],
+                      "not_admitted": st["requests"] - st["served"], "moonlet_steps": st["moonlet_steps"],
                       "parallelism": "replicas (one serving loop per GPU)"},
            "latency": {
                "step_ms_p50": st["step_ms_p50"], "step_ms_p99": st["step_ms_p99"],
@@ -793,7 +796,8 @@ def run_serving(a):
                "request_s_p50": st["request_s_p50"], "request_s_p99": st["request_s_p99"],
                "admission_wait_s_p50": st["admission_wait_s_p50"], "admission_wait_s_p99": st["admission_wait_s_p99"],
                "note": "host wall times: step = one tick (one ncorp_batch_run of k steps over every resident disk) "
-                       "/ k, one sample per disk and step; request = arrival to last step, admission wait included"},
+                       "/ k, one sample per disk and step; request = arrival to last step, admission wait included; "
+                       "request and admission figures cover the requests admitted within the window"},
            "peak_batch_bytes": getattr(backend, "peak_bytes", None),
            "peak_resident_moonlets": getattr(backend, "peak_moonlets", None),
            "hbm_budget_bytes": budget,
