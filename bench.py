@@ -576,7 +576,7 @@ def _oracle_step_worker(args):
 
 def cpu_baseline(a, cfgd, d):
     """The oracle as it stands on this host: one SBAB1 step of the same disk on one core, and one step of an
-    independent disk per core at once (the all-core figure: disks one per core, SURVEY's CPU baseline)."""
+    independent disk per core at once (the all-core figure: disks one per core, one oracle process each)."""
     import multiprocessing as mp
 
     import oracle
