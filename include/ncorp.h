@@ -471,9 +471,9 @@ int ncorp_fma_peak(int device, int precision, void *cuda_stream, double *flop_pe
  * reports after ncorp_accel on the same positions.
  * Scratch: one file-scope device array per device, sized for
  * NCORP_STATIC_MAX_N moonlets (about 3.4 MB); nothing is allocated or freed.
- * The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins on the device.
+ * The call synchronises its stream to read the status word, so it cannot be
+ * part of a CUDA graph capture.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current.
  * The array keeps the contents of the last call; each call first resets the
  * parts that must start at zero (bounding-box accumulators, status word,
  * barrier counter) and overwrites everything else before reading it.
