@@ -71,3 +71,12 @@ def test_near_roofline_counts_unordered_pairs():
 def test_host_cores_reports_nproc():
     h = bench.host_cores()
     assert h["nproc"] == os.cpu_count()
+
+
+def test_collision_prefilter_against_the_fp32_peak(monkeypatch):
+    # the pair test's prefilters run in FP32 in both precisions: its stage takes the FP32 peak even when the
+    # near field and M2L (FP64 form) take the FP64 one
+    monkeypatch.setattr(bench, "FP32_PEAK_TFLOPS", 78.0)
+    out = bench.stage_rooflines(STAGES, 100_000, 6, 137_116, 57_122_097, 22_217_601, 6777.6, 1.25)
+    assert out["collide"]["peak"] == 78.0 and out["near"]["peak"] == 1.25 and out["m2l"]["peak"] == 1.25
+    assert out["collide"]["frac"] == pytest.approx(out["collide"]["achieved"] / 78.0, abs=1e-4)
